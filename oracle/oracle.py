@@ -1,0 +1,153 @@
+"""ctypes binding of the FP64 CPU UGKS oracle (ugks_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the bench's CPU-baseline leg
+use it; the product path never imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "ugks_oracle.c")
+LIB = os.path.join(HERE, "libugks_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over faces and cells)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "ugks_oracle.h"))):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                               "-fopenmp", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int), ("umin", C.c_double), ("umax", C.c_double),
+                ("vmin", C.c_double), ("vmax", C.c_double), ("K", C.c_int),
+                ("kn", C.c_double), ("omega", C.c_double), ("alpha", C.c_double),
+                ("cfl", C.c_double), ("dt", C.c_double), ("bc_kind", C.c_int * 4),
+                ("bc_rho", C.c_double * 4), ("bc_T", C.c_double * 4), ("bc_U", C.c_double * 4)]
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        L.orc_dt.restype = C.c_double
+        L.orc_tau.restype = C.c_double
+        L.orc_get_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _cfg(cfg) -> _Cfg:
+    c = _Cfg()
+    for k in ("nx", "ny", "nu", "nv", "K"):
+        setattr(c, k, int(getattr(cfg, k)))
+    for k in ("lx", "ly", "umin", "umax", "vmin", "vmax", "kn", "omega", "alpha", "cfl", "dt"):
+        setattr(c, k, float(getattr(cfg, k)))
+    for s in range(4):
+        c.bc_kind[s] = int(cfg.bc[s].kind)
+        c.bc_rho[s] = float(cfg.bc[s].rho)
+        c.bc_T[s] = float(cfg.bc[s].T)
+        c.bc_U[s] = float(cfg.bc[s].U)
+    return c
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def vgrid(cfg):
+    u = np.empty(cfg.nu)
+    v = np.empty(cfg.nv)
+    w = np.empty(cfg.nu * cfg.nv)
+    lib().orc_vgrid(C.byref(_cfg(cfg)), _p(u), _p(v), _p(w))
+    return u, v, w
+
+
+def dt(cfg) -> float:
+    return lib().orc_dt(C.byref(_cfg(cfg)))
+
+
+def tau(cfg, rho: float, lam: float) -> float:
+    return lib().orc_tau(C.byref(_cfg(cfg)), C.c_double(rho), C.c_double(lam))
+
+
+def mt(dt_: float, tau_: float) -> np.ndarray:
+    out = np.empty(5)
+    lib().orc_mt(C.c_double(dt_), C.c_double(tau_), _p(out))
+    return out
+
+
+def gauss_moments(U: float, lam: float, nmax: int):
+    full, pos, neg = (np.empty(nmax + 1) for _ in range(3))
+    lib().orc_gauss_moments(C.c_double(U), C.c_double(lam), C.c_int(nmax), _p(full), _p(pos),
+                            _p(neg))
+    return full, pos, neg
+
+
+def slope_solve(prim, K: int, s) -> np.ndarray:
+    prim = np.ascontiguousarray(prim, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    a = np.empty(4)
+    lib().orc_slope_solve(_p(prim), C.c_int(K), _p(s), _p(a))
+    return a
+
+
+def init_maxwellian(cfg, rho, U, V, T):
+    """Pointwise Maxwellian f[nc][nq][2] and analytic W[4][nc] from primitive fields."""
+    f = np.empty((cfg.nc, cfg.nq, 2))
+    W = np.empty((4, cfg.nc))
+    arr = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, U, V, T)]
+    lib().orc_init_maxwellian(C.byref(_cfg(cfg)), *[_p(x) for x in arr], _p(f), _p(W))
+    return f, W
+
+
+def fluxes(cfg, f, W):
+    nfx = (cfg.nx + 1) * cfg.ny
+    nfy = cfg.nx * (cfg.ny + 1)
+    Fx = np.empty((nfx, 4))
+    Fy = np.empty((nfy, 4))
+    fx = np.empty((nfx, cfg.nq, 2))
+    fy = np.empty((nfy, cfg.nq, 2))
+    lib().orc_fluxes(C.byref(_cfg(cfg)), _p(np.ascontiguousarray(f)),
+                     _p(np.ascontiguousarray(W)), _p(Fx), _p(Fy), _p(fx), _p(fy))
+    return Fx, Fy, fx, fy
+
+
+def step(cfg, f, W, nsteps: int = 1):
+    """nsteps UGKS steps; returns new (f, W) (inputs untouched)."""
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    W = np.array(W, dtype=np.float64, order="C", copy=True)
+    lib().orc_step(C.byref(_cfg(cfg)), _p(f), _p(W), C.c_int(nsteps))
+    return f, W
+
+
+def step_cells(cfg, f, W, ids):
+    """One step for the listed cells only: (f_out[n][nq][2], W_out[n][4])."""
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    n = len(ids)
+    fo = np.empty((n, cfg.nq, 2))
+    Wo = np.empty((n, 4))
+    lib().orc_step_cells(C.byref(_cfg(cfg)), _p(np.ascontiguousarray(f)),
+                         _p(np.ascontiguousarray(W)), C.c_int(n),
+                         ids.ctypes.data_as(C.POINTER(C.c_int)), _p(fo), _p(Wo))
+    return fo, Wo

@@ -1,0 +1,326 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+high-precision quadrature, invariants of the scheme, exact special cases, or an
+independent brute-force evaluation of the integral solution (Eq. 2) on a tiny mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1810_08137_gb300 import inputs as I
+from tests import bruteforce as BF
+
+
+def periodic_cfg(**kw):
+    base = dict(nx=4, ny=4, lx=1.0, ly=1.0, nu=5, nv=5, umin=-3.0, umax=3.0, vmin=-3.0,
+                vmax=3.0, K=1, kn=0.05, bc=[I.BC(I.BC_PERIODIC)] * 4)
+    base.update(kw)
+    return I.Config(**base)
+
+
+def random_state(oracle, cfg, seed, amp=0.2, flow=0.3):
+    """Non-equilibrium state: Maxwellians with random (rho, U, V, T) per cell, times
+    random factors 1 +- amp per velocity and component; W from the same primitives."""
+    r = I.uniform01(seed, 4 * cfg.nc).reshape(4, cfg.nc)
+    rho = 0.8 + 0.4 * r[0]
+    U = flow * (2 * r[1] - 1)
+    V = flow * (2 * r[2] - 1)
+    T = 0.8 + 0.4 * r[3]
+    f, W = oracle.init_maxwellian(cfg, rho, U, V, T)
+    f = f * I.perturbation(seed + 1, f.shape, amp)
+    return f, W
+
+
+def quad_scale(a, b):
+    return np.max(np.abs(b)) + 1e-300
+
+
+# ---------------------------------------------------------------------------------
+# Maxwellian moments (Eq. 1) on the discrete velocity grid
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("vr,n,tol", [(4.0, 20, 2e-5), (4.0, 28, 2e-5), (10.0, 64, 1e-13)])
+@pytest.mark.parametrize("K", [0, 1, 2])
+def test_maxwellian_discrete_moments_match_closed_forms(oracle, vr, n, tol, K):
+    cfg = periodic_cfg(nx=1, ny=1, nu=n, nv=n, umin=-vr, umax=vr, vmin=-vr, vmax=vr, K=K)
+    rho, U, V, T = 1.3, 0.3, -0.2, 1.1
+    f, W = oracle.init_maxwellian(cfg, [rho], [U], [V], [T])
+    u, v, w = oracle.vgrid(cfg)
+    uq, vq = np.tile(u, n), np.repeat(v, n)
+    h, b = f[0, :, 0], f[0, :, 1]
+    disc = np.array([np.sum(w * h), np.sum(w * uq * h), np.sum(w * vq * h),
+                     np.sum(w * (0.5 * (uq ** 2 + vq ** 2) * h + 0.5 * b))])
+    # closed forms: rho, rho U, rho V, rho (|U|^2/2 + (K+2) T / 4)
+    closed = np.array([rho, rho * U, rho * V, rho * (0.5 * (U * U + V * V) + (K + 2) * T / 4)])
+    assert np.max(np.abs(disc - closed) / np.abs(closed).max()) < tol
+    assert np.allclose(W[:, 0], closed, rtol=1e-15, atol=1e-15)
+
+
+def test_velocity_grid_trapezoid_and_symmetric(oracle):
+    cfg = periodic_cfg(nu=7, nv=6, umin=-3, umax=3, vmin=-2, vmax=2)
+    u, v, w = oracle.vgrid(cfg)
+    assert np.array_equal(u, -u[::-1]) and np.array_equal(v, -v[::-1])
+    assert np.allclose(u, np.linspace(-3, 3, 7), atol=1e-15)
+    assert abs(w.sum() - 6 * 4) < 1e-13  # trapezoid integrates 1 exactly over the box
+    assert abs(w.reshape(6, 7)[0, 0] - 0.25 * 1.0 * 0.8) < 1e-15
+
+
+# ---------------------------------------------------------------------------------
+# S2: half-range Gaussian moments against Gauss-Legendre quadrature on half lines
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("U,lam", [(0.0, 1.0), (0.7, 2.0), (-1.3, 0.5), (2.5, 1.0), (-4.0, 3.0)])
+def test_half_range_moments_against_quadrature(oracle, U, lam):
+    full, pos, neg = oracle.gauss_moments(U, lam, 9)
+    sig = 1 / math.sqrt(2 * lam)
+    L = abs(U) + 16 * sig
+    x, wx = np.polynomial.legendre.leggauss(300)
+    xp, wp = (x + 1) / 2 * L, wx * L / 2
+    g = lambda y: math.sqrt(lam / math.pi) * np.exp(-lam * (y - U) ** 2)
+    for n in range(10):
+        p = np.sum(wp * g(xp) * xp ** n)
+        m = np.sum(wp * g(-xp) * (-xp) ** n)
+        scale = max(1.0, (abs(U) + 3 * sig) ** n)
+        assert abs(pos[n] - p) < 1e-13 * scale
+        assert abs(neg[n] - m) < 1e-13 * scale
+        assert abs(full[n] - (p + m)) < 1e-13 * scale
+
+
+# ---------------------------------------------------------------------------------
+# S3: Mt1..Mt5 are the time integrals of the Eq. 2 weights (high-precision quadrature)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("x", [1e-9, 1e-4, 0.01, 0.0999, 0.1, 0.1001, 0.5, 1.0, 5.0, 50.0, 600.0])
+def test_mt_against_time_quadrature(oracle, x):
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    dt = 0.37
+    tau = dt / x
+    Mt = oracle.mt(dt, tau)
+    T = mpmath.mpf(dt)
+    ta = mpmath.mpf(dt) / mpmath.mpf(x)
+    e = lambda t: mpmath.exp(-t / ta)
+    ref = [mpmath.quad(lambda t: 1 - e(t), [0, T]),
+           mpmath.quad(lambda t: ta * (e(t) - 1) + t * e(t), [0, T]),
+           mpmath.quad(lambda t: t - ta + ta * e(t), [0, T]),
+           mpmath.quad(lambda t: e(t), [0, T]),
+           mpmath.quad(lambda t: t * e(t), [0, T])]
+    scale = [dt, dt * dt, dt * dt, dt, dt * dt]
+    for i in range(5):
+        assert abs(Mt[i] - float(ref[i])) <= 2e-14 * scale[i], (i, Mt[i], float(ref[i]))
+
+
+def test_mt_limits(oracle):
+    dt = 0.2
+    Mt = oracle.mt(dt, 1e12)  # collisionless: tau -> infinity
+    assert np.allclose(Mt, [0, 0, 0, dt, dt * dt / 2], atol=1e-12)
+    Mt = oracle.mt(dt, 1e-12)  # continuum: tau -> 0
+    assert np.allclose(Mt, [dt, 0, dt * dt / 2, 0, 0], atol=1e-11)
+
+
+# ---------------------------------------------------------------------------------
+# S4: micro-slope solve reproduces the prescribed moments (Gauss-Hermite quadrature)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [0, 1, 2])
+def test_slope_solve_reproduces_moments(oracle, K):
+    r = I.uniform01(77 + K, 40).reshape(5, 8)
+    for t in range(5):
+        U, V, lam = 2 * r[t, 0] - 1, 2 * r[t, 1] - 1, 0.5 + 2 * r[t, 2]
+        s = 4 * r[t, 3:7] - 2
+        a = oracle.slope_solve([1.0, U, V, lam], K, s)
+        xh, wh = np.polynomial.hermite.hermgauss(12)
+        nodes = [U + xh / math.sqrt(lam), V + xh / math.sqrt(lam)] + [xh / math.sqrt(lam)] * K
+        grids = np.meshgrid(*nodes, indexing="ij")
+        wg = np.prod(np.meshgrid(*([wh / math.sqrt(math.pi)] * (2 + K)), indexing="ij"), axis=0)
+        u, v = grids[0], grids[1]
+        xi2 = sum(g ** 2 for g in grids[2:]) if K else 0.0
+        E = 0.5 * (u ** 2 + v ** 2 + xi2)
+        ap = a[0] + a[1] * u + a[2] * v + a[3] * E
+        mom = [np.sum(wg * ap * p) for p in (1.0, u, v, E)]
+        assert np.allclose(mom, s, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------
+# Whole-step invariants
+# ---------------------------------------------------------------------------------
+def test_uniform_maxwellian_preserved_periodic(oracle):
+    cfg = periodic_cfg(nx=6, ny=5, nu=12, nv=12, umin=-5, umax=5, vmin=-5, vmax=5)
+    n = cfg.nc
+    f, W = oracle.init_maxwellian(cfg, np.full(n, 1.1), np.full(n, 0.3), np.full(n, -0.2),
+                                  np.full(n, 0.9))
+    f1, W1 = oracle.step(cfg, f, W, 3)
+    assert np.max(np.abs(W1 - W)) <= 1e-15 * np.max(np.abs(W)) * 4
+    assert np.max(np.abs(f1 - f)) <= 2e-15 * np.max(np.abs(f))
+
+
+def test_uniform_rest_state_preserved_channel(oracle):
+    """Gas at rest with T = T_wall and equal inlet/outlet density: the channel is in
+    equilibrium; on a grid wide and fine enough that the discrete moments are exact to
+    rounding, it stays so to rounding."""
+    cfg = I.channel_config(nx=6, ny=4, n_vel=40, vrange=9.0, kn=0.1, rho_in=1.0, rho_out=1.0)
+    n = cfg.nc
+    f, W = oracle.init_maxwellian(cfg, np.ones(n), np.zeros(n), np.zeros(n), np.ones(n))
+    f1, W1 = oracle.step(cfg, f, W, 3)
+    assert np.max(np.abs(W1 - W)) <= 1e-13
+    assert np.max(np.abs(f1 - f)) <= 1e-13 * np.max(np.abs(f))
+
+
+def test_periodic_conservation(oracle):
+    cfg = periodic_cfg(nx=7, ny=5, nu=10, nv=10, umin=-5, umax=5, vmin=-5, vmax=5, kn=0.02)
+    f, W = random_state(oracle, cfg, 31)
+    tot0 = W.sum(axis=1)
+    f1, W1 = oracle.step(cfg, f, W, 4)
+    tot1 = W1.sum(axis=1)
+    assert np.max(np.abs(tot1 - tot0)) <= 1e-14 * cfg.nc * np.max(np.abs(W))
+    assert not np.allclose(W1, W)  # the state did evolve
+
+
+@pytest.mark.parametrize("K", [0, 1])
+def test_collisionless_exact_shift(oracle, K):
+    """tau -> infinity, velocities on {-1,0,1}^2, u dt = dx = dy: the axis-aligned
+    velocities shift by exactly one cell per step (free transport of Eq. 1, Eq. 2 with
+    the e^{-t/tau} -> 1 term only)."""
+    nx = ny = 8
+    cfg = periodic_cfg(nx=nx, ny=ny, nu=3, nv=3, umin=-1, umax=1, vmin=-1, vmax=1, K=K,
+                       kn=1e250, dt=0.125)
+    f, W = random_state(oracle, cfg, 5, amp=0.5)
+    f1, _ = oracle.step(cfg, f, W, 1)
+    F = f.reshape(ny, nx, 3, 3, 2)   # [j][i][m][k][comp]
+    G = f1.reshape(ny, nx, 3, 3, 2)
+    tol = 1e-14 * np.max(np.abs(f))
+    assert np.max(np.abs(G[:, :, 1, 2] - np.roll(F[:, :, 1, 2], 1, axis=1))) < tol   # u=+1
+    assert np.max(np.abs(G[:, :, 1, 0] - np.roll(F[:, :, 1, 0], -1, axis=1))) < tol  # u=-1
+    assert np.max(np.abs(G[:, :, 2, 1] - np.roll(F[:, :, 2, 1], 1, axis=0))) < tol   # v=+1
+    assert np.max(np.abs(G[:, :, 0, 1] - np.roll(F[:, :, 0, 1], -1, axis=0))) < tol  # v=-1
+    assert np.max(np.abs(G[:, :, 1, 1] - F[:, :, 1, 1])) < tol                       # rest
+
+
+def test_collisionless_half_cell_van_leer(oracle):
+    """Collisionless transport at u dt = dx/2 on a periodic row: the textbook MUSCL
+    update with van Leer slopes, f_i - nu (f_i - f_{i-1}) - nu(1-nu)/2 dx (s_i - s_{i-1})."""
+    nx = 12
+    cfg = periodic_cfg(nx=nx, ny=1, lx=1.2, ly=1.0, nu=1, nv=1, umin=1.0, umax=1.0, vmin=0.0,
+                       vmax=0.0, kn=1e250, dt=0.05)
+    r = I.uniform01(9, nx * 2)
+    f = np.zeros((nx, 1, 2))
+    f[:, 0, 0] = 3 + np.cumsum(np.where(r[:nx] > 0.3, 1.0, -2.0) * r[nx:])  # mixed extrema
+    f[:, 0, 1] = 0.5 + 0.1 * r[:nx]
+    W = np.tile(np.array([[3.0], [0.0], [0.0], [50.0]]), (1, nx))  # only f matters here
+    f1, _ = oracle.step(cfg, f, W, 1)
+    dx, nu_ = 0.1, 0.5
+    for c in range(2):
+        g = f[:, 0, c]
+        s1 = (g - np.roll(g, 1)) / dx
+        s2 = (np.roll(g, -1) - g) / dx
+        s = np.where(s1 * s2 > 0, 2 * s1 * s2 / np.where(s1 + s2 == 0, 1, s1 + s2), 0.0)
+        ref = g - nu_ * (g - np.roll(g, 1)) - nu_ * (1 - nu_) / 2 * dx * (s - np.roll(s, 1))
+        assert np.max(np.abs(f1[:, 0, c] - ref)) < 1e-14 * np.max(np.abs(g))
+
+
+def test_channel_mirror_symmetry(oracle):
+    cfg = I.channel_config(nx=10, ny=6, n_vel=12, kn=0.1)
+    rho, U, V, T = I.initial_prim(cfg, I.seed_for(1), mirror_y=True)
+    f, W = oracle.init_maxwellian(cfg, rho, U, V, T)
+    f1, W1 = oracle.step(cfg, f, W, 20)
+    Wg = W1.reshape(4, cfg.ny, cfg.nx)
+    scale = np.max(np.abs(Wg), axis=(1, 2))
+    assert np.max(np.abs(Wg[0] - Wg[0, ::-1])) < 1e-13 * scale[0]
+    assert np.max(np.abs(Wg[1] - Wg[1, ::-1])) < 1e-13 * scale[1]
+    assert np.max(np.abs(Wg[2] + Wg[2, ::-1])) < 1e-12 * scale[1]
+    assert np.max(np.abs(Wg[3] - Wg[3, ::-1])) < 1e-13 * scale[3]
+    assert scale[1] > 1e-3  # flow developed
+
+
+# ---------------------------------------------------------------------------------
+# Brute force on tiny meshes: the literal integral solution, quadrature everywhere
+# ---------------------------------------------------------------------------------
+def _compare_fluxes(oracle, cfg, f, W):
+    dt = oracle.dt(cfg)
+    Fx, Fy, fx, fy = oracle.fluxes(cfg, f, W)
+    bx, by, bfx, bfy = BF.fluxes(cfg, dt, f, W)
+    sF = max(np.max(np.abs(bx)), np.max(np.abs(by)))
+    sf = max(np.max(np.abs(bfx)), np.max(np.abs(bfy)))
+    assert np.max(np.abs(Fx - bx)) < 1e-11 * sF
+    assert np.max(np.abs(Fy - by)) < 1e-11 * sF
+    assert np.max(np.abs(fx - bfx)) < 1e-11 * sf
+    assert np.max(np.abs(fy - bfy)) < 1e-11 * sf
+
+
+@pytest.mark.parametrize("kn", [0.005, 0.1, 2.0])
+def test_bruteforce_periodic_4x4(oracle, kn):
+    cfg = periodic_cfg(nu=5, nv=4, kn=kn)
+    f, W = random_state(oracle, cfg, 11)
+    _compare_fluxes(oracle, cfg, f, W)
+
+
+@pytest.mark.parametrize("K", [0, 2])
+def test_bruteforce_periodic_internal_dof(oracle, K):
+    cfg = periodic_cfg(nu=4, nv=5, K=K, kn=0.3)
+    f, W = random_state(oracle, cfg, 12)
+    _compare_fluxes(oracle, cfg, f, W)
+
+
+def test_bruteforce_channel_4x4(oracle):
+    cfg = I.channel_config(nx=4, ny=4, n_vel=5, vrange=3.0, kn=0.1)
+    cfg.bc[2] = I.BC(I.BC_WALL, T=1.2, U=0.1)
+    f, W = random_state(oracle, cfg, 13, flow=0.2)
+    _compare_fluxes(oracle, cfg, f, W)
+
+
+def test_wall_zero_net_mass_flux(oracle):
+    cfg = I.channel_config(nx=5, ny=3, n_vel=9, kn=0.1)
+    f, W = random_state(oracle, cfg, 14)
+    Fx, Fy, fx, fy = oracle.fluxes(cfg, f, W)
+    Fy = Fy.reshape(cfg.ny + 1, cfg.nx, 4)
+    scale = np.max(np.abs(Fy[1:-1, :, 0])) + np.max(np.abs(Fx))
+    assert np.max(np.abs(Fy[0, :, 0])) < 1e-15 * scale * 10
+    assert np.max(np.abs(Fy[-1, :, 0])) < 1e-15 * scale * 10
+
+
+def test_step_cells_matches_full_step(oracle):
+    cfg = I.channel_config(nx=9, ny=5, n_vel=8, kn=0.05)
+    f, W = random_state(oracle, cfg, 15)
+    f1, W1 = oracle.step(cfg, f, W, 1)
+    ids = [0, 4, 8, 9, 22, 36, 44]
+    fo, Wo = oracle.step_cells(cfg, f, W, ids)
+    assert np.array_equal(fo, f1[ids]) and np.array_equal(Wo, W1[:, ids].T)
+
+
+def _maxwell_red(cfg, Wc, uq, vq):
+    rho = Wc[0]
+    U, V = Wc[1] / rho, Wc[2] / rho
+    lam = (cfg.K + 2) * rho / (4 * (Wc[3] - 0.5 * rho * (U * U + V * V)))
+    gh = rho * lam / math.pi * np.exp(-lam * ((uq - U) ** 2 + (vq - V) ** 2))
+    return np.stack([gh, cfg.K / (2 * lam) * gh], axis=1), BF.tau_of(cfg, rho, lam)
+
+
+@pytest.mark.parametrize("case", ["periodic", "channel"])
+def test_step_satisfies_eq3_and_eq4(oracle, case):
+    """The oracle's f^{n+1}, W^{n+1} make the residuals of Eq. 4 and of the implicit
+    Eq. 3 (as printed: trapezoidal collision term with g^{n+1}, tau^{n+1} from W^{n+1})
+    vanish, with the fluxes taken from the brute-force evaluation."""
+    if case == "periodic":
+        cfg = periodic_cfg(nu=5, nv=4, kn=0.02)
+    else:
+        cfg = I.channel_config(nx=4, ny=4, n_vel=5, vrange=3.0, kn=0.02)
+    f, W = random_state(oracle, cfg, 21)
+    dt = oracle.dt(cfg)
+    f1, W1 = oracle.step(cfg, f, W, 1)
+    Fx, Fy, fx, fy = BF.fluxes(cfg, dt, f, W)
+    nx, ny = cfg.nx, cfg.ny
+    dx, dy = cfg.lx / nx, cfg.ly / ny
+    u, _ = BF.axis(cfg.nu, cfg.umin, cfg.umax)
+    v, _ = BF.axis(cfg.nv, cfg.vmin, cfg.vmax)
+    uq, vq = np.tile(u, cfg.nv), np.repeat(v, cfg.nu)
+    assert np.max(np.abs(W1 - W)) > 1e-4  # W really changes, so tau^n != tau^{n+1}
+    for j in range(ny):
+        for i in range(nx):
+            c = j * nx + i
+            xw, xe = j * (nx + 1) + i, j * (nx + 1) + i + 1
+            ys, yn = j * nx + i, (j + 1) * nx + i
+            r4 = W1[:, c] - W[:, c] - (Fx[xw] - Fx[xe]) / dx - (Fy[ys] - Fy[yn]) / dy
+            assert np.max(np.abs(r4)) < 1e-12 * np.max(np.abs(W))
+            g1, t1 = _maxwell_red(cfg, W1[:, c], uq, vq)
+            g0, t0 = _maxwell_red(cfg, W[:, c], uq, vq)
+            r3 = (f1[c] - f[c] - (fx[xw] - fx[xe]) / dx - (fy[ys] - fy[yn]) / dy
+                  - dt / 2 * ((g1 - f1[c]) / t1 + (g0 - f[c]) / t0))
+            assert np.max(np.abs(r3)) < 1e-11 * np.max(np.abs(f))
