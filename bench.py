@@ -1,0 +1,335 @@
+"""Benchmark: explicit 2D UGKS steps on the mesh-sweep channel workload (800x400 cells,
+28^2 velocities on [-4,4]^2, Kn 0.05), in velocity-cell updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--prec fp32f|fp64]
+
+Prints one JSON line (rank 0).  One step = one UGKS step (ghost fill, velocity sums,
+interface scalars, W update, f update) over the whole workload.  `value` is timed with
+CUDA events on the library's stream with the state resident in HBM (f is 4 GB FP64 /
+2 GB FP32, far larger than L2, so no flush is needed); `e2e` goes through the C ABI with
+host buffers (pinned): every step copies f and W in, steps, and reads W back.
+The plain FP64 path and the FP32-f form (FP32 f, FP64 moments / W / interface scalars)
+are both timed; `value` is the form named by --prec and the other is reported beside it.
+Multi-GPU: one independent replica per rank (the step does not shard here), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1810_08137_gb300 import inputs as I  # noqa: E402
+
+METRIC = "velocity-cell updates/s per UGKS step"
+UNIT = "vc/s"
+KERNELS = ("ghost_x", "ghost_y", "sums", "faces", "cells", "update")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 3 + k and r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm), "reasons": reasons}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_form(ugks, torch, cfg, prec, steps, warmup, stream, prim):
+    """Time `steps` device-resident UGKS steps; per-kernel times from the library's events."""
+    s = ugks.Solver(cfg, prec, stream=stream.cuda_stream)
+    s.init_maxwellian(*prim)
+    s.step(warmup)
+    s.sync()
+    s.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = s.kernel_times()
+    s.profile(False)
+    s.sync()
+    return s, ms, kt
+
+
+def e2e_form(ugks, torch, cfg, prec, steps, stream, f_host, W_host):
+    """Through the C ABI with host buffers: per step, copy f and W in, step, read W back."""
+    s = ugks.Solver(cfg, prec, stream=stream.cuda_stream)
+    W_out = np.empty((4, cfg.nc))
+    s.set_state(f_host, W_host)  # warm-up of the path
+    s.step(1)
+    s.moments()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(f_host, W_host)
+        s.step(1)
+        W_out[:] = s.moments()
+    t = time.perf_counter() - t0
+    s.close()
+    return t
+
+
+def pinned(torch, shape):
+    t = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    return t, t.numpy()
+
+
+def cpu_baseline(cfg, prim, budget_s=20.0):
+    """The FP64 oracle as it stands, all host cores, on whole steps of the same workload."""
+    from oracle import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    f, W = oracle.init_maxwellian(cfg, *prim)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        f, W = oracle.step(cfg, f, W, 1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s / 2 or n >= 3:
+            break
+    t = time.perf_counter() - t0
+    return {"value": cfg.vc * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} full step(s) of {cfg.name} ({cfg.vc} vc/step), FP64 C oracle, "
+                      f"OpenMP over faces and cells"}
+
+
+def reference_arm(args, cfg, prim):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    # bounded sample per step: a band of rows of the same channel (same velocity grid,
+    # Kn, boundaries), sized so warmup + steps stay within ~2-3 minutes
+    f, W = oracle.init_maxwellian(cfg, *prim)
+    t0 = time.perf_counter()
+    oracle.step(cfg, f, W, 1)
+    t_full = time.perf_counter() - t0
+    total = max(1, args.steps + args.warmup)
+    frac = min(1.0, 150.0 / (total * t_full))
+    ny_s = max(2, int(cfg.ny * frac))
+    sub = cfg.replace(ny=ny_s, ly=cfg.ly * ny_s / cfg.ny)
+    sp = [x.reshape(cfg.ny, cfg.nx)[:ny_s].reshape(-1) for x in prim]
+    fs, Ws = oracle.init_maxwellian(sub, *sp)
+    fs, Ws = oracle.step(sub, fs, Ws, args.warmup)
+    t0 = time.perf_counter()
+    fs, Ws = oracle.step(sub, fs, Ws, args.steps)
+    t = time.perf_counter() - t0
+    value = sub.vc * args.steps / t
+    sample = (f"{sub.nx}x{sub.ny} band of {cfg.name} (same velocity grid, Kn, boundaries; "
+              f"{sub.vc} vc/step), {args.steps} timed steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": cfg.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp32f", choices=["fp32f", "fp64"])
+    ap.add_argument("--mesh", type=int, default=800, help="nx of the mesh sweep (ny = nx/2)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    cfg = I.workload_mesh_sweep(args.mesh)
+    prim = I.initial_prim(cfg, I.seed_for(2, args.mesh))
+    if args.impl == "reference":
+        reference_arm(args, cfg, prim)
+        return
+
+    import torch
+    from paper_1810_08137_gb300 import build, ugks
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.Stream()
+    hbm, hbm_src = peaks()
+    main_prec = ugks.FP32F if args.prec == "fp32f" else ugks.FP64
+    other_prec = ugks.FP64 if main_prec == ugks.FP32F else ugks.FP32F
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    with torch.cuda.stream(stream):
+        for prec in (other_prec, main_prec):
+            barrier()
+            with Clocks(local) as clk:
+                s, ms, kt = run_form(ugks, torch, cfg, prec, args.steps, args.warmup, stream, prim)
+            barrier()
+            ms = max_over_ranks(ms)
+            results[prec] = (ms, kt, clk.summary())
+            if prec == main_prec:
+                f_host_t, f_host = pinned(torch, (cfg.nc, cfg.nq, 2))
+                W_host_t, W_host = pinned(torch, (4, cfg.nc))
+                fd = torch.empty((cfg.nc, cfg.nq, 2), dtype=torch.float64, device="cuda")
+                Wd = torch.empty((4, cfg.nc), dtype=torch.float64, device="cuda")
+                s.get_state_device(fd, Wd)
+                s.sync()
+                f_host_t.copy_(fd)
+                W_host_t.copy_(Wd)
+                del fd, Wd
+            s.close()
+            torch.cuda.empty_cache()
+        barrier()
+        t_e2e = e2e_form(ugks, torch, cfg, main_prec, args.e2e_steps, stream, f_host, W_host)
+        t_e2e = max_over_ranks(t_e2e)
+
+    def form_json(prec):
+        ms, kt, clk = results[prec]
+        bpv = 8 if prec == ugks.FP32F else 16  # bytes per velocity-cell of f (h, b)
+        n_up, t_up = kt["update"]
+        n_sm, t_sm = kt["sums"]
+        # algorithmic bytes: update reads f once and writes it once, sums reads f once
+        ach_up = 2 * bpv * cfg.vc / (t_up / n_up * 1e-3) / 1e9
+        ach_sm = bpv * cfg.vc / (t_sm / n_sm * 1e-3) / 1e9
+        step_bytes = 3 * bpv * cfg.vc
+        out = {
+            "value": ws * cfg.vc * args.steps / (ms * 1e-3),
+            "ms_per_step": ms / args.steps,
+            "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS},
+            "roofline": {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
+                         "unit": "GB/s", "frac": ach_up / hbm, "traffic": None,
+                         "peak_source": hbm_src,
+                         "algorithmic_bytes_per_vc": 2 * bpv},
+            "roofline_sums": {"achieved": ach_sm, "frac": ach_sm / hbm, "unit": "GB/s",
+                              "algorithmic_bytes_per_vc": bpv},
+            "step_hbm_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm,
+            "clocks": clk,
+        }
+        return out
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    main = form_json(main_prec)
+    other = form_json(other_prec)
+    cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline(cfg, prim)
+    h2d = cfg.nc * cfg.nq * 2 * 8 + 4 * cfg.nc * 8
+    d2h = 4 * cfg.nc * 8
+    line = {
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f) + f64 (moments, W, interface scalars)" if main_prec == ugks.FP32F else "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg.name, "cells": cfg.nc, "velocities": cfg.nq,
+                   "vc_per_step": cfg.vc, "kn": cfg.kn, "precision": args.prec,
+                   "l2": "inputs larger than L2 (f >= 2 GB), no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": main["roofline"],
+        "kernel_ms_per_step": main["kernel_ms_per_step"],
+        "roofline_sums": main["roofline_sums"],
+        "step_hbm_frac": main["step_hbm_frac"],
+        "other_form": {"precision": "fp64" if other_prec == ugks.FP64 else "fp32f",
+                       "value": other["value"], "ms_per_step": other["ms_per_step"],
+                       "kernel_ms_per_step": other["kernel_ms_per_step"],
+                       "roofline": other["roofline"], "clocks": other["clocks"]},
+        "vs_fp64": (main["value"] / other["value"]) if main_prec == ugks.FP32F else 1.0,
+        "clocks": main["clocks"],
+        "e2e": {"value": ws * cfg.vc * args.e2e_steps / t_e2e, "unit": UNIT,
+                "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 6 * args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

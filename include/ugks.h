@@ -1,0 +1,158 @@
+/*
+ * ugks.h -- C ABI of the GB300 (sm_103a) library for the explicit 2D Unified Gas-Kinetic
+ * Scheme step of Liu, Hu & Li, "Performance Comparison on Parallel CPU and GPU Algorithms
+ * for Unified Gas-Kinetic Scheme" (arXiv:1810.08137).
+ *
+ * One step (ugks_step) is, for every cell and discrete velocity (Sec. 2):
+ *   - the interface distribution of the BGK integral solution (Eq. 2), built per interface by
+ *     the flux steps S1-S8 of the Sec. 2.B table (velocity moments, Maxwellian moments, time
+ *     weights, micro slopes, equilibrium and free-transport flux parts, micro flux);
+ *   - the conservative update of the macroscopic variables W = (rho, rho U, rho V, rho E)
+ *     (Eq. 4);
+ *   - the implicit (trapezoidal collision term) update of the distribution function (Eq. 3).
+ * The problem statement -- mesh, velocity grid, tau, CFL, wall and inlet/outlet conditions --
+ * is the one of Sec. 2 and Sec. 3.A (2D pressure-driven channel).
+ *
+ * Conventions for every call:
+ *   - The library owns all device memory it uses; host pointers are only read or written
+ *     during the call (the data is copied).  Device pointers passed to *_device calls must
+ *     stay valid until the call's work on the handle's stream has completed.
+ *   - Every call returns a status; ugks_last_error() gives a text for the last failure on a
+ *     handle.  No call aborts the process or traps the device.
+ *   - Work is enqueued on the CUDA stream given at creation (NULL: the legacy default
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *   - Numerical failure (rho <= 0, T <= 0 or NaN in a cell) is recorded on the device and
+ *     reported as UGKS_ENUMERIC by the next synchronising call.
+ *
+ * Host array layouts (the same for both precisions; FP32 storage converts on copy):
+ *   cell index   c = j*nx + i                 (x fastest), 0 <= i < nx, 0 <= j < ny
+ *   velocity     q = m*nu + k                 (u fastest), u_k, v_m
+ *   f[c][q][2]   double; component 0 = h = int f dxi, component 1 = b = int xi^2 f dxi
+ *                (reduced distributions over the K internal degrees of freedom)
+ *   W[4][c]      double; rho, rho U, rho V, rho E
+ */
+#ifndef UGKS_H
+#define UGKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  UGKS_OK = 0,
+  UGKS_EINVAL = 1,    /* invalid argument or configuration */
+  UGKS_ENOMEM = 2,    /* device allocation failed */
+  UGKS_ECUDA = 3,     /* a CUDA runtime call failed */
+  UGKS_ETIMEOUT = 4,  /* a bounded device wait gave up (persistent batch kernel) */
+  UGKS_ENUMERIC = 5   /* rho <= 0, T <= 0 or NaN appeared in a cell */
+} ugks_status;
+
+typedef enum {
+  UGKS_BC_PERIODIC = 0,  /* wrap around */
+  UGKS_BC_WALL = 1,      /* diffuse isothermal wall: zero net mass flux, wall Maxwellian */
+  UGKS_BC_PRESSURE = 2   /* ghost Maxwellian (rho_bc, U and V of the adjacent cell, T_bc) */
+} ugks_bc_kind;
+
+typedef enum {
+  UGKS_FP64 = 0,   /* f stored and transported in FP64, all arithmetic FP64 */
+  UGKS_FP32F = 1   /* f stored and transported in FP32; FP64 for the velocity-moment
+                      accumulation across lanes, W, the interface scalars (micro-slope
+                      solves, Mt time weights) and the cell update coefficients */
+} ugks_precision;
+
+enum { UGKS_SIDE_W = 0, UGKS_SIDE_E = 1, UGKS_SIDE_S = 2, UGKS_SIDE_N = 3 };
+
+typedef struct {
+  int kind;      /* ugks_bc_kind */
+  double rho;    /* UGKS_BC_PRESSURE: ghost density */
+  double T;      /* UGKS_BC_PRESSURE: ghost temperature; UGKS_BC_WALL: wall temperature */
+  double U;      /* UGKS_BC_WALL: tangential wall velocity */
+} ugks_bc;
+
+/* Problem statement (Sec. 2, Sec. 3.A).  Units: velocities in sqrt(2 k T0 / m), so the
+ * Maxwellian of Eq. 1 is g = rho (lam/pi) exp(-lam((u-U)^2+(v-V)^2)) with lam = 1/T. */
+typedef struct {
+  int nx, ny;            /* cells, >= 1 each; uniform Cartesian mesh */
+  double lx, ly;         /* domain size */
+  int nu, nv;            /* discrete velocities per axis, >= 1, nu*nv <= 65536 */
+  double umin, umax;     /* uniform grid including both ends, trapezoid weights */
+  double vmin, vmax;
+  int K;                 /* internal degrees of freedom, 0 <= K <= 8 (1: monatomic) */
+  double kn;             /* Knudsen number; tau = mu/p, mu = mu_ref T^omega */
+  double omega, alpha;   /* viscosity index and VSS alpha (0.5, 1.0: hard sphere) */
+  double cfl;            /* dt = cfl / (max|u|/dx + max|v|/dy) when dt <= 0 */
+  double dt;             /* > 0: fixed time step */
+  ugks_bc bc[4];         /* W, E, S, N; periodic must be paired (W with E, S with N) */
+  int precision;         /* ugks_precision */
+} ugks_config;
+
+typedef struct ugks_ctx* ugks_handle;
+
+/* Validate cfg, build the velocity grid, weights and time step, allocate device state
+ * (two copies of f with a two-cell ghost ring, W, per-cell velocity sums, per-face
+ * coefficients).  cuda_stream: a cudaStream_t or NULL.  On success *out is a new handle.
+ * Errors: UGKS_EINVAL (bad cfg, NULL out), UGKS_ENOMEM, UGKS_ECUDA. */
+ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* out);
+
+/* Free everything owned by h (NULL is allowed). */
+void ugks_destroy(ugks_handle h);
+
+/* Text of the last error on h (never NULL; "" if none). */
+const char* ugks_last_error(ugks_handle h);
+
+/* Time step and velocity grid actually used: u[nu], v[nv], w[nq] (any may be NULL). */
+ugks_status ugks_get_grid(ugks_handle h, double* dt, double* u, double* v, double* w);
+
+/* Device bytes owned by h. */
+size_t ugks_device_bytes(ugks_handle h);
+
+/* Copy a state from host memory: f_host[nc][nq][2], W_host[4][nc] (layouts above). */
+ugks_status ugks_set_state(ugks_handle h, const double* f_host, const double* W_host);
+
+/* Same from device memory (same layouts, FP64).  Enqueued; returns without waiting. */
+ugks_status ugks_set_state_device(ugks_handle h, const double* f_dev, const double* W_dev);
+
+/* Pointwise Maxwellian state built on the device from per-cell primitive fields
+ * (host arrays of nc values): f = g(rho, U, V, T) per velocity, b = K T/2 h,
+ * W = (rho, rho U, rho V, rho (|U|^2/2 + (K+2) T / 4)). */
+ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double* U,
+                                 const double* V, const double* T);
+
+/* Advance nsteps explicit UGKS steps (Eq. 2-4).  Enqueued on the stream; returns without
+ * waiting.  Errors found later surface at the next synchronising call. */
+ugks_status ugks_step(ugks_handle h, int nsteps);
+
+/* Wait for the stream and report a recorded numerical failure. */
+ugks_status ugks_sync(ugks_handle h);
+
+/* Copy W (host W_host[4][nc]) and, if prim_host != NULL, primitive variables
+ * prim_host[4][nc] = (rho, U, V, T).  Synchronises. */
+ugks_status ugks_moments(ugks_handle h, double* W_host, double* prim_host);
+
+/* Checkpoint: copy the full state (f_host[nc][nq][2], W_host[4][nc]).  Synchronises. */
+ugks_status ugks_get_state(ugks_handle h, double* f_host, double* W_host);
+
+/* Same into device memory (FP64 layouts above).  Enqueued; returns without waiting. */
+ugks_status ugks_get_state_device(ugks_handle h, double* f_dev, double* W_dev);
+
+/* Residual of the last step, per component c of W:
+ *   res[c] = sqrt(mean_cells (W_c^{n+1} - W_c^n)^2) / max(max_cells |W_c^{n+1}|, 1e-300).
+ * Synchronises.  Before any step res[] = 0. */
+ugks_status ugks_residual(ugks_handle h, double res[4]);
+
+/* Tracing.  enable != 0: every later ugks_step records CUDA events on the handle's
+ * stream around each of its kernels; enable == 0 stops recording and discards the
+ * records.  ugks_kernel_times synchronises and returns, per kernel of the step (order:
+ * ugks_kernel_name(0..UGKS_NKERNELS-1)), the launches recorded and their total device
+ * time in ms.  ms and launches must hold UGKS_NKERNELS entries (either may be NULL). */
+#define UGKS_NKERNELS 6
+ugks_status ugks_profile(ugks_handle h, int enable);
+ugks_status ugks_kernel_times(ugks_handle h, double* ms, long* launches);
+const char* ugks_kernel_name(int i);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,609 @@
+// C-ABI implementation of the GB300 UGKS library (declarations and contracts in
+// include/ugks.h).  Host side: validation, velocity grid, time step, device state,
+// step orchestration.  Device side: ugks_kernels.cuh.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ugks.h"
+#include "ugks_kernels.cuh"
+
+using namespace ugks;
+
+struct ugks_ctx {
+  ugks_config cfg;
+  Params P;
+  cudaStream_t stream = nullptr;
+  int prec = 0;
+  size_t t2 = 16;        // bytes per (h, b) pair in device f
+  size_t fcells = 0;     // cells of the f buffers (ghost ring 2)
+  int nwe = 0;           // cells of the W buffers (ghost ring 1)
+  void* f[2] = {nullptr, nullptr};
+  double* W[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* sums = nullptr;
+  FaceRec* fxr = nullptr;
+  FaceRec* fyr = nullptr;
+  double* Fx = nullptr;
+  double* Fy = nullptr;
+  CellRec* cells = nullptr;
+  double* rpart = nullptr;
+  int nrblocks = 0;
+  int* err = nullptr;
+  double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv]
+  double* stage = nullptr;   // FP64 staging for FP32 state conversion
+  size_t stage_bytes = 0;
+  std::vector<double> hu, hv, hwu, hwv;
+  size_t bytes = 0;
+  long steps_done = 0;
+  std::string last_error;
+  // tracing: one set of UGKS_NKERNELS+1 events per profiled step
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+};
+
+namespace {
+
+ugks_status fail(ugks_ctx* h, ugks_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+ugks_status cuda_fail(ugks_ctx* h, cudaError_t e, const char* where) {
+  return fail(h, UGKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);      \
+  } while (0)
+
+void axis(int n, double lo, double hi, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  if (n == 1) { x[0] = 0.5 * (lo + hi); w[0] = 1.0; return; }
+  const double d = (hi - lo) / (n - 1), c = 0.5 * (lo + hi);
+  for (int k = 0; k < n; k++) {
+    x[k] = c + (k - 0.5 * (n - 1)) * d;  // symmetric about the centre
+    w[k] = (k == 0 || k == n - 1) ? 0.5 * d : d;
+  }
+}
+
+const char* validate(const ugks_config* c) {
+  if (!c) return "cfg is NULL";
+  if (c->nx < 1 || c->ny < 1) return "nx, ny must be >= 1";
+  if ((long)c->nx * c->ny > 400000000L) return "too many cells";
+  if (c->nu < 1 || c->nv < 1 || c->nu > kMaxAxis || c->nv > kMaxAxis) return "nu, nv must be in [1, 512]";
+  if ((long)c->nu * c->nv > kMaxNq) return "nu*nv must be <= 65536";
+  if (!(c->lx > 0) || !(c->ly > 0)) return "lx, ly must be > 0";
+  if (c->nu > 1 && !(c->umax > c->umin)) return "umax must exceed umin";
+  if (c->nv > 1 && !(c->vmax > c->vmin)) return "vmax must exceed vmin";
+  if (c->K < 0 || c->K > 8) return "K must be in [0, 8]";
+  if (!(c->kn > 0) || !isfinite(c->kn)) return "kn must be finite and > 0";
+  if (!(c->alpha > 0) || !(c->omega >= 0) || !(c->omega < 2.5)) return "bad omega/alpha";
+  if (!(c->dt > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt > 0";
+  if (c->precision != UGKS_FP64 && c->precision != UGKS_FP32F) return "bad precision";
+  for (int s = 0; s < 4; s++) {
+    const ugks_bc& b = c->bc[s];
+    if (b.kind < 0 || b.kind > 2) return "bad boundary kind";
+    if (b.kind == UGKS_BC_PRESSURE && (!(b.rho > 0) || !(b.T > 0))) return "pressure boundary needs rho, T > 0";
+    if (b.kind == UGKS_BC_WALL && !(b.T > 0)) return "wall needs T > 0";
+  }
+  if ((c->bc[0].kind == UGKS_BC_PERIODIC) != (c->bc[1].kind == UGKS_BC_PERIODIC)) return "periodic W/E must be paired";
+  if ((c->bc[2].kind == UGKS_BC_PERIODIC) != (c->bc[3].kind == UGKS_BC_PERIODIC)) return "periodic S/N must be paired";
+  if (c->bc[0].kind == UGKS_BC_PERIODIC && c->nx < 2) return "periodic x needs nx >= 2";
+  if (c->bc[2].kind == UGKS_BC_PERIODIC && c->ny < 2) return "periodic y needs ny >= 2";
+  return nullptr;
+}
+
+template <typename T>
+size_t smem_sums(int nv) {
+  return kWarpsPerBlock * kNSum * sizeof(double) + 5 * (size_t)nv * sizeof(T);
+}
+template <typename T>
+size_t smem_update(int nv) {
+  return (1 + 6 * kWarpsPerBlock) * (size_t)nv * sizeof(T);
+}
+
+template <typename T>
+cudaError_t set_smem_limits(int nv) {
+  using T2 = typename Vec2<T>::type;
+  cudaError_t e = cudaFuncSetAttribute(k_sums<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_sums<T>(nv));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_update<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_update<T>(nv));
+}
+
+const char* const kKernelNames[UGKS_NKERNELS] = {"ghost_x", "ghost_y", "sums", "faces", "cells",
+                                                   "update"};
+
+// Records event `k` of the current profiled step (no-op when not profiling).
+cudaError_t mark(ugks_ctx* h, int k) {
+  if (!h->profiling) return cudaSuccess;
+  const size_t idx = h->events_used + k;
+  while (h->events.size() <= idx) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    h->events.push_back(e);
+  }
+  return cudaEventRecord(h->events[idx], h->stream);
+}
+
+template <typename T>
+cudaError_t launch_step(ugks_ctx* h) {
+  using T2 = typename Vec2<T>::type;
+  const Params& P = h->P;
+  cudaStream_t st = h->stream;
+  T2* fi = static_cast<T2*>(h->f[h->cur]);
+  T2* fo = static_cast<T2*>(h->f[h->cur ^ 1]);
+  double* Wi = h->W[h->cur];
+  double* Wo = h->W[h->cur ^ 1];
+  cudaError_t r;
+  if ((r = mark(h, 0)) != cudaSuccess) return r;
+  k_ghost_x<T2><<<dim3(P.ny, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
+  if ((r = mark(h, 1)) != cudaSuccess) return r;
+  k_ghost_y<T2><<<dim3(P.nx + 4, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
+  if ((r = mark(h, 2)) != cudaSuccess) return r;
+  const int nce = (P.nx + 2) * (P.ny + 2);
+  k_sums<T, T2><<<(nce + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_sums<T>(P.nv), st>>>(
+      P, fi, h->sums);
+  if ((r = mark(h, 3)) != cudaSuccess) return r;
+  const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
+  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, h->sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy);
+  if ((r = mark(h, 4)) != cudaSuccess) return r;
+  const int nc = P.nx * P.ny;
+  k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err);
+  if ((r = mark(h, 5)) != cudaSuccess) return r;
+  k_update<T, T2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
+      P, fi, fo, h->fxr, h->fyr, h->cells);
+  if ((r = mark(h, 6)) != cudaSuccess) return r;
+  if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
+  return cudaGetLastError();
+}
+
+// FP64 host/device rows <-> FP32 ring layout
+__global__ void k_rows_to_f32(const double* __restrict__ src, float2* __restrict__ dst, Params P,
+                              int j0, int nrows) {
+  const size_t row = (size_t)P.nx * P.nq;
+  const size_t n = row * nrows;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / row);
+    const size_t o = t % row;
+    const int i = (int)(o / P.nq), q = (int)(o % P.nq);
+    float2 v;
+    v.x = (float)src[2 * t];
+    v.y = (float)src[2 * t + 1];
+    dst[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q] = v;
+  }
+}
+__global__ void k_f32_to_rows(const float2* __restrict__ src, double* __restrict__ dst, Params P,
+                              int j0, int nrows) {
+  const size_t row = (size_t)P.nx * P.nq;
+  const size_t n = row * nrows;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / row);
+    const size_t o = t % row;
+    const int i = (int)(o / P.nq), q = (int)(o % P.nq);
+    const float2 v = src[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q];
+    dst[2 * t] = v.x;
+    dst[2 * t + 1] = v.y;
+  }
+}
+
+template <typename T2>
+__global__ void k_init_maxwellian(Params P, const double* __restrict__ prim, T2* __restrict__ f,
+                                  double* __restrict__ W, int nwe) {
+  const int nc = P.nx * P.ny;
+  const int cell = blockIdx.x;
+  if (cell >= nc) return;
+  const int i = cell % P.nx, j = cell / P.nx;
+  const double rho = prim[cell], U = prim[nc + cell], V = prim[2 * nc + cell], T = prim[3 * nc + cell];
+  const double lam = 1.0 / T, G = rho * lam / kPi, bf = P.K / (2.0 * lam);
+  T2* dst = f + fcell(P, i, j) * P.nq;
+  for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+    const int k = q % P.nu, m = q / P.nu;
+    const double du = P.u[k] - U, dv = P.v[m] - V;
+    const double gh = G * exp(-lam * (du * du + dv * dv));
+    T2 o;
+    o.x = gh;
+    o.y = bf * gh;
+    dst[q] = o;
+  }
+  if (threadIdx.x == 0) {
+    const int w = wcell(P, i, j);
+    W[w] = rho;
+    W[nwe + w] = rho * U;
+    W[2 * nwe + w] = rho * V;
+    W[3 * nwe + w] = rho * (0.5 * (U * U + V * V) + (P.K + 2) / (4.0 * lam));
+  }
+}
+
+__global__ void k_prim(Params P, const double* __restrict__ W, int nwe, double* __restrict__ out) {
+  const int nc = P.nx * P.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int w = wcell(P, c % P.nx, c / P.nx);
+  const double r = W[w], U = W[nwe + w] / r, V = W[2 * nwe + w] / r;
+  const double lam = (P.K + 2) * r / (4.0 * (W[3 * nwe + w] - 0.5 * r * (U * U + V * V)));
+  out[c] = r;
+  out[nc + c] = U;
+  out[2 * nc + c] = V;
+  out[3 * nc + c] = 1.0 / lam;
+}
+
+ugks_status copy_W_in(ugks_ctx* h, const double* W, cudaMemcpyKind kind) {
+  const Params& P = h->P;
+  for (int c = 0; c < 4; c++) {
+    double* dst = h->W[h->cur] + (size_t)c * h->nwe + wcell(P, 0, 0);
+    CK(cudaMemcpy2DAsync(dst, P.wx * sizeof(double), W + (size_t)c * P.nx * P.ny, P.nx * sizeof(double),
+                         P.nx * sizeof(double), P.ny, kind, h->stream));
+  }
+  return UGKS_OK;
+}
+
+ugks_status copy_W_out(ugks_ctx* h, double* W, cudaMemcpyKind kind) {
+  const Params& P = h->P;
+  for (int c = 0; c < 4; c++) {
+    const double* src = h->W[h->cur] + (size_t)c * h->nwe + wcell(P, 0, 0);
+    CK(cudaMemcpy2DAsync(W + (size_t)c * P.nx * P.ny, P.nx * sizeof(double), src, P.wx * sizeof(double),
+                         P.nx * sizeof(double), P.ny, kind, h->stream));
+  }
+  return UGKS_OK;
+}
+
+ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
+  const Params& P = h->P;
+  const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
+  const cudaMemcpyKind kind = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (h->prec == UGKS_FP64) {
+    char* dst = static_cast<char*>(h->f[h->cur]) + ((size_t)2 * P.ex + 2) * P.nq * h->t2;
+    CK(cudaMemcpy2DAsync(dst, (size_t)P.ex * P.nq * h->t2, f, row_d, row_d, P.ny, kind, h->stream));
+    return UGKS_OK;
+  }
+  float2* dst = static_cast<float2*>(h->f[h->cur]);
+  if (!from_host) {
+    k_rows_to_f32<<<1024, 256, 0, h->stream>>>(f, dst, P, 0, P.ny);
+    CK(cudaGetLastError());
+    return UGKS_OK;
+  }
+  const int rows = (int)(h->stage_bytes / row_d);
+  for (int j0 = 0; j0 < P.ny; j0 += rows) {
+    const int nr = (j0 + rows <= P.ny) ? rows : P.ny - j0;
+    CK(cudaMemcpyAsync(h->stage, f + (size_t)j0 * P.nx * P.nq * 2, nr * row_d, cudaMemcpyHostToDevice, h->stream));
+    k_rows_to_f32<<<1024, 256, 0, h->stream>>>(h->stage, dst, P, j0, nr);
+    CK(cudaGetLastError());
+  }
+  return UGKS_OK;
+}
+
+ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
+  const Params& P = h->P;
+  const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
+  const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (h->prec == UGKS_FP64) {
+    const char* src = static_cast<const char*>(h->f[h->cur]) + ((size_t)2 * P.ex + 2) * P.nq * h->t2;
+    CK(cudaMemcpy2DAsync(f, row_d, src, (size_t)P.ex * P.nq * h->t2, row_d, P.ny, kind, h->stream));
+    return UGKS_OK;
+  }
+  const float2* src = static_cast<const float2*>(h->f[h->cur]);
+  if (!to_host) {
+    k_f32_to_rows<<<1024, 256, 0, h->stream>>>(src, f, P, 0, P.ny);
+    CK(cudaGetLastError());
+    return UGKS_OK;
+  }
+  const int rows = (int)(h->stage_bytes / row_d);
+  for (int j0 = 0; j0 < P.ny; j0 += rows) {
+    const int nr = (j0 + rows <= P.ny) ? rows : P.ny - j0;
+    k_f32_to_rows<<<1024, 256, 0, h->stream>>>(src, h->stage, P, j0, nr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(f + (size_t)j0 * P.nx * P.nq * 2, h->stage, nr * row_d, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return UGKS_OK;
+}
+
+ugks_status check_err(ugks_ctx* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e) return fail(h, UGKS_ENUMERIC, "numerical failure: rho <= 0, T <= 0 or NaN in a cell");
+  return UGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* out) {
+  if (!out) return UGKS_EINVAL;
+  *out = nullptr;
+  const char* bad = validate(cfg);
+  if (bad) {
+    fprintf(stderr, "ugks_create: %s\n", bad);
+    return UGKS_EINVAL;
+  }
+  ugks_ctx* h = new ugks_ctx();
+  h->cfg = *cfg;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->prec = cfg->precision;
+  h->t2 = h->prec == UGKS_FP64 ? sizeof(double2) : sizeof(float2);
+  Params& P = h->P;
+  memset(&P, 0, sizeof P);
+  P.nx = cfg->nx; P.ny = cfg->ny; P.nu = cfg->nu; P.nv = cfg->nv; P.nq = cfg->nu * cfg->nv;
+  P.K = cfg->K;
+  P.ex = cfg->nx + 4;
+  P.wx = cfg->nx + 2;
+  P.dx = cfg->lx / cfg->nx;
+  P.dy = cfg->ly / cfg->ny;
+  axis(cfg->nu, cfg->umin, cfg->umax, h->hu, h->hwu);
+  axis(cfg->nv, cfg->vmin, cfg->vmax, h->hv, h->hwv);
+  double um = 0, vm = 0;
+  for (double x : h->hu) um = fmax(um, fabs(x));
+  for (double x : h->hv) vm = fmax(vm, fabs(x));
+  if (cfg->dt > 0) P.dt = cfg->dt;
+  else {
+    if (!(um / P.dx + vm / P.dy > 0)) { delete h; return UGKS_EINVAL; }
+    P.dt = cfg->cfl / (um / P.dx + vm / P.dy);
+  }
+  const double a = cfg->alpha, om = cfg->omega;
+  P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
+  P.omega = om;
+  for (int s = 0; s < 4; s++) {
+    P.bc_kind[s] = cfg->bc[s].kind;
+    P.bc_rho[s] = cfg->bc[s].rho;
+    P.bc_T[s] = cfg->bc[s].T;
+    P.bc_U[s] = cfg->bc[s].U;
+    if (cfg->bc[s].kind != UGKS_BC_WALL) continue;
+    // discrete moments of the outgoing wall Maxwellian (rho = 1), natural frame
+    const double lam = 1.0 / cfg->bc[s].T, Uw = cfg->bc[s].U;
+    double m[4] = {0, 0, 0, 0};
+    for (int mm = 0; mm < P.nv; mm++)
+      for (int k = 0; k < P.nu; k++) {
+        const double u = h->hu[k], v = h->hv[mm], w = h->hwu[k] * h->hwv[mm];
+        const double un = s < 2 ? u : v, ut = s < 2 ? v : u;
+        const bool outgoing = (s == 0 || s == 2) ? un > 0 : un < 0;
+        if (!outgoing) continue;
+        const double gh = lam / M_PI * exp(-lam * ((ut - Uw) * (ut - Uw) + un * un));
+        const double gb = P.K / (2.0 * lam) * gh;
+        m[0] += w * un * gh;
+        m[1] += w * un * u * gh;
+        m[2] += w * un * v * gh;
+        m[3] += w * un * (0.5 * (u * u + v * v) * gh + 0.5 * gb);
+      }
+    for (int c = 0; c < 4; c++) P.wall_mom[s][c] = m[c];
+  }
+
+  cudaError_t e;
+  auto alloc = [&](void** p, size_t n) -> bool {
+    e = cudaMalloc(p, n);
+    if (e != cudaSuccess) return false;
+    h->bytes += n;
+    return true;
+  };
+  h->fcells = (size_t)(P.nx + 4) * (P.ny + 4);
+  h->nwe = (P.nx + 2) * (P.ny + 2);
+  const size_t fbytes = h->fcells * P.nq * h->t2;
+  const int nfx = (P.nx + 1) * P.ny, nfy = P.nx * (P.ny + 1), nc = P.nx * P.ny;
+  h->nrblocks = (nc + 127) / 128;
+  bool ok = alloc(&h->f[0], fbytes) && alloc(&h->f[1], fbytes) &&
+            alloc((void**)&h->W[0], 4 * sizeof(double) * h->nwe) &&
+            alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
+            alloc((void**)&h->sums, sizeof(double) * kNSum * (size_t)h->nwe) &&
+            alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx) &&
+            alloc((void**)&h->fyr, sizeof(FaceRec) * (size_t)nfy) &&
+            alloc((void**)&h->Fx, sizeof(double) * 4 * (size_t)nfx) &&
+            alloc((void**)&h->Fy, sizeof(double) * 4 * (size_t)nfy) &&
+            alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc) &&
+            alloc((void**)&h->rpart, sizeof(double) * 8 * (size_t)h->nrblocks) &&
+            alloc((void**)&h->err, sizeof(int)) &&
+            alloc((void**)&h->d_grid, sizeof(double) * 2 * (P.nu + P.nv));
+  if (ok && h->prec == UGKS_FP32F) {
+    const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
+    size_t want = (size_t)64 << 20;
+    if (want < row_d) want = row_d;
+    if (want > row_d * P.ny) want = row_d * P.ny;
+    h->stage_bytes = want;
+    ok = alloc((void**)&h->stage, want);
+  }
+  if (!ok) {
+    ugks_destroy(h);
+    fprintf(stderr, "ugks_create: device allocation failed: %s\n", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? UGKS_ENOMEM : UGKS_ECUDA;
+  }
+  std::vector<double> grid;
+  grid.insert(grid.end(), h->hu.begin(), h->hu.end());
+  grid.insert(grid.end(), h->hv.begin(), h->hv.end());
+  grid.insert(grid.end(), h->hwu.begin(), h->hwu.end());
+  grid.insert(grid.end(), h->hwv.begin(), h->hwv.end());
+  P.u = h->d_grid;
+  P.v = h->d_grid + P.nu;
+  P.wu = h->d_grid + P.nu + P.nv;
+  P.wv = h->d_grid + 2 * P.nu + P.nv;
+  auto setup = [&]() -> cudaError_t {
+    cudaError_t r;
+    if ((r = cudaMemcpyAsync(h->d_grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess) return r;
+    for (int b = 0; b < 2; b++) {
+      if ((r = cudaMemsetAsync(h->f[b], 0, fbytes, h->stream)) != cudaSuccess) return r;
+      if ((r = cudaMemsetAsync(h->W[b], 0, 4 * sizeof(double) * h->nwe, h->stream)) != cudaSuccess) return r;
+    }
+    if ((r = cudaMemsetAsync(h->rpart, 0, sizeof(double) * 8 * h->nrblocks, h->stream)) != cudaSuccess) return r;
+    if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
+    if ((r = h->prec == UGKS_FP64 ? set_smem_limits<double>(P.nv) : set_smem_limits<float>(P.nv)) != cudaSuccess)
+      return r;
+    return cudaStreamSynchronize(h->stream);
+  };
+  e = setup();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "ugks_create: %s\n", cudaGetErrorString(e));
+    ugks_destroy(h);
+    return UGKS_ECUDA;
+  }
+  *out = h;
+  return UGKS_OK;
+}
+
+void ugks_destroy(ugks_handle h) {
+  if (!h) return;
+  void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
+                  h->cells, h->rpart, h->err, h->d_grid, h->stage};
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  delete h;
+}
+
+const char* ugks_last_error(ugks_handle h) { return h ? h->last_error.c_str() : "null handle"; }
+
+size_t ugks_device_bytes(ugks_handle h) { return h ? h->bytes : 0; }
+
+ugks_status ugks_get_grid(ugks_handle h, double* dt, double* u, double* v, double* w) {
+  if (!h) return UGKS_EINVAL;
+  if (dt) *dt = h->P.dt;
+  if (u) memcpy(u, h->hu.data(), sizeof(double) * h->P.nu);
+  if (v) memcpy(v, h->hv.data(), sizeof(double) * h->P.nv);
+  if (w)
+    for (int m = 0; m < h->P.nv; m++)
+      for (int k = 0; k < h->P.nu; k++) w[m * h->P.nu + k] = h->hwu[k] * h->hwv[m];
+  return UGKS_OK;
+}
+
+ugks_status ugks_set_state(ugks_handle h, const double* f_host, const double* W_host) {
+  if (!h || !f_host || !W_host) return fail(h, UGKS_EINVAL, "set_state: NULL argument");
+  ugks_status s = copy_f_in(h, f_host, true);
+  if (s) return s;
+  s = copy_W_in(h, W_host, cudaMemcpyHostToDevice);
+  if (s) return s;
+  CK(cudaStreamSynchronize(h->stream));
+  return UGKS_OK;
+}
+
+ugks_status ugks_set_state_device(ugks_handle h, const double* f_dev, const double* W_dev) {
+  if (!h || !f_dev || !W_dev) return fail(h, UGKS_EINVAL, "set_state_device: NULL argument");
+  ugks_status s = copy_f_in(h, f_dev, false);
+  if (s) return s;
+  return copy_W_in(h, W_dev, cudaMemcpyDeviceToDevice);
+}
+
+ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double* U, const double* V,
+                                 const double* T) {
+  if (!h || !rho || !U || !V || !T) return fail(h, UGKS_EINVAL, "init_maxwellian: NULL argument");
+  const Params& P = h->P;
+  const int nc = P.nx * P.ny;
+  for (int c = 0; c < nc; c++)
+    if (!(rho[c] > 0) || !(T[c] > 0)) return fail(h, UGKS_EINVAL, "init_maxwellian: rho and T must be > 0");
+  double* prim = h->sums;  // scratch: sums holds >= 64 * nc doubles
+  const double* src[4] = {rho, U, V, T};
+  for (int c = 0; c < 4; c++)
+    CK(cudaMemcpyAsync(prim + (size_t)c * nc, src[c], nc * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (h->prec == UGKS_FP64)
+    k_init_maxwellian<double2><<<nc, 128, 0, h->stream>>>(P, prim, static_cast<double2*>(h->f[h->cur]),
+                                                          h->W[h->cur], h->nwe);
+  else
+    k_init_maxwellian<float2><<<nc, 128, 0, h->stream>>>(P, prim, static_cast<float2*>(h->f[h->cur]),
+                                                         h->W[h->cur], h->nwe);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return UGKS_OK;
+}
+
+ugks_status ugks_step(ugks_handle h, int nsteps) {
+  if (!h || nsteps < 0) return fail(h, UGKS_EINVAL, "step: bad argument");
+  for (int s = 0; s < nsteps; s++) {
+    cudaError_t e = h->prec == UGKS_FP64 ? launch_step<double>(h) : launch_step<float>(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    h->cur ^= 1;
+    h->steps_done++;
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_sync(ugks_handle h) {
+  if (!h) return UGKS_EINVAL;
+  return check_err(h);
+}
+
+ugks_status ugks_moments(ugks_handle h, double* W_host, double* prim_host) {
+  if (!h || !W_host) return fail(h, UGKS_EINVAL, "moments: NULL argument");
+  ugks_status s = copy_W_out(h, W_host, cudaMemcpyDeviceToHost);
+  if (s) return s;
+  if (prim_host) {
+    const int nc = h->P.nx * h->P.ny;
+    k_prim<<<(nc + 127) / 128, 128, 0, h->stream>>>(h->P, h->W[h->cur], h->nwe, h->sums);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(prim_host, h->sums, 4 * sizeof(double) * nc, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return check_err(h);
+}
+
+ugks_status ugks_get_state(ugks_handle h, double* f_host, double* W_host) {
+  if (!h || !f_host || !W_host) return fail(h, UGKS_EINVAL, "get_state: NULL argument");
+  ugks_status s = copy_f_out(h, f_host, true);
+  if (s) return s;
+  s = copy_W_out(h, W_host, cudaMemcpyDeviceToHost);
+  if (s) return s;
+  return check_err(h);
+}
+
+ugks_status ugks_get_state_device(ugks_handle h, double* f_dev, double* W_dev) {
+  if (!h || !f_dev || !W_dev) return fail(h, UGKS_EINVAL, "get_state_device: NULL argument");
+  ugks_status s = copy_f_out(h, f_dev, false);
+  if (s) return s;
+  return copy_W_out(h, W_dev, cudaMemcpyDeviceToDevice);
+}
+
+ugks_status ugks_residual(ugks_handle h, double res[4]) {
+  if (!h || !res) return fail(h, UGKS_EINVAL, "residual: NULL argument");
+  std::vector<double> part((size_t)8 * h->nrblocks);
+  CK(cudaMemcpyAsync(part.data(), h->rpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ugks_status s = check_err(h);
+  if (s) return s;
+  const int nc = h->P.nx * h->P.ny;
+  for (int c = 0; c < 4; c++) {
+    double ss = 0, mx = 0;
+    for (int b = 0; b < h->nrblocks; b++) {
+      ss += part[(size_t)b * 8 + c];
+      mx = fmax(mx, part[(size_t)b * 8 + 4 + c]);
+    }
+    res[c] = h->steps_done ? sqrt(ss / nc) / fmax(mx, 1e-300) : 0.0;
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_profile(ugks_handle h, int enable) {
+  if (!h) return UGKS_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  h->profiling = enable != 0;
+  h->events_used = 0;
+  return UGKS_OK;
+}
+
+ugks_status ugks_kernel_times(ugks_handle h, double* ms, long* launches) {
+  if (!h) return UGKS_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  double acc[UGKS_NKERNELS] = {0};
+  const size_t per = UGKS_NKERNELS + 1, nsets = h->events_used / per;
+  for (size_t s = 0; s < nsets; s++)
+    for (int k = 0; k < UGKS_NKERNELS; k++) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, h->events[s * per + k], h->events[s * per + k + 1]));
+      acc[k] += t;
+    }
+  for (int k = 0; k < UGKS_NKERNELS; k++) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = (long)nsets;
+  }
+  return UGKS_OK;
+}
+
+const char* ugks_kernel_name(int i) { return (i >= 0 && i < UGKS_NKERNELS) ? kKernelNames[i] : ""; }
+
+}  // extern "C"

@@ -1,0 +1,881 @@
+// Device kernels of one explicit 2D UGKS step (Liu, Hu & Li, arXiv:1810.08137, Sec. 2).
+//
+// Per step, on one stream:
+//   k_ghost_x, k_ghost_y  boundary ghost ring (periodic image, wall zero-gradient copy,
+//                         pressure Maxwellian)
+//   k_sums                per cell and side, the velocity sums of steps S1 and S7 (W0,
+//                         tangential slope of W, free-transport sums) over one read of f
+//   k_faces               per interface, steps S2-S5 (Maxwellian moments, Mt time weights,
+//                         micro slopes a_L a_R b A, equilibrium flux) in FP64, the total
+//                         macroscopic flux, and the coefficients of the micro flux (S6, S8)
+//   k_cells               conservative W update (Eq. 4), g^n, g^{n+1}, tau^n, tau^{n+1}
+//   k_update              micro flux of the four faces and the implicit f update (Eq. 3)
+//                         over a second read of f and one write of f^{n+1}
+//
+// Layout: f[(ny+4)(nx+4)][nq] of T2 = (h, b), velocity innermost (q = m*nu + k), a ghost
+// ring two cells wide; W[4][(ny+2)(nx+2)] FP64 with a ghost ring one cell wide.
+#pragma once
+#include <math.h>
+
+#include "ugks_internal.h"
+
+namespace ugks {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kPi = 3.14159265358979323846;
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+__host__ __device__ __forceinline__ size_t fcell(const Params& P, int i, int j) {
+  return (size_t)(j + 2) * P.ex + (i + 2);
+}
+__host__ __device__ __forceinline__ int wcell(const Params& P, int i, int j) {
+  return (j + 1) * P.wx + (i + 1);
+}
+
+// van Leer limited slope of the stencil (a, c, b) times half the cell width:
+// r = sigma dx / 2 = d1 d2 / (d1 + d2) if d1 d2 > 0, else 0, with d1 = c - a, d2 = b - c.
+__device__ __forceinline__ double vl_half(double a, double c, double b) {
+  double d1 = c - a, d2 = b - c, p = d1 * d2;
+  return p > 0.0 ? p / (d1 + d2) : 0.0;
+}
+__device__ __forceinline__ float vl_half(float a, float c, float b) {
+  float d1 = c - a, d2 = b - c, p = d1 * d2;
+  return p > 0.0f ? __fdividef(p, d1 + d2) : 0.0f;
+}
+
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+__device__ __forceinline__ float texp(float x) { return expf(x); }
+
+// Sum over the warp of v[lane % N] returned to each lane (N = 16 or 32): transpose
+// reduce-scatter, N-1 shuffles instead of N*5.
+template <int N, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[N], int lane) {
+#pragma unroll
+  for (int o = N / 2; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; i++) {
+      T send = upper ? v[i] : v[i + o];
+      T keep = upper ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  T r = v[0];
+#pragma unroll
+  for (int o = N; o < 32; o <<= 1) r += __shfl_xor_sync(kFull, r, o);
+  return r;
+}
+
+// -------------------------------------------------------------------------------------
+// Boundary ghost ring
+// -------------------------------------------------------------------------------------
+template <typename T2>
+__device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int gi, int gj,
+                                int si, int sj, int side, bool write_W, int wi, int wj) {
+  const int kind = P.bc_kind[side];
+  T2* dst = f + fcell(P, gi, gj) * P.nq;
+  const T2* src = f + fcell(P, si, sj) * P.nq;
+  const int sw = wcell(P, wi, wj);
+  if (kind == 2) {  // pressure: Maxwellian(rho_bc, U and V of the adjacent cell, T_bc)
+    const double rho_a = W[sw], U = W[nwe + sw] / rho_a, V = W[2 * nwe + sw] / rho_a;
+    const double lam = 1.0 / P.bc_T[side], rho = P.bc_rho[side];
+    const double G = rho * lam / kPi, bf = P.K / (2.0 * lam);
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+      const int k = q % P.nu, m = q / P.nu;
+      const double du = P.u[k] - U, dv = P.v[m] - V;
+      const double gh = G * exp(-lam * (du * du + dv * dv));
+      T2 o;
+      o.x = gh;
+      o.y = bf * gh;
+      dst[q] = o;
+    }
+    if (write_W && threadIdx.x == 0) {
+      const int g = wcell(P, gi, gj);
+      W[g] = rho;
+      W[nwe + g] = rho * U;
+      W[2 * nwe + g] = rho * V;
+      W[3 * nwe + g] = rho * (0.5 * (U * U + V * V) + (P.K + 2) / (4.0 * lam));
+    }
+  } else {  // periodic image or zero-gradient copy next to a wall
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) dst[q] = src[q];
+    if (write_W && threadIdx.x == 0) {
+      const int g = wcell(P, gi, gj), s = wcell(P, si, sj);
+      for (int c = 0; c < 4; c++) W[c * nwe + g] = W[c * nwe + s];
+    }
+  }
+}
+
+// x-sides, rows 0..ny-1; grid (ny, 4): blockIdx.y = side*2 + layer-1.
+template <typename T2>
+__global__ void k_ghost_x(Params P, T2* f, double* W, int nwe) {
+  const int j = blockIdx.x, side = blockIdx.y >> 1, l = (blockIdx.y & 1) + 1;
+  const int kind = P.bc_kind[side];
+  const int gi = side == 0 ? -l : P.nx - 1 + l;
+  int si;
+  if (kind == 0) si = side == 0 ? P.nx - l : l - 1;
+  else si = side == 0 ? 0 : P.nx - 1;
+  const int ai = side == 0 ? 0 : P.nx - 1;  // adjacent interior cell (pressure velocity source)
+  fill_ghost_cell(P, f, W, nwe, gi, j, si, j, side, l == 1, kind == 2 ? ai : si, j);
+}
+
+// y-sides over all columns -2..nx+1 (corners included, after the x-sides);
+// grid (nx+4, 4): blockIdx.y = side*2 + layer-1, side 0: S, 1: N.
+template <typename T2>
+__global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
+  const int i = (int)blockIdx.x - 2, side = 2 + (blockIdx.y >> 1), l = (blockIdx.y & 1) + 1;
+  const int kind = P.bc_kind[side];
+  const int gj = side == 2 ? -l : P.ny - 1 + l;
+  int sj;
+  if (kind == 0) sj = side == 2 ? P.ny - l : l - 1;
+  else sj = side == 2 ? 0 : P.ny - 1;
+  const int aj = side == 2 ? 0 : P.ny - 1;
+  const bool wcol = i >= -1 && i <= P.nx;
+  const int wi = i < -1 ? -1 : (i > P.nx ? P.nx : i);
+  fill_ghost_cell(P, f, W, nwe, i, gj, i, sj, side, l == 1 && wcol, wi, kind == 2 ? aj : sj);
+}
+
+// -------------------------------------------------------------------------------------
+// Steps S1 + S7: per-cell half-range velocity sums.  One warp per cell, lane = u index
+// (chunks of 32), loop over v.  Cells: interior plus the first ghost layer of every
+// side that is not a wall.
+// -------------------------------------------------------------------------------------
+template <typename T, typename T2>
+__device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T P3, T Pb0, T Pb1,
+                                           T Q0, T Q1, T Q2, T Qb, T Z1, T Z2, T Z3, T Zb1,
+                                           int lane, double* ws_side) {
+  T v[16];
+  const T uu = u * u;
+  v[0] = wu * P0;
+  v[1] = wu * u * P0;
+  v[2] = wu * P1;
+  v[3] = wu * (T(0.5) * (uu * P0 + P2) + T(0.5) * Pb0);
+  const T ws = wu * tdx;
+  v[4] = ws * Q0;
+  v[5] = ws * u * Q0;
+  v[6] = ws * Q1;
+  v[7] = ws * (T(0.5) * (uu * Q0 + Q2) + T(0.5) * Qb);
+  v[8] = wu * P1;
+  v[9] = wu * u * P1;
+  v[10] = wu * P2;
+  v[11] = wu * (T(0.5) * (uu * P1 + P3) + T(0.5) * Pb1);
+  v[12] = wu * Z1;
+  v[13] = wu * u * Z1;
+  v[14] = wu * Z2;
+  v[15] = wu * (T(0.5) * (uu * Z1 + Z3) + T(0.5) * Zb1);
+  const T r = warp_reduce_scatter<16>(v, lane);
+  if (lane < 16) ws_side[lane] += (double)r;
+}
+
+template <typename T, typename T2>
+__global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
+                                              double* __restrict__ sums) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nv = P.nv, nu = P.nu, nq = P.nq;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* wsum = reinterpret_cast<double*>(smraw) + warp * kNSum;
+  T* mw = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(double));
+  // mw[0..4nv): wv, wv v, wv v^2, wv v^3 ; mw[4nv..5nv): v
+  for (int m = tid; m < nv; m += blockDim.x) {
+    const double vv = P.v[m], w = P.wv[m];
+    mw[m] = (T)w;
+    mw[nv + m] = (T)(w * vv);
+    mw[2 * nv + m] = (T)(w * vv * vv);
+    mw[3 * nv + m] = (T)(w * vv * vv * vv);
+    mw[4 * nv + m] = (T)vv;
+  }
+  for (int t = lane; t < kNSum; t += 32) wsum[t] = 0.0;
+  __syncthreads();
+
+  const int ncx = P.nx + 2;
+  const int cell = blockIdx.x * kWarpsPerBlock + warp;
+  if (cell >= ncx * (P.ny + 2)) return;
+  const int i = cell % ncx - 1, j = cell / ncx - 1;
+  const bool xg = i < 0 || i >= P.nx, yg = j < 0 || j >= P.ny;
+  if (xg && yg) return;
+  if ((i < 0 && P.bc_kind[0] == 1) || (i >= P.nx && P.bc_kind[1] == 1) ||
+      (j < 0 && P.bc_kind[2] == 1) || (j >= P.ny && P.bc_kind[3] == 1))
+    return;
+  const bool zs = (i < 0 && P.bc_kind[0] == 2) || (i >= P.nx && P.bc_kind[1] == 2) ||
+                  (j < 0 && P.bc_kind[2] == 2) || (j >= P.ny && P.bc_kind[3] == 2);
+
+  const T2* fc = f + fcell(P, i, j) * nq;
+  const size_t rs = (size_t)P.ex * nq;
+  const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy);
+
+  for (int k0 = 0; k0 < nu; k0 += 32) {
+    const int k = k0 + lane;
+    const bool act = k < nu;
+    const int kk = act ? k : nu - 1;
+    const T u = (T)P.u[kk];
+    const T wu = act ? (T)P.wu[kk] : T(0);
+    const T cu = u * tdx;
+    T A0 = 0, A1 = 0, A2 = 0, Ab = 0, R0 = 0, R1 = 0, R2 = 0, Rb = 0;
+    T C0 = 0, C1 = 0, C2 = 0, Cb = 0, D0 = 0, D1 = 0, D2 = 0, Db = 0;
+    T P0 = 0, P1 = 0, P2 = 0, P3 = 0, Pb0 = 0, Pb1 = 0, Q0 = 0, Q1 = 0, Q2 = 0, Qb = 0;
+    T Z1 = 0, Z2 = 0, Z3 = 0, Zb1 = 0;
+    bool south_done = false;
+    for (int m = 0; m < nv; m++) {
+      const T vv = mw[4 * nv + m];
+      if (!south_done && vv > T(0)) {
+        finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
+                          lane, wsum + kSumS);
+        P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
+        south_done = true;
+      }
+      const size_t q = (size_t)m * nu + kk;
+      const T2 c = fc[q], w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
+      T rxh = 0, rxb = 0, ryh = 0, ryb = 0;
+      if (!zs) {
+        rxh = vl_half(w.x, c.x, e.x);
+        rxb = vl_half(w.y, c.y, e.y);
+        ryh = vl_half(s.x, c.x, n.x);
+        ryb = vl_half(s.y, c.y, n.y);
+      }
+      const T cv = vv * tdy;
+      const T dh = cu * rxh + cv * ryh, db = cu * rxb + cv * ryb;
+      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m], w3 = mw[3 * nv + m];
+      A0 += w0 * c.x; A1 += w1 * c.x; A2 += w2 * c.x; Ab += w0 * c.y;
+      R0 += w0 * rxh; R1 += w1 * rxh; R2 += w2 * rxh; Rb += w0 * rxb;
+      C0 += w0 * ryh; C1 += w1 * ryh; C2 += w2 * ryh; Cb += w0 * ryb;
+      D0 += w0 * dh;  D1 += w1 * dh;  D2 += w2 * dh;  Db += w0 * db;
+      if (vv == T(0)) {
+        // H(0) = 1/2: half to the S side with f - r_y, half to the N side with f + r_y;
+        // the u_n = v weighted sums vanish.
+        const T hw = T(0.5) * w0;
+        P0 += hw * (c.x - ryh); Pb0 += hw * (c.y - ryb); Q0 += hw * rxh; Qb += hw * rxb;
+        finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
+                          lane, wsum + kSumS);
+        P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
+        south_done = true;
+        P0 += hw * (c.x + ryh); Pb0 += hw * (c.y + ryb); Q0 += hw * rxh; Qb += hw * rxb;
+      } else {
+        const T sy = vv > T(0) ? T(1) : T(-1);
+        const T fyh = c.x + sy * ryh, fyb = c.y + sy * ryb;
+        P0 += w0 * fyh; P1 += w1 * fyh; P2 += w2 * fyh; P3 += w3 * fyh;
+        Pb0 += w0 * fyb; Pb1 += w1 * fyb;
+        Q0 += w0 * rxh; Q1 += w1 * rxh; Q2 += w2 * rxh; Qb += w0 * rxb;
+        Z1 += w1 * dh; Z2 += w2 * dh; Z3 += w3 * dh; Zb1 += w1 * db;
+      }
+    }
+    if (!south_done) {
+      finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
+                        lane, wsum + kSumS);
+      P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
+    }
+    finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1, lane,
+                      wsum + kSumN);
+
+    // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
+    const T hE = u > T(0) ? T(1) : (u < T(0) ? T(0) : T(0.5));
+    const T hW = u < T(0) ? T(1) : (u > T(0) ? T(0) : T(0.5));
+    T x[32];
+    const T uu = u * u;
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const T sg = sd == 0 ? T(1) : T(-1);
+      const T wgt = wu * (sd == 0 ? hE : hW);
+      const T F0 = A0 + sg * R0, F1 = A1 + sg * R1, F2 = A2 + sg * R2, Fb = Ab + sg * Rb;
+      T* o = x + 16 * sd;
+      o[0] = wgt * F0;
+      o[1] = wgt * u * F0;
+      o[2] = wgt * F1;
+      o[3] = wgt * (T(0.5) * (uu * F0 + F2) + T(0.5) * Fb);
+      const T ws = wgt * tdy;
+      o[4] = ws * C0;
+      o[5] = ws * u * C0;
+      o[6] = ws * C1;
+      o[7] = ws * (T(0.5) * (uu * C0 + C2) + T(0.5) * Cb);
+      const T wuu = wgt * u;
+      o[8] = wuu * F0;
+      o[9] = wuu * u * F0;
+      o[10] = wuu * F1;
+      o[11] = wuu * (T(0.5) * (uu * F0 + F2) + T(0.5) * Fb);
+      o[12] = wuu * D0;
+      o[13] = wuu * u * D0;
+      o[14] = wuu * D1;
+      o[15] = wuu * (T(0.5) * (uu * D0 + D2) + T(0.5) * Db);
+    }
+    const T r = warp_reduce_scatter<32>(x, lane);
+    wsum[kSumE + lane] += (double)r;  // lanes 0..15: E side, 16..31: W side
+  }
+  __syncwarp();
+  double* out = sums + (size_t)cell * kNSum;
+  out[lane] = wsum[lane];
+  out[lane + 32] = wsum[lane + 32];
+}
+
+// -------------------------------------------------------------------------------------
+// Steps S2-S5 per interface (FP64), plus the coefficients of S6/S8 for the update kernel.
+// -------------------------------------------------------------------------------------
+
+// Moments <x^n>, n = 0..6, of the normalised 1D Gaussian sqrt(lam/pi) exp(-lam (x-U)^2):
+// full range, x > 0 and x < 0.  Integration by parts gives
+// <x^{n+2}> = U <x^{n+1}> + (n+1)/(2 lam) <x^n> on every range.
+__device__ void gauss_moments7(double U, double lam, double* M, double* Mp, double* Mn) {
+  const double h = 0.5 / lam;
+  const double e = exp(-lam * U * U) * 0.5 * rsqrt(kPi * lam);
+  M[0] = 1.0;
+  M[1] = U;
+  Mp[0] = 0.5 * erfc(-sqrt(lam) * U);
+  Mn[0] = 0.5 * erfc(sqrt(lam) * U);
+  Mp[1] = U * Mp[0] + e;
+  Mn[1] = U * Mn[0] - e;
+#pragma unroll
+  for (int n = 0; n < 5; n++) {
+    M[n + 2] = U * M[n + 1] + (n + 1) * h * M[n];
+    Mp[n + 2] = U * Mp[n + 1] + (n + 1) * h * Mp[n];
+    Mn[n + 2] = U * Mn[n + 1] + (n + 1) * h * Mn[n];
+  }
+}
+
+// <u^a v^b psi> and <u^a v^b xi^2 psi> for the normalised Maxwellian, u-moments Mu (one
+// range), v-moments Mv, <xi^2> = X2, <xi^4> = X4.
+__device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, double X2, int a, int b,
+                                        double* o) {
+  o[0] = Mu[a] * Mv[b];
+  o[1] = Mu[a + 1] * Mv[b];
+  o[2] = Mu[a] * Mv[b + 1];
+  o[3] = 0.5 * (Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2] + Mu[a] * Mv[b] * X2);
+}
+__device__ __forceinline__ void psi_xi_mom(const double* Mu, const double* Mv, double X2, double X4,
+                                           int a, int b, double* o) {
+  o[0] = Mu[a] * Mv[b] * X2;
+  o[1] = Mu[a + 1] * Mv[b] * X2;
+  o[2] = Mu[a] * Mv[b + 1] * X2;
+  o[3] = 0.5 * ((Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2]) * X2 + Mu[a] * Mv[b] * X4);
+}
+// <u^a v^b psi (c . psi)>, c . psi = c1 + c2 u + c3 v + c4 (u^2 + v^2 + xi^2)/2
+__device__ void apsi_mom(const double* Mu, const double* Mv, double X2, double X4, int a, int b,
+                         const double* c, double* o) {
+  double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+  psi_mom(Mu, Mv, X2, a, b, t0);
+  psi_mom(Mu, Mv, X2, a + 1, b, t1);
+  psi_mom(Mu, Mv, X2, a, b + 1, t2);
+  psi_mom(Mu, Mv, X2, a + 2, b, t3);
+  psi_mom(Mu, Mv, X2, a, b + 2, t4);
+  psi_xi_mom(Mu, Mv, X2, X4, a, b, t5);
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    o[i] = c[0] * t0[i] + c[1] * t1[i] + c[2] * t2[i] + 0.5 * c[3] * (t3[i] + t4[i] + t5[i]);
+}
+
+// Micro-slope solve <psi (a . psi)> = s for the normalised Maxwellian (U, V, lam), closed
+// form obtained by centring the moments.
+__device__ void micro_slope(double U, double V, double lam, int K, const double* s, double* a) {
+  const double Kp2 = K + 2.0;
+  const double a4 = 4.0 * lam * lam / Kp2 *
+                    (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - Kp2 / (2.0 * lam)));
+  const double a3 = 2.0 * lam * (s[2] - V * s[0]) - V * a4;
+  const double a2 = 2.0 * lam * (s[1] - U * s[0]) - U * a4;
+  const double a1 = s[0] - U * a2 - V * a3 - a4 * (0.5 * (U * U + V * V) + Kp2 / (4.0 * lam));
+  a[0] = a1;
+  a[1] = a2;
+  a[2] = a3;
+  a[3] = a4;
+}
+
+// Time integrals over one step of the Eq. 2 weights, x = dt/tau:
+//   Mt1 = dt c1, Mt2 = dt^2 c2, Mt3 = dt^2 c3, Mt4 = dt c4, Mt5 = dt^2 c5
+//   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x,
+// by their Taylor series below x = 0.1 (no cancellation there).
+__device__ void time_weights(double dt, double tau, double* Mt) {
+  const double x = dt / tau;
+  double c1, c2, c3, c4, c5;
+  if (x < 0.1) {
+    // term n of each series via the ratio of consecutive terms; 16 terms
+    double t4 = 1.0, s4 = 1.0;             // c4: (-x)^n/(n+1)!
+    double t5 = 0.5, s5 = 0.5;             // c5: (-1)^n (n+1) x^n/(n+2)!  (via base b5 = (-x)^n/(n+2)!)
+    double b5 = 0.5;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int n = 1; n < 16; n++) {
+      t4 *= -x / (n + 1);                  // (-x)^n/(n+1)!
+      b5 *= -x / (n + 2);                  // (-x)^n/(n+2)!
+      t5 = (n + 1) * b5;
+      s4 += t4;
+      s5 += t5;
+      s1 -= t4;                            // c1 = sum_{n>=1} -(-x)^n/(n+1)!
+      s3 -= b5;                            // c3 = sum_{n>=1} -(-x)^n/(n+2)!
+      s2 += n * b5;                        // c2 = sum_{n>=1} n (-x)^n/(n+2)!
+    }
+    c1 = s1; c2 = s2; c3 = s3; c4 = s4; c5 = s5;
+  } else {
+    const double e = exp(-x), em = -expm1(-x);
+    c4 = em / x;
+    c1 = 1.0 - c4;
+    c5 = (c4 - e) / x;
+    c3 = 0.5 - c1 / x;
+    c2 = c5 - c1 / x;
+  }
+  Mt[0] = dt * c1;
+  Mt[1] = dt * dt * c2;
+  Mt[2] = dt * dt * c3;
+  Mt[3] = dt * c4;
+  Mt[4] = dt * dt * c5;
+}
+
+// Polynomial of (a . psi) g / g_h reduced over the internal variable, in the face frame:
+// P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2); component h or b.
+__device__ __forceinline__ void shape_h(const double* a, double X2, double* p) {
+  p[0] = a[0] + 0.5 * a[3] * X2;
+  p[1] = a[1];
+  p[2] = a[2];
+  p[3] = 0.5 * a[3];
+}
+__device__ __forceinline__ void shape_b(const double* a, double X2, double X4, double* p) {
+  p[0] = a[0] * X2 + 0.5 * a[3] * X4;
+  p[1] = a[1] * X2;
+  p[2] = a[2] * X2;
+  p[3] = 0.5 * a[3] * X2;
+}
+__device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const double* pa,
+                                      const double* pb, const double* pA, double* c) {
+  c[0] = M1 + Mt3 * pA[0];
+  c[1] = Mt3 * pA[1] + Mt2 * pa[0];
+  c[2] = Mt3 * pA[2] + Mt2 * pb[0];
+  c[3] = Mt3 * pA[3] + Mt2 * pa[1];
+  c[4] = Mt2 * (pa[2] + pb[1]);
+  c[5] = Mt3 * pA[3] + Mt2 * pb[2];
+  c[6] = Mt2 * pa[3];
+  c[7] = Mt2 * pb[3];
+}
+
+// One UGKS interface in the face frame (un, ut): inputs are the interface sums (S1, S7)
+// and the cell W on both sides; output the time-integrated macroscopic flux F and the
+// micro-flux record.
+__device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
+                          const double* Ss, const double* WL, const double* WR, double delta,
+                          double* F, FaceRec& R) {
+  const int K = P.K;
+  // S2: interface primitive variables and Maxwellian moments
+  const double rho = W0[0], U = W0[1] / rho, V = W0[2] / rho;
+  const double lam = (K + 2) * rho / (4.0 * (W0[3] - 0.5 * rho * (U * U + V * V)));
+  double Mu[7], Mup[7], Mun[7], Mv[7], Mvp[7], Mvn[7];
+  gauss_moments7(U, lam, Mu, Mup, Mun);
+  gauss_moments7(V, lam, Mv, Mvp, Mvn);
+  const double X2 = K / (2.0 * lam), X4 = (K * K + 2.0 * K) / (4.0 * lam * lam);
+  // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5
+  const double tau = P.mu_ref * pow(lam, -P.omega) * 2.0 * lam / rho;
+  double Mt[5];
+  time_weights(P.dt, tau, Mt);
+  // S4: micro slopes
+  const double inv = 2.0 / (rho * delta);
+  double sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    sL[c] = (W0[c] - WL[c]) * inv;
+    sR[c] = (WR[c] - W0[c]) * inv;
+    sT[c] = St[c] / rho;
+  }
+  micro_slope(U, V, lam, K, sL, aL);
+  micro_slope(U, V, lam, K, sR, aR);
+  micro_slope(U, V, lam, K, sT, b);
+  double t1[4], t2[4], t3[4], t4[4], p1[4];
+  apsi_mom(Mup, Mv, X2, X4, 1, 0, aL, t1);
+  apsi_mom(Mun, Mv, X2, X4, 1, 0, aR, t2);
+  apsi_mom(Mu, Mv, X2, X4, 0, 1, b, t3);
+#pragma unroll
+  for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
+  micro_slope(U, V, lam, K, sA, A);
+  // S5: equilibrium part of the macroscopic flux; S7 free transport part from the sums
+  psi_mom(Mu, Mv, X2, 1, 0, p1);
+  apsi_mom(Mup, Mv, X2, X4, 2, 0, aL, t1);
+  apsi_mom(Mun, Mv, X2, X4, 2, 0, aR, t2);
+  apsi_mom(Mu, Mv, X2, X4, 1, 1, b, t3);
+  apsi_mom(Mu, Mv, X2, X4, 1, 0, A, t4);
+#pragma unroll
+  for (int c = 0; c < 4; c++)
+    F[c] = rho * (Mt[0] * p1[c] + Mt[1] * (t1[c] + t2[c] + t3[c]) + Mt[2] * t4[c]) + Mt[3] * Sf[c] -
+           Mt[4] * Ss[c];
+  // S6/S8 coefficients
+  double pa[4], pb[4], pA[4];
+  for (int sd = 0; sd < 2; sd++) {
+    const double* as = sd == 0 ? aL : aR;
+    shape_h(as, X2, pa);
+    shape_h(b, X2, pb);
+    shape_h(A, X2, pA);
+    qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
+    shape_b(as, X2, X4, pa);
+    shape_b(b, X2, X4, pb);
+    shape_b(A, X2, X4, pA);
+    qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
+  }
+  R.G = rho * lam / kPi;
+  R.Un = U;
+  R.Ut = V;
+  R.lam = lam;
+  R.Mt4 = Mt[3];
+  R.Mt5 = Mt[4];
+  R.bfac = X2;
+  R.wall = 0;
+}
+
+__global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
+                        int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
+                        double* __restrict__ Fx, double* __restrict__ Fy) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nx = P.nx, ny = P.ny;
+  const int nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
+  if (t >= nfx + nfy) return;
+  const bool isx = t < nfx;
+  int i, j, cL, cR, oL, oR, wall = 0, side = 0;
+  double delta;
+  if (isx) {
+    j = t / (nx + 1);
+    i = t % (nx + 1) - 1;
+    cL = wcell(P, i, j);
+    cR = wcell(P, i + 1, j);
+    oL = kSumE;
+    oR = kSumW;
+    delta = P.dx;
+    if (i == -1 && P.bc_kind[0] == 1) { wall = 1; side = 0; }
+    if (i == nx - 1 && P.bc_kind[1] == 1) { wall = 2; side = 1; }
+  } else {
+    const int t2 = t - nfx;
+    j = t2 / nx - 1;
+    i = t2 % nx;
+    cL = wcell(P, i, j);
+    cR = wcell(P, i, j + 1);
+    oL = kSumN;
+    oR = kSumS;
+    delta = P.dy;
+    if (j == -1 && P.bc_kind[2] == 1) { wall = 1; side = 2; }
+    if (j == ny - 1 && P.bc_kind[3] == 1) { wall = 2; side = 3; }
+  }
+  FaceRec R;
+  double F[4];
+  if (wall) {
+    // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
+    // with the density that cancels the mass flux; first order in time
+    const double* Sin = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
+                                  : sums + (size_t)cL * kNSum + oL + kOffSf;
+    const double rhow = -Sin[0] / P.wall_mom[side][0];
+#pragma unroll
+    for (int c = 0; c < 4; c++) F[c] = P.dt * (Sin[c] + rhow * P.wall_mom[side][c]);
+    const double lam = 1.0 / P.bc_T[side];
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int c = 0; c < 8; c++) R.Q[a][b][c] = 0.0;
+    R.G = rhow * lam / kPi;
+    R.Un = 0.0;
+    R.Ut = P.bc_U[side];
+    R.lam = lam;
+    R.Mt4 = P.dt;
+    R.Mt5 = 0.0;
+    R.bfac = P.K / (2.0 * lam);
+    R.wall = wall;
+  } else {
+    const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
+    const double* sL = sums + (size_t)cL * kNSum + oL;
+    const double* sR = sums + (size_t)cR * kNSum + oR;
+    double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const int s = pm[c];
+      W0[c] = sL[kOffW0 + s] + sR[kOffW0 + s];
+      St[c] = sL[kOffSt + s] + sR[kOffSt + s];
+      Sf[c] = sL[kOffSf + s] + sR[kOffSf + s];
+      Ss[c] = sL[kOffSs + s] + sR[kOffSs + s];
+      WL[c] = W[s * nwe + cL];
+      WR[c] = W[s * nwe + cR];
+    }
+    face_math(P, W0, St, Sf, Ss, WL, WR, delta, Fr, R);
+#pragma unroll
+    for (int c = 0; c < 4; c++) F[pm[c]] = Fr[c];
+  }
+  if (isx) {
+    fxr[t] = R;
+    for (int c = 0; c < 4; c++) Fx[4 * (size_t)t + c] = F[c];
+  } else {
+    fyr[t - nfx] = R;
+    for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Eq. 4 per cell, plus g^n, g^{n+1}, tau^n, tau^{n+1} for Eq. 3, residual partials and
+// the numerical-failure flag.
+// -------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_cells(Params P, const double* __restrict__ Win,
+                                               double* __restrict__ Wout, int nwe,
+                                               const double* __restrict__ Fx,
+                                               const double* __restrict__ Fy,
+                                               CellRec* __restrict__ cr, double* __restrict__ rpart,
+                                               int* __restrict__ err) {
+  __shared__ double red[8][128];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nx = P.nx, nc = P.nx * P.ny;
+  double d2[4] = {0, 0, 0, 0}, am[4] = {0, 0, 0, 0};
+  if (c < nc) {
+    const int i = c % nx, j = c / nx;
+    const size_t xw = (size_t)j * (nx + 1) + i, xe = xw + 1;
+    const size_t ys = (size_t)j * nx + i, yn = (size_t)(j + 1) * nx + i;
+    const int w = wcell(P, i, j);
+    double Wn[4], W1[4];
+    for (int k = 0; k < 4; k++) {
+      Wn[k] = Win[k * nwe + w];
+      W1[k] = Wn[k] + (Fx[4 * xw + k] - Fx[4 * xe + k]) / P.dx + (Fy[4 * ys + k] - Fy[4 * yn + k]) / P.dy;
+      Wout[k * nwe + w] = W1[k];
+      d2[k] = (W1[k] - Wn[k]) * (W1[k] - Wn[k]);
+      am[k] = fabs(W1[k]);
+    }
+    const int K = P.K;
+    const double rn = Wn[0], Un = Wn[1] / rn, Vn = Wn[2] / rn;
+    const double ln = (K + 2) * rn / (4.0 * (Wn[3] - 0.5 * rn * (Un * Un + Vn * Vn)));
+    const double r1 = W1[0], U1 = W1[1] / r1, V1 = W1[2] / r1;
+    const double l1 = (K + 2) * r1 / (4.0 * (W1[3] - 0.5 * r1 * (U1 * U1 + V1 * V1)));
+    if (!(r1 > 0.0) || !(l1 > 0.0) || !isfinite(l1) || !isfinite(U1) || !isfinite(V1))
+      atomicOr(err, 1);
+    const double tn = P.mu_ref * pow(ln, -P.omega) * 2.0 * ln / rn;
+    const double t1 = P.mu_ref * pow(l1, -P.omega) * 2.0 * l1 / r1;
+    CellRec R;
+    R.Gn = rn * ln / kPi; R.Un = Un; R.Vn = Vn; R.lamn = ln; R.bn = K / (2.0 * ln);
+    R.G1 = r1 * l1 / kPi; R.U1 = U1; R.V1 = V1; R.lam1 = l1; R.b1 = K / (2.0 * l1);
+    R.cgn = P.dt / (2.0 * tn);
+    R.cf = 1.0 - R.cgn;
+    R.cg1 = P.dt / (2.0 * t1);
+    R.inv = 1.0 / (1.0 + R.cg1);
+    cr[c] = R;
+  }
+  for (int k = 0; k < 4; k++) {
+    red[k][threadIdx.x] = d2[k];
+    red[4 + k][threadIdx.x] = am[k];
+  }
+  __syncthreads();
+  for (int s = 64; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 4; k++) {
+        red[k][threadIdx.x] += red[k][threadIdx.x + s];
+        red[4 + k][threadIdx.x] = fmax(red[4 + k][threadIdx.x], red[4 + k][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) rpart[(size_t)blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// -------------------------------------------------------------------------------------
+// S6 + S8 and Eq. 3: micro flux of the four faces from the upwind reconstruction and the
+// face records, implicit collision update.  One warp per interior cell, lane = u index,
+// loop over v.
+// -------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void poly_in_v_xface(const double* c, T u, T* q) {
+  // face frame un = u (fixed), ut = v: Q = q0 + q1 v + q2 v^2 + q3 v^3
+  const double uu = (double)u;
+  q[0] = (T)(c[0] + uu * (c[1] + uu * (c[3] + uu * c[6])));
+  q[1] = (T)(c[2] + uu * (c[4] + uu * c[7]));
+  q[2] = (T)(c[5] + uu * c[6]);
+  q[3] = (T)c[7];
+}
+template <typename T>
+__device__ __forceinline__ void poly_in_v_yface(const double* c, T u, T* q) {
+  // face frame un = v, ut = u (fixed): Q = q0 + q1 v + q2 v^2 + q3 v^3
+  const double uu = (double)u;
+  q[0] = (T)(c[0] + uu * (c[2] + uu * (c[5] + uu * c[7])));
+  q[1] = (T)(c[1] + uu * (c[4] + uu * c[6]));
+  q[2] = (T)(c[3] + uu * c[7]);
+  q[3] = (T)c[6];
+}
+
+template <typename T, typename T2>
+__global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__ f,
+                                                T2* __restrict__ fo,
+                                                const FaceRec* __restrict__ fxr,
+                                                const FaceRec* __restrict__ fyr,
+                                                const CellRec* __restrict__ cr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nv = P.nv, nu = P.nu, nq = P.nq, nx = P.nx, ny = P.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* sv = reinterpret_cast<T*>(smraw);
+  T* ev = sv + nv + warp * 6 * nv;  // [6][nv]: x W, x E, y S, y N, g^n, g^{n+1} factors in v
+  for (int m = tid; m < nv; m += blockDim.x) sv[m] = (T)P.v[m];
+  __syncthreads();
+  const int cell = blockIdx.x * kWarpsPerBlock + warp;
+  if (cell >= nx * ny) return;
+  const int i = cell % nx, j = cell / nx;
+  const FaceRec* Rf[4] = {fxr + (size_t)j * (nx + 1) + i, fxr + (size_t)j * (nx + 1) + i + 1,
+                          fyr + (size_t)j * nx + i, fyr + (size_t)(j + 1) * nx + i};
+  const CellRec C = cr[cell];
+  for (int m = lane; m < nv; m += 32) {
+    const double vv = P.v[m];
+    for (int s = 0; s < 2; s++) {  // x faces: ut = v
+      const double d = vv - Rf[s]->Ut;
+      ev[s * nv + m] = (T)exp(-Rf[s]->lam * d * d);
+    }
+    for (int s = 2; s < 4; s++) {  // y faces: un = v
+      const double d = vv - Rf[s]->Un;
+      ev[s * nv + m] = (T)exp(-Rf[s]->lam * d * d);
+    }
+    double d = vv - C.Vn;
+    ev[4 * nv + m] = (T)exp(-C.lamn * d * d);
+    d = vv - C.V1;
+    ev[5 * nv + m] = (T)exp(-C.lam1 * d * d);
+  }
+  __syncwarp();
+
+  const int wallW = Rf[0]->wall, wallE = Rf[1]->wall, wallS = Rf[2]->wall, wallN = Rf[3]->wall;
+  const T Mt4[4] = {(T)Rf[0]->Mt4, (T)Rf[1]->Mt4, (T)Rf[2]->Mt4, (T)Rf[3]->Mt4};
+  const T Mt5[4] = {(T)Rf[0]->Mt5, (T)Rf[1]->Mt5, (T)Rf[2]->Mt5, (T)Rf[3]->Mt5};
+  const T bf[4] = {(T)Rf[0]->bfac, (T)Rf[1]->bfac, (T)Rf[2]->bfac, (T)Rf[3]->bfac};
+  const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy), idx = T(1.0 / P.dx), idy = T(1.0 / P.dy);
+  const T dtT = (T)P.dt;
+  const size_t rs = (size_t)P.ex * nq;
+  const T2* fc0 = f + fcell(P, i, j) * nq;
+  T2* fo0 = fo + fcell(P, i, j) * nq;
+  const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
+
+  for (int k0 = 0; k0 < nu; k0 += 32) {
+    const int k = k0 + lane;
+    const bool act = k < nu;
+    const int kk = act ? k : nu - 1;
+    const double ud = P.u[kk];
+    const T u = (T)ud;
+    // per-lane factors in u
+    T gu[4];
+    for (int s = 0; s < 2; s++) {
+      const double d = ud - Rf[s]->Un;
+      gu[s] = (T)(Rf[s]->G * exp(-Rf[s]->lam * d * d));
+    }
+    for (int s = 2; s < 4; s++) {
+      const double d = ud - Rf[s]->Ut;
+      gu[s] = (T)(Rf[s]->G * exp(-Rf[s]->lam * d * d));
+    }
+    double d = ud - C.Un;
+    const T gun = (T)(C.Gn * exp(-C.lamn * d * d));
+    d = ud - C.U1;
+    const T gu1 = (T)(C.G1 * exp(-C.lam1 * d * d));
+    // x-face polynomial in v, side fixed by the sign of u
+    const int xs = ud > 0.0 ? 0 : 1;
+    T qW[2][4], qE[2][4], qS[2][4], qN[2][4];
+    for (int c = 0; c < 2; c++) {
+      poly_in_v_xface(Rf[0]->Q[xs][c], u, qW[c]);
+      poly_in_v_xface(Rf[1]->Q[xs][c], u, qE[c]);
+      poly_in_v_yface(Rf[2]->Q[1][c], u, qS[c]);  // v < 0 first: the u_n < 0 side
+      poly_in_v_yface(Rf[3]->Q[1][c], u, qN[c]);
+    }
+    const bool up = ud > 0.0;  // x upwind neighbour: W for u > 0, E for u < 0
+    const long xo = up ? -(long)nq : (long)nq;
+    const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
+    const T cu = u * tdx, fxu = u * idx;
+    bool yswitched = false;
+    for (int m = 0; m < nv; m++) {
+      const T vv = sv[m];
+      if (!yswitched && vv > T(0)) {
+        for (int c = 0; c < 2; c++) {
+          poly_in_v_yface(Rf[2]->Q[0][c], u, qS[c]);
+          poly_in_v_yface(Rf[3]->Q[0][c], u, qN[c]);
+        }
+        yswitched = true;
+      }
+      const bool vup = vv > T(0);
+      const long yo = vup ? -(long)rs : (long)rs;
+      const bool yz = (vup && j == 0 && pS) || (!vup && j == ny - 1 && pN);
+      const T2* p = fc0 + (size_t)m * nu + kk;
+      const T2 c = p[0], w = p[-(long)nq], e = p[nq], s = p[-(long)rs], n = p[rs];
+      const T2 xf = p[2 * xo], xs_ = p[xo - (long)rs], xn = p[xo + (long)rs];
+      const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
+      const T2 xu = up ? w : e, yu = vup ? s : n;
+      // half slopes r = sigma h / 2 of the cell, its x-upwind and its y-upwind neighbour
+      const T rxch = vl_half(w.x, c.x, e.x), rxcb = vl_half(w.y, c.y, e.y);
+      const T rych = vl_half(s.x, c.x, n.x), rycb = vl_half(s.y, c.y, n.y);
+      T rxuh, rxub, ryuh, ryub, rxvh, rxvb, ryvh, ryvb;
+      if (up) { rxuh = vl_half(xf.x, w.x, c.x); rxub = vl_half(xf.y, w.y, c.y); }
+      else    { rxuh = vl_half(c.x, e.x, xf.x); rxub = vl_half(c.y, e.y, xf.y); }
+      ryuh = vl_half(xs_.x, xu.x, xn.x);
+      ryub = vl_half(xs_.y, xu.y, xn.y);
+      rxvh = vl_half(yw.x, yu.x, ye.x);
+      rxvb = vl_half(yw.y, yu.y, ye.y);
+      if (vup) { ryvh = vl_half(yf.x, s.x, c.x); ryvb = vl_half(yf.y, s.y, c.y); }
+      else     { ryvh = vl_half(c.x, n.x, yf.x); ryvb = vl_half(c.y, n.y, yf.y); }
+      if (xz) rxuh = rxub = ryuh = ryub = T(0);
+      if (yz) rxvh = rxvb = ryvh = ryvb = T(0);
+      const T cv = vv * tdy, fyv = vv * idy;
+      // (u sigma_x + v sigma_y) of the three cells
+      const T dch = cu * rxch + cv * rych, dcb = cu * rxcb + cv * rycb;
+      const T duh = cu * rxuh + cv * ryuh, dub = cu * rxub + cv * ryub;
+      const T dvh = cu * rxvh + cv * ryvh, dvb = cu * rxvb + cv * ryvb;
+      // upwind interface values and slope terms at the four faces
+      T fWh, fWb, dWh, dWb, fEh, fEb, dEh, dEb;
+      if (up) {
+        fEh = c.x + rxch; fEb = c.y + rxcb; dEh = dch; dEb = dcb;
+        fWh = xu.x + rxuh; fWb = xu.y + rxub; dWh = duh; dWb = dub;
+      } else {
+        fWh = c.x - rxch; fWb = c.y - rxcb; dWh = dch; dWb = dcb;
+        fEh = xu.x - rxuh; fEb = xu.y - rxub; dEh = duh; dEb = dub;
+      }
+      T fSh, fSb, dSh, dSb, fNh, fNb, dNh, dNb;
+      if (vup) {
+        fNh = c.x + rych; fNb = c.y + rycb; dNh = dch; dNb = dcb;
+        fSh = yu.x + ryvh; fSb = yu.y + ryvb; dSh = dvh; dSb = dvb;
+      } else {
+        fSh = c.x - rych; fSb = c.y - rycb; dSh = dch; dSb = dcb;
+        fNh = yu.x - ryvh; fNb = yu.y - ryvb; dNh = dvh; dNb = dvb;
+      }
+      // X = Q g + Mt4 f_up - Mt5 d  (UGKS face),  X = dt f_w (wall); F~ = u_n X
+      T XWh, XWb, XEh, XEb, XSh, XSb, XNh, XNb;
+      {
+        const T g = gu[0] * ev[m];
+        if (wallW) {
+          const bool inc = !up;  // gas on the high side: incoming u < 0
+          XWh = dtT * (inc ? fWh : g);
+          XWb = dtT * (inc ? fWb : bf[0] * g);
+        } else {
+          const T Qh = ((qW[0][3] * vv + qW[0][2]) * vv + qW[0][1]) * vv + qW[0][0];
+          const T Qb = ((qW[1][3] * vv + qW[1][2]) * vv + qW[1][1]) * vv + qW[1][0];
+          XWh = Qh * g + Mt4[0] * fWh - Mt5[0] * dWh;
+          XWb = Qb * g + Mt4[0] * fWb - Mt5[0] * dWb;
+        }
+      }
+      {
+        const T g = gu[1] * ev[nv + m];
+        if (wallE) {
+          const bool inc = up;  // gas on the low side: incoming u > 0
+          XEh = dtT * (inc ? fEh : g);
+          XEb = dtT * (inc ? fEb : bf[1] * g);
+        } else {
+          const T Qh = ((qE[0][3] * vv + qE[0][2]) * vv + qE[0][1]) * vv + qE[0][0];
+          const T Qb = ((qE[1][3] * vv + qE[1][2]) * vv + qE[1][1]) * vv + qE[1][0];
+          XEh = Qh * g + Mt4[1] * fEh - Mt5[1] * dEh;
+          XEb = Qb * g + Mt4[1] * fEb - Mt5[1] * dEb;
+        }
+      }
+      {
+        const T g = gu[2] * ev[2 * nv + m];
+        if (wallS) {
+          const bool inc = !vup;
+          XSh = dtT * (inc ? fSh : g);
+          XSb = dtT * (inc ? fSb : bf[2] * g);
+        } else {
+          const T Qh = ((qS[0][3] * vv + qS[0][2]) * vv + qS[0][1]) * vv + qS[0][0];
+          const T Qb = ((qS[1][3] * vv + qS[1][2]) * vv + qS[1][1]) * vv + qS[1][0];
+          XSh = Qh * g + Mt4[2] * fSh - Mt5[2] * dSh;
+          XSb = Qb * g + Mt4[2] * fSb - Mt5[2] * dSb;
+        }
+      }
+      {
+        const T g = gu[3] * ev[3 * nv + m];
+        if (wallN) {
+          const bool inc = vup;
+          XNh = dtT * (inc ? fNh : g);
+          XNb = dtT * (inc ? fNb : bf[3] * g);
+        } else {
+          const T Qh = ((qN[0][3] * vv + qN[0][2]) * vv + qN[0][1]) * vv + qN[0][0];
+          const T Qb = ((qN[1][3] * vv + qN[1][2]) * vv + qN[1][1]) * vv + qN[1][0];
+          XNh = Qh * g + Mt4[3] * fNh - Mt5[3] * dNh;
+          XNb = Qb * g + Mt4[3] * fNb - Mt5[3] * dNb;
+        }
+      }
+      const T flh = fxu * (XWh - XEh) + fyv * (XSh - XNh);
+      const T flb = fxu * (XWb - XEb) + fyv * (XSb - XNb);
+      const T gnh = gun * ev[4 * nv + m], g1h = gu1 * ev[5 * nv + m];
+      T2 o;
+      o.x = (T)C.inv * ((T)C.cf * c.x + flh + (T)C.cg1 * g1h + (T)C.cgn * gnh);
+      o.y = (T)C.inv * ((T)C.cf * c.y + flb + (T)(C.cg1 * C.b1) * g1h + (T)(C.cgn * C.bn) * gnh);
+      if (act) fo0[(size_t)m * nu + kk] = o;
+    }
+  }
+}
+
+}  // namespace ugks

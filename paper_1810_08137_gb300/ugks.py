@@ -1,0 +1,213 @@
+"""Python binding of libugks.so (include/ugks.h): argument marshalling only.
+
+Every step of the UGKS path runs in the CUDA library; this module converts arguments,
+checks statuses and raises.  There is no CPU fallback: without the compiled library
+(or without a GPU) the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_STATUS = {0: "UGKS_OK", 1: "UGKS_EINVAL", 2: "UGKS_ENOMEM", 3: "UGKS_ECUDA",
+           4: "UGKS_ETIMEOUT", 5: "UGKS_ENUMERIC"}
+FP64, FP32F = 0, 1
+
+# Every symbol include/ugks.h declares.
+EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
+           "ugks_device_bytes", "ugks_set_state", "ugks_set_state_device",
+           "ugks_init_maxwellian", "ugks_step", "ugks_sync", "ugks_moments", "ugks_get_state",
+           "ugks_get_state_device", "ugks_residual", "ugks_profile", "ugks_kernel_times",
+           "ugks_kernel_name")
+NKERNELS = 6
+
+
+class UGKSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _BC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("rho", C.c_double), ("T", C.c_double), ("U", C.c_double)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int), ("umin", C.c_double), ("umax", C.c_double),
+                ("vmin", C.c_double), ("vmax", C.c_double), ("K", C.c_int), ("kn", C.c_double),
+                ("omega", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
+                ("dt", C.c_double), ("bc", _BC * 4), ("precision", C.c_int)]
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libugks.so (building it first if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise OSError(f"{_build.LIB} is missing; run paper_1810_08137_gb300.build.build()")
+            _build.build()
+        L = C.CDLL(_build.LIB)
+        L.ugks_create.argtypes = [C.POINTER(_Config), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.ugks_destroy.argtypes = [C.c_void_p]
+        L.ugks_destroy.restype = None
+        L.ugks_last_error.argtypes = [C.c_void_p]
+        L.ugks_last_error.restype = C.c_char_p
+        L.ugks_device_bytes.argtypes = [C.c_void_p]
+        L.ugks_device_bytes.restype = C.c_size_t
+        L.ugks_get_grid.argtypes = [C.c_void_p, _P, _P, _P, _P]
+        for name in ("ugks_set_state", "ugks_get_state", "ugks_moments"):
+            getattr(L, name).argtypes = [C.c_void_p, _P, _P]
+        for name in ("ugks_set_state_device", "ugks_get_state_device"):
+            getattr(L, name).argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ugks_init_maxwellian.argtypes = [C.c_void_p, _P, _P, _P, _P]
+        L.ugks_step.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_sync.argtypes = [C.c_void_p]
+        L.ugks_residual.argtypes = [C.c_void_p, _P]
+        L.ugks_profile.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_kernel_times.argtypes = [C.c_void_p, _P, C.POINTER(C.c_long)]
+        L.ugks_kernel_name.argtypes = [C.c_int]
+        L.ugks_kernel_name.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def to_c_config(cfg, precision: int = FP64) -> _Config:
+    c = _Config()
+    for k in ("nx", "ny", "nu", "nv", "K"):
+        setattr(c, k, int(getattr(cfg, k)))
+    for k in ("lx", "ly", "umin", "umax", "vmin", "vmax", "kn", "omega", "alpha", "cfl", "dt"):
+        setattr(c, k, float(getattr(cfg, k)))
+    for s in range(4):
+        b = cfg.bc[s]
+        c.bc[s].kind, c.bc[s].rho, c.bc[s].T, c.bc[s].U = int(b.kind), float(b.rho), float(b.T), float(b.U)
+    c.precision = int(precision)
+    return c
+
+
+def _arr(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} values, got {a.size}")
+    return a
+
+
+def _dptr(x) -> int:
+    """Device pointer of a torch CUDA tensor (float64, contiguous) or an int address."""
+    if isinstance(x, int):
+        return x
+    if not (x.is_cuda and x.is_contiguous()) or str(x.dtype) != "torch.float64":
+        raise ValueError("device buffers must be contiguous float64 CUDA tensors")
+    return x.data_ptr()
+
+
+class Solver:
+    """One UGKS instance on the GPU (ugks_create ... ugks_destroy)."""
+
+    def __init__(self, cfg, precision: int = FP64, stream=None):
+        self.cfg = cfg
+        self.precision = precision
+        self._L = lib()
+        self._h = C.c_void_p()
+        c = to_c_config(cfg, precision)
+        st = self._L.ugks_create(C.byref(c), C.c_void_p(stream or 0), C.byref(self._h))
+        if st:
+            raise UGKSError(st, "ugks_create failed (see stderr)")
+        self.nc, self.nq = cfg.nx * cfg.ny, cfg.nu * cfg.nv
+
+    def _check(self, st: int):
+        if st:
+            raise UGKSError(st, self._L.ugks_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._L.ugks_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self._L.ugks_device_bytes(self._h))
+
+    def grid(self):
+        dt = C.c_double()
+        u, v, w = np.empty(self.cfg.nu), np.empty(self.cfg.nv), np.empty(self.nq)
+        self._check(self._L.ugks_get_grid(self._h, C.byref(dt), u.ctypes.data_as(_P),
+                                          v.ctypes.data_as(_P), w.ctypes.data_as(_P)))
+        return dt.value, u, v, w
+
+    def set_state(self, f, W):
+        f = _arr(f, (self.nc, self.nq, 2))
+        W = _arr(W, (4, self.nc))
+        self._check(self._L.ugks_set_state(self._h, f.ctypes.data_as(_P), W.ctypes.data_as(_P)))
+
+    def set_state_device(self, f_dev, W_dev):
+        self._check(self._L.ugks_set_state_device(self._h, C.c_void_p(_dptr(f_dev)),
+                                                  C.c_void_p(_dptr(W_dev))))
+
+    def init_maxwellian(self, rho, U, V, T):
+        a = [_arr(x, (self.nc,)) for x in (rho, U, V, T)]
+        self._check(self._L.ugks_init_maxwellian(self._h, *[x.ctypes.data_as(_P) for x in a]))
+
+    def step(self, n: int = 1):
+        self._check(self._L.ugks_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.ugks_sync(self._h))
+
+    def moments(self, prim: bool = False):
+        W = np.empty((4, self.nc))
+        p = np.empty((4, self.nc)) if prim else None
+        self._check(self._L.ugks_moments(self._h, W.ctypes.data_as(_P),
+                                         p.ctypes.data_as(_P) if prim else None))
+        return (W, p) if prim else W
+
+    def get_state(self):
+        f = np.empty((self.nc, self.nq, 2))
+        W = np.empty((4, self.nc))
+        self._check(self._L.ugks_get_state(self._h, f.ctypes.data_as(_P), W.ctypes.data_as(_P)))
+        return f, W
+
+    def get_state_device(self, f_dev, W_dev):
+        self._check(self._L.ugks_get_state_device(self._h, C.c_void_p(_dptr(f_dev)),
+                                                  C.c_void_p(_dptr(W_dev))))
+
+    def profile(self, enable: bool = True):
+        self._check(self._L.ugks_profile(self._h, int(bool(enable))))
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (launches, total ms)} of the steps recorded since profile(True)."""
+        ms = np.zeros(NKERNELS)
+        n = (C.c_long * NKERNELS)()
+        self._check(self._L.ugks_kernel_times(self._h, ms.ctypes.data_as(_P), n))
+        return {self._L.ugks_kernel_name(k).decode(): (int(n[k]), float(ms[k]))
+                for k in range(NKERNELS)}
+
+    def residual(self) -> np.ndarray:
+        r = np.empty(4)
+        self._check(self._L.ugks_residual(self._h, r.ctypes.data_as(_P)))
+        return r
