@@ -86,6 +86,11 @@ typedef struct {
   double dt;             /* > 0: fixed time step */
   ugks_bc bc[4];         /* W, E, S, N; periodic must be paired (W with E, S with N) */
   int precision;         /* ugks_precision */
+  /* UGKS_FP32F only: reference Maxwellian g_ref(rho, U, V, T).  The FP32 buffers hold
+   * f - g_ref and every velocity sum and flux adds the exact FP64 contribution of g_ref,
+   * so FP32 rounding acts on the (small) deviation from it.  ref_T <= 0 selects
+   * (1, 0, 0, 1).  The state exchanged through this ABI is always f itself. */
+  double ref_rho, ref_U, ref_V, ref_T;
 } ugks_config;
 
 typedef struct ugks_ctx* ugks_handle;

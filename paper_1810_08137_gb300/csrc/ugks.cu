@@ -36,6 +36,7 @@ struct ugks_ctx {
   int* err = nullptr;
   double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv]
   double* stage = nullptr;   // FP64 staging for FP32 state conversion
+  float2* gref = nullptr;    // FP32 form: g_ref per velocity
   size_t stage_bytes = 0;
   std::vector<double> hu, hv, hwu, hwv;
   size_t bytes = 0;
@@ -117,8 +118,8 @@ cudaError_t set_smem_limits(int nv) {
   cudaError_t e = cudaFuncSetAttribute(k_sums<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_sums<T>(nv));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_update<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_update<T>(nv));
+  return cudaFuncSetAttribute(k_update<T, T2, (sizeof(T) == 4)>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_update<T>(nv));
 }
 
 const char* const kKernelNames[UGKS_NKERNELS] = {"ghost_x", "ghost_y", "sums", "faces", "cells",
@@ -162,8 +163,9 @@ cudaError_t launch_step(ugks_ctx* h) {
   const int nc = P.nx * P.ny;
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  k_update<T, T2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
-      P, fi, fo, h->fxr, h->fyr, h->cells);
+  k_update<T, T2, (sizeof(T) == 4)>
+      <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
+          P, fi, fo, h->fxr, h->fyr, h->cells);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
@@ -178,9 +180,11 @@ __global__ void k_rows_to_f32(const double* __restrict__ src, float2* __restrict
     const int r = (int)(t / row);
     const size_t o = t % row;
     const int i = (int)(o / P.nq), q = (int)(o % P.nq);
+    double rh, rb;
+    ref_maxwellian(P, P.u[q % P.nu], P.v[q / P.nu], rh, rb);
     float2 v;
-    v.x = (float)src[2 * t];
-    v.y = (float)src[2 * t + 1];
+    v.x = (float)(src[2 * t] - rh);
+    v.y = (float)(src[2 * t + 1] - rb);
     dst[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q] = v;
   }
 }
@@ -193,8 +197,10 @@ __global__ void k_f32_to_rows(const float2* __restrict__ src, double* __restrict
     const size_t o = t % row;
     const int i = (int)(o / P.nq), q = (int)(o % P.nq);
     const float2 v = src[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q];
-    dst[2 * t] = v.x;
-    dst[2 * t + 1] = v.y;
+    double rh, rb;
+    ref_maxwellian(P, P.u[q % P.nu], P.v[q / P.nu], rh, rb);
+    dst[2 * t] = (double)v.x + rh;
+    dst[2 * t + 1] = (double)v.y + rb;
   }
 }
 
@@ -212,9 +218,11 @@ __global__ void k_init_maxwellian(Params P, const double* __restrict__ prim, T2*
     const int k = q % P.nu, m = q / P.nu;
     const double du = P.u[k] - U, dv = P.v[m] - V;
     const double gh = G * exp(-lam * (du * du + dv * dv));
+    double rh, rb;
+    ref_maxwellian(P, P.u[k], P.v[m], rh, rb);
     T2 o;
-    o.x = gh;
-    o.y = bf * gh;
+    o.x = gh - rh;
+    o.y = bf * gh - rb;
     dst[q] = o;
   }
   if (threadIdx.x == 0) {
@@ -380,6 +388,38 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     for (int c = 0; c < 4; c++) P.wall_mom[s][c] = m[c];
   }
 
+  P.m_pos = P.nv;
+  for (int m = 0; m < P.nv; m++)
+    if (h->hv[m] > 0) { P.m_pos = m; break; }
+  std::vector<float2> gref_host;
+  if (h->prec == UGKS_FP32F) {
+    double rr = cfg->ref_rho, rU = cfg->ref_U, rV = cfg->ref_V, rT = cfg->ref_T;
+    if (!(rT > 0) || !(rr > 0)) { rr = 1.0; rU = 0.0; rV = 0.0; rT = 1.0; }
+    P.use_ref = 1;
+    P.ref_lam = 1.0 / rT;
+    P.ref_G = rr * P.ref_lam / M_PI;
+    P.ref_U = rU;
+    P.ref_V = rV;
+    P.ref_bf = P.K / (2.0 * P.ref_lam);
+    gref_host.resize((size_t)P.nq);
+    for (int m = 0; m < P.nv; m++)
+      for (int k = 0; k < P.nu; k++) {
+        const double u = h->hu[k], v = h->hv[m], w = h->hwu[k] * h->hwv[m];
+        double gh, gb;
+        ref_maxwellian(P, u, v, gh, gb);
+        gref_host[(size_t)m * P.nu + k] = make_float2((float)gh, (float)gb);
+        const double psi[4] = {gh, u * gh, v * gh, 0.5 * (u * u + v * v) * gh + 0.5 * gb};
+        const double hs[4] = {u > 0 ? 1.0 : (u < 0 ? 0.0 : 0.5), u < 0 ? 1.0 : (u > 0 ? 0.0 : 0.5),
+                              v > 0 ? 1.0 : (v < 0 ? 0.0 : 0.5), v < 0 ? 1.0 : (v > 0 ? 0.0 : 0.5)};
+        const double un[4] = {u, u, v, v};
+        for (int sd = 0; sd < 4; sd++)
+          for (int c = 0; c < 4; c++) {
+            P.refsum[sd][kOffW0 + c] += hs[sd] * w * psi[c];
+            P.refsum[sd][kOffSf + c] += hs[sd] * w * un[sd] * psi[c];
+          }
+      }
+  }
+
   cudaError_t e;
   auto alloc = [&](void** p, size_t n) -> bool {
     e = cudaMalloc(p, n);
@@ -410,7 +450,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (want < row_d) want = row_d;
     if (want > row_d * P.ny) want = row_d * P.ny;
     h->stage_bytes = want;
-    ok = alloc((void**)&h->stage, want);
+    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq);
   }
   if (!ok) {
     ugks_destroy(h);
@@ -426,6 +466,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.v = h->d_grid + P.nu;
   P.wu = h->d_grid + P.nu + P.nv;
   P.wv = h->d_grid + 2 * P.nu + P.nv;
+  P.gref = h->gref;
   auto setup = [&]() -> cudaError_t {
     cudaError_t r;
     if ((r = cudaMemcpyAsync(h->d_grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -435,6 +476,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
       if ((r = cudaMemsetAsync(h->W[b], 0, 4 * sizeof(double) * h->nwe, h->stream)) != cudaSuccess) return r;
     }
     if ((r = cudaMemsetAsync(h->rpart, 0, sizeof(double) * 8 * h->nrblocks, h->stream)) != cudaSuccess) return r;
+    if (h->gref && (r = cudaMemcpyAsync(h->gref, gref_host.data(), sizeof(float2) * gref_host.size(),
+                                        cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return r;
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
     if ((r = h->prec == UGKS_FP64 ? set_smem_limits<double>(P.nv) : set_smem_limits<float>(P.nv)) != cudaSuccess)
       return r;
@@ -453,7 +497,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
-                  h->cells, h->rpart, h->err, h->d_grid, h->stage};
+                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -52,6 +52,14 @@ struct Params {
   int bc_kind[4];
   double bc_rho[4], bc_T[4], bc_U[4];
   double wall_mom[4][4];  // per side: sum over outgoing velocities of w u_n psi g_wall(rho=1)
+  int m_pos;              // first v index with v > 0 (v ascending); nv if none
+  // Reference Maxwellian of the FP32 form: the FP32 buffers hold e = f - g_ref, and every
+  // sum or flux of f is the FP32 sum of e plus the exact FP64 sum of g_ref.
+  int use_ref;
+  double ref_G, ref_U, ref_V, ref_lam, ref_bf;  // g_ref,h = G exp(-lam((u-U)^2+(v-V)^2)), b = bf h
+  double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
+                          // sums of g_ref in the W0 and Sf slots, zero in St and Ss
+  const void* gref;       // [nq] T2 table of g_ref (FP32 form), else null
   const double* u;        // [nu]
   const double* v;        // [nv]
   const double* wu;       // [nu]

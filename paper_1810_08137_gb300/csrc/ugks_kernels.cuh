@@ -17,6 +17,8 @@
 #pragma once
 #include <math.h>
 
+#include <type_traits>
+
 #include "ugks_internal.h"
 
 namespace ugks {
@@ -69,6 +71,15 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[N], int lane) {
   return r;
 }
 
+// Reference Maxwellian (h, b) of the FP32 form at velocity (u, v); zero when unused.
+__host__ __device__ __forceinline__ void ref_maxwellian(const Params& P, double u, double v,
+                                                        double& h, double& b) {
+  if (!P.use_ref) { h = b = 0.0; return; }
+  const double du = u - P.ref_U, dv = v - P.ref_V;
+  h = P.ref_G * exp(-P.ref_lam * (du * du + dv * dv));
+  b = P.ref_bf * h;
+}
+
 // -------------------------------------------------------------------------------------
 // Boundary ghost ring
 // -------------------------------------------------------------------------------------
@@ -87,9 +98,11 @@ __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int 
       const int k = q % P.nu, m = q / P.nu;
       const double du = P.u[k] - U, dv = P.v[m] - V;
       const double gh = G * exp(-lam * (du * du + dv * dv));
+      double rh = 0.0, rb = 0.0;
+      ref_maxwellian(P, P.u[k], P.v[m], rh, rb);
       T2 o;
-      o.x = gh;
-      o.y = bf * gh;
+      o.x = gh - rh;
+      o.y = bf * gh - rb;
       dst[q] = o;
     }
     if (write_W && threadIdx.x == 0) {
@@ -549,8 +562,12 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
     // with the density that cancels the mass flux; first order in time
-    const double* Sin = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
-                                  : sums + (size_t)cL * kNSum + oL + kOffSf;
+    const int oin = wall == 1 ? oR : oL;
+    const double* Se = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
+                                 : sums + (size_t)cL * kNSum + oL + kOffSf;
+    double Sin[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) Sin[c] = Se[c] + P.refsum[oin / 16][kOffSf + c];
     const double rhow = -Sin[0] / P.wall_mom[side][0];
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = P.dt * (Sin[c] + rhow * P.wall_mom[side][c]);
@@ -572,11 +589,13 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
     const double* sR = sums + (size_t)cR * kNSum + oR;
     double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
 #pragma unroll
+    const double* rL = P.refsum[oL / 16];
+    const double* rR = P.refsum[oR / 16];
     for (int c = 0; c < 4; c++) {
       const int s = pm[c];
-      W0[c] = sL[kOffW0 + s] + sR[kOffW0 + s];
+      W0[c] = (sL[kOffW0 + s] + sR[kOffW0 + s]) + (rL[kOffW0 + s] + rR[kOffW0 + s]);
       St[c] = sL[kOffSt + s] + sR[kOffSt + s];
-      Sf[c] = sL[kOffSf + s] + sR[kOffSf + s];
+      Sf[c] = (sL[kOffSf + s] + sR[kOffSf + s]) + (rL[kOffSf + s] + rR[kOffSf + s]);
       Ss[c] = sL[kOffSs + s] + sR[kOffSs + s];
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
@@ -657,29 +676,46 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
 
 // -------------------------------------------------------------------------------------
 // S6 + S8 and Eq. 3: micro flux of the four faces from the upwind reconstruction and the
-// face records, implicit collision update.  One warp per interior cell, lane = u index,
-// loop over v.
+// face records, implicit collision update written as an increment, f^{n+1} = f^n + df,
+//   df = inv [ flux + cg1 (g^{n+1} - f^n) + cgn (g^n - f^n) ],
+// so that rounding acts on df rather than on f.  One warp per interior cell, lane = u
+// index (chunks of 32); the v loop is split into v <= 0 and v > 0 so that the y-upwind
+// side is fixed in each half.  In the FP32 form the buffers hold e = f - g_ref and the
+// g_ref part of the flux, u (Mt4_W - Mt4_E)/dx g_ref + v (Mt4_S - Mt4_N)/dy g_ref, is
+// added from FP64 face constants.
 // -------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void poly_in_v_xface(const double* c, T u, T* q) {
+__device__ __forceinline__ void poly_in_v_xface(const double* c, double u, T* q) {
   // face frame un = u (fixed), ut = v: Q = q0 + q1 v + q2 v^2 + q3 v^3
-  const double uu = (double)u;
-  q[0] = (T)(c[0] + uu * (c[1] + uu * (c[3] + uu * c[6])));
-  q[1] = (T)(c[2] + uu * (c[4] + uu * c[7]));
-  q[2] = (T)(c[5] + uu * c[6]);
+  q[0] = (T)(c[0] + u * (c[1] + u * (c[3] + u * c[6])));
+  q[1] = (T)(c[2] + u * (c[4] + u * c[7]));
+  q[2] = (T)(c[5] + u * c[6]);
   q[3] = (T)c[7];
 }
 template <typename T>
-__device__ __forceinline__ void poly_in_v_yface(const double* c, T u, T* q) {
+__device__ __forceinline__ void poly_in_v_yface(const double* c, double u, T* q) {
   // face frame un = v, ut = u (fixed): Q = q0 + q1 v + q2 v^2 + q3 v^3
-  const double uu = (double)u;
-  q[0] = (T)(c[0] + uu * (c[2] + uu * (c[5] + uu * c[7])));
-  q[1] = (T)(c[1] + uu * (c[4] + uu * c[6]));
-  q[2] = (T)(c[3] + uu * c[7]);
+  q[0] = (T)(c[0] + u * (c[2] + u * (c[5] + u * c[7])));
+  q[1] = (T)(c[1] + u * (c[4] + u * c[6]));
+  q[2] = (T)(c[3] + u * c[7]);
   q[3] = (T)c[6];
 }
 
-template <typename T, typename T2>
+template <typename T>
+__device__ __forceinline__ T horner3(const T* q, T v) {
+  return ((q[3] * v + q[2]) * v + q[1]) * v + q[0];
+}
+
+// Per-cell constants of the update kernel, converted to T once per warp.
+template <typename T>
+struct UpdCell {
+  T Mt4[4], Mt5[4], bf[4];
+  T inv, cg1, cgn, cg1b, cgnb;
+  T refx, refy;   // (Mt4_W - Mt4_E)/dx, (Mt4_S - Mt4_N)/dy (FP32 form), else 0
+  int wall[4];
+};
+
+template <typename T, typename T2, bool REF>
 __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__ f,
                                                 T2* __restrict__ fo,
                                                 const FaceRec* __restrict__ fxr,
@@ -695,35 +731,46 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
   const int cell = blockIdx.x * kWarpsPerBlock + warp;
   if (cell >= nx * ny) return;
   const int i = cell % nx, j = cell / nx;
-  const FaceRec* Rf[4] = {fxr + (size_t)j * (nx + 1) + i, fxr + (size_t)j * (nx + 1) + i + 1,
-                          fyr + (size_t)j * nx + i, fyr + (size_t)(j + 1) * nx + i};
-  const CellRec C = cr[cell];
+  const FaceRec& RW = fxr[(size_t)j * (nx + 1) + i];
+  const FaceRec& RE = fxr[(size_t)j * (nx + 1) + i + 1];
+  const FaceRec& RS = fyr[(size_t)j * nx + i];
+  const FaceRec& RN = fyr[(size_t)(j + 1) * nx + i];
+  const CellRec& C = cr[cell];
   for (int m = lane; m < nv; m += 32) {
     const double vv = P.v[m];
-    for (int s = 0; s < 2; s++) {  // x faces: ut = v
-      const double d = vv - Rf[s]->Ut;
-      ev[s * nv + m] = (T)exp(-Rf[s]->lam * d * d);
-    }
-    for (int s = 2; s < 4; s++) {  // y faces: un = v
-      const double d = vv - Rf[s]->Un;
-      ev[s * nv + m] = (T)exp(-Rf[s]->lam * d * d);
-    }
-    double d = vv - C.Vn;
-    ev[4 * nv + m] = (T)exp(-C.lamn * d * d);
-    d = vv - C.V1;
-    ev[5 * nv + m] = (T)exp(-C.lam1 * d * d);
+    double d;
+    d = vv - RW.Ut; ev[0 * nv + m] = (T)exp(-RW.lam * d * d);  // x faces: ut = v
+    d = vv - RE.Ut; ev[1 * nv + m] = (T)exp(-RE.lam * d * d);
+    d = vv - RS.Un; ev[2 * nv + m] = (T)exp(-RS.lam * d * d);  // y faces: un = v
+    d = vv - RN.Un; ev[3 * nv + m] = (T)exp(-RN.lam * d * d);
+    d = vv - C.Vn;  ev[4 * nv + m] = (T)exp(-C.lamn * d * d);
+    d = vv - C.V1;  ev[5 * nv + m] = (T)exp(-C.lam1 * d * d);
   }
   __syncwarp();
-
-  const int wallW = Rf[0]->wall, wallE = Rf[1]->wall, wallS = Rf[2]->wall, wallN = Rf[3]->wall;
-  const T Mt4[4] = {(T)Rf[0]->Mt4, (T)Rf[1]->Mt4, (T)Rf[2]->Mt4, (T)Rf[3]->Mt4};
-  const T Mt5[4] = {(T)Rf[0]->Mt5, (T)Rf[1]->Mt5, (T)Rf[2]->Mt5, (T)Rf[3]->Mt5};
-  const T bf[4] = {(T)Rf[0]->bfac, (T)Rf[1]->bfac, (T)Rf[2]->bfac, (T)Rf[3]->bfac};
+  UpdCell<T> K;
+  {
+    const FaceRec* R[4] = {&RW, &RE, &RS, &RN};
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      K.Mt4[s] = (T)R[s]->Mt4;
+      K.Mt5[s] = (T)R[s]->Mt5;
+      K.bf[s] = (T)R[s]->bfac;
+      K.wall[s] = R[s]->wall;
+    }
+    K.inv = (T)C.inv;
+    K.cg1 = (T)C.cg1;
+    K.cgn = (T)C.cgn;
+    K.cg1b = (T)(C.cg1 * C.b1);
+    K.cgnb = (T)(C.cgn * C.bn);
+    K.refx = REF ? (T)((RW.Mt4 - RE.Mt4) / P.dx) : T(0);
+    K.refy = REF ? (T)((RS.Mt4 - RN.Mt4) / P.dy) : T(0);
+  }
   const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy), idx = T(1.0 / P.dx), idy = T(1.0 / P.dy);
   const T dtT = (T)P.dt;
-  const size_t rs = (size_t)P.ex * nq;
+  const long rs = (long)P.ex * nq;
   const T2* fc0 = f + fcell(P, i, j) * nq;
   T2* fo0 = fo + fcell(P, i, j) * nq;
+  const T2* gref = static_cast<const T2*>(P.gref);
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
@@ -732,149 +779,149 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     const int kk = act ? k : nu - 1;
     const double ud = P.u[kk];
     const T u = (T)ud;
-    // per-lane factors in u
-    T gu[4];
-    for (int s = 0; s < 2; s++) {
-      const double d = ud - Rf[s]->Un;
-      gu[s] = (T)(Rf[s]->G * exp(-Rf[s]->lam * d * d));
+    T gu[4], gun, gu1;
+    {
+      double d;
+      d = ud - RW.Un; gu[0] = (T)(RW.G * exp(-RW.lam * d * d));
+      d = ud - RE.Un; gu[1] = (T)(RE.G * exp(-RE.lam * d * d));
+      d = ud - RS.Ut; gu[2] = (T)(RS.G * exp(-RS.lam * d * d));
+      d = ud - RN.Ut; gu[3] = (T)(RN.G * exp(-RN.lam * d * d));
+      d = ud - C.Un;  gun = (T)(C.Gn * exp(-C.lamn * d * d));
+      d = ud - C.U1;  gu1 = (T)(C.G1 * exp(-C.lam1 * d * d));
     }
-    for (int s = 2; s < 4; s++) {
-      const double d = ud - Rf[s]->Ut;
-      gu[s] = (T)(Rf[s]->G * exp(-Rf[s]->lam * d * d));
-    }
-    double d = ud - C.Un;
-    const T gun = (T)(C.Gn * exp(-C.lamn * d * d));
-    d = ud - C.U1;
-    const T gu1 = (T)(C.G1 * exp(-C.lam1 * d * d));
-    // x-face polynomial in v, side fixed by the sign of u
     const int xs = ud > 0.0 ? 0 : 1;
-    T qW[2][4], qE[2][4], qS[2][4], qN[2][4];
+    T qW[2][4], qE[2][4];
+#pragma unroll
     for (int c = 0; c < 2; c++) {
-      poly_in_v_xface(Rf[0]->Q[xs][c], u, qW[c]);
-      poly_in_v_xface(Rf[1]->Q[xs][c], u, qE[c]);
-      poly_in_v_yface(Rf[2]->Q[1][c], u, qS[c]);  // v < 0 first: the u_n < 0 side
-      poly_in_v_yface(Rf[3]->Q[1][c], u, qN[c]);
+      poly_in_v_xface(RW.Q[xs][c], ud, qW[c]);
+      poly_in_v_xface(RE.Q[xs][c], ud, qE[c]);
     }
     const bool up = ud > 0.0;  // x upwind neighbour: W for u > 0, E for u < 0
     const long xo = up ? -(long)nq : (long)nq;
     const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
-    const T cu = u * tdx, fxu = u * idx;
-    bool yswitched = false;
-    for (int m = 0; m < nv; m++) {
-      const T vv = sv[m];
-      if (!yswitched && vv > T(0)) {
-        for (int c = 0; c < 2; c++) {
-          poly_in_v_yface(Rf[2]->Q[0][c], u, qS[c]);
-          poly_in_v_yface(Rf[3]->Q[0][c], u, qN[c]);
-        }
-        yswitched = true;
+    const T cu = u * tdx, fxu = u * idx, refxu = u * K.refx;
+
+    // one half of the v range: VUP = (v > 0); y-upwind neighbour S for v > 0, N otherwise
+    auto half = [&](auto vup_tag, int m0, int m1) {
+      constexpr bool VUP = decltype(vup_tag)::value;
+      T qS[2][4], qN[2][4];
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        poly_in_v_yface(RS.Q[VUP ? 0 : 1][c], ud, qS[c]);
+        poly_in_v_yface(RN.Q[VUP ? 0 : 1][c], ud, qN[c]);
       }
-      const bool vup = vv > T(0);
-      const long yo = vup ? -(long)rs : (long)rs;
-      const bool yz = (vup && j == 0 && pS) || (!vup && j == ny - 1 && pN);
-      const T2* p = fc0 + (size_t)m * nu + kk;
-      const T2 c = p[0], w = p[-(long)nq], e = p[nq], s = p[-(long)rs], n = p[rs];
-      const T2 xf = p[2 * xo], xs_ = p[xo - (long)rs], xn = p[xo + (long)rs];
-      const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
-      const T2 xu = up ? w : e, yu = vup ? s : n;
-      // half slopes r = sigma h / 2 of the cell, its x-upwind and its y-upwind neighbour
-      const T rxch = vl_half(w.x, c.x, e.x), rxcb = vl_half(w.y, c.y, e.y);
-      const T rych = vl_half(s.x, c.x, n.x), rycb = vl_half(s.y, c.y, n.y);
-      T rxuh, rxub, ryuh, ryub, rxvh, rxvb, ryvh, ryvb;
-      if (up) { rxuh = vl_half(xf.x, w.x, c.x); rxub = vl_half(xf.y, w.y, c.y); }
-      else    { rxuh = vl_half(c.x, e.x, xf.x); rxub = vl_half(c.y, e.y, xf.y); }
-      ryuh = vl_half(xs_.x, xu.x, xn.x);
-      ryub = vl_half(xs_.y, xu.y, xn.y);
-      rxvh = vl_half(yw.x, yu.x, ye.x);
-      rxvb = vl_half(yw.y, yu.y, ye.y);
-      if (vup) { ryvh = vl_half(yf.x, s.x, c.x); ryvb = vl_half(yf.y, s.y, c.y); }
-      else     { ryvh = vl_half(c.x, n.x, yf.x); ryvb = vl_half(c.y, n.y, yf.y); }
-      if (xz) rxuh = rxub = ryuh = ryub = T(0);
-      if (yz) rxvh = rxvb = ryvh = ryvb = T(0);
-      const T cv = vv * tdy, fyv = vv * idy;
-      // (u sigma_x + v sigma_y) of the three cells
-      const T dch = cu * rxch + cv * rych, dcb = cu * rxcb + cv * rycb;
-      const T duh = cu * rxuh + cv * ryuh, dub = cu * rxub + cv * ryub;
-      const T dvh = cu * rxvh + cv * ryvh, dvb = cu * rxvb + cv * ryvb;
-      // upwind interface values and slope terms at the four faces
-      T fWh, fWb, dWh, dWb, fEh, fEb, dEh, dEb;
-      if (up) {
-        fEh = c.x + rxch; fEb = c.y + rxcb; dEh = dch; dEb = dcb;
-        fWh = xu.x + rxuh; fWb = xu.y + rxub; dWh = duh; dWb = dub;
-      } else {
-        fWh = c.x - rxch; fWb = c.y - rxcb; dWh = dch; dWb = dcb;
-        fEh = xu.x - rxuh; fEb = xu.y - rxub; dEh = duh; dEb = dub;
-      }
-      T fSh, fSb, dSh, dSb, fNh, fNb, dNh, dNb;
-      if (vup) {
-        fNh = c.x + rych; fNb = c.y + rycb; dNh = dch; dNb = dcb;
-        fSh = yu.x + ryvh; fSb = yu.y + ryvb; dSh = dvh; dSb = dvb;
-      } else {
-        fSh = c.x - rych; fSb = c.y - rycb; dSh = dch; dSb = dcb;
-        fNh = yu.x - ryvh; fNb = yu.y - ryvb; dNh = dvh; dNb = dvb;
-      }
-      // X = Q g + Mt4 f_up - Mt5 d  (UGKS face),  X = dt f_w (wall); F~ = u_n X
-      T XWh, XWb, XEh, XEb, XSh, XSb, XNh, XNb;
-      {
-        const T g = gu[0] * ev[m];
-        if (wallW) {
-          const bool inc = !up;  // gas on the high side: incoming u < 0
-          XWh = dtT * (inc ? fWh : g);
-          XWb = dtT * (inc ? fWb : bf[0] * g);
+      const long yo = VUP ? -rs : rs;
+      const bool yz = (VUP && j == 0 && pS) || (!VUP && j == ny - 1 && pN);
+      for (int m = m0; m < m1; m++) {
+        const T vv = sv[m];
+        const T2* p = fc0 + (size_t)m * nu + kk;
+        const T2 c = p[0], w = p[-(long)nq], e = p[nq], s = p[-rs], n = p[rs];
+        const T2 xf = p[2 * xo], xs_ = p[xo - rs], xn = p[xo + rs];
+        const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
+        const T2 xu = up ? w : e;
+        const T2 yu = VUP ? s : n;
+        // half slopes r = sigma h / 2 of the cell, its x-upwind and its y-upwind neighbour
+        const T rxch = vl_half(w.x, c.x, e.x), rxcb = vl_half(w.y, c.y, e.y);
+        const T rych = vl_half(s.x, c.x, n.x), rycb = vl_half(s.y, c.y, n.y);
+        T rxuh, rxub;
+        if (up) { rxuh = vl_half(xf.x, w.x, c.x); rxub = vl_half(xf.y, w.y, c.y); }
+        else    { rxuh = vl_half(c.x, e.x, xf.x); rxub = vl_half(c.y, e.y, xf.y); }
+        T ryuh = vl_half(xs_.x, xu.x, xn.x), ryub = vl_half(xs_.y, xu.y, xn.y);
+        T rxvh = vl_half(yw.x, yu.x, ye.x), rxvb = vl_half(yw.y, yu.y, ye.y);
+        T ryvh, ryvb;
+        if (VUP) { ryvh = vl_half(yf.x, s.x, c.x); ryvb = vl_half(yf.y, s.y, c.y); }
+        else     { ryvh = vl_half(c.x, n.x, yf.x); ryvb = vl_half(c.y, n.y, yf.y); }
+        if (xz) rxuh = rxub = ryuh = ryub = T(0);
+        if (yz) rxvh = rxvb = ryvh = ryvb = T(0);
+        const T cv = vv * tdy, fyv = vv * idy;
+        // (u sigma_x + v sigma_y) of the three cells
+        const T dch = cu * rxch + cv * rych, dcb = cu * rxcb + cv * rycb;
+        const T duh = cu * rxuh + cv * ryuh, dub = cu * rxub + cv * ryub;
+        const T dvh = cu * rxvh + cv * ryvh, dvb = cu * rxvb + cv * ryvb;
+        // upwind interface values and slope terms
+        T fWh, fWb, dWh, dWb, fEh, fEb, dEh, dEb;
+        if (up) {
+          fEh = c.x + rxch; fEb = c.y + rxcb; dEh = dch; dEb = dcb;
+          fWh = xu.x + rxuh; fWb = xu.y + rxub; dWh = duh; dWb = dub;
         } else {
-          const T Qh = ((qW[0][3] * vv + qW[0][2]) * vv + qW[0][1]) * vv + qW[0][0];
-          const T Qb = ((qW[1][3] * vv + qW[1][2]) * vv + qW[1][1]) * vv + qW[1][0];
-          XWh = Qh * g + Mt4[0] * fWh - Mt5[0] * dWh;
-          XWb = Qb * g + Mt4[0] * fWb - Mt5[0] * dWb;
+          fWh = c.x - rxch; fWb = c.y - rxcb; dWh = dch; dWb = dcb;
+          fEh = xu.x - rxuh; fEb = xu.y - rxub; dEh = duh; dEb = dub;
         }
-      }
-      {
-        const T g = gu[1] * ev[nv + m];
-        if (wallE) {
-          const bool inc = up;  // gas on the low side: incoming u > 0
-          XEh = dtT * (inc ? fEh : g);
-          XEb = dtT * (inc ? fEb : bf[1] * g);
+        T fSh, fSb, dSh, dSb, fNh, fNb, dNh, dNb;
+        if (VUP) {
+          fNh = c.x + rych; fNb = c.y + rycb; dNh = dch; dNb = dcb;
+          fSh = yu.x + ryvh; fSb = yu.y + ryvb; dSh = dvh; dSb = dvb;
         } else {
-          const T Qh = ((qE[0][3] * vv + qE[0][2]) * vv + qE[0][1]) * vv + qE[0][0];
-          const T Qb = ((qE[1][3] * vv + qE[1][2]) * vv + qE[1][1]) * vv + qE[1][0];
-          XEh = Qh * g + Mt4[1] * fEh - Mt5[1] * dEh;
-          XEb = Qb * g + Mt4[1] * fEb - Mt5[1] * dEb;
+          fSh = c.x - rych; fSb = c.y - rycb; dSh = dch; dSb = dcb;
+          fNh = yu.x - ryvh; fNb = yu.y - ryvb; dNh = dvh; dNb = dvb;
         }
-      }
-      {
-        const T g = gu[2] * ev[2 * nv + m];
-        if (wallS) {
-          const bool inc = !vup;
-          XSh = dtT * (inc ? fSh : g);
-          XSb = dtT * (inc ? fSb : bf[2] * g);
-        } else {
-          const T Qh = ((qS[0][3] * vv + qS[0][2]) * vv + qS[0][1]) * vv + qS[0][0];
-          const T Qb = ((qS[1][3] * vv + qS[1][2]) * vv + qS[1][1]) * vv + qS[1][0];
-          XSh = Qh * g + Mt4[2] * fSh - Mt5[2] * dSh;
-          XSb = Qb * g + Mt4[2] * fSb - Mt5[2] * dSb;
+        T2 gr;
+        if (REF) gr = gref[(size_t)m * nu + kk];
+        else { gr.x = T(0); gr.y = T(0); }
+        // X = Q g + Mt4 f_up - Mt5 d (UGKS face), X = dt f_w (wall); F~ = u_n X
+        T XWh, XWb, XEh, XEb, XSh, XSb, XNh, XNb;
+        {
+          const T g = gu[0] * ev[m];
+          if (K.wall[0]) {
+            const bool inc = !up;  // gas on the high side: incoming u < 0
+            XWh = inc ? dtT * fWh : dtT * (g - gr.x);
+            XWb = inc ? dtT * fWb : dtT * (K.bf[0] * g - gr.y);
+          } else {
+            XWh = horner3(qW[0], vv) * g + K.Mt4[0] * fWh - K.Mt5[0] * dWh;
+            XWb = horner3(qW[1], vv) * g + K.Mt4[0] * fWb - K.Mt5[0] * dWb;
+          }
         }
-      }
-      {
-        const T g = gu[3] * ev[3 * nv + m];
-        if (wallN) {
-          const bool inc = vup;
-          XNh = dtT * (inc ? fNh : g);
-          XNb = dtT * (inc ? fNb : bf[3] * g);
-        } else {
-          const T Qh = ((qN[0][3] * vv + qN[0][2]) * vv + qN[0][1]) * vv + qN[0][0];
-          const T Qb = ((qN[1][3] * vv + qN[1][2]) * vv + qN[1][1]) * vv + qN[1][0];
-          XNh = Qh * g + Mt4[3] * fNh - Mt5[3] * dNh;
-          XNb = Qb * g + Mt4[3] * fNb - Mt5[3] * dNb;
+        {
+          const T g = gu[1] * ev[nv + m];
+          if (K.wall[1]) {
+            const bool inc = up;  // gas on the low side: incoming u > 0
+            XEh = inc ? dtT * fEh : dtT * (g - gr.x);
+            XEb = inc ? dtT * fEb : dtT * (K.bf[1] * g - gr.y);
+          } else {
+            XEh = horner3(qE[0], vv) * g + K.Mt4[1] * fEh - K.Mt5[1] * dEh;
+            XEb = horner3(qE[1], vv) * g + K.Mt4[1] * fEb - K.Mt5[1] * dEb;
+          }
         }
+        {
+          const T g = gu[2] * ev[2 * nv + m];
+          if (K.wall[2]) {
+            XSh = !VUP ? dtT * fSh : dtT * (g - gr.x);
+            XSb = !VUP ? dtT * fSb : dtT * (K.bf[2] * g - gr.y);
+          } else {
+            XSh = horner3(qS[0], vv) * g + K.Mt4[2] * fSh - K.Mt5[2] * dSh;
+            XSb = horner3(qS[1], vv) * g + K.Mt4[2] * fSb - K.Mt5[2] * dSb;
+          }
+        }
+        {
+          const T g = gu[3] * ev[3 * nv + m];
+          if (K.wall[3]) {
+            XNh = VUP ? dtT * fNh : dtT * (g - gr.x);
+            XNb = VUP ? dtT * fNb : dtT * (K.bf[3] * g - gr.y);
+          } else {
+            XNh = horner3(qN[0], vv) * g + K.Mt4[3] * fNh - K.Mt5[3] * dNh;
+            XNb = horner3(qN[1], vv) * g + K.Mt4[3] * fNb - K.Mt5[3] * dNb;
+          }
+        }
+        T flh = fxu * (XWh - XEh) + fyv * (XSh - XNh);
+        T flb = fxu * (XWb - XEb) + fyv * (XSb - XNb);
+        if (REF) {
+          const T rr = refxu + vv * K.refy;
+          flh += rr * gr.x;
+          flb += rr * gr.y;
+        }
+        const T gnh = gun * ev[4 * nv + m], g1h = gu1 * ev[5 * nv + m];
+        // f^n = e + g_ref in the FP32 form: g - f^n = (g - g_ref) - e
+        const T dh = K.inv * (flh + K.cg1 * ((g1h - gr.x) - c.x) + K.cgn * ((gnh - gr.x) - c.x));
+        const T db = K.inv * (flb + (K.cg1b * g1h - K.cg1 * gr.y - K.cg1 * c.y) +
+                              (K.cgnb * gnh - K.cgn * gr.y - K.cgn * c.y));
+        T2 o;
+        o.x = c.x + dh;
+        o.y = c.y + db;
+        if (act) fo0[(size_t)m * nu + kk] = o;
       }
-      const T flh = fxu * (XWh - XEh) + fyv * (XSh - XNh);
-      const T flb = fxu * (XWb - XEb) + fyv * (XSb - XNb);
-      const T gnh = gun * ev[4 * nv + m], g1h = gu1 * ev[5 * nv + m];
-      T2 o;
-      o.x = (T)C.inv * ((T)C.cf * c.x + flh + (T)C.cg1 * g1h + (T)C.cgn * gnh);
-      o.y = (T)C.inv * ((T)C.cf * c.y + flb + (T)(C.cg1 * C.b1) * g1h + (T)(C.cgn * C.bn) * gnh);
-      if (act) fo0[(size_t)m * nu + kk] = o;
-    }
+    };
+    half(std::integral_constant<bool, false>{}, 0, P.m_pos);
+    half(std::integral_constant<bool, true>{}, P.m_pos, nv);
   }
 }
 

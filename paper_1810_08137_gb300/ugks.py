@@ -41,7 +41,9 @@ class _Config(C.Structure):
                 ("nu", C.c_int), ("nv", C.c_int), ("umin", C.c_double), ("umax", C.c_double),
                 ("vmin", C.c_double), ("vmax", C.c_double), ("K", C.c_int), ("kn", C.c_double),
                 ("omega", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
-                ("dt", C.c_double), ("bc", _BC * 4), ("precision", C.c_int)]
+                ("dt", C.c_double), ("bc", _BC * 4), ("precision", C.c_int),
+                ("ref_rho", C.c_double), ("ref_U", C.c_double), ("ref_V", C.c_double),
+                ("ref_T", C.c_double)]
 
 
 _lib = None
@@ -95,6 +97,8 @@ def to_c_config(cfg, precision: int = FP64) -> _Config:
         b = cfg.bc[s]
         c.bc[s].kind, c.bc[s].rho, c.bc[s].T, c.bc[s].U = int(b.kind), float(b.rho), float(b.T), float(b.U)
     c.precision = int(precision)
+    ref = getattr(cfg, "ref", None) or (0.0, 0.0, 0.0, 0.0)
+    c.ref_rho, c.ref_U, c.ref_V, c.ref_T = (float(x) for x in ref)
     return c
 
 
