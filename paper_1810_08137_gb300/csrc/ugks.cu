@@ -31,6 +31,11 @@ struct ugks_ctx {
   double* Fx = nullptr;
   double* Fy = nullptr;
   CellRec* cells = nullptr;
+  FaceRecF* fxf = nullptr;   // FP32 form: float face and cell records for the walk kernel
+  FaceRecF* fyf = nullptr;
+  CellRecF* cellf = nullptr;
+  double* mt4 = nullptr;     // Mt4 per face (x faces then y faces)
+  int nchunk_neg = 0, nchunk_pos = 0;
   double* rpart = nullptr;
   int nrblocks = 0;
   int* err = nullptr;
@@ -118,8 +123,9 @@ cudaError_t set_smem_limits(int nv) {
   cudaError_t e = cudaFuncSetAttribute(k_sums<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_sums<T>(nv));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_update<T, T2, (sizeof(T) == 4)>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_update<T>(nv));
+  if (sizeof(T) == 4) return cudaSuccess;
+  return cudaFuncSetAttribute(k_update<T, T2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_update<T>(nv));
 }
 
 const char* const kKernelNames[UGKS_NKERNELS] = {"ghost_x", "ghost_y", "sums", "faces", "cells",
@@ -158,14 +164,22 @@ cudaError_t launch_step(ugks_ctx* h) {
       P, fi, h->sums);
   if ((r = mark(h, 3)) != cudaSuccess) return r;
   const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
-  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, h->sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy);
+  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, h->sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
+                                            h->fxf, h->fyf, h->mt4);
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   const int nc = P.nx * P.ny;
-  k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err);
+  k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
+                                       h->cellf, h->mt4);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  k_update<T, T2, (sizeof(T) == 4)>
-      <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
-          P, fi, fo, h->fxr, h->fyr, h->cells);
+  if (sizeof(T) == 4) {
+    const dim3 grid((P.nx + 3) / 4, (P.ny + kWalkRows - 1) / kWalkRows, h->nchunk_neg + h->nchunk_pos);
+    k_walk<<<grid, 128, 0, st>>>(P, reinterpret_cast<const float2*>(fi), reinterpret_cast<float2*>(fo),
+                                 h->fxf, h->fyf, h->cellf, h->nchunk_neg);
+  } else {
+    k_update<T, T2, false>
+        <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
+            P, fi, fo, h->fxr, h->fyr, h->cells);
+  }
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
@@ -391,6 +405,11 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.m_pos = P.nv;
   for (int m = 0; m < P.nv; m++)
     if (h->hv[m] > 0) { P.m_pos = m; break; }
+  P.m_neg = 0;
+  for (int m = 0; m < P.nv; m++)
+    if (h->hv[m] < 0) P.m_neg = m + 1;
+  h->nchunk_neg = (P.m_neg * P.nu + 31) / 32;
+  h->nchunk_pos = ((P.nv - P.m_neg) * P.nu + 31) / 32;
   std::vector<float2> gref_host;
   if (h->prec == UGKS_FP32F) {
     double rr = cfg->ref_rho, rU = cfg->ref_U, rV = cfg->ref_V, rT = cfg->ref_T;
@@ -432,15 +451,20 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   const size_t fbytes = h->fcells * P.nq * h->t2;
   const int nfx = (P.nx + 1) * P.ny, nfy = P.nx * (P.ny + 1), nc = P.nx * P.ny;
   h->nrblocks = (nc + 127) / 128;
+  const bool f32 = h->prec == UGKS_FP32F;
   bool ok = alloc(&h->f[0], fbytes) && alloc(&h->f[1], fbytes) &&
             alloc((void**)&h->W[0], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->sums, sizeof(double) * kNSum * (size_t)h->nwe) &&
-            alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx) &&
-            alloc((void**)&h->fyr, sizeof(FaceRec) * (size_t)nfy) &&
+            (f32 ? alloc((void**)&h->fxf, sizeof(FaceRecF) * (size_t)nfx)
+                 : alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx)) &&
+            (f32 ? alloc((void**)&h->fyf, sizeof(FaceRecF) * (size_t)nfy)
+                 : alloc((void**)&h->fyr, sizeof(FaceRec) * (size_t)nfy)) &&
             alloc((void**)&h->Fx, sizeof(double) * 4 * (size_t)nfx) &&
             alloc((void**)&h->Fy, sizeof(double) * 4 * (size_t)nfy) &&
-            alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc) &&
+            alloc((void**)&h->mt4, sizeof(double) * (size_t)(nfx + nfy)) &&
+            (f32 ? alloc((void**)&h->cellf, sizeof(CellRecF) * (size_t)nc)
+                 : alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc)) &&
             alloc((void**)&h->rpart, sizeof(double) * 8 * (size_t)h->nrblocks) &&
             alloc((void**)&h->err, sizeof(int)) &&
             alloc((void**)&h->d_grid, sizeof(double) * 2 * (P.nu + P.nv));
@@ -497,7 +521,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
-                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref};
+                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->fxf, h->fyf,
+                  h->cellf, h->mt4};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -43,6 +43,22 @@ struct CellRec {
   double cf, cgn, cg1, inv;
 };
 
+// FP32 copies of the face and cell records for the FP32 form's update kernel (written by the
+// FP64 face and cell kernels, so the update kernel does no FP64 arithmetic or conversion).
+// b component of the micro flux: Q_b = X2 Q_h + kb0 + kb1 un + kb2 ut.
+struct __align__(16) FaceRecF {
+  float Q[2][8];     // Q_h per side (0: un > 0, 1: un < 0): c00 c10 c01 c20 c11 c02 cn3 ct3
+  float kb[2][4];    // kb0 kb1 kb2 (pad) per side
+  float lam, Un, Ut, G;
+  float Mt4, Mt5, X2, wall;
+};
+struct __align__(16) CellRecF {
+  float Gn, Un, Vn, lamn;
+  float G1, U1, V1, lam1;
+  float bn, b1, inv, cg1;
+  float cgn, refx, refy, pad;   // refx = (Mt4_W - Mt4_E)/dx, refy = (Mt4_S - Mt4_N)/dy
+};
+
 struct Params {
   int nx, ny, nu, nv, nq, K;
   int ex;                 // f row length in cells: nx + 4 (two-cell ghost ring)
@@ -53,6 +69,7 @@ struct Params {
   double bc_rho[4], bc_T[4], bc_U[4];
   double wall_mom[4][4];  // per side: sum over outgoing velocities of w u_n psi g_wall(rho=1)
   int m_pos;              // first v index with v > 0 (v ascending); nv if none
+  int m_neg;              // number of v indices with v < 0
   // Reference Maxwellian of the FP32 form: the FP32 buffers hold e = f - g_ref, and every
   // sum or flux of f is the FP32 sum of e plus the exact FP64 sum of g_ref.
   int use_ref;

@@ -460,7 +460,7 @@ __device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const d
 // micro-flux record.
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
                           const double* Ss, const double* WL, const double* WR, double delta,
-                          double* F, FaceRec& R) {
+                          double* F, FaceRec& R, FaceRecF* RF) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], U = W0[1] / rho, V = W0[2] / rho;
@@ -523,11 +523,28 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   R.Mt5 = Mt[4];
   R.bfac = X2;
   R.wall = 0;
+  if (RF) {
+    // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
+    // Mt2 un a4 + Mt2 ut b4), kap = (X4 - X2^2)/2 = K/(4 lam^2)
+    const double kap = 0.5 * (X4 - X2 * X2);
+    for (int sd = 0; sd < 2; sd++) {
+      const double* as = sd == 0 ? aL : aR;
+      for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)R.Q[sd][0][c];
+      RF->kb[sd][0] = (float)(kap * Mt[2] * A[3]);
+      RF->kb[sd][1] = (float)(kap * Mt[1] * as[3]);
+      RF->kb[sd][2] = (float)(kap * Mt[1] * b[3]);
+      RF->kb[sd][3] = 0.f;
+    }
+    RF->lam = (float)lam; RF->Un = (float)U; RF->Ut = (float)V; RF->G = (float)R.G;
+    RF->Mt4 = (float)Mt[3]; RF->Mt5 = (float)Mt[4]; RF->X2 = (float)X2; RF->wall = 0.f;
+  }
 }
 
 __global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
                         int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
-                        double* __restrict__ Fx, double* __restrict__ Fy) {
+                        double* __restrict__ Fx, double* __restrict__ Fy,
+                        FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
+                        double* __restrict__ mt4) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nx = P.nx, ny = P.ny;
   const int nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
@@ -558,6 +575,8 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
     if (j == ny - 1 && P.bc_kind[3] == 1) { wall = 2; side = 3; }
   }
   FaceRec R;
+  FaceRecF RFv;
+  FaceRecF* RF = fxf ? &RFv : nullptr;
   double F[4];
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
@@ -583,14 +602,22 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
     R.Mt5 = 0.0;
     R.bfac = P.K / (2.0 * lam);
     R.wall = wall;
+    if (RF) {
+      for (int a = 0; a < 2; a++) {
+        for (int c = 0; c < 8; c++) RF->Q[a][c] = 0.f;
+        for (int c = 0; c < 4; c++) RF->kb[a][c] = 0.f;
+      }
+      RF->lam = (float)lam; RF->Un = 0.f; RF->Ut = (float)R.Ut; RF->G = (float)R.G;
+      RF->Mt4 = (float)P.dt; RF->Mt5 = 0.f; RF->X2 = (float)R.bfac; RF->wall = (float)wall;
+    }
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
     const double* sL = sums + (size_t)cL * kNSum + oL;
     const double* sR = sums + (size_t)cR * kNSum + oR;
     double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
-#pragma unroll
     const double* rL = P.refsum[oL / 16];
     const double* rR = P.refsum[oR / 16];
+#pragma unroll
     for (int c = 0; c < 4; c++) {
       const int s = pm[c];
       W0[c] = (sL[kOffW0 + s] + sR[kOffW0 + s]) + (rL[kOffW0 + s] + rR[kOffW0 + s]);
@@ -600,15 +627,18 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
-    face_math(P, W0, St, Sf, Ss, WL, WR, delta, Fr, R);
+    face_math(P, W0, St, Sf, Ss, WL, WR, delta, Fr, R, RF);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[pm[c]] = Fr[c];
   }
+  mt4[t] = R.Mt4;
   if (isx) {
-    fxr[t] = R;
+    if (RF) fxf[t] = *RF;
+    else fxr[t] = R;
     for (int c = 0; c < 4; c++) Fx[4 * (size_t)t + c] = F[c];
   } else {
-    fyr[t - nfx] = R;
+    if (RF) fyf[t - nfx] = *RF;
+    else fyr[t - nfx] = R;
     for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
   }
 }
@@ -622,7 +652,8 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
                                                const double* __restrict__ Fx,
                                                const double* __restrict__ Fy,
                                                CellRec* __restrict__ cr, double* __restrict__ rpart,
-                                               int* __restrict__ err) {
+                                               int* __restrict__ err, CellRecF* __restrict__ crf,
+                                               const double* __restrict__ mt4) {
   __shared__ double red[8][128];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int nx = P.nx, nc = P.nx * P.ny;
@@ -656,7 +687,20 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
     R.cf = 1.0 - R.cgn;
     R.cg1 = P.dt / (2.0 * t1);
     R.inv = 1.0 / (1.0 + R.cg1);
-    cr[c] = R;
+    if (crf) {
+      const int nfx = (nx + 1) * P.ny;
+      CellRecF F;
+      F.Gn = (float)R.Gn; F.Un = (float)Un; F.Vn = (float)Vn; F.lamn = (float)ln;
+      F.G1 = (float)R.G1; F.U1 = (float)U1; F.V1 = (float)V1; F.lam1 = (float)l1;
+      F.bn = (float)R.bn; F.b1 = (float)R.b1; F.inv = (float)R.inv; F.cg1 = (float)R.cg1;
+      F.cgn = (float)R.cgn;
+      F.refx = (float)((mt4[xw] - mt4[xe]) / P.dx);
+      F.refy = (float)((mt4[nfx + ys] - mt4[nfx + yn]) / P.dy);
+      F.pad = 0.f;
+      crf[c] = F;
+    } else {
+      cr[c] = R;
+    }
   }
   for (int k = 0; k < 4; k++) {
     red[k][threadIdx.x] = d2[k];
@@ -922,6 +966,205 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     };
     half(std::integral_constant<bool, false>{}, 0, P.m_pos);
     half(std::integral_constant<bool, true>{}, P.m_pos, nv);
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// FP32 form, S6 + S8 and Eq. 3 as an upwind column walk.  For one velocity the micro flux
+// through a face depends only on its upwind cell, so each cell evaluates the flux through
+// its downwind x-face and downwind y-face, and takes the flux through its upwind faces
+// from the upwind neighbour: the x-upwind one is evaluated from a second register window
+// (the neighbour column), the y-upwind one is the previous row's downwind flux carried in
+// registers, because the walk runs along y in the direction of v.
+// Grid: x = column groups of 4 (one warp per column), y = tiles of kWalkRows rows,
+// z = velocity chunks of 32 (v < 0 chunks first, then v >= 0).  Lane = velocity.
+// Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + df.
+// -------------------------------------------------------------------------------------
+constexpr int kWalkRows = 64;
+
+__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+
+struct LaneVel {
+  float u, v, uu, uv, vv, ur2, vr2;
+};
+
+// Q_h and the b-component polynomial of a face record for one side, at (un, ut), where the
+// monomials are given in the face frame: m1 = un, m2 = ut, m3 = un^2, m4 = un ut, m5 = ut^2,
+// m6 = un r2, m7 = ut r2.
+__device__ __forceinline__ void eval_q(const FaceRecF* R, int side, float m1, float m2, float m3,
+                                       float m4, float m5, float m6, float m7, float& qh, float& qb) {
+  const float4 a = *reinterpret_cast<const float4*>(&R->Q[side][0]);
+  const float4 b = *reinterpret_cast<const float4*>(&R->Q[side][4]);
+  const float4 k = *reinterpret_cast<const float4*>(&R->kb[side][0]);
+  qh = a.x + a.y * m1 + a.z * m2 + a.w * m3 + b.x * m4 + b.y * m5 + b.z * m6 + b.w * m7;
+  const float X2 = R->X2;
+  qb = X2 * qh + k.x + k.y * m1 + k.z * m2;
+}
+
+// X = Q g + Mt4 f_up - Mt5 d for one face, both components (e-form f_up).
+__device__ __forceinline__ float2 face_x(const FaceRecF* R, int side, float un, float ut, float m1,
+                                         float m2, float m3, float m4, float m5, float m6, float m7,
+                                         float2 fup, float2 d) {
+  float qh, qb;
+  eval_q(R, side, m1, m2, m3, m4, m5, m6, m7, qh, qb);
+  const float4 g4 = *reinterpret_cast<const float4*>(&R->lam);  // lam Un Ut G
+  const float4 t4 = *reinterpret_cast<const float4*>(&R->Mt4);  // Mt4 Mt5 X2 wall
+  const float dn = un - g4.y, dt = ut - g4.z;
+  const float g = g4.w * __expf(-g4.x * (dn * dn + dt * dt));
+  float2 X;
+  X.x = qh * g + t4.x * fup.x - t4.y * d.x;
+  X.y = qb * g + t4.x * fup.y - t4.y * d.y;
+  return X;
+}
+
+// Flux leaving a wall into the gas, e-form: dt (g_wall - g_ref).
+__device__ __forceinline__ float2 wall_in(const FaceRecF* R, float un, float ut, float dt, float2 gr) {
+  const float4 g4 = *reinterpret_cast<const float4*>(&R->lam);
+  const float dn = un - g4.y, du = ut - g4.z;
+  const float g = g4.w * __expf(-g4.x * (dn * dn + du * du));
+  float2 X;
+  X.x = dt * (g - gr.x);
+  X.y = dt * (R->X2 * g - gr.y);
+  return X;
+}
+
+__global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict__ f,
+                                              float2* __restrict__ fo,
+                                              const FaceRecF* __restrict__ fxr,
+                                              const FaceRecF* __restrict__ fyr,
+                                              const CellRecF* __restrict__ cr, int nchunk_neg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nx = P.nx, ny = P.ny, nu = P.nu, nq = P.nq;
+  const int i = blockIdx.x * 4 + warp;
+  if (i >= nx) return;
+  const int chunk = blockIdx.z;
+  const bool vpos = chunk >= nchunk_neg;
+  const int nq_neg = P.m_neg * nu;
+  const int q = vpos ? nq_neg + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
+  const int qend = vpos ? nq : nq_neg;
+  const bool act = q < qend;
+  const int qq = act ? q : qend - 1;
+  const int k = qq % nu, m = qq / nu;
+  const float u = (float)P.u[k], v = (float)P.v[m];
+  const int su = u > 0.f ? 1 : -1;
+  const int sv = vpos ? 1 : -1;
+  const float r2 = u * u + v * v;
+  const float m_u = u, m_v = v, m_uu = u * u, m_uv = u * v, m_vv = v * v, m_ur2 = u * r2, m_vr2 = v * r2;
+  const float cu = u * (float)(2.0 / P.dx), cv = v * (float)(2.0 / P.dy);
+  const float au = fabsf(u) * (float)(1.0 / P.dx), av = fabsf(v) * (float)(1.0 / P.dy);
+  const float dtf = (float)P.dt;
+  const float2 gr = __ldg(static_cast<const float2*>(P.gref) + qq);
+  const int xside = u > 0.f ? 0 : 1, yside = vpos ? 0 : 1;
+  const int iu = i - su, iuu = i - 2 * su, id = i + su;
+  const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
+  const bool zu = (iu < 0 && pW) || (iu >= nx && pE);  // x-upwind cell is a pressure ghost
+  const int fxo = su > 0 ? 1 : 0;                       // downwind x-face offset i + fxo
+  const int fxi = su > 0 ? 0 : 1;                       // upwind x-face offset
+
+  const int j0 = blockIdx.y * kWalkRows;
+  const int j1 = min(j0 + kWalkRows, ny);
+  const int jfirst = sv > 0 ? j0 : j1 - 1, jlast = sv > 0 ? j1 - 1 : j0;
+  const long rs = (long)P.ex * nq;
+  const float2* col = f + fcell(P, i, 0) * nq + qq;      // own column, row 0
+  const float2* colu = f + fcell(P, iu, 0) * nq + qq;    // x-upwind column
+  const float2* cold = f + fcell(P, id, 0) * nq + qq;    // x-downwind column
+  const float2* coluu = f + fcell(P, iuu, 0) * nq + qq;  // far x-upwind column
+
+  // prologue: downwind y-face flux of the halo cell (i, jp), jp = jfirst - sv
+  const int jp = jfirst - sv;
+  float2 fo_p = ld2(col + (long)jp * rs), fo_c = ld2(col + (long)jfirst * rs);
+  float2 fu_p = ld2(colu + (long)jp * rs), fu_c = ld2(colu + (long)jfirst * rs);
+  float2 Xin_y;
+  {
+    const int yface = (sv > 0 ? jfirst : jp) * nx + i;  // face between jp and jfirst
+    const FaceRecF* RY = fyr + yface;
+    if (RY->wall != 0.f) {
+      Xin_y = wall_in(RY, v, u, dtf, gr);
+    } else {
+      const float2 fpp = ld2(col + (long)(jp - sv) * rs);
+      const float2 fl = ld2(f + fcell(P, i - 1, jp) * nq + qq), fr = ld2(f + fcell(P, i + 1, jp) * nq + qq);
+      const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
+      float2 rx, ry;
+      rx.x = zp ? 0.f : vl_half(fl.x, fo_p.x, fr.x);
+      rx.y = zp ? 0.f : vl_half(fl.y, fo_p.y, fr.y);
+      // +y slope of the halo cell: rows jp-1, jp, jp+1
+      const float2 lo = sv > 0 ? fpp : fo_c, hi = sv > 0 ? fo_c : fpp;
+      ry.x = zp ? 0.f : vl_half(lo.x, fo_p.x, hi.x);
+      ry.y = zp ? 0.f : vl_half(lo.y, fo_p.y, hi.y);
+      const float sy = (float)sv;
+      float2 fup, d;
+      fup.x = fo_p.x + sy * ry.x; fup.y = fo_p.y + sy * ry.y;
+      d.x = cu * rx.x + cv * ry.x; d.y = cu * rx.y + cv * ry.y;
+      Xin_y = face_x(RY, yside, v, u, m_v, m_u, m_vv, m_uv, m_uu, m_vr2, m_ur2, fup, d);
+    }
+  }
+
+  const float sx = (float)su, sy = (float)sv;
+  for (int j = jfirst;; j += sv) {
+    const float2 fo_n = ld2(col + (long)(j + sv) * rs);
+    const float2 fu_n = ld2(colu + (long)(j + sv) * rs);
+    const float2 fd = ld2(cold + (long)j * rs);
+    const float2 fuu = ld2(coluu + (long)j * rs);
+    // own slopes (+x, +y)
+    const float2 xl = su > 0 ? fu_c : fd, xr = su > 0 ? fd : fu_c;
+    const float2 yl = sv > 0 ? fo_p : fo_n, yr = sv > 0 ? fo_n : fo_p;
+    float2 rx, ry;
+    rx.x = vl_half(xl.x, fo_c.x, xr.x); rx.y = vl_half(xl.y, fo_c.y, xr.y);
+    ry.x = vl_half(yl.x, fo_c.x, yr.x); ry.y = vl_half(yl.y, fo_c.y, yr.y);
+    float2 d;
+    d.x = cu * rx.x + cv * ry.x; d.y = cu * rx.y + cv * ry.y;
+    const CellRecF* C = cr + (size_t)j * nx + i;
+    // downwind x-face
+    const FaceRecF* RXo = fxr + (size_t)j * (nx + 1) + i + fxo;
+    float2 fup;
+    fup.x = fo_c.x + sx * rx.x; fup.y = fo_c.y + sx * rx.y;
+    const float2 Xout_x = face_x(RXo, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fup, d);
+    // upwind x-face: flux leaving the x-upwind cell (or the wall)
+    const FaceRecF* RXi = fxr + (size_t)j * (nx + 1) + i + fxi;
+    float2 Xin_x;
+    if (RXi->wall != 0.f) {
+      Xin_x = wall_in(RXi, u, v, dtf, gr);
+    } else {
+      const float2 al = su > 0 ? fuu : fo_c, ar = su > 0 ? fo_c : fuu;
+      const float2 bl = sv > 0 ? fu_p : fu_n, br = sv > 0 ? fu_n : fu_p;
+      float2 rxu, ryu;
+      rxu.x = zu ? 0.f : vl_half(al.x, fu_c.x, ar.x);
+      rxu.y = zu ? 0.f : vl_half(al.y, fu_c.y, ar.y);
+      ryu.x = zu ? 0.f : vl_half(bl.x, fu_c.x, br.x);
+      ryu.y = zu ? 0.f : vl_half(bl.y, fu_c.y, br.y);
+      float2 fuw, du;
+      fuw.x = fu_c.x + sx * rxu.x; fuw.y = fu_c.y + sx * rxu.y;
+      du.x = cu * rxu.x + cv * ryu.x; du.y = cu * rxu.y + cv * ryu.y;
+      Xin_x = face_x(RXi, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fuw, du);
+    }
+    // downwind y-face
+    const FaceRecF* RYo = fyr + (size_t)(sv > 0 ? j + 1 : j) * nx + i;
+    fup.x = fo_c.x + sy * ry.x; fup.y = fo_c.y + sy * ry.y;
+    const float2 Xout_y = face_x(RYo, yside, v, u, m_v, m_u, m_vv, m_uv, m_uu, m_vr2, m_ur2, fup, d);
+    // Eq. 3 as an increment
+    const float4 c0 = *reinterpret_cast<const float4*>(&C->Gn);   // Gn Un Vn lamn
+    const float4 c1 = *reinterpret_cast<const float4*>(&C->G1);   // G1 U1 V1 lam1
+    const float4 c2 = *reinterpret_cast<const float4*>(&C->bn);   // bn b1 inv cg1
+    const float4 c3 = *reinterpret_cast<const float4*>(&C->cgn);  // cgn refx refy
+    float a = u - c0.y, b = v - c0.z;
+    const float gn = c0.x * __expf(-c0.w * (a * a + b * b));
+    a = u - c1.y; b = v - c1.z;
+    const float g1 = c1.x * __expf(-c1.w * (a * a + b * b));
+    const float rr = u * c3.y + v * c3.z;
+    const float flh = au * (Xin_x.x - Xout_x.x) + av * (Xin_y.x - Xout_y.x) + rr * gr.x;
+    const float flb = au * (Xin_x.y - Xout_x.y) + av * (Xin_y.y - Xout_y.y) + rr * gr.y;
+    const float dh = c2.z * (flh + c2.w * ((g1 - gr.x) - fo_c.x) + c3.x * ((gn - gr.x) - fo_c.x));
+    const float db = c2.z * (flb + c2.w * ((c2.y * g1 - gr.y) - fo_c.y) + c3.x * ((c2.x * gn - gr.y) - fo_c.y));
+    if (act) {
+      float2 o;
+      o.x = fo_c.x + dh;
+      o.y = fo_c.y + db;
+      fo[fcell(P, i, j) * nq + qq] = o;
+    }
+    if (j == jlast) break;
+    Xin_y = Xout_y;
+    fo_p = fo_c; fo_c = fo_n;
+    fu_p = fu_c; fu_c = fu_n;
   }
 }
 

@@ -92,6 +92,20 @@ def test_one_step_fp64_parity(U, oracle, name):
     assert rel_f(fg, fr) <= FP64_TOL, rel_f(fg, fr)
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_fp32f_parity(U, oracle, name):
+    """FP32-f form, one step from a non-equilibrium state, every edge-case configuration:
+    per-field error <= 1e-6 relative, f <= 1e-5 relative to max|f|."""
+    cfg = CASES[name]()
+    f, W = random_state(oracle, cfg, 103)
+    fr, Wr = oracle.step(cfg, f, W, 1)
+    fg, Wg = one_step(U, cfg, f, W, prec=U.FP32F)
+    ew, ef = rel_fields(Wg, Wr), rel_f(fg, fr)
+    print(f"fp32f {name}: W {ew} f {ef:.2e}")
+    assert np.all(ew <= 1e-6), ew
+    assert ef <= 1e-5, ef
+
+
 def test_init_maxwellian_parity(U, oracle):
     cfg = I.workload_channel_small()
     rho, Uf, Vf, T = I.initial_prim(cfg, I.seed_for(1))
@@ -130,6 +144,7 @@ def test_fp32f_form_200_steps(U, oracle):
         s.step(cfg.steps)
         W, prim = s.moments(prim=True)
     err = rel_fields(W, Wr)
+    print(f"fp32f 200 steps: per-field error {err}")
     assert np.all(err <= FP32_TOL), err
 
 
