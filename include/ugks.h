@@ -157,6 +157,29 @@ ugks_status ugks_profile(ugks_handle h, int enable);
 ugks_status ugks_kernel_times(ugks_handle h, double* ms, long* launches);
 const char* ugks_kernel_name(int i);
 
+/* One FP64 UGKS step on caller-owned device buffers that allocates no device memory.
+ * For callers that cannot call cudaMalloc at all -- code running where the CUDA allocator
+ * is off limits, such as inside a host framework that owns every device allocation, or
+ * where an allocation could block or fail at an awkward time -- and who therefore cannot
+ * use ugks_create.  The paper has no counterpart; it is an interface convenience.
+ *   cfg          problem statement; cfg->precision must be UGKS_FP64.
+ *   f_in, W_in   device state at t^n, layouts f[nc][nq][2], W[4][nc] (FP64), read only.
+ *   f_out, W_out device buffers for t^{n+1}, same layouts; must not overlap the inputs.
+ *   cuda_stream  cudaStream_t or NULL.  The call is synchronous: it waits for its own work
+ *                on that stream before returning, and reports UGKS_ENUMERIC for rho <= 0,
+ *                T <= 0 or NaN in a cell.
+ * All intermediates live in one fixed device array inside the library, of
+ * UGKS_NOALLOC_SCRATCH_BYTES bytes, that every GPU which loads the library holds until the
+ * process exits.  Problems whose intermediates do not fit are rejected with UGKS_EINVAL and
+ * a message on stderr; the need is about 32 (nx+4)(ny+4) nu nv + 1000 (nx+2)(ny+2) bytes.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress),
+ * so make it before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: UGKS_EINVAL (bad or oversize cfg, NULL pointer), UGKS_ECUDA, UGKS_ENUMERIC. */
+#define UGKS_NOALLOC_SCRATCH_BYTES (64u << 20)
+ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const double* W_in,
+                              double* f_out, double* W_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -341,7 +342,201 @@ ugks_status check_err(ugks_ctx* h) {
 
 }  // namespace
 
+// -------------------------------------------------------------------------------------
+// Scratch for ugks_step_noalloc: a fixed device array, no allocation at call time.
+// -------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[UGKS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
 extern "C" {
+
+ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const double* W_in,
+                              double* f_out, double* W_out, void* cuda_stream) {
+  const char* bad = validate(cfg);
+  if (bad || !f_in || !W_in || !f_out || !W_out || cfg->precision != UGKS_FP64) {
+    fprintf(stderr, "ugks_step_noalloc: %s\n",
+            bad ? bad : (cfg->precision != UGKS_FP64 ? "precision must be UGKS_FP64" : "NULL buffer"));
+    return UGKS_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // host-side setup in fixed-size arrays (no heap)
+  Params P;
+  memset(&P, 0, sizeof P);
+  P.nx = cfg->nx; P.ny = cfg->ny; P.nu = cfg->nu; P.nv = cfg->nv; P.nq = cfg->nu * cfg->nv;
+  P.K = cfg->K;
+  P.ex = cfg->nx + 4;
+  P.wx = cfg->nx + 2;
+  P.dx = cfg->lx / cfg->nx;
+  P.dy = cfg->ly / cfg->ny;
+  double grid[4 * kMaxAxis];
+  double* hu = grid;
+  double* hv = grid + P.nu;
+  double* hwu = grid + P.nu + P.nv;
+  double* hwv = grid + 2 * P.nu + P.nv;
+  auto fill_axis = [](int n, double lo, double hi, double* x, double* w) {
+    if (n == 1) { x[0] = 0.5 * (lo + hi); w[0] = 1.0; return; }
+    const double d = (hi - lo) / (n - 1), c = 0.5 * (lo + hi);
+    for (int k = 0; k < n; k++) {
+      x[k] = c + (k - 0.5 * (n - 1)) * d;
+      w[k] = (k == 0 || k == n - 1) ? 0.5 * d : d;
+    }
+  };
+  fill_axis(P.nu, cfg->umin, cfg->umax, hu, hwu);
+  fill_axis(P.nv, cfg->vmin, cfg->vmax, hv, hwv);
+  double um = 0, vm = 0;
+  for (int k = 0; k < P.nu; k++) um = fmax(um, fabs(hu[k]));
+  for (int m = 0; m < P.nv; m++) vm = fmax(vm, fabs(hv[m]));
+  if (cfg->dt > 0) P.dt = cfg->dt;
+  else {
+    if (!(um / P.dx + vm / P.dy > 0)) return UGKS_EINVAL;
+    P.dt = cfg->cfl / (um / P.dx + vm / P.dy);
+  }
+  const double a = cfg->alpha, om = cfg->omega;
+  P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
+  P.omega = om;
+  for (int sd = 0; sd < 4; sd++) {
+    P.bc_kind[sd] = cfg->bc[sd].kind;
+    P.bc_rho[sd] = cfg->bc[sd].rho;
+    P.bc_T[sd] = cfg->bc[sd].T;
+    P.bc_U[sd] = cfg->bc[sd].U;
+    if (cfg->bc[sd].kind != UGKS_BC_WALL) continue;
+    const double lam = 1.0 / cfg->bc[sd].T, Uw = cfg->bc[sd].U;
+    for (int m = 0; m < P.nv; m++)
+      for (int k = 0; k < P.nu; k++) {
+        const double u = hu[k], v = hv[m], w = hwu[k] * hwv[m];
+        const double un = sd < 2 ? u : v, ut = sd < 2 ? v : u;
+        const bool outgoing = (sd == 0 || sd == 2) ? un > 0 : un < 0;
+        if (!outgoing) continue;
+        const double gh = lam / M_PI * exp(-lam * ((ut - Uw) * (ut - Uw) + un * un));
+        const double gb = P.K / (2.0 * lam) * gh;
+        P.wall_mom[sd][0] += w * un * gh;
+        P.wall_mom[sd][1] += w * un * u * gh;
+        P.wall_mom[sd][2] += w * un * v * gh;
+        P.wall_mom[sd][3] += w * un * (0.5 * (u * u + v * v) * gh + 0.5 * gb);
+      }
+  }
+  P.m_pos = P.nv;
+  for (int m = 0; m < P.nv; m++)
+    if (hv[m] > 0) { P.m_pos = m; break; }
+  for (int m = 0; m < P.nv; m++)
+    if (hv[m] < 0) P.m_neg = m + 1;
+
+  // carve the scratch array
+  const int nx = P.nx, ny = P.ny, nq = P.nq, nc = nx * ny;
+  const int nwe = (nx + 2) * (ny + 2), nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
+  const int nrb = (nc + 127) / 128;
+  const size_t fb = (size_t)(nx + 4) * (ny + 4) * nq * sizeof(double2);
+  size_t off[16], need = 0;
+  const size_t sz[13] = {fb, fb, 4 * sizeof(double) * nwe, 4 * sizeof(double) * nwe,
+                         sizeof(double) * kNSum * (size_t)nwe, sizeof(FaceRec) * (size_t)nfx,
+                         sizeof(FaceRec) * (size_t)nfy, sizeof(double) * 4 * (size_t)nfx,
+                         sizeof(double) * 4 * (size_t)nfy, sizeof(double) * (size_t)(nfx + nfy),
+                         sizeof(CellRec) * (size_t)nc, sizeof(double) * 8 * (size_t)nrb,
+                         sizeof(double) * 2 * (P.nu + P.nv) + sizeof(int)};
+  for (int b = 0; b < 13; b++) { off[b] = need; need += align256(sz[b]); }
+  if (need > UGKS_NOALLOC_SCRATCH_BYTES) {
+    fprintf(stderr, "ugks_step_noalloc: problem needs %zu bytes of scratch, the fixed maximum is %u\n",
+            need, (unsigned)UGKS_NOALLOC_SCRATCH_BYTES);
+    return UGKS_EINVAL;
+  }
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "ugks_step_noalloc: scratch address: %s\n", cudaGetErrorString(e));
+    return UGKS_ECUDA;
+  }
+  char* sb = static_cast<char*>(base);
+  double2* f0 = reinterpret_cast<double2*>(sb + off[0]);
+  double2* f1 = reinterpret_cast<double2*>(sb + off[1]);
+  double* W0 = reinterpret_cast<double*>(sb + off[2]);
+  double* W1 = reinterpret_cast<double*>(sb + off[3]);
+  double* sums = reinterpret_cast<double*>(sb + off[4]);
+  FaceRec* fxr = reinterpret_cast<FaceRec*>(sb + off[5]);
+  FaceRec* fyr = reinterpret_cast<FaceRec*>(sb + off[6]);
+  double* Fx = reinterpret_cast<double*>(sb + off[7]);
+  double* Fy = reinterpret_cast<double*>(sb + off[8]);
+  double* mt4 = reinterpret_cast<double*>(sb + off[9]);
+  CellRec* cells = reinterpret_cast<CellRec*>(sb + off[10]);
+  double* rpart = reinterpret_cast<double*>(sb + off[11]);
+  double* dgrid = reinterpret_cast<double*>(sb + off[12]);
+  int* err = reinterpret_cast<int*>(dgrid + 2 * (P.nu + P.nv));
+  P.u = dgrid;
+  P.v = dgrid + P.nu;
+  P.wu = dgrid + P.nu + P.nv;
+  P.wv = dgrid + 2 * P.nu + P.nv;
+
+#define NA_CK(call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      fprintf(stderr, "ugks_step_noalloc: %s: %s\n", #call, cudaGetErrorString(e_));   \
+      return UGKS_ECUDA;                                                                \
+    }                                                                                   \
+  } while (0)
+  NA_CK(cudaMemcpyAsync(dgrid, grid, sizeof(double) * 2 * (P.nu + P.nv), cudaMemcpyHostToDevice, st));
+  NA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  // the previous call's contents stay in the array: clear the f ring so every cell the
+  // kernels read is defined
+  NA_CK(cudaMemsetAsync(f0, 0, fb, st));
+  NA_CK(cudaMemsetAsync(W0, 0, 4 * sizeof(double) * nwe, st));
+  const size_t row = (size_t)nx * nq * sizeof(double2);
+  NA_CK(cudaMemcpy2DAsync(reinterpret_cast<char*>(f0) + ((size_t)2 * P.ex + 2) * nq * sizeof(double2),
+                          (size_t)P.ex * nq * sizeof(double2), f_in, row, row, ny, cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < 4; c++)
+    NA_CK(cudaMemcpy2DAsync(W0 + (size_t)c * nwe + wcell(P, 0, 0), P.wx * sizeof(double),
+                            W_in + (size_t)c * nc, nx * sizeof(double), nx * sizeof(double), ny,
+                            cudaMemcpyDeviceToDevice, st));
+  NA_CK(set_smem_limits<double>(P.nv));
+  k_ghost_x<double2><<<dim3(ny, 4), 128, 0, st>>>(P, f0, W0, nwe);
+  k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
+  k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
+                            smem_sums<double>(P.nv), st>>>(P, f0, sums);
+  k_faces<<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
+  k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
+  k_update<double, double2, false><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
+                                     smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells);
+  NA_CK(cudaGetLastError());
+  NA_CK(cudaMemcpy2DAsync(f_out, row, reinterpret_cast<char*>(f1) + ((size_t)2 * P.ex + 2) * nq * sizeof(double2),
+                          (size_t)P.ex * nq * sizeof(double2), row, ny, cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < 4; c++)
+    NA_CK(cudaMemcpy2DAsync(W_out + (size_t)c * nc, nx * sizeof(double), W1 + (size_t)c * nwe + wcell(P, 0, 0),
+                            P.wx * sizeof(double), nx * sizeof(double), ny, cudaMemcpyDeviceToDevice, st));
+  int herr = 0;
+  NA_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NA_CK(cudaStreamSynchronize(st));
+#undef NA_CK
+  if (herr) {
+    fprintf(stderr, "ugks_step_noalloc: numerical failure (rho <= 0, T <= 0 or NaN)\n");
+    return UGKS_ENUMERIC;
+  }
+  return UGKS_OK;
+}
 
 ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* out) {
   if (!out) return UGKS_EINVAL;

@@ -22,7 +22,7 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_device_bytes", "ugks_set_state", "ugks_set_state_device",
            "ugks_init_maxwellian", "ugks_step", "ugks_sync", "ugks_moments", "ugks_get_state",
            "ugks_get_state_device", "ugks_residual", "ugks_profile", "ugks_kernel_times",
-           "ugks_kernel_name")
+           "ugks_kernel_name", "ugks_step_noalloc")
 NKERNELS = 6
 
 
@@ -83,6 +83,8 @@ def lib(build_if_missing: bool = True):
         L.ugks_kernel_times.argtypes = [C.c_void_p, _P, C.POINTER(C.c_long)]
         L.ugks_kernel_name.argtypes = [C.c_int]
         L.ugks_kernel_name.restype = C.c_char_p
+        L.ugks_step_noalloc.argtypes = [C.POINTER(_Config), C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -215,3 +217,14 @@ class Solver:
         r = np.empty(4)
         self._check(self._L.ugks_residual(self._h, r.ctypes.data_as(_P)))
         return r
+
+
+def step_noalloc(cfg, f_in, W_in, f_out, W_out, stream=None) -> None:
+    """ugks_step_noalloc: one FP64 step on caller-owned device buffers (torch CUDA float64
+    tensors or integer addresses), with no device allocation by the library."""
+    c = to_c_config(cfg, FP64)
+    st = lib().ugks_step_noalloc(C.byref(c), C.c_void_p(_dptr(f_in)), C.c_void_p(_dptr(W_in)),
+                                 C.c_void_p(_dptr(f_out)), C.c_void_p(_dptr(W_out)),
+                                 C.c_void_p(stream or 0))
+    if st:
+        raise UGKSError(st, "ugks_step_noalloc failed (see stderr)")
