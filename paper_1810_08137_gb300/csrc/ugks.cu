@@ -43,6 +43,7 @@ struct ugks_ctx {
   double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv]
   double* stage = nullptr;   // FP64 staging for FP32 state conversion
   float2* gref = nullptr;    // FP32 form: g_ref per velocity
+  float* ftab = nullptr;     // FP32 form: velocity tables (mvf, uwf)
   size_t stage_bytes = 0;
   std::vector<double> hu, hv, hwu, hwv;
   size_t bytes = 0;
@@ -161,12 +162,13 @@ cudaError_t launch_step(ugks_ctx* h) {
   k_ghost_y<T2><<<dim3(P.nx + 4, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
   if ((r = mark(h, 2)) != cudaSuccess) return r;
   const int nce = (P.nx + 2) * (P.ny + 2);
+  T* sums = reinterpret_cast<T*>(h->sums);  // FP32 form: FP32 sums in the same buffer
   k_sums<T, T2><<<(nce + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_sums<T>(P.nv), st>>>(
-      P, fi, h->sums);
+      P, fi, sums);
   if ((r = mark(h, 3)) != cudaSuccess) return r;
   const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
-  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, h->sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
-                                            h->fxf, h->fyf, h->mt4);
+  k_faces<T><<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
+                                               h->fxf, h->fyf, h->mt4);
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   const int nc = P.nx * P.ny;
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
@@ -420,6 +422,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   const double a = cfg->alpha, om = cfg->omega;
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
+  P.omega_half = om == 0.5;
   for (int sd = 0; sd < 4; sd++) {
     P.bc_kind[sd] = cfg->bc[sd].kind;
     P.bc_rho[sd] = cfg->bc[sd].rho;
@@ -517,7 +520,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                             smem_sums<double>(P.nv), st>>>(P, f0, sums);
-  k_faces<<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
+  k_faces<double><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
   k_update<double, double2, false><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                                      smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells);
@@ -572,6 +575,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   const double a = cfg->alpha, om = cfg->omega;
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
+  P.omega_half = om == 0.5;
   for (int s = 0; s < 4; s++) {
     P.bc_kind[s] = cfg->bc[s].kind;
     P.bc_rho[s] = cfg->bc[s].rho;
@@ -669,7 +673,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (want < row_d) want = row_d;
     if (want > row_d * P.ny) want = row_d * P.ny;
     h->stage_bytes = want;
-    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq);
+    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq) &&
+         alloc((void**)&h->ftab, sizeof(float) * (5 * (size_t)P.nv + 2 * (size_t)P.nu));
   }
   if (!ok) {
     ugks_destroy(h);
@@ -686,6 +691,21 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.wu = h->d_grid + P.nu + P.nv;
   P.wv = h->d_grid + 2 * P.nu + P.nv;
   P.gref = h->gref;
+  std::vector<float> ftab_host;
+  if (h->ftab) {
+    ftab_host.resize(5 * (size_t)P.nv + 2 * (size_t)P.nu);
+    for (int m = 0; m < P.nv; m++) {
+      const double vv = h->hv[m], w = h->hwv[m];
+      const double t[5] = {w, w * vv, w * vv * vv, w * vv * vv * vv, vv};
+      for (int c = 0; c < 5; c++) ftab_host[(size_t)c * P.nv + m] = (float)t[c];
+    }
+    for (int k = 0; k < P.nu; k++) {
+      ftab_host[5 * (size_t)P.nv + k] = (float)h->hu[k];
+      ftab_host[5 * (size_t)P.nv + P.nu + k] = (float)h->hwu[k];
+    }
+    P.mvf = h->ftab;
+    P.uwf = h->ftab + 5 * (size_t)P.nv;
+  }
   auto setup = [&]() -> cudaError_t {
     cudaError_t r;
     if ((r = cudaMemcpyAsync(h->d_grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -696,6 +716,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     }
     if ((r = cudaMemsetAsync(h->rpart, 0, sizeof(double) * 8 * h->nrblocks, h->stream)) != cudaSuccess) return r;
     if (h->gref && (r = cudaMemcpyAsync(h->gref, gref_host.data(), sizeof(float2) * gref_host.size(),
+                                        cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return r;
+    if (h->ftab && (r = cudaMemcpyAsync(h->ftab, ftab_host.data(), sizeof(float) * ftab_host.size(),
                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
@@ -717,7 +740,7 @@ void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->fxf, h->fyf,
-                  h->cellf, h->mt4};
+                  h->cellf, h->mt4, h->ftab};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs)
     if (p) cudaFree(p);

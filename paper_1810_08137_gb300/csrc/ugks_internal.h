@@ -77,6 +77,9 @@ struct Params {
   double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
   const void* gref;       // [nq] T2 table of g_ref (FP32 form), else null
+  int omega_half;         // omega == 1/2: lam^-omega = rsqrt(lam)
+  const float* mvf;       // FP32 tables: [5][nv] wv, wv v, wv v^2, wv v^3, v
+  const float* uwf;       // FP32 tables: [2][nu] u, wu
   const double* u;        // [nu]
   const double* v;        // [nv]
   const double* wu;       // [nu]

@@ -51,6 +51,12 @@ __device__ __forceinline__ float vl_half(float a, float c, float b) {
 __device__ __forceinline__ double texp(double x) { return exp(x); }
 __device__ __forceinline__ float texp(float x) { return expf(x); }
 
+// Collision time tau = mu / p with mu = mu_ref T^omega, T = 1/lam, p = rho / (2 lam).
+__device__ __forceinline__ double collision_time(const Params& P, double rho, double lam) {
+  const double lw = P.omega_half ? rsqrt(lam) : pow(lam, -P.omega);  // lam^-omega = T^omega
+  return P.mu_ref * lw * 2.0 * lam / rho;
+}
+
 // Sum over the warp of v[lane % N] returned to each lane (N = 16 or 32): transpose
 // reduce-scatter, N-1 shuffles instead of N*5.
 template <int N, typename T>
@@ -158,7 +164,7 @@ __global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
 template <typename T, typename T2>
 __device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T P3, T Pb0, T Pb1,
                                            T Q0, T Q1, T Q2, T Qb, T Z1, T Z2, T Z3, T Zb1,
-                                           int lane, double* ws_side) {
+                                           int lane, T* ws_side) {
   T v[16];
   const T uu = u * u;
   v[0] = wu * P0;
@@ -179,27 +185,39 @@ __device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T
   v[14] = wu * Z2;
   v[15] = wu * (T(0.5) * (uu * Z1 + Z3) + T(0.5) * Zb1);
   const T r = warp_reduce_scatter<16>(v, lane);
-  if (lane < 16) ws_side[lane] += (double)r;
+  if (lane < 16) ws_side[lane] += r;
+}
+
+// velocity tables in the arithmetic type (FP32 tables are rounded from FP64 on the host)
+__device__ __forceinline__ void vtab(const Params& P, int m, double* o) {
+  const double vv = P.v[m], w = P.wv[m];
+  o[0] = w; o[1] = w * vv; o[2] = w * vv * vv; o[3] = w * vv * vv * vv; o[4] = vv;
+}
+__device__ __forceinline__ void vtab(const Params& P, int m, float* o) {
+  for (int t = 0; t < 5; t++) o[t] = P.mvf[t * P.nv + m];
+}
+__device__ __forceinline__ void utab(const Params& P, int k, double& u, double& wu) {
+  u = P.u[k]; wu = P.wu[k];
+}
+__device__ __forceinline__ void utab(const Params& P, int k, float& u, float& wu) {
+  u = P.uwf[k]; wu = P.uwf[P.nu + k];
 }
 
 template <typename T, typename T2>
 __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
-                                              double* __restrict__ sums) {
+                                              T* __restrict__ sums) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nv = P.nv, nu = P.nu, nq = P.nq;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* wsum = reinterpret_cast<double*>(smraw) + warp * kNSum;
+  T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
   T* mw = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(double));
   // mw[0..4nv): wv, wv v, wv v^2, wv v^3 ; mw[4nv..5nv): v
   for (int m = tid; m < nv; m += blockDim.x) {
-    const double vv = P.v[m], w = P.wv[m];
-    mw[m] = (T)w;
-    mw[nv + m] = (T)(w * vv);
-    mw[2 * nv + m] = (T)(w * vv * vv);
-    mw[3 * nv + m] = (T)(w * vv * vv * vv);
-    mw[4 * nv + m] = (T)vv;
+    T o[5];
+    vtab(P, m, o);
+    for (int t = 0; t < 5; t++) mw[t * nv + m] = o[t];
   }
-  for (int t = lane; t < kNSum; t += 32) wsum[t] = 0.0;
+  for (int t = lane; t < kNSum; t += 32) wsum[t] = T(0);
   __syncthreads();
 
   const int ncx = P.nx + 2;
@@ -222,8 +240,9 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
     const int k = k0 + lane;
     const bool act = k < nu;
     const int kk = act ? k : nu - 1;
-    const T u = (T)P.u[kk];
-    const T wu = act ? (T)P.wu[kk] : T(0);
+    T u, wu;
+    utab(P, kk, u, wu);
+    if (!act) wu = T(0);
     const T cu = u * tdx;
     T A0 = 0, A1 = 0, A2 = 0, Ab = 0, R0 = 0, R1 = 0, R2 = 0, Rb = 0;
     T C0 = 0, C1 = 0, C2 = 0, Cb = 0, D0 = 0, D1 = 0, D2 = 0, Db = 0;
@@ -312,10 +331,10 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
       o[15] = wuu * (T(0.5) * (uu * D0 + D2) + T(0.5) * Db);
     }
     const T r = warp_reduce_scatter<32>(x, lane);
-    wsum[kSumE + lane] += (double)r;  // lanes 0..15: E side, 16..31: W side
+    wsum[kSumE + lane] += r;  // lanes 0..15: E side, 16..31: W side
   }
   __syncwarp();
-  double* out = sums + (size_t)cell * kNSum;
+  T* out = sums + (size_t)cell * kNSum;
   out[lane] = wsum[lane];
   out[lane + 32] = wsum[lane + 32];
 }
@@ -342,6 +361,15 @@ __device__ void gauss_moments7(double U, double lam, double* M, double* Mp, doub
     Mp[n + 2] = U * Mp[n + 1] + (n + 1) * h * Mp[n];
     Mn[n + 2] = U * Mn[n + 1] + (n + 1) * h * Mn[n];
   }
+}
+
+// Full-range moments only (tangential axis).
+__device__ void gauss_moments7_full(double U, double lam, double* M) {
+  const double h = 0.5 / lam;
+  M[0] = 1.0;
+  M[1] = U;
+#pragma unroll
+  for (int n = 0; n < 5; n++) M[n + 2] = U * M[n + 1] + (n + 1) * h * M[n];
 }
 
 // <u^a v^b psi> and <u^a v^b xi^2 psi> for the normalised Maxwellian, u-moments Mu (one
@@ -398,17 +426,17 @@ __device__ void time_weights(double dt, double tau, double* Mt) {
   const double x = dt / tau;
   double c1, c2, c3, c4, c5;
   if (x < 0.1) {
-    // term n of each series via the ratio of consecutive terms; 16 terms
+    // term n of each series via the ratio of consecutive terms; 12 terms (the 13th is
+    // below 1e-22 relative for x < 0.1)
     double t4 = 1.0, s4 = 1.0;             // c4: (-x)^n/(n+1)!
-    double t5 = 0.5, s5 = 0.5;             // c5: (-1)^n (n+1) x^n/(n+2)!  (via base b5 = (-x)^n/(n+2)!)
-    double b5 = 0.5;
+    double b5 = 0.5, s5 = 0.5;             // c5: (n+1) (-x)^n/(n+2)!, b5 = (-x)^n/(n+2)!
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int n = 1; n < 16; n++) {
-      t4 *= -x / (n + 1);                  // (-x)^n/(n+1)!
-      b5 *= -x / (n + 2);                  // (-x)^n/(n+2)!
-      t5 = (n + 1) * b5;
+#pragma unroll
+    for (int n = 1; n < 12; n++) {
+      t4 *= -x * (1.0 / (n + 1));          // (-x)^n/(n+1)!
+      b5 *= -x * (1.0 / (n + 2));          // (-x)^n/(n+2)!
       s4 += t4;
-      s5 += t5;
+      s5 += (n + 1) * b5;
       s1 -= t4;                            // c1 = sum_{n>=1} -(-x)^n/(n+1)!
       s3 -= b5;                            // c3 = sum_{n>=1} -(-x)^n/(n+2)!
       s2 += n * b5;                        // c2 = sum_{n>=1} n (-x)^n/(n+2)!
@@ -465,12 +493,12 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], U = W0[1] / rho, V = W0[2] / rho;
   const double lam = (K + 2) * rho / (4.0 * (W0[3] - 0.5 * rho * (U * U + V * V)));
-  double Mu[7], Mup[7], Mun[7], Mv[7], Mvp[7], Mvn[7];
+  double Mu[7], Mup[7], Mun[7], Mv[7];
   gauss_moments7(U, lam, Mu, Mup, Mun);
-  gauss_moments7(V, lam, Mv, Mvp, Mvn);
+  gauss_moments7_full(V, lam, Mv);
   const double X2 = K / (2.0 * lam), X4 = (K * K + 2.0 * K) / (4.0 * lam * lam);
   // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5
-  const double tau = P.mu_ref * pow(lam, -P.omega) * 2.0 * lam / rho;
+  const double tau = collision_time(P, rho, lam);
   double Mt[5];
   time_weights(P.dt, tau, Mt);
   // S4: micro slopes
@@ -540,7 +568,8 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   }
 }
 
-__global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
+template <typename S>
+__global__ void k_faces(Params P, const S* __restrict__ sums, const double* __restrict__ W,
                         int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
                         double* __restrict__ Fx, double* __restrict__ Fy,
                         FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
@@ -582,11 +611,11 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
     // with the density that cancels the mass flux; first order in time
     const int oin = wall == 1 ? oR : oL;
-    const double* Se = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
-                                 : sums + (size_t)cL * kNSum + oL + kOffSf;
+    const S* Se = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
+                            : sums + (size_t)cL * kNSum + oL + kOffSf;
     double Sin[4];
 #pragma unroll
-    for (int c = 0; c < 4; c++) Sin[c] = Se[c] + P.refsum[oin / 16][kOffSf + c];
+    for (int c = 0; c < 4; c++) Sin[c] = (double)Se[c] + P.refsum[oin / 16][kOffSf + c];
     const double rhow = -Sin[0] / P.wall_mom[side][0];
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = P.dt * (Sin[c] + rhow * P.wall_mom[side][c]);
@@ -612,18 +641,18 @@ __global__ void k_faces(Params P, const double* __restrict__ sums, const double*
     }
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
-    const double* sL = sums + (size_t)cL * kNSum + oL;
-    const double* sR = sums + (size_t)cR * kNSum + oR;
+    const S* sL = sums + (size_t)cL * kNSum + oL;
+    const S* sR = sums + (size_t)cR * kNSum + oR;
     double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
     const double* rL = P.refsum[oL / 16];
     const double* rR = P.refsum[oR / 16];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const int s = pm[c];
-      W0[c] = (sL[kOffW0 + s] + sR[kOffW0 + s]) + (rL[kOffW0 + s] + rR[kOffW0 + s]);
-      St[c] = sL[kOffSt + s] + sR[kOffSt + s];
-      Sf[c] = (sL[kOffSf + s] + sR[kOffSf + s]) + (rL[kOffSf + s] + rR[kOffSf + s]);
-      Ss[c] = sL[kOffSs + s] + sR[kOffSs + s];
+      W0[c] = ((double)sL[kOffW0 + s] + (double)sR[kOffW0 + s]) + (rL[kOffW0 + s] + rR[kOffW0 + s]);
+      St[c] = (double)sL[kOffSt + s] + (double)sR[kOffSt + s];
+      Sf[c] = ((double)sL[kOffSf + s] + (double)sR[kOffSf + s]) + (rL[kOffSf + s] + rR[kOffSf + s]);
+      Ss[c] = (double)sL[kOffSs + s] + (double)sR[kOffSs + s];
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
@@ -678,8 +707,8 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
     const double l1 = (K + 2) * r1 / (4.0 * (W1[3] - 0.5 * r1 * (U1 * U1 + V1 * V1)));
     if (!(r1 > 0.0) || !(l1 > 0.0) || !isfinite(l1) || !isfinite(U1) || !isfinite(V1))
       atomicOr(err, 1);
-    const double tn = P.mu_ref * pow(ln, -P.omega) * 2.0 * ln / rn;
-    const double t1 = P.mu_ref * pow(l1, -P.omega) * 2.0 * l1 / r1;
+    const double tn = collision_time(P, rn, ln);
+    const double t1 = collision_time(P, r1, l1);
     CellRec R;
     R.Gn = rn * ln / kPi; R.Un = Un; R.Vn = Vn; R.lamn = ln; R.bn = K / (2.0 * ln);
     R.G1 = r1 * l1 / kPi; R.U1 = U1; R.V1 = V1; R.lam1 = l1; R.b1 = K / (2.0 * l1);
@@ -1028,7 +1057,7 @@ __device__ __forceinline__ float2 wall_in(const FaceRecF* R, float un, float ut,
   return X;
 }
 
-__global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict__ f,
+__global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restrict__ f,
                                               float2* __restrict__ fo,
                                               const FaceRecF* __restrict__ fxr,
                                               const FaceRecF* __restrict__ fyr,
@@ -1100,12 +1129,30 @@ __global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict
   }
 
   const float sx = (float)su, sy = (float)sv;
-  for (int j = jfirst;; j += sv) {
-    const float2 fo_n = ld2(col + (long)(j + sv) * rs);
-    const float2 fu_n = ld2(colu + (long)(j + sv) * rs);
-    const float2 fd = ld2(cold + (long)j * rs);
-    const float2 fuu = ld2(coluu + (long)j * rs);
-    // own slopes (+x, +y)
+  // row-walk pointers, bumped by one row per step; f loads are issued one step ahead
+  const long fstep = sv * rs;
+  const float2* po = col + (long)jfirst * rs;
+  const float2* pu = colu + (long)jfirst * rs;
+  const float2* pd = cold + (long)jfirst * rs;
+  const float2* puu = coluu + (long)jfirst * rs;
+  float2* pw = fo + fcell(P, i, jfirst) * nq + qq;
+  const long xstep = sv * (long)(nx + 1), ystep = sv * (long)nx;
+  const FaceRecF* RXo = fxr + (size_t)jfirst * (nx + 1) + i + fxo;
+  const FaceRecF* RXi = fxr + (size_t)jfirst * (nx + 1) + i + fxi;
+  const FaceRecF* RYo = fyr + (size_t)(sv > 0 ? jfirst + 1 : jfirst) * nx + i;
+  const CellRecF* C = cr + (size_t)jfirst * nx + i;
+  float2 fo_n = ld2(po + fstep), fu_n = ld2(pu + fstep), fd = ld2(pd), fuu = ld2(puu);
+  const int nsteps = (jlast - jfirst) * sv + 1;
+  for (int s = 0; s < nsteps; s++) {
+    float2 fo_nn = fo_n, fu_nn = fu_n, fd_n = fd, fuu_n = fuu;
+    if (s + 1 < nsteps) {
+      fo_nn = ld2(po + 2 * fstep);
+      fu_nn = ld2(pu + 2 * fstep);
+      fd_n = ld2(pd + fstep);
+      fuu_n = ld2(puu + fstep);
+    }
+    // own slopes (+x, +y); the x difference towards the upwind column is shared with the
+    // upwind cell's slope
     const float2 xl = su > 0 ? fu_c : fd, xr = su > 0 ? fd : fu_c;
     const float2 yl = sv > 0 ? fo_p : fo_n, yr = sv > 0 ? fo_n : fo_p;
     float2 rx, ry;
@@ -1113,14 +1160,11 @@ __global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict
     ry.x = vl_half(yl.x, fo_c.x, yr.x); ry.y = vl_half(yl.y, fo_c.y, yr.y);
     float2 d;
     d.x = cu * rx.x + cv * ry.x; d.y = cu * rx.y + cv * ry.y;
-    const CellRecF* C = cr + (size_t)j * nx + i;
     // downwind x-face
-    const FaceRecF* RXo = fxr + (size_t)j * (nx + 1) + i + fxo;
     float2 fup;
     fup.x = fo_c.x + sx * rx.x; fup.y = fo_c.y + sx * rx.y;
     const float2 Xout_x = face_x(RXo, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fup, d);
     // upwind x-face: flux leaving the x-upwind cell (or the wall)
-    const FaceRecF* RXi = fxr + (size_t)j * (nx + 1) + i + fxi;
     float2 Xin_x;
     if (RXi->wall != 0.f) {
       Xin_x = wall_in(RXi, u, v, dtf, gr);
@@ -1138,7 +1182,6 @@ __global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict
       Xin_x = face_x(RXi, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fuw, du);
     }
     // downwind y-face
-    const FaceRecF* RYo = fyr + (size_t)(sv > 0 ? j + 1 : j) * nx + i;
     fup.x = fo_c.x + sy * ry.x; fup.y = fo_c.y + sy * ry.y;
     const float2 Xout_y = face_x(RYo, yside, v, u, m_v, m_u, m_vv, m_uv, m_uu, m_vr2, m_ur2, fup, d);
     // Eq. 3 as an increment
@@ -1159,12 +1202,14 @@ __global__ void __launch_bounds__(128) k_walk(Params P, const float2* __restrict
       float2 o;
       o.x = fo_c.x + dh;
       o.y = fo_c.y + db;
-      fo[fcell(P, i, j) * nq + qq] = o;
+      *pw = o;
     }
-    if (j == jlast) break;
     Xin_y = Xout_y;
-    fo_p = fo_c; fo_c = fo_n;
-    fu_p = fu_c; fu_c = fu_n;
+    fo_p = fo_c; fo_c = fo_n; fo_n = fo_nn;
+    fu_p = fu_c; fu_c = fu_n; fu_n = fu_nn;
+    fd = fd_n; fuu = fuu_n;
+    po += fstep; pu += fstep; pd += fstep; puu += fstep; pw += fstep;
+    RXo += xstep; RXi += xstep; RYo += ystep; C += ystep;
   }
 }
 
