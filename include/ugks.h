@@ -126,7 +126,10 @@ ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double*
                                  const double* V, const double* T);
 
 /* Advance nsteps explicit UGKS steps (Eq. 2-4).  Enqueued on the stream; returns without
- * waiting.  Errors found later surface at the next synchronising call. */
+ * waiting.  Errors found later surface at the next synchronising call.  The first call
+ * captures the step's kernels into CUDA graphs (one per ping-pong parity, on a private
+ * stream) and later calls replay them; while tracing is on (ugks_profile) the kernels are
+ * launched directly instead. */
 ugks_status ugks_step(ugks_handle h, int nsteps);
 
 /* Wait for the stream and report a recorded numerical failure. */
@@ -156,6 +159,57 @@ ugks_status ugks_residual(ugks_handle h, double res[4]);
 ugks_status ugks_profile(ugks_handle h, int enable);
 ugks_status ugks_kernel_times(ugks_handle h, double* ms, long* launches);
 const char* ugks_kernel_name(int i);
+
+/* Device bytes ugks_create would allocate for cfg (0 if cfg is invalid). */
+size_t ugks_state_bytes(const ugks_config* cfg);
+
+/* ---- Batch of independent instances ------------------------------------------------
+ * Many independent channel solves stepped together (the FP32-f form only): every kernel
+ * of the step runs once per step for all active instances, as a persistent grid over a
+ * device-resident table of (instance, tile) work items, and one step of the whole batch
+ * is one CUDA graph replay.  Instances are admitted into free slots while the batch is in
+ * use (admission checks an HBM budget) and retired when done; the table and each
+ * instance's ping-pong parity live in device memory, so admission and retirement change
+ * data, not the captured graph.  Each instance's results are bitwise those of the same
+ * instance stepped alone with ugks_step (same kernels, same order of work). */
+typedef struct ugks_batch_ctx* ugks_batch;
+
+/* max_slots <= 256 instances at a time; hbm_budget: total state bytes of the admitted
+ * instances (0: no limit); cuda_stream: cudaStream_t or NULL. */
+ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_stream, ugks_batch* out);
+void        ugks_batch_destroy(ugks_batch b);
+const char* ugks_batch_last_error(ugks_batch b);
+size_t      ugks_batch_bytes_used(ugks_batch b);
+
+/* Admit one instance (cfg->precision must be UGKS_FP32F): allocates its state if it fits
+ * the budget and a slot is free, writes the slot to *slot.  UGKS_ENOMEM: no budget or slot
+ * left (nothing allocated); UGKS_EINVAL: bad cfg. */
+ugks_status ugks_batch_admit(ugks_batch b, const ugks_config* cfg, int* slot);
+
+/* Free a slot (waits for the batch's stream first). */
+ugks_status ugks_batch_retire(ugks_batch b, int slot);
+
+/* The instance in a slot, for the single-instance calls that move state and read results
+ * (ugks_init_maxwellian, ugks_set_state(_device), ugks_get_state(_device), ugks_moments,
+ * ugks_residual, ugks_sync).  Do not call ugks_step or ugks_destroy on it.  NULL if the
+ * slot is free. */
+ugks_handle ugks_batch_instance(ugks_batch b, int slot);
+
+/* Advance every active instance by nsteps steps (one graph replay each).  Enqueued. */
+ugks_status ugks_batch_step(ugks_batch b, int nsteps);
+
+/* Wait for the batch's stream; UGKS_ENUMERIC if any instance recorded a failure. */
+ugks_status ugks_batch_sync(ugks_batch b);
+
+/* Tile shape of the f-update walk (rows per tile) for one slot; and the autotuner: for
+ * each velocity-grid class present (nu*nv <= 576, <= 1600, <= 4096, larger) it times
+ * trial_steps batch steps with 16, 32, 64 and 128 rows and keeps the fastest for that
+ * class.  The tile shape does not change the arithmetic, so tuning steps are real steps
+ * of every active instance (each advances by 4 * (trial_steps + 1) per class present).
+ * *best_ms: time per batch step measured for the last class's chosen shape (may be NULL). */
+ugks_status ugks_batch_set_walk_rows(ugks_batch b, int slot, int rows);
+int         ugks_batch_get_walk_rows(ugks_batch b, int slot);
+ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms);
 
 /* One FP64 UGKS step on caller-owned device buffers that allocates no device memory.
  * For callers that cannot call cudaMalloc at all -- code running where the CUDA allocator

@@ -12,6 +12,7 @@
 
 #include "../../include/ugks.h"
 #include "ugks_kernels.cuh"
+#include "ugks_batch.cuh"
 
 using namespace ugks;
 
@@ -49,6 +50,9 @@ struct ugks_ctx {
   size_t bytes = 0;
   long steps_done = 0;
   std::string last_error;
+  // one captured graph per ping-pong parity of the step (replayed on `stream`)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
   // tracing: one set of UGKS_NKERNELS+1 events per profiled step
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -110,6 +114,28 @@ const char* validate(const ugks_config* c) {
   return nullptr;
 }
 
+// Device bytes ugks_create allocates for cfg (cudaMalloc sizes, without allocator rounding).
+size_t predict_bytes(const ugks_config* c) {
+  const size_t nx = c->nx, ny = c->ny, nq = (size_t)c->nu * c->nv, nc = nx * ny;
+  const bool f32 = c->precision == UGKS_FP32F;
+  const size_t t2 = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t fcells = (nx + 4) * (ny + 4), nwe = (nx + 2) * (ny + 2);
+  const size_t nfx = (nx + 1) * ny, nfy = nx * (ny + 1), nrb = (nc + 127) / 128;
+  size_t b = 2 * fcells * nq * t2 + 2 * 4 * sizeof(double) * nwe + sizeof(double) * kNSum * nwe;
+  b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : sizeof(FaceRec) * (nfx + nfy);
+  b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
+  b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
+  b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * 2 * (c->nu + c->nv);
+  if (f32) {
+    const size_t row_d = nx * nq * 2 * sizeof(double);
+    size_t want = (size_t)64 << 20;
+    if (want < row_d) want = row_d;
+    if (want > row_d * ny) want = row_d * ny;
+    b += want + sizeof(float2) * nq + sizeof(float) * (5 * (size_t)c->nv + 2 * (size_t)c->nu);
+  }
+  return b;
+}
+
 template <typename T>
 size_t smem_sums(int nv) {
   return kWarpsPerBlock * kNSum * sizeof(double) + 5 * (size_t)nv * sizeof(T);
@@ -147,10 +173,9 @@ cudaError_t mark(ugks_ctx* h, int k) {
 }
 
 template <typename T>
-cudaError_t launch_step(ugks_ctx* h) {
+cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   using T2 = typename Vec2<T>::type;
   const Params& P = h->P;
-  cudaStream_t st = h->stream;
   T2* fi = static_cast<T2*>(h->f[h->cur]);
   T2* fo = static_cast<T2*>(h->f[h->cur ^ 1]);
   double* Wi = h->W[h->cur];
@@ -177,7 +202,7 @@ cudaError_t launch_step(ugks_ctx* h) {
   if (sizeof(T) == 4) {
     const dim3 grid((P.nx + 3) / 4, (P.ny + kWalkRows - 1) / kWalkRows, h->nchunk_neg + h->nchunk_pos);
     k_walk<<<grid, 128, 0, st>>>(P, reinterpret_cast<const float2*>(fi), reinterpret_cast<float2*>(fo),
-                                 h->fxf, h->fyf, h->cellf, h->nchunk_neg);
+                                 h->fxf, h->fyf, h->cellf, h->nchunk_neg, kWalkRows);
   } else {
     k_update<T, T2, false>
         <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
@@ -745,6 +770,12 @@ void ugks_destroy(ugks_handle h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (int b = 0; b < 2; b++)
+    if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
+  if (h->cap_stream) {
+    cudaStreamSynchronize(h->cap_stream);
+    cudaStreamDestroy(h->cap_stream);
+  }
   delete h;
 }
 
@@ -802,10 +833,41 @@ ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double*
   return UGKS_OK;
 }
 
+// Capture one step per ping-pong parity into a graph (private capture stream; the graphs
+// are replayed on the handle's stream, which may be the legacy default stream).
+static cudaError_t build_graphs(ugks_ctx* h) {
+  cudaError_t e;
+  if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  const int cur0 = h->cur;
+  for (int par = 0; par < 2; par++) {
+    h->cur = par;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+    const cudaError_t el = h->prec == UGKS_FP64 ? launch_step<double>(h, h->cap_stream)
+                                                : launch_step<float>(h, h->cap_stream);
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) break;
+  }
+  h->cur = cur0;
+  return e;
+}
+
 ugks_status ugks_step(ugks_handle h, int nsteps) {
   if (!h || nsteps < 0) return fail(h, UGKS_EINVAL, "step: bad argument");
+  if (!h->profiling && !h->graph[1]) {
+    cudaError_t e = build_graphs(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step graph capture");
+  }
   for (int s = 0; s < nsteps; s++) {
-    cudaError_t e = h->prec == UGKS_FP64 ? launch_step<double>(h) : launch_step<float>(h);
+    cudaError_t e;
+    if (h->profiling)  // direct launches so that the tracing events sit between kernels
+      e = h->prec == UGKS_FP64 ? launch_step<double>(h, h->stream) : launch_step<float>(h, h->stream);
+    else
+      e = cudaGraphLaunch(h->graph[h->cur], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur ^= 1;
     h->steps_done++;
@@ -892,5 +954,310 @@ ugks_status ugks_kernel_times(ugks_handle h, double* ms, long* launches) {
 }
 
 const char* ugks_kernel_name(int i) { return (i >= 0 && i < UGKS_NKERNELS) ? kKernelNames[i] : ""; }
+
+}  // extern "C"
+
+// =====================================================================================
+// Batch of independent instances (FP32-f form)
+// =====================================================================================
+struct ugks_batch_ctx {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int max_slots = 0;
+  size_t budget = 0, used = 0;
+  std::vector<ugks_ctx*> ctx;       // per slot, nullptr when free
+  std::vector<int> walk_rows;       // per slot
+  SlotDev* d_slots = nullptr;
+  BatchWork* d_work = nullptr;
+  BatchWork h_work;
+  cudaGraphExec_t graph = nullptr;
+  int grid[kPhases + 1] = {0};
+  std::string last_error;
+};
+
+namespace {
+
+constexpr size_t kBatchSumsSmem = kWarpsPerBlock * kNSum * sizeof(double) + 5 * kMaxAxis * sizeof(float);
+
+ugks_status bfail(ugks_batch_ctx* b, ugks_status s, const std::string& m) {
+  if (b) b->last_error = m;
+  return s;
+}
+
+#define BCK(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return bfail(b, UGKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+SlotDev slot_desc(const ugks_ctx* h, int walk_rows) {
+  SlotDev S;
+  memset(&S, 0, sizeof S);
+  S.P = h->P;
+  S.f[0] = static_cast<float2*>(h->f[0]);
+  S.f[1] = static_cast<float2*>(h->f[1]);
+  S.W[0] = h->W[0];
+  S.W[1] = h->W[1];
+  S.sums = reinterpret_cast<float*>(h->sums);
+  S.fxf = h->fxf;
+  S.fyf = h->fyf;
+  S.cellf = h->cellf;
+  S.Fx = h->Fx;
+  S.Fy = h->Fy;
+  S.mt4 = h->mt4;
+  S.rpart = h->rpart;
+  S.err = h->err;
+  S.nwe = h->nwe;
+  S.nrblocks = h->nrblocks;
+  S.nchunk_neg = h->nchunk_neg;
+  S.nchunk_pos = h->nchunk_pos;
+  S.walk_rows = walk_rows;
+  S.cur = h->cur;
+  return S;
+}
+
+// Rebuild the work table of the active slots and upload it (stream-ordered).
+ugks_status upload_work(ugks_batch_ctx* b) {
+  BatchWork& w = b->h_work;
+  w.n = 0;
+  for (int p = 0; p < kPhases; p++) w.start[p][0] = 0;
+  for (int s = 0; s < b->max_slots; s++) {
+    if (!b->ctx[s]) continue;
+    const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s]);
+    const int a = w.n++;
+    w.slot[a] = s;
+    for (int p = 0; p < kPhases; p++) {
+      const long next = (long)w.start[p][a] + phase_blocks(S, p);
+      if (next > 0x7fffffffL) return bfail(b, UGKS_EINVAL, "batch too large for the work table");
+      w.start[p][a + 1] = (int)next;
+    }
+  }
+  BCK(cudaMemcpyAsync(b->d_work, &w, sizeof(BatchWork), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));  // w is host memory reused by the next update
+  return UGKS_OK;
+}
+
+ugks_status upload_slot(ugks_batch_ctx* b, int s) {
+  const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s]);
+  BCK(cudaMemcpyAsync(b->d_slots + s, &S, sizeof(SlotDev), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return UGKS_OK;
+}
+
+cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
+  kb_ghost_x<<<b->grid[0], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_ghost_y<<<b->grid[1], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_sums<<<b->grid[2], 128, kBatchSumsSmem, st>>>(b->d_slots, b->d_work);
+  kb_faces<<<b->grid[3], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_cells<<<b->grid[4], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_walk<<<b->grid[5], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_flip<<<1, 256, 0, st>>>(b->d_slots, b->d_work);
+  return cudaGetLastError();
+}
+
+cudaError_t capture_batch(ugks_batch_ctx* b) {
+  cudaError_t e;
+  if (!b->cap_stream && (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  cudaGraph_t g = nullptr;
+  if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  const cudaError_t el = launch_batch(b, b->cap_stream);
+  e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (el != cudaSuccess) e = el;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+int velocity_class(const ugks_config& c) {
+  const int nq = c.nu * c.nv;
+  return nq <= 576 ? 0 : (nq <= 1600 ? 1 : (nq <= 4096 ? 2 : 3));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ugks_state_bytes(const ugks_config* cfg) {
+  return validate(cfg) ? 0 : predict_bytes(cfg);
+}
+
+ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_stream, ugks_batch* out) {
+  if (!out || max_slots < 1 || max_slots > kMaxSlots) return UGKS_EINVAL;
+  *out = nullptr;
+  ugks_batch_ctx* b = new ugks_batch_ctx();
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->max_slots = max_slots;
+  b->budget = hbm_budget;
+  b->ctx.assign(max_slots, nullptr);
+  b->walk_rows.assign(max_slots, kWalkRows);
+  memset(&b->h_work, 0, sizeof(BatchWork));
+  cudaError_t e = cudaMalloc((void**)&b->d_slots, sizeof(SlotDev) * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, sizeof(BatchWork));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_work, 0, sizeof(BatchWork), b->stream);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem);
+  // persistent grids: resident blocks per SM x SMs
+  const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
+                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_walk};
+  for (int p = 0; p < kPhases && e == cudaSuccess; p++) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, p == 2 ? kBatchSumsSmem : 0);
+    b->grid[p] = (nb > 0 ? nb : 1) * sms;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "ugks_batch_create: %s\n", cudaGetErrorString(e));
+    ugks_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? UGKS_ENOMEM : UGKS_ECUDA;
+  }
+  *out = b;
+  return UGKS_OK;
+}
+
+void ugks_batch_destroy(ugks_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (ugks_ctx* h : b->ctx)
+    if (h) ugks_destroy(h);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) {
+    cudaStreamSynchronize(b->cap_stream);
+    cudaStreamDestroy(b->cap_stream);
+  }
+  if (b->d_slots) cudaFree(b->d_slots);
+  if (b->d_work) cudaFree(b->d_work);
+  delete b;
+}
+
+const char* ugks_batch_last_error(ugks_batch b) { return b ? b->last_error.c_str() : "null batch"; }
+
+size_t ugks_batch_bytes_used(ugks_batch b) { return b ? b->used : 0; }
+
+ugks_status ugks_batch_admit(ugks_batch b, const ugks_config* cfg, int* slot) {
+  if (!b || !cfg || !slot) return bfail(b, UGKS_EINVAL, "admit: NULL argument");
+  const char* bad = validate(cfg);
+  if (bad) return bfail(b, UGKS_EINVAL, std::string("admit: ") + bad);
+  if (cfg->precision != UGKS_FP32F) return bfail(b, UGKS_EINVAL, "admit: batch instances use UGKS_FP32F");
+  const size_t need = predict_bytes(cfg);
+  if (b->budget && b->used + need > b->budget) return bfail(b, UGKS_ENOMEM, "admit: over the HBM budget");
+  int s = -1;
+  for (int k = 0; k < b->max_slots; k++)
+    if (!b->ctx[k]) { s = k; break; }
+  if (s < 0) return bfail(b, UGKS_ENOMEM, "admit: no free slot");
+  ugks_ctx* h = nullptr;
+  const ugks_status st = ugks_create(cfg, b->stream, &h);
+  if (st) return bfail(b, st, "admit: instance allocation failed");
+  b->ctx[s] = h;
+  b->used += h->bytes;
+  int cls_rows = kWalkRows;
+  for (int k = 0; k < b->max_slots; k++)  // tuned tile of the same velocity class, if any
+    if (k != s && b->ctx[k] && velocity_class(b->ctx[k]->cfg) == velocity_class(*cfg)) cls_rows = b->walk_rows[k];
+  b->walk_rows[s] = cls_rows;
+  ugks_status r = upload_slot(b, s);
+  if (!r) r = upload_work(b);
+  if (r) return r;
+  *slot = s;
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_retire(ugks_batch b, int slot) {
+  if (!b || slot < 0 || slot >= b->max_slots || !b->ctx[slot]) return bfail(b, UGKS_EINVAL, "retire: bad slot");
+  BCK(cudaStreamSynchronize(b->stream));
+  b->used -= b->ctx[slot]->bytes;
+  ugks_destroy(b->ctx[slot]);
+  b->ctx[slot] = nullptr;
+  return upload_work(b);
+}
+
+ugks_handle ugks_batch_instance(ugks_batch b, int slot) {
+  if (!b || slot < 0 || slot >= b->max_slots) return nullptr;
+  return b->ctx[slot];
+}
+
+ugks_status ugks_batch_step(ugks_batch b, int nsteps) {
+  if (!b || nsteps < 0) return bfail(b, UGKS_EINVAL, "batch step: bad argument");
+  if (!b->graph) {
+    const cudaError_t e = capture_batch(b);
+    if (e != cudaSuccess) return bfail(b, UGKS_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  }
+  for (int k = 0; k < nsteps; k++) {
+    BCK(cudaGraphLaunch(b->graph, b->stream));
+    for (ugks_ctx* h : b->ctx)
+      if (h) { h->cur ^= 1; h->steps_done++; }
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_sync(ugks_batch b) {
+  if (!b) return UGKS_EINVAL;
+  BCK(cudaStreamSynchronize(b->stream));
+  for (ugks_ctx* h : b->ctx)
+    if (h) {
+      const ugks_status s = check_err(h);
+      if (s) return bfail(b, s, "numerical failure in an instance");
+    }
+  return UGKS_OK;
+}
+
+ugks_status ugks_batch_set_walk_rows(ugks_batch b, int slot, int rows) {
+  if (!b || slot < 0 || slot >= b->max_slots || !b->ctx[slot] || rows < 1) return bfail(b, UGKS_EINVAL, "bad tile");
+  b->walk_rows[slot] = rows;
+  ugks_status r = upload_slot(b, slot);
+  return r ? r : upload_work(b);
+}
+
+int ugks_batch_get_walk_rows(ugks_batch b, int slot) {
+  return (b && slot >= 0 && slot < b->max_slots && b->ctx[slot]) ? b->walk_rows[slot] : 0;
+}
+
+ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms) {
+  if (!b || trial_steps < 1) return bfail(b, UGKS_EINVAL, "tune: bad argument");
+  static const int cand[4] = {16, 32, 64, 128};
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float best_total = 0.f;
+  for (int cls = 0; cls < 4; cls++) {
+    bool any = false;
+    for (int s = 0; s < b->max_slots; s++) any |= b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls;
+    if (!any) continue;
+    int best = kWalkRows;
+    float best_t = 1e30f;
+    for (int c = 0; c < 4; c++) {
+      for (int s = 0; s < b->max_slots; s++)
+        if (b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls) {
+          b->walk_rows[s] = cand[c];
+          ugks_status r = upload_slot(b, s);
+          if (r) return r;
+        }
+      ugks_status r = upload_work(b);
+      if (r) return r;
+      r = ugks_batch_step(b, 1);  // warm-up of this shape
+      if (r) return r;
+      BCK(cudaEventRecord(e0, b->stream));
+      r = ugks_batch_step(b, trial_steps);
+      if (r) return r;
+      BCK(cudaEventRecord(e1, b->stream));
+      BCK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      BCK(cudaEventElapsedTime(&t, e0, e1));
+      if (t < best_t) { best_t = t; best = cand[c]; }
+    }
+    for (int s = 0; s < b->max_slots; s++)
+      if (b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls) {
+        b->walk_rows[s] = best;
+        ugks_status r = upload_slot(b, s);
+        if (r) return r;
+      }
+    best_total = best_t / trial_steps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms) *best_ms = best_total;
+  return upload_work(b);
+}
 
 }  // extern "C"

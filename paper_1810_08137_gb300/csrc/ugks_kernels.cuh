@@ -129,8 +129,8 @@ __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int 
 
 // x-sides, rows 0..ny-1; grid (ny, 4): blockIdx.y = side*2 + layer-1.
 template <typename T2>
-__global__ void k_ghost_x(Params P, T2* f, double* W, int nwe) {
-  const int j = blockIdx.x, side = blockIdx.y >> 1, l = (blockIdx.y & 1) + 1;
+__device__ __forceinline__ void ghost_x_body(const Params& P, T2* f, double* W, int nwe, int bx, int by) {
+  const int j = bx, side = by >> 1, l = (by & 1) + 1;
   const int kind = P.bc_kind[side];
   const int gi = side == 0 ? -l : P.nx - 1 + l;
   int si;
@@ -139,12 +139,16 @@ __global__ void k_ghost_x(Params P, T2* f, double* W, int nwe) {
   const int ai = side == 0 ? 0 : P.nx - 1;  // adjacent interior cell (pressure velocity source)
   fill_ghost_cell(P, f, W, nwe, gi, j, si, j, side, l == 1, kind == 2 ? ai : si, j);
 }
+template <typename T2>
+__global__ void k_ghost_x(Params P, T2* f, double* W, int nwe) {
+  ghost_x_body(P, f, W, nwe, blockIdx.x, blockIdx.y);
+}
 
 // y-sides over all columns -2..nx+1 (corners included, after the x-sides);
 // grid (nx+4, 4): blockIdx.y = side*2 + layer-1, side 0: S, 1: N.
 template <typename T2>
-__global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
-  const int i = (int)blockIdx.x - 2, side = 2 + (blockIdx.y >> 1), l = (blockIdx.y & 1) + 1;
+__device__ __forceinline__ void ghost_y_body(const Params& P, T2* f, double* W, int nwe, int bx, int by) {
+  const int i = bx - 2, side = 2 + (by >> 1), l = (by & 1) + 1;
   const int kind = P.bc_kind[side];
   const int gj = side == 2 ? -l : P.ny - 1 + l;
   int sj;
@@ -154,6 +158,10 @@ __global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
   const bool wcol = i >= -1 && i <= P.nx;
   const int wi = i < -1 ? -1 : (i > P.nx ? P.nx : i);
   fill_ghost_cell(P, f, W, nwe, i, gj, i, sj, side, l == 1 && wcol, wi, kind == 2 ? aj : sj);
+}
+template <typename T2>
+__global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
+  ghost_y_body(P, f, W, nwe, blockIdx.x, blockIdx.y);
 }
 
 // -------------------------------------------------------------------------------------
@@ -204,9 +212,8 @@ __device__ __forceinline__ void utab(const Params& P, int k, float& u, float& wu
 }
 
 template <typename T, typename T2>
-__global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
-                                              T* __restrict__ sums) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict__ f,
+                                          T* __restrict__ sums, unsigned char* smraw, int bx) {
   const int nv = P.nv, nu = P.nu, nq = P.nq;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
   __syncthreads();
 
   const int ncx = P.nx + 2;
-  const int cell = blockIdx.x * kWarpsPerBlock + warp;
+  const int cell = bx * kWarpsPerBlock + warp;
   if (cell >= ncx * (P.ny + 2)) return;
   const int i = cell % ncx - 1, j = cell / ncx - 1;
   const bool xg = i < 0 || i >= P.nx, yg = j < 0 || j >= P.ny;
@@ -337,6 +344,12 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
   T* out = sums + (size_t)cell * kNSum;
   out[lane] = wsum[lane];
   out[lane + 32] = wsum[lane + 32];
+}
+template <typename T, typename T2>
+__global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
+                                              T* __restrict__ sums) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  sums_body<T, T2>(P, f, sums, smraw, blockIdx.x);
 }
 
 // -------------------------------------------------------------------------------------
@@ -569,12 +582,12 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
 }
 
 template <typename S>
-__global__ void k_faces(Params P, const S* __restrict__ sums, const double* __restrict__ W,
-                        int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
-                        double* __restrict__ Fx, double* __restrict__ Fy,
-                        FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
-                        double* __restrict__ mt4) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void faces_body(const Params& P, const S* __restrict__ sums,
+                                           const double* __restrict__ W, int nwe,
+                                           FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
+                                           double* __restrict__ Fx, double* __restrict__ Fy,
+                                           FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
+                                           double* __restrict__ mt4, int t) {
   const int nx = P.nx, ny = P.ny;
   const int nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
   if (t >= nfx + nfy) return;
@@ -671,20 +684,28 @@ __global__ void k_faces(Params P, const S* __restrict__ sums, const double* __re
     for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
   }
 }
+template <typename S>
+__global__ void k_faces(Params P, const S* __restrict__ sums, const double* __restrict__ W,
+                        int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
+                        double* __restrict__ Fx, double* __restrict__ Fy,
+                        FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
+                        double* __restrict__ mt4) {
+  faces_body<S>(P, sums, W, nwe, fxr, fyr, Fx, Fy, fxf, fyf, mt4, blockIdx.x * blockDim.x + threadIdx.x);
+}
 
 // -------------------------------------------------------------------------------------
 // Eq. 4 per cell, plus g^n, g^{n+1}, tau^n, tau^{n+1} for Eq. 3, residual partials and
 // the numerical-failure flag.
 // -------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_cells(Params P, const double* __restrict__ Win,
-                                               double* __restrict__ Wout, int nwe,
-                                               const double* __restrict__ Fx,
-                                               const double* __restrict__ Fy,
-                                               CellRec* __restrict__ cr, double* __restrict__ rpart,
-                                               int* __restrict__ err, CellRecF* __restrict__ crf,
-                                               const double* __restrict__ mt4) {
-  __shared__ double red[8][128];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cells_body(const Params& P, const double* __restrict__ Win,
+                                           double* __restrict__ Wout, int nwe,
+                                           const double* __restrict__ Fx,
+                                           const double* __restrict__ Fy, CellRec* __restrict__ cr,
+                                           double* __restrict__ rpart, int* __restrict__ err,
+                                           CellRecF* __restrict__ crf,
+                                           const double* __restrict__ mt4, double (*red)[128],
+                                           int bx) {
+  const int c = bx * blockDim.x + threadIdx.x;
   const int nx = P.nx, nc = P.nx * P.ny;
   double d2[4] = {0, 0, 0, 0}, am[4] = {0, 0, 0, 0};
   if (c < nc) {
@@ -744,7 +765,17 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
       }
     __syncthreads();
   }
-  if (threadIdx.x < 8) rpart[(size_t)blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 8) rpart[(size_t)bx * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+__global__ void __launch_bounds__(128) k_cells(Params P, const double* __restrict__ Win,
+                                               double* __restrict__ Wout, int nwe,
+                                               const double* __restrict__ Fx,
+                                               const double* __restrict__ Fy,
+                                               CellRec* __restrict__ cr, double* __restrict__ rpart,
+                                               int* __restrict__ err, CellRecF* __restrict__ crf,
+                                               const double* __restrict__ mt4) {
+  __shared__ double red[8][128];
+  cells_body(P, Win, Wout, nwe, Fx, Fy, cr, rpart, err, crf, mt4, red, blockIdx.x);
 }
 
 // -------------------------------------------------------------------------------------
@@ -1009,7 +1040,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 // z = velocity chunks of 32 (v < 0 chunks first, then v >= 0).  Lane = velocity.
 // Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + df.
 // -------------------------------------------------------------------------------------
-constexpr int kWalkRows = 64;
+constexpr int kWalkRows = 64;  // default rows per walk tile
 
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
 
@@ -1057,16 +1088,16 @@ __device__ __forceinline__ float2 wall_in(const FaceRecF* R, float un, float ut,
   return X;
 }
 
-__global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restrict__ f,
-                                              float2* __restrict__ fo,
-                                              const FaceRecF* __restrict__ fxr,
-                                              const FaceRecF* __restrict__ fyr,
-                                              const CellRecF* __restrict__ cr, int nchunk_neg) {
+__device__ __forceinline__ void walk_body(const Params& P, const float2* __restrict__ f,
+                                          float2* __restrict__ fo, const FaceRecF* __restrict__ fxr,
+                                          const FaceRecF* __restrict__ fyr,
+                                          const CellRecF* __restrict__ cr, int nchunk_neg,
+                                          int walk_rows, int bx, int by, int bz) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nx = P.nx, ny = P.ny, nu = P.nu, nq = P.nq;
-  const int i = blockIdx.x * 4 + warp;
+  const int i = bx * 4 + warp;
   if (i >= nx) return;
-  const int chunk = blockIdx.z;
+  const int chunk = bz;
   const bool vpos = chunk >= nchunk_neg;
   const int nq_neg = P.m_neg * nu;
   const int q = vpos ? nq_neg + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
@@ -1090,8 +1121,8 @@ __global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restr
   const int fxo = su > 0 ? 1 : 0;                       // downwind x-face offset i + fxo
   const int fxi = su > 0 ? 0 : 1;                       // upwind x-face offset
 
-  const int j0 = blockIdx.y * kWalkRows;
-  const int j1 = min(j0 + kWalkRows, ny);
+  const int j0 = by * walk_rows;
+  const int j1 = min(j0 + walk_rows, ny);
   const int jfirst = sv > 0 ? j0 : j1 - 1, jlast = sv > 0 ? j1 - 1 : j0;
   const long rs = (long)P.ex * nq;
   const float2* col = f + fcell(P, i, 0) * nq + qq;      // own column, row 0
@@ -1211,6 +1242,15 @@ __global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restr
     po += fstep; pu += fstep; pd += fstep; puu += fstep; pw += fstep;
     RXo += xstep; RXi += xstep; RYo += ystep; C += ystep;
   }
+}
+
+__global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restrict__ f,
+                                                 float2* __restrict__ fo,
+                                                 const FaceRecF* __restrict__ fxr,
+                                                 const FaceRecF* __restrict__ fyr,
+                                                 const CellRecF* __restrict__ cr, int nchunk_neg,
+                                                 int walk_rows) {
+  walk_body(P, f, fo, fxr, fyr, cr, nchunk_neg, walk_rows, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace ugks

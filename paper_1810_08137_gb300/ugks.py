@@ -22,7 +22,11 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_device_bytes", "ugks_set_state", "ugks_set_state_device",
            "ugks_init_maxwellian", "ugks_step", "ugks_sync", "ugks_moments", "ugks_get_state",
            "ugks_get_state_device", "ugks_residual", "ugks_profile", "ugks_kernel_times",
-           "ugks_kernel_name", "ugks_step_noalloc")
+           "ugks_kernel_name", "ugks_step_noalloc", "ugks_state_bytes", "ugks_batch_create",
+           "ugks_batch_destroy", "ugks_batch_last_error", "ugks_batch_bytes_used",
+           "ugks_batch_admit", "ugks_batch_retire", "ugks_batch_instance", "ugks_batch_step",
+           "ugks_batch_sync", "ugks_batch_set_walk_rows", "ugks_batch_get_walk_rows",
+           "ugks_batch_tune")
 NKERNELS = 6
 
 
@@ -85,6 +89,24 @@ def lib(build_if_missing: bool = True):
         L.ugks_kernel_name.restype = C.c_char_p
         L.ugks_step_noalloc.argtypes = [C.POINTER(_Config), C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
+        L.ugks_state_bytes.argtypes = [C.POINTER(_Config)]
+        L.ugks_state_bytes.restype = C.c_size_t
+        L.ugks_batch_create.argtypes = [C.c_int, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.ugks_batch_destroy.argtypes = [C.c_void_p]
+        L.ugks_batch_destroy.restype = None
+        L.ugks_batch_last_error.argtypes = [C.c_void_p]
+        L.ugks_batch_last_error.restype = C.c_char_p
+        L.ugks_batch_bytes_used.argtypes = [C.c_void_p]
+        L.ugks_batch_bytes_used.restype = C.c_size_t
+        L.ugks_batch_admit.argtypes = [C.c_void_p, C.POINTER(_Config), C.POINTER(C.c_int)]
+        L.ugks_batch_retire.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_instance.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_instance.restype = C.c_void_p
+        L.ugks_batch_step.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_sync.argtypes = [C.c_void_p]
+        L.ugks_batch_set_walk_rows.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.ugks_batch_get_walk_rows.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_tune.argtypes = [C.c_void_p, C.c_int, _P]
         _lib = L
     return _lib
 
@@ -120,28 +142,37 @@ def _dptr(x) -> int:
     return x.data_ptr()
 
 
+def state_bytes(cfg, precision: int = FP64) -> int:
+    """Device bytes ugks_create allocates for cfg."""
+    return int(lib().ugks_state_bytes(C.byref(to_c_config(cfg, precision))))
+
+
 class Solver:
     """One UGKS instance on the GPU (ugks_create ... ugks_destroy)."""
 
-    def __init__(self, cfg, precision: int = FP64, stream=None):
+    def __init__(self, cfg, precision: int = FP64, stream=None, _handle=None):
         self.cfg = cfg
         self.precision = precision
         self._L = lib()
+        self.nc, self.nq = cfg.nx * cfg.ny, cfg.nu * cfg.nv
+        self._owned = _handle is None
+        if _handle is not None:
+            self._h = C.c_void_p(_handle)
+            return
         self._h = C.c_void_p()
         c = to_c_config(cfg, precision)
         st = self._L.ugks_create(C.byref(c), C.c_void_p(stream or 0), C.byref(self._h))
         if st:
             raise UGKSError(st, "ugks_create failed (see stderr)")
-        self.nc, self.nq = cfg.nx * cfg.ny, cfg.nu * cfg.nv
 
     def _check(self, st: int):
         if st:
             raise UGKSError(st, self._L.ugks_last_error(self._h).decode())
 
     def close(self):
-        if self._h:
+        if self._h and self._owned:
             self._L.ugks_destroy(self._h)
-            self._h = C.c_void_p()
+        self._h = C.c_void_p()
 
     def __enter__(self):
         return self
@@ -228,3 +259,76 @@ def step_noalloc(cfg, f_in, W_in, f_out, W_out, stream=None) -> None:
                                  C.c_void_p(stream or 0))
     if st:
         raise UGKSError(st, "ugks_step_noalloc failed (see stderr)")
+
+
+class Batch:
+    """Independent FP32-f instances stepped together (ugks_batch_*)."""
+
+    def __init__(self, max_slots: int, hbm_budget: int = 0, stream=None):
+        self._L = lib()
+        self._b = C.c_void_p()
+        st = self._L.ugks_batch_create(int(max_slots), C.c_size_t(int(hbm_budget)),
+                                       C.c_void_p(stream or 0), C.byref(self._b))
+        if st:
+            raise UGKSError(st, "ugks_batch_create failed (see stderr)")
+        self.cfgs = {}
+
+    def _check(self, st: int):
+        if st:
+            raise UGKSError(st, self._L.ugks_batch_last_error(self._b).decode())
+
+    def close(self):
+        if self._b:
+            self._L.ugks_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def bytes_used(self) -> int:
+        return int(self._L.ugks_batch_bytes_used(self._b))
+
+    def admit(self, cfg) -> int:
+        slot = C.c_int(-1)
+        self._check(self._L.ugks_batch_admit(self._b, C.byref(to_c_config(cfg, FP32F)),
+                                             C.byref(slot)))
+        self.cfgs[slot.value] = cfg
+        return slot.value
+
+    def retire(self, slot: int):
+        self._check(self._L.ugks_batch_retire(self._b, int(slot)))
+        self.cfgs.pop(slot, None)
+
+    def instance(self, slot: int) -> Solver:
+        """View of a slot's instance (state I/O and results; not owned, do not step)."""
+        h = self._L.ugks_batch_instance(self._b, int(slot))
+        if not h:
+            raise UGKSError(1, f"slot {slot} is free")
+        return Solver(self.cfgs[slot], FP32F, _handle=h)
+
+    def step(self, n: int = 1):
+        self._check(self._L.ugks_batch_step(self._b, int(n)))
+
+    def sync(self):
+        self._check(self._L.ugks_batch_sync(self._b))
+
+    def set_walk_rows(self, slot: int, rows: int):
+        self._check(self._L.ugks_batch_set_walk_rows(self._b, int(slot), int(rows)))
+
+    def walk_rows(self, slot: int) -> int:
+        return int(self._L.ugks_batch_get_walk_rows(self._b, int(slot)))
+
+    def tune(self, trial_steps: int = 3) -> float:
+        ms = C.c_double()
+        self._check(self._L.ugks_batch_tune(self._b, int(trial_steps), C.byref(ms)))
+        return ms.value

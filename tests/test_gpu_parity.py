@@ -276,3 +276,40 @@ def test_full_size_800x400_sampled(U, oracle, prec, tol):
     err = np.max(np.abs(Wg - Wo), axis=0) / scale
     assert np.all(err <= tol), err
     assert np.max(np.abs(f1[ids] - fo)) / np.max(np.abs(fo)) <= max(tol, 1e-12) * 10
+
+
+def test_graph_replay_matches_direct_launches(U, oracle):
+    """ugks_step replays captured graphs; with tracing on it launches the kernels directly.
+    Both orders of work are the same, so the results must be bitwise identical."""
+    cfg = CASES["channel_11x6_v7_hotwall"]()
+    f, W = random_state(oracle, cfg, 77)
+    out = []
+    for prof in (False, True):
+        for prec in (U.FP64, U.FP32F):
+            with U.Solver(cfg, prec) as s:
+                s.set_state(f, W)
+                if prof:
+                    s.profile(True)
+                s.step(3)
+                out.append(s.get_state())
+    for a, b in ((0, 2), (1, 3)):
+        assert np.array_equal(out[a][0], out[b][0]) and np.array_equal(out[a][1], out[b][1])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, FP32_TOL)])
+def test_large_velocity_space(U, oracle, prec, tol):
+    """Velocity domain [-20,20]^2 (thermal speed small against the range, the paper's
+    particle-like regime), 51^2 velocities (two u chunks of 32), Kn 0.01, inlet rho 1.05:
+    200 steps from the seeded Maxwellian on a 12x6 channel, the stated tolerances."""
+    cfg = I.workload_large_velocity(51).replace(nx=12, ny=6)
+    rho, Uf, Vf, T = I.initial_prim(cfg, I.seed_for(3, 51))
+    f0, W0 = oracle.init_maxwellian(cfg, rho, Uf, Vf, T)
+    fr, Wr = oracle.step(cfg, f0, W0, 200)
+    with U.Solver(cfg, prec) as s:
+        s.init_maxwellian(rho, Uf, Vf, T)
+        s.step(200)
+        fg, Wg = s.get_state()
+    err = rel_fields(Wg, Wr)
+    print(f"large velocity space prec {prec}: {err}")
+    assert np.all(err <= tol), err
+    assert rel_f(fg, fr) <= 10 * tol
