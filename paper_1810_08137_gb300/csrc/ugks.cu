@@ -38,6 +38,11 @@ struct ugks_ctx {
   CellRecF* cellf = nullptr;
   double* mt4 = nullptr;     // Mt4 per face (x faces then y faces)
   int nchunk_neg = 0, nchunk_pos = 0;
+  // FP32 form: the step runs the batch kernels over a one-instance table, so an instance
+  // stepped alone executes exactly the code it executes inside a batch
+  SlotDev* d_slot = nullptr;
+  BatchWork* d_work = nullptr;
+  int grid1[kPhases] = {0};
   double* rpart = nullptr;
   int nrblocks = 0;
   int* err = nullptr;
@@ -132,6 +137,7 @@ size_t predict_bytes(const ugks_config* c) {
     if (want < row_d) want = row_d;
     if (want > row_d * ny) want = row_d * ny;
     b += want + sizeof(float2) * nq + sizeof(float) * (5 * (size_t)c->nv + 2 * (size_t)c->nu);
+    b += sizeof(SlotDev) + sizeof(BatchWork);
   }
   return b;
 }
@@ -172,8 +178,12 @@ cudaError_t mark(ugks_ctx* h, int k) {
   return cudaEventRecord(h->events[idx], h->stream);
 }
 
+cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st);
+cudaError_t setup_single_f32(ugks_ctx* h);
+
 template <typename T>
 cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
+  if (sizeof(T) == 4) return launch_step_f32(h, st);
   using T2 = typename Vec2<T>::type;
   const Params& P = h->P;
   T2* fi = static_cast<T2*>(h->f[h->cur]);
@@ -203,7 +213,7 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
     const dim3 grid((P.nx + 3) / 4, (P.ny + kWalkRows - 1) / kWalkRows, h->nchunk_neg + h->nchunk_pos);
     k_walk<<<grid, 128, 0, st>>>(P, reinterpret_cast<const float2*>(fi), reinterpret_cast<float2*>(fo),
                                  h->fxf, h->fyf, h->cellf, h->nchunk_neg, kWalkRows);
-  } else {
+  } else {  // FP64 form
     k_update<T, T2, false>
         <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
             P, fi, fo, h->fxr, h->fyr, h->cells);
@@ -601,6 +611,11 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
   P.omega_half = om == 0.5;
+  P.f_tdx = (float)(2.0 / P.dx);
+  P.f_tdy = (float)(2.0 / P.dy);
+  P.f_idx = (float)(1.0 / P.dx);
+  P.f_idy = (float)(1.0 / P.dy);
+  P.f_dt = (float)P.dt;
   for (int s = 0; s < 4; s++) {
     P.bc_kind[s] = cfg->bc[s].kind;
     P.bc_rho[s] = cfg->bc[s].rho;
@@ -749,7 +764,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
     if ((r = h->prec == UGKS_FP64 ? set_smem_limits<double>(P.nv) : set_smem_limits<float>(P.nv)) != cudaSuccess)
       return r;
-    return cudaStreamSynchronize(h->stream);
+    if ((r = cudaStreamSynchronize(h->stream)) != cudaSuccess) return r;
+    return h->prec == UGKS_FP32F ? setup_single_f32(h) : cudaSuccess;
   };
   e = setup();
   if (e != cudaSuccess) {
@@ -765,7 +781,7 @@ void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->fxf, h->fyf,
-                  h->cellf, h->mt4, h->ftab};
+                  h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1052,6 +1068,54 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
   kb_cells<<<b->grid[4], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_walk<<<b->grid[5], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_flip<<<1, 256, 0, st>>>(b->d_slots, b->d_work);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_single_f32(ugks_ctx* h) {
+  cudaError_t e = cudaMalloc((void**)&h->d_slot, sizeof(SlotDev));
+  if (e != cudaSuccess) return e;
+  h->bytes += sizeof(SlotDev);
+  if ((e = cudaMalloc((void**)&h->d_work, sizeof(BatchWork))) != cudaSuccess) return e;
+  h->bytes += sizeof(BatchWork);
+  const SlotDev S = slot_desc(h, kWalkRows);
+  BatchWork w;
+  memset(&w, 0, sizeof w);
+  w.n = 1;
+  w.slot[0] = 0;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
+                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_walk};
+  for (int p = 0; p < kPhases; p++) {
+    w.start[p][1] = phase_blocks(S, p);
+    int nb = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, p == 2 ? kBatchSumsSmem : 0)) != cudaSuccess)
+      return e;
+    const int cap = (nb > 0 ? nb : 1) * sms;
+    h->grid1[p] = w.start[p][1] < cap ? (w.start[p][1] > 0 ? w.start[p][1] : 1) : cap;
+  }
+  if ((e = cudaMemcpy(h->d_slot, &S, sizeof(SlotDev), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  return cudaMemcpy(h->d_work, &w, sizeof(BatchWork), cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st) {
+  cudaError_t r;
+  if ((r = mark(h, 0)) != cudaSuccess) return r;
+  kb_ghost_x<<<h->grid1[0], 128, 0, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 1)) != cudaSuccess) return r;
+  kb_ghost_y<<<h->grid1[1], 128, 0, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 2)) != cudaSuccess) return r;
+  kb_sums<<<h->grid1[2], 128, kBatchSumsSmem, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 3)) != cudaSuccess) return r;
+  kb_faces<<<h->grid1[3], 128, 0, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 4)) != cudaSuccess) return r;
+  kb_cells<<<h->grid1[4], 128, 0, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 5)) != cudaSuccess) return r;
+  kb_walk<<<h->grid1[5], 128, 0, st>>>(h->d_slot, h->d_work);
+  kb_flip<<<1, 32, 0, st>>>(h->d_slot, h->d_work);
+  if ((r = mark(h, 6)) != cudaSuccess) return r;
+  if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
 }
 

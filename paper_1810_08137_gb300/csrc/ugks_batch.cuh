@@ -82,7 +82,7 @@ __global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* _
   }
 }
 
-__global__ void __launch_bounds__(128) kb_sums(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 6) kb_sums(const SlotDev* __restrict__ slots,
                                                const BatchWork* __restrict__ wk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int total = wk->start[2][wk->n];

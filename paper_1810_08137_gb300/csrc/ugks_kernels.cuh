@@ -241,7 +241,9 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
 
   const T2* fc = f + fcell(P, i, j) * nq;
   const size_t rs = (size_t)P.ex * nq;
-  const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy);
+  T tdx, tdy;
+  if (sizeof(T) == 4) { tdx = (T)P.f_tdx; tdy = (T)P.f_tdy; }
+  else { tdx = T(2.0 / P.dx); tdy = T(2.0 / P.dy); }
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
     const int k = k0 + lane;
@@ -419,12 +421,12 @@ __device__ void apsi_mom(const double* Mu, const double* Mv, double X2, double X
 // Micro-slope solve <psi (a . psi)> = s for the normalised Maxwellian (U, V, lam), closed
 // form obtained by centring the moments.
 __device__ void micro_slope(double U, double V, double lam, int K, const double* s, double* a) {
-  const double Kp2 = K + 2.0;
-  const double a4 = 4.0 * lam * lam / Kp2 *
-                    (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - Kp2 / (2.0 * lam)));
+  // q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass
+  const double Kp2 = K + 2.0, q = Kp2 * (0.25 / lam);
+  const double a4 = lam / q * (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - 2.0 * q));
   const double a3 = 2.0 * lam * (s[2] - V * s[0]) - V * a4;
   const double a2 = 2.0 * lam * (s[1] - U * s[0]) - U * a4;
-  const double a1 = s[0] - U * a2 - V * a3 - a4 * (0.5 * (U * U + V * V) + Kp2 / (4.0 * lam));
+  const double a1 = s[0] - U * a2 - V * a3 - a4 * (0.5 * (U * U + V * V) + q);
   a[0] = a1;
   a[1] = a2;
   a[2] = a3;
@@ -504,24 +506,25 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
                           double* F, FaceRec& R, FaceRecF* RF) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
-  const double rho = W0[0], U = W0[1] / rho, V = W0[2] / rho;
-  const double lam = (K + 2) * rho / (4.0 * (W0[3] - 0.5 * rho * (U * U + V * V)));
+  const double rho = W0[0], irho = 1.0 / rho, U = W0[1] * irho, V = W0[2] * irho;
+  const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) / ((K + 2) * rho);  // 1/(4 lam)
+  const double lam = 0.25 / ilam4;
   double Mu[7], Mup[7], Mun[7], Mv[7];
   gauss_moments7(U, lam, Mu, Mup, Mun);
   gauss_moments7_full(V, lam, Mv);
-  const double X2 = K / (2.0 * lam), X4 = (K * K + 2.0 * K) / (4.0 * lam * lam);
+  const double X2 = 2.0 * K * ilam4, X4 = (K * K + 2.0 * K) * 4.0 * ilam4 * ilam4;
   // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5
   const double tau = collision_time(P, rho, lam);
   double Mt[5];
   time_weights(P.dt, tau, Mt);
   // S4: micro slopes
-  const double inv = 2.0 / (rho * delta);
+  const double inv = 2.0 * irho / delta;
   double sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
 #pragma unroll
   for (int c = 0; c < 4; c++) {
     sL[c] = (W0[c] - WL[c]) * inv;
     sR[c] = (WR[c] - W0[c]) * inv;
-    sT[c] = St[c] / rho;
+    sT[c] = St[c] * irho;
   }
   micro_slope(U, V, lam, K, sL, aL);
   micro_slope(U, V, lam, K, sR, aR);
@@ -1105,35 +1108,31 @@ __device__ __forceinline__ void walk_body(const Params& P, const float2* __restr
   const bool act = q < qend;
   const int qq = act ? q : qend - 1;
   const int k = qq % nu, m = qq / nu;
-  const float u = (float)P.u[k], v = (float)P.v[m];
+  const float u = P.uwf[k], v = P.mvf[4 * P.nv + m];
   const int su = u > 0.f ? 1 : -1;
   const int sv = vpos ? 1 : -1;
   const float r2 = u * u + v * v;
   const float m_u = u, m_v = v, m_uu = u * u, m_uv = u * v, m_vv = v * v, m_ur2 = u * r2, m_vr2 = v * r2;
-  const float cu = u * (float)(2.0 / P.dx), cv = v * (float)(2.0 / P.dy);
-  const float au = fabsf(u) * (float)(1.0 / P.dx), av = fabsf(v) * (float)(1.0 / P.dy);
-  const float dtf = (float)P.dt;
+  const float cu = u * P.f_tdx, cv = v * P.f_tdy;
+  const float au = fabsf(u) * P.f_idx, av = fabsf(v) * P.f_idy;
+  const float dtf = P.f_dt;
   const float2 gr = __ldg(static_cast<const float2*>(P.gref) + qq);
   const int xside = u > 0.f ? 0 : 1, yside = vpos ? 0 : 1;
-  const int iu = i - su, iuu = i - 2 * su, id = i + su;
+  const int iu = i - su;
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
   const bool zu = (iu < 0 && pW) || (iu >= nx && pE);  // x-upwind cell is a pressure ghost
   const int fxo = su > 0 ? 1 : 0;                       // downwind x-face offset i + fxo
-  const int fxi = su > 0 ? 0 : 1;                       // upwind x-face offset
 
   const int j0 = by * walk_rows;
   const int j1 = min(j0 + walk_rows, ny);
   const int jfirst = sv > 0 ? j0 : j1 - 1, jlast = sv > 0 ? j1 - 1 : j0;
   const long rs = (long)P.ex * nq;
   const float2* col = f + fcell(P, i, 0) * nq + qq;      // own column, row 0
-  const float2* colu = f + fcell(P, iu, 0) * nq + qq;    // x-upwind column
-  const float2* cold = f + fcell(P, id, 0) * nq + qq;    // x-downwind column
-  const float2* coluu = f + fcell(P, iuu, 0) * nq + qq;  // far x-upwind column
 
   // prologue: downwind y-face flux of the halo cell (i, jp), jp = jfirst - sv
   const int jp = jfirst - sv;
   float2 fo_p = ld2(col + (long)jp * rs), fo_c = ld2(col + (long)jfirst * rs);
-  float2 fu_p = ld2(colu + (long)jp * rs), fu_c = ld2(colu + (long)jfirst * rs);
+  float2 fu_p = ld2(col - su * nq + (long)jp * rs), fu_c = ld2(col - su * nq + (long)jfirst * rs);
   float2 Xin_y;
   {
     const int yface = (sv > 0 ? jfirst : jp) * nx + i;  // face between jp and jfirst
@@ -1160,30 +1159,28 @@ __device__ __forceinline__ void walk_body(const Params& P, const float2* __restr
   }
 
   const float sx = (float)su, sy = (float)sv;
-  // row-walk pointers, bumped by one row per step; f loads are issued one step ahead
-  const long fstep = sv * rs;
+  // row-walk state: one f pointer (own column) with the neighbour columns at a per-lane
+  // offset, one x-face record pointer (the upwind face is su records before the downwind
+  // one), 32-bit strides; f loads are issued one step ahead
+  const int xo = su * nq;                                  // own -> x-downwind column
+  const int fstep = sv * (int)rs;
   const float2* po = col + (long)jfirst * rs;
-  const float2* pu = colu + (long)jfirst * rs;
-  const float2* pd = cold + (long)jfirst * rs;
-  const float2* puu = coluu + (long)jfirst * rs;
   float2* pw = fo + fcell(P, i, jfirst) * nq + qq;
-  const long xstep = sv * (long)(nx + 1), ystep = sv * (long)nx;
+  const int xstep = sv * (nx + 1), ystep = sv * nx;
   const FaceRecF* RXo = fxr + (size_t)jfirst * (nx + 1) + i + fxo;
-  const FaceRecF* RXi = fxr + (size_t)jfirst * (nx + 1) + i + fxi;
   const FaceRecF* RYo = fyr + (size_t)(sv > 0 ? jfirst + 1 : jfirst) * nx + i;
   const CellRecF* C = cr + (size_t)jfirst * nx + i;
-  float2 fo_n = ld2(po + fstep), fu_n = ld2(pu + fstep), fd = ld2(pd), fuu = ld2(puu);
+  float2 fo_n = ld2(po + fstep), fu_n = ld2(po - xo + fstep), fd = ld2(po + xo), fuu = ld2(po - 2 * xo);
   const int nsteps = (jlast - jfirst) * sv + 1;
   for (int s = 0; s < nsteps; s++) {
     float2 fo_nn = fo_n, fu_nn = fu_n, fd_n = fd, fuu_n = fuu;
     if (s + 1 < nsteps) {
       fo_nn = ld2(po + 2 * fstep);
-      fu_nn = ld2(pu + 2 * fstep);
-      fd_n = ld2(pd + fstep);
-      fuu_n = ld2(puu + fstep);
+      fu_nn = ld2(po - xo + 2 * fstep);
+      fd_n = ld2(po + xo + fstep);
+      fuu_n = ld2(po - 2 * xo + fstep);
     }
-    // own slopes (+x, +y); the x difference towards the upwind column is shared with the
-    // upwind cell's slope
+    // own slopes (+x, +y)
     const float2 xl = su > 0 ? fu_c : fd, xr = su > 0 ? fd : fu_c;
     const float2 yl = sv > 0 ? fo_p : fo_n, yr = sv > 0 ? fo_n : fo_p;
     float2 rx, ry;
@@ -1196,6 +1193,7 @@ __device__ __forceinline__ void walk_body(const Params& P, const float2* __restr
     fup.x = fo_c.x + sx * rx.x; fup.y = fo_c.y + sx * rx.y;
     const float2 Xout_x = face_x(RXo, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fup, d);
     // upwind x-face: flux leaving the x-upwind cell (or the wall)
+    const FaceRecF* RXi = RXo - su;
     float2 Xin_x;
     if (RXi->wall != 0.f) {
       Xin_x = wall_in(RXi, u, v, dtf, gr);
@@ -1239,8 +1237,8 @@ __device__ __forceinline__ void walk_body(const Params& P, const float2* __restr
     fo_p = fo_c; fo_c = fo_n; fo_n = fo_nn;
     fu_p = fu_c; fu_c = fu_n; fu_n = fu_nn;
     fd = fd_n; fuu = fuu_n;
-    po += fstep; pu += fstep; pd += fstep; puu += fstep; pw += fstep;
-    RXo += xstep; RXi += xstep; RYo += ystep; C += ystep;
+    po += fstep; pw += fstep;
+    RXo += xstep; RYo += ystep; C += ystep;
   }
 }
 
