@@ -161,6 +161,61 @@ def cpu_baseline(cfg, prim, budget_s=20.0):
                       f"OpenMP over faces and cells"}
 
 
+def batch_bench(ugks, torch, stream, steps, warmup):
+    """Uneven batch: 64 channel instances drawn log-uniform (meshes 50x25..400x200,
+    16^2..64^2 velocities, Kn 1e-3..1, inlet rho 1.05..1.5), FP32-f, stepped together;
+    tile shapes from the autotuner; throughput over all instances."""
+    cfgs = I.workload_batch(64)
+    B = ugks.Batch(64, 150 * 2**30, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    slots = []
+    for k, c in enumerate(cfgs):
+        s = B.admit(c)
+        B.instance(s).init_maxwellian(*I.initial_prim(c, I.seed_for(4, k)))
+        slots.append(s)
+    B.sync()
+    t_admit = time.perf_counter() - t0
+    tuned_ms = B.tune(2)
+    B.step(warmup)
+    B.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    B.sync()
+    vc = sum(c.vc for c in cfgs)
+    rows = sorted({B.walk_rows(s) for s in slots})
+    out = {"workload": "batch64: meshes 50x25..400x200, 16^2..64^2 velocities, Kn 1e-3..1, "
+                       "inlet rho 1.05..1.5 (log-uniform draws, seeded)",
+           "instances": len(cfgs), "vc_per_step": vc, "value": vc * steps / (ms * 1e-3),
+           "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "precision": "fp32f",
+           "tuned_walk_rows": rows, "tuned_ms_per_step": tuned_ms,
+           "admit_s": t_admit, "device_bytes": B.bytes_used, "launches_per_step": 7}
+    B.close()
+    return out
+
+
+def serve_bench(ugks, stream, n_req=24):
+    """Poisson arrivals (20 req/s) of channel solves drawn as in the batch with meshes and
+    velocity grids scaled down (nx 20..50, 16^2..32^2) so each reaches a residual of 1e-6
+    in seconds; 150 GB HBM budget; continuous batching."""
+    from paper_1810_08137_gb300 import serve
+    cfgs, arr, prims = I.workload_serving(n_req)
+    reqs = serve.make_requests(cfgs, arr, prims)
+    srv = serve.gpu_server(150 * 2**30, 64, stream=stream.cuda_stream, tol=1e-6,
+                           max_steps=20000, check_every=50)
+    st = srv.run(reqs)
+    srv.batch_handle.close()
+    s = st.summary()
+    s.update({"workload": f"{n_req} requests, Poisson 20/s, nx 20..50, 16^2..32^2 velocities, "
+                          "Kn 1e-3..1, residual 1e-6 or 20000 steps, 150 GB budget",
+              "unit": "s (time to steady state)", "vc_unit": UNIT})
+    return s
+
+
 def reference_arm(args, cfg, prim):
     ws, rank, _ = dist()
     if rank != 0:
@@ -209,6 +264,8 @@ def main():
     ap.add_argument("--mesh", type=int, default=800, help="nx of the mesh sweep (ny = nx/2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -267,6 +324,9 @@ def main():
         barrier()
         t_e2e = e2e_form(ugks, torch, cfg, main_prec, args.e2e_steps, stream, f_host, W_host)
         t_e2e = max_over_ranks(t_e2e)
+        del f_host_t, W_host_t, f_host, W_host
+        batch = None if args.no_batch else batch_bench(ugks, torch, stream, args.steps, args.warmup)
+        serving = None if (args.no_serve or ws > 1) else serve_bench(ugks, stream)
 
     def form_json(prec):
         ms, kt, clk = results[prec]
@@ -323,9 +383,13 @@ def main():
         "clocks": main["clocks"],
         "e2e": {"value": ws * cfg.vc * args.e2e_steps / t_e2e, "unit": UNIT,
                 "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "cpu_baseline": cpu,
+        "batch": batch,
+        "serving": serving,
     }
+    if batch:
+        batch["vs_fp64_single"] = batch["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -188,3 +188,25 @@ def poisson_arrivals(rate: float, n: int, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson process with the given rate."""
     u = uniform01(seed, n)
     return np.cumsum(-np.log(u) / rate)
+
+
+def workload_serving(n_req: int = 24, seed: int = None, scale: str = "small", rate: float = 20.0):
+    """Channel-solve requests drawn as in the uneven batch (log-uniform mesh, velocity grid
+    and Kn, uniform inlet density) with Poisson arrival times.  scale="full" uses the batch
+    ranges (meshes 50x25..400x200, 16^2..64^2 velocities); scale="small" shrinks meshes to
+    nx in [20, 50] and velocity grids to [16, 32] per axis so that requests reach steady
+    state in seconds.  Returns (configs, arrival times, initial primitive fields)."""
+    seed = seed_for(5) if seed is None else seed
+    r = uniform01(seed, 4 * n_req).reshape(n_req, 4)
+    lo_x, hi_x, lo_v, hi_v = (50, 400, 16, 64) if scale == "full" else (20, 50, 16, 32)
+    cfgs, prims = [], []
+    for i in range(n_req):
+        nx = int(round(math.exp(math.log(lo_x) + r[i, 0] * (math.log(hi_x) - math.log(lo_x)))))
+        nvel = int(round(math.exp(math.log(lo_v) + r[i, 1] * (math.log(hi_v) - math.log(lo_v)))))
+        kn = math.exp(math.log(1e-3) + r[i, 2] * (math.log(1.0) - math.log(1e-3)))
+        rin = 1.05 + r[i, 3] * 0.45
+        c = channel_config(nx=nx, ny=max(1, nx // 2), n_vel=nvel, kn=kn, rho_in=rin,
+                           steps=20000, name=f"req{i}")
+        cfgs.append(c)
+        prims.append(initial_prim(c, seed + 1 + i))
+    return cfgs, poisson_arrivals(rate, n_req, seed + 10_000), prims
