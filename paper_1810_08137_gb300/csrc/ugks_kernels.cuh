@@ -257,15 +257,10 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     T C0 = 0, C1 = 0, C2 = 0, Cb = 0, D0 = 0, D1 = 0, D2 = 0, Db = 0;
     T P0 = 0, P1 = 0, P2 = 0, P3 = 0, Pb0 = 0, Pb1 = 0, Q0 = 0, Q1 = 0, Q2 = 0, Qb = 0;
     T Z1 = 0, Z2 = 0, Z3 = 0, Zb1 = 0;
-    bool south_done = false;
-    for (int m = 0; m < nv; m++) {
+    // rows with v != 0 feed the S side (v < 0, f - r_y) or the N side (v > 0, f + r_y);
+    // the loops over each half have no branches, so loads of consecutive rows overlap
+    auto row = [&](int m, T sy) {
       const T vv = mw[4 * nv + m];
-      if (!south_done && vv > T(0)) {
-        finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
-                          lane, wsum + kSumS);
-        P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
-        south_done = true;
-      }
       const size_t q = (size_t)m * nu + kk;
       const T2 c = fc[q], w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
       T rxh = 0, rxb = 0, ryh = 0, ryb = 0;
@@ -282,30 +277,47 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       R0 += w0 * rxh; R1 += w1 * rxh; R2 += w2 * rxh; Rb += w0 * rxb;
       C0 += w0 * ryh; C1 += w1 * ryh; C2 += w2 * ryh; Cb += w0 * ryb;
       D0 += w0 * dh;  D1 += w1 * dh;  D2 += w2 * dh;  Db += w0 * db;
-      if (vv == T(0)) {
-        // H(0) = 1/2: half to the S side with f - r_y, half to the N side with f + r_y;
-        // the u_n = v weighted sums vanish.
-        const T hw = T(0.5) * w0;
-        P0 += hw * (c.x - ryh); Pb0 += hw * (c.y - ryb); Q0 += hw * rxh; Qb += hw * rxb;
-        finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
-                          lane, wsum + kSumS);
-        P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
-        south_done = true;
-        P0 += hw * (c.x + ryh); Pb0 += hw * (c.y + ryb); Q0 += hw * rxh; Qb += hw * rxb;
-      } else {
-        const T sy = vv > T(0) ? T(1) : T(-1);
-        const T fyh = c.x + sy * ryh, fyb = c.y + sy * ryb;
-        P0 += w0 * fyh; P1 += w1 * fyh; P2 += w2 * fyh; P3 += w3 * fyh;
-        Pb0 += w0 * fyb; Pb1 += w1 * fyb;
-        Q0 += w0 * rxh; Q1 += w1 * rxh; Q2 += w2 * rxh; Qb += w0 * rxb;
-        Z1 += w1 * dh; Z2 += w2 * dh; Z3 += w3 * dh; Zb1 += w1 * db;
+      const T fyh = c.x + sy * ryh, fyb = c.y + sy * ryb;
+      P0 += w0 * fyh; P1 += w1 * fyh; P2 += w2 * fyh; P3 += w3 * fyh;
+      Pb0 += w0 * fyb; Pb1 += w1 * fyb;
+      Q0 += w0 * rxh; Q1 += w1 * rxh; Q2 += w2 * rxh; Qb += w0 * rxb;
+      Z1 += w1 * dh; Z2 += w2 * dh; Z3 += w3 * dh; Zb1 += w1 * db;
+    };
+    const int mneg = P.m_neg, mpos = P.m_pos;
+#pragma unroll 2
+    for (int m = 0; m < mneg; m++) row(m, T(-1));
+    if (mpos > mneg) {
+      // the v = 0 row, H(0) = 1/2: half to the S side with f - r_y, half to the N side with
+      // f + r_y; the u_n = v weighted sums vanish
+      const int m = mneg;
+      const size_t q = (size_t)m * nu + kk;
+      const T2 c = fc[q], w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
+      T rxh = 0, rxb = 0, ryh = 0, ryb = 0;
+      if (!zs) {
+        rxh = vl_half(w.x, c.x, e.x);
+        rxb = vl_half(w.y, c.y, e.y);
+        ryh = vl_half(s.x, c.x, n.x);
+        ryb = vl_half(s.y, c.y, n.y);
       }
-    }
-    if (!south_done) {
+      const T dh = cu * rxh, db = cu * rxb;  // v = 0
+      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m];
+      A0 += w0 * c.x; A1 += w1 * c.x; A2 += w2 * c.x; Ab += w0 * c.y;
+      R0 += w0 * rxh; R1 += w1 * rxh; R2 += w2 * rxh; Rb += w0 * rxb;
+      C0 += w0 * ryh; C1 += w1 * ryh; C2 += w2 * ryh; Cb += w0 * ryb;
+      D0 += w0 * dh;  D1 += w1 * dh;  D2 += w2 * dh;  Db += w0 * db;
+      const T hw = T(0.5) * w0;
+      P0 += hw * (c.x - ryh); Pb0 += hw * (c.y - ryb); Q0 += hw * rxh; Qb += hw * rxb;
+      finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
+                        lane, wsum + kSumS);
+      P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
+      P0 += hw * (c.x + ryh); Pb0 += hw * (c.y + ryb); Q0 += hw * rxh; Qb += hw * rxb;
+    } else {
       finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
                         lane, wsum + kSumS);
       P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
     }
+#pragma unroll 2
+    for (int m = mpos; m < nv; m++) row(m, T(1));
     finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1, lane,
                       wsum + kSumN);
 
