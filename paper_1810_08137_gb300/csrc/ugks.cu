@@ -209,15 +209,9 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
                                        h->cellf, h->mt4);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  if (sizeof(T) == 4) {
-    const dim3 grid((P.nx + 3) / 4, (P.ny + kWalkRows - 1) / kWalkRows, h->nchunk_neg + h->nchunk_pos);
-    k_walk<<<grid, 128, 0, st>>>(P, reinterpret_cast<const float2*>(fi), reinterpret_cast<float2*>(fo),
-                                 h->fxf, h->fyf, h->cellf, h->nchunk_neg, kWalkRows);
-  } else {  // FP64 form
-    k_update<T, T2, false>
-        <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
-            P, fi, fo, h->fxr, h->fyr, h->cells);
-  }
+  k_update<T, T2, false>
+      <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
+          P, fi, fo, h->fxr, h->fyr, h->cells);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
@@ -1066,7 +1060,7 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
   kb_sums<<<b->grid[2], 128, kBatchSumsSmem, st>>>(b->d_slots, b->d_work);
   kb_faces<<<b->grid[3], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_cells<<<b->grid[4], 128, 0, st>>>(b->d_slots, b->d_work);
-  kb_walk<<<b->grid[5], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_strip<<<b->grid[5], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_flip<<<1, 256, 0, st>>>(b->d_slots, b->d_work);
   return cudaGetLastError();
 }
@@ -1086,7 +1080,7 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
-                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_walk};
+                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases; p++) {
     w.start[p][1] = phase_blocks(S, p);
     int nb = 0;
@@ -1112,7 +1106,7 @@ cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st) {
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   kb_cells<<<h->grid1[4], 128, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  kb_walk<<<h->grid1[5], 128, 0, st>>>(h->d_slot, h->d_work);
+  kb_strip<<<h->grid1[5], 128, 0, st>>>(h->d_slot, h->d_work);
   kb_flip<<<1, 32, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
@@ -1165,7 +1159,7 @@ ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_strea
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem);
   // persistent grids: resident blocks per SM x SMs
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
-                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_walk};
+                              (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases && e == cudaSuccess; p++) {
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, p == 2 ? kBatchSumsSmem : 0);

@@ -9,7 +9,7 @@
 namespace ugks {
 
 constexpr int kMaxSlots = 256;
-constexpr int kPhases = 6;  // ghost_x, ghost_y, sums, faces, cells, walk
+constexpr int kPhases = 6;  // ghost_x, ghost_y, sums, faces, cells, update (strip walk)
 
 // What the phase kernels need about one instance.
 struct SlotDev {
@@ -46,8 +46,11 @@ __host__ __device__ inline int phase_blocks(const SlotDev& S, int phase) {
     case 2: return ((P.nx + 2) * (P.ny + 2) + kWarpsPerBlock - 1) / kWarpsPerBlock;
     case 3: return ((P.nx + 1) * P.ny + P.nx * (P.ny + 1) + 127) / 128;
     case 4: return S.nrblocks;
-    default:
-      return ((P.nx + 3) / 4) * ((P.ny + S.walk_rows - 1) / S.walk_rows) * (S.nchunk_neg + S.nchunk_pos);
+    default: {
+      const long items = (long)((P.nx + kStripW - 1) / kStripW) *
+                         ((P.ny + S.walk_rows - 1) / S.walk_rows) * (S.nchunk_neg + S.nchunk_pos);
+      return (int)((items + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    }
   }
 }
 
@@ -120,17 +123,23 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
   }
 }
 
-__global__ void __launch_bounds__(128, 8) kb_walk(const SlotDev* __restrict__ slots,
-                                                  const BatchWork* __restrict__ wk) {
+// Update sweep: one warp per work item (strip, tile, velocity chunk), strips fastest so that
+// the warps of a block share neighbour columns.
+__global__ void __launch_bounds__(128) kb_strip(const SlotDev* __restrict__ slots,
+                                                const BatchWork* __restrict__ wk) {
+  __shared__ __align__(16) float4 ring[kWarpsPerBlock][kRing * kStripChunks];
+  const int warp = threadIdx.x >> 5;
   const int total = wk->start[5][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[5], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    const int loc = vb - wk->start[5][a];
-    const int gx = (S.P.nx + 3) / 4, gy = (S.P.ny + S.walk_rows - 1) / S.walk_rows;
-    const int c = S.cur;
-    walk_body(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows, loc % gx,
-              (loc / gx) % gy, loc / (gx * gy));
+    const int ns = (S.P.nx + kStripW - 1) / kStripW, nt = (S.P.ny + S.walk_rows - 1) / S.walk_rows;
+    const int it = (vb - wk->start[5][a]) * kWarpsPerBlock + warp;
+    if (it < ns * nt * (S.nchunk_neg + S.nchunk_pos)) {
+      const int c = S.cur;
+      strip_body<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
+                          it % ns, (it / ns) % nt, it / (ns * nt), ring[warp]);
+    }
   }
 }
 

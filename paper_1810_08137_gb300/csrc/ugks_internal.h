@@ -43,20 +43,33 @@ struct CellRec {
   double cf, cgn, cg1, inv;
 };
 
-// FP32 copies of the face and cell records for the FP32 form's update kernel (written by the
-// FP64 face and cell kernels, so the update kernel does no FP64 arithmetic or conversion).
-// b component of the micro flux: Q_b = X2 Q_h + kb0 + kb1 un + kb2 ut.
+// FP32 records of the FP32 form's update kernel (written by the FP64 face and cell
+// kernels, so the update kernel does no FP64 arithmetic or conversion).  They are stated in
+// the global velocity frame on the monomials m = (1, u, v, u^2, uv, v^2, u r2, v r2),
+// r2 = u^2 + v^2, with the Maxwellian amplitude folded into the coefficients and each
+// Maxwellian written as 2^(E0 + E1 u + E2 v + E3 r2), so that a lane evaluates a face or
+// cell with fused multiply-adds and one exp2.
+//   micro flux through a face, side s = 0 (un > 0) or 1 (un < 0), e-form f_up and d:
+//     X_h = Q_h g + Mt4 f_up,h - Mt5 d_h,   Q_h = sum_k Q[s][k] m_k,
+//     X_b = Q_b g + Mt4 f_up,b - Mt5 d_b,   Q_b = K[s][3] Q_h + K[s][0] + K[s][1] u + K[s][2] v,
+//     g = 2^(E . (1, u, v, r2))
+//   inflow from a diffuse wall (wall != 0): X_h = gdt g - dt g_ref,h, X_b = gdt K[0][3] g - dt g_ref,b
 struct __align__(16) FaceRecF {
-  float Q[2][8];     // Q_h per side (0: un > 0, 1: un < 0): c00 c10 c01 c20 c11 c02 cn3 ct3
-  float kb[2][4];    // kb0 kb1 kb2 (pad) per side
-  float lam, Un, Ut, G;
-  float Mt4, Mt5, X2, wall;
+  float Q[2][8];
+  float K[2][4];
+  float E[4];
+  float Mt4, Mt5, wall, gdt;
 };
+// Eq. 3 as an increment e^{n+1} = e^n + d, per component:
+//   d_h = aui dX_h + avi dY_h + A1 g1 + An gn + c g_ref,h - Bs e_h
+//   d_b = aui dX_b + avi dY_b + A1b g1 + Anb gn + c g_ref,b - Bs e_b
+// with gn = 2^(En . (1, u, v, r2)), g1 likewise, aui = inv |u|/dx, avi = inv |v|/dy,
+// c = u irx + v iry - Bs, dX / dY the inflow minus outflow micro flux in x / y.
 struct __align__(16) CellRecF {
-  float Gn, Un, Vn, lamn;
-  float G1, U1, V1, lam1;
-  float bn, b1, inv, cg1;
-  float cgn, refx, refy, pad;   // refx = (Mt4_W - Mt4_E)/dx, refy = (Mt4_S - Mt4_N)/dy
+  float En[4];
+  float E1[4];
+  float A1, An, A1b, Anb;   // inv cg1, inv cgn, inv cg1 b1, inv cgn bn
+  float Bs, irx, iry, inv;  // inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 
 struct Params {

@@ -510,12 +510,40 @@ __device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const d
   c[7] = Mt2 * pb[3];
 }
 
+// FP32 face record from the face-frame FP64 quantities (see FaceRecF): monomials and the
+// Maxwellian exponent are moved to the global (u, v) frame (y faces: un = v, ut = u), the
+// amplitude G is folded into the polynomial coefficients and the exponent is in log2 units.
+// Qh[s]: Q_h per side on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2); kb[s]: b-polynomial
+// terms (k0, k_un, k_ut).
+__device__ void pack_face_f32(bool isx, const double (*Qh)[8], const double (*kb)[3], double X2,
+                              double G, double lam, double Un, double Ut, double Mt4, double Mt5,
+                              double wall, double gdt, FaceRecF* RF) {
+  constexpr double kLog2e = 1.4426950408889634;
+  constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+  for (int sd = 0; sd < 2; sd++) {
+    for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)(G * Qh[sd][isx ? c : py[c]]);
+    RF->K[sd][0] = (float)(G * kb[sd][0]);
+    RF->K[sd][1] = (float)(G * kb[sd][isx ? 1 : 2]);
+    RF->K[sd][2] = (float)(G * kb[sd][isx ? 2 : 1]);
+    RF->K[sd][3] = (float)X2;
+  }
+  const double Ux = isx ? Un : Ut, Vy = isx ? Ut : Un;
+  RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
+  RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
+  RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
+  RF->E[3] = (float)(-lam * kLog2e);
+  RF->Mt4 = (float)Mt4;
+  RF->Mt5 = (float)Mt5;
+  RF->wall = (float)wall;
+  RF->gdt = (float)gdt;
+}
+
 // One UGKS interface in the face frame (un, ut): inputs are the interface sums (S1, S7)
 // and the cell W on both sides; output the time-integrated macroscopic flux F and the
 // micro-flux record.
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
                           const double* Ss, const double* WL, const double* WR, double delta,
-                          double* F, FaceRec& R, FaceRecF* RF) {
+                          bool isx, double* F, FaceRec& R, FaceRecF* RF) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], irho = 1.0 / rho, U = W0[1] * irho, V = W0[2] * irho;
@@ -583,16 +611,18 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
     // Mt2 un a4 + Mt2 ut b4), kap = (X4 - X2^2)/2 = K/(4 lam^2)
     const double kap = 0.5 * (X4 - X2 * X2);
+    double kb[2][3];
     for (int sd = 0; sd < 2; sd++) {
       const double* as = sd == 0 ? aL : aR;
-      for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)R.Q[sd][0][c];
-      RF->kb[sd][0] = (float)(kap * Mt[2] * A[3]);
-      RF->kb[sd][1] = (float)(kap * Mt[1] * as[3]);
-      RF->kb[sd][2] = (float)(kap * Mt[1] * b[3]);
-      RF->kb[sd][3] = 0.f;
+      kb[sd][0] = kap * Mt[2] * A[3];
+      kb[sd][1] = kap * Mt[1] * as[3];
+      kb[sd][2] = kap * Mt[1] * b[3];
     }
-    RF->lam = (float)lam; RF->Un = (float)U; RF->Ut = (float)V; RF->G = (float)R.G;
-    RF->Mt4 = (float)Mt[3]; RF->Mt5 = (float)Mt[4]; RF->X2 = (float)X2; RF->wall = 0.f;
+    const double Qh[2][8] = {{R.Q[0][0][0], R.Q[0][0][1], R.Q[0][0][2], R.Q[0][0][3], R.Q[0][0][4],
+                              R.Q[0][0][5], R.Q[0][0][6], R.Q[0][0][7]},
+                             {R.Q[1][0][0], R.Q[1][0][1], R.Q[1][0][2], R.Q[1][0][3], R.Q[1][0][4],
+                              R.Q[1][0][5], R.Q[1][0][6], R.Q[1][0][7]}};
+    pack_face_f32(isx, Qh, kb, X2, R.G, lam, U, V, Mt[3], Mt[4], 0.0, 0.0, RF);
   }
 }
 
@@ -660,12 +690,9 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     R.bfac = P.K / (2.0 * lam);
     R.wall = wall;
     if (RF) {
-      for (int a = 0; a < 2; a++) {
-        for (int c = 0; c < 8; c++) RF->Q[a][c] = 0.f;
-        for (int c = 0; c < 4; c++) RF->kb[a][c] = 0.f;
-      }
-      RF->lam = (float)lam; RF->Un = 0.f; RF->Ut = (float)R.Ut; RF->G = (float)R.G;
-      RF->Mt4 = (float)P.dt; RF->Mt5 = 0.f; RF->X2 = (float)R.bfac; RF->wall = (float)wall;
+      const double Z8[2][8] = {}, Z3[2][3] = {};
+      pack_face_f32(isx, Z8, Z3, R.bfac, 0.0, lam, 0.0, R.Ut, P.dt, 0.0, (double)wall, P.dt * R.G,
+                    RF);
     }
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
@@ -684,7 +711,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
-    face_math(P, W0, St, Sf, Ss, WL, WR, delta, Fr, R, RF);
+    face_math(P, W0, St, Sf, Ss, WL, WR, delta, isx, Fr, R, RF);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[pm[c]] = Fr[c];
   }
@@ -754,14 +781,25 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
     R.inv = 1.0 / (1.0 + R.cg1);
     if (crf) {
       const int nfx = (nx + 1) * P.ny;
+      constexpr double kLog2e = 1.4426950408889634;
+      const double refx = (mt4[xw] - mt4[xe]) / P.dx, refy = (mt4[nfx + ys] - mt4[nfx + yn]) / P.dy;
       CellRecF F;
-      F.Gn = (float)R.Gn; F.Un = (float)Un; F.Vn = (float)Vn; F.lamn = (float)ln;
-      F.G1 = (float)R.G1; F.U1 = (float)U1; F.V1 = (float)V1; F.lam1 = (float)l1;
-      F.bn = (float)R.bn; F.b1 = (float)R.b1; F.inv = (float)R.inv; F.cg1 = (float)R.cg1;
-      F.cgn = (float)R.cgn;
-      F.refx = (float)((mt4[xw] - mt4[xe]) / P.dx);
-      F.refy = (float)((mt4[nfx + ys] - mt4[nfx + yn]) / P.dy);
-      F.pad = 0.f;
+      F.En[0] = (float)(log2(R.Gn) - ln * (Un * Un + Vn * Vn) * kLog2e);
+      F.En[1] = (float)(2.0 * ln * Un * kLog2e);
+      F.En[2] = (float)(2.0 * ln * Vn * kLog2e);
+      F.En[3] = (float)(-ln * kLog2e);
+      F.E1[0] = (float)(log2(R.G1) - l1 * (U1 * U1 + V1 * V1) * kLog2e);
+      F.E1[1] = (float)(2.0 * l1 * U1 * kLog2e);
+      F.E1[2] = (float)(2.0 * l1 * V1 * kLog2e);
+      F.E1[3] = (float)(-l1 * kLog2e);
+      F.A1 = (float)(R.inv * R.cg1);
+      F.An = (float)(R.inv * R.cgn);
+      F.A1b = (float)(R.inv * R.cg1 * R.b1);
+      F.Anb = (float)(R.inv * R.cgn * R.bn);
+      F.Bs = (float)(R.inv * (R.cg1 + R.cgn));
+      F.irx = (float)(R.inv * refx);
+      F.iry = (float)(R.inv * refy);
+      F.inv = (float)R.inv;
       crf[c] = F;
     } else {
       cr[c] = R;
@@ -1045,74 +1083,128 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 }
 
 // -------------------------------------------------------------------------------------
-// FP32 form, S6 + S8 and Eq. 3 as an upwind column walk.  For one velocity the micro flux
+// FP32 form, S6 + S8 and Eq. 3 as an upwind strip walk.  For one velocity the micro flux
 // through a face depends only on its upwind cell, so each cell evaluates the flux through
-// its downwind x-face and downwind y-face, and takes the flux through its upwind faces
-// from the upwind neighbour: the x-upwind one is evaluated from a second register window
-// (the neighbour column), the y-upwind one is the previous row's downwind flux carried in
-// registers, because the walk runs along y in the direction of v.
-// Grid: x = column groups of 4 (one warp per column), y = tiles of kWalkRows rows,
-// z = velocity chunks of 32 (v < 0 chunks first, then v >= 0).  Lane = velocity.
-// Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + df.
+// its downwind x-face and downwind y-face and receives the flux through its upwind faces
+// from its upwind neighbours.  A warp (lane = velocity) owns a strip of W adjacent columns
+// and walks it row by row in the direction of v; within a row it visits the columns in the
+// direction of u.  The x-upwind flux of a column is the previous column's downwind flux, the
+// y-upwind flux is the previous row's, both carried in registers; only the strip's first
+// column needs the flux out of the cell before the strip (U), which is evaluated from U's
+// own reconstruction.  Slopes are taken along the walk (upwind, centre, downwind), so the
+// upwind face value is f + slope and u sigma_x = |u| (2/dx) slope, with no sign selects.
+// Work item: (velocity chunk of 32, v < 0 chunks first; tile of `rows` rows; strip).
+// Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + d (CellRecF).
 // -------------------------------------------------------------------------------------
 constexpr int kWalkRows = 64;  // default rows per walk tile
+constexpr int kStripW = 2;     // columns per strip
+constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
+// 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
+constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
 
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-struct LaneVel {
-  float u, v, uu, uv, vv, ur2, vr2;
+// 16-byte asynchronous global -> shared copies (per thread), in commit groups.
+__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 2^x and 1/x with subnormal results flushed to zero (PTX approximate forms).
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// van Leer half slope of the walk-ordered stencil (a, c, b), both components.
+__device__ __forceinline__ float vl_walk(float a, float c, float b) {
+  const float d1 = c - a, d2 = b - c, p = d1 * d2;
+  return p > 0.f ? p * rcp_ftz(d1 + d2) : 0.f;
+}
+__device__ __forceinline__ float2 vl_walk2(float2 a, float2 c, float2 b) {
+  return make_float2(vl_walk(a.x, c.x, b.x), vl_walk(a.y, c.y, b.y));
+}
+
+// Per-lane velocity constants of the walk.
+struct StripLane {
+  float u, v, uu, uv, vv, ur2, vr2, r2;
+  float cu, cv;   // |u| 2/dx, |v| 2/dy: d = cu slope_x + cv slope_y
+  float au, av;   // |u| / dx, |v| / dy
+  float2 gr;      // g_ref (h, b)
+  float dt;
 };
 
-// Q_h and the b-component polynomial of a face record for one side, at (un, ut), where the
-// monomials are given in the face frame: m1 = un, m2 = ut, m3 = un^2, m4 = un ut, m5 = ut^2,
-// m6 = un r2, m7 = ut r2.
-__device__ __forceinline__ void eval_q(const FaceRecF* R, int side, float m1, float m2, float m3,
-                                       float m4, float m5, float m6, float m7, float& qh, float& qb) {
-  const float4 a = *reinterpret_cast<const float4*>(&R->Q[side][0]);
-  const float4 b = *reinterpret_cast<const float4*>(&R->Q[side][4]);
-  const float4 k = *reinterpret_cast<const float4*>(&R->kb[side][0]);
-  qh = a.x + a.y * m1 + a.z * m2 + a.w * m3 + b.x * m4 + b.y * m5 + b.z * m6 + b.w * m7;
-  const float X2 = R->X2;
-  qb = X2 * qh + k.x + k.y * m1 + k.z * m2;
+__device__ __forceinline__ float exp_poly(const float4 e, const StripLane& L) {
+  return ex2_ftz(fmaf(e.w, L.r2, fmaf(e.z, L.v, fmaf(e.y, L.u, e.x))));
 }
 
-// X = Q g + Mt4 f_up - Mt5 d for one face, both components (e-form f_up).
-__device__ __forceinline__ float2 face_x(const FaceRecF* R, int side, float un, float ut, float m1,
-                                         float m2, float m3, float m4, float m5, float m6, float m7,
-                                         float2 fup, float2 d) {
-  float qh, qb;
-  eval_q(R, side, m1, m2, m3, m4, m5, m6, m7, qh, qb);
-  const float4 g4 = *reinterpret_cast<const float4*>(&R->lam);  // lam Un Ut G
-  const float4 t4 = *reinterpret_cast<const float4*>(&R->Mt4);  // Mt4 Mt5 X2 wall
-  const float dn = un - g4.y, dt = ut - g4.z;
-  const float g = g4.w * __expf(-g4.x * (dn * dn + dt * dt));
+// Micro flux through a face for the lane's velocity (FaceRecF), e-form f_up and d.
+__device__ __forceinline__ float2 strip_face(const FaceRecF* R, int side, const StripLane& L,
+                                             float2 fup, float2 d) {
+  const float4 a = ld4(&R->Q[side][0]);
+  const float4 b = ld4(&R->Q[side][4]);
+  const float4 k = ld4(&R->K[side][0]);
+  const float4 e = ld4(&R->E[0]);
+  const float2 t = *reinterpret_cast<const float2*>(&R->Mt4);  // Mt4 Mt5
+  float qh = fmaf(b.w, L.vr2, fmaf(b.z, L.ur2, fmaf(b.y, L.vv, fmaf(b.x, L.uv, fmaf(a.w, L.uu,
+             fmaf(a.z, L.v, fmaf(a.y, L.u, a.x)))))));
+  const float qb = fmaf(k.w, qh, fmaf(k.z, L.v, fmaf(k.y, L.u, k.x)));
+  const float g = exp_poly(e, L);
   float2 X;
-  X.x = qh * g + t4.x * fup.x - t4.y * d.x;
-  X.y = qb * g + t4.x * fup.y - t4.y * d.y;
+  X.x = fmaf(qh, g, fmaf(t.x, fup.x, -t.y * d.x));
+  X.y = fmaf(qb, g, fmaf(t.x, fup.y, -t.y * d.y));
   return X;
 }
 
-// Flux leaving a wall into the gas, e-form: dt (g_wall - g_ref).
-__device__ __forceinline__ float2 wall_in(const FaceRecF* R, float un, float ut, float dt, float2 gr) {
-  const float4 g4 = *reinterpret_cast<const float4*>(&R->lam);
-  const float dn = un - g4.y, du = ut - g4.z;
-  const float g = g4.w * __expf(-g4.x * (dn * dn + du * du));
+// Flux leaving a diffuse wall into the gas, e-form.
+__device__ __forceinline__ float2 strip_wall(const FaceRecF* R, const StripLane& L) {
+  const float4 e = ld4(&R->E[0]);
+  const float gdt = R->gdt, X2 = R->K[0][3];
+  const float g = exp_poly(e, L);
   float2 X;
-  X.x = dt * (g - gr.x);
-  X.y = dt * (R->X2 * g - gr.y);
+  X.x = fmaf(gdt, g, -L.dt * L.gr.x);
+  X.y = fmaf(gdt * X2, g, -L.dt * L.gr.y);
   return X;
 }
 
-__device__ __forceinline__ void walk_body(const Params& P, const float2* __restrict__ f,
-                                          float2* __restrict__ fo, const FaceRecF* __restrict__ fxr,
-                                          const FaceRecF* __restrict__ fyr,
-                                          const CellRecF* __restrict__ cr, int nchunk_neg,
-                                          int walk_rows, int bx, int by, int bz) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Eq. 3 increment of one cell (CellRecF); Xi / Xo: inflow / outflow flux in x and y.
+__device__ __forceinline__ float2 strip_collide(const CellRecF* C, const StripLane& L, float2 e,
+                                                float2 Xix, float2 Xox, float2 Xiy, float2 Xoy) {
+  const float4 en = ld4(&C->En[0]);
+  const float4 e1 = ld4(&C->E1[0]);
+  const float4 A = ld4(&C->A1);    // A1 An A1b Anb
+  const float4 B = ld4(&C->Bs);    // Bs irx iry inv
+  const float gn = exp_poly(en, L), g1 = exp_poly(e1, L);
+  const float c = fmaf(L.v, B.z, fmaf(L.u, B.y, -B.x));
+  const float aui = L.au * B.w, avi = L.av * B.w;
+  float dh = fmaf(aui, Xix.x - Xox.x, avi * (Xiy.x - Xoy.x));
+  float db = fmaf(aui, Xix.y - Xox.y, avi * (Xiy.y - Xoy.y));
+  dh = fmaf(A.x, g1, fmaf(A.y, gn, fmaf(c, L.gr.x, fmaf(-B.x, e.x, dh))));
+  db = fmaf(A.z, g1, fmaf(A.w, gn, fmaf(c, L.gr.y, fmaf(-B.x, e.y, db))));
+  return make_float2(e.x + dh, e.y + db);
+}
+
+template <int W>
+__device__ __forceinline__ void strip_body(const Params& P, const float2* __restrict__ f,
+                                           float2* __restrict__ fo, const FaceRecF* __restrict__ fxr,
+                                           const FaceRecF* __restrict__ fyr,
+                                           const CellRecF* __restrict__ cr, int nchunk_neg,
+                                           int rows, int bx, int by, int chunk,
+                                           float4* __restrict__ ring) {
+  const int lane = threadIdx.x & 31;
   const int nx = P.nx, ny = P.ny, nu = P.nu, nq = P.nq;
-  const int i = bx * 4 + warp;
-  if (i >= nx) return;
-  const int chunk = bz;
+  const int i0 = bx * W;
+  const int wc = min(W, nx - i0);
   const bool vpos = chunk >= nchunk_neg;
   const int nq_neg = P.m_neg * nu;
   const int q = vpos ? nq_neg + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
@@ -1120,147 +1212,157 @@ __device__ __forceinline__ void walk_body(const Params& P, const float2* __restr
   const bool act = q < qend;
   const int qq = act ? q : qend - 1;
   const int k = qq % nu, m = qq / nu;
-  const float u = P.uwf[k], v = P.mvf[4 * P.nv + m];
-  const int su = u > 0.f ? 1 : -1;
+  StripLane L;
+  L.u = P.uwf[k];
+  L.v = P.mvf[4 * P.nv + m];
+  L.uu = L.u * L.u; L.uv = L.u * L.v; L.vv = L.v * L.v;
+  L.r2 = L.uu + L.vv;
+  L.ur2 = L.u * L.r2; L.vr2 = L.v * L.r2;
+  L.cu = fabsf(L.u) * P.f_tdx; L.cv = fabsf(L.v) * P.f_tdy;
+  L.au = fabsf(L.u) * P.f_idx; L.av = fabsf(L.v) * P.f_idy;
+  L.gr = __ldg(static_cast<const float2*>(P.gref) + qq);
+  L.dt = P.f_dt;
+  const int su = L.u > 0.f ? 1 : -1;
   const int sv = vpos ? 1 : -1;
-  const float r2 = u * u + v * v;
-  const float m_u = u, m_v = v, m_uu = u * u, m_uv = u * v, m_vv = v * v, m_ur2 = u * r2, m_vr2 = v * r2;
-  const float cu = u * P.f_tdx, cv = v * P.f_tdy;
-  const float au = fabsf(u) * P.f_idx, av = fabsf(v) * P.f_idy;
-  const float dtf = P.f_dt;
-  const float2 gr = __ldg(static_cast<const float2*>(P.gref) + qq);
-  const int xside = u > 0.f ? 0 : 1, yside = vpos ? 0 : 1;
-  const int iu = i - su;
+  const int xside = su > 0 ? 0 : 1, yside = vpos ? 0 : 1;
+  const int ib = su > 0 ? i0 : i0 + wc - 1;          // strip position 0 (walk order)
+  const int iU = ib - su;                              // upwind neighbour column U
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
-  const bool zu = (iu < 0 && pW) || (iu >= nx && pE);  // x-upwind cell is a pressure ghost
-  const int fxo = su > 0 ? 1 : 0;                       // downwind x-face offset i + fxo
+  const bool zu = (iU < 0 && pW) || (iU >= nx && pE);  // U is a pressure ghost: zero slopes
+  const int xo = su * nq;                              // one column in walk order, in float2
+  // walk position p (-2 = UU, -1 = U, 0..W-1 strip, W = D) -> column offset; strip positions
+  // past the strip's end read column D (they are not updated)
+  auto col = [&](int p) { return (p < wc ? p : wc) * xo; };
 
-  const int j0 = by * walk_rows;
-  const int j1 = min(j0 + walk_rows, ny);
-  const int jfirst = sv > 0 ? j0 : j1 - 1, jlast = sv > 0 ? j1 - 1 : j0;
-  const long rs = (long)P.ex * nq;
-  const float2* col = f + fcell(P, i, 0) * nq + qq;      // own column, row 0
+  const int j0 = by * rows;
+  const int j1 = min(j0 + rows, ny);
+  const int jfirst = sv > 0 ? j0 : j1 - 1;
+  const int nsteps = j1 - j0;
+  const int rs = sv * P.ex * nq;                       // one row in walk order, in float2
+  const long base = ((long)(jfirst + 2) * P.ex + ib + 2) * nq + qq;
+  const float2* pr = f + base;                         // (position 0, row jfirst)
+  float2* pw = fo + base;
 
-  // prologue: downwind y-face flux of the halo cell (i, jp), jp = jfirst - sv
-  const int jp = jfirst - sv;
-  float2 fo_p = ld2(col + (long)jp * rs), fo_c = ld2(col + (long)jfirst * rs);
-  float2 fu_p = ld2(col - su * nq + (long)jp * rs), fu_c = ld2(col - su * nq + (long)jfirst * rs);
-  float2 Xin_y;
+  // rows jfirst - sv (Pv), jfirst (Cv), jfirst + sv (Nv) at positions -1..W-1
+  float2 Pv[W + 1], Cv[W + 1], Nv[W + 1];
+#pragma unroll
+  for (int p = -1; p < W; p++) {
+    Pv[p + 1] = ld2(pr - rs + col(p));
+    Cv[p + 1] = ld2(pr + col(p));
+    Nv[p + 1] = ld2(pr + rs + col(p));
+  }
+  float2 cUU = ld2(pr + col(-2)), cD = ld2(pr + col(W));
+
+  // prologue: flux through the y-face between the halo row jp = jfirst - sv and jfirst
+  float2 Xiy[W];
   {
-    const int yface = (sv > 0 ? jfirst : jp) * nx + i;  // face between jp and jfirst
-    const FaceRecF* RY = fyr + yface;
+    const int jp = jfirst - sv;
+    const FaceRecF* RY = fyr + (long)(sv > 0 ? jfirst : jfirst + 1) * nx + ib;
+    const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
+    const float2 dp = ld2(pr - rs + col(W));
     if (RY->wall != 0.f) {
-      Xin_y = wall_in(RY, v, u, dtf, gr);
+#pragma unroll
+      for (int t = 0; t < W; t++)
+        if (t < wc) Xiy[t] = strip_wall(RY + su * t, L);
     } else {
-      const float2 fpp = ld2(col + (long)(jp - sv) * rs);
-      const float2 fl = ld2(f + fcell(P, i - 1, jp) * nq + qq), fr = ld2(f + fcell(P, i + 1, jp) * nq + qq);
-      const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
-      float2 rx, ry;
-      rx.x = zp ? 0.f : vl_half(fl.x, fo_p.x, fr.x);
-      rx.y = zp ? 0.f : vl_half(fl.y, fo_p.y, fr.y);
-      // +y slope of the halo cell: rows jp-1, jp, jp+1
-      const float2 lo = sv > 0 ? fpp : fo_c, hi = sv > 0 ? fo_c : fpp;
-      ry.x = zp ? 0.f : vl_half(lo.x, fo_p.x, hi.x);
-      ry.y = zp ? 0.f : vl_half(lo.y, fo_p.y, hi.y);
-      const float sy = (float)sv;
-      float2 fup, d;
-      fup.x = fo_p.x + sy * ry.x; fup.y = fo_p.y + sy * ry.y;
-      d.x = cu * rx.x + cv * ry.x; d.y = cu * rx.y + cv * ry.y;
-      Xin_y = face_x(RY, yside, v, u, m_v, m_u, m_vv, m_uv, m_uu, m_vr2, m_ur2, fup, d);
+#pragma unroll
+      for (int t = 0; t < W; t++) {
+        if (t < wc) {
+          const float2 pp = ld2(pr - 2 * rs + col(t));
+          const float2 c = Pv[t + 1];
+          float2 rx = vl_walk2(Pv[t], c, t + 1 < W ? Pv[t + 2] : dp);
+          float2 ry = vl_walk2(pp, c, Cv[t + 1]);
+          if (zp) rx = ry = make_float2(0.f, 0.f);
+          const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
+          Xiy[t] = strip_face(RY + su * t, yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
+        }
+      }
     }
   }
 
-  const float sx = (float)su, sy = (float)sv;
-  // row-walk state: one f pointer (own column) with the neighbour columns at a per-lane
-  // offset, one x-face record pointer (the upwind face is su records before the downwind
-  // one), 32-bit strides; f loads are issued one step ahead
-  const int xo = su * nq;                                  // own -> x-downwind column
-  const int fstep = sv * (int)rs;
-  const float2* po = col + (long)jfirst * rs;
-  float2* pw = fo + fcell(P, i, jfirst) * nq + qq;
-  const int xstep = sv * (nx + 1), ystep = sv * nx;
-  const FaceRecF* RXo = fxr + (size_t)jfirst * (nx + 1) + i + fxo;
-  const FaceRecF* RYo = fyr + (size_t)(sv > 0 ? jfirst + 1 : jfirst) * nx + i;
-  const CellRecF* C = cr + (size_t)jfirst * nx + i;
-  float2 fo_n = ld2(po + fstep), fu_n = ld2(po - xo + fstep), fd = ld2(po + xo), fuu = ld2(po - 2 * xo);
-  const int nsteps = (jlast - jfirst) * sv + 1;
+  // face and cell records of a row, staged through a ring of kRing rows in shared memory:
+  // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
+  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
+  auto stage = [&](int s) {
+    if (s < nsteps) {
+      const int j = jfirst + sv * s;
+      const float4* gx = reinterpret_cast<const float4*>(fxr + (long)j * (nx + 1) + i0);
+      const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
+      const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
+      float4* dst = ring + (s % kRing) * kStripChunks;
+      for (int c = lane; c < kStripChunks; c += 32) {
+        if (c < oY) {
+          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
+        } else if (c < oC) {
+          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
+        } else if (c - oC < wc * 4) {
+          cp_async16(dst + c, gc + (c - oC));
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  __syncwarp();                      // the ring's previous contents are no longer read
+#pragma unroll
+  for (int s = 0; s < kRing - 1; s++) stage(s);
+  // local record index of walk position t (-1 = U's face for x) within the staged row
+  const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
+  auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
   for (int s = 0; s < nsteps; s++) {
-    float2 fo_nn = fo_n, fu_nn = fu_n, fd_n = fd, fuu_n = fuu;
-    if (s + 1 < nsteps) {
-      fo_nn = ld2(po + 2 * fstep);
-      fu_nn = ld2(po - xo + 2 * fstep);
-      fd_n = ld2(po + xo + fstep);
-      fuu_n = ld2(po - 2 * xo + fstep);
-    }
-    // own slopes (+x, +y)
-    const float2 xl = su > 0 ? fu_c : fd, xr = su > 0 ? fd : fu_c;
-    const float2 yl = sv > 0 ? fo_p : fo_n, yr = sv > 0 ? fo_n : fo_p;
-    float2 rx, ry;
-    rx.x = vl_half(xl.x, fo_c.x, xr.x); rx.y = vl_half(xl.y, fo_c.y, xr.y);
-    ry.x = vl_half(yl.x, fo_c.x, yr.x); ry.y = vl_half(yl.y, fo_c.y, yr.y);
-    float2 d;
-    d.x = cu * rx.x + cv * ry.x; d.y = cu * rx.y + cv * ry.y;
-    // downwind x-face
-    float2 fup;
-    fup.x = fo_c.x + sx * rx.x; fup.y = fo_c.y + sx * rx.y;
-    const float2 Xout_x = face_x(RXo, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fup, d);
-    // upwind x-face: flux leaving the x-upwind cell (or the wall)
-    const FaceRecF* RXi = RXo - su;
-    float2 Xin_x;
+    __syncwarp();                    // every lane is done with the slot refilled next
+    stage(s + kRing - 1);
+    // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
+    float2 NN[W + 1];
+#pragma unroll
+    for (int p = -1; p < W; p++) NN[p + 1] = ld2(pr + 2 * rs + col(p));
+    const float2 nUU = ld2(pr + rs + col(-2)), nD = ld2(pr + rs + col(W));
+    cp_async_wait<kRing - 1>();
+    __syncwarp();
+    const float4* row = ring + (s % kRing) * kStripChunks;
+    const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
+    const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
+    const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
+
+    // flux into position 0 out of U (or off the wall)
+    float2 Xix;
+    const FaceRecF* RXi = RX + xl0;
     if (RXi->wall != 0.f) {
-      Xin_x = wall_in(RXi, u, v, dtf, gr);
+      Xix = strip_wall(RXi, L);
     } else {
-      const float2 al = su > 0 ? fuu : fo_c, ar = su > 0 ? fo_c : fuu;
-      const float2 bl = sv > 0 ? fu_p : fu_n, br = sv > 0 ? fu_n : fu_p;
-      float2 rxu, ryu;
-      rxu.x = zu ? 0.f : vl_half(al.x, fu_c.x, ar.x);
-      rxu.y = zu ? 0.f : vl_half(al.y, fu_c.y, ar.y);
-      ryu.x = zu ? 0.f : vl_half(bl.x, fu_c.x, br.x);
-      ryu.y = zu ? 0.f : vl_half(bl.y, fu_c.y, br.y);
-      float2 fuw, du;
-      fuw.x = fu_c.x + sx * rxu.x; fuw.y = fu_c.y + sx * rxu.y;
-      du.x = cu * rxu.x + cv * ryu.x; du.y = cu * rxu.y + cv * ryu.y;
-      Xin_x = face_x(RXi, xside, u, v, m_u, m_v, m_uu, m_uv, m_vv, m_ur2, m_vr2, fuw, du);
+      float2 rx = vl_walk2(cUU, Cv[0], Cv[1]);
+      float2 ry = vl_walk2(Pv[0], Cv[0], Nv[0]);
+      if (zu) rx = ry = make_float2(0.f, 0.f);
+      const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
+      Xix = strip_face(RXi, xside, L, make_float2(Cv[0].x + rx.x, Cv[0].y + rx.y), d);
     }
-    // downwind y-face
-    fup.x = fo_c.x + sy * ry.x; fup.y = fo_c.y + sy * ry.y;
-    const float2 Xout_y = face_x(RYo, yside, v, u, m_v, m_u, m_vv, m_uv, m_uu, m_vr2, m_ur2, fup, d);
-    // Eq. 3 as an increment
-    const float4 c0 = *reinterpret_cast<const float4*>(&C->Gn);   // Gn Un Vn lamn
-    const float4 c1 = *reinterpret_cast<const float4*>(&C->G1);   // G1 U1 V1 lam1
-    const float4 c2 = *reinterpret_cast<const float4*>(&C->bn);   // bn b1 inv cg1
-    const float4 c3 = *reinterpret_cast<const float4*>(&C->cgn);  // cgn refx refy
-    float a = u - c0.y, b = v - c0.z;
-    const float gn = c0.x * __expf(-c0.w * (a * a + b * b));
-    a = u - c1.y; b = v - c1.z;
-    const float g1 = c1.x * __expf(-c1.w * (a * a + b * b));
-    const float rr = u * c3.y + v * c3.z;
-    const float flh = au * (Xin_x.x - Xout_x.x) + av * (Xin_y.x - Xout_y.x) + rr * gr.x;
-    const float flb = au * (Xin_x.y - Xout_x.y) + av * (Xin_y.y - Xout_y.y) + rr * gr.y;
-    const float dh = c2.z * (flh + c2.w * ((g1 - gr.x) - fo_c.x) + c3.x * ((gn - gr.x) - fo_c.x));
-    const float db = c2.z * (flb + c2.w * ((c2.y * g1 - gr.y) - fo_c.y) + c3.x * ((c2.x * gn - gr.y) - fo_c.y));
-    if (act) {
-      float2 o;
-      o.x = fo_c.x + dh;
-      o.y = fo_c.y + db;
-      *pw = o;
+#pragma unroll
+    for (int t = 0; t < W; t++) {
+      if (t < wc) {
+        const float2 c = Cv[t + 1];
+        const float2 rx = vl_walk2(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
+        const float2 ry = vl_walk2(Pv[t + 1], c, Nv[t + 1]);
+        const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
+        const float2 Xox = strip_face(RXi + su * (t + 1), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
+        const float2 Xoy = strip_face(RY + cl(t), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
+        const float2 o = strip_collide(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
+        if (act) pw[col(t)] = o;
+        Xix = Xox;
+        Xiy[t] = Xoy;
+      }
     }
-    Xin_y = Xout_y;
-    fo_p = fo_c; fo_c = fo_n; fo_n = fo_nn;
-    fu_p = fu_c; fu_c = fu_n; fu_n = fu_nn;
-    fd = fd_n; fuu = fuu_n;
-    po += fstep; pw += fstep;
-    RXo += xstep; RYo += ystep; C += ystep;
+#pragma unroll
+    for (int p = 0; p <= W; p++) {
+      Pv[p] = Cv[p];
+      Cv[p] = Nv[p];
+      Nv[p] = NN[p];
+    }
+    cUU = nUU;
+    cD = nD;
+    pr += rs;
+    pw += rs;
   }
+  cp_async_wait<0>();
 }
 
-__global__ void __launch_bounds__(128, 8) k_walk(Params P, const float2* __restrict__ f,
-                                                 float2* __restrict__ fo,
-                                                 const FaceRecF* __restrict__ fxr,
-                                                 const FaceRecF* __restrict__ fyr,
-                                                 const CellRecF* __restrict__ cr, int nchunk_neg,
-                                                 int walk_rows) {
-  walk_body(P, f, fo, fxr, fyr, cr, nchunk_neg, walk_rows, blockIdx.x, blockIdx.y, blockIdx.z);
-}
 
 }  // namespace ugks
