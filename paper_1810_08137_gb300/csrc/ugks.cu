@@ -136,7 +136,7 @@ size_t predict_bytes(const ugks_config* c) {
     size_t want = (size_t)64 << 20;
     if (want < row_d) want = row_d;
     if (want > row_d * ny) want = row_d * ny;
-    b += want + sizeof(float2) * nq + sizeof(float) * (5 * (size_t)c->nv + 2 * (size_t)c->nu);
+    b += want + sizeof(float2) * nq + sizeof(float) * (6 * (size_t)c->nv + 2 * (size_t)c->nu);
     b += sizeof(SlotDev) + sizeof(BatchWork);
   }
   return b;
@@ -708,7 +708,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (want > row_d * P.ny) want = row_d * P.ny;
     h->stage_bytes = want;
     ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq) &&
-         alloc((void**)&h->ftab, sizeof(float) * (5 * (size_t)P.nv + 2 * (size_t)P.nu));
+         alloc((void**)&h->ftab, sizeof(float) * (6 * (size_t)P.nv + 2 * (size_t)P.nu));
   }
   if (!ok) {
     ugks_destroy(h);
@@ -727,18 +727,18 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.gref = h->gref;
   std::vector<float> ftab_host;
   if (h->ftab) {
-    ftab_host.resize(5 * (size_t)P.nv + 2 * (size_t)P.nu);
+    ftab_host.resize(6 * (size_t)P.nv + 2 * (size_t)P.nu);
     for (int m = 0; m < P.nv; m++) {
       const double vv = h->hv[m], w = h->hwv[m];
-      const double t[5] = {w, w * vv, w * vv * vv, w * vv * vv * vv, vv};
-      for (int c = 0; c < 5; c++) ftab_host[(size_t)c * P.nv + m] = (float)t[c];
+      const double t[6] = {w, w * vv, w * vv * vv, w * vv * vv * vv, vv, w * vv * vv * vv * vv};
+      for (int c = 0; c < 6; c++) ftab_host[(size_t)c * P.nv + m] = (float)t[c];
     }
     for (int k = 0; k < P.nu; k++) {
-      ftab_host[5 * (size_t)P.nv + k] = (float)h->hu[k];
-      ftab_host[5 * (size_t)P.nv + P.nu + k] = (float)h->hwu[k];
+      ftab_host[6 * (size_t)P.nv + k] = (float)h->hu[k];
+      ftab_host[6 * (size_t)P.nv + P.nu + k] = (float)h->hwu[k];
     }
     P.mvf = h->ftab;
-    P.uwf = h->ftab + 5 * (size_t)P.nv;
+    P.uwf = h->ftab + 6 * (size_t)P.nv;
   }
   auto setup = [&]() -> cudaError_t {
     cudaError_t r;

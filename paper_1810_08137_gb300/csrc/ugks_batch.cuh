@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
 
 // Update sweep: one warp per work item (strip, tile, velocity chunk), strips fastest so that
 // the warps of a block share neighbour columns.
-__global__ void __launch_bounds__(128) kb_strip(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 4) kb_strip(const SlotDev* __restrict__ slots,
                                                 const BatchWork* __restrict__ wk) {
   __shared__ __align__(16) float4 ring[kWarpsPerBlock][kRing * kStripChunks];
   const int warp = threadIdx.x >> 5;

@@ -91,7 +91,7 @@ struct Params {
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
   const void* gref;       // [nq] T2 table of g_ref (FP32 form), else null
   int omega_half;         // omega == 1/2: lam^-omega = rsqrt(lam)
-  const float* mvf;       // FP32 tables: [5][nv] wv, wv v, wv v^2, wv v^3, v
+  const float* mvf;       // FP32 tables: [6][nv] wv, wv v, wv v^2, wv v^3, v, wv v^4
   const float* uwf;       // FP32 tables: [2][nu] u, wu
   float f_tdx, f_tdy, f_idx, f_idy, f_dt;  // FP32 2/dx, 2/dy, 1/dx, 1/dy, dt
   const double* u;        // [nu]

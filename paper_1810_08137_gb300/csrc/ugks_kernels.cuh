@@ -43,9 +43,20 @@ __device__ __forceinline__ double vl_half(double a, double c, double b) {
   double d1 = c - a, d2 = b - c, p = d1 * d2;
   return p > 0.0 ? p / (d1 + d2) : 0.0;
 }
+// 2^x and 1/x with subnormal results flushed to zero (PTX approximate forms).
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float vl_half(float a, float c, float b) {
   float d1 = c - a, d2 = b - c, p = d1 * d2;
-  return p > 0.0f ? __fdividef(p, d1 + d2) : 0.0f;
+  return p > 0.0f ? p * rcp_ftz(d1 + d2) : 0.0f;
 }
 
 __device__ __forceinline__ double texp(double x) { return exp(x); }
@@ -197,12 +208,14 @@ __device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T
 }
 
 // velocity tables in the arithmetic type (FP32 tables are rounded from FP64 on the host)
+// o[n] = wv v^n, n = 0..4
 __device__ __forceinline__ void vtab(const Params& P, int m, double* o) {
   const double vv = P.v[m], w = P.wv[m];
-  o[0] = w; o[1] = w * vv; o[2] = w * vv * vv; o[3] = w * vv * vv * vv; o[4] = vv;
+  o[0] = w; o[1] = w * vv; o[2] = w * vv * vv; o[3] = w * vv * vv * vv; o[4] = w * vv * vv * vv * vv;
 }
 __device__ __forceinline__ void vtab(const Params& P, int m, float* o) {
-  for (int t = 0; t < 5; t++) o[t] = P.mvf[t * P.nv + m];
+  for (int t = 0; t < 4; t++) o[t] = P.mvf[t * P.nv + m];
+  o[4] = P.mvf[5 * P.nv + m];
 }
 __device__ __forceinline__ void utab(const Params& P, int k, double& u, double& wu) {
   u = P.u[k]; wu = P.wu[k];
@@ -218,7 +231,7 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
   T* mw = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(double));
-  // mw[0..4nv): wv, wv v, wv v^2, wv v^3 ; mw[4nv..5nv): v
+  // mw[n nv + m] = wv_m v_m^n, n = 0..4
   for (int m = tid; m < nv; m += blockDim.x) {
     T o[5];
     vtab(P, m, o);
@@ -245,6 +258,13 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
   if (sizeof(T) == 4) { tdx = (T)P.f_tdx; tdy = (T)P.f_tdy; }
   else { tdx = T(2.0 / P.dx); tdy = T(2.0 / P.dy); }
 
+  // Per lane (u_k) and per half of the v axis, weighted sums over the half's rows of the
+  // cell value c, the x half slope r_x and the y half slope r_y (w_n = wv v^n):
+  //   a_n = sum w_n c_h (n < 4), ab_n = sum w_n c_b (n < 2), x_n = sum w_n r_x,h (n < 4),
+  //   xb_n = sum w_n r_x,b (n < 2), y_n = sum w_n r_y,h (n < 5), yb_n = sum w_n r_y,b (n < 3).
+  // Every sum the faces need follows: the face values f -/+ r_y of the half give a_n -/+ y_n,
+  // and u sigma_x + v sigma_y = cu r_x + (2/dy) v r_y gives sum w_n (.) = cu x_n + (2/dy) y_{n+1}.
+  // The v = 0 row (H(0) = 1/2) enters both halves with half weight.
   for (int k0 = 0; k0 < nu; k0 += 32) {
     const int k = k0 + lane;
     const bool act = k < nu;
@@ -253,94 +273,91 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     utab(P, kk, u, wu);
     if (!act) wu = T(0);
     const T cu = u * tdx;
-    T A0 = 0, A1 = 0, A2 = 0, Ab = 0, R0 = 0, R1 = 0, R2 = 0, Rb = 0;
-    T C0 = 0, C1 = 0, C2 = 0, Cb = 0, D0 = 0, D1 = 0, D2 = 0, Db = 0;
-    T P0 = 0, P1 = 0, P2 = 0, P3 = 0, Pb0 = 0, Pb1 = 0, Q0 = 0, Q1 = 0, Q2 = 0, Qb = 0;
-    T Z1 = 0, Z2 = 0, Z3 = 0, Zb1 = 0;
-    // rows with v != 0 feed the S side (v < 0, f - r_y) or the N side (v > 0, f + r_y);
-    // the loops over each half have no branches, so loads of consecutive rows overlap
-    auto row = [&](int m, T sy) {
-      const T vv = mw[4 * nv + m];
+    T tA0 = 0, tA1 = 0, tA2 = 0, tAb = 0, tR0 = 0, tR1 = 0, tR2 = 0, tRb = 0;
+    T tC0 = 0, tC1 = 0, tC2 = 0, tC3 = 0, tCb0 = 0, tCb1 = 0;
+    T a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
+    auto zero = [&]() {
+      a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = T(0);
+      y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = T(0);
+    };
+    auto slopes = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
       const size_t q = (size_t)m * nu + kk;
-      const T2 c = fc[q], w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
-      T rxh = 0, rxb = 0, ryh = 0, ryb = 0;
+      c = fc[q];
+      const T2 w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
+      rxh = rxb = ryh = ryb = T(0);
       if (!zs) {
         rxh = vl_half(w.x, c.x, e.x);
         rxb = vl_half(w.y, c.y, e.y);
         ryh = vl_half(s.x, c.x, n.x);
         ryb = vl_half(s.y, c.y, n.y);
       }
-      const T cv = vv * tdy;
-      const T dh = cu * rxh + cv * ryh, db = cu * rxb + cv * ryb;
-      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m], w3 = mw[3 * nv + m];
-      A0 += w0 * c.x; A1 += w1 * c.x; A2 += w2 * c.x; Ab += w0 * c.y;
-      R0 += w0 * rxh; R1 += w1 * rxh; R2 += w2 * rxh; Rb += w0 * rxb;
-      C0 += w0 * ryh; C1 += w1 * ryh; C2 += w2 * ryh; Cb += w0 * ryb;
-      D0 += w0 * dh;  D1 += w1 * dh;  D2 += w2 * dh;  Db += w0 * db;
-      const T fyh = c.x + sy * ryh, fyb = c.y + sy * ryb;
-      P0 += w0 * fyh; P1 += w1 * fyh; P2 += w2 * fyh; P3 += w3 * fyh;
-      Pb0 += w0 * fyb; Pb1 += w1 * fyb;
-      Q0 += w0 * rxh; Q1 += w1 * rxh; Q2 += w2 * rxh; Qb += w0 * rxb;
-      Z1 += w1 * dh; Z2 += w2 * dh; Z3 += w3 * dh; Zb1 += w1 * db;
+    };
+    auto row = [&](int m) {
+      T rxh, rxb, ryh, ryb;
+      T2 c;
+      slopes(m, rxh, rxb, ryh, ryb, c);
+      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m], w3 = mw[3 * nv + m], w4 = mw[4 * nv + m];
+      a0 += w0 * c.x; a1 += w1 * c.x; a2 += w2 * c.x; a3 += w3 * c.x;
+      ab0 += w0 * c.y; ab1 += w1 * c.y;
+      x0 += w0 * rxh; x1 += w1 * rxh; x2 += w2 * rxh; x3 += w3 * rxh;
+      xb0 += w0 * rxb; xb1 += w1 * rxb;
+      y0 += w0 * ryh; y1 += w1 * ryh; y2 += w2 * ryh; y3 += w3 * ryh; y4 += w4 * ryh;
+      yb0 += w0 * ryb; yb1 += w1 * ryb; yb2 += w2 * ryb;
+    };
+    auto row_v0 = [&](int m) {  // v = 0: only the w_0 sums, half weight
+      T rxh, rxb, ryh, ryb;
+      T2 c;
+      slopes(m, rxh, rxb, ryh, ryb, c);
+      const T hw = T(0.5) * mw[m];
+      a0 += hw * c.x; ab0 += hw * c.y; x0 += hw * rxh; xb0 += hw * rxb; y0 += hw * ryh; yb0 += hw * ryb;
+    };
+    // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
+    auto close = [&](T sy, T* side) {
+      const T P0 = a0 + sy * y0, P1 = a1 + sy * y1, P2 = a2 + sy * y2, P3 = a3 + sy * y3;
+      const T Pb0 = ab0 + sy * yb0, Pb1 = ab1 + sy * yb1;
+      const T Z1 = cu * x1 + tdy * y2, Z2 = cu * x2 + tdy * y3, Z3 = cu * x3 + tdy * y4;
+      const T Zb1 = cu * xb1 + tdy * yb2;
+      finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, x0, x1, x2, xb0, Z1, Z2, Z3, Zb1, lane,
+                        side);
+      tA0 += a0; tA1 += a1; tA2 += a2; tAb += ab0;
+      tR0 += x0; tR1 += x1; tR2 += x2; tRb += xb0;
+      tC0 += y0; tC1 += y1; tC2 += y2; tC3 += y3; tCb0 += yb0; tCb1 += yb1;
     };
     const int mneg = P.m_neg, mpos = P.m_pos;
+    const bool v0 = mpos > mneg;
+    zero();
 #pragma unroll 2
-    for (int m = 0; m < mneg; m++) row(m, T(-1));
-    if (mpos > mneg) {
-      // the v = 0 row, H(0) = 1/2: half to the S side with f - r_y, half to the N side with
-      // f + r_y; the u_n = v weighted sums vanish
-      const int m = mneg;
-      const size_t q = (size_t)m * nu + kk;
-      const T2 c = fc[q], w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
-      T rxh = 0, rxb = 0, ryh = 0, ryb = 0;
-      if (!zs) {
-        rxh = vl_half(w.x, c.x, e.x);
-        rxb = vl_half(w.y, c.y, e.y);
-        ryh = vl_half(s.x, c.x, n.x);
-        ryb = vl_half(s.y, c.y, n.y);
-      }
-      const T dh = cu * rxh, db = cu * rxb;  // v = 0
-      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m];
-      A0 += w0 * c.x; A1 += w1 * c.x; A2 += w2 * c.x; Ab += w0 * c.y;
-      R0 += w0 * rxh; R1 += w1 * rxh; R2 += w2 * rxh; Rb += w0 * rxb;
-      C0 += w0 * ryh; C1 += w1 * ryh; C2 += w2 * ryh; Cb += w0 * ryb;
-      D0 += w0 * dh;  D1 += w1 * dh;  D2 += w2 * dh;  Db += w0 * db;
-      const T hw = T(0.5) * w0;
-      P0 += hw * (c.x - ryh); Pb0 += hw * (c.y - ryb); Q0 += hw * rxh; Qb += hw * rxb;
-      finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
-                        lane, wsum + kSumS);
-      P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
-      P0 += hw * (c.x + ryh); Pb0 += hw * (c.y + ryb); Q0 += hw * rxh; Qb += hw * rxb;
-    } else {
-      finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1,
-                        lane, wsum + kSumS);
-      P0 = P1 = P2 = P3 = Pb0 = Pb1 = Q0 = Q1 = Q2 = Qb = Z1 = Z2 = Z3 = Zb1 = 0;
-    }
+    for (int m = 0; m < mneg; m++) row(m);
+    if (v0) row_v0(mneg);
+    close(T(-1), wsum + kSumS);
+    zero();
+    if (v0) row_v0(mneg);
 #pragma unroll 2
-    for (int m = mpos; m < nv; m++) row(m, T(1));
-    finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, Q0, Q1, Q2, Qb, Z1, Z2, Z3, Zb1, lane,
-                      wsum + kSumN);
+    for (int m = mpos; m < nv; m++) row(m);
+    close(T(1), wsum + kSumN);
 
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
+    const T D0 = cu * tR0 + tdy * tC1, D1 = cu * tR1 + tdy * tC2, D2 = cu * tR2 + tdy * tC3;
+    const T Db = cu * tRb + tdy * tCb1;
     const T hE = u > T(0) ? T(1) : (u < T(0) ? T(0) : T(0.5));
     const T hW = u < T(0) ? T(1) : (u > T(0) ? T(0) : T(0.5));
-    T x[32];
+    T xv[32];
     const T uu = u * u;
 #pragma unroll
     for (int sd = 0; sd < 2; sd++) {
       const T sg = sd == 0 ? T(1) : T(-1);
       const T wgt = wu * (sd == 0 ? hE : hW);
-      const T F0 = A0 + sg * R0, F1 = A1 + sg * R1, F2 = A2 + sg * R2, Fb = Ab + sg * Rb;
-      T* o = x + 16 * sd;
+      const T F0 = tA0 + sg * tR0, F1 = tA1 + sg * tR1, F2 = tA2 + sg * tR2, Fb = tAb + sg * tRb;
+      T* o = xv + 16 * sd;
       o[0] = wgt * F0;
       o[1] = wgt * u * F0;
       o[2] = wgt * F1;
       o[3] = wgt * (T(0.5) * (uu * F0 + F2) + T(0.5) * Fb);
       const T ws = wgt * tdy;
-      o[4] = ws * C0;
-      o[5] = ws * u * C0;
-      o[6] = ws * C1;
-      o[7] = ws * (T(0.5) * (uu * C0 + C2) + T(0.5) * Cb);
+      o[4] = ws * tC0;
+      o[5] = ws * u * tC0;
+      o[6] = ws * tC1;
+      o[7] = ws * (T(0.5) * (uu * tC0 + tC2) + T(0.5) * tCb0);
       const T wuu = wgt * u;
       o[8] = wuu * F0;
       o[9] = wuu * u * F0;
@@ -351,7 +368,7 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       o[14] = wuu * D1;
       o[15] = wuu * (T(0.5) * (uu * D0 + D2) + T(0.5) * Db);
     }
-    const T r = warp_reduce_scatter<32>(x, lane);
+    const T r = warp_reduce_scatter<32>(xv, lane);
     wsum[kSumE + lane] += r;  // lanes 0..15: E side, 16..31: W side
   }
   __syncwarp();
@@ -1097,7 +1114,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 // Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + d (CellRecF).
 // -------------------------------------------------------------------------------------
 constexpr int kWalkRows = 64;  // default rows per walk tile
-constexpr int kStripW = 2;     // columns per strip
+constexpr int kStripW = 4;     // columns per strip
 constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
 constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
@@ -1114,17 +1131,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// 2^x and 1/x with subnormal results flushed to zero (PTX approximate forms).
-__device__ __forceinline__ float ex2_ftz(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_ftz(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // van Leer half slope of the walk-ordered stencil (a, c, b), both components.
 __device__ __forceinline__ float vl_walk(float a, float c, float b) {
