@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -46,7 +47,7 @@ struct ugks_ctx {
   double* rpart = nullptr;
   int nrblocks = 0;
   int* err = nullptr;
-  double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv]
+  double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv], [5][nv] wv v^n
   double* stage = nullptr;   // FP64 staging for FP32 state conversion
   float2* gref = nullptr;    // FP32 form: g_ref per velocity
   float* ftab = nullptr;     // FP32 form: velocity tables (mvf, uwf)
@@ -130,7 +131,7 @@ size_t predict_bytes(const ugks_config* c) {
   b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : sizeof(FaceRec) * (nfx + nfy);
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
   b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
-  b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * 2 * (c->nu + c->nv);
+  b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * (2 * (c->nu + c->nv) + 5 * c->nv);
   if (f32) {
     const size_t row_d = nx * nq * 2 * sizeof(double);
     size_t want = (size_t)64 << 20;
@@ -144,7 +145,8 @@ size_t predict_bytes(const ugks_config* c) {
 
 template <typename T>
 size_t smem_sums(int nv) {
-  return kWarpsPerBlock * kNSum * sizeof(double) + 5 * (size_t)nv * sizeof(T);
+  (void)nv;
+  return sums_smem_bytes<T>();
 }
 template <typename T>
 size_t smem_update(int nv) {
@@ -425,7 +427,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   P.wx = cfg->nx + 2;
   P.dx = cfg->lx / cfg->nx;
   P.dy = cfg->ly / cfg->ny;
-  double grid[4 * kMaxAxis];
+  double grid[4 * kMaxAxis + 5 * kMaxAxis];  // u, v, wu, wv, then [5][nv] wv v^n
   double* hu = grid;
   double* hv = grid + P.nu;
   double* hwu = grid + P.nu + P.nv;
@@ -440,6 +442,10 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   };
   fill_axis(P.nu, cfg->umin, cfg->umax, hu, hwu);
   fill_axis(P.nv, cfg->vmin, cfg->vmax, hv, hwv);
+  double* hwn = grid + 2 * (P.nu + P.nv);
+  for (int n = 0; n < 5; n++)
+    for (int m = 0; m < P.nv; m++) hwn[n * P.nv + m] = hwv[m] * std::pow(hv[m], n);
+  const int ngrid = 2 * (P.nu + P.nv) + 5 * P.nv;  // doubles in the grid block
   double um = 0, vm = 0;
   for (int k = 0; k < P.nu; k++) um = fmax(um, fabs(hu[k]));
   for (int m = 0; m < P.nv; m++) vm = fmax(vm, fabs(hv[m]));
@@ -490,7 +496,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
                          sizeof(FaceRec) * (size_t)nfy, sizeof(double) * 4 * (size_t)nfx,
                          sizeof(double) * 4 * (size_t)nfy, sizeof(double) * (size_t)(nfx + nfy),
                          sizeof(CellRec) * (size_t)nc, sizeof(double) * 8 * (size_t)nrb,
-                         sizeof(double) * 2 * (P.nu + P.nv) + sizeof(int)};
+                         sizeof(double) * ngrid + sizeof(int)};
   for (int b = 0; b < 13; b++) { off[b] = need; need += align256(sz[b]); }
   if (need > UGKS_NOALLOC_SCRATCH_BYTES) {
     fprintf(stderr, "ugks_step_noalloc: problem needs %zu bytes of scratch, the fixed maximum is %u\n",
@@ -517,7 +523,8 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   CellRec* cells = reinterpret_cast<CellRec*>(sb + off[10]);
   double* rpart = reinterpret_cast<double*>(sb + off[11]);
   double* dgrid = reinterpret_cast<double*>(sb + off[12]);
-  int* err = reinterpret_cast<int*>(dgrid + 2 * (P.nu + P.nv));
+  int* err = reinterpret_cast<int*>(dgrid + ngrid);
+  P.mvd = dgrid + 2 * (P.nu + P.nv);
   P.u = dgrid;
   P.v = dgrid + P.nu;
   P.wu = dgrid + P.nu + P.nv;
@@ -531,7 +538,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
       return UGKS_ECUDA;                                                                \
     }                                                                                   \
   } while (0)
-  NA_CK(cudaMemcpyAsync(dgrid, grid, sizeof(double) * 2 * (P.nu + P.nv), cudaMemcpyHostToDevice, st));
+  NA_CK(cudaMemcpyAsync(dgrid, grid, sizeof(double) * ngrid, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
   // the previous call's contents stay in the array: clear the f ring so every cell the
   // kernels read is defined
@@ -700,7 +707,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
                  : alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc)) &&
             alloc((void**)&h->rpart, sizeof(double) * 8 * (size_t)h->nrblocks) &&
             alloc((void**)&h->err, sizeof(int)) &&
-            alloc((void**)&h->d_grid, sizeof(double) * 2 * (P.nu + P.nv));
+            alloc((void**)&h->d_grid, sizeof(double) * (2 * (P.nu + P.nv) + 5 * P.nv));
   if (ok && h->prec == UGKS_FP32F) {
     const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
     size_t want = (size_t)64 << 20;
@@ -720,6 +727,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   grid.insert(grid.end(), h->hv.begin(), h->hv.end());
   grid.insert(grid.end(), h->hwu.begin(), h->hwu.end());
   grid.insert(grid.end(), h->hwv.begin(), h->hwv.end());
+  for (int n = 0; n < 5; n++)
+    for (int m = 0; m < P.nv; m++) grid.push_back(h->hwv[m] * std::pow(h->hv[m], n));
+  P.mvd = h->d_grid + 2 * (P.nu + P.nv);
   P.u = h->d_grid;
   P.v = h->d_grid + P.nu;
   P.wu = h->d_grid + P.nu + P.nv;
@@ -987,7 +997,7 @@ struct ugks_batch_ctx {
 
 namespace {
 
-constexpr size_t kBatchSumsSmem = kWarpsPerBlock * kNSum * sizeof(double) + 5 * kMaxAxis * sizeof(float);
+constexpr size_t kBatchSumsSmem = sums_smem_bytes<float>();
 
 ugks_status bfail(ugks_batch_ctx* b, ugks_status s, const std::string& m) {
   if (b) b->last_error = m;

@@ -85,12 +85,11 @@ __global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* _
   }
 }
 
-__global__ void __launch_bounds__(128, 6) kb_sums(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 7) kb_sums(const SlotDev* __restrict__ slots,
                                                const BatchWork* __restrict__ wk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int total = wk->start[2][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    __syncthreads();  // the previous virtual block's tables are no longer in use
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     sums_body<float, float2>(S.P, S.f[S.cur], S.sums, smraw, vb - wk->start[2][a]);

@@ -1,6 +1,7 @@
 // Internal device-side data structures of the UGKS library (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace ugks {
@@ -17,6 +18,12 @@ constexpr int kWarpsPerBlock = 4;    // warp-per-cell kernels: 4 cells per 128-t
 // A face's sums are the E (N) side of its low cell plus the W (S) side of its high cell.
 enum { kSumE = 0, kSumW = 16, kSumN = 32, kSumS = 48, kNSum = 64 };
 enum { kOffW0 = 0, kOffSt = 4, kOffSf = 8, kOffSs = 12 };
+constexpr int kSumsTotals = 14;    // per-thread totals of the sums kernel (shared memory)
+// dynamic shared memory of the sums kernel: per-warp sums, per-thread totals
+template <typename T>
+constexpr size_t sums_smem_bytes() {
+  return (kWarpsPerBlock * kNSum + kSumsTotals * 128) * sizeof(T);
+}
 
 // What the update kernel needs about one face (written by the face kernel).
 // Micro flux in the face frame (u_n normal, u_t tangential), per component c (h, b):
@@ -93,6 +100,7 @@ struct Params {
   int omega_half;         // omega == 1/2: lam^-omega = rsqrt(lam)
   const float* mvf;       // FP32 tables: [6][nv] wv, wv v, wv v^2, wv v^3, v, wv v^4
   const float* uwf;       // FP32 tables: [2][nu] u, wu
+  const double* mvd;      // [5][nv] wv v^n, n = 0..4
   float f_tdx, f_tdy, f_idx, f_idy, f_dt;  // FP32 2/dx, 2/dy, 1/dx, 1/dy, dt
   const double* u;        // [nu]
   const double* v;        // [nv]

@@ -54,6 +54,22 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// 16-byte asynchronous global -> shared copies (per thread), in commit groups.
+__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gm) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async8(void* sm, const void* gm) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(a), "l"(gm) : "memory");
+}
+// one f value (float2: 8 bytes, double2: 16 bytes)
+__device__ __forceinline__ void cp_async_f(float2* sm, const float2* gm) { cp_async8(sm, gm); }
+__device__ __forceinline__ void cp_async_f(double2* sm, const double2* gm) { cp_async16(sm, gm); }
+
 __device__ __forceinline__ float vl_half(float a, float c, float b) {
   float d1 = c - a, d2 = b - c, p = d1 * d2;
   return p > 0.0f ? p * rcp_ftz(d1 + d2) : 0.0f;
@@ -208,14 +224,15 @@ __device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T
 }
 
 // velocity tables in the arithmetic type (FP32 tables are rounded from FP64 on the host)
-// o[n] = wv v^n, n = 0..4
-__device__ __forceinline__ void vtab(const Params& P, int m, double* o) {
-  const double vv = P.v[m], w = P.wv[m];
-  o[0] = w; o[1] = w * vv; o[2] = w * vv * vv; o[3] = w * vv * vv * vv; o[4] = w * vv * vv * vv * vv;
+// wv v^n, n = 0..4, of row m (global tables, L1 resident)
+__device__ __forceinline__ void wtab(const Params& P, int m, double* o) {
+#pragma unroll
+  for (int n = 0; n < 5; n++) o[n] = __ldg(P.mvd + n * P.nv + m);
 }
-__device__ __forceinline__ void vtab(const Params& P, int m, float* o) {
-  for (int t = 0; t < 4; t++) o[t] = P.mvf[t * P.nv + m];
-  o[4] = P.mvf[5 * P.nv + m];
+__device__ __forceinline__ void wtab(const Params& P, int m, float* o) {
+#pragma unroll
+  for (int n = 0; n < 4; n++) o[n] = __ldg(P.mvf + n * P.nv + m);
+  o[4] = __ldg(P.mvf + 5 * P.nv + m);
 }
 __device__ __forceinline__ void utab(const Params& P, int k, double& u, double& wu) {
   u = P.u[k]; wu = P.wu[k];
@@ -230,15 +247,10 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
   const int nv = P.nv, nu = P.nu, nq = P.nq;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
-  T* mw = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(double));
-  // mw[n nv + m] = wv_m v_m^n, n = 0..4
-  for (int m = tid; m < nv; m += blockDim.x) {
-    T o[5];
-    vtab(P, m, o);
-    for (int t = 0; t < 5; t++) mw[t * nv + m] = o[t];
-  }
+  // per-thread totals over both halves, [14][128] (touched twice per u chunk)
+  T* tot = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(T)) + tid;
   for (int t = lane; t < kNSum; t += 32) wsum[t] = T(0);
-  __syncthreads();
+  __syncwarp();
 
   const int ncx = P.nx + 2;
   const int cell = bx * kWarpsPerBlock + warp;
@@ -258,6 +270,8 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
   if (sizeof(T) == 4) { tdx = (T)P.f_tdx; tdy = (T)P.f_tdy; }
   else { tdx = T(2.0 / P.dx); tdy = T(2.0 / P.dy); }
 
+  const int mneg = P.m_neg, mpos = P.m_pos;
+  const bool v0 = mpos > mneg;
   // Per lane (u_k) and per half of the v axis, weighted sums over the half's rows of the
   // cell value c, the x half slope r_x and the y half slope r_y (w_n = wv v^n):
   //   a_n = sum w_n c_h (n < 4), ab_n = sum w_n c_b (n < 2), x_n = sum w_n r_x,h (n < 4),
@@ -273,17 +287,18 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     utab(P, kk, u, wu);
     if (!act) wu = T(0);
     const T cu = u * tdx;
-    T tA0 = 0, tA1 = 0, tA2 = 0, tAb = 0, tR0 = 0, tR1 = 0, tR2 = 0, tRb = 0;
-    T tC0 = 0, tC1 = 0, tC2 = 0, tC3 = 0, tCb0 = 0, tCb1 = 0;
+    // totals: tA0 tA1 tA2 tAb tR0 tR1 tR2 tRb tC0 tC1 tC2 tC3 tCb0 tCb1
+#pragma unroll
+    for (int t = 0; t < kSumsTotals; t++) tot[t * 128] = T(0);
     T a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
     auto zero = [&]() {
       a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = T(0);
       y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = T(0);
     };
     auto slopes = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
-      const size_t q = (size_t)m * nu + kk;
-      c = fc[q];
-      const T2 w = fc[q - nq], e = fc[q + nq], s = fc[q - rs], n = fc[q + rs];
+      const T2* src = fc + (size_t)m * nu + kk;
+      c = src[0];
+      const T2 w = src[-nq], e = src[nq], s = src[-(long)rs], n = src[rs];
       rxh = rxb = ryh = ryb = T(0);
       if (!zs) {
         rxh = vl_half(w.x, c.x, e.x);
@@ -296,7 +311,9 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       T rxh, rxb, ryh, ryb;
       T2 c;
       slopes(m, rxh, rxb, ryh, ryb, c);
-      const T w0 = mw[m], w1 = mw[nv + m], w2 = mw[2 * nv + m], w3 = mw[3 * nv + m], w4 = mw[4 * nv + m];
+      T wn[5];
+      wtab(P, m, wn);
+      const T w0 = wn[0], w1 = wn[1], w2 = wn[2], w3 = wn[3], w4 = wn[4];
       a0 += w0 * c.x; a1 += w1 * c.x; a2 += w2 * c.x; a3 += w3 * c.x;
       ab0 += w0 * c.y; ab1 += w1 * c.y;
       x0 += w0 * rxh; x1 += w1 * rxh; x2 += w2 * rxh; x3 += w3 * rxh;
@@ -308,7 +325,9 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       T rxh, rxb, ryh, ryb;
       T2 c;
       slopes(m, rxh, rxb, ryh, ryb, c);
-      const T hw = T(0.5) * mw[m];
+      T wn[5];
+      wtab(P, m, wn);
+      const T hw = T(0.5) * wn[0];
       a0 += hw * c.x; ab0 += hw * c.y; x0 += hw * rxh; xb0 += hw * rxb; y0 += hw * ryh; yb0 += hw * ryb;
     };
     // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
@@ -319,24 +338,24 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       const T Zb1 = cu * xb1 + tdy * yb2;
       finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, x0, x1, x2, xb0, Z1, Z2, Z3, Zb1, lane,
                         side);
-      tA0 += a0; tA1 += a1; tA2 += a2; tAb += ab0;
-      tR0 += x0; tR1 += x1; tR2 += x2; tRb += xb0;
-      tC0 += y0; tC1 += y1; tC2 += y2; tC3 += y3; tCb0 += yb0; tCb1 += yb1;
+      const T h[kSumsTotals] = {a0, a1, a2, ab0, x0, x1, x2, xb0, y0, y1, y2, y3, yb0, yb1};
+#pragma unroll
+      for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
     };
-    const int mneg = P.m_neg, mpos = P.m_pos;
-    const bool v0 = mpos > mneg;
     zero();
-#pragma unroll 2
+#pragma unroll 1
     for (int m = 0; m < mneg; m++) row(m);
     if (v0) row_v0(mneg);
     close(T(-1), wsum + kSumS);
     zero();
     if (v0) row_v0(mneg);
-#pragma unroll 2
+#pragma unroll 1
     for (int m = mpos; m < nv; m++) row(m);
     close(T(1), wsum + kSumN);
-
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
+    const T tA0 = tot[0], tA1 = tot[128], tA2 = tot[256], tAb = tot[384], tR0 = tot[512];
+    const T tR1 = tot[640], tR2 = tot[768], tRb = tot[896], tC0 = tot[1024], tC1 = tot[1152];
+    const T tC2 = tot[1280], tC3 = tot[1408], tCb0 = tot[1536], tCb1 = tot[1664];
     const T D0 = cu * tR0 + tdy * tC1, D1 = cu * tR1 + tdy * tC2, D2 = cu * tR2 + tdy * tC3;
     const T Db = cu * tRb + tdy * tCb1;
     const T hE = u > T(0) ? T(1) : (u < T(0) ? T(0) : T(0.5));
@@ -1122,14 +1141,6 @@ constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-// 16-byte asynchronous global -> shared copies (per thread), in commit groups.
-__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gm) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 
 // van Leer half slope of the walk-ordered stencil (a, c, b), both components.
