@@ -44,6 +44,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# FP64 arithmetic peak of the part: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x
+# 2.07 GHz (unit counts and maximum clock; no FP64 peak is measured by the driver).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# Nominal FP64 arithmetic of the update (S6, S8, Eq. 3) per velocity-cell, exp and divide
+# counted as one operation each: 2 van Leer slopes x 2 components (20), upwind face values
+# (4), u sigma_x + v sigma_y (6), 2 face fluxes (39 each: Maxwellian 8, Q_h 15, Q_b 6,
+# X 10), collision (42).
+UPDATE_FLOPS_PER_VC = 150
+# DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
+# capture summarised in profiles/; None when the kernel has changed since that capture.
+UPDATE_TRAFFIC_PER_VC = 1223.76e6 / 62.72e6  # 400x200x28^2 capture: 750.08 MB read + 473.68 MB written
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -98,12 +111,13 @@ def dist():
 
 
 def run_form(ugks, torch, cfg, prec, steps, warmup, stream, prim):
-    """Time `steps` device-resident UGKS steps; per-kernel times from the library's events."""
+    """Time `steps` device-resident UGKS steps as the library runs them (one CUDA graph
+    replay per step), then the same number of steps again with the library's per-kernel
+    events (direct launches, one event between kernels) for the kernel breakdown."""
     s = ugks.Solver(cfg, prec, stream=stream.cuda_stream)
     s.init_maxwellian(*prim)
     s.step(warmup)
     s.sync()
-    s.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -112,10 +126,16 @@ def run_form(ugks, torch, cfg, prec, steps, warmup, stream, prim):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
+    s.profile(True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_prof = e0.elapsed_time(e1)
     kt = s.kernel_times()
     s.profile(False)
     s.sync()
-    return s, ms, kt
+    return s, ms, ms_prof, kt
 
 
 def e2e_form(ugks, torch, cfg, prec, steps, stream, f_host, W_host):
@@ -257,7 +277,7 @@ def reference_arm(args, cfg, prim):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="fp32f", choices=["fp32f", "fp64"])
@@ -303,12 +323,14 @@ def main():
     results = {}
     with torch.cuda.stream(stream):
         for prec in (other_prec, main_prec):
+            # the plain FP64 form is ~40x slower per step: time fewer of its steps
+            n = args.steps if prec == main_prec else max(3, min(args.steps, 10))
             barrier()
             with Clocks(local) as clk:
-                s, ms, kt = run_form(ugks, torch, cfg, prec, args.steps, args.warmup, stream, prim)
+                s, ms, ms_prof, kt = run_form(ugks, torch, cfg, prec, n, args.warmup, stream, prim)
             barrier()
             ms = max_over_ranks(ms)
-            results[prec] = (ms, kt, clk.summary())
+            results[prec] = (ms, ms_prof, kt, clk.summary(), n)
             if prec == main_prec:
                 f_host_t, f_host = pinned(torch, (cfg.nc, cfg.nq, 2))
                 W_host_t, W_host = pinned(torch, (4, cfg.nc))
@@ -329,29 +351,38 @@ def main():
         serving = None if (args.no_serve or ws > 1) else serve_bench(ugks, stream)
 
     def form_json(prec):
-        ms, kt, clk = results[prec]
+        ms, ms_prof, kt, clk, n = results[prec]
         bpv = 8 if prec == ugks.FP32F else 16  # bytes per velocity-cell of f (h, b)
         n_up, t_up = kt["update"]
         n_sm, t_sm = kt["sums"]
+        t_launch = t_up / n_up * 1e-3  # seconds per update launch
         # algorithmic bytes: update reads f once and writes it once, sums reads f once
-        ach_up = 2 * bpv * cfg.vc / (t_up / n_up * 1e-3) / 1e9
+        ach_up = 2 * bpv * cfg.vc / t_launch / 1e9
         ach_sm = bpv * cfg.vc / (t_sm / n_sm * 1e-3) / 1e9
         step_bytes = 3 * bpv * cfg.vc
-        out = {
-            "value": ws * cfg.vc * args.steps / (ms * 1e-3),
-            "ms_per_step": ms / args.steps,
+        if prec == ugks.FP32F:
+            traffic = None if UPDATE_TRAFFIC_PER_VC is None else UPDATE_TRAFFIC_PER_VC * cfg.vc
+            roof = {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
+                    "unit": "GB/s", "frac": ach_up / hbm, "traffic": traffic,
+                    "peak_source": hbm_src, "algorithmic_bytes_per_vc": 2 * bpv}
+        else:
+            ach = UPDATE_FLOPS_PER_VC * cfg.vc / t_launch / 1e9
+            roof = {"bound": "alu", "kernel": "update", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
+                    "unit": "GFLOP/s (FP64)", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                    "nominal_flops_per_vc": UPDATE_FLOPS_PER_VC, "hbm_frac": ach_up / hbm}
+        return {
+            "value": ws * cfg.vc * n / (ms * 1e-3),
+            "ms_per_step": ms / n,
+            "steps": n,
+            "ms_per_step_profiled": ms_prof / n,
             "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS},
-            "roofline": {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
-                         "unit": "GB/s", "frac": ach_up / hbm, "traffic": None,
-                         "peak_source": hbm_src,
-                         "algorithmic_bytes_per_vc": 2 * bpv},
+            "roofline": roof,
             "roofline_sums": {"achieved": ach_sm, "frac": ach_sm / hbm, "unit": "GB/s",
                               "algorithmic_bytes_per_vc": bpv},
-            "step_hbm_frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm,
+            "step_hbm_frac": step_bytes / (ms / n * 1e-3) / 1e9 / hbm,
             "clocks": clk,
         }
-        return out
-
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -375,15 +406,18 @@ def main():
         "kernel_ms_per_step": main["kernel_ms_per_step"],
         "roofline_sums": main["roofline_sums"],
         "step_hbm_frac": main["step_hbm_frac"],
+        "ms_per_step_profiled": main["ms_per_step_profiled"],
         "other_form": {"precision": "fp64" if other_prec == ugks.FP64 else "fp32f",
                        "value": other["value"], "ms_per_step": other["ms_per_step"],
+                       "steps": other["steps"],
                        "kernel_ms_per_step": other["kernel_ms_per_step"],
-                       "roofline": other["roofline"], "clocks": other["clocks"]},
+                       "roofline": other["roofline"], "step_hbm_frac": other["step_hbm_frac"],
+                       "clocks": other["clocks"]},
         "vs_fp64": (main["value"] / other["value"]) if main_prec == ugks.FP32F else 1.0,
         "clocks": main["clocks"],
         "e2e": {"value": ws * cfg.vc * args.e2e_steps / t_e2e, "unit": UNIT,
                 "steps": args.e2e_steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 7 * args.steps,  # 6 phase kernels + the buffer flip per step
         "cpu_baseline": cpu,
         "batch": batch,
         "serving": serving,

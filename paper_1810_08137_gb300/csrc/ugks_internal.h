@@ -67,15 +67,16 @@ struct __align__(16) FaceRecF {
   float E[4];
   float Mt4, Mt5, wall, gdt;
 };
-// Eq. 3 as an increment e^{n+1} = e^n + d, per component:
-//   d_h = aui dX_h + avi dY_h + A1 g1 + An gn + c g_ref,h - Bs e_h
-//   d_b = aui dX_b + avi dY_b + A1b g1 + Anb gn + c g_ref,b - Bs e_b
+// Eq. 3 as an increment e^{n+1} = e^n + d, per component, with the Maxwellians taken
+// relative to g_ref before they are weighted (the terms stay at the deviation's scale):
+//   d_h = aui dX_h + avi dY_h + r g_ref,h + A1 (g1 - g_ref,h) + An (gn - g_ref,h) - Bs e_h
+//   d_b = aui dX_b + avi dY_b + r g_ref,b + A1 (b1 g1 - g_ref,b) + An (bn gn - g_ref,b) - Bs e_b
 // with gn = 2^(En . (1, u, v, r2)), g1 likewise, aui = inv |u|/dx, avi = inv |v|/dy,
-// c = u irx + v iry - Bs, dX / dY the inflow minus outflow micro flux in x / y.
+// r = u irx + v iry, dX / dY the inflow minus outflow micro flux in x / y.
 struct __align__(16) CellRecF {
   float En[4];
   float E1[4];
-  float A1, An, A1b, Anb;   // inv cg1, inv cgn, inv cg1 b1, inv cgn bn
+  float A1, An, b1, bn;     // inv cg1, inv cgn, K/(2 lam^{n+1}), K/(2 lam^n)
   float Bs, irx, iry, inv;  // inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 

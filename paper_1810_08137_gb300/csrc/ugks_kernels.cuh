@@ -830,8 +830,8 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       F.E1[3] = (float)(-l1 * kLog2e);
       F.A1 = (float)(R.inv * R.cg1);
       F.An = (float)(R.inv * R.cgn);
-      F.A1b = (float)(R.inv * R.cg1 * R.b1);
-      F.Anb = (float)(R.inv * R.cgn * R.bn);
+      F.b1 = (float)R.b1;
+      F.bn = (float)R.bn;
       F.Bs = (float)(R.inv * (R.cg1 + R.cgn));
       F.irx = (float)(R.inv * refx);
       F.iry = (float)(R.inv * refy);
@@ -1199,15 +1199,15 @@ __device__ __forceinline__ float2 strip_collide(const CellRecF* C, const StripLa
                                                 float2 Xix, float2 Xox, float2 Xiy, float2 Xoy) {
   const float4 en = ld4(&C->En[0]);
   const float4 e1 = ld4(&C->E1[0]);
-  const float4 A = ld4(&C->A1);    // A1 An A1b Anb
+  const float4 A = ld4(&C->A1);    // A1 An b1 bn
   const float4 B = ld4(&C->Bs);    // Bs irx iry inv
   const float gn = exp_poly(en, L), g1 = exp_poly(e1, L);
-  const float c = fmaf(L.v, B.z, fmaf(L.u, B.y, -B.x));
+  const float r = fmaf(L.v, B.z, L.u * B.y);
   const float aui = L.au * B.w, avi = L.av * B.w;
   float dh = fmaf(aui, Xix.x - Xox.x, avi * (Xiy.x - Xoy.x));
   float db = fmaf(aui, Xix.y - Xox.y, avi * (Xiy.y - Xoy.y));
-  dh = fmaf(A.x, g1, fmaf(A.y, gn, fmaf(c, L.gr.x, fmaf(-B.x, e.x, dh))));
-  db = fmaf(A.z, g1, fmaf(A.w, gn, fmaf(c, L.gr.y, fmaf(-B.x, e.y, db))));
+  dh = fmaf(A.x, g1 - L.gr.x, fmaf(A.y, gn - L.gr.x, fmaf(r, L.gr.x, fmaf(-B.x, e.x, dh))));
+  db = fmaf(A.x, fmaf(A.z, g1, -L.gr.y), fmaf(A.y, fmaf(A.w, gn, -L.gr.y), fmaf(r, L.gr.y, fmaf(-B.x, e.y, db))));
   return make_float2(e.x + dh, e.y + db);
 }
 
