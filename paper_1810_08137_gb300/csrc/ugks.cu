@@ -120,6 +120,17 @@ const char* validate(const ugks_config* c) {
   return nullptr;
 }
 
+// Derived constants of P (after K, dx, dy, dt and mu_ref are set).
+void set_derived(Params& P) {
+  P.inv_kp2 = 1.0 / (P.K + 2);
+  P.half_dt_mu = P.dt / (2.0 * P.mu_ref);
+  P.quarter_dt_mu = P.dt / (4.0 * P.mu_ref);
+  P.d_tdx = 2.0 / P.dx;
+  P.d_tdy = 2.0 / P.dy;
+  P.d_idx = 1.0 / P.dx;
+  P.d_idy = 1.0 / P.dy;
+}
+
 // Device bytes ugks_create allocates for cfg (cudaMalloc sizes, without allocator rounding).
 size_t predict_bytes(const ugks_config* c) {
   const size_t nx = c->nx, ny = c->ny, nq = (size_t)c->nu * c->nv, nc = nx * ny;
@@ -458,6 +469,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
   P.omega_half = om == 0.5;
+  set_derived(P);
   for (int sd = 0; sd < 4; sd++) {
     P.bc_kind[sd] = cfg->bc[sd].kind;
     P.bc_rho[sd] = cfg->bc[sd].rho;
@@ -612,6 +624,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
   P.omega_half = om == 0.5;
+  set_derived(P);
   P.f_tdx = (float)(2.0 / P.dx);
   P.f_tdy = (float)(2.0 / P.dy);
   P.f_idx = (float)(1.0 / P.dx);

@@ -99,6 +99,9 @@ struct Params {
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
   const void* gref;       // [nq] T2 table of g_ref (FP32 form), else null
   int omega_half;         // omega == 1/2: lam^-omega = rsqrt(lam)
+  // derived FP64 constants (set by set_derived): 1/(K+2), dt/(2 mu_ref), dt/(4 mu_ref),
+  // 2/dx, 2/dy, 1/dx, 1/dy
+  double inv_kp2, half_dt_mu, quarter_dt_mu, d_tdx, d_tdy, d_idx, d_idy;
   const float* mvf;       // FP32 tables: [6][nv] wv, wv v, wv v^2, wv v^3, v, wv v^4
   const float* uwf;       // FP32 tables: [2][nu] u, wu
   const double* mvd;      // [5][nv] wv v^n, n = 0..4

@@ -124,18 +124,29 @@ __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int 
   const T2* src = f + fcell(P, si, sj) * P.nq;
   const int sw = wcell(P, wi, wj);
   if (kind == 2) {  // pressure: Maxwellian(rho_bc, U and V of the adjacent cell, T_bc)
+    // both Maxwellians factor into a u part and a v part: per-axis tables in shared memory
+    __shared__ double fu[kMaxAxis], fv[kMaxAxis], ru[kMaxAxis], rv[kMaxAxis];
     const double rho_a = W[sw], U = W[nwe + sw] / rho_a, V = W[2 * nwe + sw] / rho_a;
     const double lam = 1.0 / P.bc_T[side], rho = P.bc_rho[side];
     const double G = rho * lam / kPi, bf = P.K / (2.0 * lam);
+    __syncthreads();  // the tables of the previous cell are no longer read
+    for (int k = threadIdx.x; k < P.nu; k += blockDim.x) {
+      const double du = P.u[k] - U, dr = P.u[k] - P.ref_U;
+      fu[k] = G * exp(-lam * du * du);
+      ru[k] = P.use_ref ? P.ref_G * exp(-P.ref_lam * dr * dr) : 0.0;
+    }
+    for (int m = threadIdx.x; m < P.nv; m += blockDim.x) {
+      const double dv = P.v[m] - V, dr = P.v[m] - P.ref_V;
+      fv[m] = exp(-lam * dv * dv);
+      rv[m] = exp(-P.ref_lam * dr * dr);
+    }
+    __syncthreads();
     for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
       const int k = q % P.nu, m = q / P.nu;
-      const double du = P.u[k] - U, dv = P.v[m] - V;
-      const double gh = G * exp(-lam * (du * du + dv * dv));
-      double rh = 0.0, rb = 0.0;
-      ref_maxwellian(P, P.u[k], P.v[m], rh, rb);
+      const double gh = fu[k] * fv[m], rh = ru[k] * rv[m];
       T2 o;
       o.x = gh - rh;
-      o.y = bf * gh - rb;
+      o.y = bf * gh - P.ref_bf * rh;
       dst[q] = o;
     }
     if (write_W && threadIdx.x == 0) {
@@ -409,13 +420,16 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
 // Moments <x^n>, n = 0..6, of the normalised 1D Gaussian sqrt(lam/pi) exp(-lam (x-U)^2):
 // full range, x > 0 and x < 0.  Integration by parts gives
 // <x^{n+2}> = U <x^{n+1}> + (n+1)/(2 lam) <x^n> on every range.
-__device__ void gauss_moments7(double U, double lam, double* M, double* Mp, double* Mn) {
-  const double h = 0.5 / lam;
+// h = 1/(2 lam).  One erfc: the half-range mass on the far side of U is erfc(sqrt(lam)|U|)/2,
+// the near side 1 minus that.
+__device__ void gauss_moments7(double U, double lam, double h, double* M, double* Mp, double* Mn) {
+  const double sl = sqrt(lam);
   const double e = exp(-lam * U * U) * 0.5 * rsqrt(kPi * lam);
+  const double far = 0.5 * erfc(sl * fabs(U));
   M[0] = 1.0;
   M[1] = U;
-  Mp[0] = 0.5 * erfc(-sqrt(lam) * U);
-  Mn[0] = 0.5 * erfc(sqrt(lam) * U);
+  Mp[0] = U >= 0.0 ? 1.0 - far : far;
+  Mn[0] = U >= 0.0 ? far : 1.0 - far;
   Mp[1] = U * Mp[0] + e;
   Mn[1] = U * Mn[0] - e;
 #pragma unroll
@@ -427,8 +441,7 @@ __device__ void gauss_moments7(double U, double lam, double* M, double* Mp, doub
 }
 
 // Full-range moments only (tangential axis).
-__device__ void gauss_moments7_full(double U, double lam, double* M) {
-  const double h = 0.5 / lam;
+__device__ void gauss_moments7_full(double U, double h, double* M) {
   M[0] = 1.0;
   M[1] = U;
 #pragma unroll
@@ -468,10 +481,10 @@ __device__ void apsi_mom(const double* Mu, const double* Mv, double X2, double X
 
 // Micro-slope solve <psi (a . psi)> = s for the normalised Maxwellian (U, V, lam), closed
 // form obtained by centring the moments.
-__device__ void micro_slope(double U, double V, double lam, int K, const double* s, double* a) {
-  // q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass
-  const double Kp2 = K + 2.0, q = Kp2 * (0.25 / lam);
-  const double a4 = lam / q * (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - 2.0 * q));
+// q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass, c4 = lam/q.
+__device__ void micro_slope(double U, double V, double lam, double q, double c4, const double* s,
+                            double* a) {
+  const double a4 = c4 * (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - 2.0 * q));
   const double a3 = 2.0 * lam * (s[2] - V * s[0]) - V * a4;
   const double a2 = 2.0 * lam * (s[1] - U * s[0]) - U * a4;
   const double a1 = s[0] - U * a2 - V * a3 - a4 * (0.5 * (U * U + V * V) + q);
@@ -485,8 +498,7 @@ __device__ void micro_slope(double U, double V, double lam, int K, const double*
 //   Mt1 = dt c1, Mt2 = dt^2 c2, Mt3 = dt^2 c3, Mt4 = dt c4, Mt5 = dt^2 c5
 //   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x,
 // by their Taylor series below x = 0.1 (no cancellation there).
-__device__ void time_weights(double dt, double tau, double* Mt) {
-  const double x = dt / tau;
+__device__ void time_weights(double dt, double x, double* Mt) {
   double c1, c2, c3, c4, c5;
   if (x < 0.1) {
     // term n of each series via the ratio of consecutive terms; 12 terms (the 13th is
@@ -506,12 +518,12 @@ __device__ void time_weights(double dt, double tau, double* Mt) {
     }
     c1 = s1; c2 = s2; c3 = s3; c4 = s4; c5 = s5;
   } else {
-    const double e = exp(-x), em = -expm1(-x);
-    c4 = em / x;
+    const double e = exp(-x), em = -expm1(-x), ix = 1.0 / x;
+    c4 = em * ix;
     c1 = 1.0 - c4;
-    c5 = (c4 - e) / x;
-    c3 = 0.5 - c1 / x;
-    c2 = c5 - c1 / x;
+    c5 = (c4 - e) * ix;
+    c3 = 0.5 - c1 * ix;
+    c2 = c5 - c1 * ix;
   }
   Mt[0] = dt * c1;
   Mt[1] = dt * dt * c2;
@@ -578,23 +590,26 @@ __device__ void pack_face_f32(bool isx, const double (*Qh)[8], const double (*kb
 // and the cell W on both sides; output the time-integrated macroscopic flux F and the
 // micro-flux record.
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
-                          const double* Ss, const double* WL, const double* WR, double delta,
+                          const double* Ss, const double* WL, const double* WR, double tdelta,
                           bool isx, double* F, FaceRec& R, FaceRecF* RF) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], irho = 1.0 / rho, U = W0[1] * irho, V = W0[2] * irho;
-  const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) / ((K + 2) * rho);  // 1/(4 lam)
+  const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) * irho * P.inv_kp2;  // 1/(4 lam)
   const double lam = 0.25 / ilam4;
+  const double h = 2.0 * ilam4;  // 1/(2 lam)
   double Mu[7], Mup[7], Mun[7], Mv[7];
-  gauss_moments7(U, lam, Mu, Mup, Mun);
-  gauss_moments7_full(V, lam, Mv);
+  gauss_moments7(U, lam, h, Mu, Mup, Mun);
+  gauss_moments7_full(V, h, Mv);
   const double X2 = 2.0 * K * ilam4, X4 = (K * K + 2.0 * K) * 4.0 * ilam4 * ilam4;
-  // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5
-  const double tau = collision_time(P, rho, lam);
+  // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5 of
+  // x = dt/tau (omega = 1/2: x = dt rho / (2 mu_ref sqrt(lam)))
+  const double x = P.omega_half ? P.half_dt_mu * rho * rsqrt(lam) : P.dt / collision_time(P, rho, lam);
   double Mt[5];
-  time_weights(P.dt, tau, Mt);
+  time_weights(P.dt, x, Mt);
   // S4: micro slopes
-  const double inv = 2.0 * irho / delta;
+  const double inv = irho * tdelta;
+  const double q = (K + 2) * ilam4, c4 = 4.0 * lam * lam * P.inv_kp2;
   double sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
 #pragma unroll
   for (int c = 0; c < 4; c++) {
@@ -602,16 +617,16 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     sR[c] = (WR[c] - W0[c]) * inv;
     sT[c] = St[c] * irho;
   }
-  micro_slope(U, V, lam, K, sL, aL);
-  micro_slope(U, V, lam, K, sR, aR);
-  micro_slope(U, V, lam, K, sT, b);
+  micro_slope(U, V, lam, q, c4, sL, aL);
+  micro_slope(U, V, lam, q, c4, sR, aR);
+  micro_slope(U, V, lam, q, c4, sT, b);
   double t1[4], t2[4], t3[4], t4[4], p1[4];
   apsi_mom(Mup, Mv, X2, X4, 1, 0, aL, t1);
   apsi_mom(Mun, Mv, X2, X4, 1, 0, aR, t2);
   apsi_mom(Mu, Mv, X2, X4, 0, 1, b, t3);
 #pragma unroll
   for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
-  micro_slope(U, V, lam, K, sA, A);
+  micro_slope(U, V, lam, q, c4, sA, A);
   // S5: equilibrium part of the macroscopic flux; S7 free transport part from the sums
   psi_mom(Mu, Mv, X2, 1, 0, p1);
   apsi_mom(Mup, Mv, X2, X4, 2, 0, aL, t1);
@@ -630,6 +645,7 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     shape_h(b, X2, pb);
     shape_h(A, X2, pA);
     qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
+    if (RF) continue;  // the FP32 record carries the b polynomial in its own form
     shape_b(as, X2, X4, pa);
     shape_b(b, X2, X4, pb);
     shape_b(A, X2, X4, pA);
@@ -674,7 +690,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
   if (t >= nfx + nfy) return;
   const bool isx = t < nfx;
   int i, j, cL, cR, oL, oR, wall = 0, side = 0;
-  double delta;
+  double tdelta;
   if (isx) {
     j = t / (nx + 1);
     i = t % (nx + 1) - 1;
@@ -682,7 +698,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     cR = wcell(P, i + 1, j);
     oL = kSumE;
     oR = kSumW;
-    delta = P.dx;
+    tdelta = P.d_tdx;
     if (i == -1 && P.bc_kind[0] == 1) { wall = 1; side = 0; }
     if (i == nx - 1 && P.bc_kind[1] == 1) { wall = 2; side = 1; }
   } else {
@@ -693,7 +709,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     cR = wcell(P, i, j + 1);
     oL = kSumN;
     oR = kSumS;
-    delta = P.dy;
+    tdelta = P.d_tdy;
     if (j == -1 && P.bc_kind[2] == 1) { wall = 1; side = 2; }
     if (j == ny - 1 && P.bc_kind[3] == 1) { wall = 2; side = 3; }
   }
@@ -747,7 +763,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
-    face_math(P, W0, St, Sf, Ss, WL, WR, delta, isx, Fr, R, RF);
+    face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, RF);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[pm[c]] = Fr[c];
   }
@@ -794,32 +810,41 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
     double Wn[4], W1[4];
     for (int k = 0; k < 4; k++) {
       Wn[k] = Win[k * nwe + w];
-      W1[k] = Wn[k] + (Fx[4 * xw + k] - Fx[4 * xe + k]) / P.dx + (Fy[4 * ys + k] - Fy[4 * yn + k]) / P.dy;
+      W1[k] = Wn[k] + (Fx[4 * xw + k] - Fx[4 * xe + k]) * P.d_idx + (Fy[4 * ys + k] - Fy[4 * yn + k]) * P.d_idy;
       Wout[k * nwe + w] = W1[k];
       d2[k] = (W1[k] - Wn[k]) * (W1[k] - Wn[k]);
       am[k] = fabs(W1[k]);
     }
     const int K = P.K;
-    const double rn = Wn[0], Un = Wn[1] / rn, Vn = Wn[2] / rn;
-    const double ln = (K + 2) * rn / (4.0 * (Wn[3] - 0.5 * rn * (Un * Un + Vn * Vn)));
-    const double r1 = W1[0], U1 = W1[1] / r1, V1 = W1[2] / r1;
-    const double l1 = (K + 2) * r1 / (4.0 * (W1[3] - 0.5 * r1 * (U1 * U1 + V1 * V1)));
+    // 1/lam = 4 (rho E - rho |U|^2 / 2) / ((K + 2) rho); dt / (2 tau) = dt rho / (4 mu_ref
+    // lam^(1 - omega)), for omega = 1/2: dt rho / (4 mu_ref sqrt(lam))
+    const double rn = Wn[0], irn = 1.0 / rn, Un = Wn[1] * irn, Vn = Wn[2] * irn;
+    const double iln = 4.0 * (Wn[3] - 0.5 * rn * (Un * Un + Vn * Vn)) * irn * P.inv_kp2;
+    const double ln = 1.0 / iln;
+    const double r1 = W1[0], ir1 = 1.0 / r1, U1 = W1[1] * ir1, V1 = W1[2] * ir1;
+    const double il1 = 4.0 * (W1[3] - 0.5 * r1 * (U1 * U1 + V1 * V1)) * ir1 * P.inv_kp2;
+    const double l1 = 1.0 / il1;
     if (!(r1 > 0.0) || !(l1 > 0.0) || !isfinite(l1) || !isfinite(U1) || !isfinite(V1))
       atomicOr(err, 1);
-    const double tn = collision_time(P, rn, ln);
-    const double t1 = collision_time(P, r1, l1);
     CellRec R;
-    R.Gn = rn * ln / kPi; R.Un = Un; R.Vn = Vn; R.lamn = ln; R.bn = K / (2.0 * ln);
-    R.G1 = r1 * l1 / kPi; R.U1 = U1; R.V1 = V1; R.lam1 = l1; R.b1 = K / (2.0 * l1);
-    R.cgn = P.dt / (2.0 * tn);
+    R.Gn = rn * ln / kPi; R.Un = Un; R.Vn = Vn; R.lamn = ln; R.bn = 0.5 * K * iln;
+    R.G1 = r1 * l1 / kPi; R.U1 = U1; R.V1 = V1; R.lam1 = l1; R.b1 = 0.5 * K * il1;
+    if (P.omega_half) {
+      R.cgn = P.quarter_dt_mu * rn * rsqrt(ln);
+      R.cg1 = P.quarter_dt_mu * r1 * rsqrt(l1);
+    } else {
+      R.cgn = P.dt / (2.0 * collision_time(P, rn, ln));
+      R.cg1 = P.dt / (2.0 * collision_time(P, r1, l1));
+    }
     R.cf = 1.0 - R.cgn;
-    R.cg1 = P.dt / (2.0 * t1);
     R.inv = 1.0 / (1.0 + R.cg1);
     if (crf) {
       const int nfx = (nx + 1) * P.ny;
       constexpr double kLog2e = 1.4426950408889634;
-      const double refx = (mt4[xw] - mt4[xe]) / P.dx, refy = (mt4[nfx + ys] - mt4[nfx + yn]) / P.dy;
+      const double refx = (mt4[xw] - mt4[xe]) * P.d_idx, refy = (mt4[nfx + ys] - mt4[nfx + yn]) * P.d_idy;
       CellRecF F;
+      // the amplitude enters the exponent; log2 in FP64 (an approximate FP32 log2 put
+      // ~1e-7 relative noise on g per cell, visible in rho V at Kn 0.01)
       F.En[0] = (float)(log2(R.Gn) - ln * (Un * Un + Vn * Vn) * kLog2e);
       F.En[1] = (float)(2.0 * ln * Un * kLog2e);
       F.En[2] = (float)(2.0 * ln * Vn * kLog2e);
@@ -1135,8 +1160,12 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 constexpr int kWalkRows = 64;  // default rows per walk tile
 constexpr int kStripW = 4;     // columns per strip
 constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
+// Records in the ring are padded by kRecPad 16-byte chunks, so that records read by the
+// two u-sign halves of a warp fall in different shared-memory banks.
+constexpr int kRecPad = 1;
+constexpr int kFaceChunks = 8 + kRecPad, kCellChunks = 4 + kRecPad;
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
-constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
+constexpr int kStripChunks = (kStripW + 1) * kFaceChunks + kStripW * kFaceChunks + kStripW * kCellChunks;
 
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -1299,7 +1328,8 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
 
   // face and cell records of a row, staged through a ring of kRing rows in shared memory:
   // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
-  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
+  constexpr int oY = (W + 1) * kFaceChunks, oC = oY + W * kFaceChunks;
+  constexpr int nX = (W + 1) * 8, nY = W * 8, nC = W * 4;  // unpadded chunk counts
   auto stage = [&](int s) {
     if (s < nsteps) {
       const int j = jfirst + sv * s;
@@ -1307,13 +1337,15 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
       const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
       const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
       float4* dst = ring + (s % kRing) * kStripChunks;
-      for (int c = lane; c < kStripChunks; c += 32) {
-        if (c < oY) {
-          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
-        } else if (c < oC) {
-          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
-        } else if (c - oC < wc * 4) {
-          cp_async16(dst + c, gc + (c - oC));
+      for (int c = lane; c < nX + nY + nC; c += 32) {
+        if (c < nX) {
+          if (c < (wc + 1) * 8) cp_async16(dst + (c >> 3) * kFaceChunks + (c & 7), gx + c);
+        } else if (c < nX + nY) {
+          const int d = c - nX;
+          if (d < wc * 8) cp_async16(dst + oY + (d >> 3) * kFaceChunks + (d & 7), gy + d);
+        } else {
+          const int d = c - nX - nY;
+          if (d < wc * 4) cp_async16(dst + oC + (d >> 2) * kCellChunks + (d & 3), gc + d);
         }
       }
     }
@@ -1336,13 +1368,13 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
     cp_async_wait<kRing - 1>();
     __syncwarp();
     const float4* row = ring + (s % kRing) * kStripChunks;
-    const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
-    const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
-    const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
+    auto RX = [&](int r) { return reinterpret_cast<const FaceRecF*>(row + r * kFaceChunks); };
+    auto RY = [&](int r) { return reinterpret_cast<const FaceRecF*>(row + oY + r * kFaceChunks); };
+    auto CC = [&](int r) { return reinterpret_cast<const CellRecF*>(row + oC + r * kCellChunks); };
 
     // flux into position 0 out of U (or off the wall)
     float2 Xix;
-    const FaceRecF* RXi = RX + xl0;
+    const FaceRecF* RXi = RX(xl0);
     if (RXi->wall != 0.f) {
       Xix = strip_wall(RXi, L);
     } else {
@@ -1359,9 +1391,9 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
         const float2 rx = vl_walk2(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
         const float2 ry = vl_walk2(Pv[t + 1], c, Nv[t + 1]);
         const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-        const float2 Xox = strip_face(RXi + su * (t + 1), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
-        const float2 Xoy = strip_face(RY + cl(t), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
-        const float2 o = strip_collide(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
+        const float2 Xox = strip_face(RX(xl0 + su * (t + 1)), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
+        const float2 Xoy = strip_face(RY(cl(t)), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
+        const float2 o = strip_collide(CC(cl(t)), L, c, Xix, Xox, Xiy[t], Xoy);
         if (act) pw[col(t)] = o;
         Xix = Xox;
         Xiy[t] = Xoy;
