@@ -48,7 +48,10 @@ struct ugks_ctx {
   int nrblocks = 0;
   int* err = nullptr;
   double* d_grid = nullptr;  // u[nu], v[nv], wu[nu], wv[nv], [5][nv] wv v^n
-  double* stage = nullptr;   // FP64 staging for FP32 state conversion
+  double* stage = nullptr;   // FP64 staging for FP32 state conversion: two halves, stage_bytes
+  double2* grefd = nullptr;  // FP32 form: g_ref per velocity in FP64 (state conversion)
+  cudaStream_t xstream = nullptr;     // FP32 form: host <-> staging copies
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   float2* gref = nullptr;    // FP32 form: g_ref per velocity
   float* ftab = nullptr;     // FP32 form: velocity tables (mvf, uwf)
   size_t stage_bytes = 0;
@@ -146,9 +149,11 @@ size_t predict_bytes(const ugks_config* c) {
   if (f32) {
     const size_t row_d = nx * nq * 2 * sizeof(double);
     size_t want = (size_t)64 << 20;
-    if (want < row_d) want = row_d;
+    if (want < 2 * row_d) want = 2 * row_d;
     if (want > row_d * ny) want = row_d * ny;
-    b += want + sizeof(float2) * nq + sizeof(float) * (6 * (size_t)c->nv + 2 * (size_t)c->nu);
+    if (want < 2 * row_d) want = 2 * row_d;
+    b += want + (sizeof(float2) + sizeof(double2)) * nq +
+         sizeof(float) * (6 * (size_t)c->nv + 2 * (size_t)c->nu);
     b += sizeof(SlotDev) + sizeof(BatchWork);
   }
   return b;
@@ -230,38 +235,37 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// FP64 host/device rows <-> FP32 ring layout
+// FP64 host/device rows <-> FP32 ring layout (e = f - g_ref); one cell per block iteration,
+// threads over the velocities; rows j0 .. j0+nrows-1 of the physical mesh.
 __global__ void k_rows_to_f32(const double* __restrict__ src, float2* __restrict__ dst, Params P,
-                              int j0, int nrows) {
-  const size_t row = (size_t)P.nx * P.nq;
-  const size_t n = row * nrows;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / row);
-    const size_t o = t % row;
-    const int i = (int)(o / P.nq), q = (int)(o % P.nq);
-    double rh, rb;
-    ref_maxwellian(P, P.u[q % P.nu], P.v[q / P.nu], rh, rb);
-    float2 v;
-    v.x = (float)(src[2 * t] - rh);
-    v.y = (float)(src[2 * t + 1] - rb);
-    dst[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q] = v;
+                              const double2* __restrict__ grefd, int j0, int nrows) {
+  const int ncell = P.nx * nrows;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    const int r = c / P.nx, i = c - r * P.nx;
+    const double* s = src + (size_t)c * P.nq * 2;
+    float2* d = dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq;
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+      const double2 g = grefd[q];
+      d[q] = make_float2((float)(s[2 * q] - g.x), (float)(s[2 * q + 1] - g.y));
+    }
   }
 }
 __global__ void k_f32_to_rows(const float2* __restrict__ src, double* __restrict__ dst, Params P,
-                              int j0, int nrows) {
-  const size_t row = (size_t)P.nx * P.nq;
-  const size_t n = row * nrows;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / row);
-    const size_t o = t % row;
-    const int i = (int)(o / P.nq), q = (int)(o % P.nq);
-    const float2 v = src[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq + q];
-    double rh, rb;
-    ref_maxwellian(P, P.u[q % P.nu], P.v[q / P.nu], rh, rb);
-    dst[2 * t] = (double)v.x + rh;
-    dst[2 * t + 1] = (double)v.y + rb;
+                              const double2* __restrict__ grefd, int j0, int nrows) {
+  const int ncell = P.nx * nrows;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    const int r = c / P.nx, i = c - r * P.nx;
+    const float2* s = src + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq;
+    double* d = dst + (size_t)c * P.nq * 2;
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+      const float2 v = s[q];
+      const double2 g = grefd[q];
+      d[2 * q] = (double)v.x + g.x;
+      d[2 * q + 1] = (double)v.y + g.y;
+    }
   }
 }
+constexpr int kConvBlocks = 1216;  // 8 per SM
 
 template <typename T2>
 __global__ void k_init_maxwellian(Params P, const double* __restrict__ prim, T2* __restrict__ f,
@@ -337,16 +341,26 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
   }
   float2* dst = static_cast<float2*>(h->f[h->cur]);
   if (!from_host) {
-    k_rows_to_f32<<<1024, 256, 0, h->stream>>>(f, dst, P, 0, P.ny);
+    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(f, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
-  const int rows = (int)(h->stage_bytes / row_d);
-  for (int j0 = 0; j0 < P.ny; j0 += rows) {
+  // two staging halves: the copy of chunk k+1 (copy stream) overlaps the conversion of
+  // chunk k (library stream)
+  const size_t half = h->stage_bytes / 2;
+  const int rows = (int)(half / row_d);
+  int k = 0;
+  for (int j0 = 0; j0 < P.ny; j0 += rows, k++) {
     const int nr = (j0 + rows <= P.ny) ? rows : P.ny - j0;
-    CK(cudaMemcpyAsync(h->stage, f + (size_t)j0 * P.nx * P.nq * 2, nr * row_d, cudaMemcpyHostToDevice, h->stream));
-    k_rows_to_f32<<<1024, 256, 0, h->stream>>>(h->stage, dst, P, j0, nr);
+    const int b = k & 1;
+    double* buf = h->stage + b * (half / sizeof(double));
+    CK(cudaStreamWaitEvent(h->xstream, h->ev_free[b], 0));
+    CK(cudaMemcpyAsync(buf, f + (size_t)j0 * P.nx * P.nq * 2, nr * row_d, cudaMemcpyHostToDevice, h->xstream));
+    CK(cudaEventRecord(h->ev_copied[b], h->xstream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
+    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(buf, dst, P, h->grefd, j0, nr);
     CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev_free[b], h->stream));
   }
   return UGKS_OK;
 }
@@ -362,17 +376,28 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
   }
   const float2* src = static_cast<const float2*>(h->f[h->cur]);
   if (!to_host) {
-    k_f32_to_rows<<<1024, 256, 0, h->stream>>>(src, f, P, 0, P.ny);
+    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, f, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
-  const int rows = (int)(h->stage_bytes / row_d);
-  for (int j0 = 0; j0 < P.ny; j0 += rows) {
+  // conversion of chunk k+1 (library stream) overlaps the copy of chunk k (copy stream);
+  // the caller synchronises the library stream, which waits for the last copy
+  const size_t half = h->stage_bytes / 2;
+  const int rows = (int)(half / row_d);
+  int k = 0;
+  for (int j0 = 0; j0 < P.ny; j0 += rows, k++) {
     const int nr = (j0 + rows <= P.ny) ? rows : P.ny - j0;
-    k_f32_to_rows<<<1024, 256, 0, h->stream>>>(src, h->stage, P, j0, nr);
+    const int b = k & 1;
+    double* buf = h->stage + b * (half / sizeof(double));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_free[b], 0));
+    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, buf, P, h->grefd, j0, nr);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(f + (size_t)j0 * P.nx * P.nq * 2, h->stage, nr * row_d, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->ev_copied[b], h->stream));
+    CK(cudaStreamWaitEvent(h->xstream, h->ev_copied[b], 0));
+    CK(cudaMemcpyAsync(f + (size_t)j0 * P.nx * P.nq * 2, buf, nr * row_d, cudaMemcpyDeviceToHost, h->xstream));
+    CK(cudaEventRecord(h->ev_free[b], h->xstream));
   }
+  for (int b = 0; b < 2; b++) CK(cudaStreamWaitEvent(h->stream, h->ev_free[b], 0));
   return UGKS_OK;
 }
 
@@ -664,6 +689,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   h->nchunk_neg = (P.m_neg * P.nu + 31) / 32;
   h->nchunk_pos = ((P.nv - P.m_neg) * P.nu + 31) / 32;
   std::vector<float2> gref_host;
+  std::vector<double2> grefd_host;
   if (h->prec == UGKS_FP32F) {
     double rr = cfg->ref_rho, rU = cfg->ref_U, rV = cfg->ref_V, rT = cfg->ref_T;
     if (!(rT > 0) || !(rr > 0)) { rr = 1.0; rU = 0.0; rV = 0.0; rT = 1.0; }
@@ -674,12 +700,14 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     P.ref_V = rV;
     P.ref_bf = P.K / (2.0 * P.ref_lam);
     gref_host.resize((size_t)P.nq);
+    grefd_host.resize((size_t)P.nq);
     for (int m = 0; m < P.nv; m++)
       for (int k = 0; k < P.nu; k++) {
         const double u = h->hu[k], v = h->hv[m], w = h->hwu[k] * h->hwv[m];
         double gh, gb;
         ref_maxwellian(P, u, v, gh, gb);
         gref_host[(size_t)m * P.nu + k] = make_float2((float)gh, (float)gb);
+        grefd_host[(size_t)m * P.nu + k] = make_double2(gh, gb);
         const double psi[4] = {gh, u * gh, v * gh, 0.5 * (u * u + v * v) * gh + 0.5 * gb};
         const double hs[4] = {u > 0 ? 1.0 : (u < 0 ? 0.0 : 0.5), u < 0 ? 1.0 : (u > 0 ? 0.0 : 0.5),
                               v > 0 ? 1.0 : (v < 0 ? 0.0 : 0.5), v < 0 ? 1.0 : (v > 0 ? 0.0 : 0.5)};
@@ -724,11 +752,21 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   if (ok && h->prec == UGKS_FP32F) {
     const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
     size_t want = (size_t)64 << 20;
-    if (want < row_d) want = row_d;
+    if (want < 2 * row_d) want = 2 * row_d;
     if (want > row_d * P.ny) want = row_d * P.ny;
+    if (want < 2 * row_d) want = 2 * row_d;  // two halves of at least one row each
     h->stage_bytes = want;
     ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq) &&
+         alloc((void**)&h->grefd, sizeof(double2) * (size_t)P.nq) &&
          alloc((void**)&h->ftab, sizeof(float) * (6 * (size_t)P.nv + 2 * (size_t)P.nu));
+    if (ok) {
+      e = cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking);
+      for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        e = cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming);
+      }
+      ok = e == cudaSuccess;
+    }
   }
   if (!ok) {
     ugks_destroy(h);
@@ -778,6 +816,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (h->ftab && (r = cudaMemcpyAsync(h->ftab, ftab_host.data(), sizeof(float) * ftab_host.size(),
                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
+    if (h->grefd && (r = cudaMemcpyAsync(h->grefd, grefd_host.data(), sizeof(double2) * grefd_host.size(),
+                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return r;
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
     if ((r = h->prec == UGKS_FP64 ? set_smem_limits<double>(P.nv) : set_smem_limits<float>(P.nv)) != cudaSuccess)
       return r;
@@ -797,9 +838,17 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
-                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->fxf, h->fyf,
+                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->grefd, h->fxf, h->fyf,
                   h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->xstream) {
+    cudaStreamSynchronize(h->xstream);
+    cudaStreamDestroy(h->xstream);
+  }
+  for (int b = 0; b < 2; b++) {
+    if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+    if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+  }
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
