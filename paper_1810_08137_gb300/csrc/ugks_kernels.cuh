@@ -448,8 +448,8 @@ __device__ void gauss_moments7_full(double U, double h, double* M) {
   for (int n = 0; n < 5; n++) M[n + 2] = U * M[n + 1] + (n + 1) * h * M[n];
 }
 
-// <u^a v^b psi> and <u^a v^b xi^2 psi> for the normalised Maxwellian, u-moments Mu (one
-// range), v-moments Mv, <xi^2> = X2, <xi^4> = X4.
+// <u^a v^b psi> for the normalised Maxwellian, u-moments Mu (one range), v-moments Mv,
+// <xi^2> = X2.
 __device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, double X2, int a, int b,
                                         double* o) {
   o[0] = Mu[a] * Mv[b];
@@ -457,30 +457,31 @@ __device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, doub
   o[2] = Mu[a] * Mv[b + 1];
   o[3] = 0.5 * (Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2] + Mu[a] * Mv[b] * X2);
 }
-__device__ __forceinline__ void psi_xi_mom(const double* Mu, const double* Mv, double X2, double X4,
-                                           int a, int b, double* o) {
-  o[0] = Mu[a] * Mv[b] * X2;
-  o[1] = Mu[a + 1] * Mv[b] * X2;
-  o[2] = Mu[a] * Mv[b + 1] * X2;
-  o[3] = 0.5 * ((Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2]) * X2 + Mu[a] * Mv[b] * X4);
-}
-// <u^a v^b psi (c . psi)>, c . psi = c1 + c2 u + c3 v + c4 (u^2 + v^2 + xi^2)/2
+// <u^a v^b psi (c . psi)>, c . psi = c1 + c2 u + c3 v + c4 (u^2 + v^2 + xi^2)/2, from the
+// factorised moments: with M(p, q) = Mu[p] Mv[q] and h = c4/2,
+//   T(p, q) = <u^p v^q (c . psi)> = Mu[p] A(q) + Mu[p+1] c2 Mv[q] + Mu[p+2] h Mv[q],
+//   A(q) = (c1 + h X2) Mv[q] + c3 Mv[q+1] + h Mv[q+2];
+// the components are T(a, b), T(a+1, b), T(a, b+1), and for the energy
+// (T(a+2, b) + T(a, b+2) + X2 T(a, b) + h (X4 - X2^2) M(a, b)) / 2, since
+// <xi^2 (c . psi)> = X2 (c . psi with xi^2 -> X2) + h (X4 - X2^2).
 __device__ void apsi_mom(const double* Mu, const double* Mv, double X2, double X4, int a, int b,
                          const double* c, double* o) {
-  double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
-  psi_mom(Mu, Mv, X2, a, b, t0);
-  psi_mom(Mu, Mv, X2, a + 1, b, t1);
-  psi_mom(Mu, Mv, X2, a, b + 1, t2);
-  psi_mom(Mu, Mv, X2, a + 2, b, t3);
-  psi_mom(Mu, Mv, X2, a, b + 2, t4);
-  psi_xi_mom(Mu, Mv, X2, X4, a, b, t5);
+  const double h = 0.5 * c[3], c0x = c[0] + h * X2;
+  double A[3], B[3], C[3];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
-    o[i] = c[0] * t0[i] + c[1] * t1[i] + c[2] * t2[i] + 0.5 * c[3] * (t3[i] + t4[i] + t5[i]);
+  for (int q = 0; q < 3; q++) {
+    A[q] = c0x * Mv[b + q] + c[2] * Mv[b + q + 1] + h * Mv[b + q + 2];
+    B[q] = c[1] * Mv[b + q];
+    C[q] = h * Mv[b + q];
+  }
+  auto T = [&](int p, int q) { return Mu[a + p] * A[q] + Mu[a + p + 1] * B[q] + Mu[a + p + 2] * C[q]; };
+  const double t00 = T(0, 0);
+  o[0] = t00;
+  o[1] = T(1, 0);
+  o[2] = T(0, 1);
+  o[3] = 0.5 * (T(2, 0) + T(0, 2) + X2 * t00 + h * (X4 - X2 * X2) * (Mu[a] * Mv[b]));
 }
 
-// Micro-slope solve <psi (a . psi)> = s for the normalised Maxwellian (U, V, lam), closed
-// form obtained by centring the moments.
 // q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass, c4 = lam/q.
 __device__ void micro_slope(double U, double V, double lam, double q, double c4, const double* s,
                             double* a) {
@@ -494,6 +495,13 @@ __device__ void micro_slope(double U, double V, double lam, double q, double c4,
   a[3] = a4;
 }
 
+// 1/n! as a constant expression (the loops that use it are unrolled).
+__host__ __device__ constexpr double inv_factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; k++) f *= k;
+  return 1.0 / f;
+}
+
 // Time integrals over one step of the Eq. 2 weights, x = dt/tau:
 //   Mt1 = dt c1, Mt2 = dt^2 c2, Mt3 = dt^2 c3, Mt4 = dt c4, Mt5 = dt^2 c5
 //   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x,
@@ -501,22 +509,20 @@ __device__ void micro_slope(double U, double V, double lam, double q, double c4,
 __device__ void time_weights(double dt, double x, double* Mt) {
   double c1, c2, c3, c4, c5;
   if (x < 0.1) {
-    // term n of each series via the ratio of consecutive terms; 12 terms (the 13th is
-    // below 1e-22 relative for x < 0.1)
-    double t4 = 1.0, s4 = 1.0;             // c4: (-x)^n/(n+1)!
-    double b5 = 0.5, s5 = 0.5;             // c5: (n+1) (-x)^n/(n+2)!, b5 = (-x)^n/(n+2)!
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    // power series in y = -x by Horner, 12 terms (the 13th is below 1e-22 relative for
+    // x < 0.1): c4 = sum y^n/(n+1)!, c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!,
+    // c3 = x sum y^n/(n+3)!, c2 = -x sum (n+1) y^n/(n+3)!
+    const double y = -x;
+    double h4 = 0.0, h5 = 0.0, h1 = 0.0, h3 = 0.0, h2 = 0.0;
 #pragma unroll
-    for (int n = 1; n < 12; n++) {
-      t4 *= -x * (1.0 / (n + 1));          // (-x)^n/(n+1)!
-      b5 *= -x * (1.0 / (n + 2));          // (-x)^n/(n+2)!
-      s4 += t4;
-      s5 += (n + 1) * b5;
-      s1 -= t4;                            // c1 = sum_{n>=1} -(-x)^n/(n+1)!
-      s3 -= b5;                            // c3 = sum_{n>=1} -(-x)^n/(n+2)!
-      s2 += n * b5;                        // c2 = sum_{n>=1} n (-x)^n/(n+2)!
+    for (int n = 11; n >= 0; n--) {
+      h4 = h4 * y + inv_factorial(n + 1);
+      h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
+      h1 = h1 * y + inv_factorial(n + 2);
+      h3 = h3 * y + inv_factorial(n + 3);
+      h2 = h2 * y + (n + 1) * inv_factorial(n + 3);
     }
-    c1 = s1; c2 = s2; c3 = s3; c4 = s4; c5 = s5;
+    c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
   } else {
     const double e = exp(-x), em = -expm1(-x), ix = 1.0 / x;
     c4 = em * ix;
