@@ -54,7 +54,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 UPDATE_FLOPS_PER_VC = 150
 # DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
 # capture summarised in profiles/; None when the kernel has changed since that capture.
-UPDATE_TRAFFIC_PER_VC = 1223.76e6 / 62.72e6  # 400x200x28^2 capture: 750.08 MB read + 473.68 MB written
+UPDATE_TRAFFIC_PER_VC = None
 
 
 class Clocks:
@@ -101,6 +101,23 @@ class Clocks:
                           if len(r) > 3 + k and r[3 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "samples": len(sm), "reasons": reasons}
+
+
+def max_over_ranks(x: float, device) -> float:
+    """Maximum of x over the ranks of the default process group (x itself on one rank)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size: int, vc_per_step: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: every rank runs its own replica of the workload (weak scaling),
+    timed by the slowest rank."""
+    return world_size * vc_per_step * steps / (ms * 1e-3)
 
 
 def dist():
@@ -179,6 +196,34 @@ def cpu_baseline(cfg, prim, budget_s=20.0):
     return {"value": cfg.vc * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} full step(s) of {cfg.name} ({cfg.vc} vc/step), FP64 C oracle, "
                       f"OpenMP over faces and cells"}
+
+
+def large_velocity_bench(ugks, torch, stream, warmup, grids=(51, 101, 151, 201)):
+    """Large velocity space (200x100 mesh, N^2 velocities on [-20,20]^2, Kn 0.01): both
+    forms per velocity grid, graph-replayed steps timed with CUDA events."""
+    out = []
+    for n in grids:
+        cfg = I.workload_large_velocity(n)
+        prim = I.initial_prim(cfg, I.seed_for(3, n))
+        row = {"workload": cfg.name, "vc_per_step": cfg.vc}
+        for prec, name, steps in ((ugks.FP32F, "fp32f", 10), (ugks.FP64, "fp64", 2)):
+            s = ugks.Solver(cfg, prec, stream=stream.cuda_stream)
+            s.init_maxwellian(*prim)
+            s.step(warmup)
+            s.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            s.close()
+            torch.cuda.empty_cache()
+            row[name] = {"ms_per_step": ms, "value": cfg.vc / (ms * 1e-3), "steps": steps}
+        row["fp32f_vs_fp64"] = row["fp32f"]["value"] / row["fp64"]["value"]
+        out.append(row)
+    return {"unit": UNIT, "grids": out}
 
 
 def batch_bench(ugks, torch, stream, steps, warmup):
@@ -286,6 +331,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-large-velocity", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -313,12 +359,6 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     results = {}
     with torch.cuda.stream(stream):
@@ -329,7 +369,7 @@ def main():
             with Clocks(local) as clk:
                 s, ms, ms_prof, kt = run_form(ugks, torch, cfg, prec, n, args.warmup, stream, prim)
             barrier()
-            ms = max_over_ranks(ms)
+            ms = max_over_ranks(ms, "cuda")
             results[prec] = (ms, ms_prof, kt, clk.summary(), n)
             if prec == main_prec:
                 f_host_t, f_host = pinned(torch, (cfg.nc, cfg.nq, 2))
@@ -345,9 +385,10 @@ def main():
             torch.cuda.empty_cache()
         barrier()
         t_e2e = e2e_form(ugks, torch, cfg, main_prec, args.e2e_steps, stream, f_host, W_host)
-        t_e2e = max_over_ranks(t_e2e)
+        t_e2e = max_over_ranks(t_e2e, "cuda")
         del f_host_t, W_host_t, f_host, W_host
         batch = None if args.no_batch else batch_bench(ugks, torch, stream, args.steps, args.warmup)
+        large = None if args.no_large_velocity else large_velocity_bench(ugks, torch, stream, args.warmup)
         serving = None if (args.no_serve or ws > 1) else serve_bench(ugks, stream)
 
     def form_json(prec):
@@ -372,7 +413,7 @@ def main():
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
                     "nominal_flops_per_vc": UPDATE_FLOPS_PER_VC, "hbm_frac": ach_up / hbm}
         return {
-            "value": ws * cfg.vc * n / (ms * 1e-3),
+            "value": job_value(ws, cfg.vc, n, ms),
             "ms_per_step": ms / n,
             "steps": n,
             "ms_per_step_profiled": ms_prof / n,
@@ -421,6 +462,7 @@ def main():
         "cpu_baseline": cpu,
         "batch": batch,
         "serving": serving,
+        "large_velocity": large,
     }
     if batch:
         batch["vs_fp64_single"] = batch["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])

@@ -306,22 +306,34 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = T(0);
       y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = T(0);
     };
-    auto slopes = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
+    // the five stencil values of row m (centre, x-, x+, y-, y+)
+    auto load5 = [&](int m, T2 (&v)[5]) {
       const T2* src = fc + (size_t)m * nu + kk;
-      c = src[0];
-      const T2 w = src[-nq], e = src[nq], s = src[-(long)rs], n = src[rs];
+      v[0] = src[0];
+      v[1] = src[-nq];
+      v[2] = src[nq];
+      v[3] = src[-(long)rs];
+      v[4] = src[rs];
+    };
+    auto slopes5 = [&](const T2 (&v)[5], T& rxh, T& rxb, T& ryh, T& ryb) {
       rxh = rxb = ryh = ryb = T(0);
       if (!zs) {
-        rxh = vl_half(w.x, c.x, e.x);
-        rxb = vl_half(w.y, c.y, e.y);
-        ryh = vl_half(s.x, c.x, n.x);
-        ryb = vl_half(s.y, c.y, n.y);
+        rxh = vl_half(v[1].x, v[0].x, v[2].x);
+        rxb = vl_half(v[1].y, v[0].y, v[2].y);
+        ryh = vl_half(v[3].x, v[0].x, v[4].x);
+        ryb = vl_half(v[3].y, v[0].y, v[4].y);
       }
     };
-    auto row = [&](int m) {
+    auto slopes = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
+      T2 v[5];
+      load5(m, v);
+      slopes5(v, rxh, rxb, ryh, ryb);
+      c = v[0];
+    };
+    auto acc = [&](int m, const T2 (&v)[5]) {
       T rxh, rxb, ryh, ryb;
-      T2 c;
-      slopes(m, rxh, rxb, ryh, ryb, c);
+      slopes5(v, rxh, rxb, ryh, ryb);
+      const T2 c = v[0];
       T wn[5];
       wtab(P, m, wn);
       const T w0 = wn[0], w1 = wn[1], w2 = wn[2], w3 = wn[3], w4 = wn[4];
@@ -331,6 +343,16 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       xb0 += w0 * rxb; xb1 += w1 * rxb;
       y0 += w0 * ryh; y1 += w1 * ryh; y2 += w2 * ryh; y3 += w3 * ryh; y4 += w4 * ryh;
       yb0 += w0 * ryb; yb1 += w1 * ryb; yb2 += w2 * ryb;
+    };
+    // rows m0 .. m1-1 (loading the next row ahead of the arithmetic needs more registers
+    // than the occupancy this latency-bound loop depends on: measured slower)
+    auto rows = [&](int m0, int m1) {
+#pragma unroll 1
+      for (int m = m0; m < m1; m++) {
+        T2 v[5];
+        load5(m, v);
+        acc(m, v);
+      }
     };
     auto row_v0 = [&](int m) {  // v = 0: only the w_0 sums, half weight
       T rxh, rxb, ryh, ryb;
@@ -354,14 +376,12 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
     };
     zero();
-#pragma unroll 1
-    for (int m = 0; m < mneg; m++) row(m);
+    rows(0, mneg);
     if (v0) row_v0(mneg);
     close(T(-1), wsum + kSumS);
     zero();
     if (v0) row_v0(mneg);
-#pragma unroll 1
-    for (int m = mpos; m < nv; m++) row(m);
+    rows(mpos, nv);
     close(T(1), wsum + kSumN);
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
     const T tA0 = tot[0], tA1 = tot[128], tA2 = tot[256], tAb = tot[384], tR0 = tot[512];
@@ -1166,6 +1186,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 constexpr int kWalkRows = 64;  // default rows per walk tile
 constexpr int kStripW = 4;     // columns per strip
 constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
+constexpr int kStripUnroll = 1;  // rows per iteration of the walk loop (1 or 4; 4 measured slower)
 // Records in the ring are padded by kRecPad 16-byte chunks, so that records read by the
 // two u-sign halves of a warp fall in different shared-memory banks.
 constexpr int kRecPad = 1;
@@ -1363,14 +1384,18 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
   // local record index of walk position t (-1 = U's face for x) within the staged row
   const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
   auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
-  for (int s = 0; s < nsteps; s++) {
+  // one row: rows j - sv, j, j + sv in P, C, N (positions -1..W-1), UU and D of row j in
+  // uu, dd; loads row j + 2 sv into NN and UU, D of row j + sv into nuu, ndd
+  using Row = float2[W + 1];
+  auto row_step = [&](int s, Row& P_, Row& C_, Row& N_, Row& NN, float2& uu, float2& dd, float2& nuu,
+                      float2& ndd) {
     __syncwarp();                    // every lane is done with the slot refilled next
     stage(s + kRing - 1);
     // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
-    float2 NN[W + 1];
 #pragma unroll
     for (int p = -1; p < W; p++) NN[p + 1] = ld2(pr + 2 * rs + col(p));
-    const float2 nUU = ld2(pr + rs + col(-2)), nD = ld2(pr + rs + col(W));
+    nuu = ld2(pr + rs + col(-2));
+    ndd = ld2(pr + rs + col(W));
     cp_async_wait<kRing - 1>();
     __syncwarp();
     const float4* row = ring + (s % kRing) * kStripChunks;
@@ -1384,18 +1409,18 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
     if (RXi->wall != 0.f) {
       Xix = strip_wall(RXi, L);
     } else {
-      float2 rx = vl_walk2(cUU, Cv[0], Cv[1]);
-      float2 ry = vl_walk2(Pv[0], Cv[0], Nv[0]);
+      float2 rx = vl_walk2(uu, C_[0], C_[1]);
+      float2 ry = vl_walk2(P_[0], C_[0], N_[0]);
       if (zu) rx = ry = make_float2(0.f, 0.f);
       const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-      Xix = strip_face(RXi, xside, L, make_float2(Cv[0].x + rx.x, Cv[0].y + rx.y), d);
+      Xix = strip_face(RXi, xside, L, make_float2(C_[0].x + rx.x, C_[0].y + rx.y), d);
     }
 #pragma unroll
     for (int t = 0; t < W; t++) {
       if (t < wc) {
-        const float2 c = Cv[t + 1];
-        const float2 rx = vl_walk2(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
-        const float2 ry = vl_walk2(Pv[t + 1], c, Nv[t + 1]);
+        const float2 c = C_[t + 1];
+        const float2 rx = vl_walk2(C_[t], c, t + 1 < W ? C_[t + 2] : dd);
+        const float2 ry = vl_walk2(P_[t + 1], c, N_[t + 1]);
         const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
         const float2 Xox = strip_face(RX(xl0 + su * (t + 1)), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
         const float2 Xoy = strip_face(RY(cl(t)), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
@@ -1405,16 +1430,36 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
         Xiy[t] = Xoy;
       }
     }
-#pragma unroll
-    for (int p = 0; p <= W; p++) {
-      Pv[p] = Cv[p];
-      Cv[p] = Nv[p];
-      Nv[p] = NN[p];
-    }
-    cUU = nUU;
-    cD = nD;
     pr += rs;
     pw += rs;
+  };
+  if (kStripUnroll == 4) {
+    // four row buffers in rotation: each unrolled row names its buffers statically
+    Row R3;
+    float2 uu1, dd1;
+    for (int s = 0; s < nsteps; s += 4) {
+      row_step(s, Pv, Cv, Nv, R3, cUU, cD, uu1, dd1);
+      if (s + 1 >= nsteps) break;
+      row_step(s + 1, Cv, Nv, R3, Pv, uu1, dd1, cUU, cD);
+      if (s + 2 >= nsteps) break;
+      row_step(s + 2, Nv, R3, Pv, Cv, cUU, cD, uu1, dd1);
+      if (s + 3 >= nsteps) break;
+      row_step(s + 3, R3, Pv, Cv, Nv, uu1, dd1, cUU, cD);
+    }
+  } else {
+    for (int s = 0; s < nsteps; s++) {
+      Row NN;
+      float2 nUU, nD;
+      row_step(s, Pv, Cv, Nv, NN, cUU, cD, nUU, nD);
+#pragma unroll
+      for (int p = 0; p <= W; p++) {
+        Pv[p] = Cv[p];
+        Cv[p] = Nv[p];
+        Nv[p] = NN[p];
+      }
+      cUU = nUU;
+      cD = nD;
+    }
   }
   cp_async_wait<0>();
 }

@@ -1,0 +1,49 @@
+"""The multi-GPU path of bench.py (independent replicas, one per rank): the timing taken by
+the slowest rank and the whole-job throughput, on two gloo ranks on CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as tdist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = 100.0 + 25.0 * rank          # rank 1 is the slowest
+        t = bench.max_over_ranks(ms, "cpu")
+        out[rank] = (t, bench.job_value(world, 1000, 10, t))
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_sum_the_work():
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
+    for r in range(world):
+        t, v = out[r]
+        assert t == pytest.approx(125.0)
+        # 2 replicas x 1000 vc x 10 steps in 125 ms
+        assert v == pytest.approx(2 * 1000 * 10 / 0.125)
+
+
+def test_single_rank_is_unchanged():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, "cpu") == 3.5
+    assert bench.job_value(1, 100, 4, 2.0) == pytest.approx(100 * 4 / 2e-3)
