@@ -1186,13 +1186,8 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 constexpr int kWalkRows = 64;  // default rows per walk tile
 constexpr int kStripW = 4;     // columns per strip
 constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
-constexpr int kStripUnroll = 1;  // rows per iteration of the walk loop (1 or 4; 4 measured slower)
-// Records in the ring are padded by kRecPad 16-byte chunks, so that records read by the
-// two u-sign halves of a warp fall in different shared-memory banks.
-constexpr int kRecPad = 1;
-constexpr int kFaceChunks = 8 + kRecPad, kCellChunks = 4 + kRecPad;
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
-constexpr int kStripChunks = (kStripW + 1) * kFaceChunks + kStripW * kFaceChunks + kStripW * kCellChunks;
+constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
 
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -1355,8 +1350,7 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
 
   // face and cell records of a row, staged through a ring of kRing rows in shared memory:
   // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
-  constexpr int oY = (W + 1) * kFaceChunks, oC = oY + W * kFaceChunks;
-  constexpr int nX = (W + 1) * 8, nY = W * 8, nC = W * 4;  // unpadded chunk counts
+  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
   auto stage = [&](int s) {
     if (s < nsteps) {
       const int j = jfirst + sv * s;
@@ -1364,15 +1358,13 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
       const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
       const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
       float4* dst = ring + (s % kRing) * kStripChunks;
-      for (int c = lane; c < nX + nY + nC; c += 32) {
-        if (c < nX) {
-          if (c < (wc + 1) * 8) cp_async16(dst + (c >> 3) * kFaceChunks + (c & 7), gx + c);
-        } else if (c < nX + nY) {
-          const int d = c - nX;
-          if (d < wc * 8) cp_async16(dst + oY + (d >> 3) * kFaceChunks + (d & 7), gy + d);
-        } else {
-          const int d = c - nX - nY;
-          if (d < wc * 4) cp_async16(dst + oC + (d >> 2) * kCellChunks + (d & 3), gc + d);
+      for (int c = lane; c < kStripChunks; c += 32) {
+        if (c < oY) {
+          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
+        } else if (c < oC) {
+          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
+        } else if (c - oC < wc * 4) {
+          cp_async16(dst + c, gc + (c - oC));
         }
       }
     }
@@ -1384,82 +1376,58 @@ __device__ __forceinline__ void strip_body(const Params& P, const float2* __rest
   // local record index of walk position t (-1 = U's face for x) within the staged row
   const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
   auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
-  // one row: rows j - sv, j, j + sv in P, C, N (positions -1..W-1), UU and D of row j in
-  // uu, dd; loads row j + 2 sv into NN and UU, D of row j + sv into nuu, ndd
-  using Row = float2[W + 1];
-  auto row_step = [&](int s, Row& P_, Row& C_, Row& N_, Row& NN, float2& uu, float2& dd, float2& nuu,
-                      float2& ndd) {
+  for (int s = 0; s < nsteps; s++) {
     __syncwarp();                    // every lane is done with the slot refilled next
     stage(s + kRing - 1);
     // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
+    float2 NN[W + 1];
 #pragma unroll
     for (int p = -1; p < W; p++) NN[p + 1] = ld2(pr + 2 * rs + col(p));
-    nuu = ld2(pr + rs + col(-2));
-    ndd = ld2(pr + rs + col(W));
+    const float2 nUU = ld2(pr + rs + col(-2)), nD = ld2(pr + rs + col(W));
     cp_async_wait<kRing - 1>();
     __syncwarp();
     const float4* row = ring + (s % kRing) * kStripChunks;
-    auto RX = [&](int r) { return reinterpret_cast<const FaceRecF*>(row + r * kFaceChunks); };
-    auto RY = [&](int r) { return reinterpret_cast<const FaceRecF*>(row + oY + r * kFaceChunks); };
-    auto CC = [&](int r) { return reinterpret_cast<const CellRecF*>(row + oC + r * kCellChunks); };
+    const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
+    const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
+    const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
 
     // flux into position 0 out of U (or off the wall)
     float2 Xix;
-    const FaceRecF* RXi = RX(xl0);
+    const FaceRecF* RXi = RX + xl0;
     if (RXi->wall != 0.f) {
       Xix = strip_wall(RXi, L);
     } else {
-      float2 rx = vl_walk2(uu, C_[0], C_[1]);
-      float2 ry = vl_walk2(P_[0], C_[0], N_[0]);
+      float2 rx = vl_walk2(cUU, Cv[0], Cv[1]);
+      float2 ry = vl_walk2(Pv[0], Cv[0], Nv[0]);
       if (zu) rx = ry = make_float2(0.f, 0.f);
       const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-      Xix = strip_face(RXi, xside, L, make_float2(C_[0].x + rx.x, C_[0].y + rx.y), d);
+      Xix = strip_face(RXi, xside, L, make_float2(Cv[0].x + rx.x, Cv[0].y + rx.y), d);
     }
 #pragma unroll
     for (int t = 0; t < W; t++) {
       if (t < wc) {
-        const float2 c = C_[t + 1];
-        const float2 rx = vl_walk2(C_[t], c, t + 1 < W ? C_[t + 2] : dd);
-        const float2 ry = vl_walk2(P_[t + 1], c, N_[t + 1]);
+        const float2 c = Cv[t + 1];
+        const float2 rx = vl_walk2(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
+        const float2 ry = vl_walk2(Pv[t + 1], c, Nv[t + 1]);
         const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-        const float2 Xox = strip_face(RX(xl0 + su * (t + 1)), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
-        const float2 Xoy = strip_face(RY(cl(t)), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
-        const float2 o = strip_collide(CC(cl(t)), L, c, Xix, Xox, Xiy[t], Xoy);
+        const float2 Xox = strip_face(RXi + su * (t + 1), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
+        const float2 Xoy = strip_face(RY + cl(t), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
+        const float2 o = strip_collide(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
         if (act) pw[col(t)] = o;
         Xix = Xox;
         Xiy[t] = Xoy;
       }
     }
+#pragma unroll
+    for (int p = 0; p <= W; p++) {
+      Pv[p] = Cv[p];
+      Cv[p] = Nv[p];
+      Nv[p] = NN[p];
+    }
+    cUU = nUU;
+    cD = nD;
     pr += rs;
     pw += rs;
-  };
-  if (kStripUnroll == 4) {
-    // four row buffers in rotation: each unrolled row names its buffers statically
-    Row R3;
-    float2 uu1, dd1;
-    for (int s = 0; s < nsteps; s += 4) {
-      row_step(s, Pv, Cv, Nv, R3, cUU, cD, uu1, dd1);
-      if (s + 1 >= nsteps) break;
-      row_step(s + 1, Cv, Nv, R3, Pv, uu1, dd1, cUU, cD);
-      if (s + 2 >= nsteps) break;
-      row_step(s + 2, Nv, R3, Pv, Cv, cUU, cD, uu1, dd1);
-      if (s + 3 >= nsteps) break;
-      row_step(s + 3, R3, Pv, Cv, Nv, uu1, dd1, cUU, cD);
-    }
-  } else {
-    for (int s = 0; s < nsteps; s++) {
-      Row NN;
-      float2 nUU, nD;
-      row_step(s, Pv, Cv, Nv, NN, cUU, cD, nUU, nD);
-#pragma unroll
-      for (int p = 0; p <= W; p++) {
-        Pv[p] = Cv[p];
-        Cv[p] = Nv[p];
-        Nv[p] = NN[p];
-      }
-      cUU = nUU;
-      cD = nD;
-    }
   }
   cp_async_wait<0>();
 }
