@@ -9,10 +9,12 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ugks.h"
 #include "ugks_kernels.cuh"
+#include "ugks_f32.cuh"
 #include "ugks_batch.cuh"
 
 using namespace ugks;
@@ -22,7 +24,7 @@ struct ugks_ctx {
   Params P;
   cudaStream_t stream = nullptr;
   int prec = 0;
-  size_t t2 = 16;        // bytes per (h, b) pair in device f
+  size_t t2 = 16;        // FP64 form: bytes per (h, b) pair in device f
   size_t fcells = 0;     // cells of the f buffers (ghost ring 2)
   int nwe = 0;           // cells of the W buffers (ghost ring 1)
   void* f[2] = {nullptr, nullptr};
@@ -52,8 +54,8 @@ struct ugks_ctx {
   double2* grefd = nullptr;  // FP32 form: g_ref per velocity in FP64 (state conversion)
   cudaStream_t xstream = nullptr;     // FP32 form: host <-> staging copies
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  float2* gref = nullptr;    // FP32 form: g_ref per velocity
-  float* ftab = nullptr;     // FP32 form: velocity tables (mvf, uwf)
+  float4* gref4 = nullptr;   // FP32 form: g_ref per slot of the paired-row layout
+  float* ftab = nullptr;     // FP32 form: velocity tables (pwt, uwf)
   size_t stage_bytes = 0;
   std::vector<double> hu, hv, hwu, hwv;
   size_t bytes = 0;
@@ -134,14 +136,27 @@ void set_derived(Params& P) {
   P.d_idy = 1.0 / P.dy;
 }
 
+// Row pairs of the FP32 paired-row layout for a velocity axis: (v < 0 half, all).  Each half
+// of the v axis (v < 0, v >= 0) is padded to an even number of rows.
+std::pair<int, int> f32_row_pairs(int nv, double vmin, double vmax) {
+  std::vector<double> v, w;
+  axis(nv, vmin, vmax, v, w);
+  int mneg = 0;
+  for (int m = 0; m < nv; m++)
+    if (v[m] < 0) mneg = m + 1;
+  const int pn = (mneg + 1) / 2;
+  return {pn, pn + (nv - mneg + 1) / 2};
+}
+
 // Device bytes ugks_create allocates for cfg (cudaMalloc sizes, without allocator rounding).
 size_t predict_bytes(const ugks_config* c) {
   const size_t nx = c->nx, ny = c->ny, nq = (size_t)c->nu * c->nv, nc = nx * ny;
   const bool f32 = c->precision == UGKS_FP32F;
-  const size_t t2 = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t pr_all = f32_row_pairs(c->nv, c->vmin, c->vmax).second, fs = pr_all * c->nu;
+  const size_t fslot = f32 ? fs * sizeof(float4) : nq * sizeof(double2);  // f bytes per cell
   const size_t fcells = (nx + 4) * (ny + 4), nwe = (nx + 2) * (ny + 2);
   const size_t nfx = (nx + 1) * ny, nfy = nx * (ny + 1), nrb = (nc + 127) / 128;
-  size_t b = 2 * fcells * nq * t2 + 2 * 4 * sizeof(double) * nwe + sizeof(double) * kNSum * nwe;
+  size_t b = 2 * fcells * fslot + 2 * 4 * sizeof(double) * nwe + sizeof(double) * kNSum * nwe;
   b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : sizeof(FaceRec) * (nfx + nfy);
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
   b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
@@ -152,8 +167,8 @@ size_t predict_bytes(const ugks_config* c) {
     if (want < 2 * row_d) want = 2 * row_d;
     if (want > row_d * ny) want = row_d * ny;
     if (want < 2 * row_d) want = 2 * row_d;
-    b += want + (sizeof(float2) + sizeof(double2)) * nq +
-         sizeof(float) * (6 * (size_t)c->nv + 2 * (size_t)c->nu);
+    b += want + sizeof(float4) * fs + sizeof(double2) * nq +
+         sizeof(float) * (12 * pr_all + 2 * (size_t)c->nu);
     b += sizeof(SlotDev) + sizeof(BatchWork);
   }
   return b;
@@ -169,15 +184,13 @@ size_t smem_update(int nv) {
   return (1 + 6 * kWarpsPerBlock) * (size_t)nv * sizeof(T);
 }
 
-template <typename T>
-cudaError_t set_smem_limits(int nv) {
-  using T2 = typename Vec2<T>::type;
-  cudaError_t e = cudaFuncSetAttribute(k_sums<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_sums<T>(nv));
+// dynamic shared memory limits of the FP64 form's sums and update kernels
+cudaError_t set_smem_limits_fp64(int nv) {
+  cudaError_t e = cudaFuncSetAttribute(k_sums<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_sums<double>(nv));
   if (e != cudaSuccess) return e;
-  if (sizeof(T) == 4) return cudaSuccess;
-  return cudaFuncSetAttribute(k_update<T, T2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_update<T>(nv));
+  return cudaFuncSetAttribute(k_update<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_update<double>(nv));
 }
 
 const char* const kKernelNames[UGKS_NKERNELS] = {"ghost_x", "ghost_y", "sums", "faces", "cells",
@@ -201,7 +214,9 @@ cudaError_t setup_single_f32(ugks_ctx* h);
 
 template <typename T>
 cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
-  if (sizeof(T) == 4) return launch_step_f32(h, st);
+  if constexpr (sizeof(T) == 4) {
+    return launch_step_f32(h, st);
+  } else {
   using T2 = typename Vec2<T>::type;
   const Params& P = h->P;
   T2* fi = static_cast<T2*>(h->f[h->cur]);
@@ -227,44 +242,15 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
                                        h->cellf, h->mt4);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  k_update<T, T2, false>
+  k_update<T, T2>
       <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
           P, fi, fo, h->fxr, h->fyr, h->cells);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
+  }
 }
 
-// FP64 host/device rows <-> FP32 ring layout (e = f - g_ref); one cell per block iteration,
-// threads over the velocities; rows j0 .. j0+nrows-1 of the physical mesh.
-__global__ void k_rows_to_f32(const double* __restrict__ src, float2* __restrict__ dst, Params P,
-                              const double2* __restrict__ grefd, int j0, int nrows) {
-  const int ncell = P.nx * nrows;
-  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
-    const int r = c / P.nx, i = c - r * P.nx;
-    const double* s = src + (size_t)c * P.nq * 2;
-    float2* d = dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq;
-    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
-      const double2 g = grefd[q];
-      d[q] = make_float2((float)(s[2 * q] - g.x), (float)(s[2 * q + 1] - g.y));
-    }
-  }
-}
-__global__ void k_f32_to_rows(const float2* __restrict__ src, double* __restrict__ dst, Params P,
-                              const double2* __restrict__ grefd, int j0, int nrows) {
-  const int ncell = P.nx * nrows;
-  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
-    const int r = c / P.nx, i = c - r * P.nx;
-    const float2* s = src + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.nq;
-    double* d = dst + (size_t)c * P.nq * 2;
-    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
-      const float2 v = s[q];
-      const double2 g = grefd[q];
-      d[2 * q] = (double)v.x + g.x;
-      d[2 * q + 1] = (double)v.y + g.y;
-    }
-  }
-}
 constexpr int kConvBlocks = 1216;  // 8 per SM
 
 template <typename T2>
@@ -339,7 +325,7 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
     CK(cudaMemcpy2DAsync(dst, (size_t)P.ex * P.nq * h->t2, f, row_d, row_d, P.ny, kind, h->stream));
     return UGKS_OK;
   }
-  float2* dst = static_cast<float2*>(h->f[h->cur]);
+  float4* dst = static_cast<float4*>(h->f[h->cur]);
   if (!from_host) {
     k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(f, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
@@ -374,7 +360,7 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
     CK(cudaMemcpy2DAsync(f, row_d, src, (size_t)P.ex * P.nq * h->t2, row_d, P.ny, kind, h->stream));
     return UGKS_OK;
   }
-  const float2* src = static_cast<const float2*>(h->f[h->cur]);
+  const float4* src = static_cast<const float4*>(h->f[h->cur]);
   if (!to_host) {
     k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, f, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
@@ -588,14 +574,14 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
     NA_CK(cudaMemcpy2DAsync(W0 + (size_t)c * nwe + wcell(P, 0, 0), P.wx * sizeof(double),
                             W_in + (size_t)c * nc, nx * sizeof(double), nx * sizeof(double), ny,
                             cudaMemcpyDeviceToDevice, st));
-  NA_CK(set_smem_limits<double>(P.nv));
+  NA_CK(set_smem_limits_fp64(P.nv));
   k_ghost_x<double2><<<dim3(ny, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                             smem_sums<double>(P.nv), st>>>(P, f0, sums);
   k_faces<double><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
-  k_update<double, double2, false><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
+  k_update<double, double2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                                      smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpy2DAsync(f_out, row, reinterpret_cast<char*>(f1) + ((size_t)2 * P.ex + 2) * nq * sizeof(double2),
@@ -686,9 +672,16 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.m_neg = 0;
   for (int m = 0; m < P.nv; m++)
     if (h->hv[m] < 0) P.m_neg = m + 1;
-  h->nchunk_neg = (P.m_neg * P.nu + 31) / 32;
-  h->nchunk_pos = ((P.nv - P.m_neg) * P.nu + 31) / 32;
-  std::vector<float2> gref_host;
+  {
+    const std::pair<int, int> rp = f32_row_pairs(P.nv, cfg->vmin, cfg->vmax);
+    P.pr_neg = rp.first;
+    P.pr_all = rp.second;
+    P.fs = P.pr_all * P.nu;
+  }
+  // FP32 walk: chunks of 32 slots within each half of the v axis
+  h->nchunk_neg = (P.pr_neg * P.nu + 31) / 32;
+  h->nchunk_pos = ((P.pr_all - P.pr_neg) * P.nu + 31) / 32;
+  std::vector<float4> gref_host;
   std::vector<double2> grefd_host;
   if (h->prec == UGKS_FP32F) {
     double rr = cfg->ref_rho, rU = cfg->ref_U, rV = cfg->ref_V, rT = cfg->ref_T;
@@ -699,14 +692,12 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     P.ref_U = rU;
     P.ref_V = rV;
     P.ref_bf = P.K / (2.0 * P.ref_lam);
-    gref_host.resize((size_t)P.nq);
     grefd_host.resize((size_t)P.nq);
     for (int m = 0; m < P.nv; m++)
       for (int k = 0; k < P.nu; k++) {
         const double u = h->hu[k], v = h->hv[m], w = h->hwu[k] * h->hwv[m];
         double gh, gb;
         ref_maxwellian(P, u, v, gh, gb);
-        gref_host[(size_t)m * P.nu + k] = make_float2((float)gh, (float)gb);
         grefd_host[(size_t)m * P.nu + k] = make_double2(gh, gb);
         const double psi[4] = {gh, u * gh, v * gh, 0.5 * (u * u + v * v) * gh + 0.5 * gb};
         const double hs[4] = {u > 0 ? 1.0 : (u < 0 ? 0.0 : 0.5), u < 0 ? 1.0 : (u > 0 ? 0.0 : 0.5),
@@ -717,6 +708,14 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             P.refsum[sd][kOffW0 + c] += hs[sd] * w * psi[c];
             P.refsum[sd][kOffSf + c] += hs[sd] * w * un[sd] * psi[c];
           }
+      }
+    // g_ref per slot of the paired-row layout (h, h', b, b')
+    gref_host.resize((size_t)P.fs);
+    for (int pr = 0; pr < P.pr_all; pr++)
+      for (int k = 0; k < P.nu; k++) {
+        const double2 g0 = grefd_host[(size_t)prow(P, 2 * pr) * P.nu + k];
+        const double2 g1 = grefd_host[(size_t)prow(P, 2 * pr + 1) * P.nu + k];
+        gref_host[(size_t)pr * P.nu + k] = make_float4((float)g0.x, (float)g1.x, (float)g0.y, (float)g1.y);
       }
   }
 
@@ -729,7 +728,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   };
   h->fcells = (size_t)(P.nx + 4) * (P.ny + 4);
   h->nwe = (P.nx + 2) * (P.ny + 2);
-  const size_t fbytes = h->fcells * P.nq * h->t2;
+  const size_t fbytes = h->fcells * (h->prec == UGKS_FP64 ? P.nq * sizeof(double2) : P.fs * sizeof(float4));
   const int nfx = (P.nx + 1) * P.ny, nfy = P.nx * (P.ny + 1), nc = P.nx * P.ny;
   h->nrblocks = (nc + 127) / 128;
   const bool f32 = h->prec == UGKS_FP32F;
@@ -756,9 +755,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (want > row_d * P.ny) want = row_d * P.ny;
     if (want < 2 * row_d) want = 2 * row_d;  // two halves of at least one row each
     h->stage_bytes = want;
-    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref, sizeof(float2) * (size_t)P.nq) &&
+    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref4, sizeof(float4) * (size_t)P.fs) &&
          alloc((void**)&h->grefd, sizeof(double2) * (size_t)P.nq) &&
-         alloc((void**)&h->ftab, sizeof(float) * (6 * (size_t)P.nv + 2 * (size_t)P.nu));
+         alloc((void**)&h->ftab, sizeof(float) * (12 * (size_t)P.pr_all + 2 * (size_t)P.nu));
     if (ok) {
       e = cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking);
       for (int b = 0; b < 2 && e == cudaSuccess; b++) {
@@ -785,21 +784,29 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.v = h->d_grid + P.nu;
   P.wu = h->d_grid + P.nu + P.nv;
   P.wv = h->d_grid + 2 * P.nu + P.nv;
-  P.gref = h->gref;
+  P.gref4 = h->gref4;
   std::vector<float> ftab_host;
   if (h->ftab) {
-    ftab_host.resize(6 * (size_t)P.nv + 2 * (size_t)P.nu);
-    for (int m = 0; m < P.nv; m++) {
-      const double vv = h->hv[m], w = h->hwv[m];
-      const double t[6] = {w, w * vv, w * vv * vv, w * vv * vv * vv, vv, w * vv * vv * vv * vv};
-      for (int c = 0; c < 6; c++) ftab_host[(size_t)c * P.nv + m] = (float)t[c];
-    }
+    // [pr_all][12]: (w0 w0' w1 w1') (w2 w2' w3 w3') (w4 w4' v v'), then u[nu], wu[nu]
+    ftab_host.assign(12 * (size_t)P.pr_all + 2 * (size_t)P.nu, 0.f);
+    const bool v0 = P.m_pos > P.m_neg;
+    for (int pr = 0; pr < P.pr_all; pr++)
+      for (int h2 = 0; h2 < 2; h2++) {
+        const int r = 2 * pr + h2, m = prow(P, r);
+        const bool real = padrow(P, m) == r;  // padded rows repeat a row with zero weight
+        const double vv = h->hv[m];
+        double w = real ? h->hwv[m] : 0.0;
+        if (real && v0 && m == P.m_neg) w *= 0.5;  // v = 0: half to each half of the v axis
+        float* t = &ftab_host[12 * (size_t)pr];
+        for (int n = 0; n < 5; n++) t[2 * n + h2] = (float)(w * std::pow(vv, n));
+        t[10 + h2] = (float)vv;
+      }
     for (int k = 0; k < P.nu; k++) {
-      ftab_host[6 * (size_t)P.nv + k] = (float)h->hu[k];
-      ftab_host[6 * (size_t)P.nv + P.nu + k] = (float)h->hwu[k];
+      ftab_host[12 * (size_t)P.pr_all + k] = (float)h->hu[k];
+      ftab_host[12 * (size_t)P.pr_all + P.nu + k] = (float)h->hwu[k];
     }
-    P.mvf = h->ftab;
-    P.uwf = h->ftab + 6 * (size_t)P.nv;
+    P.pwt = reinterpret_cast<const float4*>(h->ftab);
+    P.uwf = h->ftab + 12 * (size_t)P.pr_all;
   }
   auto setup = [&]() -> cudaError_t {
     cudaError_t r;
@@ -810,7 +817,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
       if ((r = cudaMemsetAsync(h->W[b], 0, 4 * sizeof(double) * h->nwe, h->stream)) != cudaSuccess) return r;
     }
     if ((r = cudaMemsetAsync(h->rpart, 0, sizeof(double) * 8 * h->nrblocks, h->stream)) != cudaSuccess) return r;
-    if (h->gref && (r = cudaMemcpyAsync(h->gref, gref_host.data(), sizeof(float2) * gref_host.size(),
+    if (h->gref4 && (r = cudaMemcpyAsync(h->gref4, gref_host.data(), sizeof(float4) * gref_host.size(),
                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
     if (h->ftab && (r = cudaMemcpyAsync(h->ftab, ftab_host.data(), sizeof(float) * ftab_host.size(),
@@ -820,8 +827,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
                                          cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
-    if ((r = h->prec == UGKS_FP64 ? set_smem_limits<double>(P.nv) : set_smem_limits<float>(P.nv)) != cudaSuccess)
-      return r;
+    if (h->prec == UGKS_FP64 && (r = set_smem_limits_fp64(P.nv)) != cudaSuccess) return r;
     if ((r = cudaStreamSynchronize(h->stream)) != cudaSuccess) return r;
     return h->prec == UGKS_FP32F ? setup_single_f32(h) : cudaSuccess;
   };
@@ -838,7 +844,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
-                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref, h->grefd, h->fxf, h->fyf,
+                  h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref4, h->grefd, h->fxf, h->fyf,
                   h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->xstream) {
@@ -908,8 +914,8 @@ ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double*
     k_init_maxwellian<double2><<<nc, 128, 0, h->stream>>>(P, prim, static_cast<double2*>(h->f[h->cur]),
                                                           h->W[h->cur], h->nwe);
   else
-    k_init_maxwellian<float2><<<nc, 128, 0, h->stream>>>(P, prim, static_cast<float2*>(h->f[h->cur]),
-                                                         h->W[h->cur], h->nwe);
+    k_init_maxwellian_p<<<nc, 128, 0, h->stream>>>(P, prim, static_cast<float4*>(h->f[h->cur]),
+                                                   h->W[h->cur], h->nwe);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return UGKS_OK;
@@ -1076,8 +1082,8 @@ SlotDev slot_desc(const ugks_ctx* h, int walk_rows) {
   SlotDev S;
   memset(&S, 0, sizeof S);
   S.P = h->P;
-  S.f[0] = static_cast<float2*>(h->f[0]);
-  S.f[1] = static_cast<float2*>(h->f[1]);
+  S.f[0] = static_cast<float4*>(h->f[0]);
+  S.f[1] = static_cast<float4*>(h->f[1]);
   S.W[0] = h->W[0];
   S.W[1] = h->W[1];
   S.sums = reinterpret_cast<float*>(h->sums);

@@ -14,7 +14,7 @@ constexpr int kPhases = 6;  // ghost_x, ghost_y, sums, faces, cells, update (str
 // What the phase kernels need about one instance.
 struct SlotDev {
   Params P;
-  float2* f[2];
+  float4* f[2];
   double* W[2];
   float* sums;
   FaceRecF* fxf;
@@ -85,14 +85,14 @@ __global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* _
   }
 }
 
-__global__ void __launch_bounds__(128, 7) kb_sums(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 4) kb_sums(const SlotDev* __restrict__ slots,
                                                const BatchWork* __restrict__ wk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int total = wk->start[2][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    sums_body<float, float2>(S.P, S.f[S.cur], S.sums, smraw, vb - wk->start[2][a]);
+    sums_body_p(S.P, S.f[S.cur], S.sums, smraw, vb - wk->start[2][a]);
   }
 }
 
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
 
 // Update sweep: one warp per work item (strip, tile, velocity chunk), strips fastest so that
 // the warps of a block share neighbour columns.
-__global__ void __launch_bounds__(128, 4) kb_strip(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 2) kb_strip(const SlotDev* __restrict__ slots,
                                                 const BatchWork* __restrict__ wk) {
   __shared__ __align__(16) float4 ring[kWarpsPerBlock][kRing * kStripChunks];
   const int warp = threadIdx.x >> 5;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128, 4) kb_strip(const SlotDev* __restrict__ s
     const int it = (vb - wk->start[5][a]) * kWarpsPerBlock + warp;
     if (it < ns * nt * (S.nchunk_neg + S.nchunk_pos)) {
       const int c = S.cur;
-      strip_body<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
+      strip_body_p<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
                           it % ns, (it / ns) % nt, it / (ns * nt), ring[warp]);
     }
   }

@@ -1,0 +1,625 @@
+// FP32-f form of the step (FP32 f, FP64 moments / W / interface scalars) in the paired-row
+// layout: ghost fill, the per-cell velocity sums of S1 + S7, and the upwind strip walk of
+// S6, S8 and Eq. 3 (Liu, Hu & Li, arXiv:1810.08137, Sec. 2), plus state conversion and
+// initialisation.  The interface (S2-S5) and cell (Eq. 4) kernels are shared with the FP64
+// form and write the FP32 records read here.
+//
+// Layout.  The v axis is split into its v < 0 rows and its v >= 0 rows; each half is padded
+// to an even number of rows by repeating its last row, and the padded rows are taken in
+// pairs (pr_neg pairs with v < 0, then the v >= 0 pairs, pr_all in total).  A cell holds
+// fs = pr_all * nu float4 slots; slot s = pr * nu + k holds (h, h', b, b') of padded rows
+// 2 pr and 2 pr + 1 at u_k, stored as e = f - g_ref.  The thread that owns a slot owns two
+// velocities with the same u and the same sign of v, so they walk the mesh in the same
+// order, and its arithmetic on them runs as packed FP32 pairs (one instruction for both).
+// Padded rows have zero quadrature weight: the walk updates them like any velocity and the
+// sums never see them.
+#pragma once
+
+namespace ugks {
+
+// ---- packed FP32 pairs (sm_100 family: one instruction for both lanes of a pair) ----
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, exactly as a single subtraction (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
+
+// (h, b) of the two velocities of a slot
+struct P4 {
+  float2 h, b;
+};
+__device__ __forceinline__ P4 ldp(const float4* p) {
+  const float4 v = __ldg(p);
+  return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void stp(float4* p, const P4& v) { *p = make_float4(v.h.x, v.h.y, v.b.x, v.b.y); }
+__device__ __forceinline__ P4 add4(const P4& a, const P4& b) { return {add2(a.h, b.h), add2(a.b, b.b)}; }
+__device__ __forceinline__ P4 zero4() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
+// van Leer half slope r = d1 d2 / (d1 + d2) if d1 d2 > 0 else 0 (d1 = c - a, d2 = b - c),
+// both velocities of a pair
+__device__ __forceinline__ float2 vl_p(float2 a, float2 c, float2 b) {
+  const float2 d1 = sub2(c, a), d2 = sub2(b, c);
+  const float2 p = mul2(d1, d2);
+  const float2 s = add2(d1, d2);
+  const float2 q = mul2(p, make_float2(rcp_ftz(s.x), rcp_ftz(s.y)));
+  return make_float2(p.x > 0.f ? q.x : 0.f, p.y > 0.f ? q.y : 0.f);
+}
+__device__ __forceinline__ P4 vl4(const P4& a, const P4& c, const P4& b) {
+  return {vl_p(a.h, c.h, b.h), vl_p(a.b, c.b, b.b)};
+}
+
+// Real velocity row of padded row r (the pad of each half repeats the half's last row).
+__host__ __device__ __forceinline__ int prow(const Params& P, int r) {
+  const int rn = 2 * P.pr_neg;
+  return r < rn ? (r < P.m_neg - 1 ? r : P.m_neg - 1)
+                : P.m_neg + (r - rn < P.nv - P.m_neg - 1 ? r - rn : P.nv - P.m_neg - 1);
+}
+// Padded row of real row m.
+__host__ __device__ __forceinline__ int padrow(const Params& P, int m) {
+  return m < P.m_neg ? m : 2 * P.pr_neg + (m - P.m_neg);
+}
+
+// -------------------------------------------------------------------------------------
+// Ghost ring (same rules as the FP64 form's fill_ghost_cell: pressure Maxwellian, periodic
+// image, zero-gradient copy next to a wall), over the slots of the paired layout.
+// -------------------------------------------------------------------------------------
+__device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, int gi, int gj,
+                                int si, int sj, int side, bool write_W, int wi, int wj) {
+  const int kind = P.bc_kind[side];
+  float4* dst = f + fcell(P, gi, gj) * P.fs;
+  const float4* src = f + fcell(P, si, sj) * P.fs;
+  const int sw = wcell(P, wi, wj);
+  if (kind == 2) {
+    __shared__ double fu[kMaxAxis], fv[kMaxAxis], ru[kMaxAxis], rv[kMaxAxis];
+    const double rho_a = W[sw], U = W[nwe + sw] / rho_a, V = W[2 * nwe + sw] / rho_a;
+    const double lam = 1.0 / P.bc_T[side], rho = P.bc_rho[side];
+    const double G = rho * lam / kPi, bf = P.K / (2.0 * lam);
+    __syncthreads();  // the tables of the previous cell are no longer read
+    for (int k = threadIdx.x; k < P.nu; k += blockDim.x) {
+      const double du = P.u[k] - U, dr = P.u[k] - P.ref_U;
+      fu[k] = G * exp(-lam * du * du);
+      ru[k] = P.ref_G * exp(-P.ref_lam * dr * dr);
+    }
+    for (int m = threadIdx.x; m < P.nv; m += blockDim.x) {
+      const double dv = P.v[m] - V, dr = P.v[m] - P.ref_V;
+      fv[m] = exp(-lam * dv * dv);
+      rv[m] = exp(-P.ref_lam * dr * dr);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < P.fs; s += blockDim.x) {
+      const int pr = s / P.nu, k = s - pr * P.nu;
+      const int m0 = prow(P, 2 * pr), m1 = prow(P, 2 * pr + 1);
+      const double g0 = fu[k] * fv[m0], r0 = ru[k] * rv[m0];
+      const double g1 = fu[k] * fv[m1], r1 = ru[k] * rv[m1];
+      dst[s] = make_float4((float)(g0 - r0), (float)(g1 - r1), (float)(bf * g0 - P.ref_bf * r0),
+                           (float)(bf * g1 - P.ref_bf * r1));
+    }
+    if (write_W && threadIdx.x == 0) {
+      const int g = wcell(P, gi, gj);
+      W[g] = rho;
+      W[nwe + g] = rho * U;
+      W[2 * nwe + g] = rho * V;
+      W[3 * nwe + g] = rho * (0.5 * (U * U + V * V) + (P.K + 2) / (4.0 * lam));
+    }
+  } else {
+    for (int s = threadIdx.x; s < P.fs; s += blockDim.x) dst[s] = src[s];
+    if (write_W && threadIdx.x == 0) {
+      const int g = wcell(P, gi, gj), s = wcell(P, si, sj);
+      for (int c = 0; c < 4; c++) W[c * nwe + g] = W[c * nwe + s];
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// S1 + S7: per-cell half-range velocity sums (the sums of the FP64 form's sums_body, same
+// output layout), one warp per cell, lane = u index (chunks of 32), loop over row pairs.
+// Per lane and half of the v axis, with w_n = wv v^n, the weighted sums of the cell value c,
+// the x half slope r_x and the y half slope r_y:
+//   a_n = sum w_n c_h (n < 4), ab_n = sum w_n c_b (n < 2), x_n = sum w_n r_x,h (n < 4),
+//   xb_n = sum w_n r_x,b (n < 2), y_n = sum w_n r_y,h (n < 5), yb_n = sum w_n r_y,b (n < 3),
+// each kept as a pair (one accumulator per row of the pair) and added at the end of the half.
+// The v = 0 row (H(0) = 1/2) enters both halves with half weight: the weight table carries
+// its half weight in the v >= 0 half and its part of the v < 0 half is added separately.
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
+                                            float* __restrict__ sums, unsigned char* smraw, int bx) {
+  const int nu = P.nu, fs = P.fs;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* wsum = reinterpret_cast<float*>(smraw) + warp * kNSum;
+  float* tot = reinterpret_cast<float*>(smraw + kWarpsPerBlock * kNSum * sizeof(float)) + tid;
+  for (int t = lane; t < kNSum; t += 32) wsum[t] = 0.f;
+  __syncwarp();
+
+  const int ncx = P.nx + 2;
+  const int cell = bx * kWarpsPerBlock + warp;
+  if (cell >= ncx * (P.ny + 2)) return;
+  const int i = cell % ncx - 1, j = cell / ncx - 1;
+  const bool xg = i < 0 || i >= P.nx, yg = j < 0 || j >= P.ny;
+  if (xg && yg) return;
+  if ((i < 0 && P.bc_kind[0] == 1) || (i >= P.nx && P.bc_kind[1] == 1) ||
+      (j < 0 && P.bc_kind[2] == 1) || (j >= P.ny && P.bc_kind[3] == 1))
+    return;
+  const bool zs = (i < 0 && P.bc_kind[0] == 2) || (i >= P.nx && P.bc_kind[1] == 2) ||
+                  (j < 0 && P.bc_kind[2] == 2) || (j >= P.ny && P.bc_kind[3] == 2);
+
+  const float4* fc = f + fcell(P, i, j) * fs;
+  const long rs = (long)P.ex * fs;
+  const float tdx = P.f_tdx, tdy = P.f_tdy;
+  const int pn = P.pr_neg, pa = P.pr_all;
+  const bool v0 = P.m_pos > P.m_neg;
+  const float4* wt = P.pwt;
+
+  for (int k0 = 0; k0 < nu; k0 += 32) {
+    const int k = k0 + lane;
+    const bool act = k < nu;
+    const int kk = act ? k : nu - 1;
+    const float u = P.uwf[kk];
+    const float wu = act ? P.uwf[nu + kk] : 0.f;
+    const float cu = u * tdx;
+#pragma unroll
+    for (int t = 0; t < kSumsTotals; t++) tot[t * 128] = 0.f;
+    float2 a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
+    auto zero = [&]() {
+      const float2 z = make_float2(0.f, 0.f);
+      a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = z;
+      y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = z;
+    };
+    // one row pair: stencil, slopes, accumulation; returns the centre and its slopes
+    auto pair = [&](int pr, P4& c, P4& rx, P4& ry) {
+      const float4* src = fc + (long)pr * nu + kk;
+      c = ldp(src);
+      const P4 w = ldp(src - fs), e = ldp(src + fs), s = ldp(src - rs), n = ldp(src + rs);
+      if (zs) {
+        rx = ry = zero4();
+      } else {
+        rx = vl4(w, c, e);
+        ry = vl4(s, c, n);
+      }
+      const float4 t0 = __ldg(wt + 3 * pr), t1 = __ldg(wt + 3 * pr + 1), t2 = __ldg(wt + 3 * pr + 2);
+      const float2 w0 = make_float2(t0.x, t0.y), w1 = make_float2(t0.z, t0.w);
+      const float2 w2 = make_float2(t1.x, t1.y), w3 = make_float2(t1.z, t1.w);
+      const float2 w4 = make_float2(t2.x, t2.y);
+      a0 = fma2(w0, c.h, a0); a1 = fma2(w1, c.h, a1); a2 = fma2(w2, c.h, a2); a3 = fma2(w3, c.h, a3);
+      ab0 = fma2(w0, c.b, ab0); ab1 = fma2(w1, c.b, ab1);
+      x0 = fma2(w0, rx.h, x0); x1 = fma2(w1, rx.h, x1); x2 = fma2(w2, rx.h, x2); x3 = fma2(w3, rx.h, x3);
+      xb0 = fma2(w0, rx.b, xb0); xb1 = fma2(w1, rx.b, xb1);
+      y0 = fma2(w0, ry.h, y0); y1 = fma2(w1, ry.h, y1); y2 = fma2(w2, ry.h, y2); y3 = fma2(w3, ry.h, y3);
+      y4 = fma2(w4, ry.h, y4);
+      yb0 = fma2(w0, ry.b, yb0); yb1 = fma2(w1, ry.b, yb1); yb2 = fma2(w2, ry.b, yb2);
+    };
+    // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
+    auto close = [&](float sy, float* side) {
+      const float A0 = hsum(a0), A1 = hsum(a1), A2 = hsum(a2), A3 = hsum(a3);
+      const float AB0 = hsum(ab0), AB1 = hsum(ab1);
+      const float X0 = hsum(x0), X1 = hsum(x1), X2 = hsum(x2), X3 = hsum(x3);
+      const float XB0 = hsum(xb0), XB1 = hsum(xb1);
+      const float Y0 = hsum(y0), Y1 = hsum(y1), Y2 = hsum(y2), Y3 = hsum(y3), Y4 = hsum(y4);
+      const float YB0 = hsum(yb0), YB1 = hsum(yb1), YB2 = hsum(yb2);
+      const float P0 = A0 + sy * Y0, P1 = A1 + sy * Y1, P2 = A2 + sy * Y2, P3 = A3 + sy * Y3;
+      const float Pb0 = AB0 + sy * YB0, Pb1 = AB1 + sy * YB1;
+      const float Z1 = cu * X1 + tdy * Y2, Z2 = cu * X2 + tdy * Y3, Z3 = cu * X3 + tdy * Y4;
+      const float Zb1 = cu * XB1 + tdy * YB2;
+      finalize_y<float, float2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, X0, X1, X2, XB0, Z1, Z2, Z3, Zb1,
+                                lane, side);
+      const float h[kSumsTotals] = {A0, A1, A2, AB0, X0, X1, X2, XB0, Y0, Y1, Y2, Y3, YB0, YB1};
+#pragma unroll
+      for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
+    };
+    // v >= 0 half; its first pair holds the v = 0 row (if any) as its first row
+    zero();
+    float s0h = 0.f, s0b = 0.f, s0xh = 0.f, s0xb = 0.f, s0yh = 0.f, s0yb = 0.f;
+    if (pa > pn) {
+      P4 c, rx, ry;
+      pair(pn, c, rx, ry);
+      if (v0) {
+        const float hw = __ldg(&wt[3 * pn].x);
+        s0h = hw * c.h.x; s0b = hw * c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
+        s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
+      }
+#pragma unroll 1
+      for (int pr = pn + 1; pr < pa; pr++) pair(pr, c, rx, ry);
+    }
+    close(1.f, wsum + kSumN);
+    // v < 0 half, with the v = 0 row's half weight
+    zero();
+    a0.x = s0h; ab0.x = s0b; x0.x = s0xh; xb0.x = s0xb; y0.x = s0yh; yb0.x = s0yb;
+#pragma unroll 1
+    for (int pr = 0; pr < pn; pr++) {
+      P4 c, rx, ry;
+      pair(pr, c, rx, ry);
+    }
+    close(-1.f, wsum + kSumS);
+    // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
+    const float tA0 = tot[0], tA1 = tot[128], tA2 = tot[256], tAb = tot[384], tR0 = tot[512];
+    const float tR1 = tot[640], tR2 = tot[768], tRb = tot[896], tC0 = tot[1024], tC1 = tot[1152];
+    const float tC2 = tot[1280], tC3 = tot[1408], tCb0 = tot[1536], tCb1 = tot[1664];
+    const float D0 = cu * tR0 + tdy * tC1, D1 = cu * tR1 + tdy * tC2, D2 = cu * tR2 + tdy * tC3;
+    const float Db = cu * tRb + tdy * tCb1;
+    const float hE = u > 0.f ? 1.f : (u < 0.f ? 0.f : 0.5f);
+    const float hW = u < 0.f ? 1.f : (u > 0.f ? 0.f : 0.5f);
+    float xv[32];
+    const float uu = u * u;
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const float sg = sd == 0 ? 1.f : -1.f;
+      const float wgt = wu * (sd == 0 ? hE : hW);
+      const float F0 = tA0 + sg * tR0, F1 = tA1 + sg * tR1, F2 = tA2 + sg * tR2, Fb = tAb + sg * tRb;
+      float* o = xv + 16 * sd;
+      o[0] = wgt * F0;
+      o[1] = wgt * u * F0;
+      o[2] = wgt * F1;
+      o[3] = wgt * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+      const float ws = wgt * tdy;
+      o[4] = ws * tC0;
+      o[5] = ws * u * tC0;
+      o[6] = ws * tC1;
+      o[7] = ws * (0.5f * (uu * tC0 + tC2) + 0.5f * tCb0);
+      const float wuu = wgt * u;
+      o[8] = wuu * F0;
+      o[9] = wuu * u * F0;
+      o[10] = wuu * F1;
+      o[11] = wuu * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+      o[12] = wuu * D0;
+      o[13] = wuu * u * D0;
+      o[14] = wuu * D1;
+      o[15] = wuu * (0.5f * (uu * D0 + D2) + 0.5f * Db);
+    }
+    const float r = warp_reduce_scatter<32>(xv, lane);
+    wsum[kSumE + lane] += r;  // lanes 0..15: E side, 16..31: W side
+  }
+  __syncwarp();
+  float* out = sums + (size_t)cell * kNSum;
+  out[lane] = wsum[lane];
+  out[lane + 32] = wsum[lane + 32];
+}
+
+// -------------------------------------------------------------------------------------
+// S6 + S8 and Eq. 3 as an upwind strip walk.  For one velocity the micro flux through a face
+// depends only on its upwind cell, so each cell evaluates the flux through its downwind
+// x-face and downwind y-face and receives the flux through its upwind faces from its upwind
+// neighbours.  A warp (lane = slot: two velocities with the same u and the same sign of v)
+// owns a strip of W adjacent columns and walks it row by row in the direction of v; within
+// a row it visits the columns in the direction of u.  The x-upwind flux of a column is the
+// previous column's downwind flux, the y-upwind flux is the previous row's, both carried in
+// registers; only the strip's first column needs the flux out of the cell before the strip
+// (U), evaluated from U's own reconstruction.  Slopes are taken along the walk (upwind,
+// centre, downwind), so the upwind face value is f + slope and u sigma_x = |u| (2/dx) slope.
+// Work item: (slot chunk of 32, v < 0 chunks first; tile of `rows` rows; strip).
+// -------------------------------------------------------------------------------------
+constexpr int kWalkRows = 64;  // default rows per walk tile
+constexpr int kStripW = 4;     // columns per strip
+constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
+// 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
+constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Per-lane velocity constants of the walk (u shared by the pair, v per velocity).
+struct PairLane {
+  float u, uu, cu, au, dt;   // u, u^2, |u| 2/dx, |u|/dx, dt
+  float2 v, uv, vv, r2, ur2, vr2;
+  float2 cv, av;             // |v| 2/dy, |v|/dy
+  float2 grh, grb, ngrh, ngrb;  // g_ref (h, b) and its negative
+};
+
+// 2^(E0 + E1 u + E2 v + E3 r2) for both velocities
+__device__ __forceinline__ float2 exp_p(const float4 e, const PairLane& L) {
+  const float2 a = fma2(f2(e.w), L.r2, fma2(f2(e.z), L.v, f2(fmaf(e.y, L.u, e.x))));
+  return make_float2(ex2_ftz(a.x), ex2_ftz(a.y));
+}
+
+// Micro flux through a face (FaceRecF), e-form f_up and d = u sigma_x + v sigma_y.
+__device__ __forceinline__ P4 face_p(const FaceRecF* R, int side, const PairLane& L, const P4& fup,
+                                     const P4& d) {
+  const float4 a = ld4(&R->Q[side][0]);
+  const float4 b = ld4(&R->Q[side][4]);
+  const float4 k = ld4(&R->K[side][0]);
+  const float4 e = ld4(&R->E[0]);
+  const float2 t = *reinterpret_cast<const float2*>(&R->Mt4);  // Mt4, -Mt5
+  float2 qh = fma2(f2(a.z), L.v, f2(fmaf(a.y, L.u, a.x)));
+  qh = fma2(f2(a.w), f2(L.uu), qh);
+  qh = fma2(f2(b.x), L.uv, qh);
+  qh = fma2(f2(b.y), L.vv, qh);
+  qh = fma2(f2(b.z), L.ur2, qh);
+  qh = fma2(f2(b.w), L.vr2, qh);
+  const float2 qb = fma2(f2(k.w), qh, fma2(f2(k.z), L.v, f2(fmaf(k.y, L.u, k.x))));
+  const float2 g = exp_p(e, L);
+  P4 X;
+  X.h = fma2(qh, g, fma2(f2(t.x), fup.h, mul2(f2(t.y), d.h)));
+  X.b = fma2(qb, g, fma2(f2(t.x), fup.b, mul2(f2(t.y), d.b)));
+  return X;
+}
+
+// Flux leaving a diffuse wall into the gas, e-form.
+__device__ __forceinline__ P4 wall_p(const FaceRecF* R, const PairLane& L) {
+  const float4 e = ld4(&R->E[0]);
+  const float gdt = R->gdt, X2 = R->K[0][3];
+  const float2 g = exp_p(e, L);
+  const float ndt = -L.dt;
+  P4 X;
+  X.h = fma2(f2(gdt), g, mul2(f2(ndt), L.grh));
+  X.b = fma2(f2(gdt * X2), g, mul2(f2(ndt), L.grb));
+  return X;
+}
+
+// Eq. 3 increment of one cell (CellRecF); Xi / Xo: inflow / outflow flux in x and y.
+__device__ __forceinline__ P4 collide_p(const CellRecF* C, const PairLane& L, const P4& e,
+                                        const P4& Xix, const P4& Xox, const P4& Xiy, const P4& Xoy) {
+  const float4 en = ld4(&C->En[0]);
+  const float4 e1 = ld4(&C->E1[0]);
+  const float4 A = ld4(&C->A1);    // A1 An b1 bn
+  const float4 B = ld4(&C->nBs);   // -Bs irx iry inv
+  const float2 gn = exp_p(en, L), g1 = exp_p(e1, L);
+  const float2 r = fma2(L.v, f2(B.z), f2(L.u * B.y));
+  const float aui = L.au * B.w;
+  const float2 avi = mul2(L.av, f2(B.w));
+  float2 dh = fma2(f2(aui), sub2(Xix.h, Xox.h), mul2(avi, sub2(Xiy.h, Xoy.h)));
+  float2 db = fma2(f2(aui), sub2(Xix.b, Xox.b), mul2(avi, sub2(Xiy.b, Xoy.b)));
+  dh = fma2(f2(A.x), add2(g1, L.ngrh),
+            fma2(f2(A.y), add2(gn, L.ngrh), fma2(r, L.grh, fma2(f2(B.x), e.h, dh))));
+  db = fma2(f2(A.x), fma2(f2(A.z), g1, L.ngrb),
+            fma2(f2(A.y), fma2(f2(A.w), gn, L.ngrb), fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
+  return {add2(e.h, dh), add2(e.b, db)};
+}
+
+__device__ __forceinline__ P4 slope_d(const PairLane& L, const P4& rx, const P4& ry) {
+  return {fma2(f2(L.cu), rx.h, mul2(L.cv, ry.h)), fma2(f2(L.cu), rx.b, mul2(L.cv, ry.b))};
+}
+
+template <int W>
+__device__ __forceinline__ void strip_body_p(const Params& P, const float4* __restrict__ f,
+                                             float4* __restrict__ fo, const FaceRecF* __restrict__ fxr,
+                                             const FaceRecF* __restrict__ fyr,
+                                             const CellRecF* __restrict__ cr, int nchunk_neg,
+                                             int rows, int bx, int by, int chunk,
+                                             float4* __restrict__ ring) {
+  const int lane = threadIdx.x & 31;
+  const int nx = P.nx, ny = P.ny, nu = P.nu, fs = P.fs;
+  const int i0 = bx * W;
+  const int wc = min(W, nx - i0);
+  const bool vpos = chunk >= nchunk_neg;
+  const int sn = P.pr_neg * nu;                        // slots of the v < 0 half
+  const int s = vpos ? sn + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
+  const int send = vpos ? fs : sn;
+  const bool act = s < send;
+  const int ss = act ? s : send - 1;
+  const int pr = ss / nu, k = ss - pr * nu;
+  PairLane L;
+  L.u = P.uwf[k];
+  {
+    const float4 t2 = __ldg(P.pwt + 3 * pr + 2);
+    L.v = make_float2(t2.z, t2.w);
+  }
+  L.uu = L.u * L.u;
+  L.uv = mul2(f2(L.u), L.v);
+  L.vv = mul2(L.v, L.v);
+  L.r2 = add2(f2(L.uu), L.vv);
+  L.ur2 = mul2(f2(L.u), L.r2);
+  L.vr2 = mul2(L.v, L.r2);
+  L.cu = fabsf(L.u) * P.f_tdx;
+  L.au = fabsf(L.u) * P.f_idx;
+  L.cv = make_float2(fabsf(L.v.x) * P.f_tdy, fabsf(L.v.y) * P.f_tdy);
+  L.av = make_float2(fabsf(L.v.x) * P.f_idy, fabsf(L.v.y) * P.f_idy);
+  {
+    const float4 g = __ldg(P.gref4 + ss);
+    L.grh = make_float2(g.x, g.y);
+    L.grb = make_float2(g.z, g.w);
+    L.ngrh = make_float2(-g.x, -g.y);
+    L.ngrb = make_float2(-g.z, -g.w);
+  }
+  L.dt = P.f_dt;
+  const int su = L.u > 0.f ? 1 : -1;
+  const int sv = vpos ? 1 : -1;
+  const int xside = su > 0 ? 0 : 1, yside = vpos ? 0 : 1;
+  const int ib = su > 0 ? i0 : i0 + wc - 1;            // strip position 0 (walk order)
+  const int iU = ib - su;                              // upwind neighbour column U
+  const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
+  const bool zu = (iU < 0 && pW) || (iU >= nx && pE);  // U is a pressure ghost: zero slopes
+  const int xo = su * fs;                              // one column in walk order, in slots
+  // walk position p (-2 = UU, -1 = U, 0..W-1 strip, W = D) -> column offset; strip positions
+  // past the strip's end read column D (they are not updated)
+  auto col = [&](int p) { return (p < wc ? p : wc) * xo; };
+
+  const int j0 = by * rows;
+  const int j1 = min(j0 + rows, ny);
+  const int jfirst = sv > 0 ? j0 : j1 - 1;
+  const int nsteps = j1 - j0;
+  const long rs = (long)sv * P.ex * fs;                // one row in walk order, in slots
+  const long base = ((long)(jfirst + 2) * P.ex + ib + 2) * fs + ss;
+  const float4* pr_ = f + base;                        // (position 0, row jfirst)
+  float4* pw = fo + base;
+
+  // rows jfirst - sv (Pv), jfirst (Cv), jfirst + sv (Nv) at positions -1..W-1
+  P4 Pv[W + 1], Cv[W + 1], Nv[W + 1];
+#pragma unroll
+  for (int p = -1; p < W; p++) {
+    Pv[p + 1] = ldp(pr_ - rs + col(p));
+    Cv[p + 1] = ldp(pr_ + col(p));
+    Nv[p + 1] = ldp(pr_ + rs + col(p));
+  }
+  P4 cUU = ldp(pr_ + col(-2)), cD = ldp(pr_ + col(W));
+
+  // prologue: flux through the y-face between the halo row jp = jfirst - sv and jfirst
+  P4 Xiy[W];
+  {
+    const int jp = jfirst - sv;
+    const FaceRecF* RY = fyr + (long)(sv > 0 ? jfirst : jfirst + 1) * nx + ib;
+    const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
+    const P4 dp = ldp(pr_ - rs + col(W));
+    if (RY->wall != 0.f) {
+#pragma unroll
+      for (int t = 0; t < W; t++)
+        if (t < wc) Xiy[t] = wall_p(RY + su * t, L);
+    } else {
+#pragma unroll
+      for (int t = 0; t < W; t++) {
+        if (t < wc) {
+          const P4 pp = ldp(pr_ - 2 * rs + col(t));
+          const P4 c = Pv[t + 1];
+          P4 rx = vl4(Pv[t], c, t + 1 < W ? Pv[t + 2] : dp);
+          P4 ry = vl4(pp, c, Cv[t + 1]);
+          if (zp) rx = ry = zero4();
+          Xiy[t] = face_p(RY + su * t, yside, L, add4(c, ry), slope_d(L, rx, ry));
+        }
+      }
+    }
+  }
+
+  // face and cell records of a row, staged through a ring of kRing rows in shared memory:
+  // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
+  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
+  auto stage = [&](int st) {
+    if (st < nsteps) {
+      const int j = jfirst + sv * st;
+      const float4* gx = reinterpret_cast<const float4*>(fxr + (long)j * (nx + 1) + i0);
+      const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
+      const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
+      float4* dst = ring + (st % kRing) * kStripChunks;
+      for (int c = lane; c < kStripChunks; c += 32) {
+        if (c < oY) {
+          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
+        } else if (c < oC) {
+          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
+        } else if (c - oC < wc * 4) {
+          cp_async16(dst + c, gc + (c - oC));
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  __syncwarp();                      // the ring's previous contents are no longer read
+#pragma unroll
+  for (int st = 0; st < kRing - 1; st++) stage(st);
+  // local record index of walk position t (-1 = U's face for x) within the staged row
+  const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
+  auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
+  for (int st = 0; st < nsteps; st++) {
+    __syncwarp();                    // every lane is done with the slot refilled next
+    stage(st + kRing - 1);
+    // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
+    P4 NN[W + 1];
+#pragma unroll
+    for (int p = -1; p < W; p++) NN[p + 1] = ldp(pr_ + 2 * rs + col(p));
+    const P4 nUU = ldp(pr_ + rs + col(-2)), nD = ldp(pr_ + rs + col(W));
+    cp_async_wait<kRing - 1>();
+    __syncwarp();
+    const float4* row = ring + (st % kRing) * kStripChunks;
+    const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
+    const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
+    const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
+
+    // flux into position 0 out of U (or off the wall)
+    P4 Xix;
+    const FaceRecF* RXi = RX + xl0;
+    if (RXi->wall != 0.f) {
+      Xix = wall_p(RXi, L);
+    } else {
+      P4 rx = vl4(cUU, Cv[0], Cv[1]);
+      P4 ry = vl4(Pv[0], Cv[0], Nv[0]);
+      if (zu) rx = ry = zero4();
+      Xix = face_p(RXi, xside, L, add4(Cv[0], rx), slope_d(L, rx, ry));
+    }
+#pragma unroll
+    for (int t = 0; t < W; t++) {
+      if (t < wc) {
+        const P4 c = Cv[t + 1];
+        const P4 rx = vl4(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
+        const P4 ry = vl4(Pv[t + 1], c, Nv[t + 1]);
+        const P4 d = slope_d(L, rx, ry);
+        const P4 Xox = face_p(RXi + su * (t + 1), xside, L, add4(c, rx), d);
+        const P4 Xoy = face_p(RY + cl(t), yside, L, add4(c, ry), d);
+        const P4 o = collide_p(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
+        if (act) stp(pw + col(t), o);
+        Xix = Xox;
+        Xiy[t] = Xoy;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p <= W; p++) {
+      Pv[p] = Cv[p];
+      Cv[p] = Nv[p];
+      Nv[p] = NN[p];
+    }
+    cUU = nUU;
+    cD = nD;
+    pr_ += rs;
+    pw += rs;
+  }
+  cp_async_wait<0>();
+}
+
+// -------------------------------------------------------------------------------------
+// State conversion and initialisation (set-up and checkpoint paths, not the step)
+// -------------------------------------------------------------------------------------
+// FP64 rows [cell][q][(h, b)] (rows j0 .. j0+nrows-1) -> paired slots, e = f - g_ref.
+__global__ void k_rows_to_f32(const double* __restrict__ src, float4* __restrict__ dst, Params P,
+                              const double2* __restrict__ grefd, int j0, int nrows) {
+  const int ncell = P.nx * nrows;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    const int r = c / P.nx, i = c - r * P.nx;
+    const double* s = src + (size_t)c * P.nq * 2;
+    float4* d = dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs;
+    for (int t = threadIdx.x; t < P.fs; t += blockDim.x) {
+      const int pr = t / P.nu, k = t - pr * P.nu;
+      const int q0 = prow(P, 2 * pr) * P.nu + k, q1 = prow(P, 2 * pr + 1) * P.nu + k;
+      const double2 g0 = grefd[q0], g1 = grefd[q1];
+      d[t] = make_float4((float)(s[2 * q0] - g0.x), (float)(s[2 * q1] - g1.x),
+                         (float)(s[2 * q0 + 1] - g0.y), (float)(s[2 * q1 + 1] - g1.y));
+    }
+  }
+}
+// paired slots -> FP64 rows, f = e + g_ref
+__global__ void k_f32_to_rows(const float4* __restrict__ src, double* __restrict__ dst, Params P,
+                              const double2* __restrict__ grefd, int j0, int nrows) {
+  const int ncell = P.nx * nrows;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    const int r = c / P.nx, i = c - r * P.nx;
+    const float4* s = src + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs;
+    double* d = dst + (size_t)c * P.nq * 2;
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+      const int m = q / P.nu, k = q - m * P.nu, pr = padrow(P, m);
+      const float4 v = s[(pr >> 1) * P.nu + k];
+      const double2 g = grefd[q];
+      d[2 * q] = (double)((pr & 1) ? v.y : v.x) + g.x;
+      d[2 * q + 1] = (double)((pr & 1) ? v.w : v.z) + g.y;
+    }
+  }
+}
+
+// Pointwise Maxwellian of (rho, U, V, T) per cell, paired slots, and W.
+__global__ void k_init_maxwellian_p(Params P, const double* __restrict__ prim, float4* __restrict__ f,
+                                    double* __restrict__ W, int nwe) {
+  const int nc = P.nx * P.ny;
+  const int cell = blockIdx.x;
+  if (cell >= nc) return;
+  const int i = cell % P.nx, j = cell / P.nx;
+  const double rho = prim[cell], U = prim[nc + cell], V = prim[2 * nc + cell], T = prim[3 * nc + cell];
+  const double lam = 1.0 / T, G = rho * lam / kPi, bf = P.K / (2.0 * lam);
+  float4* dst = f + fcell(P, i, j) * P.fs;
+  for (int t = threadIdx.x; t < P.fs; t += blockDim.x) {
+    const int pr = t / P.nu, k = t - pr * P.nu;
+    double o[4];
+    for (int h = 0; h < 2; h++) {
+      const int m = prow(P, 2 * pr + h);
+      const double du = P.u[k] - U, dv = P.v[m] - V;
+      const double gh = G * exp(-lam * (du * du + dv * dv));
+      double rh, rb;
+      ref_maxwellian(P, P.u[k], P.v[m], rh, rb);
+      o[h] = gh - rh;
+      o[2 + h] = bf * gh - rb;
+    }
+    dst[t] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+  }
+  if (threadIdx.x == 0) {
+    const int w = wcell(P, i, j);
+    W[w] = rho;
+    W[nwe + w] = rho * U;
+    W[2 * nwe + w] = rho * V;
+    W[3 * nwe + w] = rho * (0.5 * (U * U + V * V) + (P.K + 2) / (4.0 * lam));
+  }
+}
+
+}  // namespace ugks

@@ -57,27 +57,27 @@ struct CellRec {
 // Maxwellian written as 2^(E0 + E1 u + E2 v + E3 r2), so that a lane evaluates a face or
 // cell with fused multiply-adds and one exp2.
 //   micro flux through a face, side s = 0 (un > 0) or 1 (un < 0), e-form f_up and d:
-//     X_h = Q_h g + Mt4 f_up,h - Mt5 d_h,   Q_h = sum_k Q[s][k] m_k,
-//     X_b = Q_b g + Mt4 f_up,b - Mt5 d_b,   Q_b = K[s][3] Q_h + K[s][0] + K[s][1] u + K[s][2] v,
+//     X_h = Q_h g + Mt4 f_up,h + nMt5 d_h,  Q_h = sum_k Q[s][k] m_k,  nMt5 = -Mt5,
+//     X_b = Q_b g + Mt4 f_up,b + nMt5 d_b,  Q_b = K[s][3] Q_h + K[s][0] + K[s][1] u + K[s][2] v,
 //     g = 2^(E . (1, u, v, r2))
 //   inflow from a diffuse wall (wall != 0): X_h = gdt g - dt g_ref,h, X_b = gdt K[0][3] g - dt g_ref,b
 struct __align__(16) FaceRecF {
   float Q[2][8];
   float K[2][4];
   float E[4];
-  float Mt4, Mt5, wall, gdt;
+  float Mt4, nMt5, wall, gdt;
 };
 // Eq. 3 as an increment e^{n+1} = e^n + d, per component, with the Maxwellians taken
 // relative to g_ref before they are weighted (the terms stay at the deviation's scale):
-//   d_h = aui dX_h + avi dY_h + r g_ref,h + A1 (g1 - g_ref,h) + An (gn - g_ref,h) - Bs e_h
-//   d_b = aui dX_b + avi dY_b + r g_ref,b + A1 (b1 g1 - g_ref,b) + An (bn gn - g_ref,b) - Bs e_b
+//   d_h = aui dX_h + avi dY_h + r g_ref,h + A1 (g1 - g_ref,h) + An (gn - g_ref,h) + nBs e_h
+//   d_b = aui dX_b + avi dY_b + r g_ref,b + A1 (b1 g1 - g_ref,b) + An (bn gn - g_ref,b) + nBs e_b
 // with gn = 2^(En . (1, u, v, r2)), g1 likewise, aui = inv |u|/dx, avi = inv |v|/dy,
 // r = u irx + v iry, dX / dY the inflow minus outflow micro flux in x / y.
 struct __align__(16) CellRecF {
   float En[4];
   float E1[4];
   float A1, An, b1, bn;     // inv cg1, inv cgn, K/(2 lam^{n+1}), K/(2 lam^n)
-  float Bs, irx, iry, inv;  // inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
+  float nBs, irx, iry, inv; // -inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 
 struct Params {
@@ -97,12 +97,17 @@ struct Params {
   double ref_G, ref_U, ref_V, ref_lam, ref_bf;  // g_ref,h = G exp(-lam((u-U)^2+(v-V)^2)), b = bf h
   double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
-  const void* gref;       // [nq] T2 table of g_ref (FP32 form), else null
+  // FP32 form, paired-row layout (see ugks_f32.cuh): pr_neg row pairs with v < 0, pr_all
+  // row pairs in total, fs = pr_all * nu float4 slots per cell
+  int pr_neg, pr_all, fs;
+  const float4* gref4;    // [fs] g_ref of each slot (h, h', b, b')
+  const float4* pwt;      // [pr_all][3]: (w0 w0' w1 w1') (w2 w2' w3 w3') (w4 w4' v v'),
+                          // w_n = wv v^n of the pair's two rows; zero on padded rows, half
+                          // of wv on the v = 0 row
   int omega_half;         // omega == 1/2: lam^-omega = rsqrt(lam)
   // derived FP64 constants (set by set_derived): 1/(K+2), dt/(2 mu_ref), dt/(4 mu_ref),
   // 2/dx, 2/dy, 1/dx, 1/dy
   double inv_kp2, half_dt_mu, quarter_dt_mu, d_tdx, d_tdy, d_idx, d_idy;
-  const float* mvf;       // FP32 tables: [6][nv] wv, wv v, wv v^2, wv v^3, v, wv v^4
   const float* uwf;       // FP32 tables: [2][nu] u, wu
   const double* mvd;      // [5][nv] wv v^n, n = 0..4
   float f_tdx, f_tdy, f_idx, f_idy, f_dt;  // FP32 2/dx, 2/dy, 1/dx, 1/dy, dt

@@ -11,6 +11,8 @@
 //   k_cells               conservative W update (Eq. 4), g^n, g^{n+1}, tau^n, tau^{n+1}
 //   k_update              micro flux of the four faces and the implicit f update (Eq. 3)
 //                         over a second read of f and one write of f^{n+1}
+// These are the FP64 form's kernels; the FP32-f form (FP32 f in a paired-row layout) has
+// its own ghost fill, sums and update in ugks_f32.cuh and shares k_faces and k_cells.
 //
 // Layout: f[(ny+4)(nx+4)][nq] of T2 = (h, b), velocity innermost (q = m*nu + k), a ghost
 // ring two cells wide; W[4][(ny+2)(nx+2)] FP64 with a ghost ring one cell wide.
@@ -70,13 +72,6 @@ __device__ __forceinline__ void cp_async8(void* sm, const void* gm) {
 __device__ __forceinline__ void cp_async_f(float2* sm, const float2* gm) { cp_async8(sm, gm); }
 __device__ __forceinline__ void cp_async_f(double2* sm, const double2* gm) { cp_async16(sm, gm); }
 
-__device__ __forceinline__ float vl_half(float a, float c, float b) {
-  float d1 = c - a, d2 = b - c, p = d1 * d2;
-  return p > 0.0f ? p * rcp_ftz(d1 + d2) : 0.0f;
-}
-
-__device__ __forceinline__ double texp(double x) { return exp(x); }
-__device__ __forceinline__ float texp(float x) { return expf(x); }
 
 // Collision time tau = mu / p with mu = mu_ref T^omega, T = 1/lam, p = rho / (2 lam).
 __device__ __forceinline__ double collision_time(const Params& P, double rho, double lam) {
@@ -165,6 +160,10 @@ __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int 
   }
 }
 
+// FP32 paired-row layout (ugks_f32.cuh)
+__device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, int gi, int gj,
+                                int si, int sj, int side, bool write_W, int wi, int wj);
+
 // x-sides, rows 0..ny-1; grid (ny, 4): blockIdx.y = side*2 + layer-1.
 template <typename T2>
 __device__ __forceinline__ void ghost_x_body(const Params& P, T2* f, double* W, int nwe, int bx, int by) {
@@ -234,22 +233,13 @@ __device__ __forceinline__ void finalize_y(T u, T wu, T tdx, T P0, T P1, T P2, T
   if (lane < 16) ws_side[lane] += r;
 }
 
-// velocity tables in the arithmetic type (FP32 tables are rounded from FP64 on the host)
 // wv v^n, n = 0..4, of row m (global tables, L1 resident)
 __device__ __forceinline__ void wtab(const Params& P, int m, double* o) {
 #pragma unroll
   for (int n = 0; n < 5; n++) o[n] = __ldg(P.mvd + n * P.nv + m);
 }
-__device__ __forceinline__ void wtab(const Params& P, int m, float* o) {
-#pragma unroll
-  for (int n = 0; n < 4; n++) o[n] = __ldg(P.mvf + n * P.nv + m);
-  o[4] = __ldg(P.mvf + 5 * P.nv + m);
-}
 __device__ __forceinline__ void utab(const Params& P, int k, double& u, double& wu) {
   u = P.u[k]; wu = P.wu[k];
-}
-__device__ __forceinline__ void utab(const Params& P, int k, float& u, float& wu) {
-  u = P.uwf[k]; wu = P.uwf[P.nu + k];
 }
 
 template <typename T, typename T2>
@@ -607,7 +597,7 @@ __device__ void pack_face_f32(bool isx, const double (*Qh)[8], const double (*kb
   RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
   RF->E[3] = (float)(-lam * kLog2e);
   RF->Mt4 = (float)Mt4;
-  RF->Mt5 = (float)Mt5;
+  RF->nMt5 = (float)(-Mt5);
   RF->wall = (float)wall;
   RF->gdt = (float)gdt;
 }
@@ -883,7 +873,7 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       F.An = (float)(R.inv * R.cgn);
       F.b1 = (float)R.b1;
       F.bn = (float)R.bn;
-      F.Bs = (float)(R.inv * (R.cg1 + R.cgn));
+      F.nBs = (float)(-(R.inv * (R.cg1 + R.cgn)));
       F.irx = (float)(R.inv * refx);
       F.iry = (float)(R.inv * refy);
       F.inv = (float)R.inv;
@@ -924,9 +914,7 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
 //   df = inv [ flux + cg1 (g^{n+1} - f^n) + cgn (g^n - f^n) ],
 // so that rounding acts on df rather than on f.  One warp per interior cell, lane = u
 // index (chunks of 32); the v loop is split into v <= 0 and v > 0 so that the y-upwind
-// side is fixed in each half.  In the FP32 form the buffers hold e = f - g_ref and the
-// g_ref part of the flux, u (Mt4_W - Mt4_E)/dx g_ref + v (Mt4_S - Mt4_N)/dy g_ref, is
-// added from FP64 face constants.
+// side is fixed in each half.  FP64 form.
 // -------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void poly_in_v_xface(const double* c, double u, T* q) {
@@ -955,11 +943,10 @@ template <typename T>
 struct UpdCell {
   T Mt4[4], Mt5[4], bf[4];
   T inv, cg1, cgn, cg1b, cgnb;
-  T refx, refy;   // (Mt4_W - Mt4_E)/dx, (Mt4_S - Mt4_N)/dy (FP32 form), else 0
   int wall[4];
 };
 
-template <typename T, typename T2, bool REF>
+template <typename T, typename T2>
 __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__ f,
                                                 T2* __restrict__ fo,
                                                 const FaceRec* __restrict__ fxr,
@@ -1006,15 +993,12 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     K.cgn = (T)C.cgn;
     K.cg1b = (T)(C.cg1 * C.b1);
     K.cgnb = (T)(C.cgn * C.bn);
-    K.refx = REF ? (T)((RW.Mt4 - RE.Mt4) / P.dx) : T(0);
-    K.refy = REF ? (T)((RS.Mt4 - RN.Mt4) / P.dy) : T(0);
   }
   const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy), idx = T(1.0 / P.dx), idy = T(1.0 / P.dy);
   const T dtT = (T)P.dt;
   const long rs = (long)P.ex * nq;
   const T2* fc0 = f + fcell(P, i, j) * nq;
   T2* fo0 = fo + fcell(P, i, j) * nq;
-  const T2* gref = static_cast<const T2*>(P.gref);
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
@@ -1043,7 +1027,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     const bool up = ud > 0.0;  // x upwind neighbour: W for u > 0, E for u < 0
     const long xo = up ? -(long)nq : (long)nq;
     const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
-    const T cu = u * tdx, fxu = u * idx, refxu = u * K.refx;
+    const T cu = u * tdx, fxu = u * idx;
 
     // one half of the v range: VUP = (v > 0); y-upwind neighbour S for v > 0, N otherwise
     auto half = [&](auto vup_tag, int m0, int m1) {
@@ -1099,17 +1083,14 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
           fSh = c.x - rych; fSb = c.y - rycb; dSh = dch; dSb = dcb;
           fNh = yu.x - ryvh; fNb = yu.y - ryvb; dNh = dvh; dNb = dvb;
         }
-        T2 gr;
-        if (REF) gr = gref[(size_t)m * nu + kk];
-        else { gr.x = T(0); gr.y = T(0); }
         // X = Q g + Mt4 f_up - Mt5 d (UGKS face), X = dt f_w (wall); F~ = u_n X
         T XWh, XWb, XEh, XEb, XSh, XSb, XNh, XNb;
         {
           const T g = gu[0] * ev[m];
           if (K.wall[0]) {
             const bool inc = !up;  // gas on the high side: incoming u < 0
-            XWh = inc ? dtT * fWh : dtT * (g - gr.x);
-            XWb = inc ? dtT * fWb : dtT * (K.bf[0] * g - gr.y);
+            XWh = inc ? dtT * fWh : dtT * g;
+            XWb = inc ? dtT * fWb : dtT * (K.bf[0] * g);
           } else {
             XWh = horner3(qW[0], vv) * g + K.Mt4[0] * fWh - K.Mt5[0] * dWh;
             XWb = horner3(qW[1], vv) * g + K.Mt4[0] * fWb - K.Mt5[0] * dWb;
@@ -1119,8 +1100,8 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
           const T g = gu[1] * ev[nv + m];
           if (K.wall[1]) {
             const bool inc = up;  // gas on the low side: incoming u > 0
-            XEh = inc ? dtT * fEh : dtT * (g - gr.x);
-            XEb = inc ? dtT * fEb : dtT * (K.bf[1] * g - gr.y);
+            XEh = inc ? dtT * fEh : dtT * g;
+            XEb = inc ? dtT * fEb : dtT * (K.bf[1] * g);
           } else {
             XEh = horner3(qE[0], vv) * g + K.Mt4[1] * fEh - K.Mt5[1] * dEh;
             XEb = horner3(qE[1], vv) * g + K.Mt4[1] * fEb - K.Mt5[1] * dEb;
@@ -1129,8 +1110,8 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         {
           const T g = gu[2] * ev[2 * nv + m];
           if (K.wall[2]) {
-            XSh = !VUP ? dtT * fSh : dtT * (g - gr.x);
-            XSb = !VUP ? dtT * fSb : dtT * (K.bf[2] * g - gr.y);
+            XSh = !VUP ? dtT * fSh : dtT * g;
+            XSb = !VUP ? dtT * fSb : dtT * (K.bf[2] * g);
           } else {
             XSh = horner3(qS[0], vv) * g + K.Mt4[2] * fSh - K.Mt5[2] * dSh;
             XSb = horner3(qS[1], vv) * g + K.Mt4[2] * fSb - K.Mt5[2] * dSb;
@@ -1139,8 +1120,8 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         {
           const T g = gu[3] * ev[3 * nv + m];
           if (K.wall[3]) {
-            XNh = VUP ? dtT * fNh : dtT * (g - gr.x);
-            XNb = VUP ? dtT * fNb : dtT * (K.bf[3] * g - gr.y);
+            XNh = VUP ? dtT * fNh : dtT * g;
+            XNb = VUP ? dtT * fNb : dtT * (K.bf[3] * g);
           } else {
             XNh = horner3(qN[0], vv) * g + K.Mt4[3] * fNh - K.Mt5[3] * dNh;
             XNb = horner3(qN[1], vv) * g + K.Mt4[3] * fNb - K.Mt5[3] * dNb;
@@ -1148,16 +1129,9 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         }
         T flh = fxu * (XWh - XEh) + fyv * (XSh - XNh);
         T flb = fxu * (XWb - XEb) + fyv * (XSb - XNb);
-        if (REF) {
-          const T rr = refxu + vv * K.refy;
-          flh += rr * gr.x;
-          flb += rr * gr.y;
-        }
         const T gnh = gun * ev[4 * nv + m], g1h = gu1 * ev[5 * nv + m];
-        // f^n = e + g_ref in the FP32 form: g - f^n = (g - g_ref) - e
-        const T dh = K.inv * (flh + K.cg1 * ((g1h - gr.x) - c.x) + K.cgn * ((gnh - gr.x) - c.x));
-        const T db = K.inv * (flb + (K.cg1b * g1h - K.cg1 * gr.y - K.cg1 * c.y) +
-                              (K.cgnb * gnh - K.cgn * gr.y - K.cgn * c.y));
+        const T dh = K.inv * (flh + K.cg1 * (g1h - c.x) + K.cgn * (gnh - c.x));
+        const T db = K.inv * (flb + (K.cg1b * g1h - K.cg1 * c.y) + (K.cgnb * gnh - K.cgn * c.y));
         T2 o;
         o.x = c.x + dh;
         o.y = c.y + db;
@@ -1167,269 +1141,6 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     half(std::integral_constant<bool, false>{}, 0, P.m_pos);
     half(std::integral_constant<bool, true>{}, P.m_pos, nv);
   }
-}
-
-// -------------------------------------------------------------------------------------
-// FP32 form, S6 + S8 and Eq. 3 as an upwind strip walk.  For one velocity the micro flux
-// through a face depends only on its upwind cell, so each cell evaluates the flux through
-// its downwind x-face and downwind y-face and receives the flux through its upwind faces
-// from its upwind neighbours.  A warp (lane = velocity) owns a strip of W adjacent columns
-// and walks it row by row in the direction of v; within a row it visits the columns in the
-// direction of u.  The x-upwind flux of a column is the previous column's downwind flux, the
-// y-upwind flux is the previous row's, both carried in registers; only the strip's first
-// column needs the flux out of the cell before the strip (U), which is evaluated from U's
-// own reconstruction.  Slopes are taken along the walk (upwind, centre, downwind), so the
-// upwind face value is f + slope and u sigma_x = |u| (2/dx) slope, with no sign selects.
-// Work item: (velocity chunk of 32, v < 0 chunks first; tile of `rows` rows; strip).
-// Buffers hold e = f - g_ref; the update is e^{n+1} = e^n + d (CellRecF).
-// -------------------------------------------------------------------------------------
-constexpr int kWalkRows = 64;  // default rows per walk tile
-constexpr int kStripW = 4;     // columns per strip
-constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
-// 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
-constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
-
-__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-
-
-
-// van Leer half slope of the walk-ordered stencil (a, c, b), both components.
-__device__ __forceinline__ float vl_walk(float a, float c, float b) {
-  const float d1 = c - a, d2 = b - c, p = d1 * d2;
-  return p > 0.f ? p * rcp_ftz(d1 + d2) : 0.f;
-}
-__device__ __forceinline__ float2 vl_walk2(float2 a, float2 c, float2 b) {
-  return make_float2(vl_walk(a.x, c.x, b.x), vl_walk(a.y, c.y, b.y));
-}
-
-// Per-lane velocity constants of the walk.
-struct StripLane {
-  float u, v, uu, uv, vv, ur2, vr2, r2;
-  float cu, cv;   // |u| 2/dx, |v| 2/dy: d = cu slope_x + cv slope_y
-  float au, av;   // |u| / dx, |v| / dy
-  float2 gr;      // g_ref (h, b)
-  float dt;
-};
-
-__device__ __forceinline__ float exp_poly(const float4 e, const StripLane& L) {
-  return ex2_ftz(fmaf(e.w, L.r2, fmaf(e.z, L.v, fmaf(e.y, L.u, e.x))));
-}
-
-// Micro flux through a face for the lane's velocity (FaceRecF), e-form f_up and d.
-__device__ __forceinline__ float2 strip_face(const FaceRecF* R, int side, const StripLane& L,
-                                             float2 fup, float2 d) {
-  const float4 a = ld4(&R->Q[side][0]);
-  const float4 b = ld4(&R->Q[side][4]);
-  const float4 k = ld4(&R->K[side][0]);
-  const float4 e = ld4(&R->E[0]);
-  const float2 t = *reinterpret_cast<const float2*>(&R->Mt4);  // Mt4 Mt5
-  float qh = fmaf(b.w, L.vr2, fmaf(b.z, L.ur2, fmaf(b.y, L.vv, fmaf(b.x, L.uv, fmaf(a.w, L.uu,
-             fmaf(a.z, L.v, fmaf(a.y, L.u, a.x)))))));
-  const float qb = fmaf(k.w, qh, fmaf(k.z, L.v, fmaf(k.y, L.u, k.x)));
-  const float g = exp_poly(e, L);
-  float2 X;
-  X.x = fmaf(qh, g, fmaf(t.x, fup.x, -t.y * d.x));
-  X.y = fmaf(qb, g, fmaf(t.x, fup.y, -t.y * d.y));
-  return X;
-}
-
-// Flux leaving a diffuse wall into the gas, e-form.
-__device__ __forceinline__ float2 strip_wall(const FaceRecF* R, const StripLane& L) {
-  const float4 e = ld4(&R->E[0]);
-  const float gdt = R->gdt, X2 = R->K[0][3];
-  const float g = exp_poly(e, L);
-  float2 X;
-  X.x = fmaf(gdt, g, -L.dt * L.gr.x);
-  X.y = fmaf(gdt * X2, g, -L.dt * L.gr.y);
-  return X;
-}
-
-// Eq. 3 increment of one cell (CellRecF); Xi / Xo: inflow / outflow flux in x and y.
-__device__ __forceinline__ float2 strip_collide(const CellRecF* C, const StripLane& L, float2 e,
-                                                float2 Xix, float2 Xox, float2 Xiy, float2 Xoy) {
-  const float4 en = ld4(&C->En[0]);
-  const float4 e1 = ld4(&C->E1[0]);
-  const float4 A = ld4(&C->A1);    // A1 An b1 bn
-  const float4 B = ld4(&C->Bs);    // Bs irx iry inv
-  const float gn = exp_poly(en, L), g1 = exp_poly(e1, L);
-  const float r = fmaf(L.v, B.z, L.u * B.y);
-  const float aui = L.au * B.w, avi = L.av * B.w;
-  float dh = fmaf(aui, Xix.x - Xox.x, avi * (Xiy.x - Xoy.x));
-  float db = fmaf(aui, Xix.y - Xox.y, avi * (Xiy.y - Xoy.y));
-  dh = fmaf(A.x, g1 - L.gr.x, fmaf(A.y, gn - L.gr.x, fmaf(r, L.gr.x, fmaf(-B.x, e.x, dh))));
-  db = fmaf(A.x, fmaf(A.z, g1, -L.gr.y), fmaf(A.y, fmaf(A.w, gn, -L.gr.y), fmaf(r, L.gr.y, fmaf(-B.x, e.y, db))));
-  return make_float2(e.x + dh, e.y + db);
-}
-
-template <int W>
-__device__ __forceinline__ void strip_body(const Params& P, const float2* __restrict__ f,
-                                           float2* __restrict__ fo, const FaceRecF* __restrict__ fxr,
-                                           const FaceRecF* __restrict__ fyr,
-                                           const CellRecF* __restrict__ cr, int nchunk_neg,
-                                           int rows, int bx, int by, int chunk,
-                                           float4* __restrict__ ring) {
-  const int lane = threadIdx.x & 31;
-  const int nx = P.nx, ny = P.ny, nu = P.nu, nq = P.nq;
-  const int i0 = bx * W;
-  const int wc = min(W, nx - i0);
-  const bool vpos = chunk >= nchunk_neg;
-  const int nq_neg = P.m_neg * nu;
-  const int q = vpos ? nq_neg + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
-  const int qend = vpos ? nq : nq_neg;
-  const bool act = q < qend;
-  const int qq = act ? q : qend - 1;
-  const int k = qq % nu, m = qq / nu;
-  StripLane L;
-  L.u = P.uwf[k];
-  L.v = P.mvf[4 * P.nv + m];
-  L.uu = L.u * L.u; L.uv = L.u * L.v; L.vv = L.v * L.v;
-  L.r2 = L.uu + L.vv;
-  L.ur2 = L.u * L.r2; L.vr2 = L.v * L.r2;
-  L.cu = fabsf(L.u) * P.f_tdx; L.cv = fabsf(L.v) * P.f_tdy;
-  L.au = fabsf(L.u) * P.f_idx; L.av = fabsf(L.v) * P.f_idy;
-  L.gr = __ldg(static_cast<const float2*>(P.gref) + qq);
-  L.dt = P.f_dt;
-  const int su = L.u > 0.f ? 1 : -1;
-  const int sv = vpos ? 1 : -1;
-  const int xside = su > 0 ? 0 : 1, yside = vpos ? 0 : 1;
-  const int ib = su > 0 ? i0 : i0 + wc - 1;          // strip position 0 (walk order)
-  const int iU = ib - su;                              // upwind neighbour column U
-  const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
-  const bool zu = (iU < 0 && pW) || (iU >= nx && pE);  // U is a pressure ghost: zero slopes
-  const int xo = su * nq;                              // one column in walk order, in float2
-  // walk position p (-2 = UU, -1 = U, 0..W-1 strip, W = D) -> column offset; strip positions
-  // past the strip's end read column D (they are not updated)
-  auto col = [&](int p) { return (p < wc ? p : wc) * xo; };
-
-  const int j0 = by * rows;
-  const int j1 = min(j0 + rows, ny);
-  const int jfirst = sv > 0 ? j0 : j1 - 1;
-  const int nsteps = j1 - j0;
-  const int rs = sv * P.ex * nq;                       // one row in walk order, in float2
-  const long base = ((long)(jfirst + 2) * P.ex + ib + 2) * nq + qq;
-  const float2* pr = f + base;                         // (position 0, row jfirst)
-  float2* pw = fo + base;
-
-  // rows jfirst - sv (Pv), jfirst (Cv), jfirst + sv (Nv) at positions -1..W-1
-  float2 Pv[W + 1], Cv[W + 1], Nv[W + 1];
-#pragma unroll
-  for (int p = -1; p < W; p++) {
-    Pv[p + 1] = ld2(pr - rs + col(p));
-    Cv[p + 1] = ld2(pr + col(p));
-    Nv[p + 1] = ld2(pr + rs + col(p));
-  }
-  float2 cUU = ld2(pr + col(-2)), cD = ld2(pr + col(W));
-
-  // prologue: flux through the y-face between the halo row jp = jfirst - sv and jfirst
-  float2 Xiy[W];
-  {
-    const int jp = jfirst - sv;
-    const FaceRecF* RY = fyr + (long)(sv > 0 ? jfirst : jfirst + 1) * nx + ib;
-    const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
-    const float2 dp = ld2(pr - rs + col(W));
-    if (RY->wall != 0.f) {
-#pragma unroll
-      for (int t = 0; t < W; t++)
-        if (t < wc) Xiy[t] = strip_wall(RY + su * t, L);
-    } else {
-#pragma unroll
-      for (int t = 0; t < W; t++) {
-        if (t < wc) {
-          const float2 pp = ld2(pr - 2 * rs + col(t));
-          const float2 c = Pv[t + 1];
-          float2 rx = vl_walk2(Pv[t], c, t + 1 < W ? Pv[t + 2] : dp);
-          float2 ry = vl_walk2(pp, c, Cv[t + 1]);
-          if (zp) rx = ry = make_float2(0.f, 0.f);
-          const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-          Xiy[t] = strip_face(RY + su * t, yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
-        }
-      }
-    }
-  }
-
-  // face and cell records of a row, staged through a ring of kRing rows in shared memory:
-  // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
-  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
-  auto stage = [&](int s) {
-    if (s < nsteps) {
-      const int j = jfirst + sv * s;
-      const float4* gx = reinterpret_cast<const float4*>(fxr + (long)j * (nx + 1) + i0);
-      const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
-      const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
-      float4* dst = ring + (s % kRing) * kStripChunks;
-      for (int c = lane; c < kStripChunks; c += 32) {
-        if (c < oY) {
-          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
-        } else if (c < oC) {
-          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
-        } else if (c - oC < wc * 4) {
-          cp_async16(dst + c, gc + (c - oC));
-        }
-      }
-    }
-    cp_async_commit();
-  };
-  __syncwarp();                      // the ring's previous contents are no longer read
-#pragma unroll
-  for (int s = 0; s < kRing - 1; s++) stage(s);
-  // local record index of walk position t (-1 = U's face for x) within the staged row
-  const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
-  auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
-  for (int s = 0; s < nsteps; s++) {
-    __syncwarp();                    // every lane is done with the slot refilled next
-    stage(s + kRing - 1);
-    // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
-    float2 NN[W + 1];
-#pragma unroll
-    for (int p = -1; p < W; p++) NN[p + 1] = ld2(pr + 2 * rs + col(p));
-    const float2 nUU = ld2(pr + rs + col(-2)), nD = ld2(pr + rs + col(W));
-    cp_async_wait<kRing - 1>();
-    __syncwarp();
-    const float4* row = ring + (s % kRing) * kStripChunks;
-    const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
-    const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
-    const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
-
-    // flux into position 0 out of U (or off the wall)
-    float2 Xix;
-    const FaceRecF* RXi = RX + xl0;
-    if (RXi->wall != 0.f) {
-      Xix = strip_wall(RXi, L);
-    } else {
-      float2 rx = vl_walk2(cUU, Cv[0], Cv[1]);
-      float2 ry = vl_walk2(Pv[0], Cv[0], Nv[0]);
-      if (zu) rx = ry = make_float2(0.f, 0.f);
-      const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-      Xix = strip_face(RXi, xside, L, make_float2(Cv[0].x + rx.x, Cv[0].y + rx.y), d);
-    }
-#pragma unroll
-    for (int t = 0; t < W; t++) {
-      if (t < wc) {
-        const float2 c = Cv[t + 1];
-        const float2 rx = vl_walk2(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
-        const float2 ry = vl_walk2(Pv[t + 1], c, Nv[t + 1]);
-        const float2 d = make_float2(fmaf(L.cu, rx.x, L.cv * ry.x), fmaf(L.cu, rx.y, L.cv * ry.y));
-        const float2 Xox = strip_face(RXi + su * (t + 1), xside, L, make_float2(c.x + rx.x, c.y + rx.y), d);
-        const float2 Xoy = strip_face(RY + cl(t), yside, L, make_float2(c.x + ry.x, c.y + ry.y), d);
-        const float2 o = strip_collide(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
-        if (act) pw[col(t)] = o;
-        Xix = Xox;
-        Xiy[t] = Xoy;
-      }
-    }
-#pragma unroll
-    for (int p = 0; p <= W; p++) {
-      Pv[p] = Cv[p];
-      Cv[p] = Nv[p];
-      Nv[p] = NN[p];
-    }
-    cUU = nUU;
-    cD = nD;
-    pr += rs;
-    pw += rs;
-  }
-  cp_async_wait<0>();
 }
 
 
