@@ -1157,6 +1157,9 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem)) !=
+      cudaSuccess)
+    return e;
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
                               (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases; p++) {

@@ -85,7 +85,7 @@ __global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* _
   }
 }
 
-__global__ void __launch_bounds__(128, 4) kb_sums(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 5) kb_sums(const SlotDev* __restrict__ slots,
                                                const BatchWork* __restrict__ wk) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int total = wk->start[2][wk->n];
@@ -122,8 +122,7 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
   }
 }
 
-// Update sweep: one warp per work item (strip, tile, velocity chunk), strips fastest so that
-// the warps of a block share neighbour columns.
+// Update sweep: one warp per work item (strip, tile, velocity chunk).
 __global__ void __launch_bounds__(128, 2) kb_strip(const SlotDev* __restrict__ slots,
                                                 const BatchWork* __restrict__ wk) {
   __shared__ __align__(16) float4 ring[kWarpsPerBlock][kRing * kStripChunks];
@@ -134,10 +133,13 @@ __global__ void __launch_bounds__(128, 2) kb_strip(const SlotDev* __restrict__ s
     const SlotDev& S = slots[wk->slot[a]];
     const int ns = (S.P.nx + kStripW - 1) / kStripW, nt = (S.P.ny + S.walk_rows - 1) / S.walk_rows;
     const int it = (vb - wk->start[5][a]) * kWarpsPerBlock + warp;
-    if (it < ns * nt * (S.nchunk_neg + S.nchunk_pos)) {
+    const int nch = S.nchunk_neg + S.nchunk_pos;
+    if (it < ns * nt * nch) {
       const int c = S.cur;
+      // velocity chunks fastest: the warps of a block share the strip's records and halo
+      const int bx = (it / nch) % ns, by = it / (nch * ns), ck = it % nch;
       strip_body_p<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
-                          it % ns, (it / ns) % nt, it / (ns * nt), ring[warp]);
+                            bx, by, ck, ring[warp]);
     }
   }
 }

@@ -24,7 +24,6 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 // a - b, exactly as a single subtraction (b * -1 is exact)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
 
 // (h, b) of the two velocities of a slot
 struct P4 {
@@ -120,7 +119,7 @@ __device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, 
 // the x half slope r_x and the y half slope r_y:
 //   a_n = sum w_n c_h (n < 4), ab_n = sum w_n c_b (n < 2), x_n = sum w_n r_x,h (n < 4),
 //   xb_n = sum w_n r_x,b (n < 2), y_n = sum w_n r_y,h (n < 5), yb_n = sum w_n r_y,b (n < 3),
-// each kept as a pair (one accumulator per row of the pair) and added at the end of the half.
+// accumulated over both rows of each pair.
 // The v = 0 row (H(0) = 1/2) enters both halves with half weight: the weight table carries
 // its half weight in the v >= 0 half and its part of the v < 0 half is added separately.
 // -------------------------------------------------------------------------------------
@@ -146,7 +145,9 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
                   (j < 0 && P.bc_kind[2] == 2) || (j >= P.ny && P.bc_kind[3] == 2);
 
   const float4* fc = f + fcell(P, i, j) * fs;
-  const long rs = (long)P.ex * fs;
+  // neighbour offsets; a cell next to a pressure ghost (zero slopes) reads itself, which
+  // makes every van Leer slope exactly zero
+  const long ox = zs ? 0 : fs, oy = zs ? 0 : (long)P.ex * fs;
   const float tdx = P.f_tdx, tdy = P.f_tdy;
   const int pn = P.pr_neg, pa = P.pr_all;
   const bool v0 = P.m_pos > P.m_neg;
@@ -161,43 +162,37 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     const float cu = u * tdx;
 #pragma unroll
     for (int t = 0; t < kSumsTotals; t++) tot[t * 128] = 0.f;
-    float2 a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
+    float a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
     auto zero = [&]() {
-      const float2 z = make_float2(0.f, 0.f);
-      a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = z;
-      y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = z;
+      a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = 0.f;
+      y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = 0.f;
     };
     // one row pair: stencil, slopes, accumulation; returns the centre and its slopes
     auto pair = [&](int pr, P4& c, P4& rx, P4& ry) {
       const float4* src = fc + (long)pr * nu + kk;
       c = ldp(src);
-      const P4 w = ldp(src - fs), e = ldp(src + fs), s = ldp(src - rs), n = ldp(src + rs);
-      if (zs) {
-        rx = ry = zero4();
-      } else {
-        rx = vl4(w, c, e);
-        ry = vl4(s, c, n);
-      }
+      const P4 w = ldp(src - ox), e = ldp(src + ox), s = ldp(src - oy), n = ldp(src + oy);
+      rx = vl4(w, c, e);
+      ry = vl4(s, c, n);
       const float4 t0 = __ldg(wt + 3 * pr), t1 = __ldg(wt + 3 * pr + 1), t2 = __ldg(wt + 3 * pr + 2);
       const float2 w0 = make_float2(t0.x, t0.y), w1 = make_float2(t0.z, t0.w);
       const float2 w2 = make_float2(t1.x, t1.y), w3 = make_float2(t1.z, t1.w);
       const float2 w4 = make_float2(t2.x, t2.y);
-      a0 = fma2(w0, c.h, a0); a1 = fma2(w1, c.h, a1); a2 = fma2(w2, c.h, a2); a3 = fma2(w3, c.h, a3);
-      ab0 = fma2(w0, c.b, ab0); ab1 = fma2(w1, c.b, ab1);
-      x0 = fma2(w0, rx.h, x0); x1 = fma2(w1, rx.h, x1); x2 = fma2(w2, rx.h, x2); x3 = fma2(w3, rx.h, x3);
-      xb0 = fma2(w0, rx.b, xb0); xb1 = fma2(w1, rx.b, xb1);
-      y0 = fma2(w0, ry.h, y0); y1 = fma2(w1, ry.h, y1); y2 = fma2(w2, ry.h, y2); y3 = fma2(w3, ry.h, y3);
-      y4 = fma2(w4, ry.h, y4);
-      yb0 = fma2(w0, ry.b, yb0); yb1 = fma2(w1, ry.b, yb1); yb2 = fma2(w2, ry.b, yb2);
+      // one scalar accumulator per sum over both rows of the pair (fewer registers than a
+      // packed pair of accumulators, which buys the occupancy this latency-bound loop needs)
+      auto acc = [](float& a, float2 w, float2 v) { a = fmaf(w.y, v.y, fmaf(w.x, v.x, a)); };
+      acc(a0, w0, c.h); acc(a1, w1, c.h); acc(a2, w2, c.h); acc(a3, w3, c.h);
+      acc(ab0, w0, c.b); acc(ab1, w1, c.b);
+      acc(x0, w0, rx.h); acc(x1, w1, rx.h); acc(x2, w2, rx.h); acc(x3, w3, rx.h);
+      acc(xb0, w0, rx.b); acc(xb1, w1, rx.b);
+      acc(y0, w0, ry.h); acc(y1, w1, ry.h); acc(y2, w2, ry.h); acc(y3, w3, ry.h); acc(y4, w4, ry.h);
+      acc(yb0, w0, ry.b); acc(yb1, w1, ry.b); acc(yb2, w2, ry.b);
     };
     // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
     auto close = [&](float sy, float* side) {
-      const float A0 = hsum(a0), A1 = hsum(a1), A2 = hsum(a2), A3 = hsum(a3);
-      const float AB0 = hsum(ab0), AB1 = hsum(ab1);
-      const float X0 = hsum(x0), X1 = hsum(x1), X2 = hsum(x2), X3 = hsum(x3);
-      const float XB0 = hsum(xb0), XB1 = hsum(xb1);
-      const float Y0 = hsum(y0), Y1 = hsum(y1), Y2 = hsum(y2), Y3 = hsum(y3), Y4 = hsum(y4);
-      const float YB0 = hsum(yb0), YB1 = hsum(yb1), YB2 = hsum(yb2);
+      const float A0 = a0, A1 = a1, A2 = a2, A3 = a3, AB0 = ab0, AB1 = ab1;
+      const float X0 = x0, X1 = x1, X2 = x2, X3 = x3, XB0 = xb0, XB1 = xb1;
+      const float Y0 = y0, Y1 = y1, Y2 = y2, Y3 = y3, Y4 = y4, YB0 = yb0, YB1 = yb1, YB2 = yb2;
       const float P0 = A0 + sy * Y0, P1 = A1 + sy * Y1, P2 = A2 + sy * Y2, P3 = A3 + sy * Y3;
       const float Pb0 = AB0 + sy * YB0, Pb1 = AB1 + sy * YB1;
       const float Z1 = cu * X1 + tdy * Y2, Z2 = cu * X2 + tdy * Y3, Z3 = cu * X3 + tdy * Y4;
@@ -208,28 +203,29 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
 #pragma unroll
       for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
     };
-    // v >= 0 half; its first pair holds the v = 0 row (if any) as its first row
+    // row pairs in the order v >= 0 half, then v < 0 half; the first v >= 0 pair holds the
+    // v = 0 row (if any) as its first row
     zero();
     float s0h = 0.f, s0b = 0.f, s0xh = 0.f, s0xb = 0.f, s0yh = 0.f, s0yb = 0.f;
-    if (pa > pn) {
+#pragma unroll 1
+    for (int t = 0; t < pa; t++) {
+      if (t == pa - pn) {  // first v < 0 pair: close the v >= 0 half
+        close(1.f, wsum + kSumN);
+        zero();
+        a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
+      }
       P4 c, rx, ry;
-      pair(pn, c, rx, ry);
-      if (v0) {
+      pair(t < pa - pn ? pn + t : t - (pa - pn), c, rx, ry);
+      if (t == 0 && v0) {  // the v = 0 row's half weight for the v < 0 half
         const float hw = __ldg(&wt[3 * pn].x);
         s0h = hw * c.h.x; s0b = hw * c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
         s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
       }
-#pragma unroll 1
-      for (int pr = pn + 1; pr < pa; pr++) pair(pr, c, rx, ry);
     }
-    close(1.f, wsum + kSumN);
-    // v < 0 half, with the v = 0 row's half weight
-    zero();
-    a0.x = s0h; ab0.x = s0b; x0.x = s0xh; xb0.x = s0xb; y0.x = s0yh; yb0.x = s0yb;
-#pragma unroll 1
-    for (int pr = 0; pr < pn; pr++) {
-      P4 c, rx, ry;
-      pair(pr, c, rx, ry);
+    if (pn == 0) {  // no v < 0 half: the loop did not close the v >= 0 half
+      close(1.f, wsum + kSumN);
+      zero();
+      a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
     }
     close(-1.f, wsum + kSumS);
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.

@@ -21,7 +21,7 @@ enum { kOffW0 = 0, kOffSt = 4, kOffSf = 8, kOffSs = 12 };
 constexpr int kSumsTotals = 14;    // per-thread totals of the sums kernel (shared memory)
 // dynamic shared memory of the sums kernel: per-warp sums, per-thread totals
 template <typename T>
-constexpr size_t sums_smem_bytes() {
+__host__ __device__ constexpr size_t sums_smem_bytes() {
   return (kWarpsPerBlock * kNSum + kSumsTotals * 128) * sizeof(T);
 }
 
