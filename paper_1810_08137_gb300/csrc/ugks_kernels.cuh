@@ -430,11 +430,13 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
 // Moments <x^n>, n = 0..6, of the normalised 1D Gaussian sqrt(lam/pi) exp(-lam (x-U)^2):
 // full range, x > 0 and x < 0.  Integration by parts gives
 // <x^{n+2}> = U <x^{n+1}> + (n+1)/(2 lam) <x^n> on every range.
-// h = 1/(2 lam).  One erfc: the half-range mass on the far side of U is erfc(sqrt(lam)|U|)/2,
-// the near side 1 minus that.
-__device__ void gauss_moments7(double U, double lam, double h, double* M, double* Mp, double* Mn) {
-  const double sl = sqrt(lam);
-  const double e = exp(-lam * U * U) * 0.5 * rsqrt(kPi * lam);
+// h = 1/(2 lam), rl = 1/sqrt(lam).  One erfc: the half-range mass on the far side of U is
+// erfc(sqrt(lam)|U|)/2, the near side 1 minus that.
+__device__ void gauss_moments7(double U, double lam, double h, double rl, double* M, double* Mp,
+                               double* Mn) {
+  constexpr double kHalfRsqrtPi = 0.28209479177387814347;  // 1 / (2 sqrt(pi))
+  const double sl = lam * rl;
+  const double e = exp(-lam * U * U) * (kHalfRsqrtPi * rl);
   const double far = 0.5 * erfc(sl * fabs(U));
   M[0] = 1.0;
   M[1] = U;
@@ -474,22 +476,30 @@ __device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, doub
 // the components are T(a, b), T(a+1, b), T(a, b+1), and for the energy
 // (T(a+2, b) + T(a, b+2) + X2 T(a, b) + h (X4 - X2^2) M(a, b)) / 2, since
 // <xi^2 (c . psi)> = X2 (c . psi with xi^2 -> X2) + h (X4 - X2^2).
-__device__ void apsi_mom(const double* Mu, const double* Mv, double X2, double X4, int a, int b,
-                         const double* c, double* o) {
-  const double h = 0.5 * c[3], c0x = c[0] + h * X2;
-  double A[3], B[3], C[3];
+// The tables A, B, C depend on (c, Mv, b) only and are shared by evaluations at several
+// (Mu, a); X4m = X4 - X2^2.
+struct APsi {
+  double A[3], B[3], C[3], h, mvb;
+};
+__device__ __forceinline__ void apsi_prep(const double* Mv, double X2, int b, const double* c, APsi& t) {
+  t.h = 0.5 * c[3];
+  const double c0x = c[0] + t.h * X2;
 #pragma unroll
   for (int q = 0; q < 3; q++) {
-    A[q] = c0x * Mv[b + q] + c[2] * Mv[b + q + 1] + h * Mv[b + q + 2];
-    B[q] = c[1] * Mv[b + q];
-    C[q] = h * Mv[b + q];
+    t.A[q] = c0x * Mv[b + q] + c[2] * Mv[b + q + 1] + t.h * Mv[b + q + 2];
+    t.B[q] = c[1] * Mv[b + q];
+    t.C[q] = t.h * Mv[b + q];
   }
-  auto T = [&](int p, int q) { return Mu[a + p] * A[q] + Mu[a + p + 1] * B[q] + Mu[a + p + 2] * C[q]; };
+  t.mvb = Mv[b];
+}
+__device__ __forceinline__ void apsi_eval(const APsi& t, const double* Mu, double X2, double X4m, int a,
+                                          double* o) {
+  auto T = [&](int p, int q) { return Mu[a + p] * t.A[q] + Mu[a + p + 1] * t.B[q] + Mu[a + p + 2] * t.C[q]; };
   const double t00 = T(0, 0);
   o[0] = t00;
   o[1] = T(1, 0);
   o[2] = T(0, 1);
-  o[3] = 0.5 * (T(2, 0) + T(0, 2) + X2 * t00 + h * (X4 - X2 * X2) * (Mu[a] * Mv[b]));
+  o[3] = 0.5 * (T(2, 0) + T(0, 2) + X2 * t00 + t.h * X4m * (Mu[a] * t.mvb));
 }
 
 // q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass, c4 = lam/q.
@@ -516,23 +526,32 @@ __host__ __device__ constexpr double inv_factorial(int n) {
 //   Mt1 = dt c1, Mt2 = dt^2 c2, Mt3 = dt^2 c3, Mt4 = dt c4, Mt5 = dt^2 c5
 //   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x,
 // by their Taylor series below x = 0.1 (no cancellation there).
+// Power series of the c_k in y = -x by Horner, NT terms: c4 = sum y^n/(n+1)!,
+// c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!, c3 = x sum y^n/(n+3)!,
+// c2 = -x sum (n+1) y^n/(n+3)!.
+template <int NT>
+__device__ __forceinline__ void time_series(double x, double& c1, double& c2, double& c3, double& c4,
+                                            double& c5) {
+  const double y = -x;
+  double h4 = 0.0, h5 = 0.0, h1 = 0.0, h3 = 0.0, h2 = 0.0;
+#pragma unroll
+  for (int n = NT - 1; n >= 0; n--) {
+    h4 = h4 * y + inv_factorial(n + 1);
+    h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
+    h1 = h1 * y + inv_factorial(n + 2);
+    h3 = h3 * y + inv_factorial(n + 3);
+    h2 = h2 * y + (n + 1) * inv_factorial(n + 3);
+  }
+  c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
+}
 __device__ void time_weights(double dt, double x, double* Mt) {
   double c1, c2, c3, c4, c5;
-  if (x < 0.1) {
-    // power series in y = -x by Horner, 12 terms (the 13th is below 1e-22 relative for
-    // x < 0.1): c4 = sum y^n/(n+1)!, c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!,
-    // c3 = x sum y^n/(n+3)!, c2 = -x sum (n+1) y^n/(n+3)!
-    const double y = -x;
-    double h4 = 0.0, h5 = 0.0, h1 = 0.0, h3 = 0.0, h2 = 0.0;
-#pragma unroll
-    for (int n = 11; n >= 0; n--) {
-      h4 = h4 * y + inv_factorial(n + 1);
-      h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
-      h1 = h1 * y + inv_factorial(n + 2);
-      h3 = h3 * y + inv_factorial(n + 3);
-      h2 = h2 * y + (n + 1) * inv_factorial(n + 3);
-    }
-    c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
+  if (x < 0.01) {
+    // 8 terms: the first one left out is below 1e-20 relative for x < 0.01
+    time_series<8>(x, c1, c2, c3, c4, c5);
+  } else if (x < 0.1) {
+    // 12 terms: the first one left out is below 1e-22 relative for x < 0.1
+    time_series<12>(x, c1, c2, c3, c4, c5);
   } else {
     const double e = exp(-x), em = -expm1(-x), ix = 1.0 / x;
     c4 = em * ix;
@@ -614,13 +633,15 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) * irho * P.inv_kp2;  // 1/(4 lam)
   const double lam = 0.25 / ilam4;
   const double h = 2.0 * ilam4;  // 1/(2 lam)
+  const double rl = rsqrt(lam);
   double Mu[7], Mup[7], Mun[7], Mv[7];
-  gauss_moments7(U, lam, h, Mu, Mup, Mun);
+  gauss_moments7(U, lam, h, rl, Mu, Mup, Mun);
   gauss_moments7_full(V, h, Mv);
   const double X2 = 2.0 * K * ilam4, X4 = (K * K + 2.0 * K) * 4.0 * ilam4 * ilam4;
+  const double X4m = X4 - X2 * X2;
   // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5 of
   // x = dt/tau (omega = 1/2: x = dt rho / (2 mu_ref sqrt(lam)))
-  const double x = P.omega_half ? P.half_dt_mu * rho * rsqrt(lam) : P.dt / collision_time(P, rho, lam);
+  const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
   double Mt[5];
   time_weights(P.dt, x, Mt);
   // S4: micro slopes
@@ -636,37 +657,28 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   micro_slope(U, V, lam, q, c4, sL, aL);
   micro_slope(U, V, lam, q, c4, sR, aR);
   micro_slope(U, V, lam, q, c4, sT, b);
+  APsi tL, tR, tb, tA;
+  apsi_prep(Mv, X2, 0, aL, tL);
+  apsi_prep(Mv, X2, 0, aR, tR);
+  apsi_prep(Mv, X2, 1, b, tb);
   double t1[4], t2[4], t3[4], t4[4], p1[4];
-  apsi_mom(Mup, Mv, X2, X4, 1, 0, aL, t1);
-  apsi_mom(Mun, Mv, X2, X4, 1, 0, aR, t2);
-  apsi_mom(Mu, Mv, X2, X4, 0, 1, b, t3);
+  apsi_eval(tL, Mup, X2, X4m, 1, t1);
+  apsi_eval(tR, Mun, X2, X4m, 1, t2);
+  apsi_eval(tb, Mu, X2, X4m, 0, t3);
 #pragma unroll
   for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
   micro_slope(U, V, lam, q, c4, sA, A);
+  apsi_prep(Mv, X2, 0, A, tA);
   // S5: equilibrium part of the macroscopic flux; S7 free transport part from the sums
   psi_mom(Mu, Mv, X2, 1, 0, p1);
-  apsi_mom(Mup, Mv, X2, X4, 2, 0, aL, t1);
-  apsi_mom(Mun, Mv, X2, X4, 2, 0, aR, t2);
-  apsi_mom(Mu, Mv, X2, X4, 1, 1, b, t3);
-  apsi_mom(Mu, Mv, X2, X4, 1, 0, A, t4);
+  apsi_eval(tL, Mup, X2, X4m, 2, t1);
+  apsi_eval(tR, Mun, X2, X4m, 2, t2);
+  apsi_eval(tb, Mu, X2, X4m, 1, t3);
+  apsi_eval(tA, Mu, X2, X4m, 1, t4);
 #pragma unroll
   for (int c = 0; c < 4; c++)
     F[c] = rho * (Mt[0] * p1[c] + Mt[1] * (t1[c] + t2[c] + t3[c]) + Mt[2] * t4[c]) + Mt[3] * Sf[c] -
            Mt[4] * Ss[c];
-  // S6/S8 coefficients
-  double pa[4], pb[4], pA[4];
-  for (int sd = 0; sd < 2; sd++) {
-    const double* as = sd == 0 ? aL : aR;
-    shape_h(as, X2, pa);
-    shape_h(b, X2, pb);
-    shape_h(A, X2, pA);
-    qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
-    if (RF) continue;  // the FP32 record carries the b polynomial in its own form
-    shape_b(as, X2, X4, pa);
-    shape_b(b, X2, X4, pb);
-    shape_b(A, X2, X4, pA);
-    qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
-  }
   R.G = rho * lam / kPi;
   R.Un = U;
   R.Ut = V;
@@ -676,21 +688,77 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   R.bfac = X2;
   R.wall = 0;
   if (RF) {
-    // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
-    // Mt2 un a4 + Mt2 ut b4), kap = (X4 - X2^2)/2 = K/(4 lam^2)
-    const double kap = 0.5 * (X4 - X2 * X2);
-    double kb[2][3];
-    for (int sd = 0; sd < 2; sd++) {
-      const double* as = sd == 0 ? aL : aR;
-      kb[sd][0] = kap * Mt[2] * A[3];
-      kb[sd][1] = kap * Mt[1] * as[3];
-      kb[sd][2] = kap * Mt[1] * b[3];
+    // FP32 record: its coefficients are stored in FP32, so they are formed in FP32 from the
+    // FP64 slopes, time weights and amplitude (S6/S8 coefficients, global frame)
+    float fa[2][4], fb[4], fA[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      fa[0][c] = (float)aL[c];
+      fa[1][c] = (float)aR[c];
+      fb[c] = (float)b[c];
+      fA[c] = (float)A[c];
     }
-    const double Qh[2][8] = {{R.Q[0][0][0], R.Q[0][0][1], R.Q[0][0][2], R.Q[0][0][3], R.Q[0][0][4],
-                              R.Q[0][0][5], R.Q[0][0][6], R.Q[0][0][7]},
-                             {R.Q[1][0][0], R.Q[1][0][1], R.Q[1][0][2], R.Q[1][0][3], R.Q[1][0][4],
-                              R.Q[1][0][5], R.Q[1][0][6], R.Q[1][0][7]}};
-    pack_face_f32(isx, Qh, kb, X2, R.G, lam, U, V, Mt[3], Mt[4], 0.0, 0.0, RF);
+    const float fX2 = (float)X2, fG = (float)R.G, fM1 = (float)Mt[0], fM2 = (float)Mt[1];
+    const float fM3 = (float)Mt[2];
+    const float kap = (float)(0.5 * X4m);  // (X4 - X2^2)/2 = K/(4 lam^2)
+    // shape polynomial of (a . psi) g / g_h reduced over the internal variable, face frame:
+    // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2)
+    auto shape = [&](const float* a4, float* o) {
+      o[0] = fmaf(0.5f * a4[3], fX2, a4[0]);
+      o[1] = a4[1];
+      o[2] = a4[2];
+      o[3] = 0.5f * a4[3];
+    };
+    float pb[4], pA[4];
+    shape(fb, pb);
+    shape(fA, pA);
+    constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+    for (int sd = 0; sd < 2; sd++) {
+      float pa[4], Qf[8];
+      shape(fa[sd], pa);
+      // Q_h on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2)
+      Qf[0] = fmaf(fM3, pA[0], fM1);
+      Qf[1] = fmaf(fM3, pA[1], fM2 * pa[0]);
+      Qf[2] = fmaf(fM3, pA[2], fM2 * pb[0]);
+      Qf[3] = fmaf(fM3, pA[3], fM2 * pa[1]);
+      Qf[4] = fM2 * (pa[2] + pb[1]);
+      Qf[5] = fmaf(fM3, pA[3], fM2 * pb[2]);
+      Qf[6] = fM2 * pa[3];
+      Qf[7] = fM2 * pb[3];
+#pragma unroll
+      for (int c = 0; c < 8; c++) RF->Q[sd][c] = fG * Qf[isx ? c : py[c]];
+      // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
+      // Mt2 un a4 + Mt2 ut b4)
+      const float k0 = fG * kap * fM3 * fA[3], kn = fG * kap * fM2 * fa[sd][3], kt = fG * kap * fM2 * fb[3];
+      RF->K[sd][0] = k0;
+      RF->K[sd][1] = isx ? kn : kt;
+      RF->K[sd][2] = isx ? kt : kn;
+      RF->K[sd][3] = fX2;
+    }
+    constexpr double kLog2e = 1.4426950408889634;
+    const double Ux = isx ? U : V, Vy = isx ? V : U;
+    RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
+    RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
+    RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
+    RF->E[3] = (float)(-lam * kLog2e);
+    RF->Mt4 = (float)Mt[3];
+    RF->nMt5 = (float)(-Mt[4]);
+    RF->wall = 0.f;
+    RF->gdt = 0.f;
+    return;
+  }
+  // S6/S8 coefficients (FP64 record)
+  double pa[4], pb[4], pA[4];
+  for (int sd = 0; sd < 2; sd++) {
+    const double* as = sd == 0 ? aL : aR;
+    shape_h(as, X2, pa);
+    shape_h(b, X2, pb);
+    shape_h(A, X2, pA);
+    qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
+    shape_b(as, X2, X4, pa);
+    shape_b(b, X2, X4, pb);
+    shape_b(A, X2, X4, pA);
+    qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
   }
 }
 
