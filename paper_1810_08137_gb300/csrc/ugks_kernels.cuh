@@ -39,11 +39,24 @@ __host__ __device__ __forceinline__ int wcell(const Params& P, int i, int j) {
   return (j + 1) * P.wx + (i + 1);
 }
 
+// 1/s from the hardware FP64 reciprocal estimate and two Newton steps (each doubles the
+// number of correct bits), within a few ulp of 1/s for normal s; an IEEE divide costs more
+// FP64 instructions, and FP64 issues at 1/64 of the FP32 rate on this part.
+__device__ __forceinline__ double rcp_nr(double s) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(s));
+  double e = fma(-s, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-s, r, 1.0);
+  return fma(r, e, r);
+}
 // van Leer limited slope of the stencil (a, c, b) times half the cell width:
 // r = sigma dx / 2 = d1 d2 / (d1 + d2) if d1 d2 > 0, else 0, with d1 = c - a, d2 = b - c.
+// (d1 d2 > 0 implies d1 + d2 != 0; a product small enough to make d1 + d2 subnormal
+// underflows to 0 and takes the zero branch.)
 __device__ __forceinline__ double vl_half(double a, double c, double b) {
   double d1 = c - a, d2 = b - c, p = d1 * d2;
-  return p > 0.0 ? p / (d1 + d2) : 0.0;
+  return p > 0.0 ? p * rcp_nr(d1 + d2) : 0.0;
 }
 // 2^x and 1/x with subnormal results flushed to zero (PTX approximate forms).
 __device__ __forceinline__ float ex2_ftz(float x) {
