@@ -606,30 +606,25 @@ __device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const d
   c[7] = Mt2 * pb[3];
 }
 
-// FP32 face record from the face-frame FP64 quantities (see FaceRecF): monomials and the
-// Maxwellian exponent are moved to the global (u, v) frame (y faces: un = v, ut = u), the
-// amplitude G is folded into the polynomial coefficients and the exponent is in log2 units.
-// Qh[s]: Q_h per side on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2); kb[s]: b-polynomial
-// terms (k0, k_un, k_ut).
-__device__ void pack_face_f32(bool isx, const double (*Qh)[8], const double (*kb)[3], double X2,
-                              double G, double lam, double Un, double Ut, double Mt4, double Mt5,
-                              double wall, double gdt, FaceRecF* RF) {
+// FP32 record of a diffuse-wall face (see FaceRecF): the wall Maxwellian with amplitude gdt
+// = dt G_w, no polynomial terms; stated in the global velocity frame (y faces: un = v).
+__device__ void wall_face_f32(bool isx, double X2, double lam, double Ut, double dt, int wall, double gdt,
+                              FaceRecF* RF) {
   constexpr double kLog2e = 1.4426950408889634;
-  constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+#pragma unroll
   for (int sd = 0; sd < 2; sd++) {
-    for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)(G * Qh[sd][isx ? c : py[c]]);
-    RF->K[sd][0] = (float)(G * kb[sd][0]);
-    RF->K[sd][1] = (float)(G * kb[sd][isx ? 1 : 2]);
-    RF->K[sd][2] = (float)(G * kb[sd][isx ? 2 : 1]);
+#pragma unroll
+    for (int c = 0; c < 8; c++) RF->Q[sd][c] = 0.f;
+    RF->K[sd][0] = RF->K[sd][1] = RF->K[sd][2] = 0.f;
     RF->K[sd][3] = (float)X2;
   }
-  const double Ux = isx ? Un : Ut, Vy = isx ? Ut : Un;
+  const double Ux = isx ? 0.0 : Ut, Vy = isx ? Ut : 0.0;
   RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
   RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
   RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
   RF->E[3] = (float)(-lam * kLog2e);
-  RF->Mt4 = (float)Mt4;
-  RF->nMt5 = (float)(-Mt5);
+  RF->Mt4 = (float)dt;
+  RF->nMt5 = 0.f;
   RF->wall = (float)wall;
   RF->gdt = (float)gdt;
 }
@@ -726,6 +721,7 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     shape(fb, pb);
     shape(fA, pA);
     constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+#pragma unroll
     for (int sd = 0; sd < 2; sd++) {
       float pa[4], Qf[8];
       shape(fa[sd], pa);
@@ -739,7 +735,7 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
       Qf[6] = fM2 * pa[3];
       Qf[7] = fM2 * pb[3];
 #pragma unroll
-      for (int c = 0; c < 8; c++) RF->Q[sd][c] = fG * Qf[isx ? c : py[c]];
+      for (int c = 0; c < 8; c++) RF->Q[sd][c] = fG * (isx ? Qf[c] : Qf[py[c]]);
       // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
       // Mt2 un a4 + Mt2 ut b4)
       const float k0 = fG * kap * fM3 * fA[3], kn = fG * kap * fM2 * fa[sd][3], kt = fG * kap * fM2 * fb[3];
@@ -839,9 +835,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     R.bfac = P.K / (2.0 * lam);
     R.wall = wall;
     if (RF) {
-      const double Z8[2][8] = {}, Z3[2][3] = {};
-      pack_face_f32(isx, Z8, Z3, R.bfac, 0.0, lam, 0.0, R.Ut, P.dt, 0.0, (double)wall, P.dt * R.G,
-                    RF);
+      wall_face_f32(isx, R.bfac, lam, R.Ut, P.dt, wall, P.dt * R.G, RF);
     }
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
@@ -862,7 +856,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     }
     face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, RF);
 #pragma unroll
-    for (int c = 0; c < 4; c++) F[pm[c]] = Fr[c];
+    for (int c = 0; c < 4; c++) F[c] = (c == 1 || c == 2) && !isx ? Fr[3 - c] : Fr[c];
   }
   mt4[t] = R.Mt4;
   if (isx) {
