@@ -113,7 +113,10 @@ ugks_status ugks_get_grid(ugks_handle h, double* dt, double* u, double* v, doubl
 /* Device bytes owned by h. */
 size_t ugks_device_bytes(ugks_handle h);
 
-/* Copy a state from host memory: f_host[nc][nq][2], W_host[4][nc] (layouts above). */
+/* Copy a state from host memory: f_host[nc][nq][2], W_host[4][nc] (layouts above).
+ * Synchronises; the host arrays are only read during the call.  FP32-f form: page-locked
+ * (pinned or registered) f_host is read in place by the conversion kernel; pageable memory
+ * goes through a device staging buffer.  f_host must hold the whole array either way. */
 ugks_status ugks_set_state(ugks_handle h, const double* f_host, const double* W_host);
 
 /* Same from device memory (same layouts, FP64).  Enqueued; returns without waiting. */
@@ -139,7 +142,9 @@ ugks_status ugks_sync(ugks_handle h);
  * prim_host[4][nc] = (rho, U, V, T).  Synchronises. */
 ugks_status ugks_moments(ugks_handle h, double* W_host, double* prim_host);
 
-/* Checkpoint: copy the full state (f_host[nc][nq][2], W_host[4][nc]).  Synchronises. */
+/* Checkpoint: copy the full state (f_host[nc][nq][2], W_host[4][nc]).  Synchronises.
+ * FP32-f form: page-locked f_host is written in place by the conversion kernel, pageable
+ * memory through a device staging buffer. */
 ugks_status ugks_get_state(ugks_handle h, double* f_host, double* W_host);
 
 /* Same into device memory (FP64 layouts above).  Enqueued; returns without waiting. */

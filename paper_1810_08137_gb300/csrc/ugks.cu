@@ -136,6 +136,17 @@ void set_derived(Params& P) {
   P.d_idy = 1.0 / P.dy;
 }
 
+// Bytes of one half of the FP32 form's host staging buffer: about 32 MiB, at least one mesh
+// row of FP64 f and at most half the mesh, rounded up to 256 bytes so that both halves are
+// aligned for any access.
+size_t stage_half_bytes(size_t row_d, size_t ny) {
+  size_t want = (size_t)64 << 20;
+  if (want < 2 * row_d) want = 2 * row_d;
+  if (want > row_d * ny) want = row_d * ny;
+  if (want < 2 * row_d) want = 2 * row_d;  // two halves of at least one row each
+  return ((want / 2) + 255) & ~(size_t)255;
+}
+
 // Row pairs of the FP32 paired-row layout for a velocity axis: (v < 0 half, all).  Each half
 // of the v axis (v < 0, v >= 0) is padded to an even number of rows.
 std::pair<int, int> f32_row_pairs(int nv, double vmin, double vmax) {
@@ -163,11 +174,7 @@ size_t predict_bytes(const ugks_config* c) {
   b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * (2 * (c->nu + c->nv) + 5 * c->nv);
   if (f32) {
     const size_t row_d = nx * nq * 2 * sizeof(double);
-    size_t want = (size_t)64 << 20;
-    if (want < 2 * row_d) want = 2 * row_d;
-    if (want > row_d * ny) want = row_d * ny;
-    if (want < 2 * row_d) want = 2 * row_d;
-    b += want + sizeof(float4) * fs + sizeof(double2) * nq +
+    b += 2 * stage_half_bytes(row_d, ny) + sizeof(float4) * fs + sizeof(double2) * nq +
          sizeof(float) * (12 * pr_all + 2 * (size_t)c->nu);
     b += sizeof(SlotDev) + sizeof(BatchWork);
   }
@@ -316,6 +323,23 @@ ugks_status copy_W_out(ugks_ctx* h, double* W, cudaMemcpyKind kind) {
   return UGKS_OK;
 }
 
+// Device address of `bytes` bytes of host memory at p that kernels can read and write
+// directly: page-locked or registered host memory (on this GB300 node reached over
+// NVLink-C2C), whose first and last byte map into one contiguous device range.  nullptr for
+// pageable memory, which goes through the staging buffer instead.
+void* device_view(const void* p, size_t bytes) {
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
+      cudaPointerGetAttributes(&a1, static_cast<const char*>(p) + bytes - 1) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer ||
+      static_cast<char*>(a1.devicePointer) != static_cast<char*>(a0.devicePointer) + bytes - 1)
+    return nullptr;
+  return a0.devicePointer;
+}
+
 ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
   const Params& P = h->P;
   const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
@@ -326,8 +350,9 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
     return UGKS_OK;
   }
   float4* dst = static_cast<float4*>(h->f[h->cur]);
-  if (!from_host) {
-    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(f, dst, P, h->grefd, 0, P.ny);
+  const double* src = from_host ? static_cast<const double*>(device_view(f, row_d * P.ny)) : f;
+  if (src) {  // device memory, or host memory the conversion kernel reads in place
+    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
@@ -361,8 +386,9 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
     return UGKS_OK;
   }
   const float4* src = static_cast<const float4*>(h->f[h->cur]);
-  if (!to_host) {
-    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, f, P, h->grefd, 0, P.ny);
+  double* dst = to_host ? static_cast<double*>(device_view(f, row_d * P.ny)) : f;
+  if (dst) {  // device memory, or host memory the conversion kernel writes in place
+    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
@@ -750,12 +776,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             alloc((void**)&h->d_grid, sizeof(double) * (2 * (P.nu + P.nv) + 5 * P.nv));
   if (ok && h->prec == UGKS_FP32F) {
     const size_t row_d = (size_t)P.nx * P.nq * 2 * sizeof(double);
-    size_t want = (size_t)64 << 20;
-    if (want < 2 * row_d) want = 2 * row_d;
-    if (want > row_d * P.ny) want = row_d * P.ny;
-    if (want < 2 * row_d) want = 2 * row_d;  // two halves of at least one row each
-    h->stage_bytes = want;
-    ok = alloc((void**)&h->stage, want) && alloc((void**)&h->gref4, sizeof(float4) * (size_t)P.fs) &&
+    h->stage_bytes = 2 * stage_half_bytes(row_d, P.ny);
+    ok = alloc((void**)&h->stage, h->stage_bytes) && alloc((void**)&h->gref4, sizeof(float4) * (size_t)P.fs) &&
          alloc((void**)&h->grefd, sizeof(double2) * (size_t)P.nq) &&
          alloc((void**)&h->ftab, sizeof(float) * (12 * (size_t)P.pr_all + 2 * (size_t)P.nu));
     if (ok) {

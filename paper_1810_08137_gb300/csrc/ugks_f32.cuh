@@ -550,37 +550,47 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
 // -------------------------------------------------------------------------------------
 // State conversion and initialisation (set-up and checkpoint paths, not the step)
 // -------------------------------------------------------------------------------------
-// FP64 rows [cell][q][(h, b)] (rows j0 .. j0+nrows-1) -> paired slots, e = f - g_ref.
+// FP64 rows [cell][q][(h, b)] (rows j0 .. j0+nrows-1) -> paired slots, e = f - g_ref.  One
+// thread per velocity in the order of the rows (adjacent 8-byte reads, coalesced also when
+// the rows are host memory read over the C2C link; the rows need only 8-byte alignment); it
+// writes its two components into its slot and, for the last row of an odd half, into the
+// padding row that repeats it.
 __global__ void k_rows_to_f32(const double* __restrict__ src, float4* __restrict__ dst, Params P,
                               const double2* __restrict__ grefd, int j0, int nrows) {
   const int ncell = P.nx * nrows;
   for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
     const int r = c / P.nx, i = c - r * P.nx;
     const double* s = src + (size_t)c * P.nq * 2;
-    float4* d = dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs;
-    for (int t = threadIdx.x; t < P.fs; t += blockDim.x) {
-      const int pr = t / P.nu, k = t - pr * P.nu;
-      const int q0 = prow(P, 2 * pr) * P.nu + k, q1 = prow(P, 2 * pr + 1) * P.nu + k;
-      const double2 g0 = grefd[q0], g1 = grefd[q1];
-      d[t] = make_float4((float)(s[2 * q0] - g0.x), (float)(s[2 * q1] - g1.x),
-                         (float)(s[2 * q0 + 1] - g0.y), (float)(s[2 * q1 + 1] - g1.y));
+    float* d = reinterpret_cast<float*>(dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs);
+    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
+      const int m = q / P.nu, k = q - m * P.nu, pr = padrow(P, m);
+      const double2 g = grefd[q];
+      const float h = (float)(s[2 * q] - g.x), b = (float)(s[2 * q + 1] - g.y);
+      float* o = d + 4 * ((size_t)(pr >> 1) * P.nu + k) + (pr & 1);
+      o[0] = h;
+      o[2] = b;
+      if (!(pr & 1) && prow(P, pr + 1) == m) {  // padding row of an odd half
+        o[1] = h;
+        o[3] = b;
+      }
     }
   }
 }
-// paired slots -> FP64 rows, f = e + g_ref
+// paired slots -> FP64 rows, f = e + g_ref; one thread per velocity in the order of the rows
+// (adjacent 8-byte writes; the rows need only 8-byte alignment)
 __global__ void k_f32_to_rows(const float4* __restrict__ src, double* __restrict__ dst, Params P,
                               const double2* __restrict__ grefd, int j0, int nrows) {
   const int ncell = P.nx * nrows;
   for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
     const int r = c / P.nx, i = c - r * P.nx;
-    const float4* s = src + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs;
+    const float* s = reinterpret_cast<const float*>(src + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs);
     double* d = dst + (size_t)c * P.nq * 2;
     for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
       const int m = q / P.nu, k = q - m * P.nu, pr = padrow(P, m);
-      const float4 v = s[(pr >> 1) * P.nu + k];
+      const float* e = s + 4 * ((size_t)(pr >> 1) * P.nu + k) + (pr & 1);
       const double2 g = grefd[q];
-      d[2 * q] = (double)((pr & 1) ? v.y : v.x) + g.x;
-      d[2 * q + 1] = (double)((pr & 1) ? v.w : v.z) + g.y;
+      d[2 * q] = (double)e[0] + g.x;
+      d[2 * q + 1] = (double)e[2] + g.y;
     }
   }
 }

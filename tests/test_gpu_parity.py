@@ -65,6 +65,14 @@ CASES = {
     "channel_1x3_v6": lambda: I.channel_config(nx=1, ny=3, n_vel=6),
     "channel_5x1_v9": lambda: I.channel_config(nx=5, ny=1, n_vel=9),
     "channel_40x20_v20": lambda: I.workload_channel_small(),
+    # degenerate velocity grids of the FP32-f paired-row layout (each half of the v axis
+    # padded to an even number of rows): a single v = 0 row, all v < 0, all v > 0, and an
+    # asymmetric grid whose halves differ in size, with nu > 32
+    "periodic_5x4_v6x1": lambda: periodic_cfg(nx=5, ny=4, nu=6, nv=1, vmin=0.0, vmax=0.0),
+    "periodic_5x4_v5x7_vneg": lambda: periodic_cfg(nx=5, ny=4, nu=5, nv=7, vmin=-3.0, vmax=-0.5),
+    "periodic_5x4_v5x6_vpos": lambda: periodic_cfg(nx=5, ny=4, nu=5, nv=6, vmin=0.5, vmax=3.0),
+    "periodic_6x5_v35x8_asym": lambda: periodic_cfg(nx=6, ny=5, nu=35, nv=8, vmin=-3.0, vmax=1.5,
+                                                    kn=0.1),
 }
 
 
