@@ -718,6 +718,11 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     P.ref_U = rU;
     P.ref_V = rV;
     P.ref_bf = P.K / (2.0 * P.ref_lam);
+    const double kLog2e = 1.4426950408889634;
+    P.ref_E[0] = std::log2(P.ref_G) - P.ref_lam * (rU * rU + rV * rV) * kLog2e;
+    P.ref_E[1] = 2.0 * P.ref_lam * rU * kLog2e;
+    P.ref_E[2] = 2.0 * P.ref_lam * rV * kLog2e;
+    P.ref_E[3] = -P.ref_lam * kLog2e;
     grefd_host.resize((size_t)P.nq);
     for (int m = 0; m < P.nv; m++)
       for (int k = 0; k < P.nu; k++) {

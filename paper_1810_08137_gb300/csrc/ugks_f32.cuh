@@ -296,15 +296,37 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 // Per-lane velocity constants of the walk (u shared by the pair, v per velocity).
 struct PairLane {
   float u, uu, cu, au, dt;   // u, u^2, |u| 2/dx, |u|/dx, dt
+  float bref;                // b_ref = K / (2 lam_ref): g_ref,b = b_ref g_ref,h
   float2 v, uv, vv, r2, ur2, vr2;
   float2 cv, av;             // |v| 2/dy, |v|/dy
-  float2 grh, grb, ngrh, ngrb;  // g_ref (h, b) and its negative
+  float2 grh, grb;           // g_ref (h, b)
 };
 
+// E0 + E1 u + E2 v + E3 r2 for both velocities
+__device__ __forceinline__ float2 epoly_p(const float4 e, const PairLane& L) {
+  return fma2(f2(e.w), L.r2, fma2(f2(e.z), L.v, f2(fmaf(e.y, L.u, e.x))));
+}
 // 2^(E0 + E1 u + E2 v + E3 r2) for both velocities
 __device__ __forceinline__ float2 exp_p(const float4 e, const PairLane& L) {
-  const float2 a = fma2(f2(e.w), L.r2, fma2(f2(e.z), L.v, f2(fmaf(e.y, L.u, e.x))));
+  const float2 a = epoly_p(e, L);
   return make_float2(ex2_ftz(a.x), ex2_ftz(a.y));
+}
+// 2^x - 1 for both lanes, to FP32 precision relative to the result: the Taylor series of
+// 2^x - 1 = sum_{n>=1} (x ln 2)^n / n! (7 terms; the first one left out is below 2e-8
+// relative for |x| <= 1/2), else 2^x - 1 from the exp2 estimate (no cancellation there).
+__device__ __forceinline__ float2 ex2m1_p(float2 x) {
+  constexpr float c1 = 0.69314718055994531f, c2 = 0.24022650695910071f, c3 = 0.055504108664821580f;
+  constexpr float c4 = 0.0096181291076284772f, c5 = 0.0013333558146428443f;
+  constexpr float c6 = 1.5403530393381609e-4f, c7 = 1.5252733804059841e-5f;
+  float2 p = fma2(f2(c7), x, f2(c6));
+  p = fma2(p, x, f2(c5));
+  p = fma2(p, x, f2(c4));
+  p = fma2(p, x, f2(c3));
+  p = fma2(p, x, f2(c2));
+  p = fma2(p, x, f2(c1));
+  p = mul2(p, x);
+  return make_float2(fabsf(x.x) <= 0.5f ? p.x : ex2_ftz(x.x) - 1.f,
+                     fabsf(x.y) <= 0.5f ? p.y : ex2_ftz(x.y) - 1.f);
 }
 
 // Micro flux through a face (FaceRecF), e-form f_up and d = u sigma_x + v sigma_y.
@@ -329,35 +351,38 @@ __device__ __forceinline__ P4 face_p(const FaceRecF* R, int side, const PairLane
   return X;
 }
 
-// Flux leaving a diffuse wall into the gas, e-form.
+// Flux leaving a diffuse wall into the gas, e-form: dt (g_w - g_ref) for h and
+// dt (b_w g_w - b_ref g_ref) = dt (b_w D + (b_w - b_ref) g_ref,h) for b, D = g_w - g_ref formed
+// from the wall exponent relative to g_ref's (FaceRecF).
 __device__ __forceinline__ P4 wall_p(const FaceRecF* R, const PairLane& L) {
   const float4 e = ld4(&R->E[0]);
-  const float gdt = R->gdt, X2 = R->K[0][3];
-  const float2 g = exp_p(e, L);
-  const float ndt = -L.dt;
+  const float dt = R->gdt, bw = R->K[0][3];
+  const float2 D = mul2(L.grh, ex2m1_p(epoly_p(e, L)));
   P4 X;
-  X.h = fma2(f2(gdt), g, mul2(f2(ndt), L.grh));
-  X.b = fma2(f2(gdt * X2), g, mul2(f2(ndt), L.grb));
+  X.h = mul2(f2(dt), D);
+  X.b = mul2(f2(dt), fma2(f2(bw), D, mul2(f2(bw - L.bref), L.grh)));
   return X;
 }
 
 // Eq. 3 increment of one cell (CellRecF); Xi / Xo: inflow / outflow flux in x and y.
 __device__ __forceinline__ P4 collide_p(const CellRecF* C, const PairLane& L, const P4& e,
                                         const P4& Xix, const P4& Xox, const P4& Xiy, const P4& Xoy) {
-  const float4 en = ld4(&C->En[0]);
-  const float4 e1 = ld4(&C->E1[0]);
-  const float4 A = ld4(&C->A1);    // A1 An b1 bn
+  const float4 en = ld4(&C->dEn[0]);
+  const float4 e1 = ld4(&C->dE1[0]);
+  const float4 A = ld4(&C->A1);    // A1 An db1 dbn
   const float4 B = ld4(&C->nBs);   // -Bs irx iry inv
-  const float2 gn = exp_p(en, L), g1 = exp_p(e1, L);
+  // g - g_ref for g^n and g^{n+1}, from the exponents relative to g_ref's
+  const float2 Dn = mul2(L.grh, ex2m1_p(epoly_p(en, L))), D1 = mul2(L.grh, ex2m1_p(epoly_p(e1, L)));
   const float2 r = fma2(L.v, f2(B.z), f2(L.u * B.y));
   const float aui = L.au * B.w;
   const float2 avi = mul2(L.av, f2(B.w));
   float2 dh = fma2(f2(aui), sub2(Xix.h, Xox.h), mul2(avi, sub2(Xiy.h, Xoy.h)));
   float2 db = fma2(f2(aui), sub2(Xix.b, Xox.b), mul2(avi, sub2(Xiy.b, Xoy.b)));
-  dh = fma2(f2(A.x), add2(g1, L.ngrh),
-            fma2(f2(A.y), add2(gn, L.ngrh), fma2(r, L.grh, fma2(f2(B.x), e.h, dh))));
-  db = fma2(f2(A.x), fma2(f2(A.z), g1, L.ngrb),
-            fma2(f2(A.y), fma2(f2(A.w), gn, L.ngrb), fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
+  // b g - g_ref,b = b D + (b - b_ref) g_ref,h
+  dh = fma2(f2(A.x), D1, fma2(f2(A.y), Dn, fma2(r, L.grh, fma2(f2(B.x), e.h, dh))));
+  db = fma2(f2(A.x), fma2(f2(A.z + L.bref), D1, mul2(f2(A.z), L.grh)),
+            fma2(f2(A.y), fma2(f2(A.w + L.bref), Dn, mul2(f2(A.w), L.grh)),
+                 fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
   return {add2(e.h, dh), add2(e.b, db)};
 }
 
@@ -403,10 +428,9 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
     const float4 g = __ldg(P.gref4 + ss);
     L.grh = make_float2(g.x, g.y);
     L.grb = make_float2(g.z, g.w);
-    L.ngrh = make_float2(-g.x, -g.y);
-    L.ngrb = make_float2(-g.z, -g.w);
   }
   L.dt = P.f_dt;
+  L.bref = (float)P.ref_bf;
   const int su = L.u > 0.f ? 1 : -1;
   const int sv = vpos ? 1 : -1;
   const int xside = su > 0 ? 0 : 1, yside = vpos ? 0 : 1;

@@ -60,7 +60,9 @@ struct CellRec {
 //     X_h = Q_h g + Mt4 f_up,h + nMt5 d_h,  Q_h = sum_k Q[s][k] m_k,  nMt5 = -Mt5,
 //     X_b = Q_b g + Mt4 f_up,b + nMt5 d_b,  Q_b = K[s][3] Q_h + K[s][0] + K[s][1] u + K[s][2] v,
 //     g = 2^(E . (1, u, v, r2))
-//   inflow from a diffuse wall (wall != 0): X_h = gdt g - dt g_ref,h, X_b = gdt K[0][3] g - dt g_ref,b
+//   inflow from a diffuse wall (wall != 0): X_h = gdt D, X_b = gdt (K[0][3] D + (K[0][3] - b_ref)
+//     g_ref,h), D = g_w - g_ref,h = g_ref,h (2^(E . (1, u, v, r2)) - 1) with E the wall
+//     Maxwellian's exponent relative to g_ref's and gdt = dt
 struct __align__(16) FaceRecF {
   float Q[2][8];
   float K[2][4];
@@ -69,14 +71,18 @@ struct __align__(16) FaceRecF {
 };
 // Eq. 3 as an increment e^{n+1} = e^n + d, per component, with the Maxwellians taken
 // relative to g_ref before they are weighted (the terms stay at the deviation's scale):
-//   d_h = aui dX_h + avi dY_h + r g_ref,h + A1 (g1 - g_ref,h) + An (gn - g_ref,h) + nBs e_h
-//   d_b = aui dX_b + avi dY_b + r g_ref,b + A1 (b1 g1 - g_ref,b) + An (bn gn - g_ref,b) + nBs e_b
-// with gn = 2^(En . (1, u, v, r2)), g1 likewise, aui = inv |u|/dx, avi = inv |v|/dy,
-// r = u irx + v iry, dX / dY the inflow minus outflow micro flux in x / y.
+//   d_h = aui dX_h + avi dY_h + r g_ref,h + A1 D1 + An Dn + nBs e_h
+//   d_b = aui dX_b + avi dY_b + r g_ref,b + A1 (b1 D1 + db1 g_ref,h) + An (bn Dn + dbn g_ref,h)
+//         + nBs e_b
+// with D = g - g_ref,h = g_ref,h (2^(dE . (1, u, v, r2)) - 1) for g^n and g^{n+1}, where dE are
+// the exponent coefficients of g relative to those of g_ref (formed in FP64, so they are
+// small and exact for a state near the reference, and D keeps FP32 precision relative to
+// itself); b = db + b_ref, aui = inv |u|/dx, avi = inv |v|/dy, r = u irx + v iry, dX / dY the
+// inflow minus outflow micro flux in x / y.
 struct __align__(16) CellRecF {
-  float En[4];
-  float E1[4];
-  float A1, An, b1, bn;     // inv cg1, inv cgn, K/(2 lam^{n+1}), K/(2 lam^n)
+  float dEn[4];
+  float dE1[4];
+  float A1, An, db1, dbn;   // inv cg1, inv cgn, K/(2 lam^{n+1}) - b_ref, K/(2 lam^n) - b_ref
   float nBs, irx, iry, inv; // -inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 
@@ -95,6 +101,7 @@ struct Params {
   // sum or flux of f is the FP32 sum of e plus the exact FP64 sum of g_ref.
   int use_ref;
   double ref_G, ref_U, ref_V, ref_lam, ref_bf;  // g_ref,h = G exp(-lam((u-U)^2+(v-V)^2)), b = bf h
+  double ref_E[4];        // g_ref,h = 2^(ref_E . (1, u, v, u^2 + v^2))
   double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
   // FP32 form, paired-row layout (see ugks_f32.cuh): pr_neg row pairs with v < 0, pr_all

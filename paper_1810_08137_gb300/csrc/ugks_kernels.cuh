@@ -606,10 +606,12 @@ __device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const d
   c[7] = Mt2 * pb[3];
 }
 
-// FP32 record of a diffuse-wall face (see FaceRecF): the wall Maxwellian with amplitude gdt
-// = dt G_w, no polynomial terms; stated in the global velocity frame (y faces: un = v).
-__device__ void wall_face_f32(bool isx, double X2, double lam, double Ut, double dt, int wall, double gdt,
-                              FaceRecF* RF) {
+// FP32 record of a diffuse-wall face (see FaceRecF): no polynomial terms; the wall
+// Maxwellian g_w = G_w exp(-lam |c - U_w|^2) enters as its exponent relative to g_ref's
+// (log2 units, formed in FP64), so that the walk forms g_w - g_ref without cancellation;
+// global velocity frame (y faces: un = v).
+__device__ void wall_face_f32(const Params& P, bool isx, double X2, double lam, double Ut, double G,
+                              int wall, FaceRecF* RF) {
   constexpr double kLog2e = 1.4426950408889634;
 #pragma unroll
   for (int sd = 0; sd < 2; sd++) {
@@ -619,14 +621,16 @@ __device__ void wall_face_f32(bool isx, double X2, double lam, double Ut, double
     RF->K[sd][3] = (float)X2;
   }
   const double Ux = isx ? 0.0 : Ut, Vy = isx ? Ut : 0.0;
-  RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
-  RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
-  RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
-  RF->E[3] = (float)(-lam * kLog2e);
-  RF->Mt4 = (float)dt;
+  // (a wall density rho_w <= 0 only arises from a state that is already unphysical; it is
+  // clamped so that the record stays finite, and the FP64 W update reports the failure)
+  RF->E[0] = (float)((log2(fmax(G, 1e-300)) - lam * (Ux * Ux + Vy * Vy) * kLog2e) - P.ref_E[0]);
+  RF->E[1] = (float)(2.0 * lam * Ux * kLog2e - P.ref_E[1]);
+  RF->E[2] = (float)(2.0 * lam * Vy * kLog2e - P.ref_E[2]);
+  RF->E[3] = (float)(-lam * kLog2e - P.ref_E[3]);
+  RF->Mt4 = (float)P.dt;
   RF->nMt5 = 0.f;
   RF->wall = (float)wall;
-  RF->gdt = (float)gdt;
+  RF->gdt = (float)P.dt;
 }
 
 // One UGKS interface in the face frame (un, ut): inputs are the interface sums (S1, S7)
@@ -695,6 +699,39 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   R.Mt5 = Mt[4];
   R.bfac = X2;
   R.wall = 0;
+#ifdef UGKS_X_REC64
+  if (RF) {
+    constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+    const double kap = 0.5 * X4m;
+    double pa[4], pb[4], pA[4], Qh[8];
+    shape_h(b, X2, pb);
+    shape_h(A, X2, pA);
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const double* as = sd == 0 ? aL : aR;
+      shape_h(as, X2, pa);
+      qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, Qh);
+#pragma unroll
+      for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)(R.G * (isx ? Qh[c] : Qh[py[c]]));
+      const double k0 = kap * Mt[2] * A[3], kn = kap * Mt[1] * as[3], kt = kap * Mt[1] * b[3];
+      RF->K[sd][0] = (float)(R.G * k0);
+      RF->K[sd][1] = (float)(R.G * (isx ? kn : kt));
+      RF->K[sd][2] = (float)(R.G * (isx ? kt : kn));
+      RF->K[sd][3] = (float)X2;
+    }
+    constexpr double kLog2e = 1.4426950408889634;
+    const double Ux = isx ? U : V, Vy = isx ? V : U;
+    RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
+    RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
+    RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
+    RF->E[3] = (float)(-lam * kLog2e);
+    RF->Mt4 = (float)Mt[3];
+    RF->nMt5 = (float)(-Mt[4]);
+    RF->wall = 0.f;
+    RF->gdt = 0.f;
+    return;
+  }
+#endif
   if (RF) {
     // FP32 record: its coefficients are stored in FP32, so they are formed in FP32 from the
     // FP64 slopes, time weights and amplitude (S6/S8 coefficients, global frame)
@@ -835,7 +872,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     R.bfac = P.K / (2.0 * lam);
     R.wall = wall;
     if (RF) {
-      wall_face_f32(isx, R.bfac, lam, R.Ut, P.dt, wall, P.dt * R.G, RF);
+      wall_face_f32(P, isx, R.bfac, lam, R.Ut, R.G, wall, RF);
     }
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
@@ -936,18 +973,20 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       CellRecF F;
       // the amplitude enters the exponent; log2 in FP64 (an approximate FP32 log2 put
       // ~1e-7 relative noise on g per cell, visible in rho V at Kn 0.01)
-      F.En[0] = (float)(log2(R.Gn) - ln * (Un * Un + Vn * Vn) * kLog2e);
-      F.En[1] = (float)(2.0 * ln * Un * kLog2e);
-      F.En[2] = (float)(2.0 * ln * Vn * kLog2e);
-      F.En[3] = (float)(-ln * kLog2e);
-      F.E1[0] = (float)(log2(R.G1) - l1 * (U1 * U1 + V1 * V1) * kLog2e);
-      F.E1[1] = (float)(2.0 * l1 * U1 * kLog2e);
-      F.E1[2] = (float)(2.0 * l1 * V1 * kLog2e);
-      F.E1[3] = (float)(-l1 * kLog2e);
+      // exponents of g^n, g^{n+1} relative to those of g_ref (log2 units), in FP64
+      const double r0 = P.ref_E[0], r1 = P.ref_E[1], r2 = P.ref_E[2], r3 = P.ref_E[3];
+      F.dEn[0] = (float)((log2(R.Gn) - ln * (Un * Un + Vn * Vn) * kLog2e) - r0);
+      F.dEn[1] = (float)(2.0 * ln * Un * kLog2e - r1);
+      F.dEn[2] = (float)(2.0 * ln * Vn * kLog2e - r2);
+      F.dEn[3] = (float)(-ln * kLog2e - r3);
+      F.dE1[0] = (float)((log2(R.G1) - l1 * (U1 * U1 + V1 * V1) * kLog2e) - r0);
+      F.dE1[1] = (float)(2.0 * l1 * U1 * kLog2e - r1);
+      F.dE1[2] = (float)(2.0 * l1 * V1 * kLog2e - r2);
+      F.dE1[3] = (float)(-l1 * kLog2e - r3);
       F.A1 = (float)(R.inv * R.cg1);
       F.An = (float)(R.inv * R.cgn);
-      F.b1 = (float)R.b1;
-      F.bn = (float)R.bn;
+      F.db1 = (float)(R.b1 - P.ref_bf);
+      F.dbn = (float)(R.bn - P.ref_bf);
       F.nBs = (float)(-(R.inv * (R.cg1 + R.cgn)));
       F.irx = (float)(R.inv * refx);
       F.iry = (float)(R.inv * refy);

@@ -241,6 +241,34 @@ def test_device_state_roundtrip(U, oracle):
     assert rel_f(fo.cpu().numpy(), fr) <= FP64_TOL
 
 
+@pytest.mark.parametrize("name", ["periodic_13x7_v37", "channel_9x5_v21"])
+def test_fp32f_state_through_pinned_host_buffers(U, oracle, name):
+    """FP32-f form: set_state / get_state with page-locked host buffers (converted in place
+    by the kernels) give bitwise the state of the staged path for pageable buffers.  The
+    9x5 mesh with 21^2 velocities has staging halves that are not a multiple of 16 bytes
+    before rounding."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    cfg = (CASES[name]() if name in CASES else
+           I.channel_config(nx=9, ny=5, n_vel=21, kn=0.05, rho_in=1.45))
+    f, W = random_state(oracle, cfg, 11)
+    with U.Solver(cfg, U.FP32F) as s:
+        s.set_state(f, W)
+        s.step(2)
+        fa, Wa = s.get_state()
+    pin_in = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+    pin_in.numpy()[:] = f
+    pin_out = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+    Wb = np.empty_like(W)
+    P = ctypes.POINTER(ctypes.c_double)
+    with U.Solver(cfg, U.FP32F) as s:
+        s.set_state(pin_in.numpy(), W)
+        s.step(2)
+        s._check(s._L.ugks_get_state(s._h, pin_out.numpy().ctypes.data_as(P), Wb.ctypes.data_as(P)))
+    assert np.array_equal(pin_out.numpy(), fa)
+    assert np.array_equal(Wb, Wa)
+
+
 def test_numeric_failure_is_reported(U, oracle):
     """A state with negative density is caught by the cell kernel's check and surfaces as
     UGKS_ENUMERIC at the next synchronising call (no device trap)."""
@@ -284,6 +312,55 @@ def test_full_size_800x400_sampled(U, oracle, prec, tol):
     err = np.max(np.abs(Wg - Wo), axis=0) / scale
     assert np.all(err <= tol), err
     assert np.max(np.abs(f1[ids] - fo)) / np.max(np.abs(fo)) <= max(tol, 1e-12) * 10
+
+
+@pytest.mark.parametrize("nvel", [101, 201])
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, 1e-5)])
+def test_large_velocity_full_mesh_sampled(U, oracle, nvel, prec, tol):
+    """Large-velocity workload at full size (200x100 cells, nvel^2 velocities on
+    [-20,20]^2, Kn 0.01), in the launch configuration the bench times: 5 steps from the
+    seeded Maxwellian, then one more step checked on sampled cells against the oracle run on
+    the same state."""
+    cfg = I.workload_large_velocity(nvel)
+    rho, Uf, Vf, T = I.initial_prim(cfg, I.seed_for(3, nvel))
+    ids = _sample_ids(cfg, 12, 77)
+    with U.Solver(cfg, prec) as s:
+        s.init_maxwellian(rho, Uf, Vf, T)
+        s.step(5)
+        f, W = s.get_state()
+        s.step(1)
+        f1, W1 = s.get_state()
+    fo, Wo = oracle.step_cells(cfg, f, W, ids)
+    del f
+    Wg = W1[:, ids].T
+    scale = np.max(np.abs(W1), axis=1)
+    err = np.max(np.abs(Wg - Wo), axis=0) / scale
+    assert np.all(err <= tol), err
+    assert np.max(np.abs(f1[ids] - fo)) / np.max(np.abs(fo)) <= max(tol, 1e-12) * 10
+
+
+@pytest.mark.parametrize("name,steps", [("mesh_800x400_v28", 200), ("large_velocity_v101", 50),
+                                        ("large_velocity_v201", 50)])
+def test_fp32f_against_fp64_long_runs(U, name, steps):
+    """Transitive parity of long runs at full size: the FP32-f form against the plain FP64
+    form (whose every step matches the oracle to 1e-12, see the sampled full-size tests)
+    from the same seeded Maxwellian, per-field error of W <= 1e-5 relative."""
+    if name.startswith("mesh"):
+        cfg = I.workload_mesh_sweep(800)
+        prim = I.initial_prim(cfg, I.seed_for(2, 800))
+    else:
+        n = int(name.rsplit("_v", 1)[1])
+        cfg = I.workload_large_velocity(n)
+        prim = I.initial_prim(cfg, I.seed_for(3, n))
+    Ws = []
+    for prec in (U.FP64, U.FP32F):
+        with U.Solver(cfg, prec) as s:
+            s.init_maxwellian(*prim)
+            s.step(steps)
+            Ws.append(s.moments())
+    err = rel_fields(Ws[1], Ws[0])
+    print(f"{name} {steps} steps: FP32-f vs FP64 {err}")
+    assert np.all(err <= 1e-5), err
 
 
 def test_graph_replay_matches_direct_launches(U, oracle):
