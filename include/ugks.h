@@ -57,9 +57,11 @@ typedef enum {
 
 typedef enum {
   UGKS_FP64 = 0,   /* f stored and transported in FP64, all arithmetic FP64 */
-  UGKS_FP32F = 1   /* f stored and transported in FP32; FP64 for the velocity-moment
-                      accumulation across lanes, W, the interface scalars (micro-slope
-                      solves, Mt time weights) and the cell update coefficients */
+  UGKS_FP32F = 1   /* f stored and transported in FP32 as f - g_ref; its velocity sums
+                      are FP32 and are combined in FP64 with the exact sums of g_ref; FP64
+                      for W, the interface scalars (micro-slope solves, Mt time weights,
+                      equilibrium flux), the cell update coefficients and the exponents of
+                      the collision and wall Maxwellians relative to g_ref */
 } ugks_precision;
 
 enum { UGKS_SIDE_W = 0, UGKS_SIDE_E = 1, UGKS_SIDE_S = 2, UGKS_SIDE_N = 3 };
@@ -88,8 +90,9 @@ typedef struct {
   int precision;         /* ugks_precision */
   /* UGKS_FP32F only: reference Maxwellian g_ref(rho, U, V, T).  The FP32 buffers hold
    * f - g_ref and every velocity sum and flux adds the exact FP64 contribution of g_ref,
-   * so FP32 rounding acts on the (small) deviation from it.  ref_T <= 0 selects
-   * (1, 0, 0, 1).  The state exchanged through this ABI is always f itself. */
+   * so FP32 rounding acts on the (small) deviation from it; a reference near the flow's
+   * mean state keeps that deviation small.  ref_T <= 0 selects (1, 0, 0, 1).  The state
+   * exchanged through this ABI is always f itself. */
   double ref_rho, ref_U, ref_V, ref_T;
 } ugks_config;
 

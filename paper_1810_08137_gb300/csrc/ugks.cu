@@ -638,7 +638,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   h->cfg = *cfg;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->prec = cfg->precision;
-  h->t2 = h->prec == UGKS_FP64 ? sizeof(double2) : sizeof(float2);
+  h->t2 = sizeof(double2);  // FP64 form (the FP32-f form stores float4 slots of two velocities)
   Params& P = h->P;
   memset(&P, 0, sizeof P);
   P.nx = cfg->nx; P.ny = cfg->ny; P.nu = cfg->nu; P.nv = cfg->nv; P.nq = cfg->nu * cfg->nv;
