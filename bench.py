@@ -48,10 +48,10 @@ def peaks():
 # 2.07 GHz (unit counts and maximum clock; no FP64 peak is measured by the driver).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # Nominal FP64 arithmetic of the update (S6, S8, Eq. 3) per velocity-cell, exp and divide
-# counted as one operation each: 2 van Leer slopes x 2 components (20), upwind face values
-# (4), u sigma_x + v sigma_y (6), 2 face fluxes (39 each: Maxwellian 8, Q_h 15, Q_b 6,
-# X 10), collision (42).
-UPDATE_FLOPS_PER_VC = 150
+# counted as one operation each: upwind face values (4), u sigma_x + v sigma_y (6), 2 face
+# fluxes (39 each: Maxwellian 8, Q_h 15, Q_b 6, X 10), collision (42).  The van Leer slopes
+# (20 more) are formed once per velocity-cell by the FP64 sums kernel and read back here.
+UPDATE_FLOPS_PER_VC = 130
 # DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
 # capture summarised in profiles/; None when the kernel has changed since that capture.
 UPDATE_TRAFFIC_PER_VC = (595.991040e6 + 466.211328e6) / 62.72e6  # kb_strip, 400x200x28^2 capture

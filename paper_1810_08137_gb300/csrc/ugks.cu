@@ -31,6 +31,7 @@ struct ugks_ctx {
   double* W[2] = {nullptr, nullptr};
   int cur = 0;
   double* sums = nullptr;
+  double2* slopes = nullptr;  // FP64 form: van Leer slopes kept by the sums kernel for the update
   FaceRec* fxr = nullptr;
   FaceRec* fyr = nullptr;
   double* Fx = nullptr;
@@ -172,6 +173,7 @@ size_t predict_bytes(const ugks_config* c) {
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
   b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
   b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * (2 * (c->nu + c->nv) + 5 * c->nv);
+  if (!f32) b += nwe * nq * 2 * sizeof(double2);  // slope buffer
   if (f32) {
     const size_t row_d = nx * nq * 2 * sizeof(double);
     b += 2 * stage_half_bytes(row_d, ny) + sizeof(float4) * fs + sizeof(double2) * nq +
@@ -196,7 +198,10 @@ cudaError_t set_smem_limits_fp64(int nv) {
   cudaError_t e = cudaFuncSetAttribute(k_sums<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_sums<double>(nv));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_update<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_update<double, double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_update<double>(nv));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_update<double, double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_update<double>(nv));
 }
 
@@ -239,7 +244,7 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   const int nce = (P.nx + 2) * (P.ny + 2);
   T* sums = reinterpret_cast<T*>(h->sums);  // FP32 form: FP32 sums in the same buffer
   k_sums<T, T2><<<(nce + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_sums<T>(P.nv), st>>>(
-      P, fi, sums);
+      P, fi, sums, reinterpret_cast<T2*>(h->slopes));
   if ((r = mark(h, 3)) != cudaSuccess) return r;
   const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
   k_faces<T><<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
@@ -249,9 +254,9 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
                                        h->cellf, h->mt4);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  k_update<T, T2>
+  k_update<T, T2, true>
       <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
-          P, fi, fo, h->fxr, h->fyr, h->cells);
+          P, fi, fo, h->fxr, h->fyr, h->cells, reinterpret_cast<const T2*>(h->slopes));
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
@@ -604,11 +609,12 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   k_ghost_x<double2><<<dim3(ny, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
-                            smem_sums<double>(P.nv), st>>>(P, f0, sums);
+                            smem_sums<double>(P.nv), st>>>(P, f0, sums, nullptr);
   k_faces<double><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
-  k_update<double, double2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
-                                     smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells);
+  // slopes are formed again in the update kernel: the scratch array holds no slope buffer
+  k_update<double, double2, false><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
+                                     smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells, nullptr);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpy2DAsync(f_out, row, reinterpret_cast<char*>(f1) + ((size_t)2 * P.ex + 2) * nq * sizeof(double2),
                           (size_t)P.ex * nq * sizeof(double2), row, ny, cudaMemcpyDeviceToDevice, st));
@@ -767,6 +773,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             alloc((void**)&h->W[0], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->sums, sizeof(double) * kNSum * (size_t)h->nwe) &&
+            (f32 || alloc((void**)&h->slopes, sizeof(double2) * 2 * (size_t)h->nwe * P.nq)) &&
             (f32 ? alloc((void**)&h->fxf, sizeof(FaceRecF) * (size_t)nfx)
                  : alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx)) &&
             (f32 ? alloc((void**)&h->fyf, sizeof(FaceRecF) * (size_t)nfy)
@@ -844,6 +851,10 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
       if ((r = cudaMemsetAsync(h->W[b], 0, 4 * sizeof(double) * h->nwe, h->stream)) != cudaSuccess) return r;
     }
     if ((r = cudaMemsetAsync(h->rpart, 0, sizeof(double) * 8 * h->nrblocks, h->stream)) != cudaSuccess) return r;
+    // slopes of cells the sums kernel never forms (wall ghosts, corners) stay zero
+    if (h->slopes && (r = cudaMemsetAsync(h->slopes, 0, sizeof(double2) * 2 * (size_t)h->nwe * P.nq,
+                                          h->stream)) != cudaSuccess)
+      return r;
     if (h->gref4 && (r = cudaMemcpyAsync(h->gref4, gref_host.data(), sizeof(float4) * gref_host.size(),
                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
@@ -870,7 +881,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
-  void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->fxr, h->fyr, h->Fx, h->Fy,
+  void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->slopes, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref4, h->grefd, h->fxf, h->fyf,
                   h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
   if (h->stream) cudaStreamSynchronize(h->stream);

@@ -255,9 +255,12 @@ __device__ __forceinline__ void utab(const Params& P, int k, double& u, double& 
   u = P.u[k]; wu = P.wu[k];
 }
 
+// slopes: null, or [(nx+2)(ny+2) cells (W indexing)][nq][2] of (r_x,h r_x,b), (r_y,h r_y,b),
+// written for every cell whose sums are formed (the update kernel then reads them)
 template <typename T, typename T2>
 __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict__ f,
-                                          T* __restrict__ sums, unsigned char* smraw, int bx) {
+                                          T* __restrict__ sums, unsigned char* smraw, int bx,
+                                          T2* __restrict__ slopes = nullptr) {
   const int nv = P.nv, nu = P.nu, nq = P.nq;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
@@ -280,6 +283,7 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
 
   const T2* fc = f + fcell(P, i, j) * nq;
   const size_t rs = (size_t)P.ex * nq;
+  T2* slc = slopes ? slopes + (size_t)wcell(P, i, j) * nq * 2 : nullptr;
   T tdx, tdy;
   if (sizeof(T) == 4) { tdx = (T)P.f_tdx; tdy = (T)P.f_tdy; }
   else { tdx = T(2.0 / P.dx); tdy = T(2.0 / P.dy); }
@@ -327,7 +331,18 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
         ryb = vl_half(v[3].y, v[0].y, v[4].y);
       }
     };
-    auto slopes = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
+    // keep the slopes of row m for the update kernel
+    auto store = [&](int m, T rxh, T rxb, T ryh, T ryb) {
+      if (slc && act) {
+        T2* q = slc + 2 * ((size_t)m * nu + k);
+        T2 a, b;
+        a.x = rxh; a.y = rxb;
+        b.x = ryh; b.y = ryb;
+        q[0] = a;
+        q[1] = b;
+      }
+    };
+    auto slopes_of = [&](int m, T& rxh, T& rxb, T& ryh, T& ryb, T2& c) {
       T2 v[5];
       load5(m, v);
       slopes5(v, rxh, rxb, ryh, ryb);
@@ -336,6 +351,7 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     auto acc = [&](int m, const T2 (&v)[5]) {
       T rxh, rxb, ryh, ryb;
       slopes5(v, rxh, rxb, ryh, ryb);
+      store(m, rxh, rxb, ryh, ryb);
       const T2 c = v[0];
       T wn[5];
       wtab(P, m, wn);
@@ -360,7 +376,8 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     auto row_v0 = [&](int m) {  // v = 0: only the w_0 sums, half weight
       T rxh, rxb, ryh, ryb;
       T2 c;
-      slopes(m, rxh, rxb, ryh, ryb, c);
+      slopes_of(m, rxh, rxb, ryh, ryb, c);
+      store(m, rxh, rxb, ryh, ryb);
       T wn[5];
       wtab(P, m, wn);
       const T hw = T(0.5) * wn[0];
@@ -431,9 +448,9 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
 }
 template <typename T, typename T2>
 __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
-                                              T* __restrict__ sums) {
+                                              T* __restrict__ sums, T2* __restrict__ slopes) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  sums_body<T, T2>(P, f, sums, smraw, blockIdx.x);
+  sums_body<T, T2>(P, f, sums, smraw, blockIdx.x, slopes);
 }
 
 // -------------------------------------------------------------------------------------
@@ -1060,12 +1077,16 @@ struct UpdCell {
   int wall[4];
 };
 
-template <typename T, typename T2>
+// SLOPES: the van Leer slopes of the cell and of its upwind neighbours come from the sums
+// kernel's slope buffer sl ([(nx+2)(ny+2)][nq][2], W cell indexing) instead of being formed
+// again here (12 per velocity-cell); both give the same values.
+template <typename T, typename T2, bool SLOPES>
 __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__ f,
                                                 T2* __restrict__ fo,
                                                 const FaceRec* __restrict__ fxr,
                                                 const FaceRec* __restrict__ fyr,
-                                                const CellRec* __restrict__ cr) {
+                                                const CellRec* __restrict__ cr,
+                                                const T2* __restrict__ sl) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nv = P.nv, nu = P.nu, nq = P.nq, nx = P.nx, ny = P.ny;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1113,6 +1134,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
   const long rs = (long)P.ex * nq;
   const T2* fc0 = f + fcell(P, i, j) * nq;
   T2* fo0 = fo + fcell(P, i, j) * nq;
+  const T2* sl0 = SLOPES ? sl + (size_t)wcell(P, i, j) * nq * 2 : nullptr;  // this cell's slopes
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
@@ -1140,6 +1162,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     }
     const bool up = ud > 0.0;  // x upwind neighbour: W for u > 0, E for u < 0
     const long xo = up ? -(long)nq : (long)nq;
+    const long xso = up ? -(long)nq : (long)nq;  // x-upwind cell in the slope buffer, in q
     const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
     const T cu = u * tdx, fxu = u * idx;
 
@@ -1153,26 +1176,35 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         poly_in_v_yface(RN.Q[VUP ? 0 : 1][c], ud, qN[c]);
       }
       const long yo = VUP ? -rs : rs;
+      const long yso = VUP ? -(long)P.wx * nq : (long)P.wx * nq;  // y-upwind cell, in q
       const bool yz = (VUP && j == 0 && pS) || (!VUP && j == ny - 1 && pN);
       for (int m = m0; m < m1; m++) {
         const T vv = sv[m];
         const T2* p = fc0 + (size_t)m * nu + kk;
-        const T2 c = p[0], w = p[-(long)nq], e = p[nq], s = p[-rs], n = p[rs];
-        const T2 xf = p[2 * xo], xs_ = p[xo - rs], xn = p[xo + rs];
-        const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
-        const T2 xu = up ? w : e;
-        const T2 yu = VUP ? s : n;
+        const T2 c = p[0];
+        const T2 xu = p[xo], yu = p[yo];
         // half slopes r = sigma h / 2 of the cell, its x-upwind and its y-upwind neighbour
-        const T rxch = vl_half(w.x, c.x, e.x), rxcb = vl_half(w.y, c.y, e.y);
-        const T rych = vl_half(s.x, c.x, n.x), rycb = vl_half(s.y, c.y, n.y);
-        T rxuh, rxub;
-        if (up) { rxuh = vl_half(xf.x, w.x, c.x); rxub = vl_half(xf.y, w.y, c.y); }
-        else    { rxuh = vl_half(c.x, e.x, xf.x); rxub = vl_half(c.y, e.y, xf.y); }
-        T ryuh = vl_half(xs_.x, xu.x, xn.x), ryub = vl_half(xs_.y, xu.y, xn.y);
-        T rxvh = vl_half(yw.x, yu.x, ye.x), rxvb = vl_half(yw.y, yu.y, ye.y);
-        T ryvh, ryvb;
-        if (VUP) { ryvh = vl_half(yf.x, s.x, c.x); ryvb = vl_half(yf.y, s.y, c.y); }
-        else     { ryvh = vl_half(c.x, n.x, yf.x); ryvb = vl_half(c.y, n.y, yf.y); }
+        T rxch, rxcb, rych, rycb, rxuh, rxub, ryuh, ryub, rxvh, rxvb, ryvh, ryvb;
+        if (SLOPES) {
+          const T2* q = sl0 + 2 * ((size_t)m * nu + kk);
+          const T2 a = q[0], b = q[1], au = q[2 * xso], bu = q[2 * xso + 1];
+          const T2 av = q[2 * yso], bv = q[2 * yso + 1];
+          rxch = a.x; rxcb = a.y; rych = b.x; rycb = b.y;
+          rxuh = au.x; rxub = au.y; ryuh = bu.x; ryub = bu.y;
+          rxvh = av.x; rxvb = av.y; ryvh = bv.x; ryvb = bv.y;
+        } else {
+          const T2 w = p[-(long)nq], e = p[nq], s = p[-rs], n = p[rs];
+          const T2 xf = p[2 * xo], xs_ = p[xo - rs], xn = p[xo + rs];
+          const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
+          rxch = vl_half(w.x, c.x, e.x); rxcb = vl_half(w.y, c.y, e.y);
+          rych = vl_half(s.x, c.x, n.x); rycb = vl_half(s.y, c.y, n.y);
+          if (up) { rxuh = vl_half(xf.x, w.x, c.x); rxub = vl_half(xf.y, w.y, c.y); }
+          else    { rxuh = vl_half(c.x, e.x, xf.x); rxub = vl_half(c.y, e.y, xf.y); }
+          ryuh = vl_half(xs_.x, xu.x, xn.x); ryub = vl_half(xs_.y, xu.y, xn.y);
+          rxvh = vl_half(yw.x, yu.x, ye.x); rxvb = vl_half(yw.y, yu.y, ye.y);
+          if (VUP) { ryvh = vl_half(yf.x, s.x, c.x); ryvb = vl_half(yf.y, s.y, c.y); }
+          else     { ryvh = vl_half(c.x, n.x, yf.x); ryvb = vl_half(c.y, n.y, yf.y); }
+        }
         if (xz) rxuh = rxub = ryuh = ryub = T(0);
         if (yz) rxvh = rxvb = ryvh = ryvb = T(0);
         const T cv = vv * tdy, fyv = vv * idy;
