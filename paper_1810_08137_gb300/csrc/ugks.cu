@@ -729,6 +729,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     P.ref_E[1] = 2.0 * P.ref_lam * rU * kLog2e;
     P.ref_E[2] = 2.0 * P.ref_lam * rV * kLog2e;
     P.ref_E[3] = -P.ref_lam * kLog2e;
+    P.ref_iG = 1.0 / P.ref_G;
+    P.ref_E0u = -P.ref_lam * (rU * rU + rV * rV) * kLog2e;
     grefd_host.resize((size_t)P.nq);
     for (int m = 0; m < P.nv; m++)
       for (int k = 0; k < P.nu; k++) {

@@ -102,6 +102,7 @@ struct Params {
   int use_ref;
   double ref_G, ref_U, ref_V, ref_lam, ref_bf;  // g_ref,h = G exp(-lam((u-U)^2+(v-V)^2)), b = bf h
   double ref_E[4];        // g_ref,h = 2^(ref_E . (1, u, v, u^2 + v^2))
+  double ref_iG, ref_E0u;  // 1 / ref_G; ref_E[0] - log2(ref_G)
   double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
   // FP32 form, paired-row layout (see ugks_f32.cuh): pr_neg row pairs with v < 0, pr_all

@@ -462,32 +462,33 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
 // <x^{n+2}> = U <x^{n+1}> + (n+1)/(2 lam) <x^n> on every range.
 // h = 1/(2 lam), rl = 1/sqrt(lam).  One erfc: the half-range mass on the far side of U is
 // erfc(sqrt(lam)|U|)/2, the near side 1 minus that.
-__device__ void gauss_moments7(double U, double lam, double h, double rl, double* M, double* Mp,
-                               double* Mn) {
-  constexpr double kHalfRsqrtPi = 0.28209479177387814347;  // 1 / (2 sqrt(pi))
-  const double sl = lam * rl;
-  const double e = exp(-lam * U * U) * (kHalfRsqrtPi * rl);
-  const double far = 0.5 * erfc(sl * fabs(U));
-  M[0] = 1.0;
+template <typename T>
+__device__ void gauss_moments7(T U, T lam, T h, T rl, T* M, T* Mp, T* Mn) {
+  constexpr T kHalfRsqrtPi = T(0.28209479177387814347);  // 1 / (2 sqrt(pi))
+  const T sl = lam * rl;
+  const T e = exp(-lam * U * U) * (kHalfRsqrtPi * rl);
+  const T far = T(0.5) * erfc(sl * fabs(U));
+  M[0] = T(1);
   M[1] = U;
-  Mp[0] = U >= 0.0 ? 1.0 - far : far;
-  Mn[0] = U >= 0.0 ? far : 1.0 - far;
+  Mp[0] = U >= T(0) ? T(1) - far : far;
+  Mn[0] = U >= T(0) ? far : T(1) - far;
   Mp[1] = U * Mp[0] + e;
   Mn[1] = U * Mn[0] - e;
 #pragma unroll
   for (int n = 0; n < 5; n++) {
-    M[n + 2] = U * M[n + 1] + (n + 1) * h * M[n];
-    Mp[n + 2] = U * Mp[n + 1] + (n + 1) * h * Mp[n];
-    Mn[n + 2] = U * Mn[n + 1] + (n + 1) * h * Mn[n];
+    M[n + 2] = U * M[n + 1] + T(n + 1) * h * M[n];
+    Mp[n + 2] = U * Mp[n + 1] + T(n + 1) * h * Mp[n];
+    Mn[n + 2] = U * Mn[n + 1] + T(n + 1) * h * Mn[n];
   }
 }
 
 // Full-range moments only (tangential axis).
-__device__ void gauss_moments7_full(double U, double h, double* M) {
-  M[0] = 1.0;
+template <typename T>
+__device__ void gauss_moments7_full(T U, T h, T* M) {
+  M[0] = T(1);
   M[1] = U;
 #pragma unroll
-  for (int n = 0; n < 5; n++) M[n + 2] = U * M[n + 1] + (n + 1) * h * M[n];
+  for (int n = 0; n < 5; n++) M[n + 2] = U * M[n + 1] + T(n + 1) * h * M[n];
 }
 
 // <u^a v^b psi> for the normalised Maxwellian, u-moments Mu (one range), v-moments Mv,
@@ -508,12 +509,14 @@ __device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, doub
 // <xi^2 (c . psi)> = X2 (c . psi with xi^2 -> X2) + h (X4 - X2^2).
 // The tables A, B, C depend on (c, Mv, b) only and are shared by evaluations at several
 // (Mu, a); X4m = X4 - X2^2.
+template <typename T>
 struct APsi {
-  double A[3], B[3], C[3], h, mvb;
+  T A[3], B[3], C[3], h, mvb;
 };
-__device__ __forceinline__ void apsi_prep(const double* Mv, double X2, int b, const double* c, APsi& t) {
-  t.h = 0.5 * c[3];
-  const double c0x = c[0] + t.h * X2;
+template <typename T>
+__device__ __forceinline__ void apsi_prep(const T* Mv, T X2, int b, const T* c, APsi<T>& t) {
+  t.h = T(0.5) * c[3];
+  const T c0x = c[0] + t.h * X2;
 #pragma unroll
   for (int q = 0; q < 3; q++) {
     t.A[q] = c0x * Mv[b + q] + c[2] * Mv[b + q + 1] + t.h * Mv[b + q + 2];
@@ -522,23 +525,23 @@ __device__ __forceinline__ void apsi_prep(const double* Mv, double X2, int b, co
   }
   t.mvb = Mv[b];
 }
-__device__ __forceinline__ void apsi_eval(const APsi& t, const double* Mu, double X2, double X4m, int a,
-                                          double* o) {
-  auto T = [&](int p, int q) { return Mu[a + p] * t.A[q] + Mu[a + p + 1] * t.B[q] + Mu[a + p + 2] * t.C[q]; };
-  const double t00 = T(0, 0);
+template <typename T>
+__device__ __forceinline__ void apsi_eval(const APsi<T>& t, const T* Mu, T X2, T X4m, int a, T* o) {
+  auto Tm = [&](int p, int q) { return Mu[a + p] * t.A[q] + Mu[a + p + 1] * t.B[q] + Mu[a + p + 2] * t.C[q]; };
+  const T t00 = Tm(0, 0);
   o[0] = t00;
-  o[1] = T(1, 0);
-  o[2] = T(0, 1);
-  o[3] = 0.5 * (T(2, 0) + T(0, 2) + X2 * t00 + t.h * X4m * (Mu[a] * t.mvb));
+  o[1] = Tm(1, 0);
+  o[2] = Tm(0, 1);
+  o[3] = T(0.5) * (Tm(2, 0) + Tm(0, 2) + X2 * t00 + t.h * X4m * (Mu[a] * t.mvb));
 }
 
 // q = (K+2)/(4 lam) is the mean internal plus thermal energy per unit mass, c4 = lam/q.
-__device__ void micro_slope(double U, double V, double lam, double q, double c4, const double* s,
-                            double* a) {
-  const double a4 = c4 * (2.0 * s[3] - 2.0 * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - 2.0 * q));
-  const double a3 = 2.0 * lam * (s[2] - V * s[0]) - V * a4;
-  const double a2 = 2.0 * lam * (s[1] - U * s[0]) - U * a4;
-  const double a1 = s[0] - U * a2 - V * a3 - a4 * (0.5 * (U * U + V * V) + q);
+template <typename T>
+__device__ void micro_slope(T U, T V, T lam, T q, T c4, const T* s, T* a) {
+  const T a4 = c4 * (T(2) * s[3] - T(2) * (U * s[1] + V * s[2]) + s[0] * (U * U + V * V - T(2) * q));
+  const T a3 = T(2) * lam * (s[2] - V * s[0]) - V * a4;
+  const T a2 = T(2) * lam * (s[1] - U * s[0]) - U * a4;
+  const T a1 = s[0] - U * a2 - V * a3 - a4 * (T(0.5) * (U * U + V * V) + q);
   a[0] = a1;
   a[1] = a2;
   a[2] = a3;
@@ -558,30 +561,41 @@ __host__ __device__ constexpr double inv_factorial(int n) {
 // by their Taylor series below x = 0.1 (no cancellation there).
 // Power series of the c_k in y = -x by Horner, NT terms: c4 = sum y^n/(n+1)!,
 // c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!, c3 = x sum y^n/(n+3)!,
-// c2 = -x sum (n+1) y^n/(n+3)!.
+// c2 = -x sum (n+1) y^n/(n+3)!.  The sums of c4, c5, c1 and those of c3, c2 are two
+// functions, so that the latter can run in FP32.
 template <int NT>
-__device__ __forceinline__ void time_series(double x, double& c1, double& c2, double& c3, double& c4,
-                                            double& c5) {
-  const double y = -x;
-  double h4 = 0.0, h5 = 0.0, h1 = 0.0, h3 = 0.0, h2 = 0.0;
+__device__ __forceinline__ void time_series_145(double y, double& h4, double& h5, double& h1) {
+  h4 = 0.0, h5 = 0.0, h1 = 0.0;
 #pragma unroll
   for (int n = NT - 1; n >= 0; n--) {
     h4 = h4 * y + inv_factorial(n + 1);
     h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
     h1 = h1 * y + inv_factorial(n + 2);
-    h3 = h3 * y + inv_factorial(n + 3);
-    h2 = h2 * y + (n + 1) * inv_factorial(n + 3);
   }
-  c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
+}
+template <int NT, typename T>
+__device__ __forceinline__ void time_series_23(T y, T& h3, T& h2) {
+  h3 = T(0), h2 = T(0);
+#pragma unroll
+  for (int n = NT - 1; n >= 0; n--) {
+    h3 = h3 * y + T(inv_factorial(n + 3));
+    h2 = h2 * y + T((n + 1) * inv_factorial(n + 3));
+  }
 }
 __device__ void time_weights(double dt, double x, double* Mt) {
   double c1, c2, c3, c4, c5;
-  if (x < 0.01) {
-    // 8 terms: the first one left out is below 1e-20 relative for x < 0.01
-    time_series<8>(x, c1, c2, c3, c4, c5);
-  } else if (x < 0.1) {
-    // 12 terms: the first one left out is below 1e-22 relative for x < 0.1
-    time_series<12>(x, c1, c2, c3, c4, c5);
+  if (x < 0.1) {
+    // 8 terms below x = 0.01, 12 below 0.1: the first term left out is below 1e-20 and
+    // 1e-22 relative
+    double h4, h5, h1, h3, h2;
+    if (x < 0.01) {
+      time_series_145<8>(-x, h4, h5, h1);
+      time_series_23<8>(-x, h3, h2);
+    } else {
+      time_series_145<12>(-x, h4, h5, h1);
+      time_series_23<12>(-x, h3, h2);
+    }
+    c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
   } else {
     const double e = exp(-x), em = -expm1(-x), ix = 1.0 / x;
     c4 = em * ix;
@@ -595,6 +609,36 @@ __device__ void time_weights(double dt, double x, double* Mt) {
   Mt[2] = dt * dt * c3;
   Mt[3] = dt * c4;
   Mt[4] = dt * dt * c5;
+}
+// The same weights with Mt2 and Mt3 (the weights of the micro-slope terms) in FP32.
+__device__ void time_weights_f32(double dt, double x, double* Mt, float& Mt2, float& Mt3) {
+  double c1, c4, c5;
+  float c2, c3;
+  if (x < 0.1) {
+    double h4, h5, h1;
+    float h3, h2;
+    if (x < 0.01) {
+      time_series_145<8>(-x, h4, h5, h1);
+      time_series_23<8>(-(float)x, h3, h2);
+    } else {
+      time_series_145<12>(-x, h4, h5, h1);
+      time_series_23<12>(-(float)x, h3, h2);
+    }
+    c4 = h4; c5 = h5; c1 = x * h1; c3 = (float)x * h3; c2 = -(float)x * h2;
+  } else {
+    const double e = exp(-x), em = -expm1(-x), ix = rcp_nr(x);
+    c4 = em * ix;
+    c1 = 1.0 - c4;
+    c5 = (c4 - e) * ix;
+    c3 = (float)(0.5 - c1 * ix);
+    c2 = (float)(c5 - c1 * ix);
+  }
+  const float fdt = (float)dt;
+  Mt[0] = dt * c1;
+  Mt[3] = dt * c4;
+  Mt[4] = dt * dt * c5;
+  Mt2 = fdt * fdt * c2;
+  Mt3 = fdt * fdt * c3;
 }
 
 // Polynomial of (a . psi) g / g_h reduced over the internal variable, in the face frame:
@@ -627,27 +671,27 @@ __device__ __forceinline__ void qcoef(double M1, double Mt2, double Mt3, const d
 // Maxwellian g_w = G_w exp(-lam |c - U_w|^2) enters as its exponent relative to g_ref's
 // (log2 units, formed in FP64), so that the walk forms g_w - g_ref without cancellation;
 // global velocity frame (y faces: un = v).
-__device__ void wall_face_f32(const Params& P, bool isx, double X2, double lam, double Ut, double G,
-                              int wall, FaceRecF* RF) {
+__device__ __forceinline__ void wall_face_f32(const Params& P, bool isx, double X2, double lam, double Ut, double G,
+                              int wall, FaceRecF& RF) {
   constexpr double kLog2e = 1.4426950408889634;
 #pragma unroll
   for (int sd = 0; sd < 2; sd++) {
 #pragma unroll
-    for (int c = 0; c < 8; c++) RF->Q[sd][c] = 0.f;
-    RF->K[sd][0] = RF->K[sd][1] = RF->K[sd][2] = 0.f;
-    RF->K[sd][3] = (float)X2;
+    for (int c = 0; c < 8; c++) RF.Q[sd][c] = 0.f;
+    RF.K[sd][0] = RF.K[sd][1] = RF.K[sd][2] = 0.f;
+    RF.K[sd][3] = (float)X2;
   }
   const double Ux = isx ? 0.0 : Ut, Vy = isx ? Ut : 0.0;
   // (a wall density rho_w <= 0 only arises from a state that is already unphysical; it is
   // clamped so that the record stays finite, and the FP64 W update reports the failure)
-  RF->E[0] = (float)((log2(fmax(G, 1e-300)) - lam * (Ux * Ux + Vy * Vy) * kLog2e) - P.ref_E[0]);
-  RF->E[1] = (float)(2.0 * lam * Ux * kLog2e - P.ref_E[1]);
-  RF->E[2] = (float)(2.0 * lam * Vy * kLog2e - P.ref_E[2]);
-  RF->E[3] = (float)(-lam * kLog2e - P.ref_E[3]);
-  RF->Mt4 = (float)P.dt;
-  RF->nMt5 = 0.f;
-  RF->wall = (float)wall;
-  RF->gdt = (float)P.dt;
+  RF.E[0] = (float)((log2(fmax(G, 1e-300)) - lam * (Ux * Ux + Vy * Vy) * kLog2e) - P.ref_E[0]);
+  RF.E[1] = (float)(2.0 * lam * Ux * kLog2e - P.ref_E[1]);
+  RF.E[2] = (float)(2.0 * lam * Vy * kLog2e - P.ref_E[2]);
+  RF.E[3] = (float)(-lam * kLog2e - P.ref_E[3]);
+  RF.Mt4 = (float)P.dt;
+  RF.nMt5 = 0.f;
+  RF.wall = (float)wall;
+  RF.gdt = (float)P.dt;
 }
 
 // One UGKS interface in the face frame (un, ut): inputs are the interface sums (S1, S7)
@@ -655,7 +699,7 @@ __device__ void wall_face_f32(const Params& P, bool isx, double X2, double lam, 
 // micro-flux record.
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
                           const double* Ss, const double* WL, const double* WR, double tdelta,
-                          bool isx, double* F, FaceRec& R, FaceRecF* RF) {
+                          bool isx, double* F, FaceRec& R) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], irho = 1.0 / rho, U = W0[1] * irho, V = W0[2] * irho;
@@ -686,7 +730,7 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   micro_slope(U, V, lam, q, c4, sL, aL);
   micro_slope(U, V, lam, q, c4, sR, aR);
   micro_slope(U, V, lam, q, c4, sT, b);
-  APsi tL, tR, tb, tA;
+  APsi<double> tL, tR, tb, tA;
   apsi_prep(Mv, X2, 0, aL, tL);
   apsi_prep(Mv, X2, 0, aR, tR);
   apsi_prep(Mv, X2, 1, b, tb);
@@ -716,100 +760,6 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   R.Mt5 = Mt[4];
   R.bfac = X2;
   R.wall = 0;
-#ifdef UGKS_X_REC64
-  if (RF) {
-    constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
-    const double kap = 0.5 * X4m;
-    double pa[4], pb[4], pA[4], Qh[8];
-    shape_h(b, X2, pb);
-    shape_h(A, X2, pA);
-#pragma unroll
-    for (int sd = 0; sd < 2; sd++) {
-      const double* as = sd == 0 ? aL : aR;
-      shape_h(as, X2, pa);
-      qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, Qh);
-#pragma unroll
-      for (int c = 0; c < 8; c++) RF->Q[sd][c] = (float)(R.G * (isx ? Qh[c] : Qh[py[c]]));
-      const double k0 = kap * Mt[2] * A[3], kn = kap * Mt[1] * as[3], kt = kap * Mt[1] * b[3];
-      RF->K[sd][0] = (float)(R.G * k0);
-      RF->K[sd][1] = (float)(R.G * (isx ? kn : kt));
-      RF->K[sd][2] = (float)(R.G * (isx ? kt : kn));
-      RF->K[sd][3] = (float)X2;
-    }
-    constexpr double kLog2e = 1.4426950408889634;
-    const double Ux = isx ? U : V, Vy = isx ? V : U;
-    RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
-    RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
-    RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
-    RF->E[3] = (float)(-lam * kLog2e);
-    RF->Mt4 = (float)Mt[3];
-    RF->nMt5 = (float)(-Mt[4]);
-    RF->wall = 0.f;
-    RF->gdt = 0.f;
-    return;
-  }
-#endif
-  if (RF) {
-    // FP32 record: its coefficients are stored in FP32, so they are formed in FP32 from the
-    // FP64 slopes, time weights and amplitude (S6/S8 coefficients, global frame)
-    float fa[2][4], fb[4], fA[4];
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      fa[0][c] = (float)aL[c];
-      fa[1][c] = (float)aR[c];
-      fb[c] = (float)b[c];
-      fA[c] = (float)A[c];
-    }
-    const float fX2 = (float)X2, fG = (float)R.G, fM1 = (float)Mt[0], fM2 = (float)Mt[1];
-    const float fM3 = (float)Mt[2];
-    const float kap = (float)(0.5 * X4m);  // (X4 - X2^2)/2 = K/(4 lam^2)
-    // shape polynomial of (a . psi) g / g_h reduced over the internal variable, face frame:
-    // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2)
-    auto shape = [&](const float* a4, float* o) {
-      o[0] = fmaf(0.5f * a4[3], fX2, a4[0]);
-      o[1] = a4[1];
-      o[2] = a4[2];
-      o[3] = 0.5f * a4[3];
-    };
-    float pb[4], pA[4];
-    shape(fb, pb);
-    shape(fA, pA);
-    constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
-#pragma unroll
-    for (int sd = 0; sd < 2; sd++) {
-      float pa[4], Qf[8];
-      shape(fa[sd], pa);
-      // Q_h on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2)
-      Qf[0] = fmaf(fM3, pA[0], fM1);
-      Qf[1] = fmaf(fM3, pA[1], fM2 * pa[0]);
-      Qf[2] = fmaf(fM3, pA[2], fM2 * pb[0]);
-      Qf[3] = fmaf(fM3, pA[3], fM2 * pa[1]);
-      Qf[4] = fM2 * (pa[2] + pb[1]);
-      Qf[5] = fmaf(fM3, pA[3], fM2 * pb[2]);
-      Qf[6] = fM2 * pa[3];
-      Qf[7] = fM2 * pb[3];
-#pragma unroll
-      for (int c = 0; c < 8; c++) RF->Q[sd][c] = fG * (isx ? Qf[c] : Qf[py[c]]);
-      // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
-      // Mt2 un a4 + Mt2 ut b4)
-      const float k0 = fG * kap * fM3 * fA[3], kn = fG * kap * fM2 * fa[sd][3], kt = fG * kap * fM2 * fb[3];
-      RF->K[sd][0] = k0;
-      RF->K[sd][1] = isx ? kn : kt;
-      RF->K[sd][2] = isx ? kt : kn;
-      RF->K[sd][3] = fX2;
-    }
-    constexpr double kLog2e = 1.4426950408889634;
-    const double Ux = isx ? U : V, Vy = isx ? V : U;
-    RF->E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
-    RF->E[1] = (float)(2.0 * lam * Ux * kLog2e);
-    RF->E[2] = (float)(2.0 * lam * Vy * kLog2e);
-    RF->E[3] = (float)(-lam * kLog2e);
-    RF->Mt4 = (float)Mt[3];
-    RF->nMt5 = (float)(-Mt[4]);
-    RF->wall = 0.f;
-    RF->gdt = 0.f;
-    return;
-  }
   // S6/S8 coefficients (FP64 record)
   double pa[4], pb[4], pA[4];
   for (int sd = 0; sd < 2; sd++) {
@@ -823,6 +773,128 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     shape_b(A, X2, X4, pA);
     qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
   }
+}
+
+// The same interface for the FP32-f form, whose walk consumes the micro slopes, time weights
+// and amplitude in FP32. The terms of the macroscopic flux that are first order in dt
+// (Mt1 rho <un psi> over the full range, Mt4 S_f, Mt5 S_sigma) and the Maxwellian's exponent
+// are formed in FP64; the terms that carry the micro slopes a_L, a_R, b, A (weights Mt2 and
+// Mt3, second order in dt; relative to the first-order terms they are
+// O(min(dt, tau) |grad W| / W), and the slopes are differences of FP64 W formed in FP64) are
+// formed in FP32 with the half-range moments they need. The FP32 rounding of those terms
+// is below 1e-7 of terms that are themselves small against the flux, and GB300 executes
+// FP64 at 1/64 of the FP32 rate.
+__device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St, const double* Sf,
+                              const double* Ss, const double* WL, const double* WR, double tdelta,
+                              bool isx, double* F, double& Mt4, FaceRecF& RF) {
+  const int K = P.K;
+  // S2: interface primitive variables (FP64)
+  const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
+  const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) * irho * P.inv_kp2;  // 1/(4 lam)
+  const double lam = 0.25 * rcp_nr(ilam4);
+  const double h = 2.0 * ilam4;  // 1/(2 lam)
+  const double rl = rsqrt(lam);
+  const double X2 = 2.0 * K * ilam4;
+  // S3: collision time and Mt1..Mt5 (FP64)
+  const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
+  double Mt[5];
+  float fM2, fM3;
+  time_weights_f32(P.dt, x, Mt, fM2, fM3);
+  // S5, first-order part: rho Mt1 <un psi> over the full range (FP64)
+  double Mu[7], Mv[7], p1[4];
+  gauss_moments7_full(U, h, Mu);
+  gauss_moments7_full(V, h, Mv);
+  psi_mom(Mu, Mv, X2, 1, 0, p1);
+  // S2, S4, S5 second-order part (FP32): half-range moments, micro slopes, compatibility
+  const float fU = (float)U, fV = (float)V, flam = (float)lam, fh = (float)h;
+  const float fX2 = (float)X2, fX4m = (float)(K * 8.0 * ilam4 * ilam4);  // X4 - X2^2
+  float fMu[7], fMup[7], fMun[7], fMv[7];
+  gauss_moments7(fU, flam, fh, (float)rl, fMu, fMup, fMun);
+  gauss_moments7_full(fV, fh, fMv);
+  const float q = (float)((K + 2) * ilam4), c4 = (float)(4.0 * lam * lam * P.inv_kp2);
+  const float inv = (float)(irho * tdelta), firho = (float)irho;
+  float sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    sL[c] = (float)(W0[c] - WL[c]) * inv;
+    sR[c] = (float)(WR[c] - W0[c]) * inv;
+    sT[c] = (float)St[c] * firho;
+  }
+  micro_slope(fU, fV, flam, q, c4, sL, aL);
+  micro_slope(fU, fV, flam, q, c4, sR, aR);
+  micro_slope(fU, fV, flam, q, c4, sT, b);
+  APsi<float> tL, tR, tb, tA;
+  apsi_prep(fMv, fX2, 0, aL, tL);
+  apsi_prep(fMv, fX2, 0, aR, tR);
+  apsi_prep(fMv, fX2, 1, b, tb);
+  float t1[4], t2[4], t3[4], t4[4];
+  apsi_eval(tL, fMup, fX2, fX4m, 1, t1);
+  apsi_eval(tR, fMun, fX2, fX4m, 1, t2);
+  apsi_eval(tb, fMu, fX2, fX4m, 0, t3);
+#pragma unroll
+  for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
+  micro_slope(fU, fV, flam, q, c4, sA, A);
+  apsi_prep(fMv, fX2, 0, A, tA);
+  apsi_eval(tL, fMup, fX2, fX4m, 2, t1);
+  apsi_eval(tR, fMun, fX2, fX4m, 2, t2);
+  apsi_eval(tb, fMu, fX2, fX4m, 1, t3);
+  apsi_eval(tA, fMu, fX2, fX4m, 1, t4);
+  const float fM1 = (float)Mt[0];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const float second = fM2 * (t1[c] + t2[c] + t3[c]) + fM3 * t4[c];
+    F[c] = rho * (Mt[0] * p1[c] + (double)second) + Mt[3] * Sf[c] - Mt[4] * Ss[c];
+  }
+  Mt4 = Mt[3];
+  // FP32 record of the micro flux (S6/S8 coefficients, global frame)
+  const float fG = (float)(rho * lam / kPi);
+  const float kap = 0.5f * fX4m;  // (X4 - X2^2)/2 = K/(4 lam^2)
+  // shape polynomial of (a . psi) g / g_h reduced over the internal variable, face frame:
+  // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2)
+  auto shape = [&](const float* a4, float* o) {
+    o[0] = fmaf(0.5f * a4[3], fX2, a4[0]);
+    o[1] = a4[1];
+    o[2] = a4[2];
+    o[3] = 0.5f * a4[3];
+  };
+  float pb[4], pA[4];
+  shape(b, pb);
+  shape(A, pA);
+  constexpr int py[8] = {0, 2, 1, 5, 4, 3, 7, 6};
+#pragma unroll
+  for (int sd = 0; sd < 2; sd++) {
+    const float* as = sd == 0 ? aL : aR;
+    float pa[4], Qf[8];
+    shape(as, pa);
+    // Q_h on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2)
+    Qf[0] = fmaf(fM3, pA[0], fM1);
+    Qf[1] = fmaf(fM3, pA[1], fM2 * pa[0]);
+    Qf[2] = fmaf(fM3, pA[2], fM2 * pb[0]);
+    Qf[3] = fmaf(fM3, pA[3], fM2 * pa[1]);
+    Qf[4] = fM2 * (pa[2] + pb[1]);
+    Qf[5] = fmaf(fM3, pA[3], fM2 * pb[2]);
+    Qf[6] = fM2 * pa[3];
+    Qf[7] = fM2 * pb[3];
+#pragma unroll
+    for (int c = 0; c < 8; c++) RF.Q[sd][c] = fG * (isx ? Qf[c] : Qf[py[c]]);
+    // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
+    // Mt2 un a4 + Mt2 ut b4)
+    const float k0 = fG * kap * fM3 * A[3], kn = fG * kap * fM2 * as[3], kt = fG * kap * fM2 * b[3];
+    RF.K[sd][0] = k0;
+    RF.K[sd][1] = isx ? kn : kt;
+    RF.K[sd][2] = isx ? kt : kn;
+    RF.K[sd][3] = fX2;
+  }
+  constexpr double kLog2e = 1.4426950408889634;
+  const double Ux = isx ? U : V, Vy = isx ? V : U;
+  RF.E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
+  RF.E[1] = (float)(2.0 * lam * Ux * kLog2e);
+  RF.E[2] = (float)(2.0 * lam * Vy * kLog2e);
+  RF.E[3] = (float)(-lam * kLog2e);
+  RF.Mt4 = (float)Mt[3];
+  RF.nMt5 = (float)(-Mt[4]);
+  RF.wall = 0.f;
+  RF.gdt = 0.f;
 }
 
 template <typename S>
@@ -861,8 +933,8 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     if (j == ny - 1 && P.bc_kind[3] == 1) { wall = 2; side = 3; }
   }
   FaceRec R;
-  FaceRecF RFv;
-  FaceRecF* RF = fxf ? &RFv : nullptr;
+  FaceRecF RF;
+  const bool f32 = fxf != nullptr;
   double F[4];
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
@@ -888,9 +960,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     R.Mt5 = 0.0;
     R.bfac = P.K / (2.0 * lam);
     R.wall = wall;
-    if (RF) {
-      wall_face_f32(P, isx, R.bfac, lam, R.Ut, R.G, wall, RF);
-    }
+    if (f32) wall_face_f32(P, isx, R.bfac, lam, R.Ut, R.G, wall, RF);
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
     const S* sL = sums + (size_t)cL * kNSum + oL;
@@ -908,17 +978,20 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
-    face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, RF);
+    if (f32)
+      face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
+    else
+      face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = (c == 1 || c == 2) && !isx ? Fr[3 - c] : Fr[c];
   }
   mt4[t] = R.Mt4;
   if (isx) {
-    if (RF) fxf[t] = *RF;
+    if (f32) fxf[t] = RF;
     else fxr[t] = R;
     for (int c = 0; c < 4; c++) Fx[4 * (size_t)t + c] = F[c];
   } else {
-    if (RF) fyf[t - nfx] = *RF;
+    if (f32) fyf[t - nfx] = RF;
     else fyr[t - nfx] = R;
     for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
   }
@@ -962,13 +1035,15 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
     }
     const int K = P.K;
     // 1/lam = 4 (rho E - rho |U|^2 / 2) / ((K + 2) rho); dt / (2 tau) = dt rho / (4 mu_ref
-    // lam^(1 - omega)), for omega = 1/2: dt rho / (4 mu_ref sqrt(lam))
-    const double rn = Wn[0], irn = 1.0 / rn, Un = Wn[1] * irn, Vn = Wn[2] * irn;
+    // lam^(1 - omega)), for omega = 1/2: dt rho / (4 mu_ref sqrt(lam)).  Reciprocals from
+    // the refined estimate (a few ulp; a zero or non-finite input gives a non-finite
+    // result, which the failure check below reports as an IEEE divide's would).
+    const double rn = Wn[0], irn = rcp_nr(rn), Un = Wn[1] * irn, Vn = Wn[2] * irn;
     const double iln = 4.0 * (Wn[3] - 0.5 * rn * (Un * Un + Vn * Vn)) * irn * P.inv_kp2;
-    const double ln = 1.0 / iln;
-    const double r1 = W1[0], ir1 = 1.0 / r1, U1 = W1[1] * ir1, V1 = W1[2] * ir1;
+    const double ln = rcp_nr(iln);
+    const double r1 = W1[0], ir1 = rcp_nr(r1), U1 = W1[1] * ir1, V1 = W1[2] * ir1;
     const double il1 = 4.0 * (W1[3] - 0.5 * r1 * (U1 * U1 + V1 * V1)) * ir1 * P.inv_kp2;
-    const double l1 = 1.0 / il1;
+    const double l1 = rcp_nr(il1);
     if (!(r1 > 0.0) || !(l1 > 0.0) || !isfinite(l1) || !isfinite(U1) || !isfinite(V1))
       atomicOr(err, 1);
     CellRec R;
@@ -982,21 +1057,26 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       R.cg1 = P.dt / (2.0 * collision_time(P, r1, l1));
     }
     R.cf = 1.0 - R.cgn;
-    R.inv = 1.0 / (1.0 + R.cg1);
+    R.inv = rcp_nr(1.0 + R.cg1);
     if (crf) {
       const int nfx = (nx + 1) * P.ny;
       constexpr double kLog2e = 1.4426950408889634;
       const double refx = (mt4[xw] - mt4[xe]) * P.d_idx, refy = (mt4[nfx + ys] - mt4[nfx + yn]) * P.d_idy;
       CellRecF F;
-      // the amplitude enters the exponent; log2 in FP64 (an approximate FP32 log2 put
-      // ~1e-7 relative noise on g per cell, visible in rho V at Kn 0.01)
-      // exponents of g^n, g^{n+1} relative to those of g_ref (log2 units), in FP64
-      const double r0 = P.ref_E[0], r1 = P.ref_E[1], r2 = P.ref_E[2], r3 = P.ref_E[3];
-      F.dEn[0] = (float)((log2(R.Gn) - ln * (Un * Un + Vn * Vn) * kLog2e) - r0);
+      // exponents of g^n, g^{n+1} relative to those of g_ref (log2 units), in FP64 but for
+      // the amplitude's log2(G / G_ref) = log2(1 + d), d = G / G_ref - 1 formed in FP64 and
+      // log1p in FP32: its error is an ulp of a result that is small where G is near
+      // G_ref (an FP32 log2 of G itself put ~1e-7 relative noise on g per cell, visible in
+      // rho V at Kn 0.01)
+      constexpr float kLog2ef = 1.44269504f;
+      const double r0 = P.ref_E0u, r1 = P.ref_E[1], r2 = P.ref_E[2], r3 = P.ref_E[3];
+      const double ldn = (double)(log1pf((float)fma(R.Gn, P.ref_iG, -1.0)) * kLog2ef);
+      const double ld1 = (double)(log1pf((float)fma(R.G1, P.ref_iG, -1.0)) * kLog2ef);
+      F.dEn[0] = (float)((ldn - ln * (Un * Un + Vn * Vn) * kLog2e) - r0);
       F.dEn[1] = (float)(2.0 * ln * Un * kLog2e - r1);
       F.dEn[2] = (float)(2.0 * ln * Vn * kLog2e - r2);
       F.dEn[3] = (float)(-ln * kLog2e - r3);
-      F.dE1[0] = (float)((log2(R.G1) - l1 * (U1 * U1 + V1 * V1) * kLog2e) - r0);
+      F.dE1[0] = (float)((ld1 - l1 * (U1 * U1 + V1 * V1) * kLog2e) - r0);
       F.dE1[1] = (float)(2.0 * l1 * U1 * kLog2e - r1);
       F.dE1[2] = (float)(2.0 * l1 * V1 * kLog2e - r2);
       F.dE1[3] = (float)(-l1 * kLog2e - r3);
