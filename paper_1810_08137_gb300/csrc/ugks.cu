@@ -1106,6 +1106,8 @@ struct ugks_batch_ctx {
 namespace {
 
 constexpr size_t kBatchSumsSmem = sums_smem_bytes<float>();
+// dynamic shared memory of the batch kernel of phase p
+constexpr size_t phase_smem(int p) { return p == 2 ? kBatchSumsSmem : (p == 5 ? kStripSmem : 0); }
 
 ugks_status bfail(ugks_batch_ctx* b, ugks_status s, const std::string& m) {
   if (b) b->last_error = m;
@@ -1178,7 +1180,7 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
   kb_sums<<<b->grid[2], 128, kBatchSumsSmem, st>>>(b->d_slots, b->d_work);
   kb_faces<<<b->grid[3], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_cells<<<b->grid[4], 128, 0, st>>>(b->d_slots, b->d_work);
-  kb_strip<<<b->grid[5], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_strip<<<b->grid[5], 128, kStripSmem, st>>>(b->d_slots, b->d_work);
   kb_flip<<<1, 256, 0, st>>>(b->d_slots, b->d_work);
   return cudaGetLastError();
 }
@@ -1200,12 +1202,15 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   if ((e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem)) !=
       cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
+      cudaSuccess)
+    return e;
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
                               (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases; p++) {
     w.start[p][1] = phase_blocks(S, p);
     int nb = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, p == 2 ? kBatchSumsSmem : 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, phase_smem(p))) != cudaSuccess)
       return e;
     const int cap = (nb > 0 ? nb : 1) * sms;
     h->grid1[p] = w.start[p][1] < cap ? (w.start[p][1] > 0 ? w.start[p][1] : 1) : cap;
@@ -1227,7 +1232,7 @@ cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st) {
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   kb_cells<<<h->grid1[4], 128, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  kb_strip<<<h->grid1[5], 128, 0, st>>>(h->d_slot, h->d_work);
+  kb_strip<<<h->grid1[5], 128, kStripSmem, st>>>(h->d_slot, h->d_work);
   kb_flip<<<1, 32, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
@@ -1278,12 +1283,13 @@ ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_strea
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem);
   // persistent grids: resident blocks per SM x SMs
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
                               (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases && e == cudaSuccess; p++) {
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, p == 2 ? kBatchSumsSmem : 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, phase_smem(p));
     b->grid[p] = (nb > 0 ? nb : 1) * sms;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
 }
 
 // Update sweep: one warp per work item (strip, tile, velocity chunk).
-__global__ void __launch_bounds__(128, 2) kb_strip(const SlotDev* __restrict__ slots,
+__global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ slots,
                                                 const BatchWork* __restrict__ wk) {
-  __shared__ __align__(16) float4 ring[kWarpsPerBlock][kRing * kStripChunks];
+  extern __shared__ __align__(16) float4 strip_sm[];  // kStripSmem bytes
   const int warp = threadIdx.x >> 5;
   const int total = wk->start[5][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128, 2) kb_strip(const SlotDev* __restrict__ s
       // velocity chunks fastest: the warps of a block share the strip's records and halo
       const int bx = (it / nch) % ns, by = it / (nch * ns), ck = it % nch;
       strip_body_p<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
-                            bx, by, ck, ring[warp]);
+                            bx, by, ck, strip_sm + warp * kStripWarpF4);
     }
   }
 }

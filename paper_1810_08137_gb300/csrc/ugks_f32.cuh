@@ -33,6 +33,10 @@ __device__ __forceinline__ P4 ldp(const float4* p) {
   const float4 v = __ldg(p);
   return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
+__device__ __forceinline__ P4 ldp_s(const float4* p) {
+  const float4 v = *p;
+  return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
 __device__ __forceinline__ void stp(float4* p, const P4& v) { *p = make_float4(v.h.x, v.h.y, v.b.x, v.b.y); }
 __device__ __forceinline__ P4 add4(const P4& a, const P4& b) { return {add2(a.h, b.h), add2(a.b, b.b)}; }
 __device__ __forceinline__ P4 zero4() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
@@ -287,9 +291,14 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
 // -------------------------------------------------------------------------------------
 constexpr int kWalkRows = 64;  // default rows per walk tile
 constexpr int kStripW = 4;     // columns per strip
-constexpr int kRing = 3;       // rows of face and cell records staged in shared memory
+constexpr int kRing = 2;       // rows of face and cell records staged in shared memory
+constexpr int kFRing = 4;      // rows of f staged in shared memory: P, C, N and the next one
+constexpr int kFPos = kStripW + 3;  // walk positions of a staged f row: UU, U, strip, D
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
 constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
+// shared memory of one warp of the walk (float4): f ring, then record ring
+constexpr int kStripWarpF4 = kFRing * kFPos * 32 + kRing * kStripChunks;
+constexpr size_t kStripSmem = (size_t)kWarpsPerBlock * kStripWarpF4 * sizeof(float4);
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
@@ -396,7 +405,7 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
                                              const FaceRecF* __restrict__ fyr,
                                              const CellRecF* __restrict__ cr, int nchunk_neg,
                                              int rows, int bx, int by, int chunk,
-                                             float4* __restrict__ ring) {
+                                             float4* __restrict__ sm) {
   const int lane = threadIdx.x & 31;
   const int nx = P.nx, ny = P.ny, nu = P.nu, fs = P.fs;
   const int i0 = bx * W;
@@ -452,45 +461,52 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
   const float4* pr_ = f + base;                        // (position 0, row jfirst)
   float4* pw = fo + base;
 
-  // rows jfirst - sv (Pv), jfirst (Cv), jfirst + sv (Nv) at positions -1..W-1
-  P4 Pv[W + 1], Cv[W + 1], Nv[W + 1];
-#pragma unroll
-  for (int p = -1; p < W; p++) {
-    Pv[p + 1] = ldp(pr_ - rs + col(p));
-    Cv[p + 1] = ldp(pr_ + col(p));
-    Nv[p + 1] = ldp(pr_ + rs + col(p));
-  }
-  P4 cUU = ldp(pr_ + col(-2)), cD = ldp(pr_ + col(W));
-
   // prologue: flux through the y-face between the halo row jp = jfirst - sv and jfirst
+  // (read from global memory: once per walk)
   P4 Xiy[W];
   {
     const int jp = jfirst - sv;
     const FaceRecF* RY = fyr + (long)(sv > 0 ? jfirst : jfirst + 1) * nx + ib;
     const bool zp = (jp < 0 && pS) || (jp >= ny && pN);
-    const P4 dp = ldp(pr_ - rs + col(W));
     if (RY->wall != 0.f) {
 #pragma unroll
       for (int t = 0; t < W; t++)
         if (t < wc) Xiy[t] = wall_p(RY + su * t, L);
     } else {
+      const float4* rp = pr_ - rs;                     // row jp
+      P4 a = ldp(rp + col(-1)), c = ldp(rp + col(0));
 #pragma unroll
       for (int t = 0; t < W; t++) {
         if (t < wc) {
-          const P4 pp = ldp(pr_ - 2 * rs + col(t));
-          const P4 c = Pv[t + 1];
-          P4 rx = vl4(Pv[t], c, t + 1 < W ? Pv[t + 2] : dp);
-          P4 ry = vl4(pp, c, Cv[t + 1]);
+          const P4 b = ldp(rp + col(t + 1));
+          P4 rx = vl4(a, c, b);
+          P4 ry = vl4(ldp(rp - rs + col(t)), c, ldp(pr_ + col(t)));
           if (zp) rx = ry = zero4();
           Xiy[t] = face_p(RY + su * t, yside, L, add4(c, ry), slope_d(L, rx, ry));
+          a = c;
+          c = b;
         }
       }
     }
   }
 
-  // face and cell records of a row, staged through a ring of kRing rows in shared memory:
-  // [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side][cells i0..i0+wc-1]
+  // f rows q = 0 .. nsteps + 1 (row jfirst + (q - 1) sv) pass through a ring of kFRing rows
+  // in shared memory, each at the walk positions -2 .. W (UU, U, strip, D); a lane copies
+  // and reads only its own slot's column.  The face and cell records of a row pass through a
+  // ring of kRing rows: [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side]
+  // [cells i0..i0+wc-1], read by every lane.  Row st's records and f row st + 2 form one
+  // commit group, issued one row ahead.
+  float4* fring = sm;
+  float4* ring = sm + kFRing * kFPos * 32;
   constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
+  auto stage_f = [&](int q) {
+    if (q <= nsteps + 1) {
+      const float4* src = pr_ + (long)(q - 1) * rs;
+      float4* dst = fring + (q % kFRing) * (kFPos * 32) + lane;
+#pragma unroll
+      for (int p = -2; p <= W; p++) cp_async16_cg(dst + (p + 2) * 32, src + col(p));
+    }
+  };
   auto stage = [&](int st) {
     if (st < nsteps) {
       const int j = jfirst + sv * st;
@@ -508,64 +524,60 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
         }
       }
     }
+    stage_f(st + 2);
     cp_async_commit();
   };
-  __syncwarp();                      // the ring's previous contents are no longer read
-#pragma unroll
-  for (int st = 0; st < kRing - 1; st++) stage(st);
+  __syncwarp();                      // the rings' previous contents are no longer read
+  stage_f(0);
+  stage_f(1);
+  stage(0);
   // local record index of walk position t (-1 = U's face for x) within the staged row
   const int xl0 = su > 0 ? 0 : wc;   // x-face between U and position 0
   auto cl = [&](int t) { return su > 0 ? t : wc - 1 - t; };
   for (int st = 0; st < nsteps; st++) {
-    __syncwarp();                    // every lane is done with the slot refilled next
-    stage(st + kRing - 1);
-    // loads for the next row (rows up to jlast + 2 sv lie in the ghost ring)
-    P4 NN[W + 1];
-#pragma unroll
-    for (int p = -1; p < W; p++) NN[p + 1] = ldp(pr_ + 2 * rs + col(p));
-    const P4 nUU = ldp(pr_ + rs + col(-2)), nD = ldp(pr_ + rs + col(W));
-    cp_async_wait<kRing - 1>();
+    __syncwarp();                    // every lane is done with the slots refilled next
+    stage(st + 1);
+    cp_async_wait<1>();
     __syncwarp();
     const float4* row = ring + (st % kRing) * kStripChunks;
     const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
     const FaceRecF* RY = reinterpret_cast<const FaceRecF*>(row + oY);
     const CellRecF* CC = reinterpret_cast<const CellRecF*>(row + oC);
+    // rows P (st), C (st + 1), N (st + 2) of the f ring, at walk position 0
+    const float4* fP = fring + (st % kFRing) * (kFPos * 32) + 64 + lane;
+    const float4* fC = fring + ((st + 1) % kFRing) * (kFPos * 32) + 64 + lane;
+    const float4* fN = fring + ((st + 2) % kFRing) * (kFPos * 32) + 64 + lane;
+    auto at = [](const float4* r, int p) { return ldp_s(r + p * 32); };
 
     // flux into position 0 out of U (or off the wall)
+    P4 cm = at(fC, -1), c0 = at(fC, 0);
     P4 Xix;
     const FaceRecF* RXi = RX + xl0;
     if (RXi->wall != 0.f) {
       Xix = wall_p(RXi, L);
     } else {
-      P4 rx = vl4(cUU, Cv[0], Cv[1]);
-      P4 ry = vl4(Pv[0], Cv[0], Nv[0]);
+      P4 rx = vl4(at(fC, -2), cm, c0);
+      P4 ry = vl4(at(fP, -1), cm, at(fN, -1));
       if (zu) rx = ry = zero4();
-      Xix = face_p(RXi, xside, L, add4(Cv[0], rx), slope_d(L, rx, ry));
+      Xix = face_p(RXi, xside, L, add4(cm, rx), slope_d(L, rx, ry));
     }
 #pragma unroll
     for (int t = 0; t < W; t++) {
       if (t < wc) {
-        const P4 c = Cv[t + 1];
-        const P4 rx = vl4(Cv[t], c, t + 1 < W ? Cv[t + 2] : cD);
-        const P4 ry = vl4(Pv[t + 1], c, Nv[t + 1]);
+        const P4 cn = at(fC, t + 1);
+        const P4 rx = vl4(cm, c0, cn);
+        const P4 ry = vl4(at(fP, t), c0, at(fN, t));
         const P4 d = slope_d(L, rx, ry);
-        const P4 Xox = face_p(RXi + su * (t + 1), xside, L, add4(c, rx), d);
-        const P4 Xoy = face_p(RY + cl(t), yside, L, add4(c, ry), d);
-        const P4 o = collide_p(CC + cl(t), L, c, Xix, Xox, Xiy[t], Xoy);
+        const P4 Xox = face_p(RXi + su * (t + 1), xside, L, add4(c0, rx), d);
+        const P4 Xoy = face_p(RY + cl(t), yside, L, add4(c0, ry), d);
+        const P4 o = collide_p(CC + cl(t), L, c0, Xix, Xox, Xiy[t], Xoy);
         if (act) stp(pw + col(t), o);
         Xix = Xox;
         Xiy[t] = Xoy;
+        cm = c0;
+        c0 = cn;
       }
     }
-#pragma unroll
-    for (int p = 0; p <= W; p++) {
-      Pv[p] = Cv[p];
-      Cv[p] = Nv[p];
-      Nv[p] = NN[p];
-    }
-    cUU = nUU;
-    cD = nD;
-    pr_ += rs;
     pw += rs;
   }
   cp_async_wait<0>();

@@ -74,6 +74,11 @@ __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gm) : "memory");
 }
+// The same, cached in L2 only (data read once by this warp).
+__device__ __forceinline__ void cp_async16_cg(void* sm, const void* gm) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gm) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
