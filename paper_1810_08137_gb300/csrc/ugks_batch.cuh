@@ -138,8 +138,14 @@ __global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ s
       const int c = S.cur;
       // velocity chunks fastest: the warps of a block share the strip's records and halo
       const int bx = (it / nch) % ns, by = it / (nch * ns), ck = it % nch;
-      strip_body_p<kStripW>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg, S.walk_rows,
-                            bx, by, ck, strip_sm + warp * kStripWarpF4);
+      // full strips (all but the last of a row when kStripW does not divide nx) with the
+      // strip width known at compile time
+      if ((bx + 1) * kStripW <= S.P.nx)
+        strip_body_p<kStripW, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                    S.walk_rows, bx, by, ck, strip_sm + warp * kStripWarpF4);
+      else
+        strip_body_p<kStripW, false>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                     S.walk_rows, bx, by, ck, strip_sm + warp * kStripWarpF4);
     }
   }
 }

@@ -207,29 +207,31 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
 #pragma unroll
       for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
     };
-    // row pairs in the order v >= 0 half, then v < 0 half; the first v >= 0 pair holds the
-    // v = 0 row (if any) as its first row
+    // the v >= 0 half (pairs pn .. pa - 1), then the v < 0 half (pairs 0 .. pn - 1); the first
+    // v >= 0 pair holds the v = 0 row (if any) as its first row
     zero();
     float s0h = 0.f, s0b = 0.f, s0xh = 0.f, s0xb = 0.f, s0yh = 0.f, s0yb = 0.f;
-#pragma unroll 1
-    for (int t = 0; t < pa; t++) {
-      if (t == pa - pn) {  // first v < 0 pair: close the v >= 0 half
-        close(1.f, wsum + kSumN);
-        zero();
-        a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
-      }
+    if (pa > pn) {
       P4 c, rx, ry;
-      pair(t < pa - pn ? pn + t : t - (pa - pn), c, rx, ry);
-      if (t == 0 && v0) {  // the v = 0 row's half weight for the v < 0 half
+      pair(pn, c, rx, ry);
+      if (v0) {  // the v = 0 row's half weight for the v < 0 half
         const float hw = __ldg(&wt[3 * pn].x);
         s0h = hw * c.h.x; s0b = hw * c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
         s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
       }
     }
-    if (pn == 0) {  // no v < 0 half: the loop did not close the v >= 0 half
-      close(1.f, wsum + kSumN);
-      zero();
-      a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
+#pragma unroll 1
+    for (int pr = pn + 1; pr < pa; pr++) {
+      P4 c, rx, ry;
+      pair(pr, c, rx, ry);
+    }
+    close(1.f, wsum + kSumN);
+    zero();
+    a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
+#pragma unroll 1
+    for (int pr = 0; pr < pn; pr++) {
+      P4 c, rx, ry;
+      pair(pr, c, rx, ry);
     }
     close(-1.f, wsum + kSumS);
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
@@ -399,7 +401,7 @@ __device__ __forceinline__ P4 slope_d(const PairLane& L, const P4& rx, const P4&
   return {fma2(f2(L.cu), rx.h, mul2(L.cv, ry.h)), fma2(f2(L.cu), rx.b, mul2(L.cv, ry.b))};
 }
 
-template <int W>
+template <int W, bool FULL>
 __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __restrict__ f,
                                              float4* __restrict__ fo, const FaceRecF* __restrict__ fxr,
                                              const FaceRecF* __restrict__ fyr,
@@ -409,7 +411,7 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
   const int lane = threadIdx.x & 31;
   const int nx = P.nx, ny = P.ny, nu = P.nu, fs = P.fs;
   const int i0 = bx * W;
-  const int wc = min(W, nx - i0);
+  const int wc = FULL ? W : min(W, nx - i0);         // columns of this strip (FULL: W)
   const bool vpos = chunk >= nchunk_neg;
   const int sn = P.pr_neg * nu;                        // slots of the v < 0 half
   const int s = vpos ? sn + (chunk - nchunk_neg) * 32 + lane : chunk * 32 + lane;
