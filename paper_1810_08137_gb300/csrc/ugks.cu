@@ -748,6 +748,12 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             P.refsum[sd][kOffSf + c] += hs[sd] * w * un[sd] * psi[c];
           }
       }
+    for (int c = 0; c < 4; c++) {
+      P.refpair[0][c] = P.refsum[kSumE / 16][kOffW0 + c] + P.refsum[kSumW / 16][kOffW0 + c];
+      P.refpair[0][4 + c] = P.refsum[kSumE / 16][kOffSf + c] + P.refsum[kSumW / 16][kOffSf + c];
+      P.refpair[1][c] = P.refsum[kSumN / 16][kOffW0 + c] + P.refsum[kSumS / 16][kOffW0 + c];
+      P.refpair[1][4 + c] = P.refsum[kSumN / 16][kOffSf + c] + P.refsum[kSumS / 16][kOffSf + c];
+    }
     // g_ref per slot of the paired-row layout (h, h', b, b')
     gref_host.resize((size_t)P.fs);
     for (int pr = 0; pr < P.pr_all; pr++)

@@ -105,6 +105,8 @@ struct Params {
   double ref_iG, ref_E0u;  // 1 / ref_G; ref_E[0] - log2(ref_G)
   double refsum[4][16];   // per side E, W, N, S (order of kSumE..kSumS / 16): half-range
                           // sums of g_ref in the W0 and Sf slots, zero in St and Ss
+  double refpair[2][8];   // refsum of both sides of a face: x faces (E + W), y faces (N + S);
+                          // W0 slots then Sf slots
   // FP32 form, paired-row layout (see ugks_f32.cuh): pr_neg row pairs with v < 0, pr_all
   // row pairs in total, fs = pr_all * nu float4 slots per cell
   int pr_neg, pr_all, fs;

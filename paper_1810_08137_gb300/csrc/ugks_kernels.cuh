@@ -578,6 +578,25 @@ __device__ __forceinline__ void time_series_145(double y, double& h4, double& h5
     h1 = h1 * y + inv_factorial(n + 2);
   }
 }
+template <int NT>
+__device__ __forceinline__ void time_series_14(double y, double& h4, double& h1) {
+  h4 = 0.0, h1 = 0.0;
+#pragma unroll
+  for (int n = NT - 1; n >= 0; n--) {
+    h4 = h4 * y + inv_factorial(n + 1);
+    h1 = h1 * y + inv_factorial(n + 2);
+  }
+}
+template <int NT>
+__device__ __forceinline__ void time_series_235(float y, float& h3, float& h2, float& h5) {
+  h3 = 0.f, h2 = 0.f, h5 = 0.f;
+#pragma unroll
+  for (int n = NT - 1; n >= 0; n--) {
+    h3 = h3 * y + (float)inv_factorial(n + 3);
+    h2 = h2 * y + (float)((n + 1) * inv_factorial(n + 3));
+    h5 = h5 * y + (float)((n + 1) * inv_factorial(n + 2));
+  }
+}
 template <int NT, typename T>
 __device__ __forceinline__ void time_series_23(T y, T& h3, T& h2) {
   h3 = T(0), h2 = T(0);
@@ -615,35 +634,37 @@ __device__ void time_weights(double dt, double x, double* Mt) {
   Mt[3] = dt * c4;
   Mt[4] = dt * dt * c5;
 }
-// The same weights with Mt2 and Mt3 (the weights of the micro-slope terms) in FP32.
-__device__ void time_weights_f32(double dt, double x, double* Mt, float& Mt2, float& Mt3) {
-  double c1, c4, c5;
-  float c2, c3;
+// The same weights with Mt2, Mt3 and Mt5 (the weights of the terms that carry slopes:
+// second order in dt) in FP32; Mt1 and Mt4 in FP64.
+__device__ void time_weights_f32(double dt, double x, double* Mt, float& Mt2, float& Mt3, float& Mt5) {
+  double c1, c4;
+  float c2, c3, c5;
   if (x < 0.1) {
-    double h4, h5, h1;
-    float h3, h2;
+    double h4, h1;
+    float h5, h3, h2;
     if (x < 0.01) {
-      time_series_145<8>(-x, h4, h5, h1);
-      time_series_23<8>(-(float)x, h3, h2);
+      time_series_14<8>(-x, h4, h1);
+      time_series_235<8>(-(float)x, h3, h2, h5);
     } else {
-      time_series_145<12>(-x, h4, h5, h1);
-      time_series_23<12>(-(float)x, h3, h2);
+      time_series_14<12>(-x, h4, h1);
+      time_series_235<12>(-(float)x, h3, h2, h5);
     }
-    c4 = h4; c5 = h5; c1 = x * h1; c3 = (float)x * h3; c2 = -(float)x * h2;
+    c4 = h4; c1 = x * h1; c5 = h5; c3 = (float)x * h3; c2 = -(float)x * h2;
   } else {
     const double e = exp(-x), em = -expm1(-x), ix = rcp_nr(x);
     c4 = em * ix;
     c1 = 1.0 - c4;
-    c5 = (c4 - e) * ix;
+    const double d5 = (c4 - e) * ix;
+    c5 = (float)d5;
     c3 = (float)(0.5 - c1 * ix);
-    c2 = (float)(c5 - c1 * ix);
+    c2 = (float)(d5 - c1 * ix);
   }
   const float fdt = (float)dt;
   Mt[0] = dt * c1;
   Mt[3] = dt * c4;
-  Mt[4] = dt * dt * c5;
   Mt2 = fdt * fdt * c2;
   Mt3 = fdt * fdt * c3;
+  Mt5 = fdt * fdt * c5;
 }
 
 // Polynomial of (a . psi) g / g_h reduced over the internal variable, in the face frame:
@@ -789,9 +810,10 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
 // formed in FP32 with the half-range moments they need. The FP32 rounding of those terms
 // is below 1e-7 of terms that are themselves small against the flux, and GB300 executes
 // FP64 at 1/64 of the FP32 rate.
-__device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St, const double* Sf,
-                              const double* Ss, const double* WL, const double* WR, double tdelta,
-                              bool isx, double* F, double& Mt4, FaceRecF& RF) {
+__device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const float* St,
+                                              const double* Sf, const float* Ss, const double* WL,
+                                              const double* WR, double tdelta, bool isx, double* F,
+                                              double& Mt4, FaceRecF& RF) {
   const int K = P.K;
   // S2: interface primitive variables (FP64)
   const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
@@ -803,8 +825,8 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   // S3: collision time and Mt1..Mt5 (FP64)
   const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
   double Mt[5];
-  float fM2, fM3;
-  time_weights_f32(P.dt, x, Mt, fM2, fM3);
+  float fM2, fM3, fM5;
+  time_weights_f32(P.dt, x, Mt, fM2, fM3, fM5);
   // S5, first-order part: rho Mt1 <un psi> over the full range (FP64)
   double Mu[7], Mv[7], p1[4];
   gauss_moments7_full(U, h, Mu);
@@ -823,7 +845,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   for (int c = 0; c < 4; c++) {
     sL[c] = (float)(W0[c] - WL[c]) * inv;
     sR[c] = (float)(WR[c] - W0[c]) * inv;
-    sT[c] = (float)St[c] * firho;
+    sT[c] = St[c] * firho;
   }
   micro_slope(fU, fV, flam, q, c4, sL, aL);
   micro_slope(fU, fV, flam, q, c4, sR, aR);
@@ -848,7 +870,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
 #pragma unroll
   for (int c = 0; c < 4; c++) {
     const float second = fM2 * (t1[c] + t2[c] + t3[c]) + fM3 * t4[c];
-    F[c] = rho * (Mt[0] * p1[c] + (double)second) + Mt[3] * Sf[c] - Mt[4] * Ss[c];
+    F[c] = rho * (Mt[0] * p1[c] + (double)second) + Mt[3] * Sf[c] - (double)(fM5 * Ss[c]);
   }
   Mt4 = Mt[3];
   // FP32 record of the micro flux (S6/S8 coefficients, global frame)
@@ -897,7 +919,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   RF.E[2] = (float)(2.0 * lam * Vy * kLog2e);
   RF.E[3] = (float)(-lam * kLog2e);
   RF.Mt4 = (float)Mt[3];
-  RF.nMt5 = (float)(-Mt[4]);
+  RF.nMt5 = -fM5;
   RF.wall = 0.f;
   RF.gdt = 0.f;
 }
@@ -939,7 +961,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
   }
   FaceRec R;
   FaceRecF RF;
-  const bool f32 = fxf != nullptr;
+  constexpr bool f32 = std::is_same<S, float>::value;  // FP32-f form: FP32 sums and records
   double F[4];
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
@@ -971,20 +993,25 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     const S* sL = sums + (size_t)cL * kNSum + oL;
     const S* sR = sums + (size_t)cR * kNSum + oR;
     double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
-    const double* rL = P.refsum[oL / 16];
-    const double* rR = P.refsum[oR / 16];
+    float Stf[4], Ssf[4];
+    const double* rp = P.refpair[isx ? 0 : 1];  // g_ref sums of both sides (FP32-f form)
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const int s = pm[c];
-      W0[c] = ((double)sL[kOffW0 + s] + (double)sR[kOffW0 + s]) + (rL[kOffW0 + s] + rR[kOffW0 + s]);
-      St[c] = (double)sL[kOffSt + s] + (double)sR[kOffSt + s];
-      Sf[c] = ((double)sL[kOffSf + s] + (double)sR[kOffSf + s]) + (rL[kOffSf + s] + rR[kOffSf + s]);
-      Ss[c] = (double)sL[kOffSs + s] + (double)sR[kOffSs + s];
+      W0[c] = ((double)sL[kOffW0 + s] + (double)sR[kOffW0 + s]) + rp[s];
+      Sf[c] = ((double)sL[kOffSf + s] + (double)sR[kOffSf + s]) + rp[4 + s];
+      if constexpr (f32) {
+        Stf[c] = sL[kOffSt + s] + sR[kOffSt + s];
+        Ssf[c] = sL[kOffSs + s] + sR[kOffSs + s];
+      } else {
+        St[c] = (double)sL[kOffSt + s] + (double)sR[kOffSt + s];
+        Ss[c] = (double)sL[kOffSs + s] + (double)sR[kOffSs + s];
+      }
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
-    if (f32)
-      face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
+    if constexpr (f32)
+      face_math_f32(P, W0, Stf, Sf, Ssf, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
     else
       face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R);
 #pragma unroll
