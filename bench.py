@@ -54,7 +54,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 UPDATE_FLOPS_PER_VC = 130
 # DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
 # capture summarised in profiles/; None when the kernel has changed since that capture.
-UPDATE_TRAFFIC_PER_VC = (595.991040e6 + 466.211328e6) / 62.72e6  # kb_strip, 400x200x28^2 capture
+UPDATE_TRAFFIC_PER_VC = (596.680448e6 + 465.463808e6) / 62.72e6  # kb_strip, 400x200x28^2 capture
 
 
 class Clocks:

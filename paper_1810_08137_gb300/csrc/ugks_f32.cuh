@@ -171,13 +171,20 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
       a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = 0.f;
       y0 = y1 = y2 = y3 = y4 = yb0 = yb1 = yb2 = 0.f;
     };
-    // one row pair: stencil, slopes, accumulation; returns the centre and its slopes
-    auto pair = [&](int pr, P4& c, P4& rx, P4& ry) {
+    // stencil of one row pair (centre and its four neighbours), loaded one pair ahead of its
+    // use so that each warp has two pairs' loads in flight
+    struct Sten {
+      P4 c, w, e, s, n;
+    };
+    auto load = [&](int pr) {
       const float4* src = fc + (long)pr * nu + kk;
-      c = ldp(src);
-      const P4 w = ldp(src - ox), e = ldp(src + ox), s = ldp(src - oy), n = ldp(src + oy);
-      rx = vl4(w, c, e);
-      ry = vl4(s, c, n);
+      return Sten{ldp(src), ldp(src - ox), ldp(src + ox), ldp(src - oy), ldp(src + oy)};
+    };
+    // one row pair: slopes and accumulation; returns the slopes
+    auto use = [&](int pr, const Sten& q, P4& rx, P4& ry) {
+      rx = vl4(q.w, q.c, q.e);
+      ry = vl4(q.s, q.c, q.n);
+      const P4 c = q.c;
       const float4 t0 = __ldg(wt + 3 * pr), t1 = __ldg(wt + 3 * pr + 1), t2 = __ldg(wt + 3 * pr + 2);
       const float2 w0 = make_float2(t0.x, t0.y), w1 = make_float2(t0.z, t0.w);
       const float2 w2 = make_float2(t1.x, t1.y), w3 = make_float2(t1.z, t1.w);
@@ -212,26 +219,34 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     zero();
     float s0h = 0.f, s0b = 0.f, s0xh = 0.f, s0xb = 0.f, s0yh = 0.f, s0yb = 0.f;
     if (pa > pn) {
-      P4 c, rx, ry;
-      pair(pn, c, rx, ry);
+      Sten q = load(pn);
+      Sten nq = load(pn + 1 < pa ? pn + 1 : pn);
+      P4 rx, ry;
+      use(pn, q, rx, ry);
       if (v0) {  // the v = 0 row's half weight for the v < 0 half
         const float hw = __ldg(&wt[3 * pn].x);
-        s0h = hw * c.h.x; s0b = hw * c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
+        s0h = hw * q.c.h.x; s0b = hw * q.c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
         s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
       }
-    }
 #pragma unroll 1
-    for (int pr = pn + 1; pr < pa; pr++) {
-      P4 c, rx, ry;
-      pair(pr, c, rx, ry);
+      for (int pr = pn + 1; pr < pa; pr++) {
+        q = nq;
+        nq = load(pr + 1 < pa ? pr + 1 : pr);  // the last pair reloads itself (in bounds)
+        use(pr, q, rx, ry);
+      }
     }
     close(1.f, wsum + kSumN);
     zero();
     a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
+    if (pn > 0) {
+      Sten nq = load(0);
 #pragma unroll 1
-    for (int pr = 0; pr < pn; pr++) {
-      P4 c, rx, ry;
-      pair(pr, c, rx, ry);
+      for (int pr = 0; pr < pn; pr++) {
+        const Sten q = nq;
+        nq = load(pr + 1 < pn ? pr + 1 : pr);
+        P4 rx, ry;
+        use(pr, q, rx, ry);
+      }
     }
     close(-1.f, wsum + kSumS);
     // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
