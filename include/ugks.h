@@ -59,9 +59,12 @@ typedef enum {
   UGKS_FP64 = 0,   /* f stored and transported in FP64, all arithmetic FP64 */
   UGKS_FP32F = 1   /* f stored and transported in FP32 as f - g_ref; its velocity sums
                       are FP32 and are combined in FP64 with the exact sums of g_ref; FP64
-                      for W, the interface scalars (micro-slope solves, Mt time weights,
-                      equilibrium flux), the cell update coefficients and the exponents of
-                      the collision and wall Maxwellians relative to g_ref */
+                      for W, the interface terms first order in dt (interface W and
+                      primitive variables, Mt1, Mt4, equilibrium flux of g0, Mt4 S_f), the
+                      cell update coefficients and the exponents of the collision and wall
+                      Maxwellians relative to g_ref; FP32 for the terms that carry slopes
+                      (micro-slope solves and their Mt2, Mt3 terms, Mt5 S_sigma), formed
+                      from slopes of W differenced in FP64 */
 } ugks_precision;
 
 enum { UGKS_SIDE_W = 0, UGKS_SIDE_E = 1, UGKS_SIDE_S = 2, UGKS_SIDE_N = 3 };
