@@ -264,6 +264,9 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
 }
 
 constexpr int kConvBlocks = 1216;  // 8 per SM
+// 16-byte alignment of a caller's FP64 rows (the state conversion kernels then move each
+// (h, b) pair as one 16-byte access)
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 template <typename T2>
 __global__ void k_init_maxwellian(Params P, const double* __restrict__ prim, T2* __restrict__ f,
@@ -357,7 +360,10 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
   float4* dst = static_cast<float4*>(h->f[h->cur]);
   const double* src = from_host ? static_cast<const double*>(device_view(f, row_d * P.ny)) : f;
   if (src) {  // device memory, or host memory the conversion kernel reads in place
-    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
+    if (aligned16(src))
+      k_rows_to_f32<true><<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
+    else
+      k_rows_to_f32<false><<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
@@ -374,7 +380,7 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
     CK(cudaMemcpyAsync(buf, f + (size_t)j0 * P.nx * P.nq * 2, nr * row_d, cudaMemcpyHostToDevice, h->xstream));
     CK(cudaEventRecord(h->ev_copied[b], h->xstream));
     CK(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
-    k_rows_to_f32<<<kConvBlocks, 256, 0, h->stream>>>(buf, dst, P, h->grefd, j0, nr);
+    k_rows_to_f32<true><<<kConvBlocks, 256, 0, h->stream>>>(buf, dst, P, h->grefd, j0, nr);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_free[b], h->stream));
   }
@@ -393,7 +399,10 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
   const float4* src = static_cast<const float4*>(h->f[h->cur]);
   double* dst = to_host ? static_cast<double*>(device_view(f, row_d * P.ny)) : f;
   if (dst) {  // device memory, or host memory the conversion kernel writes in place
-    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
+    if (aligned16(dst))
+      k_f32_to_rows<true><<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
+    else
+      k_f32_to_rows<false><<<kConvBlocks, 256, 0, h->stream>>>(src, dst, P, h->grefd, 0, P.ny);
     CK(cudaGetLastError());
     return UGKS_OK;
   }
@@ -407,7 +416,7 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
     const int b = k & 1;
     double* buf = h->stage + b * (half / sizeof(double));
     CK(cudaStreamWaitEvent(h->stream, h->ev_free[b], 0));
-    k_f32_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(src, buf, P, h->grefd, j0, nr);
+    k_f32_to_rows<true><<<kConvBlocks, 256, 0, h->stream>>>(src, buf, P, h->grefd, j0, nr);
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_copied[b], h->stream));
     CK(cudaStreamWaitEvent(h->xstream, h->ev_copied[b], 0));

@@ -604,33 +604,39 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
 // State conversion and initialisation (set-up and checkpoint paths, not the step)
 // -------------------------------------------------------------------------------------
 // FP64 rows [cell][q][(h, b)] (rows j0 .. j0+nrows-1) -> paired slots, e = f - g_ref.  One
-// thread per velocity in the order of the rows (adjacent 8-byte reads, coalesced also when
-// the rows are host memory read over the C2C link; the rows need only 8-byte alignment); it
-// writes its two components into its slot and, for the last row of an odd half, into the
-// padding row that repeats it.
+// thread per slot (grid-stride over all slots of the rows): it reads (h, b) of its two rows
+// at u_k (a padding row repeats the half's last row, so it reads that row twice) and writes
+// the slot with one 16-byte store.  Adjacent threads read adjacent (h, b) pairs of a row,
+// coalesced also when the rows are host memory read over the C2C link; A16: the rows are
+// 16-byte aligned and each pair is one 16-byte load, else two 8-byte loads (the rows need
+// only 8-byte alignment).
+template <bool A16>
 __global__ void k_rows_to_f32(const double* __restrict__ src, float4* __restrict__ dst, Params P,
                               const double2* __restrict__ grefd, int j0, int nrows) {
-  const int ncell = P.nx * nrows;
-  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
-    const int r = c / P.nx, i = c - r * P.nx;
-    const double* s = src + (size_t)c * P.nq * 2;
-    float* d = reinterpret_cast<float*>(dst + ((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs);
-    for (int q = threadIdx.x; q < P.nq; q += blockDim.x) {
-      const int m = q / P.nu, k = q - m * P.nu, pr = padrow(P, m);
-      const double2 g = grefd[q];
-      const float h = (float)(s[2 * q] - g.x), b = (float)(s[2 * q + 1] - g.y);
-      float* o = d + 4 * ((size_t)(pr >> 1) * P.nu + k) + (pr & 1);
-      o[0] = h;
-      o[2] = b;
-      if (!(pr & 1) && prow(P, pr + 1) == m) {  // padding row of an odd half
-        o[1] = h;
-        o[3] = b;
-      }
+  const long nslot = (long)P.nx * nrows * P.fs;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nslot; t += (long)gridDim.x * blockDim.x) {
+    const long c = t / P.fs;
+    const int s = (int)(t - c * P.fs);
+    const int r = (int)(c / P.nx), i = (int)(c - (long)r * P.nx);
+    const int pr = s / P.nu, k = s - pr * P.nu;
+    const int q0 = prow(P, 2 * pr) * P.nu + k, q1 = prow(P, 2 * pr + 1) * P.nu + k;
+    const double* row = src + (size_t)c * P.nq * 2;
+    double2 a, b;
+    if constexpr (A16) {
+      a = reinterpret_cast<const double2*>(row)[q0];
+      b = reinterpret_cast<const double2*>(row)[q1];
+    } else {
+      a = make_double2(row[2 * q0], row[2 * q0 + 1]);
+      b = make_double2(row[2 * q1], row[2 * q1 + 1]);
     }
+    const double2 g0 = grefd[q0], g1 = grefd[q1];
+    dst[((size_t)(j0 + r + 2) * P.ex + i + 2) * P.fs + s] =
+        make_float4((float)(a.x - g0.x), (float)(b.x - g1.x), (float)(a.y - g0.y), (float)(b.y - g1.y));
   }
 }
 // paired slots -> FP64 rows, f = e + g_ref; one thread per velocity in the order of the rows
-// (adjacent 8-byte writes; the rows need only 8-byte alignment)
+// (adjacent (h, b) pairs; A16: one 16-byte store per pair, else two 8-byte stores)
+template <bool A16>
 __global__ void k_f32_to_rows(const float4* __restrict__ src, double* __restrict__ dst, Params P,
                               const double2* __restrict__ grefd, int j0, int nrows) {
   const int ncell = P.nx * nrows;
@@ -642,8 +648,13 @@ __global__ void k_f32_to_rows(const float4* __restrict__ src, double* __restrict
       const int m = q / P.nu, k = q - m * P.nu, pr = padrow(P, m);
       const float* e = s + 4 * ((size_t)(pr >> 1) * P.nu + k) + (pr & 1);
       const double2 g = grefd[q];
-      d[2 * q] = (double)e[0] + g.x;
-      d[2 * q + 1] = (double)e[2] + g.y;
+      const double h = (double)e[0] + g.x, b = (double)e[2] + g.y;
+      if constexpr (A16) {
+        reinterpret_cast<double2*>(d)[q] = make_double2(h, b);
+      } else {
+        d[2 * q] = h;
+        d[2 * q + 1] = b;
+      }
     }
   }
 }
