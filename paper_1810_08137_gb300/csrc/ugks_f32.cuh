@@ -1,7 +1,7 @@
-// FP32-f form of the step (FP32 f, FP64 moments / W / interface scalars) in the paired-row
-// layout: ghost fill, the per-cell velocity sums of S1 + S7, and the upwind strip walk of
-// S6, S8 and Eq. 3 (Liu, Hu & Li, arXiv:1810.08137, Sec. 2), plus state conversion and
-// initialisation.  The interface (S2-S5) and cell (Eq. 4) kernels are shared with the FP64
+// FP32-f form of the step (FP32 f; FP64 W, cell scalars and first-order interface terms) in
+// the paired-row layout: ghost fill, the per-cell velocity sums of S1 + S7, and the upwind
+// strip walk of S6, S8 and Eq. 3 (Liu, Hu & Li, arXiv:1810.08137, Sec. 2), plus state
+// conversion and initialisation.  The interface (S2-S5) and cell (Eq. 4) kernels are shared with the FP64
 // form and write the FP32 records read here.
 //
 // Layout.  The v axis is split into its v < 0 rows and its v >= 0 rows; each half is padded

@@ -7,12 +7,14 @@
 //                         tangential slope of W, free-transport sums) over one read of f
 //   k_faces               per interface, steps S2-S5 (Maxwellian moments, Mt time weights,
 //                         micro slopes a_L a_R b A, equilibrium flux) in FP64, the total
-//                         macroscopic flux, and the coefficients of the micro flux (S6, S8)
+//                         macroscopic flux, and the coefficients of the micro flux (S6, S8);
+//                         the FP32-f form runs the terms that carry slopes in FP32
 //   k_cells               conservative W update (Eq. 4), g^n, g^{n+1}, tau^n, tau^{n+1}
 //   k_update              micro flux of the four faces and the implicit f update (Eq. 3)
 //                         over a second read of f and one write of f^{n+1}
 // These are the FP64 form's kernels; the FP32-f form (FP32 f in a paired-row layout) has
-// its own ghost fill, sums and update in ugks_f32.cuh and shares k_faces and k_cells.
+// its own ghost fill, sums and update in ugks_f32.cuh and shares the interface and cell
+// bodies (faces_body, cells_body).
 //
 // Layout: f[(ny+4)(nx+4)][nq] of T2 = (h, b), velocity innermost (q = m*nu + k), a ghost
 // ring two cells wide; W[4][(ny+2)(nx+2)] FP64 with a ghost ring one cell wide.
@@ -459,7 +461,8 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
 }
 
 // -------------------------------------------------------------------------------------
-// Steps S2-S5 per interface (FP64), plus the coefficients of S6/S8 for the update kernel.
+// Steps S2-S5 per interface, plus the coefficients of S6/S8 for the update kernel: all FP64
+// in the FP64 form; first-order terms FP64 and slope-carrying terms FP32 in the FP32-f form.
 // -------------------------------------------------------------------------------------
 
 // Moments <x^n>, n = 0..6, of the normalised 1D Gaussian sqrt(lam/pi) exp(-lam (x-U)^2):
@@ -822,7 +825,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   const double h = 2.0 * ilam4;  // 1/(2 lam)
   const double rl = rsqrt(lam);
   const double X2 = 2.0 * K * ilam4;
-  // S3: collision time and Mt1..Mt5 (FP64)
+  // S3: collision time and Mt1, Mt4 (FP64), Mt2, Mt3, Mt5 (FP32)
   const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
   double Mt[5];
   float fM2, fM3, fM5;
