@@ -73,7 +73,18 @@ CASES = {
     "periodic_5x4_v5x6_vpos": lambda: periodic_cfg(nx=5, ny=4, nu=5, nv=6, vmin=0.5, vmax=3.0),
     "periodic_6x5_v35x8_asym": lambda: periodic_cfg(nx=6, ny=5, nu=35, nv=8, vmin=-3.0, vmax=1.5,
                                                     kn=0.1),
+    # general viscosity laws (R3): variable hard sphere with omega = 0.81 and variable soft
+    # sphere with omega = 0.75, alpha = 1.4 (tau through T^omega instead of the hard-sphere
+    # shortcut), the latter in a channel at small Kn (dt/tau above 0.1 in many faces)
+    "periodic_7x5_v9_vhs": lambda: periodic_cfg(nx=7, ny=5, nu=9, nv=9, kn=0.05, omega=0.81),
+    "channel_9x6_v11_vss": lambda: _vss(),
 }
+
+
+def _vss():
+    cfg = I.channel_config(nx=9, ny=6, n_vel=11, kn=0.01)
+    cfg.omega, cfg.alpha = 0.75, 1.4
+    return cfg
 
 
 def _hotwall():
