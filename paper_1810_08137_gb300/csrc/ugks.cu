@@ -32,6 +32,7 @@ struct ugks_ctx {
   int cur = 0;
   double* sums = nullptr;
   double2* slopes = nullptr;  // FP64 form: van Leer slopes kept by the sums kernel for the update
+  double2* xflux = nullptr;   // FP64 form: micro flux of every face and velocity, x faces then y
   FaceRec* fxr = nullptr;
   FaceRec* fyr = nullptr;
   double* Fx = nullptr;
@@ -173,7 +174,7 @@ size_t predict_bytes(const ugks_config* c) {
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
   b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
   b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * (2 * (c->nu + c->nv) + 5 * c->nv);
-  if (!f32) b += nwe * nq * 2 * sizeof(double2);  // slope buffer
+  if (!f32) b += nwe * nq * 2 * sizeof(double2) + (nfx + nfy) * nq * sizeof(double2);  // slopes, face fluxes
   if (f32) {
     const size_t row_d = nx * nq * 2 * sizeof(double);
     b += 2 * stage_half_bytes(row_d, ny) + sizeof(float4) * fs + sizeof(double2) * nq +
@@ -192,6 +193,14 @@ template <typename T>
 size_t smem_update(int nv) {
   return (1 + 6 * kWarpsPerBlock) * (size_t)nv * sizeof(T);
 }
+template <typename T>
+size_t smem_face_flux(int nv) {
+  return (1 + 4 * kWarpsPerBlock) * (size_t)nv * sizeof(T);
+}
+template <typename T>
+size_t smem_cell_update(int nv) {
+  return (1 + 2 * kWarpsPerBlock) * (size_t)nv * sizeof(T);
+}
 
 // dynamic shared memory limits of the FP64 form's sums and update kernels
 cudaError_t set_smem_limits_fp64(int nv) {
@@ -200,6 +209,12 @@ cudaError_t set_smem_limits_fp64(int nv) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_update<double, double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem_update<double>(nv));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_face_flux<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_face_flux<double>(nv));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cell_update<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_cell_update<double>(nv));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_update<double, double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_update<double>(nv));
@@ -254,9 +269,13 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
                                        h->cellf, h->mt4);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  k_update<T, T2, true>
-      <<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_update<T>(P.nv), st>>>(
-          P, fi, fo, h->fxr, h->fyr, h->cells, reinterpret_cast<const T2*>(h->slopes));
+  // the update in two passes: every face flux once, then Eq. 3 per velocity-cell
+  T2* Xx = reinterpret_cast<T2*>(h->xflux);
+  T2* Xy = Xx + (size_t)(P.nx + 1) * P.ny * P.nq;
+  const int ub = (nc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_face_flux<T, T2><<<ub, 32 * kWarpsPerBlock, smem_face_flux<T>(P.nv), st>>>(
+      P, fi, h->fxr, h->fyr, reinterpret_cast<const T2*>(h->slopes), Xx, Xy);
+  k_cell_update<T, T2><<<ub, 32 * kWarpsPerBlock, smem_cell_update<T>(P.nv), st>>>(P, fi, fo, h->cells, Xx, Xy);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
@@ -791,6 +810,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->sums, sizeof(double) * kNSum * (size_t)h->nwe) &&
             (f32 || alloc((void**)&h->slopes, sizeof(double2) * 2 * (size_t)h->nwe * P.nq)) &&
+            (f32 || alloc((void**)&h->xflux, sizeof(double2) * (size_t)(nfx + nfy) * P.nq)) &&
             (f32 ? alloc((void**)&h->fxf, sizeof(FaceRecF) * (size_t)nfx)
                  : alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx)) &&
             (f32 ? alloc((void**)&h->fyf, sizeof(FaceRecF) * (size_t)nfy)
@@ -898,7 +918,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
 
 void ugks_destroy(ugks_handle h) {
   if (!h) return;
-  void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->slopes, h->fxr, h->fyr, h->Fx, h->Fy,
+  void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->slopes, h->xflux, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref4, h->grefd, h->fxf, h->fyf,
                   h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
   if (h->stream) cudaStreamSynchronize(h->stream);

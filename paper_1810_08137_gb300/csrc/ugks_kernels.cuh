@@ -1405,4 +1405,242 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
 }
 
 
+// -------------------------------------------------------------------------------------
+// The same update in two passes, FP64 form: every (face, velocity) micro flux once.
+// k_face_flux: one warp per interior cell, lane = u index; for each velocity the cell forms
+// the flux X = Q g + Mt4 f_up - Mt5 d_up (or the wall flux) through its downwind x-face and
+// y-face from its own reconstruction, and a cell next to the boundary also forms the flux
+// whose upwind side is the ghost cell or the wall.  Every face and velocity is written by
+// exactly one warp, into Xx [(nx+1) ny][nq] and Xy [nx (ny+1)][nq] (face-major, velocity
+// innermost).  k_cell_update then reads the four fluxes of each velocity-cell and applies
+// Eq. 3.  The arithmetic of each flux and of the update is that of k_update, which forms
+// the four face fluxes of every velocity-cell (each interior flux twice).
+// -------------------------------------------------------------------------------------
+template <typename T>
+struct FaceK {
+  T Mt4, Mt5, bf;
+  int wall;
+};
+template <typename T, typename T2>
+__global__ void __launch_bounds__(128) k_face_flux(Params P, const T2* __restrict__ f,
+                                                   const FaceRec* __restrict__ fxr,
+                                                   const FaceRec* __restrict__ fyr,
+                                                   const T2* __restrict__ sl, T2* __restrict__ Xx,
+                                                   T2* __restrict__ Xy) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nv = P.nv, nu = P.nu, nq = P.nq, nx = P.nx, ny = P.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* sv = reinterpret_cast<T*>(smraw);
+  T* ev = sv + nv + warp * 4 * nv;  // [4][nv]: x W, x E, y S, y N factors in v
+  for (int m = tid; m < nv; m += blockDim.x) sv[m] = (T)P.v[m];
+  __syncthreads();
+  const int cell = blockIdx.x * kWarpsPerBlock + warp;
+  if (cell >= nx * ny) return;
+  const int i = cell % nx, j = cell / nx;
+  const FaceRec& RW = fxr[(size_t)j * (nx + 1) + i];
+  const FaceRec& RE = fxr[(size_t)j * (nx + 1) + i + 1];
+  const FaceRec& RS = fyr[(size_t)j * nx + i];
+  const FaceRec& RN = fyr[(size_t)(j + 1) * nx + i];
+  for (int m = lane; m < nv; m += 32) {
+    const double vv = P.v[m];
+    double d;
+    d = vv - RW.Ut; ev[0 * nv + m] = (T)exp(-RW.lam * d * d);  // x faces: ut = v
+    d = vv - RE.Ut; ev[1 * nv + m] = (T)exp(-RE.lam * d * d);
+    d = vv - RS.Un; ev[2 * nv + m] = (T)exp(-RS.lam * d * d);  // y faces: un = v
+    d = vv - RN.Un; ev[3 * nv + m] = (T)exp(-RN.lam * d * d);
+  }
+  __syncwarp();
+  auto faceK = [](const FaceRec& R) { return FaceK<T>{(T)R.Mt4, (T)R.Mt5, (T)R.bfac, R.wall}; };
+  const FaceK<T> KW = faceK(RW), KE = faceK(RE), KS = faceK(RS), KN = faceK(RN);
+  const T tdx = T(2.0 / P.dx), tdy = T(2.0 / P.dy);
+  const T dtT = (T)P.dt;
+  const long rs = (long)P.ex * nq;
+  const T2* fc0 = f + fcell(P, i, j) * nq;
+  const T2* sl0 = sl + (size_t)wcell(P, i, j) * nq * 2;  // this cell's slopes
+  T2* xw0 = Xx + ((size_t)j * (nx + 1) + i) * nq;        // W face of the cell; E face: + nq
+  T2* ys0 = Xy + ((size_t)j * nx + i) * nq;              // S face; N face: + nx nq
+  const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
+
+  // X of a face from the face value fh, fb and slope term dh, db of its upwind side; inc:
+  // the gas side is upwind (a wall face then passes dt f_up, else dt g_wall)
+  auto flux = [&](const FaceK<T>& F, const T (&qh)[4], const T (&qb)[4], T vv, T g, T fh, T fb,
+                  T dh, T db, bool inc) {
+    T2 X;
+    if (F.wall) {
+      X.x = inc ? dtT * fh : dtT * g;
+      X.y = inc ? dtT * fb : dtT * (F.bf * g);
+    } else {
+      X.x = horner3(qh, vv) * g + F.Mt4 * fh - F.Mt5 * dh;
+      X.y = horner3(qb, vv) * g + F.Mt4 * fb - F.Mt5 * db;
+    }
+    return X;
+  };
+
+  for (int k0 = 0; k0 < nu; k0 += 32) {
+    const int k = k0 + lane;
+    const bool act = k < nu;
+    const int kk = act ? k : nu - 1;
+    const double ud = P.u[kk];
+    const T u = (T)ud;
+    T gu[4];
+    {
+      double d;
+      d = ud - RW.Un; gu[0] = (T)(RW.G * exp(-RW.lam * d * d));
+      d = ud - RE.Un; gu[1] = (T)(RE.G * exp(-RE.lam * d * d));
+      d = ud - RS.Ut; gu[2] = (T)(RS.G * exp(-RS.lam * d * d));
+      d = ud - RN.Ut; gu[3] = (T)(RN.G * exp(-RN.lam * d * d));
+    }
+    const int xs = ud > 0.0 ? 0 : 1;  // upwind side of the x-face records
+    const bool up = ud > 0.0;         // downwind x-face: E for u > 0, W otherwise
+    const T sgx = up ? T(1) : T(-1);  // f_up = f + sgx r_x on the downwind face
+    // the downwind x-face (formed by this cell for every velocity) and the upwind one
+    // (formed here only when its upwind side is a ghost cell or a wall)
+    const FaceRec& RXd = up ? RE : RW;
+    const FaceRec& RXg = up ? RW : RE;
+    const FaceK<T> KXd = up ? KE : KW, KXg = up ? KW : KE;
+    const T gXd = up ? gu[1] : gu[0], gXg = up ? gu[0] : gu[1];
+    const T* evXd = ev + (up ? nv : 0);
+    const T* evXg = ev + (up ? 0 : nv);
+    T2* xd0 = up ? xw0 + nq : xw0;
+    T2* xg0 = up ? xw0 : xw0 + nq;
+    T qX[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; c++) poly_in_v_xface(RXd.Q[xs][c], ud, qX[c]);
+    const long xo = up ? -(long)nq : (long)nq;  // x-upwind neighbour in f, in q
+    const bool xg = up ? i == 0 : i == nx - 1;  // it is a ghost cell (or a wall)
+    const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
+    const T cu = u * tdx;
+
+    auto half = [&](auto vup_tag, int m0, int m1) {
+      constexpr bool VUP = decltype(vup_tag)::value;  // downwind y-face: N for v > 0, S otherwise
+      constexpr int ys = VUP ? 0 : 1;
+      const FaceRec& RYd = VUP ? RN : RS;
+      const FaceRec& RYg = VUP ? RS : RN;
+      const FaceK<T>& KYd = VUP ? KN : KS;
+      const FaceK<T>& KYg = VUP ? KS : KN;
+      const T gYd = VUP ? gu[3] : gu[2], gYg = VUP ? gu[2] : gu[3];
+      const T* evYd = ev + (VUP ? 3 : 2) * nv;
+      const T* evYg = ev + (VUP ? 2 : 3) * nv;
+      T2* yd0 = VUP ? ys0 + (size_t)nx * nq : ys0;
+      T2* yg0 = VUP ? ys0 : ys0 + (size_t)nx * nq;
+      constexpr T sgy = VUP ? T(1) : T(-1);
+      T qY[2][4];
+#pragma unroll
+      for (int c = 0; c < 2; c++) poly_in_v_yface(RYd.Q[ys][c], ud, qY[c]);
+      const long yo = VUP ? -rs : rs;                             // y-upwind neighbour in f
+      const long yso = VUP ? -(long)P.wx * nq : (long)P.wx * nq;  // ... in the slope buffer
+      const bool yg = VUP ? j == 0 : j == ny - 1;
+      const bool yz = (VUP && j == 0 && pS) || (!VUP && j == ny - 1 && pN);
+      for (int m = m0; m < m1; m++) {
+        const T vv = sv[m];
+        const size_t q = (size_t)m * nu + kk;
+        const T2* p = fc0 + q;
+        const T2 c = p[0];
+        const T2* sq = sl0 + 2 * q;
+        const T2 a = sq[0], b = sq[1];  // half slopes r_x, r_y of the cell (h, b)
+        const T cv = vv * tdy;
+        const T dch = cu * a.x + cv * b.x, dcb = cu * a.y + cv * b.y;
+        T2 X = flux(KXd, qX[0], qX[1], vv, gXd * evXd[m], c.x + sgx * a.x, c.y + sgx * a.y, dch,
+                    dcb, true);
+        if (act) xd0[q] = X;
+        if (xg) {
+          const T2 xu = p[xo];
+          const T2* su = sq + 2 * xo;
+          T2 au = su[0], bu = su[1];
+          if (xz) au.x = au.y = bu.x = bu.y = T(0);
+          const T duh = cu * au.x + cv * bu.x, dub = cu * au.y + cv * bu.y;
+          T qg[2][4];
+#pragma unroll
+          for (int cc = 0; cc < 2; cc++) poly_in_v_xface(RXg.Q[xs][cc], ud, qg[cc]);
+          X = flux(KXg, qg[0], qg[1], vv, gXg * evXg[m], xu.x + sgx * au.x, xu.y + sgx * au.y, duh,
+                   dub, false);
+          if (act) xg0[q] = X;
+        }
+        X = flux(KYd, qY[0], qY[1], vv, gYd * evYd[m], c.x + sgy * b.x, c.y + sgy * b.y, dch, dcb,
+                 true);
+        if (act) yd0[q] = X;
+        if (yg) {
+          const T2 yu = p[yo];
+          const T2* sw = sq + 2 * yso;
+          T2 av = sw[0], bv = sw[1];
+          if (yz) av.x = av.y = bv.x = bv.y = T(0);
+          const T dvh = cu * av.x + cv * bv.x, dvb = cu * av.y + cv * bv.y;
+          T qg[2][4];
+#pragma unroll
+          for (int cc = 0; cc < 2; cc++) poly_in_v_yface(RYg.Q[ys][cc], ud, qg[cc]);
+          X = flux(KYg, qg[0], qg[1], vv, gYg * evYg[m], yu.x + sgy * bv.x, yu.y + sgy * bv.y, dvh,
+                   dvb, false);
+          if (act) yg0[q] = X;
+        }
+      }
+    };
+    half(std::integral_constant<bool, false>{}, 0, P.m_pos);
+    half(std::integral_constant<bool, true>{}, P.m_pos, nv);
+  }
+}
+
+// Eq. 3 from the four face fluxes of each velocity-cell (k_face_flux), FP64 form.
+template <typename T, typename T2>
+__global__ void __launch_bounds__(128) k_cell_update(Params P, const T2* __restrict__ f,
+                                                     T2* __restrict__ fo,
+                                                     const CellRec* __restrict__ cr,
+                                                     const T2* __restrict__ Xx,
+                                                     const T2* __restrict__ Xy) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nv = P.nv, nu = P.nu, nq = P.nq, nx = P.nx, ny = P.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* sv = reinterpret_cast<T*>(smraw);
+  T* ev = sv + nv + warp * 2 * nv;  // [2][nv]: g^n, g^{n+1} factors in v
+  for (int m = tid; m < nv; m += blockDim.x) sv[m] = (T)P.v[m];
+  __syncthreads();
+  const int cell = blockIdx.x * kWarpsPerBlock + warp;
+  if (cell >= nx * ny) return;
+  const int i = cell % nx, j = cell / nx;
+  const CellRec& C = cr[cell];
+  for (int m = lane; m < nv; m += 32) {
+    const double vv = P.v[m];
+    double d;
+    d = vv - C.Vn; ev[m] = (T)exp(-C.lamn * d * d);
+    d = vv - C.V1; ev[nv + m] = (T)exp(-C.lam1 * d * d);
+  }
+  __syncwarp();
+  const T inv = (T)C.inv, cg1 = (T)C.cg1, cgn = (T)C.cgn;
+  const T cg1b = (T)(C.cg1 * C.b1), cgnb = (T)(C.cgn * C.bn);
+  const T idx = T(1.0 / P.dx), idy = T(1.0 / P.dy);
+  const T2* fc0 = f + fcell(P, i, j) * nq;
+  T2* fo0 = fo + fcell(P, i, j) * nq;
+  const T2* xw0 = Xx + ((size_t)j * (nx + 1) + i) * nq;
+  const T2* ys0 = Xy + ((size_t)j * nx + i) * nq;
+  for (int k0 = 0; k0 < nu; k0 += 32) {
+    const int k = k0 + lane;
+    const bool act = k < nu;
+    const int kk = act ? k : nu - 1;
+    const double ud = P.u[kk];
+    const T u = (T)ud;
+    T gun, gu1;
+    {
+      double d;
+      d = ud - C.Un; gun = (T)(C.Gn * exp(-C.lamn * d * d));
+      d = ud - C.U1; gu1 = (T)(C.G1 * exp(-C.lam1 * d * d));
+    }
+    const T fxu = u * idx;
+    for (int m = 0; m < nv; m++) {
+      const T vv = sv[m];
+      const T fyv = vv * idy;
+      const size_t q = (size_t)m * nu + kk;
+      const T2 c = fc0[q];
+      const T2 XW = xw0[q], XE = xw0[nq + q], XS = ys0[q], XN = ys0[(size_t)nx * nq + q];
+      T flh = fxu * (XW.x - XE.x) + fyv * (XS.x - XN.x);
+      T flb = fxu * (XW.y - XE.y) + fyv * (XS.y - XN.y);
+      const T gnh = gun * ev[m], g1h = gu1 * ev[nv + m];
+      const T dh = inv * (flh + cg1 * (g1h - c.x) + cgn * (gnh - c.x));
+      const T db = inv * (flb + (cg1b * g1h - cg1 * c.y) + (cgnb * gnh - cgn * c.y));
+      T2 o;
+      o.x = c.x + dh;
+      o.y = c.y + db;
+      if (act) fo0[q] = o;
+    }
+  }
+}
+
 }  // namespace ugks
