@@ -396,7 +396,7 @@ def main():
         bpv = 8 if prec == ugks.FP32F else 16  # bytes per velocity-cell of f (h, b)
         n_up, t_up = kt["update"]
         n_sm, t_sm = kt["sums"]
-        t_launch = t_up / n_up * 1e-3  # seconds per update launch
+        t_launch = t_up / n_up * 1e-3  # seconds per update (FP64 form: its two passes together)
         # algorithmic bytes: update reads f once and writes it once, sums reads f once
         ach_up = 2 * bpv * cfg.vc / t_launch / 1e9
         ach_sm = bpv * cfg.vc / (t_sm / n_sm * 1e-3) / 1e9

@@ -10,8 +10,12 @@
 //                         macroscopic flux, and the coefficients of the micro flux (S6, S8);
 //                         the FP32-f form runs the terms that carry slopes in FP32
 //   k_cells               conservative W update (Eq. 4), g^n, g^{n+1}, tau^n, tau^{n+1}
-//   k_update              micro flux of the four faces and the implicit f update (Eq. 3)
-//                         over a second read of f and one write of f^{n+1}
+//   k_face_flux           micro flux of every face and velocity (S6, S8), once, from its
+//                         upwind cell, into face-flux buffers (second read of f)
+//   k_cell_update         the implicit f update (Eq. 3) from the four fluxes of each
+//                         velocity-cell, one write of f^{n+1}
+//   (k_update, the same update in one pass that forms each interior flux twice, serves the
+//   allocation-free entry point)
 // These are the FP64 form's kernels; the FP32-f form (FP32 f in a paired-row layout) has
 // its own ghost fill, sums and update in ugks_f32.cuh and shares the interface and cell
 // bodies (faces_body, cells_body).
