@@ -234,6 +234,16 @@ def test_residual_matches_definition(U, oracle):
     assert np.allclose(res, ref, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("name", ["periodic_13x7_v37", "channel_40x20_v20", "periodic_5x4_v6x1"])
+def test_state_bytes_predicts_allocation(U, name):
+    """ugks_state_bytes (used for admission against an HBM budget) equals the device bytes
+    ugks_create allocates, in both forms."""
+    cfg = CASES[name]()
+    for prec in (U.FP64, U.FP32F):
+        with U.Solver(cfg, prec) as s:
+            assert s.device_bytes == U.state_bytes(cfg, prec), (prec, s.device_bytes)
+
+
 def test_device_state_roundtrip(U, oracle):
     torch = pytest.importorskip("torch")
     cfg = CASES["periodic_13x7_v37"]()
