@@ -293,7 +293,7 @@ def _maxwell_red(cfg, Wc, uq, vq):
     return np.stack([gh, cfg.K / (2 * lam) * gh], axis=1), BF.tau_of(cfg, rho, lam)
 
 
-@pytest.mark.parametrize("case", ["periodic", "channel"])
+@pytest.mark.parametrize("case", ["periodic", "channel", "channel_vss"])
 def test_step_satisfies_eq3_and_eq4(oracle, case):
     """The oracle's f^{n+1}, W^{n+1} make the residuals of Eq. 4 and of the implicit
     Eq. 3 (as printed: trapezoidal collision term with g^{n+1}, tau^{n+1} from W^{n+1})
@@ -302,6 +302,8 @@ def test_step_satisfies_eq3_and_eq4(oracle, case):
         cfg = periodic_cfg(nu=5, nv=4, kn=0.02)
     else:
         cfg = I.channel_config(nx=4, ny=4, n_vel=5, vrange=3.0, kn=0.02)
+        if case == "channel_vss":  # variable soft sphere: tau through T^omega, alpha != 1
+            cfg.omega, cfg.alpha = 0.75, 1.4
     f, W = random_state(oracle, cfg, 21)
     dt = oracle.dt(cfg)
     f1, W1 = oracle.step(cfg, f, W, 1)
