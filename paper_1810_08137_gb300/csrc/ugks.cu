@@ -207,16 +207,13 @@ cudaError_t set_smem_limits_fp64(int nv) {
   cudaError_t e = cudaFuncSetAttribute(k_sums<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_sums<double>(nv));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_update<double, double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_update<double>(nv));
-  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_face_flux<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem_face_flux<double>(nv));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_cell_update<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem_cell_update<double>(nv));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_update<double, double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_update<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_update<double>(nv));
 }
 
@@ -641,8 +638,8 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   k_faces<double><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
   // slopes are formed again in the update kernel: the scratch array holds no slope buffer
-  k_update<double, double2, false><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
-                                     smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells, nullptr);
+  k_update<double, double2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
+                              smem_update<double>(P.nv), st>>>(P, f0, f1, fxr, fyr, cells);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpy2DAsync(f_out, row, reinterpret_cast<char*>(f1) + ((size_t)2 * P.ex + 2) * nq * sizeof(double2),
                           (size_t)P.ex * nq * sizeof(double2), row, ny, cudaMemcpyDeviceToDevice, st));

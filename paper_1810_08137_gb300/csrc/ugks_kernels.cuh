@@ -1196,16 +1196,14 @@ struct UpdCell {
   int wall[4];
 };
 
-// SLOPES: the van Leer slopes of the cell and of its upwind neighbours come from the sums
-// kernel's slope buffer sl ([(nx+2)(ny+2)][nq][2], W cell indexing) instead of being formed
-// again here (12 per velocity-cell); both give the same values.
-template <typename T, typename T2, bool SLOPES>
+// The van Leer slopes of the cell and of its upwind neighbours are formed here (12 per
+// velocity-cell), so the kernel needs no slope buffer.
+template <typename T, typename T2>
 __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__ f,
                                                 T2* __restrict__ fo,
                                                 const FaceRec* __restrict__ fxr,
                                                 const FaceRec* __restrict__ fyr,
-                                                const CellRec* __restrict__ cr,
-                                                const T2* __restrict__ sl) {
+                                                const CellRec* __restrict__ cr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nv = P.nv, nu = P.nu, nq = P.nq, nx = P.nx, ny = P.ny;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1253,7 +1251,6 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
   const long rs = (long)P.ex * nq;
   const T2* fc0 = f + fcell(P, i, j) * nq;
   T2* fo0 = fo + fcell(P, i, j) * nq;
-  const T2* sl0 = SLOPES ? sl + (size_t)wcell(P, i, j) * nq * 2 : nullptr;  // this cell's slopes
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
@@ -1281,7 +1278,6 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
     }
     const bool up = ud > 0.0;  // x upwind neighbour: W for u > 0, E for u < 0
     const long xo = up ? -(long)nq : (long)nq;
-    const long xso = up ? -(long)nq : (long)nq;  // x-upwind cell in the slope buffer, in q
     const bool xz = (up && i == 0 && pW) || (!up && i == nx - 1 && pE);
     const T cu = u * tdx, fxu = u * idx;
 
@@ -1295,7 +1291,6 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         poly_in_v_yface(RN.Q[VUP ? 0 : 1][c], ud, qN[c]);
       }
       const long yo = VUP ? -rs : rs;
-      const long yso = VUP ? -(long)P.wx * nq : (long)P.wx * nq;  // y-upwind cell, in q
       const bool yz = (VUP && j == 0 && pS) || (!VUP && j == ny - 1 && pN);
       for (int m = m0; m < m1; m++) {
         const T vv = sv[m];
@@ -1304,14 +1299,7 @@ __global__ void __launch_bounds__(128) k_update(Params P, const T2* __restrict__
         const T2 xu = p[xo], yu = p[yo];
         // half slopes r = sigma h / 2 of the cell, its x-upwind and its y-upwind neighbour
         T rxch, rxcb, rych, rycb, rxuh, rxub, ryuh, ryub, rxvh, rxvb, ryvh, ryvb;
-        if (SLOPES) {
-          const T2* q = sl0 + 2 * ((size_t)m * nu + kk);
-          const T2 a = q[0], b = q[1], au = q[2 * xso], bu = q[2 * xso + 1];
-          const T2 av = q[2 * yso], bv = q[2 * yso + 1];
-          rxch = a.x; rxcb = a.y; rych = b.x; rycb = b.y;
-          rxuh = au.x; rxub = au.y; ryuh = bu.x; ryub = bu.y;
-          rxvh = av.x; rxvb = av.y; ryvh = bv.x; ryvb = bv.y;
-        } else {
+        {
           const T2 w = p[-(long)nq], e = p[nq], s = p[-rs], n = p[rs];
           const T2 xf = p[2 * xo], xs_ = p[xo - rs], xn = p[xo + rs];
           const T2 yf = p[2 * yo], yw = p[yo - (long)nq], ye = p[yo + (long)nq];
