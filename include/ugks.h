@@ -45,7 +45,8 @@ typedef enum {
   UGKS_EINVAL = 1,    /* invalid argument or configuration */
   UGKS_ENOMEM = 2,    /* device allocation failed */
   UGKS_ECUDA = 3,     /* a CUDA runtime call failed */
-  UGKS_ETIMEOUT = 4,  /* a bounded device wait gave up (persistent batch kernel) */
+  UGKS_ETIMEOUT = 4,  /* reserved for a bounded device wait that gives up; no kernel of this
+                         version waits on another, so no call returns it */
   UGKS_ENUMERIC = 5   /* rho <= 0, T <= 0 or NaN appeared in a cell */
 } ugks_status;
 
