@@ -60,3 +60,25 @@ def test_create_rejects_bad_config_without_gpu():
     bad.bc = [I.BC(I.BC_PERIODIC), I.BC(I.BC_WALL), I.BC(I.BC_WALL), I.BC(I.BC_WALL)]
     with pytest.raises(ugks.UGKSError):
         ugks.Solver(bad)
+
+
+def test_state_bytes_without_gpu():
+    """ugks_state_bytes is host arithmetic (no CUDA call): 0 for an invalid configuration;
+    otherwise the f copies dominate it (FP64: plus the slope and face-flux buffers), with
+    O(cells + faces) bytes of records on top, and it grows with the mesh."""
+    from paper_1810_08137_gb300 import inputs as I
+    from paper_1810_08137_gb300 import ugks
+    assert ugks.state_bytes(I.channel_config(nx=0)) == 0
+    cfg = I.channel_config(nx=40, ny=20, n_vel=20)
+    nq, nx, ny = 400, 40, 20
+    ring, wring = (nx + 4) * (ny + 4), (nx + 2) * (ny + 2)
+    faces = (nx + 1) * ny + nx * (ny + 1)
+    big64 = 2 * ring * nq * 16 + wring * nq * 32 + faces * nq * 16
+    b64 = ugks.state_bytes(cfg, ugks.FP64)
+    assert big64 < b64 < big64 + 2000 * (ring + faces)
+    fs = 10 * 20  # 20 rows: 10 per half of the v axis, 5 row pairs each; 20 u values
+    big32 = 2 * ring * fs * 16
+    b32 = ugks.state_bytes(cfg, ugks.FP32F)
+    stage = 2 * (32 << 20)  # the two staging halves of the host-state conversion
+    assert big32 < b32 < big32 + stage + 2000 * (ring + faces)
+    assert ugks.state_bytes(I.channel_config(nx=80, ny=40, n_vel=20), ugks.FP64) > b64
