@@ -5,6 +5,7 @@ use it; the product path never imports it.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -16,14 +17,21 @@ SRC = os.path.join(HERE, "ugks_oracle.c")
 LIB = os.path.join(HERE, "libugks_oracle.so")
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source file of the oracle into the shared library `out` (gcc, OpenMP
+    over faces and cells).  The source must include ugks_oracle.h from this directory."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                           "-fopenmp", "-I", HERE, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP over faces and cells)."""
+    """Compile the oracle (if its source is newer than the library)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "ugks_oracle.h"))):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                               "-fopenmp", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
+        compile_source(SRC, LIB)
     return LIB
 
 
@@ -40,16 +48,35 @@ _lib = None
 _P = C.POINTER(C.c_double)
 
 
+def _load(path: str):
+    L = C.CDLL(path)
+    L.orc_dt.restype = C.c_double
+    L.orc_tau.restype = C.c_double
+    L.orc_get_threads.restype = C.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(LIB)
-        L.orc_dt.restype = C.c_double
-        L.orc_tau.restype = C.c_double
-        L.orc_get_threads.restype = C.c_int
-        _lib = L
+        _lib = _load(LIB)
     return _lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Route every call of this module to another build of the oracle (a copy with a
+    deliberately planted mistake, in the tests that show the pins catch it)."""
+    global _lib
+    old = lib()
+    threads = old.orc_get_threads()
+    _lib = _load(path)
+    _lib.orc_set_threads(threads)
+    try:
+        yield
+    finally:
+        _lib = old
 
 
 def _cfg(cfg) -> _Cfg:

@@ -183,7 +183,7 @@ def wall_face(cfg, dt, unq, utq, wq, f_face, interior_high, Tw, Uw, K):
 
 def fluxes(cfg, dt, f, W):
     """All face fluxes of the mesh, same storage order as the oracle's orc_fluxes.
-    Supports periodic sides and the channel (pressure x-sides, wall y-sides)."""
+    Every side may be periodic (paired), a diffuse wall or a pressure ghost."""
     nx, ny, nq, K = cfg.nx, cfg.ny, cfg.nq, cfg.K
     dx, dy = cfg.lx / nx, cfg.ly / ny
     u, wu = axis(cfg.nu, cfg.umin, cfg.umax)
@@ -221,6 +221,9 @@ def fluxes(cfg, dt, f, W):
                 adj = 2 if side == 0 else nx + 1
                 fe[2:-2, col] = fe[2:-2, adj]
                 We[:, 2:-2, col] = We[:, 2:-2, adj]
+    # y sides over every column, the x-ghost columns included (corners): periodic image,
+    # zero-gradient copy next to a wall, or a pressure Maxwellian with the velocity of the
+    # cell (or x-ghost) next to it in the same column
     for side, rows in ((2, (1, 0)), (3, (ny + 2, ny + 3))):
         for row in rows:
             if kinds[side] == PERIODIC:
@@ -232,7 +235,17 @@ def fluxes(cfg, dt, f, W):
                 fe[row] = fe[adj]
                 We[:, row] = We[:, adj]
             else:
-                raise NotImplementedError
+                adj = 2 if side == 2 else ny + 1
+                bc = cfg.bc[side]
+                lam = 1.0 / bc.T
+                for col in range(nx + 4):
+                    Ua = We[1, adj, col] / We[0, adj, col]
+                    Va = We[2, adj, col] / We[0, adj, col]
+                    gh = bc.rho * lam / math.pi * np.exp(-lam * ((uq - Ua) ** 2 + (vq - Va) ** 2))
+                    fe[row, col, :, 0] = gh
+                    fe[row, col, :, 1] = K / (2 * lam) * gh
+                    We[:, row, col] = [bc.rho, bc.rho * Ua, bc.rho * Va,
+                                       bc.rho * (0.5 * (Ua ** 2 + Va ** 2) + (K + 2) / (4 * lam))]
     sx = np.zeros_like(fe)
     sy = np.zeros_like(fe)
     sx[:, 1:-1] = vanleer((fe[:, 1:-1] - fe[:, :-2]) / dx, (fe[:, 2:] - fe[:, 1:-1]) / dx)
@@ -241,6 +254,10 @@ def fluxes(cfg, dt, f, W):
         sx[:, :2] = 0; sy[:, :2] = 0
     if kinds[1] == PRESSURE:
         sx[:, -2:] = 0; sy[:, -2:] = 0
+    if kinds[2] == PRESSURE:
+        sx[:2] = 0; sy[:2] = 0
+    if kinds[3] == PRESSURE:
+        sx[-2:] = 0; sy[-2:] = 0
 
     def face(un, ut, fL, snL, stL, WL, fR, snR, stR, WR, delta):
         H = np.where(un > 0, 1.0, np.where(un < 0, 0.0, 0.5))[:, None]
@@ -260,10 +277,17 @@ def fluxes(cfg, dt, f, W):
         for i in range(-1, nx):
             n = j * (nx + 1) + i + 1
             J, IL, IR = j + 2, i + 2, i + 3
-            if i == -1 and kinds[0] == WALL or i == nx - 1 and kinds[1] == WALL:
-                raise NotImplementedError
-            Fx[n], fx[n] = face(uq, vq, fe[J, IL], sx[J, IL], sy[J, IL], We[:, J, IL],
-                                fe[J, IR], sx[J, IR], sy[J, IR], We[:, J, IR], dx)
+            if i == -1 and kinds[0] == WALL:
+                bc = cfg.bc[0]  # gas on the high side of the face: interior value f - s dx/2
+                f_face = fe[J, IR] - sx[J, IR] * dx / 2
+                Fx[n], fx[n] = wall_face(cfg, dt, uq, vq, wq, f_face, True, bc.T, bc.U, K)
+            elif i == nx - 1 and kinds[1] == WALL:
+                bc = cfg.bc[1]  # gas on the low side: f + s dx/2
+                f_face = fe[J, IL] + sx[J, IL] * dx / 2
+                Fx[n], fx[n] = wall_face(cfg, dt, uq, vq, wq, f_face, False, bc.T, bc.U, K)
+            else:
+                Fx[n], fx[n] = face(uq, vq, fe[J, IL], sx[J, IL], sy[J, IL], We[:, J, IL],
+                                    fe[J, IR], sx[J, IR], sy[J, IR], We[:, J, IR], dx)
     rot = [0, 2, 1, 3]
     Fy = np.zeros((nx * (ny + 1), 4))
     fy = np.zeros((nx * (ny + 1), nq, 2))

@@ -87,6 +87,55 @@ def test_half_range_moments_against_quadrature(oracle, U, lam):
 
 
 # ---------------------------------------------------------------------------------
+# S3: collision time tau = mu / p against the hard-sphere and VHS viscosity laws
+# ---------------------------------------------------------------------------------
+def test_tau_hard_sphere_closed_form(oracle):
+    """Hard-sphere gas (omega = 1/2, alpha = 1): the reference viscosity for a mean free
+    path Kn (velocities in sqrt(2kT0/m), so sqrt(2 pi R T0) = sqrt(pi)) is Bird's
+    mu_ref = (5 sqrt(pi) / 16) Kn, and at rho = 1, T = 1 the pressure is p = 1/2, so
+    tau = mu / p = (5 sqrt(pi) / 8) Kn.  The values below are worked by hand:
+    5 sqrt(pi) / 16 = 0.5538918284...; Kn = 0.1 gives tau = 0.1107783656..."""
+    cfg = periodic_cfg(kn=0.1, omega=0.5, alpha=1.0)
+    assert abs(oracle.tau(cfg, 1.0, 1.0) - 0.11077836568) < 1e-11
+    # p = rho T / 2 and mu = mu_ref T^(1/2): tau = 2 mu_ref T^(-1/2) / rho
+    # (rho = 2, T = 4: tau = 2 * 0.05538918284 / 2 / 2 = 0.02769459142)
+    assert abs(oracle.tau(cfg, 2.0, 0.25) - 0.02769459142) < 1e-11
+
+
+@pytest.mark.parametrize("omega", [0.5, 0.74, 0.81])
+def test_tau_vhs_law(oracle, omega):
+    """Variable hard sphere (alpha = 1): Bird's VHS mean-free-path relation gives
+    mu_ref = 15 sqrt(pi) Kn / (2 (5 - 2 omega)(7 - 2 omega)); the viscosity scales as
+    T^omega and tau = mu / p with p = rho T / 2."""
+    kn, rho, T = 0.037, 1.3, 1.7
+    cfg = periodic_cfg(kn=kn, omega=omega, alpha=1.0)
+    mu_ref = 15 * math.sqrt(math.pi) * kn / (2 * (5 - 2 * omega) * (7 - 2 * omega))
+    want = mu_ref * T ** omega / (rho * T / 2)
+    assert abs(oracle.tau(cfg, rho, 1.0 / T) - want) < 1e-14 * want
+    # the temperature law alone: tau(T) / tau(1) = T^(omega - 1) at fixed rho
+    ratio = oracle.tau(cfg, rho, 1.0 / T) / oracle.tau(cfg, rho, 1.0)
+    assert abs(ratio - T ** (omega - 1)) < 1e-14
+
+
+# ---------------------------------------------------------------------------------
+# Time step from the CFL number
+# ---------------------------------------------------------------------------------
+def test_dt_hand_values(oracle):
+    """dt = CFL / (max|u|/dx + max|v|/dy), worked by hand.  The 40 x 20 channel on 5 x 1
+    with 20^2 velocities on [-4, 4]^2: dx = 0.125, dy = 0.05, max|u| = max|v| = 4, so
+    dt = 0.8 / (32 + 80) = 0.8 / 112."""
+    cfg = I.workload_channel_small()
+    assert abs(oracle.dt(cfg) - 0.8 / 112) < 1e-17
+    # an asymmetric grid: u in {-3, -2, -1, 0, 1} (max|u| = 3), v in {-0.5, 0.5, 1.5}
+    # (max|v| = 1.5); dx = 0.5, dy = 0.25: dt = 0.5 / (6 + 6) = 1/24
+    cfg = periodic_cfg(nx=4, ny=4, lx=2.0, ly=1.0, nu=5, nv=3, umin=-3, umax=1, vmin=-0.5,
+                       vmax=1.5, cfl=0.5)
+    assert abs(oracle.dt(cfg) - 1.0 / 24) < 1e-16
+    # a fixed dt overrides the CFL rule
+    assert oracle.dt(cfg.replace(dt=0.0123)) == 0.0123
+
+
+# ---------------------------------------------------------------------------------
 # S3: Mt1..Mt5 are the time integrals of the Eq. 2 weights (high-precision quadrature)
 # ---------------------------------------------------------------------------------
 @pytest.mark.parametrize("x", [1e-9, 1e-4, 0.01, 0.0999, 0.1, 0.1001, 0.5, 1.0, 5.0, 50.0, 600.0])
@@ -263,6 +312,16 @@ def test_bruteforce_channel_4x4(oracle):
     cfg = I.channel_config(nx=4, ny=4, n_vel=5, vrange=3.0, kn=0.1)
     cfg.bc[2] = I.BC(I.BC_WALL, T=1.2, U=0.1)
     f, W = random_state(oracle, cfg, 13, flow=0.2)
+    _compare_fluxes(oracle, cfg, f, W)
+
+
+def test_bruteforce_walls_x_pressure_y_4x4(oracle):
+    """The oracle's x-wall faces (gas on either side) and its y-pressure ghosts, including
+    the corner ghosts next to x-walls."""
+    cfg = periodic_cfg(nx=4, ny=4, nu=5, nv=6, kn=0.1)
+    cfg.bc = [I.BC(I.BC_WALL, T=1.15, U=-0.2), I.BC(I.BC_WALL, T=0.9, U=0.1),
+              I.BC(I.BC_PRESSURE, rho=1.2, T=1.1), I.BC(I.BC_PRESSURE, rho=0.95, T=1.0)]
+    f, W = random_state(oracle, cfg, 16, flow=0.2)
     _compare_fluxes(oracle, cfg, f, W)
 
 
