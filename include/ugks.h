@@ -238,9 +238,13 @@ ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms);
  * UGKS_NOALLOC_SCRATCH_BYTES bytes, that every GPU which loads the library holds until the
  * process exits.  Problems whose intermediates do not fit are rejected with UGKS_EINVAL and
  * a message on stderr; the need is about 32 (nx+4)(ny+4) nu nv + 1000 (nx+2)(ny+2) bytes.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress),
- * so make it before any stream capture.  Every call shares the array: calls that overlap
- * on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Every call made outside stream capture looks up that array's device address
+ * (cudaGetSymbolAddress), so a device reset or a recreated context is picked up by the
+ * next such call; a call made while its stream is being captured uses the address found by
+ * the last call outside capture on that device (none: UGKS_ECUDA).  So make the first call
+ * on a device, and the first call after a reset, before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
  * Errors: UGKS_EINVAL (bad or oversize cfg, NULL pointer), UGKS_ECUDA, UGKS_ENUMERIC. */
 #define UGKS_NOALLOC_SCRATCH_BYTES (64u << 20)
 ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const double* W_in,

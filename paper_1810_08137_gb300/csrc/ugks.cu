@@ -464,18 +464,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device, looked up once per device.
-cudaError_t noalloc_scratch(void** out) {
+// Device address of the scratch array on the current device.  Outside stream capture the
+// address is looked up on every call, so that a context that was torn down and created again
+// (cudaDeviceReset, or a host framework recreating the primary context) never leaves a stale
+// address behind: the module is loaded again there and the array may move.  While `st` is
+// being captured the lookup (which may load the module) is not made, and the address of the
+// last call outside capture on this device is used; with none the call fails.
+cudaError_t noalloc_scratch(cudaStream_t st, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();  // e.g. the legacy stream while another stream captures globally
+    cs = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = p;
+  } else if (!g_noalloc_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
@@ -583,7 +595,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
     return UGKS_EINVAL;
   }
   void* base = nullptr;
-  cudaError_t e = noalloc_scratch(&base);
+  cudaError_t e = noalloc_scratch(st, &base);
   if (e != cudaSuccess) {
     fprintf(stderr, "ugks_step_noalloc: scratch address: %s\n", cudaGetErrorString(e));
     return UGKS_ECUDA;
@@ -1375,7 +1387,15 @@ ugks_status ugks_batch_admit(ugks_batch b, const ugks_config* cfg, int* slot) {
   b->walk_rows[s] = cls_rows;
   ugks_status r = upload_slot(b, s);
   if (!r) r = upload_work(b);
-  if (r) return r;
+  if (r) {  // undo the admission: the caller gets no slot index to retire
+    const std::string msg = b->last_error;
+    cudaStreamSynchronize(b->stream);
+    b->used -= h->bytes;
+    ugks_destroy(h);
+    b->ctx[s] = nullptr;
+    upload_work(b);  // best effort: the table of the instances still admitted
+    return bfail(b, r, "admit: " + msg);
+  }
   *slot = s;
   return UGKS_OK;
 }
