@@ -45,8 +45,8 @@ typedef enum {
   UGKS_EINVAL = 1,    /* invalid argument or configuration */
   UGKS_ENOMEM = 2,    /* device allocation failed */
   UGKS_ECUDA = 3,     /* a CUDA runtime call failed */
-  UGKS_ETIMEOUT = 4,  /* reserved for a bounded device wait that gives up; no kernel of this
-                         version waits on another, so no call returns it */
+  UGKS_ETIMEOUT = 4,  /* a bounded device wait gave up (grid barrier of the batch's
+                         persistent step, ugks_batch_sync) */
   UGKS_ENUMERIC = 5   /* rho <= 0, T <= 0 or NaN appeared in a cell */
 } ugks_status;
 
@@ -58,14 +58,17 @@ typedef enum {
 
 typedef enum {
   UGKS_FP64 = 0,   /* f stored and transported in FP64, all arithmetic FP64 */
-  UGKS_FP32F = 1   /* f stored and transported in FP32 as f - g_ref; its velocity sums
-                      are FP32 and are combined in FP64 with the exact sums of g_ref; FP64
-                      for W, the interface terms first order in dt (interface W and
-                      primitive variables, Mt1, Mt4, equilibrium flux of g0, Mt4 S_f), the
-                      cell update coefficients and the exponents of the collision and wall
-                      Maxwellians relative to g_ref; FP32 for the terms that carry slopes
-                      (micro-slope solves and their Mt2, Mt3 terms, Mt5 S_sigma), formed
-                      from slopes of W differenced in FP64 */
+  UGKS_FP32F = 1   /* f stored and transported in FP32 as f - g_ref.  FP64 for: the
+                      velocity-space moment accumulation (FP32 products summed over chunks
+                      of at most 8 rows of one warp, every sum across chunks in FP64, then
+                      the exact FP64 sums of g_ref added), the interface scalars S2-S5 (W0,
+                      primitive variables, half-range moments, Mt1..Mt5 including the
+                      exp(-dt/tau) series at small tau, the micro-slope solves a_L, a_R, b, A,
+                      the macroscopic flux), the conservative W update (Eq. 4), the cell
+                      coefficients of Eq. 3 and the exponents of the collision and wall
+                      Maxwellians relative to g_ref.  FP32 for the per-velocity work on f:
+                      reconstruction, micro flux and the Eq. 3 update, from FP32 records of
+                      those FP64 coefficients */
 } ugks_precision;
 
 enum { UGKS_SIDE_W = 0, UGKS_SIDE_E = 1, UGKS_SIDE_S = 2, UGKS_SIDE_N = 3 };
@@ -176,10 +179,13 @@ const char* ugks_kernel_name(int i);
 size_t ugks_state_bytes(const ugks_config* cfg);
 
 /* ---- Batch of independent instances ------------------------------------------------
- * Many independent channel solves stepped together (the FP32-f form only): every kernel
- * of the step runs once per step for all active instances, as a persistent grid over a
+ * Many independent channel solves stepped together (the FP32-f form only): every phase of
+ * the step runs once per step for all active instances, as a persistent grid over a
  * device-resident table of (instance, tile) work items, and one step of the whole batch
- * is one CUDA graph replay.  Instances are admitted into free slots while the batch is in
+ * is one CUDA graph replay.  By default the step is ONE cooperative launch of a persistent
+ * kernel that runs the six phases (ghost x, ghost y, sums, interfaces, cells, walk) with a
+ * grid-wide barrier between them; ugks_batch_set_persistent(b, 0) selects seven phase
+ * launches instead (the same phase code and order of work).  Instances are admitted into free slots while the batch is in
  * use (admission checks an HBM budget) and retired when done; the table and each
  * instance's ping-pong parity live in device memory, so admission and retirement change
  * data, not the captured graph.  Each instance's results are bitwise those of the same
@@ -210,17 +216,36 @@ ugks_handle ugks_batch_instance(ugks_batch b, int slot);
 /* Advance every active instance by nsteps steps (one graph replay each).  Enqueued. */
 ugks_status ugks_batch_step(ugks_batch b, int nsteps);
 
-/* Wait for the batch's stream; UGKS_ENUMERIC if any instance recorded a failure. */
+/* Wait for the batch's stream; UGKS_ENUMERIC if any instance recorded a failure;
+ * UGKS_ETIMEOUT if a grid barrier of the persistent step gave up waiting since the last
+ * call (the flag is cleared; the instances' states are then undefined and must be set
+ * again before stepping). */
 ugks_status ugks_batch_sync(ugks_batch b);
 
-/* Tile shape of the f-update walk (rows per tile) for one slot; and the autotuner: for
- * each velocity-grid class present (nu*nv <= 576, <= 1600, <= 4096, larger) it times
- * trial_steps batch steps with 16, 32, 64 and 128 rows and keeps the fastest for that
- * class.  The tile shape does not change the arithmetic, so tuning steps are real steps
- * of every active instance (each advances by 4 * (trial_steps + 1) per class present).
- * *best_ms: time per batch step measured for the last class's chosen shape (may be NULL). */
+/* Step mode: enable != 0, one cooperative launch per step (the default where the device
+ * supports cooperative launch); 0, seven phase launches.  Synchronises; UGKS_EINVAL if
+ * cooperative launch is unavailable. */
+ugks_status ugks_batch_set_persistent(ugks_batch b, int enable);
+int         ugks_batch_get_persistent(ugks_batch b);
+
+/* Bound of every wait at the persistent step's grid barriers, in polls of about 0.13 us
+ * (default 8e6, about 1 s).  A block that waits longer, or that sees another block give
+ * up, ends the launch; ugks_batch_sync then reports UGKS_ETIMEOUT.  Synchronises. */
+ugks_status ugks_batch_set_wait_limit(ugks_batch b, unsigned long long polls);
+
+/* Tile shape of the f-update walk for one slot: the cell tile (rows per tile; a tile is
+ * 4 columns wide) and the velocity tile (chunks of 32 velocity slots walked by consecutive
+ * warps for the same cell tile; 0 = all chunks of the cell).  The autotuner: for each
+ * velocity-grid class present (nu*nv <= 576, <= 1600, <= 4096, larger) it times
+ * trial_steps batch steps for every cell tile of 16, 32, 64, 128 rows times velocity tile
+ * of all, 2 and 1 chunks, and keeps the fastest for that class.  The tile shape does not
+ * change the arithmetic, so tuning steps are real steps of every active instance (each
+ * advances by 12 (trial_steps + 1) per class present).  *best_ms: time per batch step
+ * measured for the last class's chosen shape (may be NULL). */
 ugks_status ugks_batch_set_walk_rows(ugks_batch b, int slot, int rows);
 int         ugks_batch_get_walk_rows(ugks_batch b, int slot);
+ugks_status ugks_batch_set_walk_vtile(ugks_batch b, int slot, int chunks);
+int         ugks_batch_get_walk_vtile(ugks_batch b, int slot);
 ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms);
 
 /* One FP64 UGKS step on caller-owned device buffers that allocates no device memory.

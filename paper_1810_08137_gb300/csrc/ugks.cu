@@ -254,13 +254,12 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   k_ghost_y<T2><<<dim3(P.nx + 4, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
   if ((r = mark(h, 2)) != cudaSuccess) return r;
   const int nce = (P.nx + 2) * (P.ny + 2);
-  T* sums = reinterpret_cast<T*>(h->sums);  // FP32 form: FP32 sums in the same buffer
+  double* sums = h->sums;
   k_sums<T, T2><<<(nce + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, smem_sums<T>(P.nv), st>>>(
       P, fi, sums, reinterpret_cast<T2*>(h->slopes));
   if ((r = mark(h, 3)) != cudaSuccess) return r;
   const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
-  k_faces<T><<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
-                                               h->fxf, h->fyf, h->mt4);
+  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy, h->mt4);
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   const int nc = P.nx * P.ny;
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
@@ -647,7 +646,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                             smem_sums<double>(P.nv), st>>>(P, f0, sums, nullptr);
-  k_faces<double><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4);
+  k_faces<<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
   // slopes are formed again in the update kernel: the scratch array holds no slope buffer
   k_update<double, double2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
@@ -1138,7 +1137,11 @@ struct ugks_batch_ctx {
   int max_slots = 0;
   size_t budget = 0, used = 0;
   std::vector<ugks_ctx*> ctx;       // per slot, nullptr when free
-  std::vector<int> walk_rows;       // per slot
+  std::vector<int> walk_rows;       // per slot: cell tile of the walk (rows)
+  std::vector<int> walk_vtile;      // per slot: velocity tile of the walk (chunks, 0 = all)
+  bool persistent = false;          // one cooperative launch per step (else phase launches)
+  int grid_step = 0;                // co-resident blocks of the persistent step kernel
+  BarrierDev* d_bar = nullptr;      // its grid barrier (count, gen, wait limit, timeout flag)
   SlotDev* d_slots = nullptr;
   BatchWork* d_work = nullptr;
   BatchWork h_work;
@@ -1149,7 +1152,7 @@ struct ugks_batch_ctx {
 
 namespace {
 
-constexpr size_t kBatchSumsSmem = sums_smem_bytes<float>();
+constexpr size_t kBatchSumsSmem = 0;  // the FP32-f sums kernel keeps its sums in registers
 // dynamic shared memory of the batch kernel of phase p
 constexpr size_t phase_smem(int p) { return p == 2 ? kBatchSumsSmem : (p == 5 ? kStripSmem : 0); }
 
@@ -1164,7 +1167,7 @@ ugks_status bfail(ugks_batch_ctx* b, ugks_status s, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, UGKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-SlotDev slot_desc(const ugks_ctx* h, int walk_rows) {
+SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile = 0) {
   SlotDev S;
   memset(&S, 0, sizeof S);
   S.P = h->P;
@@ -1172,7 +1175,7 @@ SlotDev slot_desc(const ugks_ctx* h, int walk_rows) {
   S.f[1] = static_cast<float4*>(h->f[1]);
   S.W[0] = h->W[0];
   S.W[1] = h->W[1];
-  S.sums = reinterpret_cast<float*>(h->sums);
+  S.sums = h->sums;
   S.fxf = h->fxf;
   S.fyf = h->fyf;
   S.cellf = h->cellf;
@@ -1186,6 +1189,7 @@ SlotDev slot_desc(const ugks_ctx* h, int walk_rows) {
   S.nchunk_neg = h->nchunk_neg;
   S.nchunk_pos = h->nchunk_pos;
   S.walk_rows = walk_rows;
+  S.walk_vtile = walk_vtile;
   S.cur = h->cur;
   return S;
 }
@@ -1197,7 +1201,7 @@ ugks_status upload_work(ugks_batch_ctx* b) {
   for (int p = 0; p < kPhases; p++) w.start[p][0] = 0;
   for (int s = 0; s < b->max_slots; s++) {
     if (!b->ctx[s]) continue;
-    const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s]);
+    const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s], b->walk_vtile[s]);
     const int a = w.n++;
     w.slot[a] = s;
     for (int p = 0; p < kPhases; p++) {
@@ -1212,13 +1216,30 @@ ugks_status upload_work(ugks_batch_ctx* b) {
 }
 
 ugks_status upload_slot(ugks_batch_ctx* b, int s) {
-  const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s]);
+  const SlotDev S = slot_desc(b->ctx[s], b->walk_rows[s], b->walk_vtile[s]);
   BCK(cudaMemcpyAsync(b->d_slots + s, &S, sizeof(SlotDev), cudaMemcpyHostToDevice, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   return UGKS_OK;
 }
 
 cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
+  if (b->persistent) {
+    // one cooperative launch: every block is resident, so the grid barriers can complete
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof lc);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.gridDim = dim3(b->grid_step);
+    lc.blockDim = dim3(128);
+    lc.dynamicSmemBytes = kStepSmem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kb_step, b->d_slots, (const BatchWork*)b->d_work, b->d_bar);
+  }
   kb_ghost_x<<<b->grid[0], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_ghost_y<<<b->grid[1], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_sums<<<b->grid[2], 128, kBatchSumsSmem, st>>>(b->d_slots, b->d_work);
@@ -1297,6 +1318,9 @@ cudaError_t capture_batch(ugks_batch_ctx* b) {
   return e;
 }
 
+// Default wait of the persistent step's grid barriers: about 1 s of 128 ns polls.
+constexpr unsigned long long kDefaultWaitPolls = 8000000ull;
+
 int velocity_class(const ugks_config& c) {
   const int nq = c.nu * c.nv;
   return nq <= 576 ? 0 : (nq <= 1600 ? 1 : (nq <= 4096 ? 2 : 3));
@@ -1319,6 +1343,7 @@ ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_strea
   b->budget = hbm_budget;
   b->ctx.assign(max_slots, nullptr);
   b->walk_rows.assign(max_slots, kWalkRows);
+  b->walk_vtile.assign(max_slots, 0);
   memset(&b->h_work, 0, sizeof(BatchWork));
   cudaError_t e = cudaMalloc((void**)&b->d_slots, sizeof(SlotDev) * max_slots);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_work, sizeof(BatchWork));
@@ -1335,6 +1360,23 @@ ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_strea
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fns[p], 128, phase_smem(p));
     b->grid[p] = (nb > 0 ? nb : 1) * sms;
+  }
+  // persistent step: every block must be resident at once (cooperative launch)
+  int coop = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmem);
+  if (e == cudaSuccess) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kb_step, 128, kStepSmem);
+    b->grid_step = nb * sms;
+    b->persistent = coop && nb > 0;
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_bar, sizeof(BarrierDev));
+  if (e == cudaSuccess) {
+    BarrierDev bar;
+    memset(&bar, 0, sizeof bar);
+    bar.limit = kDefaultWaitPolls;
+    e = cudaMemcpyAsync(b->d_bar, &bar, sizeof bar, cudaMemcpyHostToDevice, b->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -1358,6 +1400,7 @@ void ugks_batch_destroy(ugks_batch b) {
   }
   if (b->d_slots) cudaFree(b->d_slots);
   if (b->d_work) cudaFree(b->d_work);
+  if (b->d_bar) cudaFree(b->d_bar);
   delete b;
 }
 
@@ -1381,10 +1424,14 @@ ugks_status ugks_batch_admit(ugks_batch b, const ugks_config* cfg, int* slot) {
   if (st) return bfail(b, st, "admit: instance allocation failed");
   b->ctx[s] = h;
   b->used += h->bytes;
-  int cls_rows = kWalkRows;
+  int cls_rows = kWalkRows, cls_vt = 0;
   for (int k = 0; k < b->max_slots; k++)  // tuned tile of the same velocity class, if any
-    if (k != s && b->ctx[k] && velocity_class(b->ctx[k]->cfg) == velocity_class(*cfg)) cls_rows = b->walk_rows[k];
+    if (k != s && b->ctx[k] && velocity_class(b->ctx[k]->cfg) == velocity_class(*cfg)) {
+      cls_rows = b->walk_rows[k];
+      cls_vt = b->walk_vtile[k];
+    }
   b->walk_rows[s] = cls_rows;
+  b->walk_vtile[s] = cls_vt;
   ugks_status r = upload_slot(b, s);
   if (!r) r = upload_work(b);
   if (r) {  // undo the admission: the caller gets no slot index to retire
@@ -1431,6 +1478,22 @@ ugks_status ugks_batch_step(ugks_batch b, int nsteps) {
 ugks_status ugks_batch_sync(ugks_batch b) {
   if (!b) return UGKS_EINVAL;
   BCK(cudaStreamSynchronize(b->stream));
+  int berr = 0;
+  BCK(cudaMemcpy(&berr, &b->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (berr) {
+    BCK(cudaMemset(&b->d_bar->err, 0, sizeof(int)));
+    // an interrupted launch did not flip the instances' buffers on the device: take each
+    // instance's parity back from the device so that state I/O addresses the right buffer
+    for (int s = 0; s < b->max_slots; s++)
+      if (b->ctx[s]) {
+        int cur = 0;
+        BCK(cudaMemcpy(&cur, &b->d_slots[s].cur, sizeof(int), cudaMemcpyDeviceToHost));
+        b->ctx[s]->cur = cur;
+      }
+    return bfail(b, UGKS_ETIMEOUT,
+                 "a grid barrier of the persistent step gave up waiting; the instances' states "
+                 "are undefined (set them again)");
+  }
   for (ugks_ctx* h : b->ctx)
     if (h) {
       const ugks_status s = check_err(h);
@@ -1450,51 +1513,88 @@ int ugks_batch_get_walk_rows(ugks_batch b, int slot) {
   return (b && slot >= 0 && slot < b->max_slots && b->ctx[slot]) ? b->walk_rows[slot] : 0;
 }
 
+ugks_status ugks_batch_set_walk_vtile(ugks_batch b, int slot, int chunks) {
+  if (!b || slot < 0 || slot >= b->max_slots || !b->ctx[slot] || chunks < 0)
+    return bfail(b, UGKS_EINVAL, "bad velocity tile");
+  b->walk_vtile[slot] = chunks;
+  ugks_status r = upload_slot(b, slot);
+  return r ? r : upload_work(b);
+}
+
+int ugks_batch_get_walk_vtile(ugks_batch b, int slot) {
+  return (b && slot >= 0 && slot < b->max_slots && b->ctx[slot]) ? b->walk_vtile[slot] : -1;
+}
+
+ugks_status ugks_batch_set_persistent(ugks_batch b, int enable) {
+  if (!b) return UGKS_EINVAL;
+  if (enable && !(b->grid_step > 0))
+    return bfail(b, UGKS_EINVAL, "persistent step: cooperative launch unavailable on this device");
+  BCK(cudaStreamSynchronize(b->stream));
+  if ((enable != 0) != b->persistent && b->graph) {
+    cudaGraphExecDestroy(b->graph);  // captured again at the next step
+    b->graph = nullptr;
+  }
+  b->persistent = enable != 0;
+  return UGKS_OK;
+}
+
+int ugks_batch_get_persistent(ugks_batch b) { return b && b->persistent ? 1 : 0; }
+
+ugks_status ugks_batch_set_wait_limit(ugks_batch b, unsigned long long polls) {
+  if (!b) return UGKS_EINVAL;
+  BCK(cudaStreamSynchronize(b->stream));
+  BCK(cudaMemcpy(&b->d_bar->limit, &polls, sizeof polls, cudaMemcpyHostToDevice));
+  return UGKS_OK;
+}
+
 ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms) {
   if (!b || trial_steps < 1) return bfail(b, UGKS_EINVAL, "tune: bad argument");
-  static const int cand[4] = {16, 32, 64, 128};
+  // cell tile (rows of the walk) x velocity tile (32-slot chunks per tile, 0 = all)
+  static const int cand_rows[4] = {16, 32, 64, 128};
+  static const int cand_vt[3] = {0, 2, 1};
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   float best_total = 0.f;
-  for (int cls = 0; cls < 4; cls++) {
+  ugks_status r = UGKS_OK;
+  for (int cls = 0; cls < 4 && !r; cls++) {
     bool any = false;
     for (int s = 0; s < b->max_slots; s++) any |= b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls;
     if (!any) continue;
-    int best = kWalkRows;
+    int best_r = kWalkRows, best_v = 0;
     float best_t = 1e30f;
-    for (int c = 0; c < 4; c++) {
+    auto apply = [&](int rows, int vt) -> ugks_status {
       for (int s = 0; s < b->max_slots; s++)
         if (b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls) {
-          b->walk_rows[s] = cand[c];
-          ugks_status r = upload_slot(b, s);
-          if (r) return r;
+          b->walk_rows[s] = rows;
+          b->walk_vtile[s] = vt;
+          const ugks_status q = upload_slot(b, s);
+          if (q) return q;
         }
-      ugks_status r = upload_work(b);
-      if (r) return r;
-      r = ugks_batch_step(b, 1);  // warm-up of this shape
-      if (r) return r;
-      BCK(cudaEventRecord(e0, b->stream));
-      r = ugks_batch_step(b, trial_steps);
-      if (r) return r;
-      BCK(cudaEventRecord(e1, b->stream));
-      BCK(cudaEventSynchronize(e1));
-      float t = 0.f;
-      BCK(cudaEventElapsedTime(&t, e0, e1));
-      if (t < best_t) { best_t = t; best = cand[c]; }
-    }
-    for (int s = 0; s < b->max_slots; s++)
-      if (b->ctx[s] && velocity_class(b->ctx[s]->cfg) == cls) {
-        b->walk_rows[s] = best;
-        ugks_status r = upload_slot(b, s);
-        if (r) return r;
+      return upload_work(b);
+    };
+    for (int ci = 0; ci < 4 && !r; ci++)
+      for (int vi = 0; vi < 3 && !r; vi++) {
+        if ((r = apply(cand_rows[ci], cand_vt[vi]))) break;
+        if ((r = ugks_batch_step(b, 1))) break;  // warm-up of this shape
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) { r = bfail(b, UGKS_ECUDA, "tune: event"); break; }
+        if ((r = ugks_batch_step(b, trial_steps))) break;
+        float t = 0.f;
+        if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+          r = bfail(b, UGKS_ECUDA, "tune: timing");
+          break;
+        }
+        if (t < best_t) { best_t = t; best_r = cand_rows[ci]; best_v = cand_vt[vi]; }
       }
+    if (!r) r = apply(best_r, best_v);
     best_total = best_t / trial_steps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (r) return r;
   if (best_ms) *best_ms = best_total;
-  return upload_work(b);
+  return ugks_batch_sync(b);
 }
 
 }  // extern "C"

@@ -1,8 +1,10 @@
-// Batched execution of many independent UGKS instances (FP32-f form): every kernel of the
+// Batched execution of many independent UGKS instances (FP32-f form): every phase of the
 // step runs once per step for all active instances, as a persistent grid that walks a
-// device-resident work table of virtual blocks, and the whole step is one CUDA graph
-// replay.  The table (and each instance's ping-pong parity) lives in device memory, so
-// admitting or retiring an instance changes data, not the captured graph.
+// device-resident work table of virtual blocks.  The step is either one cooperative launch
+// of kb_step (all phases, grid barriers with bounded waits between them) or seven phase
+// launches; either way one CUDA graph replay.  The table (and each instance's ping-pong
+// parity) lives in device memory, so admitting or retiring an instance changes data, not
+// the captured graph.
 // Included by ugks.cu (same translation unit as the single-instance kernels).
 #pragma once
 
@@ -16,7 +18,7 @@ struct SlotDev {
   Params P;
   float4* f[2];
   double* W[2];
-  float* sums;
+  double* sums;
   FaceRecF* fxf;
   FaceRecF* fyf;
   CellRecF* cellf;
@@ -26,7 +28,8 @@ struct SlotDev {
   double* rpart;
   int* err;
   int nwe, nrblocks, nchunk_neg, nchunk_pos;
-  int walk_rows;   // tile rows of the walk kernel (autotuned per velocity-grid class)
+  int walk_rows;   // cell tile of the walk: rows per tile (autotuned per velocity-grid class)
+  int walk_vtile;  // velocity tile of the walk: 32-slot chunks per tile, 0 = all (autotuned)
   int cur;         // ping-pong parity, flipped on the device after every step
 };
 
@@ -65,52 +68,51 @@ __device__ __forceinline__ int find_instance(const int* start, int n, int vb) {
   return lo;
 }
 
-__global__ void kb_ghost_x(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+// ---- phase bodies: one pass of a phase over the whole work table, grid-strided ----------
+__device__ __forceinline__ void ghost_x_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                              double* tab) {
   const int total = wk->start[0][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[0], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     const int loc = vb - wk->start[0][a], c = S.cur;
-    ghost_x_body(S.P, S.f[c], S.W[c], S.nwe, loc % S.P.ny, loc / S.P.ny);
+    ghost_x_body(S.P, S.f[c], S.W[c], S.nwe, loc % S.P.ny, loc / S.P.ny, tab);
   }
 }
 
-__global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+__device__ __forceinline__ void ghost_y_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                              double* tab) {
   const int total = wk->start[1][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[1], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     const int loc = vb - wk->start[1][a], c = S.cur, w = S.P.nx + 4;
-    ghost_y_body(S.P, S.f[c], S.W[c], S.nwe, loc % w, loc / w);
+    ghost_y_body(S.P, S.f[c], S.W[c], S.nwe, loc % w, loc / w, tab);
   }
 }
 
-__global__ void __launch_bounds__(128, 5) kb_sums(const SlotDev* __restrict__ slots,
-                                               const BatchWork* __restrict__ wk) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void sums_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
   const int total = wk->start[2][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    sums_body_p(S.P, S.f[S.cur], S.sums, smraw, vb - wk->start[2][a]);
+    sums_body_p(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a]);
   }
 }
 
-__global__ void __launch_bounds__(128) kb_faces(const SlotDev* __restrict__ slots,
-                                                const BatchWork* __restrict__ wk) {
+__device__ __forceinline__ void faces_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
   const int total = wk->start[3][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[3], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     const int loc = vb - wk->start[3][a];
-    faces_body<float>(S.P, S.sums, S.W[S.cur], S.nwe, nullptr, nullptr, S.Fx, S.Fy, S.fxf, S.fyf,
-                      S.mt4, loc * 128 + threadIdx.x);
+    faces_body<true>(S.P, S.sums, S.W[S.cur], S.nwe, nullptr, nullptr, S.Fx, S.Fy, S.fxf, S.fyf,
+                     S.mt4, loc * 128 + threadIdx.x);
   }
 }
 
-__global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slots,
-                                                const BatchWork* __restrict__ wk) {
-  __shared__ double red[8][128];
+__device__ __forceinline__ void cells_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                            double (*red)[128]) {
   const int total = wk->start[4][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     __syncthreads();  // red[] of the previous virtual block has been read
@@ -122,10 +124,31 @@ __global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slot
   }
 }
 
-// Update sweep: one warp per work item (strip, tile, velocity chunk).
-__global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ slots,
-                                                const BatchWork* __restrict__ wk) {
-  extern __shared__ __align__(16) float4 strip_sm[];  // kStripSmem bytes
+// Work item `it` of an instance's walk -> (strip bx, row tile by, velocity chunk ck).  The
+// chunks are grouped into velocity tiles of walk_vtile chunks (0: all chunks of the cell);
+// items run velocity tile slowest, then row tile, then strip, chunk of the tile fastest, so
+// that consecutive warps (the warps of a block) walk the same strip and rows for the chunks
+// of one velocity tile (sharing its face and cell records in L1), and a tile of one chunk
+// puts adjacent strips on consecutive warps (sharing f halo columns instead).
+__device__ __forceinline__ void walk_item(const SlotDev& S, int ns, int nt, int it, int& bx, int& by, int& ck) {
+  const int nch = S.nchunk_neg + S.nchunk_pos;
+  const int vt = (S.walk_vtile > 0 && S.walk_vtile < nch) ? S.walk_vtile : nch;
+  const int per = nt * ns * vt;  // items of a full velocity tile
+  const int nvt = (nch + vt - 1) / vt;
+  int t = it / per;
+  if (t > nvt - 1) t = nvt - 1;
+  int rem = it - t * per;
+  const int vts = (t == nvt - 1) ? nch - t * vt : vt;  // chunks of this velocity tile
+  const int c = rem % vts;
+  rem /= vts;
+  bx = rem % ns;
+  by = rem / ns;
+  ck = t * vt + c;
+}
+
+// Update sweep: one warp per work item (strip, row tile, velocity chunk).
+__device__ __forceinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                            float4* strip_sm) {
   const int warp = threadIdx.x >> 5;
   const int total = wk->start[5][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -136,8 +159,8 @@ __global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ s
     const int nch = S.nchunk_neg + S.nchunk_pos;
     if (it < ns * nt * nch) {
       const int c = S.cur;
-      // velocity chunks fastest: the warps of a block share the strip's records and halo
-      const int bx = (it / nch) % ns, by = it / (nch * ns), ck = it % nch;
+      int bx, by, ck;
+      walk_item(S, ns, nt, it, bx, by, ck);
       // full strips (all but the last of a row when kStripW does not divide nx) with the
       // strip width known at compile time
       if ((bx + 1) * kStripW <= S.P.nx)
@@ -150,9 +173,118 @@ __global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ s
   }
 }
 
+// ---- one kernel per phase (the step as a graph of seven launches) ------------------------
+__global__ void kb_ghost_x(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+  __shared__ double tab[kGhostTab];
+  ghost_x_phase(slots, wk, tab);
+}
+
+__global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+  __shared__ double tab[kGhostTab];
+  ghost_y_phase(slots, wk, tab);
+}
+
+__global__ void __launch_bounds__(128, 5) kb_sums(const SlotDev* __restrict__ slots,
+                                               const BatchWork* __restrict__ wk) {
+  sums_phase(slots, wk);
+}
+
+__global__ void __launch_bounds__(128) kb_faces(const SlotDev* __restrict__ slots,
+                                                const BatchWork* __restrict__ wk) {
+  faces_phase(slots, wk);
+}
+
+__global__ void __launch_bounds__(128) kb_cells(const SlotDev* __restrict__ slots,
+                                                const BatchWork* __restrict__ wk) {
+  __shared__ double red[8][128];
+  cells_phase(slots, wk, red);
+}
+
+__global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ slots,
+                                                const BatchWork* __restrict__ wk) {
+  extern __shared__ __align__(16) float4 strip_sm[];  // kStripSmem bytes
+  strip_phase(slots, wk, strip_sm);
+}
+
 // After the step: every active instance swaps its buffers.
 __global__ void kb_flip(SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
   for (int a = threadIdx.x; a < wk->n; a += blockDim.x) slots[wk->slot[a]].cur ^= 1;
+}
+
+// ---- the whole step as one persistent cooperative launch ---------------------------------
+// Grid-wide barrier between the phases, with a bounded wait: a block that has waited
+// `limit` polls (about 0.13 us each) without the generation advancing, or that sees another
+// block's timeout, records kBarrierTimeout in `err` and the whole grid leaves the kernel at
+// that barrier (the host reports UGKS_ETIMEOUT).  No phase has copies in flight at a
+// barrier (the walk waits for its own cp.async groups before it returns).  count and gen
+// are zeroed before every launch; limit and err persist.
+struct BarrierDev {
+  unsigned int count;       // blocks arrived at the current barrier
+  unsigned int gen;         // barriers completed in this launch
+  unsigned long long limit; // polls before a block gives up
+  int err;                  // kBarrierTimeout once any block gave up (cleared by the host)
+  int pad;
+};
+constexpr int kBarrierTimeout = 1;
+
+__device__ __forceinline__ bool grid_sync(BarrierDev* g) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile BarrierDev* vg = g;
+    const unsigned int gen = vg->gen;
+    __threadfence();  // this block's results are visible before it arrives
+    const unsigned int arrived = atomicAdd(&g->count, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const unsigned long long limit = vg->limit;
+      unsigned long long n = 0;
+      while (vg->gen == gen) {
+        if (vg->err != 0 || n >= limit) {
+          atomicOr(&g->err, kBarrierTimeout);
+          good = 0;
+          break;
+        }
+        n++;
+        __nanosleep(128);
+      }
+    }
+    __threadfence();  // the other blocks' results are visible after it
+    ok = good && vg->err == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// dynamic shared memory of the persistent step: the largest phase's (the walk's rings; the
+// ghost tables and the cells reduction alias its start)
+constexpr size_t kStepSmem = kStripSmem;
+static_assert(kStepSmem >= sizeof(double) * kGhostTab && kStepSmem >= sizeof(double) * 8 * 128,
+              "persistent step: shared memory of every phase");
+
+__global__ void __launch_bounds__(128, 3) kb_step(SlotDev* __restrict__ slots,
+                                               const BatchWork* __restrict__ wk,
+                                               BarrierDev* __restrict__ bar) {
+  extern __shared__ __align__(16) float4 step_sm[];
+  double* tab = reinterpret_cast<double*>(step_sm);
+  ghost_x_phase(slots, wk, tab);
+  if (!grid_sync(bar)) return;
+  ghost_y_phase(slots, wk, tab);
+  if (!grid_sync(bar)) return;
+  sums_phase(slots, wk);
+  if (!grid_sync(bar)) return;
+  faces_phase(slots, wk);
+  if (!grid_sync(bar)) return;
+  cells_phase(slots, wk, reinterpret_cast<double(*)[128]>(step_sm));
+  if (!grid_sync(bar)) return;
+  strip_phase(slots, wk, step_sm);
+  if (!grid_sync(bar)) return;
+  if (blockIdx.x == 0)
+    for (int a = threadIdx.x; a < wk->n; a += blockDim.x) slots[wk->slot[a]].cur ^= 1;
 }
 
 }  // namespace ugks

@@ -70,13 +70,17 @@ __host__ __device__ __forceinline__ int padrow(const Params& P, int m) {
 // image, zero-gradient copy next to a wall), over the slots of the paired layout.
 // -------------------------------------------------------------------------------------
 __device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, int gi, int gj,
-                                int si, int sj, int side, bool write_W, int wi, int wj) {
+                                int si, int sj, int side, bool write_W, int wi, int wj,
+                                double* tab) {
   const int kind = P.bc_kind[side];
   float4* dst = f + fcell(P, gi, gj) * P.fs;
   const float4* src = f + fcell(P, si, sj) * P.fs;
   const int sw = wcell(P, wi, wj);
   if (kind == 2) {
-    __shared__ double fu[kMaxAxis], fv[kMaxAxis], ru[kMaxAxis], rv[kMaxAxis];
+    double* fu = tab;
+    double* fv = tab + kMaxAxis;
+    double* ru = tab + 2 * kMaxAxis;
+    double* rv = tab + 3 * kMaxAxis;
     const double rho_a = W[sw], U = W[nwe + sw] / rho_a, V = W[2 * nwe + sw] / rho_a;
     const double lam = 1.0 / P.bc_T[side], rho = P.bc_rho[side];
     const double G = rho * lam / kPi, bf = P.K / (2.0 * lam);
@@ -118,24 +122,102 @@ __device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, 
 
 // -------------------------------------------------------------------------------------
 // S1 + S7: per-cell half-range velocity sums (the sums of the FP64 form's sums_body, same
-// output layout), one warp per cell, lane = u index (chunks of 32), loop over row pairs.
-// Per lane and half of the v axis, with w_n = wv v^n, the weighted sums of the cell value c,
-// the x half slope r_x and the y half slope r_y:
+// output layout, FP64), one warp per cell, lane = u index (chunks of 32), loop over row
+// pairs.  Per lane and half of the v axis, with w_n = wv v^n, the weighted sums of the cell
+// value c, the x half slope r_x and the y half slope r_y:
 //   a_n = sum w_n c_h (n < 4), ab_n = sum w_n c_b (n < 2), x_n = sum w_n r_x,h (n < 4),
 //   xb_n = sum w_n r_x,b (n < 2), y_n = sum w_n r_y,h (n < 5), yb_n = sum w_n r_y,b (n < 3),
 // accumulated over both rows of each pair.
+// Precision: these FP32 sums run over a chunk of at most kSumChunkPairs row pairs
+// (2 kSumChunkPairs rows); at the end of each chunk the warp weights them by the lane's u
+// terms and reduces them across its lanes in FP32, and each lane adds the face sums it owns
+// (one E/W value, and for lanes < 16 one N and one S value) to FP64 accumulators.  So FP32
+// rounding acts within a chunk of one warp (at most 2 kSumChunkPairs rows x 32 lanes of the
+// deviation e = f - g_ref), and every sum across chunks, velocity chunks and halves is FP64.
 // The v = 0 row (H(0) = 1/2) enters both halves with half weight: the weight table carries
 // its half weight in the v >= 0 half and its part of the v < 0 half is added separately.
 // -------------------------------------------------------------------------------------
-__device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
-                                            float* __restrict__ sums, unsigned char* smraw, int bx) {
-  const int nu = P.nu, fs = P.fs;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* wsum = reinterpret_cast<float*>(smraw) + warp * kNSum;
-  float* tot = reinterpret_cast<float*>(smraw + kWarpsPerBlock * kNSum * sizeof(float)) + tid;
-  for (int t = lane; t < kNSum; t += 32) wsum[t] = 0.f;
-  __syncwarp();
+constexpr int kSumChunkPairs = 4;  // row pairs (2 rows each) per FP32 chunk
 
+// The chunk's contribution to the 16 face sums of the y side of its half (sy = +1: N side,
+// -1: S side), from the per-lane FP32 chunk sums; summed over the warp, entry lane % 16.
+__device__ __forceinline__ float chunk_y_sums(float u, float wu, float cu, float tdx, float tdy, float sy,
+                                              float a0, float a1, float a2, float a3, float ab0, float ab1,
+                                              float x0, float x1, float x2, float x3, float xb0, float xb1,
+                                              float y0, float y1, float y2, float y3, float y4, float yb0,
+                                              float yb1, float yb2, int lane) {
+  // face values of the half: c -/+ r_y; free-transport slope sums: cu x_n + (2/dy) y_{n+1}
+  const float P0 = a0 + sy * y0, P1 = a1 + sy * y1, P2 = a2 + sy * y2, P3 = a3 + sy * y3;
+  const float Pb0 = ab0 + sy * yb0, Pb1 = ab1 + sy * yb1;
+  const float Z1 = cu * x1 + tdy * y2, Z2 = cu * x2 + tdy * y3, Z3 = cu * x3 + tdy * y4;
+  const float Zb1 = cu * xb1 + tdy * yb2;
+  float v[16];
+  const float uu = u * u;
+  v[0] = wu * P0;
+  v[1] = wu * u * P0;
+  v[2] = wu * P1;
+  v[3] = wu * (0.5f * (uu * P0 + P2) + 0.5f * Pb0);
+  const float ws = wu * tdx;
+  v[4] = ws * x0;
+  v[5] = ws * u * x0;
+  v[6] = ws * x1;
+  v[7] = ws * (0.5f * (uu * x0 + x2) + 0.5f * xb0);
+  v[8] = wu * P1;
+  v[9] = wu * u * P1;
+  v[10] = wu * P2;
+  v[11] = wu * (0.5f * (uu * P1 + P3) + 0.5f * Pb1);
+  v[12] = wu * Z1;
+  v[13] = wu * u * Z1;
+  v[14] = wu * Z2;
+  v[15] = wu * (0.5f * (uu * Z1 + Z3) + 0.5f * Zb1);
+  return warp_reduce_scatter<16>(v, lane);
+}
+
+// The chunk's contribution to the 32 face sums of the x sides (E: entries 0..15 from u > 0
+// with f + r_x, W: 16..31 from u < 0 with f - r_x, u = 0 half to each); entry lane.
+__device__ __forceinline__ float chunk_x_sums(float u, float wu, float cu, float tdy,
+                                              float a0, float a1, float a2, float ab0,
+                                              float x0, float x1, float x2, float xb0,
+                                              float y0, float y1, float y2, float y3, float yb0,
+                                              float yb1, int lane) {
+  const float D0 = cu * x0 + tdy * y1, D1 = cu * x1 + tdy * y2, D2 = cu * x2 + tdy * y3;
+  const float Db = cu * xb0 + tdy * yb1;
+  const float hE = u > 0.f ? 1.f : (u < 0.f ? 0.f : 0.5f);
+  const float hW = u < 0.f ? 1.f : (u > 0.f ? 0.f : 0.5f);
+  float xv[32];
+  const float uu = u * u;
+#pragma unroll
+  for (int sd = 0; sd < 2; sd++) {
+    const float sg = sd == 0 ? 1.f : -1.f;
+    const float wgt = wu * (sd == 0 ? hE : hW);
+    const float F0 = a0 + sg * x0, F1 = a1 + sg * x1, F2 = a2 + sg * x2, Fb = ab0 + sg * xb0;
+    float* o = xv + 16 * sd;
+    o[0] = wgt * F0;
+    o[1] = wgt * u * F0;
+    o[2] = wgt * F1;
+    o[3] = wgt * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+    const float ws = wgt * tdy;
+    o[4] = ws * y0;
+    o[5] = ws * u * y0;
+    o[6] = ws * y1;
+    o[7] = ws * (0.5f * (uu * y0 + y2) + 0.5f * yb0);
+    const float wuu = wgt * u;
+    o[8] = wuu * F0;
+    o[9] = wuu * u * F0;
+    o[10] = wuu * F1;
+    o[11] = wuu * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+    o[12] = wuu * D0;
+    o[13] = wuu * u * D0;
+    o[14] = wuu * D1;
+    o[15] = wuu * (0.5f * (uu * D0 + D2) + 0.5f * Db);
+  }
+  return warp_reduce_scatter<32>(xv, lane);
+}
+
+__device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
+                                            double* __restrict__ sums, int bx) {
+  const int nu = P.nu, fs = P.fs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncx = P.nx + 2;
   const int cell = bx * kWarpsPerBlock + warp;
   if (cell >= ncx * (P.ny + 2)) return;
@@ -156,6 +238,8 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
   const int pn = P.pr_neg, pa = P.pr_all;
   const bool v0 = P.m_pos > P.m_neg;
   const float4* wt = P.pwt;
+  // FP64 face sums owned by this lane: E/W entry `lane`; N and S entries `lane` (lane < 16)
+  double sx = 0.0, sn = 0.0, ss = 0.0;
 
   for (int k0 = 0; k0 < nu; k0 += 32) {
     const int k = k0 + lane;
@@ -164,8 +248,6 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     const float u = P.uwf[kk];
     const float wu = act ? P.uwf[nu + kk] : 0.f;
     const float cu = u * tdx;
-#pragma unroll
-    for (int t = 0; t < kSumsTotals; t++) tot[t * 128] = 0.f;
     float a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
     auto zero = [&]() {
       a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = 0.f;
@@ -199,20 +281,14 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
       acc(y0, w0, ry.h); acc(y1, w1, ry.h); acc(y2, w2, ry.h); acc(y3, w3, ry.h); acc(y4, w4, ry.h);
       acc(yb0, w0, ry.b); acc(yb1, w1, ry.b); acc(yb2, w2, ry.b);
     };
-    // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
-    auto close = [&](float sy, float* side) {
-      const float A0 = a0, A1 = a1, A2 = a2, A3 = a3, AB0 = ab0, AB1 = ab1;
-      const float X0 = x0, X1 = x1, X2 = x2, X3 = x3, XB0 = xb0, XB1 = xb1;
-      const float Y0 = y0, Y1 = y1, Y2 = y2, Y3 = y3, Y4 = y4, YB0 = yb0, YB1 = yb1, YB2 = yb2;
-      const float P0 = A0 + sy * Y0, P1 = A1 + sy * Y1, P2 = A2 + sy * Y2, P3 = A3 + sy * Y3;
-      const float Pb0 = AB0 + sy * YB0, Pb1 = AB1 + sy * YB1;
-      const float Z1 = cu * X1 + tdy * Y2, Z2 = cu * X2 + tdy * Y3, Z3 = cu * X3 + tdy * Y4;
-      const float Zb1 = cu * XB1 + tdy * YB2;
-      finalize_y<float, float2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, X0, X1, X2, XB0, Z1, Z2, Z3, Zb1,
-                                lane, side);
-      const float h[kSumsTotals] = {A0, A1, A2, AB0, X0, X1, X2, XB0, Y0, Y1, Y2, Y3, YB0, YB1};
-#pragma unroll
-      for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
+    // end of a chunk of the half whose y side is sy: warp sums in FP32, then FP64
+    auto flush = [&](float sy, double& sside) {
+      const float ry = chunk_y_sums(u, wu, cu, tdx, tdy, sy, a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3,
+                                    xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2, lane);
+      const float rx = chunk_x_sums(u, wu, cu, tdy, a0, a1, a2, ab0, x0, x1, x2, xb0, y0, y1, y2, y3,
+                                    yb0, yb1, lane);
+      sside += (double)ry;
+      sx += (double)rx;
     };
     // the v >= 0 half (pairs pn .. pa - 1), then the v < 0 half (pairs 0 .. pn - 1); the first
     // v >= 0 pair holds the v = 0 row (if any) as its first row
@@ -228,69 +304,48 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
         s0h = hw * q.c.h.x; s0b = hw * q.c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
         s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
       }
+      int n = 1;
 #pragma unroll 1
       for (int pr = pn + 1; pr < pa; pr++) {
+        if (n == kSumChunkPairs) {
+          flush(1.f, sn);
+          zero();
+          n = 0;
+        }
         q = nq;
         nq = load(pr + 1 < pa ? pr + 1 : pr);  // the last pair reloads itself (in bounds)
         use(pr, q, rx, ry);
+        n++;
       }
     }
-    close(1.f, wsum + kSumN);
+    flush(1.f, sn);
     zero();
     a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
     if (pn > 0) {
       Sten nq = load(0);
+      int n = 0;
 #pragma unroll 1
       for (int pr = 0; pr < pn; pr++) {
+        if (n == kSumChunkPairs) {
+          flush(-1.f, ss);
+          zero();
+          n = 0;
+        }
         const Sten q = nq;
         nq = load(pr + 1 < pn ? pr + 1 : pr);
         P4 rx, ry;
         use(pr, q, rx, ry);
+        n++;
       }
     }
-    close(-1.f, wsum + kSumS);
-    // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each.
-    const float tA0 = tot[0], tA1 = tot[128], tA2 = tot[256], tAb = tot[384], tR0 = tot[512];
-    const float tR1 = tot[640], tR2 = tot[768], tRb = tot[896], tC0 = tot[1024], tC1 = tot[1152];
-    const float tC2 = tot[1280], tC3 = tot[1408], tCb0 = tot[1536], tCb1 = tot[1664];
-    const float D0 = cu * tR0 + tdy * tC1, D1 = cu * tR1 + tdy * tC2, D2 = cu * tR2 + tdy * tC3;
-    const float Db = cu * tRb + tdy * tCb1;
-    const float hE = u > 0.f ? 1.f : (u < 0.f ? 0.f : 0.5f);
-    const float hW = u < 0.f ? 1.f : (u > 0.f ? 0.f : 0.5f);
-    float xv[32];
-    const float uu = u * u;
-#pragma unroll
-    for (int sd = 0; sd < 2; sd++) {
-      const float sg = sd == 0 ? 1.f : -1.f;
-      const float wgt = wu * (sd == 0 ? hE : hW);
-      const float F0 = tA0 + sg * tR0, F1 = tA1 + sg * tR1, F2 = tA2 + sg * tR2, Fb = tAb + sg * tRb;
-      float* o = xv + 16 * sd;
-      o[0] = wgt * F0;
-      o[1] = wgt * u * F0;
-      o[2] = wgt * F1;
-      o[3] = wgt * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
-      const float ws = wgt * tdy;
-      o[4] = ws * tC0;
-      o[5] = ws * u * tC0;
-      o[6] = ws * tC1;
-      o[7] = ws * (0.5f * (uu * tC0 + tC2) + 0.5f * tCb0);
-      const float wuu = wgt * u;
-      o[8] = wuu * F0;
-      o[9] = wuu * u * F0;
-      o[10] = wuu * F1;
-      o[11] = wuu * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
-      o[12] = wuu * D0;
-      o[13] = wuu * u * D0;
-      o[14] = wuu * D1;
-      o[15] = wuu * (0.5f * (uu * D0 + D2) + 0.5f * Db);
-    }
-    const float r = warp_reduce_scatter<32>(xv, lane);
-    wsum[kSumE + lane] += r;  // lanes 0..15: E side, 16..31: W side
+    flush(-1.f, ss);
   }
-  __syncwarp();
-  float* out = sums + (size_t)cell * kNSum;
-  out[lane] = wsum[lane];
-  out[lane + 32] = wsum[lane + 32];
+  double* out = sums + (size_t)cell * kNSum;
+  out[kSumE + lane] = sx;  // lanes 0..15: E side, 16..31: W side
+  if (lane < 16) {
+    out[kSumN + lane] = sn;
+    out[kSumS + lane] = ss;
+  }
 }
 
 // -------------------------------------------------------------------------------------

@@ -135,16 +135,22 @@ __host__ __device__ __forceinline__ void ref_maxwellian(const Params& P, double 
 // -------------------------------------------------------------------------------------
 // Boundary ghost ring
 // -------------------------------------------------------------------------------------
+// tab: shared memory of the block for 4 kMaxAxis doubles (per-axis Maxwellian factors)
+constexpr int kGhostTab = 4 * kMaxAxis;
 template <typename T2>
 __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int gi, int gj,
-                                int si, int sj, int side, bool write_W, int wi, int wj) {
+                                int si, int sj, int side, bool write_W, int wi, int wj,
+                                double* tab) {
   const int kind = P.bc_kind[side];
   T2* dst = f + fcell(P, gi, gj) * P.nq;
   const T2* src = f + fcell(P, si, sj) * P.nq;
   const int sw = wcell(P, wi, wj);
   if (kind == 2) {  // pressure: Maxwellian(rho_bc, U and V of the adjacent cell, T_bc)
     // both Maxwellians factor into a u part and a v part: per-axis tables in shared memory
-    __shared__ double fu[kMaxAxis], fv[kMaxAxis], ru[kMaxAxis], rv[kMaxAxis];
+    double* fu = tab;
+    double* fv = tab + kMaxAxis;
+    double* ru = tab + 2 * kMaxAxis;
+    double* rv = tab + 3 * kMaxAxis;
     const double rho_a = W[sw], U = W[nwe + sw] / rho_a, V = W[2 * nwe + sw] / rho_a;
     const double lam = 1.0 / P.bc_T[side], rho = P.bc_rho[side];
     const double G = rho * lam / kPi, bf = P.K / (2.0 * lam);
@@ -186,11 +192,13 @@ __device__ void fill_ghost_cell(const Params& P, T2* f, double* W, int nwe, int 
 
 // FP32 paired-row layout (ugks_f32.cuh)
 __device__ void fill_ghost_cell(const Params& P, float4* f, double* W, int nwe, int gi, int gj,
-                                int si, int sj, int side, bool write_W, int wi, int wj);
+                                int si, int sj, int side, bool write_W, int wi, int wj,
+                                double* tab);
 
 // x-sides, rows 0..ny-1; grid (ny, 4): blockIdx.y = side*2 + layer-1.
 template <typename T2>
-__device__ __forceinline__ void ghost_x_body(const Params& P, T2* f, double* W, int nwe, int bx, int by) {
+__device__ __forceinline__ void ghost_x_body(const Params& P, T2* f, double* W, int nwe, int bx, int by,
+                                             double* tab) {
   const int j = bx, side = by >> 1, l = (by & 1) + 1;
   const int kind = P.bc_kind[side];
   const int gi = side == 0 ? -l : P.nx - 1 + l;
@@ -198,17 +206,19 @@ __device__ __forceinline__ void ghost_x_body(const Params& P, T2* f, double* W, 
   if (kind == 0) si = side == 0 ? P.nx - l : l - 1;
   else si = side == 0 ? 0 : P.nx - 1;
   const int ai = side == 0 ? 0 : P.nx - 1;  // adjacent interior cell (pressure velocity source)
-  fill_ghost_cell(P, f, W, nwe, gi, j, si, j, side, l == 1, kind == 2 ? ai : si, j);
+  fill_ghost_cell(P, f, W, nwe, gi, j, si, j, side, l == 1, kind == 2 ? ai : si, j, tab);
 }
 template <typename T2>
 __global__ void k_ghost_x(Params P, T2* f, double* W, int nwe) {
-  ghost_x_body(P, f, W, nwe, blockIdx.x, blockIdx.y);
+  __shared__ double tab[kGhostTab];
+  ghost_x_body(P, f, W, nwe, blockIdx.x, blockIdx.y, tab);
 }
 
 // y-sides over all columns -2..nx+1 (corners included, after the x-sides);
 // grid (nx+4, 4): blockIdx.y = side*2 + layer-1, side 0: S, 1: N.
 template <typename T2>
-__device__ __forceinline__ void ghost_y_body(const Params& P, T2* f, double* W, int nwe, int bx, int by) {
+__device__ __forceinline__ void ghost_y_body(const Params& P, T2* f, double* W, int nwe, int bx, int by,
+                                             double* tab) {
   const int i = bx - 2, side = 2 + (by >> 1), l = (by & 1) + 1;
   const int kind = P.bc_kind[side];
   const int gj = side == 2 ? -l : P.ny - 1 + l;
@@ -218,11 +228,12 @@ __device__ __forceinline__ void ghost_y_body(const Params& P, T2* f, double* W, 
   const int aj = side == 2 ? 0 : P.ny - 1;
   const bool wcol = i >= -1 && i <= P.nx;
   const int wi = i < -1 ? -1 : (i > P.nx ? P.nx : i);
-  fill_ghost_cell(P, f, W, nwe, i, gj, i, sj, side, l == 1 && wcol, wi, kind == 2 ? aj : sj);
+  fill_ghost_cell(P, f, W, nwe, i, gj, i, sj, side, l == 1 && wcol, wi, kind == 2 ? aj : sj, tab);
 }
 template <typename T2>
 __global__ void k_ghost_y(Params P, T2* f, double* W, int nwe) {
-  ghost_y_body(P, f, W, nwe, blockIdx.x, blockIdx.y);
+  __shared__ double tab[kGhostTab];
+  ghost_y_body(P, f, W, nwe, blockIdx.x, blockIdx.y, tab);
 }
 
 // -------------------------------------------------------------------------------------
@@ -573,8 +584,7 @@ __host__ __device__ constexpr double inv_factorial(int n) {
 // by their Taylor series below x = 0.1 (no cancellation there).
 // Power series of the c_k in y = -x by Horner, NT terms: c4 = sum y^n/(n+1)!,
 // c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!, c3 = x sum y^n/(n+3)!,
-// c2 = -x sum (n+1) y^n/(n+3)!.  The sums of c4, c5, c1 and those of c3, c2 are two
-// functions, so that the latter can run in FP32.
+// c2 = -x sum (n+1) y^n/(n+3)!.
 template <int NT>
 __device__ __forceinline__ void time_series_145(double y, double& h4, double& h5, double& h1) {
   h4 = 0.0, h5 = 0.0, h1 = 0.0;
@@ -583,25 +593,6 @@ __device__ __forceinline__ void time_series_145(double y, double& h4, double& h5
     h4 = h4 * y + inv_factorial(n + 1);
     h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
     h1 = h1 * y + inv_factorial(n + 2);
-  }
-}
-template <int NT>
-__device__ __forceinline__ void time_series_14(double y, double& h4, double& h1) {
-  h4 = 0.0, h1 = 0.0;
-#pragma unroll
-  for (int n = NT - 1; n >= 0; n--) {
-    h4 = h4 * y + inv_factorial(n + 1);
-    h1 = h1 * y + inv_factorial(n + 2);
-  }
-}
-template <int NT>
-__device__ __forceinline__ void time_series_235(float y, float& h3, float& h2, float& h5) {
-  h3 = 0.f, h2 = 0.f, h5 = 0.f;
-#pragma unroll
-  for (int n = NT - 1; n >= 0; n--) {
-    h3 = h3 * y + (float)inv_factorial(n + 3);
-    h2 = h2 * y + (float)((n + 1) * inv_factorial(n + 3));
-    h5 = h5 * y + (float)((n + 1) * inv_factorial(n + 2));
   }
 }
 template <int NT, typename T>
@@ -641,39 +632,6 @@ __device__ void time_weights(double dt, double x, double* Mt) {
   Mt[3] = dt * c4;
   Mt[4] = dt * dt * c5;
 }
-// The same weights with Mt2, Mt3 and Mt5 (the weights of the terms that carry slopes:
-// second order in dt) in FP32; Mt1 and Mt4 in FP64.
-__device__ void time_weights_f32(double dt, double x, double* Mt, float& Mt2, float& Mt3, float& Mt5) {
-  double c1, c4;
-  float c2, c3, c5;
-  if (x < 0.1) {
-    double h4, h1;
-    float h5, h3, h2;
-    if (x < 0.01) {
-      time_series_14<8>(-x, h4, h1);
-      time_series_235<8>(-(float)x, h3, h2, h5);
-    } else {
-      time_series_14<12>(-x, h4, h1);
-      time_series_235<12>(-(float)x, h3, h2, h5);
-    }
-    c4 = h4; c1 = x * h1; c5 = h5; c3 = (float)x * h3; c2 = -(float)x * h2;
-  } else {
-    const double e = exp(-x), em = -expm1(-x), ix = rcp_nr(x);
-    c4 = em * ix;
-    c1 = 1.0 - c4;
-    const double d5 = (c4 - e) * ix;
-    c5 = (float)d5;
-    c3 = (float)(0.5 - c1 * ix);
-    c2 = (float)(d5 - c1 * ix);
-  }
-  const float fdt = (float)dt;
-  Mt[0] = dt * c1;
-  Mt[3] = dt * c4;
-  Mt2 = fdt * fdt * c2;
-  Mt3 = fdt * fdt * c3;
-  Mt5 = fdt * fdt * c5;
-}
-
 // Polynomial of (a . psi) g / g_h reduced over the internal variable, in the face frame:
 // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2); component h or b.
 __device__ __forceinline__ void shape_h(const double* a, double X2, double* p) {
@@ -727,17 +685,24 @@ __device__ __forceinline__ void wall_face_f32(const Params& P, bool isx, double 
   RF.gdt = (float)P.dt;
 }
 
-// One UGKS interface in the face frame (un, ut): inputs are the interface sums (S1, S7)
-// and the cell W on both sides; output the time-integrated macroscopic flux F and the
-// micro-flux record.
-__device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
-                          const double* Ss, const double* WL, const double* WR, double tdelta,
-                          bool isx, double* F, FaceRec& R) {
+// S2-S5 of one UGKS interface in the face frame (un, ut), all in FP64: interface primitive
+// variables, Maxwellian moments (full and half range), collision time and Mt1..Mt5, the
+// micro slopes a_L, a_R, b and the time slope A (compatibility condition), and the
+// time-integrated macroscopic flux F (equilibrium part from analytic moments, free-transport
+// part from the sums).  Inputs: the interface sums (S1, S7) and the cell W on both sides.
+struct FaceCore {
+  double rho, U, V, lam, X2, X4;
+  double Mt[5];
+  double aL[4], aR[4], b[4], A[4];
+};
+__device__ __forceinline__ void face_core(const Params& P, const double* W0, const double* St,
+                                          const double* Sf, const double* Ss, const double* WL,
+                                          const double* WR, double tdelta, double* F, FaceCore& c) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
-  const double rho = W0[0], irho = 1.0 / rho, U = W0[1] * irho, V = W0[2] * irho;
+  const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
   const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) * irho * P.inv_kp2;  // 1/(4 lam)
-  const double lam = 0.25 / ilam4;
+  const double lam = 0.25 * rcp_nr(ilam4);
   const double h = 2.0 * ilam4;  // 1/(2 lam)
   const double rl = rsqrt(lam);
   double Mu[7], Mup[7], Mun[7], Mv[7];
@@ -748,33 +713,33 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5 of
   // x = dt/tau (omega = 1/2: x = dt rho / (2 mu_ref sqrt(lam)))
   const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
-  double Mt[5];
-  time_weights(P.dt, x, Mt);
+  time_weights(P.dt, x, c.Mt);
+  const double* Mt = c.Mt;
   // S4: micro slopes
   const double inv = irho * tdelta;
   const double q = (K + 2) * ilam4, c4 = 4.0 * lam * lam * P.inv_kp2;
-  double sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
+  double sL[4], sR[4], sT[4], sA[4];
 #pragma unroll
-  for (int c = 0; c < 4; c++) {
-    sL[c] = (W0[c] - WL[c]) * inv;
-    sR[c] = (WR[c] - W0[c]) * inv;
-    sT[c] = St[c] * irho;
+  for (int k = 0; k < 4; k++) {
+    sL[k] = (W0[k] - WL[k]) * inv;
+    sR[k] = (WR[k] - W0[k]) * inv;
+    sT[k] = St[k] * irho;
   }
-  micro_slope(U, V, lam, q, c4, sL, aL);
-  micro_slope(U, V, lam, q, c4, sR, aR);
-  micro_slope(U, V, lam, q, c4, sT, b);
+  micro_slope(U, V, lam, q, c4, sL, c.aL);
+  micro_slope(U, V, lam, q, c4, sR, c.aR);
+  micro_slope(U, V, lam, q, c4, sT, c.b);
   APsi<double> tL, tR, tb, tA;
-  apsi_prep(Mv, X2, 0, aL, tL);
-  apsi_prep(Mv, X2, 0, aR, tR);
-  apsi_prep(Mv, X2, 1, b, tb);
+  apsi_prep(Mv, X2, 0, c.aL, tL);
+  apsi_prep(Mv, X2, 0, c.aR, tR);
+  apsi_prep(Mv, X2, 1, c.b, tb);
   double t1[4], t2[4], t3[4], t4[4], p1[4];
   apsi_eval(tL, Mup, X2, X4m, 1, t1);
   apsi_eval(tR, Mun, X2, X4m, 1, t2);
   apsi_eval(tb, Mu, X2, X4m, 0, t3);
 #pragma unroll
-  for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
-  micro_slope(U, V, lam, q, c4, sA, A);
-  apsi_prep(Mv, X2, 0, A, tA);
+  for (int k = 0; k < 4; k++) sA[k] = -(t1[k] + t2[k] + t3[k]);
+  micro_slope(U, V, lam, q, c4, sA, c.A);
+  apsi_prep(Mv, X2, 0, c.A, tA);
   // S5: equilibrium part of the macroscopic flux; S7 free transport part from the sums
   psi_mom(Mu, Mv, X2, 1, 0, p1);
   apsi_eval(tL, Mup, X2, X4m, 2, t1);
@@ -782,13 +747,29 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   apsi_eval(tb, Mu, X2, X4m, 1, t3);
   apsi_eval(tA, Mu, X2, X4m, 1, t4);
 #pragma unroll
-  for (int c = 0; c < 4; c++)
-    F[c] = rho * (Mt[0] * p1[c] + Mt[1] * (t1[c] + t2[c] + t3[c]) + Mt[2] * t4[c]) + Mt[3] * Sf[c] -
-           Mt[4] * Ss[c];
-  R.G = rho * lam / kPi;
-  R.Un = U;
-  R.Ut = V;
-  R.lam = lam;
+  for (int k = 0; k < 4; k++)
+    F[k] = rho * (Mt[0] * p1[k] + Mt[1] * (t1[k] + t2[k] + t3[k]) + Mt[2] * t4[k]) + Mt[3] * Sf[k] -
+           Mt[4] * Ss[k];
+  c.rho = rho;
+  c.U = U;
+  c.V = V;
+  c.lam = lam;
+  c.X2 = X2;
+  c.X4 = X4;
+}
+
+// FP64 form: the interface (face_core) and its FP64 micro-flux record.
+__device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
+                          const double* Ss, const double* WL, const double* WR, double tdelta,
+                          bool isx, double* F, FaceRec& R) {
+  FaceCore c;
+  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
+  const double* Mt = c.Mt;
+  const double X2 = c.X2, X4 = c.X4;
+  R.G = c.rho * c.lam / kPi;
+  R.Un = c.U;
+  R.Ut = c.V;
+  R.lam = c.lam;
   R.Mt4 = Mt[3];
   R.Mt5 = Mt[4];
   R.bfac = X2;
@@ -796,93 +777,42 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   // S6/S8 coefficients (FP64 record)
   double pa[4], pb[4], pA[4];
   for (int sd = 0; sd < 2; sd++) {
-    const double* as = sd == 0 ? aL : aR;
+    const double* as = sd == 0 ? c.aL : c.aR;
     shape_h(as, X2, pa);
-    shape_h(b, X2, pb);
-    shape_h(A, X2, pA);
+    shape_h(c.b, X2, pb);
+    shape_h(c.A, X2, pA);
     qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
     shape_b(as, X2, X4, pa);
-    shape_b(b, X2, X4, pb);
-    shape_b(A, X2, X4, pA);
+    shape_b(c.b, X2, X4, pb);
+    shape_b(c.A, X2, X4, pA);
     qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
   }
 }
 
-// The same interface for the FP32-f form, whose walk consumes the micro slopes, time weights
-// and amplitude in FP32. The terms of the macroscopic flux that are first order in dt
-// (Mt1 rho <un psi> over the full range, Mt4 S_f, Mt5 S_sigma) and the Maxwellian's exponent
-// are formed in FP64; the terms that carry the micro slopes a_L, a_R, b, A (weights Mt2 and
-// Mt3, second order in dt; relative to the first-order terms they are
-// O(min(dt, tau) |grad W| / W), and the slopes are differences of FP64 W formed in FP64) are
-// formed in FP32 with the half-range moments they need. The FP32 rounding of those terms
-// is below 1e-7 of terms that are themselves small against the flux, and GB300 executes
-// FP64 at 1/64 of the FP32 rate.
-__device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const float* St,
-                                              const double* Sf, const float* Ss, const double* WL,
+// FP32-f form: the same FP64 interface (face_core: primitive variables, half-range moments,
+// Mt1..Mt5, micro-slope solves, compatibility condition, macroscopic flux), then the FP32
+// record its update walk reads.  The record is rounded to FP32 from the FP64 slopes and
+// weights: the walk applies it to FP32 f.
+__device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St,
+                                              const double* Sf, const double* Ss, const double* WL,
                                               const double* WR, double tdelta, bool isx, double* F,
                                               double& Mt4, FaceRecF& RF) {
-  const int K = P.K;
-  // S2: interface primitive variables (FP64)
-  const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
-  const double ilam4 = (W0[3] - 0.5 * rho * (U * U + V * V)) * irho * P.inv_kp2;  // 1/(4 lam)
-  const double lam = 0.25 * rcp_nr(ilam4);
-  const double h = 2.0 * ilam4;  // 1/(2 lam)
-  const double rl = rsqrt(lam);
-  const double X2 = 2.0 * K * ilam4;
-  // S3: collision time and Mt1, Mt4 (FP64), Mt2, Mt3, Mt5 (FP32)
-  const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
-  double Mt[5];
-  float fM2, fM3, fM5;
-  time_weights_f32(P.dt, x, Mt, fM2, fM3, fM5);
-  // S5, first-order part: rho Mt1 <un psi> over the full range (FP64)
-  double Mu[7], Mv[7], p1[4];
-  gauss_moments7_full(U, h, Mu);
-  gauss_moments7_full(V, h, Mv);
-  psi_mom(Mu, Mv, X2, 1, 0, p1);
-  // S2, S4, S5 second-order part (FP32): half-range moments, micro slopes, compatibility
-  const float fU = (float)U, fV = (float)V, flam = (float)lam, fh = (float)h;
-  const float fX2 = (float)X2, fX4m = (float)(K * 8.0 * ilam4 * ilam4);  // X4 - X2^2
-  float fMu[7], fMup[7], fMun[7], fMv[7];
-  gauss_moments7(fU, flam, fh, (float)rl, fMu, fMup, fMun);
-  gauss_moments7_full(fV, fh, fMv);
-  const float q = (float)((K + 2) * ilam4), c4 = (float)(4.0 * lam * lam * P.inv_kp2);
-  const float inv = (float)(irho * tdelta), firho = (float)irho;
-  float sL[4], sR[4], sT[4], sA[4], aL[4], aR[4], b[4], A[4];
-#pragma unroll
-  for (int c = 0; c < 4; c++) {
-    sL[c] = (float)(W0[c] - WL[c]) * inv;
-    sR[c] = (float)(WR[c] - W0[c]) * inv;
-    sT[c] = St[c] * firho;
-  }
-  micro_slope(fU, fV, flam, q, c4, sL, aL);
-  micro_slope(fU, fV, flam, q, c4, sR, aR);
-  micro_slope(fU, fV, flam, q, c4, sT, b);
-  APsi<float> tL, tR, tb, tA;
-  apsi_prep(fMv, fX2, 0, aL, tL);
-  apsi_prep(fMv, fX2, 0, aR, tR);
-  apsi_prep(fMv, fX2, 1, b, tb);
-  float t1[4], t2[4], t3[4], t4[4];
-  apsi_eval(tL, fMup, fX2, fX4m, 1, t1);
-  apsi_eval(tR, fMun, fX2, fX4m, 1, t2);
-  apsi_eval(tb, fMu, fX2, fX4m, 0, t3);
-#pragma unroll
-  for (int c = 0; c < 4; c++) sA[c] = -(t1[c] + t2[c] + t3[c]);
-  micro_slope(fU, fV, flam, q, c4, sA, A);
-  apsi_prep(fMv, fX2, 0, A, tA);
-  apsi_eval(tL, fMup, fX2, fX4m, 2, t1);
-  apsi_eval(tR, fMun, fX2, fX4m, 2, t2);
-  apsi_eval(tb, fMu, fX2, fX4m, 1, t3);
-  apsi_eval(tA, fMu, fX2, fX4m, 1, t4);
-  const float fM1 = (float)Mt[0];
-#pragma unroll
-  for (int c = 0; c < 4; c++) {
-    const float second = fM2 * (t1[c] + t2[c] + t3[c]) + fM3 * t4[c];
-    F[c] = rho * (Mt[0] * p1[c] + (double)second) + Mt[3] * Sf[c] - (double)(fM5 * Ss[c]);
-  }
+  FaceCore c;
+  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
+  const double* Mt = c.Mt;
   Mt4 = Mt[3];
-  // FP32 record of the micro flux (S6/S8 coefficients, global frame)
-  const float fG = (float)(rho * lam / kPi);
-  const float kap = 0.5f * fX4m;  // (X4 - X2^2)/2 = K/(4 lam^2)
+  const float fM1 = (float)Mt[0], fM2 = (float)Mt[1], fM3 = (float)Mt[2];
+  const float fX2 = (float)c.X2;
+  const float fG = (float)(c.rho * c.lam / kPi);
+  const float kap = (float)(0.5 * (c.X4 - c.X2 * c.X2));  // (X4 - X2^2)/2 = K/(4 lam^2)
+  float aL[4], aR[4], b[4], A[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    aL[k] = (float)c.aL[k];
+    aR[k] = (float)c.aR[k];
+    b[k] = (float)c.b[k];
+    A[k] = (float)c.A[k];
+  }
   // shape polynomial of (a . psi) g / g_h reduced over the internal variable, face frame:
   // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2)
   auto shape = [&](const float* a4, float* o) {
@@ -910,7 +840,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
     Qf[6] = fM2 * pa[3];
     Qf[7] = fM2 * pb[3];
 #pragma unroll
-    for (int c = 0; c < 8; c++) RF.Q[sd][c] = fG * (isx ? Qf[c] : Qf[py[c]]);
+    for (int k = 0; k < 8; k++) RF.Q[sd][k] = fG * (isx ? Qf[k] : Qf[py[k]]);
     // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
     // Mt2 un a4 + Mt2 ut b4)
     const float k0 = fG * kap * fM3 * A[3], kn = fG * kap * fM2 * as[3], kt = fG * kap * fM2 * b[3];
@@ -920,19 +850,21 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
     RF.K[sd][3] = fX2;
   }
   constexpr double kLog2e = 1.4426950408889634;
-  const double Ux = isx ? U : V, Vy = isx ? V : U;
+  const double lam = c.lam, Ux = isx ? c.U : c.V, Vy = isx ? c.V : c.U;
   RF.E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
   RF.E[1] = (float)(2.0 * lam * Ux * kLog2e);
   RF.E[2] = (float)(2.0 * lam * Vy * kLog2e);
   RF.E[3] = (float)(-lam * kLog2e);
   RF.Mt4 = (float)Mt[3];
-  RF.nMt5 = -fM5;
+  RF.nMt5 = (float)(-Mt[4]);
   RF.wall = 0.f;
   RF.gdt = 0.f;
 }
 
-template <typename S>
-__device__ __forceinline__ void faces_body(const Params& P, const S* __restrict__ sums,
+// F32REC: the FP32-f form (FP32 face records for its walk); else the FP64 form's records.
+// Both forms' sums are FP64.
+template <bool F32REC>
+__device__ __forceinline__ void faces_body(const Params& P, const double* __restrict__ sums,
                                            const double* __restrict__ W, int nwe,
                                            FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
                                            double* __restrict__ Fx, double* __restrict__ Fy,
@@ -968,17 +900,17 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
   }
   FaceRec R;
   FaceRecF RF;
-  constexpr bool f32 = std::is_same<S, float>::value;  // FP32-f form: FP32 sums and records
+  constexpr bool f32 = F32REC;
   double F[4];
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
     // with the density that cancels the mass flux; first order in time
     const int oin = wall == 1 ? oR : oL;
-    const S* Se = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
-                            : sums + (size_t)cL * kNSum + oL + kOffSf;
+    const double* Se = wall == 1 ? sums + (size_t)cR * kNSum + oR + kOffSf
+                                 : sums + (size_t)cL * kNSum + oL + kOffSf;
     double Sin[4];
 #pragma unroll
-    for (int c = 0; c < 4; c++) Sin[c] = (double)Se[c] + P.refsum[oin / 16][kOffSf + c];
+    for (int c = 0; c < 4; c++) Sin[c] = Se[c] + P.refsum[oin / 16][kOffSf + c];
     const double rhow = -Sin[0] / P.wall_mom[side][0];
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = P.dt * (Sin[c] + rhow * P.wall_mom[side][c]);
@@ -997,28 +929,22 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     if (f32) wall_face_f32(P, isx, R.bfac, lam, R.Ut, R.G, wall, RF);
   } else {
     const int pm[4] = {0, isx ? 1 : 2, isx ? 2 : 1, 3};  // natural -> face frame
-    const S* sL = sums + (size_t)cL * kNSum + oL;
-    const S* sR = sums + (size_t)cR * kNSum + oR;
+    const double* sL = sums + (size_t)cL * kNSum + oL;
+    const double* sR = sums + (size_t)cR * kNSum + oR;
     double W0[4], St[4], Sf[4], Ss[4], WL[4], WR[4], Fr[4];
-    float Stf[4], Ssf[4];
     const double* rp = P.refpair[isx ? 0 : 1];  // g_ref sums of both sides (FP32-f form)
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       const int s = pm[c];
-      W0[c] = ((double)sL[kOffW0 + s] + (double)sR[kOffW0 + s]) + rp[s];
-      Sf[c] = ((double)sL[kOffSf + s] + (double)sR[kOffSf + s]) + rp[4 + s];
-      if constexpr (f32) {
-        Stf[c] = sL[kOffSt + s] + sR[kOffSt + s];
-        Ssf[c] = sL[kOffSs + s] + sR[kOffSs + s];
-      } else {
-        St[c] = (double)sL[kOffSt + s] + (double)sR[kOffSt + s];
-        Ss[c] = (double)sL[kOffSs + s] + (double)sR[kOffSs + s];
-      }
+      W0[c] = (sL[kOffW0 + s] + sR[kOffW0 + s]) + rp[s];
+      Sf[c] = (sL[kOffSf + s] + sR[kOffSf + s]) + rp[4 + s];
+      St[c] = sL[kOffSt + s] + sR[kOffSt + s];
+      Ss[c] = sL[kOffSs + s] + sR[kOffSs + s];
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
     if constexpr (f32)
-      face_math_f32(P, W0, Stf, Sf, Ssf, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
+      face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
     else
       face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R);
 #pragma unroll
@@ -1035,13 +961,12 @@ __device__ __forceinline__ void faces_body(const Params& P, const S* __restrict_
     for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
   }
 }
-template <typename S>
-__global__ void k_faces(Params P, const S* __restrict__ sums, const double* __restrict__ W,
+// FP64 form
+__global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
                         int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
-                        double* __restrict__ Fx, double* __restrict__ Fy,
-                        FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
-                        double* __restrict__ mt4) {
-  faces_body<S>(P, sums, W, nwe, fxr, fyr, Fx, Fy, fxf, fyf, mt4, blockIdx.x * blockDim.x + threadIdx.x);
+                        double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ mt4) {
+  faces_body<false>(P, sums, W, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4,
+                    blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // -------------------------------------------------------------------------------------

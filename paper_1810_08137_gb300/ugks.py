@@ -26,7 +26,8 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_batch_destroy", "ugks_batch_last_error", "ugks_batch_bytes_used",
            "ugks_batch_admit", "ugks_batch_retire", "ugks_batch_instance", "ugks_batch_step",
            "ugks_batch_sync", "ugks_batch_set_walk_rows", "ugks_batch_get_walk_rows",
-           "ugks_batch_tune")
+           "ugks_batch_set_walk_vtile", "ugks_batch_get_walk_vtile", "ugks_batch_set_persistent",
+           "ugks_batch_get_persistent", "ugks_batch_set_wait_limit", "ugks_batch_tune")
 NKERNELS = 6
 
 
@@ -106,6 +107,11 @@ def lib(build_if_missing: bool = True):
         L.ugks_batch_sync.argtypes = [C.c_void_p]
         L.ugks_batch_set_walk_rows.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.ugks_batch_get_walk_rows.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_set_walk_vtile.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.ugks_batch_get_walk_vtile.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_set_persistent.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_batch_get_persistent.argtypes = [C.c_void_p]
+        L.ugks_batch_set_wait_limit.argtypes = [C.c_void_p, C.c_ulonglong]
         L.ugks_batch_tune.argtypes = [C.c_void_p, C.c_int, _P]
         _lib = L
     return _lib
@@ -327,6 +333,22 @@ class Batch:
 
     def walk_rows(self, slot: int) -> int:
         return int(self._L.ugks_batch_get_walk_rows(self._b, int(slot)))
+
+    def set_walk_vtile(self, slot: int, chunks: int):
+        self._check(self._L.ugks_batch_set_walk_vtile(self._b, int(slot), int(chunks)))
+
+    def walk_vtile(self, slot: int) -> int:
+        return int(self._L.ugks_batch_get_walk_vtile(self._b, int(slot)))
+
+    @property
+    def persistent(self) -> bool:
+        return bool(self._L.ugks_batch_get_persistent(self._b))
+
+    def set_persistent(self, enable: bool):
+        self._check(self._L.ugks_batch_set_persistent(self._b, int(bool(enable))))
+
+    def set_wait_limit(self, polls: int):
+        self._check(self._L.ugks_batch_set_wait_limit(self._b, C.c_ulonglong(int(polls))))
 
     def tune(self, trial_steps: int = 3) -> float:
         ms = C.c_double()

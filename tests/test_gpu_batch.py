@@ -109,15 +109,70 @@ def test_batch_tile_shape_and_tuner_do_not_change_results(U):
         for x, y, p in zip(s1, s2, prims):
             B1.instance(x).init_maxwellian(*p)
             B2.instance(y).init_maxwellian(*p)
-        for x in s2:
+        for k, x in enumerate(s2):
             B2.set_walk_rows(x, 3)  # tiles of 3 rows: many tile seams
+            B2.set_walk_vtile(x, 1 + k % 2)  # velocity tiles of 1 and 2 chunks
         B1.step(4)
         B2.step(4)
-        ms = B1.tune(1)  # advances B1 by 4*(1+1) steps per velocity class present
+        ms = B1.tune(1)  # advances B1 by 12*(1+1) steps per velocity class present
         assert ms > 0
         for x in s1:
             assert B1.walk_rows(x) in (16, 32, 64, 128)
+            assert B1.walk_vtile(x) in (0, 1, 2)
         for x, y in zip(s1, s2):
             fa, Wa = B2.instance(y).get_state()
             fb, Wb = alone(U, cfgs[s2.index(y)], prims[s2.index(y)], 4)
             assert np.array_equal(fa, fb) and np.array_equal(Wa, Wb)
+
+
+def test_batch_persistent_and_phase_launches_bitwise(U):
+    """The persistent step (one cooperative launch, grid barriers between the phases) and
+    the seven phase launches run the same phase code in the same order of work: bitwise
+    equal results, and equal to each instance stepped alone."""
+    cfgs = mix_configs()
+    prims = [prim_of(c, 40 + k) for k, c in enumerate(cfgs)]
+    out = []
+    for persistent in (True, False):
+        with U.Batch(8) as B:
+            assert B.persistent  # the default where cooperative launch is available
+            B.set_persistent(persistent)
+            slots = [B.admit(c) for c in cfgs]
+            for s, p in zip(slots, prims):
+                B.instance(s).init_maxwellian(*p)
+            B.step(5)
+            B.sync()
+            out.append([B.instance(s).get_state() for s in slots])
+    for k in range(len(cfgs)):
+        ref = alone(U, cfgs[k], prims[k], 5)
+        for mode in (0, 1):
+            assert np.array_equal(out[mode][k][0], ref[0]), (cfgs[k].name, mode)
+            assert np.array_equal(out[mode][k][1], ref[1]), (cfgs[k].name, mode)
+
+
+def test_batch_persistent_barrier_timeout_is_reported(U):
+    """A grid barrier of the persistent step whose wait bound runs out (bound 0: every block
+    that is not the last to arrive gives up at once) ends the launch without trapping the
+    device; ugks_batch_sync reports UGKS_ETIMEOUT, and with the bound restored and the
+    state set again the batch steps correctly (the context stays usable)."""
+    a, b, c, _ = mix_configs()
+    pa, pb = prim_of(a, 50), prim_of(b, 51)
+    ra = alone(U, a, pa, 3)
+    with U.Batch(4) as B:
+        sa, sb = B.admit(a), B.admit(b)
+        B.instance(sa).init_maxwellian(*pa)
+        B.instance(sb).init_maxwellian(*pb)
+        B.set_wait_limit(0)
+        B.step(3)  # 18 barriers: a block reaching one before the last block arrives gives up
+        with pytest.raises(U.UGKSError) as e:
+            B.sync()
+        assert e.value.status == 4  # UGKS_ETIMEOUT
+        B.sync()  # the flag was cleared
+        B.set_wait_limit(8_000_000)
+        B.instance(sa).init_maxwellian(*pa)
+        B.instance(sb).init_maxwellian(*pb)
+        # the parity of each instance is wherever the interrupted step left it; a state set
+        # again and stepped from there must match the alone run
+        B.step(3)
+        B.sync()
+        fa, Wa = B.instance(sa).get_state()
+    assert np.array_equal(fa, ra[0]) and np.array_equal(Wa, ra[1])
