@@ -44,14 +44,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 arithmetic peak of the part: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x
-# 2.07 GHz (unit counts and maximum clock; no FP64 peak is measured by the driver).
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# Nominal FP64 arithmetic of the update (S6, S8, Eq. 3) per velocity-cell, exp and divide
-# counted as one operation each: upwind face values (4), u sigma_x + v sigma_y (6), 2 face
-# fluxes (39 each: Maxwellian 8, Q_h 15, Q_b 6, X 10), collision (42).  The van Leer slopes
-# (20 more) are formed once per velocity-cell by the FP64 sums kernel and read back here.
-UPDATE_FLOPS_PER_VC = 130
+# FP64 form: FP64 flops per velocity-cell as executed (FMA = 2 flops), from the ncu
+# instruction counts of its kernels (DFMA, DMUL, DADD per velocity-cell; the capture in
+# profiles/fp64_step_kernels_channel_200x100_v28.md): the update's two passes
+# 2 x 58.8 + 25.6 + 12.5, the sums kernel 2 x 43.4 + 13.3 + 18.4.  The peak is measured
+# in the run (ugks_fp64_rate: chains of FP64 FMAs on every SM).
+FP64_UPDATE_FLOPS_PER_VC = 2 * 58.8 + 25.6 + 12.5
+FP64_SUMS_FLOPS_PER_VC = 2 * 43.4 + 13.3 + 18.4
 # DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
 # capture summarised in profiles/; None when the kernel has changed since that capture.
 UPDATE_TRAFFIC_PER_VC = (596.680448e6 + 465.463808e6) / 62.72e6  # kb_strip, 400x200x28^2 capture
@@ -218,9 +217,15 @@ def large_velocity_bench(ugks, torch, stream, warmup, grids=(51, 101, 151, 201))
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1) / steps
+            # per-kernel breakdown from the library's events (direct launches)
+            s.profile(True)
+            s.step(max(1, steps // 2))
+            kt = s.kernel_times()
+            s.profile(False)
             s.close()
             torch.cuda.empty_cache()
-            row[name] = {"ms_per_step": ms, "value": cfg.vc / (ms * 1e-3), "steps": steps}
+            row[name] = {"ms_per_step": ms, "value": cfg.vc / (ms * 1e-3), "steps": steps,
+                         "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS}}
         row["fp32f_vs_fp64"] = row["fp32f"]["value"] / row["fp64"]["value"]
         out.append(row)
     return {"unit": UNIT, "grids": out}
@@ -258,7 +263,9 @@ def batch_bench(ugks, torch, stream, steps, warmup):
            "instances": len(cfgs), "vc_per_step": vc, "value": vc * steps / (ms * 1e-3),
            "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "precision": "fp32f",
            "tuned_walk_rows": rows, "tuned_ms_per_step": tuned_ms,
-           "admit_s": t_admit, "device_bytes": B.bytes_used, "launches_per_step": 7}
+           "admit_s": t_admit, "device_bytes": B.bytes_used,
+           "persistent": B.persistent, "launches_per_step": 1 if B.persistent else 7,
+           "tuned_walk_vtile": sorted({B.walk_vtile(s) for s in slots})}
     B.close()
     return out
 
@@ -381,6 +388,7 @@ def main():
 
     results = {}
     with torch.cuda.stream(stream):
+        fp64_peak = ugks.fp64_rate(stream.cuda_stream)
         for prec in (other_prec, main_prec):
             # the plain FP64 form is ~40x slower per step: time fewer of its steps
             n = args.steps if prec == main_prec else max(3, min(args.steps, 10))
@@ -425,12 +433,18 @@ def main():
             roof = {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
                     "unit": "GB/s", "frac": ach_up / hbm, "traffic": traffic,
                     "peak_source": hbm_src, "algorithmic_bytes_per_vc": 2 * bpv}
+            roof_sums = {"achieved": ach_sm, "frac": ach_sm / hbm, "unit": "GB/s",
+                         "algorithmic_bytes_per_vc": bpv}
         else:
-            ach = UPDATE_FLOPS_PER_VC * cfg.vc / t_launch / 1e9
-            roof = {"bound": "alu", "kernel": "update", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
-                    "unit": "GFLOP/s (FP64)", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
-                    "nominal_flops_per_vc": UPDATE_FLOPS_PER_VC, "hbm_frac": ach_up / hbm}
+            ach = FP64_UPDATE_FLOPS_PER_VC * cfg.vc / t_launch / 1e9
+            roof = {"bound": "alu", "kernel": "update", "achieved": ach, "peak": fp64_peak,
+                    "unit": "GFLOP/s (FP64)", "frac": ach / fp64_peak, "traffic": None,
+                    "peak_source": "measured in this run (ugks_fp64_rate)",
+                    "flops_per_vc": FP64_UPDATE_FLOPS_PER_VC, "hbm_frac": ach_up / hbm}
+            ach_s = FP64_SUMS_FLOPS_PER_VC * cfg.vc / (t_sm / n_sm * 1e-3) / 1e9
+            roof_sums = {"bound": "alu", "achieved": ach_s, "peak": fp64_peak,
+                         "unit": "GFLOP/s (FP64)", "frac": ach_s / fp64_peak,
+                         "flops_per_vc": FP64_SUMS_FLOPS_PER_VC, "hbm_frac": ach_sm / hbm}
         return {
             "value": job_value(ws, cfg.vc, n, ms),
             "ms_per_step": ms / n,
@@ -438,8 +452,7 @@ def main():
             "ms_per_step_profiled": ms_prof / n,
             "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS},
             "roofline": roof,
-            "roofline_sums": {"achieved": ach_sm, "frac": ach_sm / hbm, "unit": "GB/s",
-                              "algorithmic_bytes_per_vc": bpv},
+            "roofline_sums": roof_sums,
             "step_hbm_frac": step_bytes / (ms / n * 1e-3) / 1e9 / hbm,
             "clocks": clk,
         }
@@ -471,7 +484,8 @@ def main():
                        "value": other["value"], "ms_per_step": other["ms_per_step"],
                        "steps": other["steps"],
                        "kernel_ms_per_step": other["kernel_ms_per_step"],
-                       "roofline": other["roofline"], "step_hbm_frac": other["step_hbm_frac"],
+                       "roofline": other["roofline"], "roofline_sums": other["roofline_sums"],
+                       "step_hbm_frac": other["step_hbm_frac"],
                        "clocks": other["clocks"]},
         "vs_fp64": (main["value"] / other["value"]) if main_prec == ugks.FP32F else 1.0,
         "clocks": main["clocks"],

@@ -178,6 +178,12 @@ const char* ugks_kernel_name(int i);
 /* Device bytes ugks_create would allocate for cfg (0 if cfg is invalid). */
 size_t ugks_state_bytes(const ugks_config* cfg);
 
+/* Measured FP64 arithmetic rate of the current device (GFLOP/s, a fused multiply-add
+ * counted as 2): independent chains of FP64 FMAs on every SM, best of three timed launches
+ * on cuda_stream (NULL: the legacy stream).  A diagnostic for the FP64 form's roofline; the
+ * paper has no counterpart.  Synchronises. */
+ugks_status ugks_fp64_rate(void* cuda_stream, double* gflops);
+
 /* ---- Batch of independent instances ------------------------------------------------
  * Many independent channel solves stepped together (the FP32-f form only): every phase of
  * the step runs once per step for all active instances, as a persistent grid over a

@@ -668,6 +668,56 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   return UGKS_OK;
 }
 
+// -------------------------------------------------------------------------------------
+// FP64 arithmetic rate of the device (the roofline of the FP64 form's kernels): every
+// thread runs 8 independent chains of dependent FP64 fused multiply-adds.
+// -------------------------------------------------------------------------------------
+__global__ void k_fp64_rate(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = fma(x[k], a, b);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) r += x[k];
+  if (r == 1.2345e300) out[0] = r;  // keeps the chains live; never true for these inputs
+}
+
+ugks_status ugks_fp64_rate(void* cuda_stream, double* gflops) {
+  if (!gflops) return UGKS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return UGKS_ECUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return UGKS_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return UGKS_ECUDA; }
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaError_t e = cudaSuccess;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {  // first launch: warm-up
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+      k_fp64_rate<<<blocks, threads, 0, st>>>(nullptr, iters, 0.999999, 1e-7);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return UGKS_ECUDA;
+  *gflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e9;
+  return UGKS_OK;
+}
+
 ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* out) {
   if (!out) return UGKS_EINVAL;
   *out = nullptr;

@@ -69,7 +69,10 @@ __device__ __forceinline__ int find_instance(const int* start, int n, int vb) {
 }
 
 // ---- phase bodies: one pass of a phase over the whole work table, grid-strided ----------
-__device__ __forceinline__ void ghost_x_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+// Not inlined: the persistent step and the phase kernels call the same compiled body, so an
+// instance's floating-point results do not depend on which of them runs it (inlined into
+// different kernels, the compiler may fuse a multiply and an add differently).
+__device__ __noinline__ void ghost_x_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                               double* tab) {
   const int total = wk->start[0][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -80,7 +83,7 @@ __device__ __forceinline__ void ghost_x_phase(const SlotDev* __restrict__ slots,
   }
 }
 
-__device__ __forceinline__ void ghost_y_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+__device__ __noinline__ void ghost_y_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                               double* tab) {
   const int total = wk->start[1][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -91,7 +94,7 @@ __device__ __forceinline__ void ghost_y_phase(const SlotDev* __restrict__ slots,
   }
 }
 
-__device__ __forceinline__ void sums_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+__device__ __noinline__ void sums_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
   const int total = wk->start[2][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
@@ -100,7 +103,7 @@ __device__ __forceinline__ void sums_phase(const SlotDev* __restrict__ slots, co
   }
 }
 
-__device__ __forceinline__ void faces_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+__device__ __noinline__ void faces_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
   const int total = wk->start[3][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[3], wk->n, vb);
@@ -111,7 +114,7 @@ __device__ __forceinline__ void faces_phase(const SlotDev* __restrict__ slots, c
   }
 }
 
-__device__ __forceinline__ void cells_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+__device__ __noinline__ void cells_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                             double (*red)[128]) {
   const int total = wk->start[4][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
@@ -147,7 +150,7 @@ __device__ __forceinline__ void walk_item(const SlotDev& S, int ns, int nt, int 
 }
 
 // Update sweep: one warp per work item (strip, row tile, velocity chunk).
-__device__ __forceinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+__device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                             float4* strip_sm) {
   const int warp = threadIdx.x >> 5;
   const int total = wk->start[5][wk->n];

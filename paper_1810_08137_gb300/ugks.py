@@ -27,7 +27,8 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_batch_admit", "ugks_batch_retire", "ugks_batch_instance", "ugks_batch_step",
            "ugks_batch_sync", "ugks_batch_set_walk_rows", "ugks_batch_get_walk_rows",
            "ugks_batch_set_walk_vtile", "ugks_batch_get_walk_vtile", "ugks_batch_set_persistent",
-           "ugks_batch_get_persistent", "ugks_batch_set_wait_limit", "ugks_batch_tune")
+           "ugks_batch_get_persistent", "ugks_batch_set_wait_limit", "ugks_batch_tune",
+           "ugks_fp64_rate")
 NKERNELS = 6
 
 
@@ -113,6 +114,7 @@ def lib(build_if_missing: bool = True):
         L.ugks_batch_get_persistent.argtypes = [C.c_void_p]
         L.ugks_batch_set_wait_limit.argtypes = [C.c_void_p, C.c_ulonglong]
         L.ugks_batch_tune.argtypes = [C.c_void_p, C.c_int, _P]
+        L.ugks_fp64_rate.argtypes = [C.c_void_p, _P]
         _lib = L
     return _lib
 
@@ -254,6 +256,15 @@ class Solver:
         r = np.empty(4)
         self._check(self._L.ugks_residual(self._h, r.ctypes.data_as(_P)))
         return r
+
+
+def fp64_rate(stream=None) -> float:
+    """ugks_fp64_rate: measured FP64 FMA throughput of the current device, GFLOP/s."""
+    g = C.c_double()
+    st = lib().ugks_fp64_rate(C.c_void_p(stream or 0), C.byref(g))
+    if st:
+        raise UGKSError(st, "ugks_fp64_rate failed")
+    return g.value
 
 
 def step_noalloc(cfg, f_in, W_in, f_out, W_out, stream=None) -> None:
