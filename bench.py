@@ -246,6 +246,21 @@ def batch_bench(ugks, torch, stream, steps, warmup):
     B.sync()
     t_admit = time.perf_counter() - t0
     tuned_ms = B.tune(2)
+    # both step modes, same tiles: one persistent launch vs seven phase launches per step
+    mode_ms = {}
+    tuned_mode = B.persistent
+    for mode in (True, False):
+        B.set_persistent(mode)
+        B.step(2)
+        B.sync()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        B.step(5)
+        a1.record(stream)
+        a1.synchronize()
+        mode_ms["persistent" if mode else "phases"] = a0.elapsed_time(a1) / 5
+    B.set_persistent(tuned_mode)
     B.step(warmup)
     B.sync()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -265,6 +280,7 @@ def batch_bench(ugks, torch, stream, steps, warmup):
            "tuned_walk_rows": rows, "tuned_ms_per_step": tuned_ms,
            "admit_s": t_admit, "device_bytes": B.bytes_used,
            "persistent": B.persistent, "launches_per_step": 1 if B.persistent else 7,
+           "ms_per_step_by_mode": mode_ms,
            "tuned_walk_vtile": sorted({B.walk_vtile(s) for s in slots})}
     B.close()
     return out
@@ -389,8 +405,8 @@ def main():
     results = {}
     with torch.cuda.stream(stream):
         fp64_peak = ugks.fp64_rate(stream.cuda_stream)
-        for prec in (other_prec, main_prec):
-            # the plain FP64 form is ~40x slower per step: time fewer of its steps
+        for prec in (other_prec, ugks.DF64, main_prec):
+            # the FP64-accurate forms are slower per step: time fewer of their steps
             n = args.steps if prec == main_prec else max(3, min(args.steps, 10))
             barrier()
             with Clocks(local) as clk:
@@ -421,6 +437,17 @@ def main():
     def form_json(prec):
         ms, ms_prof, kt, clk, n = results[prec]
         bpv = 8 if prec == ugks.FP32F else 16  # bytes per velocity-cell of f (h, b)
+        if prec == ugks.DF64:
+            n_up, t_up = kt["update"]
+            n_sm, t_sm = kt["sums"]
+            ach_up = 2 * bpv * cfg.vc / (t_up / n_up * 1e-3) / 1e9
+            return {"value": job_value(ws, cfg.vc, n, ms), "ms_per_step": ms / n, "steps": n,
+                    "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS},
+                    "roofline": {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
+                                 "unit": "GB/s", "frac": ach_up / hbm, "traffic": None,
+                                 "peak_source": hbm_src, "algorithmic_bytes_per_vc": 2 * bpv},
+                    "step_hbm_frac": 2 * bpv * cfg.vc / (ms / n * 1e-3) / 1e9 / hbm,
+                    "clocks": clk}
         n_up, t_up = kt["update"]
         n_sm, t_sm = kt["sums"]
         t_launch = t_up / n_up * 1e-3  # seconds per update (FP64 form: its two passes together)
@@ -462,6 +489,7 @@ def main():
         return
     main = form_json(main_prec)
     other = form_json(other_prec)
+    dff = form_json(ugks.DF64)
     cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline(cfg, prim)
     h2d = cfg.nc * cfg.nq * 2 * 8 + 4 * cfg.nc * 8
     d2h = 4 * cfg.nc * 8
@@ -487,6 +515,9 @@ def main():
                        "roofline": other["roofline"], "roofline_sums": other["roofline_sums"],
                        "step_hbm_frac": other["step_hbm_frac"],
                        "clocks": other["clocks"]},
+        "df64_form": dict(dff, precision="df64: FP64-accurate, double-FP32 f and per-velocity "
+                                          "arithmetic on the FP32 pipe, FP64 interface and cell scalars",
+                          vs_fp64=dff["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])),
         "vs_fp64": (main["value"] / other["value"]) if main_prec == ugks.FP32F else 1.0,
         "clocks": main["clocks"],
         "e2e": {"value": ws * cfg.vc * args.e2e_steps / t_e2e, "unit": UNIT,

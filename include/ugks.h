@@ -68,7 +68,13 @@ typedef enum {
                       coefficients of Eq. 3 and the exponents of the collision and wall
                       Maxwellians relative to g_ref.  FP32 for the per-velocity work on f:
                       reconstruction, micro flux and the Eq. 3 update, from FP32 records of
-                      those FP64 coefficients */
+                      those FP64 coefficients */,
+  UGKS_DF64 = 2    /* FP64-accurate, on the FP32 pipe: f stored as double-FP32 pairs (an
+                      unevaluated sum of two FP32 numbers, about 48 significand bits) and
+                      every per-velocity operation (van Leer slopes, velocity sums, micro
+                      flux, Eq. 3) in double-FP32 arithmetic built from error-free
+                      transformations; interface and cell scalars (S2-S5, Eq. 4) in FP64.
+                      Meets the FP64 form's tolerance (1e-12 per field per step) */
 } ugks_precision;
 
 enum { UGKS_SIDE_W = 0, UGKS_SIDE_E = 1, UGKS_SIDE_S = 2, UGKS_SIDE_N = 3 };
@@ -244,10 +250,11 @@ ugks_status ugks_batch_set_wait_limit(ugks_batch b, unsigned long long polls);
  * warps for the same cell tile; 0 = all chunks of the cell).  The autotuner: for each
  * velocity-grid class present (nu*nv <= 576, <= 1600, <= 4096, larger) it times
  * trial_steps batch steps for every cell tile of 16, 32, 64, 128 rows times velocity tile
- * of all, 2 and 1 chunks, and keeps the fastest for that class.  The tile shape does not
- * change the arithmetic, so tuning steps are real steps of every active instance (each
- * advances by 12 (trial_steps + 1) per class present).  *best_ms: time per batch step
- * measured for the last class's chosen shape (may be NULL). */
+ * of all, 2 and 1 chunks, and keeps the fastest for that class; then it times the step
+ * in both modes (ugks_batch_set_persistent) and keeps the faster.  Neither the tile shape
+ * nor the mode changes the arithmetic, so tuning steps are real steps of every active
+ * instance (each advances by 12 (trial_steps + 1) per class present, plus
+ * 2 (trial_steps + 1)).  *best_ms: time per batch step in the chosen mode (may be NULL). */
 ugks_status ugks_batch_set_walk_rows(ugks_batch b, int slot, int rows);
 int         ugks_batch_get_walk_rows(ugks_batch b, int slot);
 ugks_status ugks_batch_set_walk_vtile(ugks_batch b, int slot, int chunks);

@@ -15,6 +15,7 @@
 #include "../../include/ugks.h"
 #include "ugks_kernels.cuh"
 #include "ugks_f32.cuh"
+#include "ugks_df.cuh"
 #include "ugks_batch.cuh"
 
 using namespace ugks;
@@ -42,6 +43,10 @@ struct ugks_ctx {
   FaceRecF* fyf = nullptr;
   CellRecF* cellf = nullptr;
   double* mt4 = nullptr;     // Mt4 per face (x faces then y faces)
+  FaceRecD* fxd = nullptr;   // DF64 form: double-FP32 face and cell records, grid tables
+  FaceRecD* fyd = nullptr;
+  CellRecD* celld = nullptr;
+  float2* gdf = nullptr;
   int nchunk_neg = 0, nchunk_pos = 0;
   // FP32 form: the step runs the batch kernels over a one-instance table, so an instance
   // stepped alone executes exactly the code it executes inside a batch
@@ -113,7 +118,8 @@ const char* validate(const ugks_config* c) {
   if (!(c->kn > 0) || !isfinite(c->kn)) return "kn must be finite and > 0";
   if (!(c->alpha > 0) || !(c->omega >= 0) || !(c->omega < 2.5)) return "bad omega/alpha";
   if (!(c->dt > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt > 0";
-  if (c->precision != UGKS_FP64 && c->precision != UGKS_FP32F) return "bad precision";
+  if (c->precision != UGKS_FP64 && c->precision != UGKS_FP32F && c->precision != UGKS_DF64)
+    return "bad precision";
   for (int s = 0; s < 4; s++) {
     const ugks_bc& b = c->bc[s];
     if (b.kind < 0 || b.kind > 2) return "bad boundary kind";
@@ -164,15 +170,16 @@ std::pair<int, int> f32_row_pairs(int nv, double vmin, double vmax) {
 // Device bytes ugks_create allocates for cfg (cudaMalloc sizes, without allocator rounding).
 size_t predict_bytes(const ugks_config* c) {
   const size_t nx = c->nx, ny = c->ny, nq = (size_t)c->nu * c->nv, nc = nx * ny;
-  const bool f32 = c->precision == UGKS_FP32F;
+  const bool f32 = c->precision == UGKS_FP32F, dfm = c->precision == UGKS_DF64;
   const size_t pr_all = f32_row_pairs(c->nv, c->vmin, c->vmax).second, fs = pr_all * c->nu;
   const size_t fslot = f32 ? fs * sizeof(float4) : nq * sizeof(double2);  // f bytes per cell
   const size_t fcells = (nx + 4) * (ny + 4), nwe = (nx + 2) * (ny + 2);
   const size_t nfx = (nx + 1) * ny, nfy = nx * (ny + 1), nrb = (nc + 127) / 128;
   size_t b = 2 * fcells * fslot + 2 * 4 * sizeof(double) * nwe + sizeof(double) * kNSum * nwe;
-  b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : sizeof(FaceRec) * (nfx + nfy);
+  b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : (dfm ? sizeof(FaceRecD) : sizeof(FaceRec)) * (nfx + nfy);
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
-  b += f32 ? sizeof(CellRecF) * nc : sizeof(CellRec) * nc;
+  b += f32 ? sizeof(CellRecF) * nc : (dfm ? sizeof(CellRecD) : sizeof(CellRec)) * nc;
+  if (dfm) b += sizeof(float2) * (2 * (size_t)c->nu + 6 * (size_t)c->nv);
   b += sizeof(double) * 8 * nrb + sizeof(int) + sizeof(double) * (2 * (c->nu + c->nv) + 5 * c->nv);
   if (!f32) b += nwe * nq * 2 * sizeof(double2) + (nfx + nfy) * nq * sizeof(double2);  // slopes, face fluxes
   if (f32) {
@@ -259,7 +266,8 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
       P, fi, sums, reinterpret_cast<T2*>(h->slopes));
   if ((r = mark(h, 3)) != cudaSuccess) return r;
   const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
-  k_faces<<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy, h->mt4);
+  k_faces<kRecF64><<<(nf + 127) / 128, 128, 0, st>>>(P, sums, Wi, h->nwe, h->fxr, h->fyr, h->Fx, h->Fy,
+                                                     h->mt4);
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   const int nc = P.nx * P.ny;
   k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, h->cells, h->rpart, h->err,
@@ -276,6 +284,59 @@ cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
   return cudaGetLastError();
   }
+}
+
+// DF64 form: ghost ring, double-FP32 sums, FP64 interface and cell scalars (double-FP32
+// records), double-FP32 face fluxes and Eq. 3.
+size_t smem_face_flux_df(int nv) { return (size_t)4 * kWarpsPerBlock * nv * sizeof(df); }
+size_t smem_cell_update_df(int nv) { return (size_t)2 * kWarpsPerBlock * nv * sizeof(df); }
+cudaError_t set_smem_limits_df(int nv) {
+  cudaError_t e = cudaFuncSetAttribute(k_face_flux_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_face_flux_df(nv));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cell_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_cell_update_df(nv));
+}
+
+cudaError_t launch_step_df(ugks_ctx* h, cudaStream_t st) {
+  const Params& P = h->P;
+  DF4* fi = static_cast<DF4*>(h->f[h->cur]);
+  DF4* fo = static_cast<DF4*>(h->f[h->cur ^ 1]);
+  double* Wi = h->W[h->cur];
+  double* Wo = h->W[h->cur ^ 1];
+  DF4* sl = reinterpret_cast<DF4*>(h->slopes);
+  cudaError_t r;
+  if ((r = mark(h, 0)) != cudaSuccess) return r;
+  k_ghost_x<DF4><<<dim3(P.ny, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
+  if ((r = mark(h, 1)) != cudaSuccess) return r;
+  k_ghost_y<DF4><<<dim3(P.nx + 4, 4), 128, 0, st>>>(P, fi, Wi, h->nwe);
+  if ((r = mark(h, 2)) != cudaSuccess) return r;
+  const int nce = (P.nx + 2) * (P.ny + 2);
+  k_sums_df<<<(nce + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock, 0, st>>>(P, fi, h->sums, sl);
+  if ((r = mark(h, 3)) != cudaSuccess) return r;
+  const int nf = (P.nx + 1) * P.ny + P.nx * (P.ny + 1);
+  k_faces<kRecDF><<<(nf + 127) / 128, 128, 0, st>>>(P, h->sums, Wi, h->nwe, h->fxd, h->fyd, h->Fx, h->Fy,
+                                                    h->mt4);
+  if ((r = mark(h, 4)) != cudaSuccess) return r;
+  const int nc = P.nx * P.ny;
+  k_cells<<<h->nrblocks, 128, 0, st>>>(P, Wi, Wo, h->nwe, h->Fx, h->Fy, nullptr, h->rpart, h->err, nullptr,
+                                       h->mt4, h->celld);
+  if ((r = mark(h, 5)) != cudaSuccess) return r;
+  DF4* Xx = reinterpret_cast<DF4*>(h->xflux);
+  DF4* Xy = Xx + (size_t)(P.nx + 1) * P.ny * P.nq;
+  const int ub = (nc + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_face_flux_df<<<ub, 32 * kWarpsPerBlock, smem_face_flux_df(P.nv), st>>>(P, fi, h->fxd, h->fyd, sl, Xx, Xy);
+  k_cell_update_df<<<ub, 32 * kWarpsPerBlock, smem_cell_update_df(P.nv), st>>>(P, fi, fo, h->celld, Xx, Xy);
+  if ((r = mark(h, 6)) != cudaSuccess) return r;
+  if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
+  return cudaGetLastError();
+}
+
+// One step of the handle's form, enqueued on st.
+cudaError_t launch_any(ugks_ctx* h, cudaStream_t st) {
+  if (h->prec == UGKS_FP64) return launch_step<double>(h, st);
+  if (h->prec == UGKS_DF64) return launch_step_df(h, st);
+  return launch_step<float>(h, st);
 }
 
 constexpr int kConvBlocks = 1216;  // 8 per SM
@@ -372,6 +433,17 @@ ugks_status copy_f_in(ugks_ctx* h, const double* f, bool from_host) {
     CK(cudaMemcpy2DAsync(dst, (size_t)P.ex * P.nq * h->t2, f, row_d, row_d, P.ny, kind, h->stream));
     return UGKS_OK;
   }
+  if (h->prec == UGKS_DF64) {
+    // host rows pass through the slope buffer (32 B per velocity-cell >= 16 B of FP64 rows)
+    const double* src = f;
+    if (from_host) {
+      CK(cudaMemcpyAsync(h->slopes, f, row_d * P.ny, cudaMemcpyHostToDevice, h->stream));
+      src = reinterpret_cast<const double*>(h->slopes);
+    }
+    k_rows_to_df<<<kConvBlocks, 256, 0, h->stream>>>(src, static_cast<DF4*>(h->f[h->cur]), P, 0, P.ny);
+    CK(cudaGetLastError());
+    return UGKS_OK;
+  }
   float4* dst = static_cast<float4*>(h->f[h->cur]);
   const double* src = from_host ? static_cast<const double*>(device_view(f, row_d * P.ny)) : f;
   if (src) {  // device memory, or host memory the conversion kernel reads in place
@@ -409,6 +481,13 @@ ugks_status copy_f_out(ugks_ctx* h, double* f, bool to_host) {
   if (h->prec == UGKS_FP64) {
     const char* src = static_cast<const char*>(h->f[h->cur]) + ((size_t)2 * P.ex + 2) * P.nq * h->t2;
     CK(cudaMemcpy2DAsync(f, row_d, src, (size_t)P.ex * P.nq * h->t2, row_d, P.ny, kind, h->stream));
+    return UGKS_OK;
+  }
+  if (h->prec == UGKS_DF64) {
+    double* dst = to_host ? reinterpret_cast<double*>(h->slopes) : f;
+    k_df_to_rows<<<kConvBlocks, 256, 0, h->stream>>>(static_cast<const DF4*>(h->f[h->cur]), dst, P, 0, P.ny);
+    CK(cudaGetLastError());
+    if (to_host) CK(cudaMemcpyAsync(f, dst, row_d * P.ny, cudaMemcpyDeviceToHost, h->stream));
     return UGKS_OK;
   }
   const float4* src = static_cast<const float4*>(h->f[h->cur]);
@@ -646,7 +725,7 @@ ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const 
   k_ghost_y<double2><<<dim3(nx + 4, 4), 128, 0, st>>>(P, f0, W0, nwe);
   k_sums<double, double2><<<(nwe + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
                             smem_sums<double>(P.nv), st>>>(P, f0, sums, nullptr);
-  k_faces<<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, mt4);
+  k_faces<kRecF64><<<(nfx + nfy + 127) / 128, 128, 0, st>>>(P, sums, W0, nwe, fxr, fyr, Fx, Fy, mt4);
   k_cells<<<nrb, 128, 0, st>>>(P, W0, W1, nwe, Fx, Fy, cells, rpart, err, nullptr, mt4);
   // slopes are formed again in the update kernel: the scratch array holds no slope buffer
   k_update<double, double2><<<(nc + kWarpsPerBlock - 1) / kWarpsPerBlock, 32 * kWarpsPerBlock,
@@ -859,10 +938,10 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   };
   h->fcells = (size_t)(P.nx + 4) * (P.ny + 4);
   h->nwe = (P.nx + 2) * (P.ny + 2);
-  const size_t fbytes = h->fcells * (h->prec == UGKS_FP64 ? P.nq * sizeof(double2) : P.fs * sizeof(float4));
+  const size_t fbytes = h->fcells * (h->prec == UGKS_FP32F ? P.fs * sizeof(float4) : P.nq * sizeof(double2));
   const int nfx = (P.nx + 1) * P.ny, nfy = P.nx * (P.ny + 1), nc = P.nx * P.ny;
   h->nrblocks = (nc + 127) / 128;
-  const bool f32 = h->prec == UGKS_FP32F;
+  const bool f32 = h->prec == UGKS_FP32F, dfm = h->prec == UGKS_DF64;
   bool ok = alloc(&h->f[0], fbytes) && alloc(&h->f[1], fbytes) &&
             alloc((void**)&h->W[0], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
@@ -870,14 +949,18 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             (f32 || alloc((void**)&h->slopes, sizeof(double2) * 2 * (size_t)h->nwe * P.nq)) &&
             (f32 || alloc((void**)&h->xflux, sizeof(double2) * (size_t)(nfx + nfy) * P.nq)) &&
             (f32 ? alloc((void**)&h->fxf, sizeof(FaceRecF) * (size_t)nfx)
-                 : alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx)) &&
+                 : dfm ? alloc((void**)&h->fxd, sizeof(FaceRecD) * (size_t)nfx)
+                       : alloc((void**)&h->fxr, sizeof(FaceRec) * (size_t)nfx)) &&
             (f32 ? alloc((void**)&h->fyf, sizeof(FaceRecF) * (size_t)nfy)
-                 : alloc((void**)&h->fyr, sizeof(FaceRec) * (size_t)nfy)) &&
+                 : dfm ? alloc((void**)&h->fyd, sizeof(FaceRecD) * (size_t)nfy)
+                       : alloc((void**)&h->fyr, sizeof(FaceRec) * (size_t)nfy)) &&
             alloc((void**)&h->Fx, sizeof(double) * 4 * (size_t)nfx) &&
             alloc((void**)&h->Fy, sizeof(double) * 4 * (size_t)nfy) &&
             alloc((void**)&h->mt4, sizeof(double) * (size_t)(nfx + nfy)) &&
             (f32 ? alloc((void**)&h->cellf, sizeof(CellRecF) * (size_t)nc)
-                 : alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc)) &&
+                 : dfm ? alloc((void**)&h->celld, sizeof(CellRecD) * (size_t)nc)
+                       : alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc)) &&
+            (!dfm || alloc((void**)&h->gdf, sizeof(float2) * (2 * (size_t)P.nu + 6 * (size_t)P.nv))) &&
             alloc((void**)&h->rpart, sizeof(double) * 8 * (size_t)h->nrblocks) &&
             alloc((void**)&h->err, sizeof(int)) &&
             alloc((void**)&h->d_grid, sizeof(double) * (2 * (P.nu + P.nv) + 5 * P.nv));
@@ -914,6 +997,25 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.wu = h->d_grid + P.nu + P.nv;
   P.wv = h->d_grid + 2 * P.nu + P.nv;
   P.gref4 = h->gref4;
+  std::vector<float2> gdf_host;
+  if (dfm) {
+    // u[nu], wu[nu], v[nv], [5][nv] wv v^n and the mesh constants as double-FP32 pairs
+    auto sp = [](double x) {
+      const float hi = (float)x;
+      return make_float2(hi, (float)(x - (double)hi));
+    };
+    for (double x : h->hu) gdf_host.push_back(sp(x));
+    for (double x : h->hwu) gdf_host.push_back(sp(x));
+    for (double x : h->hv) gdf_host.push_back(sp(x));
+    for (int n = 0; n < 5; n++)
+      for (int m = 0; m < P.nv; m++) gdf_host.push_back(sp(h->hwv[m] * std::pow(h->hv[m], n)));
+    P.gdf = h->gdf;
+    P.df_tdx = sp(2.0 / P.dx);
+    P.df_tdy = sp(2.0 / P.dy);
+    P.df_idx = sp(1.0 / P.dx);
+    P.df_idy = sp(1.0 / P.dy);
+    P.df_dt = sp(P.dt);
+  }
   std::vector<float> ftab_host;
   if (h->ftab) {
     // [pr_all][12]: (w0 w0' w1 w1') (w2 w2' w3 w3') (w4 w4' v v'), then u[nu], wu[nu]
@@ -959,8 +1061,12 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
     if (h->grefd && (r = cudaMemcpyAsync(h->grefd, grefd_host.data(), sizeof(double2) * grefd_host.size(),
                                          cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
       return r;
+    if (h->gdf && (r = cudaMemcpyAsync(h->gdf, gdf_host.data(), sizeof(float2) * gdf_host.size(),
+                                       cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return r;
     if ((r = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream)) != cudaSuccess) return r;
     if (h->prec == UGKS_FP64 && (r = set_smem_limits_fp64(P.nv)) != cudaSuccess) return r;
+    if (h->prec == UGKS_DF64 && (r = set_smem_limits_df(P.nv)) != cudaSuccess) return r;
     if ((r = cudaStreamSynchronize(h->stream)) != cudaSuccess) return r;
     return h->prec == UGKS_FP32F ? setup_single_f32(h) : cudaSuccess;
   };
@@ -978,7 +1084,7 @@ void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->slopes, h->xflux, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref4, h->grefd, h->fxf, h->fyf,
-                  h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work};
+                  h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work, h->fxd, h->fyd, h->celld, h->gdf};
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->xstream) {
     cudaStreamSynchronize(h->xstream);
@@ -1046,6 +1152,9 @@ ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double*
   if (h->prec == UGKS_FP64)
     k_init_maxwellian<double2><<<nc, 128, 0, h->stream>>>(P, prim, static_cast<double2*>(h->f[h->cur]),
                                                           h->W[h->cur], h->nwe);
+  else if (h->prec == UGKS_DF64)
+    k_init_maxwellian_df<<<nc, 128, 0, h->stream>>>(P, prim, static_cast<DF4*>(h->f[h->cur]), h->W[h->cur],
+                                                    h->nwe);
   else
     k_init_maxwellian_p<<<nc, 128, 0, h->stream>>>(P, prim, static_cast<float4*>(h->f[h->cur]),
                                                    h->W[h->cur], h->nwe);
@@ -1065,8 +1174,7 @@ static cudaError_t build_graphs(ugks_ctx* h) {
     h->cur = par;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
-    const cudaError_t el = h->prec == UGKS_FP64 ? launch_step<double>(h, h->cap_stream)
-                                                : launch_step<float>(h, h->cap_stream);
+    const cudaError_t el = launch_any(h, h->cap_stream);
     e = cudaStreamEndCapture(h->cap_stream, &g);
     if (el != cudaSuccess) e = el;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[par], g, 0);
@@ -1086,7 +1194,7 @@ ugks_status ugks_step(ugks_handle h, int nsteps) {
   for (int s = 0; s < nsteps; s++) {
     cudaError_t e;
     if (h->profiling)  // direct launches so that the tracing events sit between kernels
-      e = h->prec == UGKS_FP64 ? launch_step<double>(h, h->stream) : launch_step<float>(h, h->stream);
+      e = launch_any(h, h->stream);
     else
       e = cudaGraphLaunch(h->graph[h->cur], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
@@ -1639,6 +1747,26 @@ ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms) {
       }
     if (!r) r = apply(best_r, best_v);
     best_total = best_t / trial_steps;
+  }
+  // step mode: one persistent launch (six grid barriers per step) against seven phase
+  // launches; the barriers cost more than the launches when the batch holds little work
+  if (!r && b->grid_step > 0) {
+    float t_mode[2] = {0.f, 0.f};
+    for (int m = 0; m < 2 && !r; m++) {
+      if ((r = ugks_batch_set_persistent(b, m))) break;
+      if ((r = ugks_batch_step(b, 1))) break;
+      float t = 0.f;
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) { r = bfail(b, UGKS_ECUDA, "tune: event"); break; }
+      if ((r = ugks_batch_step(b, trial_steps))) break;
+      if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+        r = bfail(b, UGKS_ECUDA, "tune: timing");
+        break;
+      }
+      t_mode[m] = t;
+    }
+    if (!r) r = ugks_batch_set_persistent(b, t_mode[1] <= t_mode[0] ? 1 : 0);
+    if (!r) best_total = fminf(t_mode[0], t_mode[1]) / trial_steps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -109,8 +109,8 @@ __device__ __noinline__ void faces_phase(const SlotDev* __restrict__ slots, cons
     const int a = find_instance(wk->start[3], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     const int loc = vb - wk->start[3][a];
-    faces_body<true>(S.P, S.sums, S.W[S.cur], S.nwe, nullptr, nullptr, S.Fx, S.Fy, S.fxf, S.fyf,
-                     S.mt4, loc * 128 + threadIdx.x);
+    faces_body<kRecF32>(S.P, S.sums, S.W[S.cur], S.nwe, S.fxf, S.fyf, S.Fx, S.Fy, S.mt4,
+                        loc * 128 + threadIdx.x);
   }
 }
 

@@ -86,6 +86,21 @@ struct __align__(16) CellRecF {
   float nBs, irx, iry, inv; // -inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 
+// DF64 form: f of one velocity, (h, b) as double-FP32 pairs (h = hh + hl, b = bh + bl)
+struct __align__(16) DF4 {
+  float hh, hl, bh, bl;
+};
+// DF64 form: the FP64 records (FaceRec, CellRec) as double-FP32 pairs, written by the FP64
+// interface and cell kernels for the DF64 update kernels (which do no FP64 arithmetic)
+struct __align__(16) FaceRecD {
+  float2 Q[2][2][8];
+  float2 G, Un, Ut, lam, Mt4, Mt5, bfac;
+  int wall, pad;
+};
+struct __align__(16) CellRecD {
+  float2 Gn, Un, Vn, lamn, bn, G1, U1, V1, lam1, b1, inv, cgn, cg1, pad;
+};
+
 struct Params {
   int nx, ny, nu, nv, nq, K;
   int ex;                 // f row length in cells: nx + 4 (two-cell ghost ring)
@@ -125,6 +140,10 @@ struct Params {
   const double* v;        // [nv]
   const double* wu;       // [nu]
   const double* wv;       // [nv]
+  // DF64 form: the same grid tables as double-FP32 pairs (hi, lo): [nu] u, [nu] wu, [nv] v,
+  // [5][nv] wv v^n; 2/dx, 2/dy, 1/dx, 1/dy, dt
+  const float2* gdf;
+  float2 df_tdx, df_tdy, df_idx, df_idy, df_dt;
 };
 
 }  // namespace ugks

@@ -861,14 +861,38 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   RF.gdt = 0.f;
 }
 
-// F32REC: the FP32-f form (FP32 face records for its walk); else the FP64 form's records.
-// Both forms' sums are FP64.
-template <bool F32REC>
+// Record kind written for the update kernels: FP64 FaceRec (FP64 form), FP32 FaceRecF
+// (FP32-f form), double-FP32 FaceRecD (DF64 form).  Every form's sums are FP64.
+enum { kRecF64 = 0, kRecF32 = 1, kRecDF = 2 };
+
+__device__ __forceinline__ float2 split_df(double a) {
+  const float h = __double2float_rn(a);
+  return make_float2(h, __double2float_rn(a - (double)h));
+}
+__device__ __forceinline__ void face_rec_df(const FaceRec& R, FaceRecD& D) {
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+      for (int c = 0; c < 8; c++) D.Q[a][b][c] = split_df(R.Q[a][b][c]);
+  D.G = split_df(R.G);
+  D.Un = split_df(R.Un);
+  D.Ut = split_df(R.Ut);
+  D.lam = split_df(R.lam);
+  D.Mt4 = split_df(R.Mt4);
+  D.Mt5 = split_df(R.Mt5);
+  D.bfac = split_df(R.bfac);
+  D.wall = R.wall;
+  D.pad = 0;
+}
+
+// rx, ry: the x- and y-face records of kind REC (FaceRec, FaceRecF or FaceRecD).
+template <int REC>
 __device__ __forceinline__ void faces_body(const Params& P, const double* __restrict__ sums,
                                            const double* __restrict__ W, int nwe,
-                                           FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
+                                           void* __restrict__ rx, void* __restrict__ ry,
                                            double* __restrict__ Fx, double* __restrict__ Fy,
-                                           FaceRecF* __restrict__ fxf, FaceRecF* __restrict__ fyf,
                                            double* __restrict__ mt4, int t) {
   const int nx = P.nx, ny = P.ny;
   const int nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
@@ -900,7 +924,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
   }
   FaceRec R;
   FaceRecF RF;
-  constexpr bool f32 = F32REC;
+  constexpr bool f32 = REC == kRecF32;
   double F[4];
   if (wall) {
     // diffuse wall: incoming half range from the gas cell's sums, outgoing wall Maxwellian
@@ -951,28 +975,36 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
     for (int c = 0; c < 4; c++) F[c] = (c == 1 || c == 2) && !isx ? Fr[3 - c] : Fr[c];
   }
   mt4[t] = R.Mt4;
+  const int r = isx ? t : t - nfx;
+  void* dst = isx ? rx : ry;
+  if constexpr (REC == kRecF32) {
+    static_cast<FaceRecF*>(dst)[r] = RF;
+  } else if constexpr (REC == kRecDF) {
+    FaceRecD D;
+    face_rec_df(R, D);
+    static_cast<FaceRecD*>(dst)[r] = D;
+  } else {
+    static_cast<FaceRec*>(dst)[r] = R;
+  }
   if (isx) {
-    if (f32) fxf[t] = RF;
-    else fxr[t] = R;
     for (int c = 0; c < 4; c++) Fx[4 * (size_t)t + c] = F[c];
   } else {
-    if (f32) fyf[t - nfx] = RF;
-    else fyr[t - nfx] = R;
     for (int c = 0; c < 4; c++) Fy[4 * (size_t)(t - nfx) + c] = F[c];
   }
 }
-// FP64 form
+// FP64 form (REC = kRecF64) and DF64 form (REC = kRecDF)
+template <int REC>
 __global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
-                        int nwe, FaceRec* __restrict__ fxr, FaceRec* __restrict__ fyr,
+                        int nwe, void* __restrict__ rx, void* __restrict__ ry,
                         double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ mt4) {
-  faces_body<false>(P, sums, W, nwe, fxr, fyr, Fx, Fy, nullptr, nullptr, mt4,
-                    blockIdx.x * blockDim.x + threadIdx.x);
+  faces_body<REC>(P, sums, W, nwe, rx, ry, Fx, Fy, mt4, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // -------------------------------------------------------------------------------------
 // Eq. 4 per cell, plus g^n, g^{n+1}, tau^n, tau^{n+1} for Eq. 3, residual partials and
 // the numerical-failure flag.
 // -------------------------------------------------------------------------------------
+// Records written: crf (FP32-f form) if set, else crd (DF64 form) if set, else cr (FP64).
 __device__ __forceinline__ void cells_body(const Params& P, const double* __restrict__ Win,
                                            double* __restrict__ Wout, int nwe,
                                            const double* __restrict__ Fx,
@@ -980,7 +1012,7 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
                                            double* __restrict__ rpart, int* __restrict__ err,
                                            CellRecF* __restrict__ crf,
                                            const double* __restrict__ mt4, double (*red)[128],
-                                           int bx) {
+                                           int bx, CellRecD* __restrict__ crd = nullptr) {
   const int c = bx * blockDim.x + threadIdx.x;
   const int nx = P.nx, nc = P.nx * P.ny;
   double d2[4] = {0, 0, 0, 0}, am[4] = {0, 0, 0, 0};
@@ -1053,6 +1085,15 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       F.iry = (float)(R.inv * refy);
       F.inv = (float)R.inv;
       crf[c] = F;
+    } else if (crd) {
+      CellRecD D;
+      D.Gn = split_df(R.Gn); D.Un = split_df(R.Un); D.Vn = split_df(R.Vn);
+      D.lamn = split_df(R.lamn); D.bn = split_df(R.bn);
+      D.G1 = split_df(R.G1); D.U1 = split_df(R.U1); D.V1 = split_df(R.V1);
+      D.lam1 = split_df(R.lam1); D.b1 = split_df(R.b1);
+      D.inv = split_df(R.inv); D.cgn = split_df(R.cgn); D.cg1 = split_df(R.cg1);
+      D.pad = make_float2(0.f, 0.f);
+      crd[c] = D;
     } else {
       cr[c] = R;
     }
@@ -1078,9 +1119,10 @@ __global__ void __launch_bounds__(128) k_cells(Params P, const double* __restric
                                                const double* __restrict__ Fy,
                                                CellRec* __restrict__ cr, double* __restrict__ rpart,
                                                int* __restrict__ err, CellRecF* __restrict__ crf,
-                                               const double* __restrict__ mt4) {
+                                               const double* __restrict__ mt4,
+                                               CellRecD* __restrict__ crd = nullptr) {
   __shared__ double red[8][128];
-  cells_body(P, Win, Wout, nwe, Fx, Fy, cr, rpart, err, crf, mt4, red, blockIdx.x);
+  cells_body(P, Win, Wout, nwe, Fx, Fy, cr, rpart, err, crf, mt4, red, blockIdx.x, crd);
 }
 
 // -------------------------------------------------------------------------------------

@@ -155,11 +155,43 @@ def make_requests(cfgs, arrivals, prims):
             for k, (c, a, p) in enumerate(zip(cfgs, arrivals, prims))]
 
 
-def gpu_server(hbm_budget: int, max_slots: int, stream=None, **kw) -> Server:
+class ModeSwitchingBatch:
+    """A batch engine whose step mode follows the work in flight: one persistent launch per
+    step (six grid barriers) when the active instances hold at least `persistent_min_vc`
+    velocity-cells, else seven phase launches, whose fixed cost is lower for small batches.
+    The mode does not change results (the same phase code runs either way)."""
+
+    def __init__(self, batch, persistent_min_vc: int):
+        self._b = batch
+        self._min = int(persistent_min_vc)
+        self._vc = {}
+
+    def __getattr__(self, name):
+        return getattr(self._b, name)
+
+    def admit(self, cfg):
+        slot = self._b.admit(cfg)
+        self._vc[slot] = cfg.nx * cfg.ny * cfg.nu * cfg.nv
+        return slot
+
+    def retire(self, slot):
+        self._b.retire(slot)
+        self._vc.pop(slot, None)
+
+    def step(self, n: int = 1):
+        want = sum(self._vc.values()) >= self._min
+        if want != self._b.persistent:
+            self._b.set_persistent(want)
+        self._b.step(n)
+
+
+def gpu_server(hbm_budget: int, max_slots: int, stream=None, persistent_min_vc: int = 200_000_000,
+               **kw) -> Server:
     """A Server over the CUDA batch engine."""
     from . import ugks
     batch = ugks.Batch(max_slots, hbm_budget, stream=stream)
-    srv = Server(batch, lambda c: ugks.state_bytes(c, ugks.FP32F), hbm_budget, max_slots, **kw)
+    engine = ModeSwitchingBatch(batch, persistent_min_vc) if batch.persistent else batch
+    srv = Server(engine, lambda c: ugks.state_bytes(c, ugks.FP32F), hbm_budget, max_slots, **kw)
     srv.batch_handle = batch
     return srv
 

@@ -15,7 +15,7 @@ from . import build as _build
 
 _STATUS = {0: "UGKS_OK", 1: "UGKS_EINVAL", 2: "UGKS_ENOMEM", 3: "UGKS_ECUDA",
            4: "UGKS_ETIMEOUT", 5: "UGKS_ENUMERIC"}
-FP64, FP32F = 0, 1
+FP64, FP32F, DF64 = 0, 1, 2
 
 # Every symbol include/ugks.h declares.
 EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",

@@ -114,7 +114,7 @@ def test_batch_tile_shape_and_tuner_do_not_change_results(U):
             B2.set_walk_vtile(x, 1 + k % 2)  # velocity tiles of 1 and 2 chunks
         B1.step(4)
         B2.step(4)
-        ms = B1.tune(1)  # advances B1 by 12*(1+1) steps per velocity class present
+        ms = B1.tune(1)  # advances B1 by 12*(1+1) per velocity class present, plus 2*(1+1)
         assert ms > 0
         for x in s1:
             assert B1.walk_rows(x) in (16, 32, 64, 128)

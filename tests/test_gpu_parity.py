@@ -112,6 +112,18 @@ def test_one_step_fp64_parity(U, oracle, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_one_step_df64_parity(U, oracle, name):
+    """DF64 form (double-FP32 f and per-velocity arithmetic): the FP64 tolerance."""
+    cfg = CASES[name]()
+    f, W = random_state(oracle, cfg, 101)
+    fr, Wr = oracle.step(cfg, f, W, 1)
+    fg, Wg = one_step(U, cfg, f, W, prec=U.DF64)
+    print(f"df64 {name}: W {rel_fields(Wg, Wr)} f {rel_f(fg, fr):.2e}")
+    assert np.all(rel_fields(Wg, Wr) <= FP64_TOL), rel_fields(Wg, Wr)
+    assert rel_f(fg, fr) <= FP64_TOL, rel_f(fg, fr)
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_one_step_fp32f_parity(U, oracle, name):
     """FP32-f form, one step from a non-equilibrium state, every edge-case configuration:
     per-field error <= 1e-6 relative, f <= 1e-5 relative to max|f|."""
@@ -136,14 +148,15 @@ def test_init_maxwellian_parity(U, oracle):
     assert rel_f(fg, fr) <= 1e-15
 
 
-def test_channel_config1_200_steps_fp64(U, oracle):
+@pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "df64"])
+def test_channel_config1_200_steps_fp64(U, oracle, prec):
     """Channel 40x20 cells, 20^2 velocities, Kn 0.1, 200 steps from the seeded
     Maxwellian: per-step parity compounds over 200 steps; require 1e-11."""
     cfg = I.workload_channel_small()
     rho, Uf, Vf, T = I.initial_prim(cfg, I.seed_for(1))
     f0, W0 = oracle.init_maxwellian(cfg, rho, Uf, Vf, T)
     fr, Wr = oracle.step(cfg, f0, W0, cfg.steps)
-    with U.Solver(cfg) as s:
+    with U.Solver(cfg, prec) as s:
         s.init_maxwellian(rho, Uf, Vf, T)
         s.step(cfg.steps)
         fg, Wg = s.get_state()
@@ -195,7 +208,7 @@ def test_collisionless_exact_shift_gpu(U, oracle):
 def test_periodic_conservation_gpu(U, oracle):
     cfg = periodic_cfg(nx=16, ny=12, nu=12, nv=12, umin=-5, umax=5, vmin=-5, vmax=5, kn=0.02)
     f, W = random_state(oracle, cfg, 33)
-    for prec in (U.FP64, U.FP32F):
+    for prec in (U.FP64, U.FP32F, U.DF64):
         with U.Solver(cfg, prec) as s:
             s.set_state(f, W)
             s.step(10)
@@ -237,9 +250,9 @@ def test_residual_matches_definition(U, oracle):
 @pytest.mark.parametrize("name", ["periodic_13x7_v37", "channel_40x20_v20", "periodic_5x4_v6x1"])
 def test_state_bytes_predicts_allocation(U, name):
     """ugks_state_bytes (used for admission against an HBM budget) equals the device bytes
-    ugks_create allocates, in both forms."""
+    ugks_create allocates, in every form."""
     cfg = CASES[name]()
-    for prec in (U.FP64, U.FP32F):
+    for prec in (U.FP64, U.FP32F, U.DF64):
         with U.Solver(cfg, prec) as s:
             assert s.device_bytes == U.state_bytes(cfg, prec), (prec, s.device_bytes)
 
@@ -313,7 +326,7 @@ def _sample_ids(cfg, n_random, seed):
     return sorted(set(edge + [int(x * (nx * ny)) for x in r]))
 
 
-@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, 1e-5), (2, FP64_TOL)])
 def test_full_size_800x400_sampled(U, oracle, prec, tol):
     """Mesh-sweep workload at full size (800x400 cells, 28^2 velocities), in the launch
     configuration the bench times: 20 steps from the seeded Maxwellian, then one more step
@@ -336,7 +349,7 @@ def test_full_size_800x400_sampled(U, oracle, prec, tol):
 
 
 @pytest.mark.parametrize("nvel", [101, 201])
-@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, 1e-5), (2, FP64_TOL)])
 def test_large_velocity_full_mesh_sampled(U, oracle, nvel, prec, tol):
     """Large-velocity workload at full size (200x100 cells, nvel^2 velocities on
     [-20,20]^2, Kn 0.01), in the launch configuration the bench times: 5 steps from the
@@ -391,14 +404,14 @@ def test_graph_replay_matches_direct_launches(U, oracle):
     f, W = random_state(oracle, cfg, 77)
     out = []
     for prof in (False, True):
-        for prec in (U.FP64, U.FP32F):
+        for prec in (U.FP64, U.FP32F, U.DF64):
             with U.Solver(cfg, prec) as s:
                 s.set_state(f, W)
                 if prof:
                     s.profile(True)
                 s.step(3)
                 out.append(s.get_state())
-    for a, b in ((0, 2), (1, 3)):
+    for a, b in ((0, 3), (1, 4), (2, 5)):
         assert np.array_equal(out[a][0], out[b][0]) and np.array_equal(out[a][1], out[b][1])
 
 

@@ -123,3 +123,38 @@ def test_poisson_arrivals_are_seeded_and_increasing():
     b = I.poisson_arrivals(20.0, 64, I.seed_for(5))
     assert np.array_equal(a, b) and np.all(np.diff(a) > 0)
     assert 1.5 < a[-1] < 6.0  # 64 arrivals at 20/s
+
+
+def test_mode_switching_follows_work_in_flight():
+    """The served batch runs one persistent launch per step when the admitted work is large
+    and phase launches when it is small (no GPU: a fake engine records the mode per step)."""
+    from paper_1810_08137_gb300 import serve
+
+    class Fake:
+        def __init__(self):
+            self.persistent, self.modes, self.n = True, [], 0
+
+        def set_persistent(self, on):
+            self.persistent = bool(on)
+
+        def admit(self, cfg):
+            self.n += 1
+            return self.n
+
+        def retire(self, slot):
+            pass
+
+        def step(self, n=1):
+            self.modes.append(self.persistent)
+
+    small = I.channel_config(nx=10, ny=5, n_vel=8)        # 3200 vc
+    big = I.channel_config(nx=100, ny=50, n_vel=40)       # 8e6 vc
+    eng = serve.ModeSwitchingBatch(Fake(), persistent_min_vc=1_000_000)
+    a = eng.admit(small)
+    eng.step()
+    b = eng.admit(big)
+    eng.step()
+    eng.retire(b)
+    eng.step()
+    eng.retire(a)
+    assert eng._b.modes == [False, True, False]
