@@ -52,8 +52,10 @@ def peaks():
 FP64_UPDATE_FLOPS_PER_VC = 2 * 58.8 + 25.6 + 12.5
 FP64_SUMS_FLOPS_PER_VC = 2 * 43.4 + 13.3 + 18.4
 # DRAM traffic of the FP32-f update kernel per velocity-cell (read + write), from the ncu
-# capture summarised in profiles/; None when the kernel has changed since that capture.
-UPDATE_TRAFFIC_PER_VC = (596.680448e6 + 465.463808e6) / 62.72e6  # kb_strip, 400x200x28^2 capture
+# capture of the current kernel summarised in profiles/fp32f_step_kernels_channel_400x200_v28.md
+# (dram__bytes_read.sum + dram__bytes_write.sum of one kb_strip launch at 400x200x28^2);
+# set to None when the kernel changes until it is captured again.
+UPDATE_TRAFFIC_PER_VC = (599.202048e6 + 464.385536e6) / 62.72e6
 
 
 class Clocks:
