@@ -45,8 +45,9 @@ typedef enum {
   UGKS_EINVAL = 1,    /* invalid argument or configuration */
   UGKS_ENOMEM = 2,    /* device allocation failed */
   UGKS_ECUDA = 3,     /* a CUDA runtime call failed */
-  UGKS_ETIMEOUT = 4,  /* a bounded device wait gave up (grid barrier of the batch's
-                         persistent step, ugks_batch_sync) */
+  UGKS_ETIMEOUT = 4,  /* a bounded device wait gave up: a grid barrier of the batch's
+                         persistent step (ugks_batch_sync), or the FP32-f update walk's wait
+                         for its asynchronous record copies (next synchronising call) */
   UGKS_ENUMERIC = 5   /* rho <= 0, T <= 0 or NaN appeared in a cell */
 } ugks_status;
 
@@ -151,8 +152,18 @@ ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double*
  * launched directly instead. */
 ugks_status ugks_step(ugks_handle h, int nsteps);
 
-/* Wait for the stream and report a recorded numerical failure. */
+/* Wait for the stream and report a recorded failure: UGKS_ENUMERIC, or UGKS_ETIMEOUT when a
+ * bounded device wait gave up.  A new state (ugks_set_state*, ugks_init_maxwellian) clears
+ * the recorded failures. */
 ugks_status ugks_sync(ugks_handle h);
+
+/* Bound of the FP32-f update walk's wait for its asynchronous record copies, in polls of
+ * the mbarrier (each suspends the waiting lanes for a hardware-chosen time; the default
+ * 2^22 is at least about a second).  When a wait runs out the walk records it and returns
+ * after draining its copies in flight; the next synchronising call reports UGKS_ETIMEOUT
+ * and the state is undefined until set again.  No effect on the other forms.
+ * Synchronises. */
+ugks_status ugks_set_wait_limit(ugks_handle h, long long polls);
 
 /* Copy W (host W_host[4][nc]) and, if prim_host != NULL, primitive variables
  * prim_host[4][nc] = (rho, U, V, T).  Synchronises. */

@@ -242,6 +242,7 @@ cudaError_t mark(ugks_ctx* h, int k) {
 
 cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st);
 cudaError_t setup_single_f32(ugks_ctx* h);
+SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile = 0);
 
 template <typename T>
 cudaError_t launch_step(ugks_ctx* h, cudaStream_t st) {
@@ -525,6 +526,7 @@ ugks_status check_err(ugks_ctx* h) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (e & 2) return fail(h, UGKS_ETIMEOUT, "a bounded wait of the update walk for its record copies gave up");
   if (e) return fail(h, UGKS_ENUMERIC, "numerical failure: rho <= 0, T <= 0 or NaN in a cell");
   return UGKS_OK;
 }
@@ -838,6 +840,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.f_idx = (float)(1.0 / P.dx);
   P.f_idy = (float)(1.0 / P.dy);
   P.f_dt = (float)P.dt;
+  P.walk_wait_polls = kWalkWaitPolls;
   for (int s = 0; s < 4; s++) {
     P.bc_kind[s] = cfg->bc[s].kind;
     P.bc_rho[s] = cfg->bc[s].rho;
@@ -1121,8 +1124,15 @@ ugks_status ugks_get_grid(ugks_handle h, double* dt, double* u, double* v, doubl
   return UGKS_OK;
 }
 
+// A new state clears the failures recorded for the previous one.
+ugks_status clear_err(ugks_ctx* h) {
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+  return UGKS_OK;
+}
+
 ugks_status ugks_set_state(ugks_handle h, const double* f_host, const double* W_host) {
   if (!h || !f_host || !W_host) return fail(h, UGKS_EINVAL, "set_state: NULL argument");
+  if (clear_err(h)) return UGKS_ECUDA;
   ugks_status s = copy_f_in(h, f_host, true);
   if (s) return s;
   s = copy_W_in(h, W_host, cudaMemcpyHostToDevice);
@@ -1133,6 +1143,7 @@ ugks_status ugks_set_state(ugks_handle h, const double* f_host, const double* W_
 
 ugks_status ugks_set_state_device(ugks_handle h, const double* f_dev, const double* W_dev) {
   if (!h || !f_dev || !W_dev) return fail(h, UGKS_EINVAL, "set_state_device: NULL argument");
+  if (clear_err(h)) return UGKS_ECUDA;
   ugks_status s = copy_f_in(h, f_dev, false);
   if (s) return s;
   return copy_W_in(h, W_dev, cudaMemcpyDeviceToDevice);
@@ -1141,6 +1152,7 @@ ugks_status ugks_set_state_device(ugks_handle h, const double* f_dev, const doub
 ugks_status ugks_init_maxwellian(ugks_handle h, const double* rho, const double* U, const double* V,
                                  const double* T) {
   if (!h || !rho || !U || !V || !T) return fail(h, UGKS_EINVAL, "init_maxwellian: NULL argument");
+  if (clear_err(h)) return UGKS_ECUDA;
   const Params& P = h->P;
   const int nc = P.nx * P.ny;
   for (int c = 0; c < nc; c++)
@@ -1200,6 +1212,17 @@ ugks_status ugks_step(ugks_handle h, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur ^= 1;
     h->steps_done++;
+  }
+  return UGKS_OK;
+}
+
+ugks_status ugks_set_wait_limit(ugks_handle h, long long polls) {
+  if (!h || polls < 0) return fail(h, UGKS_EINVAL, "set_wait_limit: bad argument");
+  h->P.walk_wait_polls = polls > (1LL << 30) ? (1 << 30) : (int)polls;
+  if (h->d_slot) {  // the FP32-f step reads its parameters from its slot descriptor
+    CK(cudaStreamSynchronize(h->stream));
+    const SlotDev S = slot_desc(h, kWalkRows);
+    CK(cudaMemcpy(h->d_slot, &S, sizeof(SlotDev), cudaMemcpyHostToDevice));
   }
   return UGKS_OK;
 }
@@ -1325,7 +1348,7 @@ ugks_status bfail(ugks_batch_ctx* b, ugks_status s, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, UGKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile = 0) {
+SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile) {
   SlotDev S;
   memset(&S, 0, sizeof S);
   S.P = h->P;

@@ -152,7 +152,19 @@ __device__ __forceinline__ void walk_item(const SlotDev& S, int ns, int nt, int 
 // Update sweep: one warp per work item (strip, row tile, velocity chunk).
 __device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                             float4* strip_sm) {
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this warp's two mbarriers of the record ring (shared memory may have served another
+  // phase before: initialise them here)
+  float4* wsm = strip_sm + warp * kStripWarpF4;
+  const uint32_t bars = smem_addr(wsm + kFRing * kFPos * 32 + kRing * kStripChunks);
+  if (lane == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  unsigned nrec = 0;
+  bool ok = true;
   const int total = wk->start[5][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[5], wk->n, vb);
@@ -166,12 +178,13 @@ __device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, cons
       walk_item(S, ns, nt, it, bx, by, ck);
       // full strips (all but the last of a row when kStripW does not divide nx) with the
       // strip width known at compile time
+      if (!ok) continue;  // a wait of this warp gave up: its walks are skipped (err is set)
       if ((bx + 1) * kStripW <= S.P.nx)
-        strip_body_p<kStripW, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
-                                    S.walk_rows, bx, by, ck, strip_sm + warp * kStripWarpF4);
+        ok = strip_body_p<kStripW, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                         S.walk_rows, bx, by, ck, wsm, nrec, S.err);
       else
-        strip_body_p<kStripW, false>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
-                                     S.walk_rows, bx, by, ck, strip_sm + warp * kStripWarpF4);
+        ok = strip_body_p<kStripW, false>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                          S.walk_rows, bx, by, ck, wsm, nrec, S.err);
     }
   }
 }

@@ -103,6 +103,46 @@ __device__ __forceinline__ df df_exp(df x) {
   return {__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)};
 }
 
+// ---- two double-FP32 numbers at once (two velocities of a lane), on packed FP32 pairs ----
+// The operations of the scalar double-FP32 type, lane by lane: each packed instruction does
+// the same operation on the .x and .y parts, so the results equal the scalar ones bitwise.
+struct df2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ df2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+  const df2 s = two_sum2(a.hi, b.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(a.lo, b.lo)));
+}
+__device__ __forceinline__ df2 df2_neg(df2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ df2 df2_sub(df2 a, df2 b) { return df2_add(a, df2_neg(b)); }
+__device__ __forceinline__ df2 df2_mul(df2 a, df2 b) {
+  const float2 p = mul2(a.hi, b.hi);
+  const float2 e = fma2(a.lo, b.hi, fma2(a.hi, b.lo, fma2(a.hi, b.hi, neg2(p))));
+  return fast_two_sum2(p, e);
+}
+// a b + c
+__device__ __forceinline__ df2 df2_fma(df2 a, df2 b, df2 c) {
+  const float2 p = mul2(a.hi, b.hi);
+  const float2 pl = fma2(a.lo, b.hi, fma2(a.hi, b.lo, fma2(a.hi, b.hi, neg2(p))));
+  const df2 s = two_sum2(c.hi, p);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(c.lo, pl)));
+}
+__device__ __forceinline__ df2 df2_bcast(df a) { return {make_float2(a.hi, a.hi), make_float2(a.lo, a.lo)}; }
+__device__ __forceinline__ df2 df2_of(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ df df2_x(df2 a) { return {a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df df2_y(df2 a) { return {a.hi.y, a.lo.y}; }
+__device__ __forceinline__ df2 df2_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
 // =====================================================================================
 // DF64 form of the step: f stored as double-FP32 pairs (DF4), the per-velocity arithmetic of
 // the sums (S1, S7), the micro flux (S6, S8) and the implicit update (Eq. 3) in double-FP32
@@ -253,6 +293,91 @@ __global__ void k_init_maxwellian_df(Params P, const double* __restrict__ prim, 
 // cell whose sums are formed go to the slope buffer (two DF4 per velocity-cell: r_x and r_y
 // of h and b) for the face-flux kernel.
 // -------------------------------------------------------------------------------------
+// The per-lane sums of one half of the v axis (a_n, ab_n, x_n, xb_n, y_n, yb_n as in sums_body).
+struct SumsHalfDF {
+  df a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
+};
+// Close a half (north: the N side, else S): its 16 face sums reduced over the warp into
+// `side` (lanes < 16), and its sums added to the totals of the x sides.  Not inlined: one copy
+// of this long reduction serves both halves (the kernel's code otherwise misses the
+// instruction cache).
+__device__ __noinline__ void close_half_df(const SumsHalfDF& h, df u, df wu, df cu, df tdx, df tdy, bool north,
+                                           int lane, df& side, df* tot) {
+  auto pm = [&](df a, df y) { return north ? df_add(a, y) : df_sub(a, y); };
+  const df P0 = pm(h.a0, h.y0), P1 = pm(h.a1, h.y1), P2 = pm(h.a2, h.y2), P3 = pm(h.a3, h.y3);
+  const df Pb0 = pm(h.ab0, h.yb0), Pb1 = pm(h.ab1, h.yb1);
+  const df Z1 = df_fma(cu, h.x1, df_mul(tdy, h.y2)), Z2 = df_fma(cu, h.x2, df_mul(tdy, h.y3));
+  const df Z3 = df_fma(cu, h.x3, df_mul(tdy, h.y4)), Zb1 = df_fma(cu, h.xb1, df_mul(tdy, h.yb2));
+  const df uu = df_mul(u, u);
+  // (uu A + B)/2 + C/2
+  auto e4 = [&](df A, df B, df C) { return df_half(df_add(df_fma(uu, A, B), C)); };
+  df v[16];
+  v[0] = df_mul(wu, P0);
+  v[1] = df_mul(df_mul(wu, u), P0);
+  v[2] = df_mul(wu, P1);
+  v[3] = df_mul(wu, e4(P0, P2, Pb0));
+  const df ws = df_mul(wu, tdx);
+  v[4] = df_mul(ws, h.x0);
+  v[5] = df_mul(df_mul(ws, u), h.x0);
+  v[6] = df_mul(ws, h.x1);
+  v[7] = df_mul(ws, e4(h.x0, h.x2, h.xb0));
+  v[8] = df_mul(wu, P1);
+  v[9] = df_mul(df_mul(wu, u), P1);
+  v[10] = df_mul(wu, P2);
+  v[11] = df_mul(wu, e4(P1, P3, Pb1));
+  v[12] = df_mul(wu, Z1);
+  v[13] = df_mul(df_mul(wu, u), Z1);
+  v[14] = df_mul(wu, Z2);
+  v[15] = df_mul(wu, e4(Z1, Z3, Zb1));
+  const df r = warp_reduce_scatter_df<16>(v, lane);
+  if (lane < 16) side = df_add(side, r);
+  const df add[kSumsTotals] = {h.a0, h.a1, h.a2, h.ab0, h.x0, h.x1, h.x2, h.xb0, h.y0, h.y1, h.y2, h.y3, h.yb0, h.yb1};
+#pragma unroll
+  for (int t = 0; t < kSumsTotals; t++) tot[t] = df_add(tot[t], add[t]);
+}
+
+// The face sums of the x sides from the totals over both halves (E: u > 0 with f + r_x,
+// W: u < 0 with f - r_x, u = 0 half to each), reduced over the warp: entry `lane`.
+__device__ __noinline__ df x_sums_df(const df* tot, df u, df wu, df cu, df tdy, int lane) {
+  const df tA0 = tot[0], tA1 = tot[1], tA2 = tot[2], tAb = tot[3], tR0 = tot[4], tR1 = tot[5];
+  const df tR2 = tot[6], tRb = tot[7], tC0 = tot[8], tC1 = tot[9], tC2 = tot[10], tC3 = tot[11];
+  const df tCb0 = tot[12], tCb1 = tot[13];
+  const df D0 = df_fma(cu, tR0, df_mul(tdy, tC1)), D1 = df_fma(cu, tR1, df_mul(tdy, tC2));
+  const df D2 = df_fma(cu, tR2, df_mul(tdy, tC3)), Db = df_fma(cu, tRb, df_mul(tdy, tCb1));
+  const bool upos = u.hi > 0.f, uneg = u.hi < 0.f;
+  const df uu = df_mul(u, u);
+  auto e4 = [&](df A, df B, df C) { return df_half(df_add(df_fma(uu, A, B), C)); };
+  df xv[32];
+#pragma unroll
+  for (int sd = 0; sd < 2; sd++) {
+    // weight: wu on the upwind side, wu/2 on both sides for u = 0, 0 otherwise
+    const bool full = sd == 0 ? upos : uneg, none = sd == 0 ? uneg : upos;
+    const df wgt = none ? df_zero() : (full ? wu : df_half(wu));
+    auto pmx = [&](df a, df x) { return sd == 0 ? df_add(a, x) : df_sub(a, x); };
+    const df F0 = pmx(tA0, tR0), F1 = pmx(tA1, tR1), F2 = pmx(tA2, tR2), Fb = pmx(tAb, tRb);
+    df* o = xv + 16 * sd;
+    const df wgu = df_mul(wgt, u);
+    o[0] = df_mul(wgt, F0);
+    o[1] = df_mul(wgu, F0);
+    o[2] = df_mul(wgt, F1);
+    o[3] = df_mul(wgt, e4(F0, F2, Fb));
+    const df ws = df_mul(wgt, tdy);
+    o[4] = df_mul(ws, tC0);
+    o[5] = df_mul(df_mul(ws, u), tC0);
+    o[6] = df_mul(ws, tC1);
+    o[7] = df_mul(ws, e4(tC0, tC2, tCb0));
+    o[8] = df_mul(wgu, F0);
+    o[9] = df_mul(df_mul(wgu, u), F0);
+    o[10] = df_mul(wgu, F1);
+    o[11] = df_mul(wgu, e4(F0, F2, Fb));
+    o[12] = df_mul(wgu, D0);
+    o[13] = df_mul(df_mul(wgu, u), D0);
+    o[14] = df_mul(wgu, D1);
+    o[15] = df_mul(wgu, e4(D0, D2, Db));
+  }
+  return warp_reduce_scatter_df<32>(xv, lane);
+}
+
 __global__ void __launch_bounds__(128) k_sums_df(Params P, const DF4* __restrict__ f,
                                                  double* __restrict__ sums, DF4* __restrict__ slopes) {
   const int nv = P.nv, nu = P.nu, nq = P.nq;
@@ -341,39 +466,11 @@ __global__ void __launch_bounds__(128) k_sums_df(Params P, const DF4* __restrict
       x0 = df_fma(hw, rxh, x0); xb0 = df_fma(hw, rxb, xb0);
       y0 = df_fma(hw, ryh, y0); yb0 = df_fma(hw, ryb, yb0);
     };
-    // close a half: its face sums (sy = -1: S side, +1: N side), then add it to the totals
+    // close a half: its face sums, then add it to the totals
     auto close = [&](bool north, df& side) {
-      auto pm = [&](df a, df y) { return north ? df_add(a, y) : df_sub(a, y); };
-      const df P0 = pm(a0, y0), P1 = pm(a1, y1), P2 = pm(a2, y2), P3 = pm(a3, y3);
-      const df Pb0 = pm(ab0, yb0), Pb1 = pm(ab1, yb1);
-      const df Z1 = df_fma(cu, x1, df_mul(tdy, y2)), Z2 = df_fma(cu, x2, df_mul(tdy, y3));
-      const df Z3 = df_fma(cu, x3, df_mul(tdy, y4)), Zb1 = df_fma(cu, xb1, df_mul(tdy, yb2));
-      const df uu = df_mul(u, u);
-      // (uu A + B)/2 + C/2
-      auto e4 = [&](df A, df B, df C) { return df_half(df_add(df_fma(uu, A, B), C)); };
-      df v[16];
-      v[0] = df_mul(wu, P0);
-      v[1] = df_mul(df_mul(wu, u), P0);
-      v[2] = df_mul(wu, P1);
-      v[3] = df_mul(wu, e4(P0, P2, Pb0));
-      const df ws = df_mul(wu, tdx);
-      v[4] = df_mul(ws, x0);
-      v[5] = df_mul(df_mul(ws, u), x0);
-      v[6] = df_mul(ws, x1);
-      v[7] = df_mul(ws, e4(x0, x2, xb0));
-      v[8] = df_mul(wu, P1);
-      v[9] = df_mul(df_mul(wu, u), P1);
-      v[10] = df_mul(wu, P2);
-      v[11] = df_mul(wu, e4(P1, P3, Pb1));
-      v[12] = df_mul(wu, Z1);
-      v[13] = df_mul(df_mul(wu, u), Z1);
-      v[14] = df_mul(wu, Z2);
-      v[15] = df_mul(wu, e4(Z1, Z3, Zb1));
-      const df r = warp_reduce_scatter_df<16>(v, lane);
-      if (lane < 16) side = df_add(side, r);
-      const df h[kSumsTotals] = {a0, a1, a2, ab0, x0, x1, x2, xb0, y0, y1, y2, y3, yb0, yb1};
-#pragma unroll
-      for (int t = 0; t < kSumsTotals; t++) tot[t] = df_add(tot[t], h[t]);
+      const SumsHalfDF h = {a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1,
+                            y0, y1, y2, y3, y4, yb0, yb1, yb2};
+      close_half_df(h, u, wu, cu, tdx, tdy, north, lane, side, tot);
     };
     zero();
     rows(0, mneg);
@@ -383,44 +480,7 @@ __global__ void __launch_bounds__(128) k_sums_df(Params P, const DF4* __restrict
     if (v0) row_v0(mneg);
     rows(mpos, nv);
     close(true, on);
-    // x sides: E gets u > 0 (f + r_x), W gets u < 0 (f - r_x), u = 0 half to each
-    const df tA0 = tot[0], tA1 = tot[1], tA2 = tot[2], tAb = tot[3], tR0 = tot[4], tR1 = tot[5];
-    const df tR2 = tot[6], tRb = tot[7], tC0 = tot[8], tC1 = tot[9], tC2 = tot[10], tC3 = tot[11];
-    const df tCb0 = tot[12], tCb1 = tot[13];
-    const df D0 = df_fma(cu, tR0, df_mul(tdy, tC1)), D1 = df_fma(cu, tR1, df_mul(tdy, tC2));
-    const df D2 = df_fma(cu, tR2, df_mul(tdy, tC3)), Db = df_fma(cu, tRb, df_mul(tdy, tCb1));
-    const bool upos = u.hi > 0.f, uneg = u.hi < 0.f;
-    const df uu = df_mul(u, u);
-    auto e4 = [&](df A, df B, df C) { return df_half(df_add(df_fma(uu, A, B), C)); };
-    df xv[32];
-#pragma unroll
-    for (int sd = 0; sd < 2; sd++) {
-      // weight: wu on the upwind side, wu/2 on both sides for u = 0, 0 otherwise
-      const bool full = sd == 0 ? upos : uneg, none = sd == 0 ? uneg : upos;
-      const df wgt = none ? df_zero() : (full ? wu : df_half(wu));
-      auto pmx = [&](df a, df x) { return sd == 0 ? df_add(a, x) : df_sub(a, x); };
-      const df F0 = pmx(tA0, tR0), F1 = pmx(tA1, tR1), F2 = pmx(tA2, tR2), Fb = pmx(tAb, tRb);
-      df* o = xv + 16 * sd;
-      const df wgu = df_mul(wgt, u);
-      o[0] = df_mul(wgt, F0);
-      o[1] = df_mul(wgu, F0);
-      o[2] = df_mul(wgt, F1);
-      o[3] = df_mul(wgt, e4(F0, F2, Fb));
-      const df ws = df_mul(wgt, tdy);
-      o[4] = df_mul(ws, tC0);
-      o[5] = df_mul(df_mul(ws, u), tC0);
-      o[6] = df_mul(ws, tC1);
-      o[7] = df_mul(ws, e4(tC0, tC2, tCb0));
-      o[8] = df_mul(wgu, F0);
-      o[9] = df_mul(df_mul(wgu, u), F0);
-      o[10] = df_mul(wgu, F1);
-      o[11] = df_mul(wgu, e4(F0, F2, Fb));
-      o[12] = df_mul(wgu, D0);
-      o[13] = df_mul(df_mul(wgu, u), D0);
-      o[14] = df_mul(wgu, D1);
-      o[15] = df_mul(wgu, e4(D0, D2, Db));
-    }
-    ox = df_add(ox, warp_reduce_scatter_df<32>(xv, lane));
+    ox = df_add(ox, x_sums_df(tot, u, wu, cu, tdy, lane));
   }
   double* out = sums + (size_t)cell * kNSum;
   out[kSumE + lane] = to_double(ox);  // lanes 0..15: E side, 16..31: W side
@@ -499,17 +559,31 @@ __global__ void __launch_bounds__(128) k_face_flux_df(Params P, const DF4* __res
   DF4* ys0 = Xy + ((size_t)j * nx + i) * nq;              // S face; N face: + nx nq
   const bool pW = P.bc_kind[0] == 2, pE = P.bc_kind[1] == 2, pS = P.bc_kind[2] == 2, pN = P.bc_kind[3] == 2;
 
-  // X of a face from the face value (fh, fb) and slope term (dh_, db_) of its upwind side;
-  // inc: the gas side is upwind (a wall face then passes dt f_up, else dt g_wall)
-  auto flux = [&](const FaceKD& F, const df (&qh)[4], const df (&qb)[4], df vv, df g, df fh, df fb,
-                  df dh_, df db_, bool inc) {
+  // X of a face for the two velocities of a lane (packed): face value (fh, fb) and slope term
+  // (dh_, db_) of its upwind side; inc: the gas side is upwind (a wall face then passes
+  // dt f_up, else dt g_wall)
+  const df2 dt2 = df2_bcast(dtT);
+  bool act_ = false;  // this lane's u index is a real one (set per chunk of 32 u)
+  auto flux = [&](const FaceKD& F, const df (&qh)[4], const df (&qb)[4], df2 vv, df2 g, df2 fh, df2 fb,
+                  df2 dh_, df2 db_, bool inc, df2& xh, df2& xb) {
     if (F.wall) {
-      return inc ? mk4(df_mul(dtT, fh), df_mul(dtT, fb))
-                 : mk4(df_mul(dtT, g), df_mul(dtT, df_mul(F.bf, g)));
+      xh = inc ? df2_mul(dt2, fh) : df2_mul(dt2, g);
+      xb = inc ? df2_mul(dt2, fb) : df2_mul(dt2, df2_mul(df2_bcast(F.bf), g));
+      return;
     }
-    const df xh = df_sub(df_fma(horner3_df(qh, vv), g, df_mul(F.Mt4, fh)), df_mul(F.Mt5, dh_));
-    const df xb = df_sub(df_fma(horner3_df(qb, vv), g, df_mul(F.Mt4, fb)), df_mul(F.Mt5, db_));
-    return mk4(xh, xb);
+    auto horner = [&](const df (&q)[4]) {
+      return df2_fma(df2_fma(df2_fma(df2_bcast(q[3]), vv, df2_bcast(q[2])), vv, df2_bcast(q[1])), vv,
+                     df2_bcast(q[0]));
+    };
+    const df2 m4 = df2_bcast(F.Mt4), m5 = df2_bcast(F.Mt5);
+    xh = df2_sub(df2_fma(horner(qh), g, df2_mul(m4, fh)), df2_mul(m5, dh_));
+    xb = df2_sub(df2_fma(horner(qb), g, df2_mul(m4, fb)), df2_mul(m5, db_));
+  };
+  // store the pair of a face's fluxes: row A always, row B when it is a real row
+  auto put = [&](DF4* base, size_t qA, size_t qB, bool hasB, df2 xh, df2 xb) {
+    if (!act_) return;
+    base[qA] = mk4(df2_x(xh), df2_x(xb));
+    if (hasB) base[qB] = mk4(df2_y(xh), df2_y(xb));
   };
   auto gfac = [](const FaceRecD& R, df u, float2 U) {
     return df_mul(dfv(R.G), df_exp(neg_lam_sq(dfv(R.lam), df_sub(u, dfv(U)))));
@@ -519,6 +593,7 @@ __global__ void __launch_bounds__(128) k_face_flux_df(Params P, const DF4* __res
     const int k = k0 + lane;
     const bool act = k < nu;
     const int kk = act ? k : nu - 1;
+    act_ = act;
     const df u = dfv(tu[kk]);
     df gu[4];
     gu[0] = gfac(RW, u, RW.Un);
@@ -562,51 +637,66 @@ __global__ void __launch_bounds__(128) k_face_flux_df(Params P, const DF4* __res
       const long yso = VUP ? -(long)P.wx * nq : (long)P.wx * nq;  // ... in the slope buffer
       const bool yg = VUP ? j == 0 : j == ny - 1;
       const bool yz = (VUP && j == 0 && pS) || (!VUP && j == ny - 1 && pN);
-      for (int m = m0; m < m1; m++) {
-        const df vv = dfv(tv[m]);
-        const size_t q = (size_t)m * nu + kk;
-        const DF4* p = fc0 + q;
-        const DF4 c = p[0];
-        const DF4* sq = sl0 + 2 * q;
-        const DF4 a = sq[0], b = sq[1];  // half slopes r_x, r_y of the cell (h, b)
-        const df cv = df_mul(vv, tdy);
-        const df dch = df_fma(cu, dh(a), df_mul(cv, dh(b))), dcb = df_fma(cu, db(a), df_mul(cv, db(b)));
-        // f_up = f + r on the downwind face of the cell (r_x for u > 0, -r_x for u < 0)
-        const df fxh = up ? df_add(dh(c), dh(a)) : df_sub(dh(c), dh(a));
-        const df fxb = up ? df_add(db(c), db(a)) : df_sub(db(c), db(a));
-        DF4 X = flux(KXd, qX[0], qX[1], vv, df_mul(gXd, evXd[m]), fxh, fxb, dch, dcb, true);
-        if (act) xd0[q] = X;
+      // two rows at a time (packed pairs; an odd last row is paired with itself)
+      for (int m = m0; m < m1; m += 2) {
+        const bool hasB = m + 1 < m1;
+        const int mB = hasB ? m + 1 : m;
+        const df2 vv = df2_of(dfv(tv[m]), dfv(tv[mB]));
+        const size_t qA = (size_t)m * nu + kk, qB = (size_t)mB * nu + kk;
+        const DF4* pA = fc0 + qA;
+        const DF4* pB = fc0 + qB;
+        const DF4 cA = pA[0], cB = pB[0];
+        const DF4* sA = sl0 + 2 * qA;
+        const DF4* sB = sl0 + 2 * qB;
+        const DF4 aA = sA[0], bA = sA[1], aB = sB[0], bB = sB[1];  // half slopes r_x, r_y
+        const df2 ch = df2_of(dh(cA), dh(cB)), cb = df2_of(db(cA), db(cB));
+        const df2 axh = df2_of(dh(aA), dh(aB)), axb = df2_of(db(aA), db(aB));
+        const df2 ayh = df2_of(dh(bA), dh(bB)), ayb = df2_of(db(bA), db(bB));
+        const df2 cv = df2_mul(vv, df2_bcast(tdy));
+        const df2 cu2 = df2_bcast(cu);
+        const df2 dch = df2_fma(cu2, axh, df2_mul(cv, ayh)), dcb = df2_fma(cu2, axb, df2_mul(cv, ayb));
+        df2 xh, xb;
+        // downwind x face: f_up = f + r_x (u > 0) or f - r_x (u < 0)
+        flux(KXd, qX[0], qX[1], vv, df2_mul(df2_bcast(gXd), df2_of(evXd[m], evXd[mB])),
+             up ? df2_add(ch, axh) : df2_sub(ch, axh), up ? df2_add(cb, axb) : df2_sub(cb, axb), dch, dcb,
+             true, xh, xb);
+        put(xd0, qA, qB, hasB, xh, xb);
         if (xg) {
-          const DF4 xu = p[xo];
-          const DF4* su = sq + 2 * xo;
-          DF4 au = su[0], bu = su[1];
-          if (xz) au = bu = mk4(df_zero(), df_zero());
-          const df duh = df_fma(cu, dh(au), df_mul(cv, dh(bu))), dub = df_fma(cu, db(au), df_mul(cv, db(bu)));
+          const DF4 xuA = pA[xo], xuB = pB[xo];
+          DF4 auA = sA[2 * xo], buA = sA[2 * xo + 1], auB = sB[2 * xo], buB = sB[2 * xo + 1];
+          if (xz) auA = buA = auB = buB = mk4(df_zero(), df_zero());
+          const df2 uxh = df2_of(dh(auA), dh(auB)), uxb = df2_of(db(auA), db(auB));
+          const df2 uyh = df2_of(dh(buA), dh(buB)), uyb = df2_of(db(buA), db(buB));
+          const df2 duh = df2_fma(cu2, uxh, df2_mul(cv, uyh)), dub = df2_fma(cu2, uxb, df2_mul(cv, uyb));
+          const df2 gh_ = df2_of(dh(xuA), dh(xuB)), gb_ = df2_of(db(xuA), db(xuB));
           df qg[2][4];
 #pragma unroll
           for (int cc = 0; cc < 2; cc++) poly_v_df(RXg.Q[xs][cc], u, true, qg[cc]);
-          const df gh_ = up ? df_add(dh(xu), dh(au)) : df_sub(dh(xu), dh(au));
-          const df gb_ = up ? df_add(db(xu), db(au)) : df_sub(db(xu), db(au));
-          X = flux(KXg, qg[0], qg[1], vv, df_mul(gXg, evXg[m]), gh_, gb_, duh, dub, false);
-          if (act) xg0[q] = X;
+          flux(KXg, qg[0], qg[1], vv, df2_mul(df2_bcast(gXg), df2_of(evXg[m], evXg[mB])),
+               up ? df2_add(gh_, uxh) : df2_sub(gh_, uxh), up ? df2_add(gb_, uxb) : df2_sub(gb_, uxb), duh,
+               dub, false, xh, xb);
+          put(xg0, qA, qB, hasB, xh, xb);
         }
-        const df fyh = VUP ? df_add(dh(c), dh(b)) : df_sub(dh(c), dh(b));
-        const df fyb = VUP ? df_add(db(c), db(b)) : df_sub(db(c), db(b));
-        X = flux(KYd, qY[0], qY[1], vv, df_mul(gYd, evYd[m]), fyh, fyb, dch, dcb, true);
-        if (act) yd0[q] = X;
+        // downwind y face: f_up = f + r_y (v > 0) or f - r_y (v < 0)
+        flux(KYd, qY[0], qY[1], vv, df2_mul(df2_bcast(gYd), df2_of(evYd[m], evYd[mB])),
+             VUP ? df2_add(ch, ayh) : df2_sub(ch, ayh), VUP ? df2_add(cb, ayb) : df2_sub(cb, ayb), dch, dcb,
+             true, xh, xb);
+        put(yd0, qA, qB, hasB, xh, xb);
         if (yg) {
-          const DF4 yu = p[yo];
-          const DF4* sw = sq + 2 * yso;
-          DF4 av = sw[0], bv = sw[1];
-          if (yz) av = bv = mk4(df_zero(), df_zero());
-          const df dvh = df_fma(cu, dh(av), df_mul(cv, dh(bv))), dvb = df_fma(cu, db(av), df_mul(cv, db(bv)));
+          const DF4 yuA = pA[yo], yuB = pB[yo];
+          DF4 avA = sA[2 * yso], bvA = sA[2 * yso + 1], avB = sB[2 * yso], bvB = sB[2 * yso + 1];
+          if (yz) avA = bvA = avB = bvB = mk4(df_zero(), df_zero());
+          const df2 vxh = df2_of(dh(avA), dh(avB)), vxb = df2_of(db(avA), db(avB));
+          const df2 vyh = df2_of(dh(bvA), dh(bvB)), vyb = df2_of(db(bvA), db(bvB));
+          const df2 dvh = df2_fma(cu2, vxh, df2_mul(cv, vyh)), dvb = df2_fma(cu2, vxb, df2_mul(cv, vyb));
+          const df2 gh_ = df2_of(dh(yuA), dh(yuB)), gb_ = df2_of(db(yuA), db(yuB));
           df qg[2][4];
 #pragma unroll
           for (int cc = 0; cc < 2; cc++) poly_v_df(RYg.Q[ys][cc], u, false, qg[cc]);
-          const df gh_ = VUP ? df_add(dh(yu), dh(bv)) : df_sub(dh(yu), dh(bv));
-          const df gb_ = VUP ? df_add(db(yu), db(bv)) : df_sub(db(yu), db(bv));
-          X = flux(KYg, qg[0], qg[1], vv, df_mul(gYg, evYg[m]), gh_, gb_, dvh, dvb, false);
-          if (act) yg0[q] = X;
+          flux(KYg, qg[0], qg[1], vv, df2_mul(df2_bcast(gYg), df2_of(evYg[m], evYg[mB])),
+               VUP ? df2_add(gh_, vyh) : df2_sub(gh_, vyh), VUP ? df2_add(gb_, vyb) : df2_sub(gb_, vyb),
+               dvh, dvb, false, xh, xb);
+          put(yg0, qA, qB, hasB, xh, xb);
         }
       }
     };
@@ -652,20 +742,34 @@ __global__ void __launch_bounds__(128) k_cell_update_df(Params P, const DF4* __r
     const df u = dfv(tu[kk]);
     const df gun = df_mul(dfv(C.Gn), df_exp(neg_lam_sq(dfv(C.lamn), df_sub(u, dfv(C.Un)))));
     const df gu1 = df_mul(dfv(C.G1), df_exp(neg_lam_sq(dfv(C.lam1), df_sub(u, dfv(C.U1)))));
-    const df fxu = df_mul(u, idx);
-    for (int m = 0; m < nv; m++) {
-      const df fyv = df_mul(dfv(tv[m]), idy);
-      const size_t q = (size_t)m * nu + kk;
-      const DF4 c = fc0[q];
-      const DF4 XW = xw0[q], XE = xw0[nq + q], XS = ys0[q], XN = ys0[(size_t)nx * nq + q];
-      const df flh = df_fma(fxu, df_sub(dh(XW), dh(XE)), df_mul(fyv, df_sub(dh(XS), dh(XN))));
-      const df flb = df_fma(fxu, df_sub(db(XW), db(XE)), df_mul(fyv, df_sub(db(XS), db(XN))));
-      const df gnh = df_mul(gun, ev[m]), g1h = df_mul(gu1, ev[nv + m]);
-      const df ch = dh(c), cb = db(c);
-      const df dhh = df_mul(inv, df_add(flh, df_add(df_mul(cg1, df_sub(g1h, ch)), df_mul(cgn, df_sub(gnh, ch)))));
-      const df dbb = df_mul(inv, df_add(flb, df_add(df_sub(df_mul(cg1b, g1h), df_mul(cg1, cb)),
-                                                    df_sub(df_mul(cgnb, gnh), df_mul(cgn, cb)))));
-      if (act) fo0[q] = mk4(df_add(ch, dhh), df_add(cb, dbb));
+    const df2 fxu = df2_bcast(df_mul(u, idx));
+    const df2 gun2 = df2_bcast(gun), gu12 = df2_bcast(gu1);
+    const df2 inv2 = df2_bcast(inv), cg12 = df2_bcast(cg1), cgn2 = df2_bcast(cgn);
+    const df2 cg1b2 = df2_bcast(cg1b), cgnb2 = df2_bcast(cgnb);
+    // two rows at a time (packed pairs; an odd last row is paired with itself)
+    for (int m = 0; m < nv; m += 2) {
+      const bool hasB = m + 1 < nv;
+      const int mB = hasB ? m + 1 : m;
+      const df2 fyv = df2_mul(df2_of(dfv(tv[m]), dfv(tv[mB])), df2_bcast(idy));
+      const size_t qA = (size_t)m * nu + kk, qB = (size_t)mB * nu + kk;
+      const DF4 cA = fc0[qA], cB = fc0[qB];
+      const DF4 WA = xw0[qA], EA = xw0[nq + qA], SA = ys0[qA], NA = ys0[(size_t)nx * nq + qA];
+      const DF4 WB = xw0[qB], EB = xw0[nq + qB], SB = ys0[qB], NB = ys0[(size_t)nx * nq + qB];
+      const df2 flh = df2_fma(fxu, df2_sub(df2_of(dh(WA), dh(WB)), df2_of(dh(EA), dh(EB))),
+                              df2_mul(fyv, df2_sub(df2_of(dh(SA), dh(SB)), df2_of(dh(NA), dh(NB)))));
+      const df2 flb = df2_fma(fxu, df2_sub(df2_of(db(WA), db(WB)), df2_of(db(EA), db(EB))),
+                              df2_mul(fyv, df2_sub(df2_of(db(SA), db(SB)), df2_of(db(NA), db(NB)))));
+      const df2 gnh = df2_mul(gun2, df2_of(ev[m], ev[mB])), g1h = df2_mul(gu12, df2_of(ev[nv + m], ev[nv + mB]));
+      const df2 ch = df2_of(dh(cA), dh(cB)), cb = df2_of(db(cA), db(cB));
+      const df2 dhh = df2_mul(inv2, df2_add(flh, df2_add(df2_mul(cg12, df2_sub(g1h, ch)),
+                                                         df2_mul(cgn2, df2_sub(gnh, ch)))));
+      const df2 dbb = df2_mul(inv2, df2_add(flb, df2_add(df2_sub(df2_mul(cg1b2, g1h), df2_mul(cg12, cb)),
+                                                         df2_sub(df2_mul(cgnb2, gnh), df2_mul(cgn2, cb)))));
+      const df2 nh = df2_add(ch, dhh), nb = df2_add(cb, dbb);
+      if (act) {
+        fo0[qA] = mk4(df2_x(nh), df2_x(nb));
+        if (hasB) fo0[qB] = mk4(df2_y(nh), df2_y(nb));
+      }
     }
   }
 }

@@ -369,10 +369,41 @@ constexpr int kFPos = kStripW + 3;  // walk positions of a staged f row: UU, U, 
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
 constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
 // shared memory of one warp of the walk (float4): f ring, then record ring
-constexpr int kStripWarpF4 = kFRing * kFPos * 32 + kRing * kStripChunks;
+// ... and one 16-byte slot for the two mbarriers of the record ring
+constexpr int kStripWarpF4 = kFRing * kFPos * 32 + kRing * kStripChunks + 1;
 constexpr size_t kStripSmem = (size_t)kWarpsPerBlock * kStripWarpF4 * sizeof(float4);
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// ---- bulk asynchronous copies (the tensor-memory-access unit) with mbarrier completion ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// one try of the wait for phase `parity`; true once that phase has completed
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Polls of a bounded mbarrier wait in the walk (each try suspends the thread for a
+// hardware-chosen time): about a second at the least before the walk gives up.
+constexpr int kWalkWaitPolls = 1 << 22;
 
 // Per-lane velocity constants of the walk (u shared by the pair, v per velocity).
 struct PairLane {
@@ -471,13 +502,18 @@ __device__ __forceinline__ P4 slope_d(const PairLane& L, const P4& rx, const P4&
   return {fma2(f2(L.cu), rx.h, mul2(L.cv, ry.h)), fma2(f2(L.cu), rx.b, mul2(L.cv, ry.b))};
 }
 
+// sm: this warp's shared memory (kStripWarpF4 float4: f ring, record ring, two mbarriers,
+// initialised by the caller); nrec: record stages this warp has issued on them so far (the
+// phases of the mbarriers follow from it).  Returns false if a wait for records gave up
+// (err then has bit 1 set).
 template <int W, bool FULL>
-__device__ __forceinline__ void strip_body_p(const Params& P, const float4* __restrict__ f,
+__device__ __forceinline__ bool strip_body_p(const Params& P, const float4* __restrict__ f,
                                              float4* __restrict__ fo, const FaceRecF* __restrict__ fxr,
                                              const FaceRecF* __restrict__ fyr,
                                              const CellRecF* __restrict__ cr, int nchunk_neg,
                                              int rows, int bx, int by, int chunk,
-                                             float4* __restrict__ sm) {
+                                             float4* __restrict__ sm, unsigned& nrec,
+                                             int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int nx = P.nx, ny = P.ny, nu = P.nu, fs = P.fs;
   const int i0 = bx * W;
@@ -564,12 +600,14 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
 
   // f rows q = 0 .. nsteps + 1 (row jfirst + (q - 1) sv) pass through a ring of kFRing rows
   // in shared memory, each at the walk positions -2 .. W (UU, U, strip, D); a lane copies
-  // and reads only its own slot's column.  The face and cell records of a row pass through a
-  // ring of kRing rows: [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the downwind side]
-  // [cells i0..i0+wc-1], read by every lane.  Row st's records and f row st + 2 form one
-  // commit group, issued one row ahead.
+  // (cp.async) and reads only its own slot's column.  The face and cell records of a row
+  // pass through a ring of kRing rows: [x-faces i0..i0+wc][y-faces i0..i0+wc-1 on the
+  // downwind side][cells i0..i0+wc-1], read by every lane: three contiguous segments, each
+  // one bulk copy issued by lane 0 and completed on the ring slot's mbarrier.  Row st's
+  // records and f row st + 2 are issued one row ahead.
   float4* fring = sm;
   float4* ring = sm + kFRing * kFPos * 32;
+  const uint32_t bars = smem_addr(ring + kRing * kStripChunks);  // mbarrier of ring slot b at bars + 8 b
   constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
   auto stage_f = [&](int q) {
     if (q <= nsteps + 1) {
@@ -580,24 +618,32 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
     }
   };
   auto stage = [&](int st) {
-    if (st < nsteps) {
+    if (st < nsteps && lane == 0) {
       const int j = jfirst + sv * st;
-      const float4* gx = reinterpret_cast<const float4*>(fxr + (long)j * (nx + 1) + i0);
-      const float4* gy = reinterpret_cast<const float4*>(fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0);
-      const float4* gc = reinterpret_cast<const float4*>(cr + (long)j * nx + i0);
+      const FaceRecF* gx = fxr + (long)j * (nx + 1) + i0;
+      const FaceRecF* gy = fyr + (long)(sv > 0 ? j + 1 : j) * nx + i0;
+      const CellRecF* gc = cr + (long)j * nx + i0;
       float4* dst = ring + (st % kRing) * kStripChunks;
-      for (int c = lane; c < kStripChunks; c += 32) {
-        if (c < oY) {
-          if (c < (wc + 1) * 8) cp_async16(dst + c, gx + c);
-        } else if (c < oC) {
-          if (c - oY < wc * 8) cp_async16(dst + c, gy + (c - oY));
-        } else if (c - oC < wc * 4) {
-          cp_async16(dst + c, gc + (c - oC));
-        }
-      }
+      const uint32_t bar = bars + 8 * ((nrec + st) % kRing);
+      const uint32_t bx_ = (wc + 1) * sizeof(FaceRecF), by_ = wc * sizeof(FaceRecF), bc_ = wc * sizeof(CellRecF);
+      // the generic-proxy reads of this ring slot (two rows ago) are ordered before the
+      // copies that overwrite it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, bx_ + by_ + bc_);
+      bulk_g2s(smem_addr(dst), gx, bx_, bar);
+      bulk_g2s(smem_addr(dst + oY), gy, by_, bar);
+      bulk_g2s(smem_addr(dst + oC), gc, bc_, bar);
     }
     stage_f(st + 2);
     cp_async_commit();
+  };
+  // wait (bounded by `polls`) for the records of row st; the same verdict on every lane
+  auto wait_rec = [&](int st, int polls) {
+    const unsigned k = nrec + st;
+    const uint32_t bar = bars + 8 * (k % kRing), parity = (k / kRing) & 1;
+    bool ok = false;
+    for (int it = 0; it < polls && !ok; it++) ok = mbar_try_wait(bar, parity);
+    return __all_sync(kFull, ok);
   };
   __syncwarp();                      // the rings' previous contents are no longer read
   stage_f(0);
@@ -610,6 +656,16 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
     __syncwarp();                    // every lane is done with the slots refilled next
     stage(st + 1);
     cp_async_wait<1>();
+    if (!wait_rec(st, P.walk_wait_polls)) {
+      // give up: wait (bounded) for the copies already issued, so that none lands after the
+      // walk has returned, record the failure, return
+      cp_async_wait<0>();
+      wait_rec(st, kWalkWaitPolls);
+      if (st + 1 < nsteps) wait_rec(st + 1, kWalkWaitPolls);
+      if (lane == 0) atomicOr(err, 2);
+      nrec += nsteps;
+      return false;
+    }
     __syncwarp();
     const float4* row = ring + (st % kRing) * kStripChunks;
     const FaceRecF* RX = reinterpret_cast<const FaceRecF*>(row);
@@ -653,6 +709,8 @@ __device__ __forceinline__ void strip_body_p(const Params& P, const float4* __re
     pw += rs;
   }
   cp_async_wait<0>();
+  nrec += nsteps;
+  return true;
 }
 
 // -------------------------------------------------------------------------------------

@@ -136,6 +136,7 @@ struct Params {
   const float* uwf;       // FP32 tables: [2][nu] u, wu
   const double* mvd;      // [5][nv] wv v^n, n = 0..4
   float f_tdx, f_tdy, f_idx, f_idy, f_dt;  // FP32 2/dx, 2/dy, 1/dx, 1/dy, dt
+  int walk_wait_polls;    // FP32-f walk: bound of its wait for record copies (polls)
   const double* u;        // [nu]
   const double* v;        // [nv]
   const double* wu;       // [nu]

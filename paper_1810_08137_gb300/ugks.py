@@ -28,7 +28,7 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_batch_sync", "ugks_batch_set_walk_rows", "ugks_batch_get_walk_rows",
            "ugks_batch_set_walk_vtile", "ugks_batch_get_walk_vtile", "ugks_batch_set_persistent",
            "ugks_batch_get_persistent", "ugks_batch_set_wait_limit", "ugks_batch_tune",
-           "ugks_fp64_rate")
+           "ugks_fp64_rate", "ugks_set_wait_limit")
 NKERNELS = 6
 
 
@@ -115,6 +115,7 @@ def lib(build_if_missing: bool = True):
         L.ugks_batch_set_wait_limit.argtypes = [C.c_void_p, C.c_ulonglong]
         L.ugks_batch_tune.argtypes = [C.c_void_p, C.c_int, _P]
         L.ugks_fp64_rate.argtypes = [C.c_void_p, _P]
+        L.ugks_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
         _lib = L
     return _lib
 
@@ -251,6 +252,9 @@ class Solver:
         self._check(self._L.ugks_kernel_times(self._h, ms.ctypes.data_as(_P), n))
         return {self._L.ugks_kernel_name(k).decode(): (int(n[k]), float(ms[k]))
                 for k in range(NKERNELS)}
+
+    def set_wait_limit(self, polls: int):
+        self._check(self._L.ugks_set_wait_limit(self._h, C.c_longlong(int(polls))))
 
     def residual(self) -> np.ndarray:
         r = np.empty(4)

@@ -432,3 +432,26 @@ def test_large_velocity_space(U, oracle, prec, tol):
     print(f"large velocity space prec {prec}: {err}")
     assert np.all(err <= tol), err
     assert rel_f(fg, fr) <= 10 * tol
+
+
+def test_fp32f_walk_wait_timeout_is_reported(U, oracle):
+    """The FP32-f update walk waits (bounded) for the bulk copies of its face and cell
+    records.  With the bound set to zero polls the wait runs out at once: the walk drains its
+    copies in flight, records the failure and returns, and the next synchronising call reports
+    UGKS_ETIMEOUT without trapping the device.  A new state clears it, and with the default
+    bound the instance steps exactly as a fresh one."""
+    cfg = CASES["channel_11x6_v7_hotwall"]()
+    f, W = random_state(oracle, cfg, 61)
+    with U.Solver(cfg, U.FP32F) as s:
+        s.set_state(f, W)
+        s.set_wait_limit(0)
+        s.step(1)
+        with pytest.raises(U.UGKSError) as e:
+            s.sync()
+        assert e.value.status == 4  # UGKS_ETIMEOUT
+        s.set_wait_limit(1 << 22)
+        s.set_state(f, W)
+        s.step(2)
+        fa, Wa = s.get_state()
+    fb, Wb = one_step(U, cfg, f, W, prec=U.FP32F, n=2)
+    assert np.array_equal(fa, fb) and np.array_equal(Wa, Wb)
