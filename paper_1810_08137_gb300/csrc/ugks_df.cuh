@@ -1,67 +1,13 @@
-// Double-FP32 arithmetic for the DF64 form: a value is the unevaluated sum hi + lo of two
-// FP32 numbers with |lo| <= ulp(hi) / 2, about 48 significand bits, computed on the FP32 pipe
-// (GB300 executes FP64 at 1/64 of the FP32 rate).  Built from error-free transformations:
-//   two_sum       s + e = a + b exactly, s = fl(a + b) (Knuth, TAOCP vol. 2, Sec. 4.2.2)
-//   fast_two_sum  the same when |a| >= |b| or a = 0 (Dekker 1971)
-//   two_prod      p + e = a b exactly, p = fl(a b), e from one fused multiply-add
-// The sums and products below round like the "sloppy" double-float operations: relative error
-// a few 2^-48 for products and for sums of like-signed terms; a sum of nearly cancelling
-// terms is exact in its high parts and carries an absolute error of a few 2^-48 of its
-// operands, the same as the rounding of the stored operands themselves.  Every operation uses
-// explicitly rounded intrinsics, so the compiler cannot fuse or reorder them.
+// Double-FP32 arithmetic of the DF64 form beyond the scalar core of ugks_dfcore.cuh
+// (error-free transformations, sums, products): division, lazily normalised running sums,
+// e^x, and the same operations on packed FP32 pairs (two velocities per lane); then the DF64
+// form's kernels.
 #pragma once
+
+#include "ugks_dfcore.cuh"
 
 namespace ugks {
 
-struct df {
-  float hi, lo;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-
-__device__ __forceinline__ df df_of(float a) { return {a, 0.f}; }
-// From FP64 (set-up and per-cell constants only: FP64 conversions run on the FP64 pipe)
-__device__ __forceinline__ df df_of(double a) {
-  const float h = __double2float_rn(a);
-  return {h, __double2float_rn(a - (double)h)};
-}
-__device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }
-
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_add(df a, df b) {
-  const df s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const df p = two_prod(a.hi, b.hi);
-  const float e = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, p.lo));
-  return fast_two_sum(p.hi, e);
-}
-__device__ __forceinline__ df df_mul(df a, float b) {
-  const df p = two_prod(a.hi, b);
-  return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
-}
-// a b + c
-__device__ __forceinline__ df df_fma(df a, df b, df c) {
-  const df p = two_prod(a.hi, b.hi);
-  const float pl = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, p.lo));
-  const df s = two_sum(c.hi, p.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, pl)));
-}
 // a / b: quotient of the high parts, one correction from the double-FP32 remainder
 __device__ __forceinline__ df df_div(df a, df b) {
   float r;
@@ -71,7 +17,16 @@ __device__ __forceinline__ df df_div(df a, df b) {
   const df rem = df_sub(a, df_mul(b, q1));
   return fast_two_sum(q1, __fmul_rn(rem.hi, r));
 }
-__device__ __forceinline__ bool df_gt0(df a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+// Running sum acc + a b without renormalising: the rounding error of the high-part sum and
+// the product's low parts go to acc.lo, which is left to grow (by at most an ulp of acc.hi
+// per term); df_norm restores |lo| <= ulp(hi)/2 once the sum is complete.
+__device__ __forceinline__ df df_acc(df acc, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pl = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.hi, b.hi, -p)));
+  const df s = two_sum(acc.hi, p);
+  return {s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, pl))};
+}
+__device__ __forceinline__ df df_norm(df a) { return two_sum(a.hi, a.lo); }
 
 // e^x for x <= 0 (Maxwellian factors), about 2^-44 relative: x = k ln2 + r with
 // |r| <= ln2 / 2, e^r = (e^(r/8))^8, e^(r/8) by its Taylor series to the 8th power in Horner
@@ -448,13 +403,13 @@ __global__ void __launch_bounds__(128) k_sums_df(Params P, const DF4* __restrict
         const df w0 = dfv(twn[m]), w1 = dfv(twn[nv + m]), w2 = dfv(twn[2 * nv + m]);
         const df w3 = dfv(twn[3 * nv + m]), w4 = dfv(twn[4 * nv + m]);
         const df ch = dh(c), cb = db(c);
-        a0 = df_fma(w0, ch, a0); a1 = df_fma(w1, ch, a1); a2 = df_fma(w2, ch, a2); a3 = df_fma(w3, ch, a3);
-        ab0 = df_fma(w0, cb, ab0); ab1 = df_fma(w1, cb, ab1);
-        x0 = df_fma(w0, rxh, x0); x1 = df_fma(w1, rxh, x1); x2 = df_fma(w2, rxh, x2); x3 = df_fma(w3, rxh, x3);
-        xb0 = df_fma(w0, rxb, xb0); xb1 = df_fma(w1, rxb, xb1);
-        y0 = df_fma(w0, ryh, y0); y1 = df_fma(w1, ryh, y1); y2 = df_fma(w2, ryh, y2);
-        y3 = df_fma(w3, ryh, y3); y4 = df_fma(w4, ryh, y4);
-        yb0 = df_fma(w0, ryb, yb0); yb1 = df_fma(w1, ryb, yb1); yb2 = df_fma(w2, ryb, yb2);
+        a0 = df_acc(a0, w0, ch); a1 = df_acc(a1, w1, ch); a2 = df_acc(a2, w2, ch); a3 = df_acc(a3, w3, ch);
+        ab0 = df_acc(ab0, w0, cb); ab1 = df_acc(ab1, w1, cb);
+        x0 = df_acc(x0, w0, rxh); x1 = df_acc(x1, w1, rxh); x2 = df_acc(x2, w2, rxh); x3 = df_acc(x3, w3, rxh);
+        xb0 = df_acc(xb0, w0, rxb); xb1 = df_acc(xb1, w1, rxb);
+        y0 = df_acc(y0, w0, ryh); y1 = df_acc(y1, w1, ryh); y2 = df_acc(y2, w2, ryh);
+        y3 = df_acc(y3, w3, ryh); y4 = df_acc(y4, w4, ryh);
+        yb0 = df_acc(yb0, w0, ryb); yb1 = df_acc(yb1, w1, ryb); yb2 = df_acc(yb2, w2, ryb);
       }
     };
     auto row_v0 = [&](int m) {  // v = 0: only the w_0 sums, half weight
@@ -462,14 +417,16 @@ __global__ void __launch_bounds__(128) k_sums_df(Params P, const DF4* __restrict
       DF4 c;
       slopes_of(m, rxh, rxb, ryh, ryb, c);
       const df hw = df_half(dfv(twn[m]));
-      a0 = df_fma(hw, dh(c), a0); ab0 = df_fma(hw, db(c), ab0);
-      x0 = df_fma(hw, rxh, x0); xb0 = df_fma(hw, rxb, xb0);
-      y0 = df_fma(hw, ryh, y0); yb0 = df_fma(hw, ryb, yb0);
+      a0 = df_acc(a0, hw, dh(c)); ab0 = df_acc(ab0, hw, db(c));
+      x0 = df_acc(x0, hw, rxh); xb0 = df_acc(xb0, hw, rxb);
+      y0 = df_acc(y0, hw, ryh); yb0 = df_acc(yb0, hw, ryb);
     };
     // close a half: its face sums, then add it to the totals
     auto close = [&](bool north, df& side) {
-      const SumsHalfDF h = {a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1,
-                            y0, y1, y2, y3, y4, yb0, yb1, yb2};
+      const SumsHalfDF h = {df_norm(a0), df_norm(a1), df_norm(a2), df_norm(a3), df_norm(ab0),
+                            df_norm(ab1), df_norm(x0), df_norm(x1), df_norm(x2), df_norm(x3),
+                            df_norm(xb0), df_norm(xb1), df_norm(y0), df_norm(y1), df_norm(y2),
+                            df_norm(y3), df_norm(y4), df_norm(yb0), df_norm(yb1), df_norm(yb2)};
       close_half_df(h, u, wu, cu, tdx, tdy, north, lane, side, tot);
     };
     zero();

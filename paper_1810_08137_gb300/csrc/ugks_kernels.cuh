@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "ugks_internal.h"
+#include "ugks_dfcore.cuh"
 
 namespace ugks {
 
@@ -483,26 +484,34 @@ __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f
 // Moments <x^n>, n = 0..6, of the normalised 1D Gaussian sqrt(lam/pi) exp(-lam (x-U)^2):
 // full range, x > 0 and x < 0.  Integration by parts gives
 // <x^{n+2}> = U <x^{n+1}> + (n+1)/(2 lam) <x^n> on every range.
-// h = 1/(2 lam), rl = 1/sqrt(lam).  One erfc: the half-range mass on the far side of U is
-// erfc(sqrt(lam)|U|)/2, the near side 1 minus that.
+// h = 1/(2 lam); the starting values come from gauss_half_start (FP64): the half-range
+// masses mp0, mn0 and e = <x>_{x>0} - U mp0 = sqrt(lam/pi) exp(-lam U^2) / (2 lam).
 template <typename T>
-__device__ void gauss_moments7(T U, T lam, T h, T rl, T* M, T* Mp, T* Mn) {
-  constexpr T kHalfRsqrtPi = T(0.28209479177387814347);  // 1 / (2 sqrt(pi))
-  const T sl = lam * rl;
-  const T e = exp(-lam * U * U) * (kHalfRsqrtPi * rl);
-  const T far = T(0.5) * erfc(sl * fabs(U));
+__device__ void gauss_moments7(T U, T h, T mp0, T mn0, T e, T* M, T* Mp, T* Mn) {
   M[0] = T(1);
   M[1] = U;
-  Mp[0] = U >= T(0) ? T(1) - far : far;
-  Mn[0] = U >= T(0) ? far : T(1) - far;
+  Mp[0] = mp0;
+  Mn[0] = mn0;
   Mp[1] = U * Mp[0] + e;
   Mn[1] = U * Mn[0] - e;
 #pragma unroll
   for (int n = 0; n < 5; n++) {
-    M[n + 2] = U * M[n + 1] + T(n + 1) * h * M[n];
-    Mp[n + 2] = U * Mp[n + 1] + T(n + 1) * h * Mp[n];
-    Mn[n + 2] = U * Mn[n + 1] + T(n + 1) * h * Mn[n];
+    const T nh = T(n + 1) * h;
+    M[n + 2] = U * M[n + 1] + nh * M[n];
+    Mp[n + 2] = U * Mp[n + 1] + nh * Mp[n];
+    Mn[n + 2] = U * Mn[n + 1] + nh * Mn[n];
   }
+}
+// One erfc: the half-range mass on the far side of U is erfc(sqrt(lam)|U|)/2, the near side
+// 1 minus that; rl = 1/sqrt(lam).
+__device__ __forceinline__ void gauss_half_start(double U, double lam, double rl, double& mp0, double& mn0,
+                                                 double& e) {
+  constexpr double kHalfRsqrtPi = 0.28209479177387814347;  // 1 / (2 sqrt(pi))
+  const double sl = lam * rl;
+  e = exp(-lam * U * U) * (kHalfRsqrtPi * rl);
+  const double far = 0.5 * erfc(sl * fabs(U));
+  mp0 = U >= 0.0 ? 1.0 - far : far;
+  mn0 = U >= 0.0 ? far : 1.0 - far;
 }
 
 // Full-range moments only (tangential axis).
@@ -516,12 +525,12 @@ __device__ void gauss_moments7_full(T U, T h, T* M) {
 
 // <u^a v^b psi> for the normalised Maxwellian, u-moments Mu (one range), v-moments Mv,
 // <xi^2> = X2.
-__device__ __forceinline__ void psi_mom(const double* Mu, const double* Mv, double X2, int a, int b,
-                                        double* o) {
+template <typename T>
+__device__ __forceinline__ void psi_mom(const T* Mu, const T* Mv, T X2, int a, int b, T* o) {
   o[0] = Mu[a] * Mv[b];
   o[1] = Mu[a + 1] * Mv[b];
   o[2] = Mu[a] * Mv[b + 1];
-  o[3] = 0.5 * (Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2] + Mu[a] * Mv[b] * X2);
+  o[3] = T(0.5) * (Mu[a + 2] * Mv[b] + Mu[a] * Mv[b + 2] + Mu[a] * Mv[b] * X2);
 }
 // <u^a v^b psi (c . psi)>, c . psi = c1 + c2 u + c3 v + c4 (u^2 + v^2 + xi^2)/2, from the
 // factorised moments: with M(p, q) = Mu[p] Mv[q] and h = c4/2,
@@ -685,19 +694,28 @@ __device__ __forceinline__ void wall_face_f32(const Params& P, bool isx, double 
   RF.gdt = (float)P.dt;
 }
 
-// S2-S5 of one UGKS interface in the face frame (un, ut), all in FP64: interface primitive
-// variables, Maxwellian moments (full and half range), collision time and Mt1..Mt5, the
-// micro slopes a_L, a_R, b and the time slope A (compatibility condition), and the
-// time-integrated macroscopic flux F (equilibrium part from analytic moments, free-transport
-// part from the sums).  Inputs: the interface sums (S1, S7) and the cell W on both sides.
-struct FaceCore {
+// S2-S5 of one UGKS interface in the face frame (un, ut): interface primitive variables,
+// Maxwellian moments (full and half range), collision time and Mt1..Mt5, the micro slopes
+// a_L, a_R, b and the time slope A (compatibility condition), and the time-integrated
+// macroscopic flux F (equilibrium part from analytic moments, free-transport part from the
+// sums).  Inputs: the interface sums (S1, S7) and the cell W on both sides.
+// Arithmetic: the primitive variables, exp and erfc of the half-range moments, tau and
+// Mt1..Mt5, the slope targets and the free-transport part of F in FP64; the moment
+// recurrences, the micro-slope solves, the compatibility moments and the equilibrium part of
+// F in T: double (FP64 form, DF64 form) or dd, double-FP32 on the FP32 pipe (FP32-f form,
+// about 2^-48 relative per operation, where FP64 would spend ~420 of its ~610 operations per
+// face on the 1/64-rate FP64 pipe).
+template <typename T>
+struct FaceCoreT {
   double rho, U, V, lam, X2, X4;
   double Mt[5];
-  double aL[4], aR[4], b[4], A[4];
+  T aL[4], aR[4], b[4], A[4];
 };
+using FaceCore = FaceCoreT<double>;
+template <typename T>
 __device__ __forceinline__ void face_core(const Params& P, const double* W0, const double* St,
                                           const double* Sf, const double* Ss, const double* WL,
-                                          const double* WR, double tdelta, double* F, FaceCore& c) {
+                                          const double* WR, double tdelta, double* F, FaceCoreT<T>& c) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
@@ -705,11 +723,14 @@ __device__ __forceinline__ void face_core(const Params& P, const double* W0, con
   const double lam = 0.25 * rcp_nr(ilam4);
   const double h = 2.0 * ilam4;  // 1/(2 lam)
   const double rl = rsqrt(lam);
-  double Mu[7], Mup[7], Mun[7], Mv[7];
-  gauss_moments7(U, lam, h, rl, Mu, Mup, Mun);
-  gauss_moments7_full(V, h, Mv);
+  double mp0, mn0, e;
+  gauss_half_start(U, lam, rl, mp0, mn0, e);
+  const T Ut = T(U), Vt = T(V), ht = T(h);
+  T Mu[7], Mup[7], Mun[7], Mv[7];
+  gauss_moments7<T>(Ut, ht, T(mp0), T(mn0), T(e), Mu, Mup, Mun);
+  gauss_moments7_full<T>(Vt, ht, Mv);
   const double X2 = 2.0 * K * ilam4, X4 = (K * K + 2.0 * K) * 4.0 * ilam4 * ilam4;
-  const double X4m = X4 - X2 * X2;
+  const T X2t = T(X2), X4m = T(X4 - X2 * X2);
   // S3: collision time tau = mu/p, mu = mu_ref T^omega, p = rho/(2 lam), and Mt1..Mt5 of
   // x = dt/tau (omega = 1/2: x = dt rho / (2 mu_ref sqrt(lam)))
   const double x = P.omega_half ? P.half_dt_mu * rho * rl : P.dt / collision_time(P, rho, lam);
@@ -717,38 +738,52 @@ __device__ __forceinline__ void face_core(const Params& P, const double* W0, con
   const double* Mt = c.Mt;
   // S4: micro slopes
   const double inv = irho * tdelta;
-  const double q = (K + 2) * ilam4, c4 = 4.0 * lam * lam * P.inv_kp2;
-  double sL[4], sR[4], sT[4], sA[4];
+  const T lamt = T(lam), q = T((K + 2) * ilam4), c4 = T(4.0 * lam * lam * P.inv_kp2);
+  T sL[4], sR[4], sT[4], sA[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    sL[k] = (W0[k] - WL[k]) * inv;
-    sR[k] = (WR[k] - W0[k]) * inv;
-    sT[k] = St[k] * irho;
+    sL[k] = T((W0[k] - WL[k]) * inv);
+    sR[k] = T((WR[k] - W0[k]) * inv);
+    sT[k] = T(St[k] * irho);
   }
-  micro_slope(U, V, lam, q, c4, sL, c.aL);
-  micro_slope(U, V, lam, q, c4, sR, c.aR);
-  micro_slope(U, V, lam, q, c4, sT, c.b);
-  APsi<double> tL, tR, tb, tA;
-  apsi_prep(Mv, X2, 0, c.aL, tL);
-  apsi_prep(Mv, X2, 0, c.aR, tR);
-  apsi_prep(Mv, X2, 1, c.b, tb);
-  double t1[4], t2[4], t3[4], t4[4], p1[4];
-  apsi_eval(tL, Mup, X2, X4m, 1, t1);
-  apsi_eval(tR, Mun, X2, X4m, 1, t2);
-  apsi_eval(tb, Mu, X2, X4m, 0, t3);
+  micro_slope<T>(Ut, Vt, lamt, q, c4, sL, c.aL);
+  micro_slope<T>(Ut, Vt, lamt, q, c4, sR, c.aR);
+  micro_slope<T>(Ut, Vt, lamt, q, c4, sT, c.b);
+  // moments of (u_n a_L, u_n a_R, u_t b) . psi g at the orders the compatibility condition
+  // (t) and the flux (n: one more u_n) need; each table is dropped once evaluated
+  T t1[4], t2[4], t3[4], n1[4], n2[4], n3[4], t4[4], p1[4];
+  {
+    APsi<T> tL;
+    apsi_prep<T>(Mv, X2t, 0, c.aL, tL);
+    apsi_eval<T>(tL, Mup, X2t, X4m, 1, t1);
+    apsi_eval<T>(tL, Mup, X2t, X4m, 2, n1);
+  }
+  {
+    APsi<T> tR;
+    apsi_prep<T>(Mv, X2t, 0, c.aR, tR);
+    apsi_eval<T>(tR, Mun, X2t, X4m, 1, t2);
+    apsi_eval<T>(tR, Mun, X2t, X4m, 2, n2);
+  }
+  {
+    APsi<T> tb;
+    apsi_prep<T>(Mv, X2t, 1, c.b, tb);
+    apsi_eval<T>(tb, Mu, X2t, X4m, 0, t3);
+    apsi_eval<T>(tb, Mu, X2t, X4m, 1, n3);
+  }
 #pragma unroll
   for (int k = 0; k < 4; k++) sA[k] = -(t1[k] + t2[k] + t3[k]);
-  micro_slope(U, V, lam, q, c4, sA, c.A);
-  apsi_prep(Mv, X2, 0, c.A, tA);
+  micro_slope<T>(Ut, Vt, lamt, q, c4, sA, c.A);
+  {
+    APsi<T> tA;
+    apsi_prep<T>(Mv, X2t, 0, c.A, tA);
+    apsi_eval<T>(tA, Mu, X2t, X4m, 1, t4);
+  }
   // S5: equilibrium part of the macroscopic flux; S7 free transport part from the sums
-  psi_mom(Mu, Mv, X2, 1, 0, p1);
-  apsi_eval(tL, Mup, X2, X4m, 2, t1);
-  apsi_eval(tR, Mun, X2, X4m, 2, t2);
-  apsi_eval(tb, Mu, X2, X4m, 1, t3);
-  apsi_eval(tA, Mu, X2, X4m, 1, t4);
+  psi_mom<T>(Mu, Mv, X2t, 1, 0, p1);
+  const T M1 = T(Mt[0]), M2 = T(Mt[1]), M3 = T(Mt[2]), rhot = T(rho);
 #pragma unroll
   for (int k = 0; k < 4; k++)
-    F[k] = rho * (Mt[0] * p1[k] + Mt[1] * (t1[k] + t2[k] + t3[k]) + Mt[2] * t4[k]) + Mt[3] * Sf[k] -
+    F[k] = to_double(rhot * (M1 * p1[k] + M2 * (n1[k] + n2[k] + n3[k]) + M3 * t4[k])) + Mt[3] * Sf[k] -
            Mt[4] * Ss[k];
   c.rho = rho;
   c.U = U;
@@ -789,16 +824,16 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   }
 }
 
-// FP32-f form: the same FP64 interface (face_core: primitive variables, half-range moments,
-// Mt1..Mt5, micro-slope solves, compatibility condition, macroscopic flux), then the FP32
-// record its update walk reads.  The record is rounded to FP32 from the FP64 slopes and
-// weights: the walk applies it to FP32 f.
+// FP32-f form: the interface (face_core with its polynomial work in double-FP32: primitive
+// variables, half-range moments, Mt1..Mt5, micro-slope solves, compatibility condition,
+// macroscopic flux), then the FP32 record its update walk reads.  The record is rounded to
+// FP32 from the double-FP32 slopes and FP64 weights: the walk applies it to FP32 f.
 __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St,
                                               const double* Sf, const double* Ss, const double* WL,
                                               const double* WR, double tdelta, bool isx, double* F,
                                               double& Mt4, FaceRecF& RF) {
-  FaceCore c;
-  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
+  FaceCoreT<dd> c;
+  face_core<dd>(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
   const double* Mt = c.Mt;
   Mt4 = Mt[3];
   const float fM1 = (float)Mt[0], fM2 = (float)Mt[1], fM3 = (float)Mt[2];
@@ -808,10 +843,10 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   float aL[4], aR[4], b[4], A[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    aL[k] = (float)c.aL[k];
-    aR[k] = (float)c.aR[k];
-    b[k] = (float)c.b[k];
-    A[k] = (float)c.A[k];
+    aL[k] = to_float(c.aL[k]);
+    aR[k] = to_float(c.aR[k]);
+    b[k] = to_float(c.b[k]);
+    A[k] = to_float(c.A[k]);
   }
   // shape polynomial of (a . psi) g / g_h reduced over the internal variable, face frame:
   // P(un, ut) = p0 + p1 un + p2 ut + p3 (un^2 + ut^2)
