@@ -233,6 +233,44 @@ def large_velocity_bench(ugks, torch, stream, warmup, grids=(51, 101, 151, 201))
     return {"unit": UNIT, "grids": out}
 
 
+def split_bench(ugks, torch, stream, warmup, grids=(101, 201)):
+    """Velocity-space split of the FP32-f sums on a small mesh with a large velocity grid
+    (the large-velocity channel's grid, [-20,20]^2 and Kn 0.01, on the 40x20 mesh of the
+    small channel): the automatic split against one warp per cell, graph-replayed steps."""
+    out = []
+    for n in grids:
+        base = I.workload_large_velocity(n)
+        cfg = base.replace(nx=40, ny=20, name=f"channel_40x20_v{n}_r20")
+        prim = I.initial_prim(cfg, I.seed_for(3, 1000 + n))
+        row = {"workload": cfg.name, "vc_per_step": cfg.vc}
+        s = ugks.Solver(cfg, ugks.FP32F, stream=stream.cuda_stream)
+        s.init_maxwellian(*prim)
+        auto = s.sums_split
+        for split in sorted({1, auto}):
+            s.set_sums_split(split)
+            s.step(warmup)
+            s.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            steps = 20
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            s.profile(True)
+            s.step(10)
+            kt = s.kernel_times()
+            s.profile(False)
+            row[f"split{split}"] = {"ms_per_step": ms, "value": cfg.vc / (ms * 1e-3),
+                                    "sums_ms": kt["sums"][1] / max(kt["sums"][0], 1)}
+        s.close()
+        row["auto_split"] = auto
+        row["speedup"] = row["split1"]["ms_per_step"] / row[f"split{auto}"]["ms_per_step"]
+        out.append(row)
+    return {"unit": UNIT, "grids": out}
+
+
 def batch_bench(ugks, torch, stream, steps, warmup):
     """Uneven batch: 64 channel instances drawn log-uniform (meshes 50x25..400x200,
     16^2..64^2 velocities, Kn 1e-3..1, inlet rho 1.05..1.5), FP32-f, stepped together;
@@ -434,6 +472,7 @@ def main():
         del f_host_t, W_host_t, f_host, W_host
         batch = None if args.no_batch else batch_bench(ugks, torch, stream, args.steps, args.warmup)
         large = None if args.no_large_velocity else large_velocity_bench(ugks, torch, stream, args.warmup)
+        split = None if args.no_large_velocity else split_bench(ugks, torch, stream, args.warmup)
         serving = None if (args.no_serve or ws > 1) else serve_bench(ugks, stream)
 
     def form_json(prec):
@@ -529,6 +568,7 @@ def main():
         "batch": batch,
         "serving": serving,
         "large_velocity": large,
+        "sums_split": split,
     }
     if batch:
         batch["vs_fp64_single"] = batch["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])

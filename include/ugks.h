@@ -165,6 +165,19 @@ ugks_status ugks_sync(ugks_handle h);
  * Synchronises. */
 ugks_status ugks_set_wait_limit(ugks_handle h, long long polls);
 
+/* Velocity-space split of the FP32-f sums (S1 + S7 of the Sec. 2.B flux table; the paper's
+ * large-velocity-space regime of Sec. 3.B): `warps` warps (1, 2 or 4) share each cell's
+ * velocity space, each summing a contiguous range of velocity rows per half of the v axis,
+ * and their FP64 face sums are added in shared memory in a fixed order.  0 selects the
+ * automatic choice that ugks_create also makes: more warps per cell while the cells alone
+ * would leave the kernel's resident warps under-filled (small meshes, large velocity
+ * grids) and every warp keeps at least 16 velocity rows.  The result depends on `warps` only
+ * through the order of the FP64 additions.  UGKS_EINVAL for other values or another form.
+ * Synchronises; the next ugks_step captures its graphs again. */
+ugks_status ugks_set_sums_split(ugks_handle h, int warps);
+/* Current warps per cell of the FP32-f sums (0 for another form or a NULL handle). */
+int ugks_get_sums_split(ugks_handle h);
+
 /* Copy W (host W_host[4][nc]) and, if prim_host != NULL, primitive variables
  * prim_host[4][nc] = (rho, U, V, T).  Synchronises. */
 ugks_status ugks_moments(ugks_handle h, double* W_host, double* prim_host);

@@ -21,7 +21,8 @@ def compile_source(src: str, out: str) -> str:
     """Compile one C source file of the oracle into the shared library `out` (gcc, OpenMP
     over faces and cells).  The source must include ugks_oracle.h from this directory."""
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+    # no floating-point contraction: the same rounding on x86 and aarch64
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-D_GNU_SOURCE", "-fPIC", "-shared",
                            "-fopenmp", "-I", HERE, "-o", tmp, src, "-lm"])
     os.replace(tmp, out)
     return out

@@ -9,7 +9,10 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libugks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+# host code without floating-point contraction: the velocity grid and the tables built on
+# the host round the same way on x86 and aarch64 (GCC contracts a*b + c into an FMA on
+# aarch64 in C++ by default, which moved a v = 0 node of an asymmetric grid off zero)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
 
 SOURCES = ["ugks.cu"]
 

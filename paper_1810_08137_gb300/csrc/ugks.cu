@@ -48,6 +48,7 @@ struct ugks_ctx {
   CellRecD* celld = nullptr;
   float2* gdf = nullptr;
   int nchunk_neg = 0, nchunk_pos = 0;
+  int sums_split = 1;        // FP32 form: warps per cell of the sums kernel (velocity-space split)
   // FP32 form: the step runs the batch kernels over a one-instance table, so an instance
   // stepped alone executes exactly the code it executes inside a batch
   SlotDev* d_slot = nullptr;
@@ -242,6 +243,8 @@ cudaError_t mark(ugks_ctx* h, int k) {
 
 cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st);
 cudaError_t setup_single_f32(ugks_ctx* h);
+cudaError_t upload_single_f32(ugks_ctx* h);
+int auto_sums_split(const Params& P, int sms);
 SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile = 0);
 
 template <typename T>
@@ -1227,6 +1230,26 @@ ugks_status ugks_set_wait_limit(ugks_handle h, long long polls) {
   return UGKS_OK;
 }
 
+ugks_status ugks_set_sums_split(ugks_handle h, int warps) {
+  if (!h || !(warps == 0 || warps == 1 || warps == 2 || warps == 4))
+    return fail(h, UGKS_EINVAL, "set_sums_split: warps must be 0, 1, 2 or 4");
+  if (!h->d_slot) return fail(h, UGKS_EINVAL, "set_sums_split: FP32-f form only");
+  CK(cudaStreamSynchronize(h->stream));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  h->sums_split = warps == 0 ? auto_sums_split(h->P, sms) : warps;
+  CK(upload_single_f32(h));
+  for (int b = 0; b < 2; b++)  // the captured steps hold the old grid: capture them again
+    if (h->graph[b]) {
+      CK(cudaGraphExecDestroy(h->graph[b]));
+      h->graph[b] = nullptr;
+    }
+  return UGKS_OK;
+}
+
+int ugks_get_sums_split(ugks_handle h) { return (h && h->d_slot) ? h->sums_split : 0; }
+
 ugks_status ugks_sync(ugks_handle h) {
   if (!h) return UGKS_EINVAL;
   return check_err(h);
@@ -1371,6 +1394,7 @@ SlotDev slot_desc(const ugks_ctx* h, int walk_rows, int walk_vtile) {
   S.nchunk_pos = h->nchunk_pos;
   S.walk_rows = walk_rows;
   S.walk_vtile = walk_vtile;
+  S.sums_split = h->sums_split;
   S.cur = h->cur;
   return S;
 }
@@ -1431,12 +1455,24 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t setup_single_f32(ugks_ctx* h) {
-  cudaError_t e = cudaMalloc((void**)&h->d_slot, sizeof(SlotDev));
-  if (e != cudaSuccess) return e;
-  h->bytes += sizeof(SlotDev);
-  if ((e = cudaMalloc((void**)&h->d_work, sizeof(BatchWork))) != cudaSuccess) return e;
-  h->bytes += sizeof(BatchWork);
+// Warps per cell of the FP32-f sums kernel chosen from the mesh and the device: split the
+// velocity space of each cell over 2 or 4 warps while the cells alone would fill fewer than
+// two waves of the kernel's resident warps (sms x 5 blocks x 4 warps) and every warp keeps at
+// least two FP32 chunks of row pairs per half of the v axis.
+int auto_sums_split(const Params& P, int sms) {
+  const long cells = (long)(P.nx + 2) * (P.ny + 2), resident = (long)sms * 5 * kWarpsPerBlock;
+  int pmin = P.pr_neg < P.pr_all - P.pr_neg ? P.pr_neg : P.pr_all - P.pr_neg;
+  if (pmin == 0) pmin = P.pr_all;
+  int split = 1;
+  while (split < kWarpsPerBlock && cells * split < 2 * resident && pmin >= 2 * split * kSumChunkPairs)
+    split *= 2;
+  return split;
+}
+
+// Slot descriptor, one-instance work table and grid sizes of the FP32-f step (uploaded again
+// when a tile shape or the sums split changes).
+cudaError_t upload_single_f32(ugks_ctx* h) {
+  cudaError_t e;
   const SlotDev S = slot_desc(h, kWalkRows);
   BatchWork w;
   memset(&w, 0, sizeof w);
@@ -1445,12 +1481,6 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
-      cudaSuccess)
-    return e;
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
                               (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};
   for (int p = 0; p < kPhases; p++) {
@@ -1463,6 +1493,25 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   }
   if ((e = cudaMemcpy(h->d_slot, &S, sizeof(SlotDev), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
   return cudaMemcpy(h->d_work, &w, sizeof(BatchWork), cudaMemcpyHostToDevice);
+}
+
+cudaError_t setup_single_f32(ugks_ctx* h) {
+  cudaError_t e = cudaMalloc((void**)&h->d_slot, sizeof(SlotDev));
+  if (e != cudaSuccess) return e;
+  h->bytes += sizeof(SlotDev);
+  if ((e = cudaMalloc((void**)&h->d_work, sizeof(BatchWork))) != cudaSuccess) return e;
+  h->bytes += sizeof(BatchWork);
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  h->sums_split = auto_sums_split(h->P, sms);
+  if ((e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
+      cudaSuccess)
+    return e;
+  return upload_single_f32(h);
 }
 
 cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st) {

@@ -30,6 +30,7 @@ struct SlotDev {
   int nwe, nrblocks, nchunk_neg, nchunk_pos;
   int walk_rows;   // cell tile of the walk: rows per tile (autotuned per velocity-grid class)
   int walk_vtile;  // velocity tile of the walk: 32-slot chunks per tile, 0 = all (autotuned)
+  int sums_split;  // warps per cell in the sums phase (1, 2 or 4): velocity-space split
   int cur;         // ping-pong parity, flipped on the device after every step
 };
 
@@ -46,7 +47,7 @@ __host__ __device__ inline int phase_blocks(const SlotDev& S, int phase) {
   switch (phase) {
     case 0: return P.ny * 4;
     case 1: return (P.nx + 4) * 4;
-    case 2: return ((P.nx + 2) * (P.ny + 2) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    case 2: return ((P.nx + 2) * (P.ny + 2) * S.sums_split + kWarpsPerBlock - 1) / kWarpsPerBlock;
     case 3: return ((P.nx + 1) * P.ny + P.nx * (P.ny + 1) + 127) / 128;
     case 4: return S.nrblocks;
     default: {
@@ -94,12 +95,16 @@ __device__ __noinline__ void ghost_y_phase(const SlotDev* __restrict__ slots, co
   }
 }
 
-__device__ __noinline__ void sums_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+__device__ __noinline__ void sums_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                        double (*red)[kNSum]) {
   const int total = wk->start[2][wk->n];
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    sums_body_p(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a]);
+    if (S.sums_split > 1)
+      sums_body_split(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], S.sums_split, red);
+    else
+      sums_body_p<false>(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], 1, red);
   }
 }
 
@@ -202,7 +207,8 @@ __global__ void kb_ghost_y(const SlotDev* __restrict__ slots, const BatchWork* _
 
 __global__ void __launch_bounds__(128, 5) kb_sums(const SlotDev* __restrict__ slots,
                                                const BatchWork* __restrict__ wk) {
-  sums_phase(slots, wk);
+  __shared__ double red[kWarpsPerBlock][kNSum];  // face sums of split cells
+  sums_phase(slots, wk, red);
 }
 
 __global__ void __launch_bounds__(128) kb_faces(const SlotDev* __restrict__ slots,
@@ -279,7 +285,8 @@ __device__ __forceinline__ bool grid_sync(BarrierDev* g) {
 // dynamic shared memory of the persistent step: the largest phase's (the walk's rings; the
 // ghost tables and the cells reduction alias its start)
 constexpr size_t kStepSmem = kStripSmem;
-static_assert(kStepSmem >= sizeof(double) * kGhostTab && kStepSmem >= sizeof(double) * 8 * 128,
+static_assert(kStepSmem >= sizeof(double) * kGhostTab && kStepSmem >= sizeof(double) * 8 * 128 &&
+                  kStepSmem >= sizeof(double) * kWarpsPerBlock * kNSum,
               "persistent step: shared memory of every phase");
 
 __global__ void __launch_bounds__(128, 3) kb_step(SlotDev* __restrict__ slots,
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(128, 3) kb_step(SlotDev* __restrict__ slots,
   if (!grid_sync(bar)) return;
   ghost_y_phase(slots, wk, tab);
   if (!grid_sync(bar)) return;
-  sums_phase(slots, wk);
+  sums_phase(slots, wk, reinterpret_cast<double(*)[kNSum]>(step_sm));
   if (!grid_sync(bar)) return;
   faces_phase(slots, wk);
   if (!grid_sync(bar)) return;

@@ -175,6 +175,11 @@ __device__ __forceinline__ float chunk_y_sums(float u, float wu, float cu, float
 
 // The chunk's contribution to the 32 face sums of the x sides (E: entries 0..15 from u > 0
 // with f + r_x, W: 16..31 from u < 0 with f - r_x, u = 0 half to each); entry lane.
+// A transpose reduce-scatter in which a lane's own values are laid out by its lane bits 4
+// and 3, so that those two exchange levels need no selects: every lane forms the 16 entries
+// of the side it keeps (W on lanes 16..31, E on lanes 0..15) and the 16 of the side it sends
+// to lane ^ 16; and since entries 8..11 of a side are u times entries 0..3, a lane with bit 3
+// set holds u times its entries 0..3 in slots 0..3 and the unscaled ones in slots 8..11.
 __device__ __forceinline__ float chunk_x_sums(float u, float wu, float cu, float tdy,
                                               float a0, float a1, float a2, float ab0,
                                               float x0, float x1, float x2, float xb0,
@@ -184,49 +189,79 @@ __device__ __forceinline__ float chunk_x_sums(float u, float wu, float cu, float
   const float Db = cu * xb0 + tdy * yb1;
   const float hE = u > 0.f ? 1.f : (u < 0.f ? 0.f : 0.5f);
   const float hW = u < 0.f ? 1.f : (u > 0.f ? 0.f : 0.5f);
-  float xv[32];
+  const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+  const float mk = up8 ? u : 1.f, ms = up8 ? 1.f : u;  // scales of slots 0..3 and 8..11
   const float uu = u * u;
-#pragma unroll
-  for (int sd = 0; sd < 2; sd++) {
-    const float sg = sd == 0 ? 1.f : -1.f;
-    const float wgt = wu * (sd == 0 ? hE : hW);
+  // the 16 entries of one side (sign sg of r_x, weight wgt), slots 0..3 / 8..11 as above
+  auto side = [&](float sg, float wgt, float* o) {
     const float F0 = a0 + sg * x0, F1 = a1 + sg * x1, F2 = a2 + sg * x2, Fb = ab0 + sg * xb0;
-    float* o = xv + 16 * sd;
-    o[0] = wgt * F0;
-    o[1] = wgt * u * F0;
-    o[2] = wgt * F1;
-    o[3] = wgt * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+    const float b0 = wgt * F0, b1 = wgt * u * F0, b2 = wgt * F1;
+    const float b3 = wgt * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
+    o[0] = mk * b0; o[1] = mk * b1; o[2] = mk * b2; o[3] = mk * b3;
+    o[8] = ms * b0; o[9] = ms * b1; o[10] = ms * b2; o[11] = ms * b3;
     const float ws = wgt * tdy;
     o[4] = ws * y0;
     o[5] = ws * u * y0;
     o[6] = ws * y1;
     o[7] = ws * (0.5f * (uu * y0 + y2) + 0.5f * yb0);
     const float wuu = wgt * u;
-    o[8] = wuu * F0;
-    o[9] = wuu * u * F0;
-    o[10] = wuu * F1;
-    o[11] = wuu * (0.5f * (uu * F0 + F2) + 0.5f * Fb);
     o[12] = wuu * D0;
     o[13] = wuu * u * D0;
     o[14] = wuu * D1;
     o[15] = wuu * (0.5f * (uu * D0 + D2) + 0.5f * Db);
+  };
+  float kv[16], sv[16];
+  side(up16 ? -1.f : 1.f, wu * (up16 ? hW : hE), kv);
+  side(up16 ? 1.f : -1.f, wu * (up16 ? hE : hW), sv);
+#pragma unroll
+  for (int i = 0; i < 16; i++) kv[i] += __shfl_xor_sync(kFull, sv[i], 16);
+#pragma unroll
+  for (int i = 0; i < 4; i++) kv[i] += __shfl_xor_sync(kFull, kv[i + 8], 8);
+#pragma unroll
+  for (int i = 4; i < 8; i++) {
+    const float send = up8 ? kv[i] : kv[i + 8];
+    const float keep = up8 ? kv[i + 8] : kv[i];
+    kv[i] = keep + __shfl_xor_sync(kFull, send, 8);
   }
-  return warp_reduce_scatter<32>(xv, lane);
+#pragma unroll
+  for (int o = 4; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; i++) {
+      const float send = upper ? kv[i] : kv[i + o];
+      const float keep = upper ? kv[i + o] : kv[i];
+      kv[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return kv[0];
 }
 
+// Velocity-space split (split = 1, 2 or 4 warps per cell, the warps of one cell in one
+// block): warp g of a cell's group takes the g-th of `split` contiguous ranges of row pairs in
+// each half of the v axis, and the group's FP64 face sums are added in shared memory (`red`,
+// kWarpsPerBlock x kNSum doubles) in the order g = 0, 1, ... by the group's first warp.  With
+// split > 1 every warp of the block reaches the two block barriers, so the caller's block
+// must be uniform in `split` (it is: a block's cells belong to one instance).
+// SPLIT = false: one warp per cell (split 1), without the range and reduction code; the
+// caller inlines it and calls the split instance as a function of its own (sums_body_split),
+// so that the split path's registers do not weigh on the one-warp path.
+template <bool SPLIT>
 __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
-                                            double* __restrict__ sums, int bx) {
+                                            double* __restrict__ sums, int bx, int split_,
+                                            double (*red)[kNSum]) {
   const int nu = P.nu, fs = P.fs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncx = P.nx + 2;
-  const int cell = bx * kWarpsPerBlock + warp;
-  if (cell >= ncx * (P.ny + 2)) return;
+  const int split = SPLIT ? split_ : 1;
+  const int gw = bx * kWarpsPerBlock + warp;
+  const int cell = SPLIT ? gw / split : gw, g = SPLIT ? gw - cell * split : 0;
   const int i = cell % ncx - 1, j = cell / ncx - 1;
   const bool xg = i < 0 || i >= P.nx, yg = j < 0 || j >= P.ny;
-  if (xg && yg) return;
-  if ((i < 0 && P.bc_kind[0] == 1) || (i >= P.nx && P.bc_kind[1] == 1) ||
-      (j < 0 && P.bc_kind[2] == 1) || (j >= P.ny && P.bc_kind[3] == 1))
-    return;
+  // a cell whose sums are never read: corner ghosts, ghosts behind a wall, past the end
+  const bool skip = cell >= ncx * (P.ny + 2) || (xg && yg) || (i < 0 && P.bc_kind[0] == 1) ||
+                    (i >= P.nx && P.bc_kind[1] == 1) || (j < 0 && P.bc_kind[2] == 1) ||
+                    (j >= P.ny && P.bc_kind[3] == 1);
+  if (!SPLIT && skip) return;
   const bool zs = (i < 0 && P.bc_kind[0] == 2) || (i >= P.nx && P.bc_kind[1] == 2) ||
                   (j < 0 && P.bc_kind[2] == 2) || (j >= P.ny && P.bc_kind[3] == 2);
 
@@ -241,7 +276,15 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
   // FP64 face sums owned by this lane: E/W entry `lane`; N and S entries `lane` (lane < 16)
   double sx = 0.0, sn = 0.0, ss = 0.0;
 
-  for (int k0 = 0; k0 < nu; k0 += 32) {
+  // this warp's row pairs: [p0, p1) of the v >= 0 half (pairs pn .. pa - 1) and [q0, q1) of
+  // the v < 0 half (pairs 0 .. pn - 1); the v = 0 row's share of the v < 0 half goes with the
+  // first v >= 0 pair
+  const int p0 = SPLIT ? pn + (int)((long)(pa - pn) * g / split) : pn;
+  const int p1 = SPLIT ? pn + (int)((long)(pa - pn) * (g + 1) / split) : pa;
+  const int q0 = SPLIT ? (int)((long)pn * g / split) : 0;
+  const int q1 = SPLIT ? (int)((long)pn * (g + 1) / split) : pn;
+
+  for (int k0 = (SPLIT && skip) ? nu : 0; k0 < nu; k0 += 32) {
     const int k = k0 + lane;
     const bool act = k < nu;
     const int kk = act ? k : nu - 1;
@@ -294,26 +337,26 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     // v >= 0 pair holds the v = 0 row (if any) as its first row
     zero();
     float s0h = 0.f, s0b = 0.f, s0xh = 0.f, s0xb = 0.f, s0yh = 0.f, s0yb = 0.f;
-    if (pa > pn) {
-      Sten q = load(pn);
-      Sten nq = load(pn + 1 < pa ? pn + 1 : pn);
+    if (p1 > p0) {
+      Sten q = load(p0);
+      Sten nq = load(p0 + 1 < p1 ? p0 + 1 : p0);
       P4 rx, ry;
-      use(pn, q, rx, ry);
-      if (v0) {  // the v = 0 row's half weight for the v < 0 half
+      use(p0, q, rx, ry);
+      if (v0 && (!SPLIT || p0 == pn)) {  // the v = 0 row's half weight for the v < 0 half
         const float hw = __ldg(&wt[3 * pn].x);
         s0h = hw * q.c.h.x; s0b = hw * q.c.b.x; s0xh = hw * rx.h.x; s0xb = hw * rx.b.x;
         s0yh = hw * ry.h.x; s0yb = hw * ry.b.x;
       }
       int n = 1;
 #pragma unroll 1
-      for (int pr = pn + 1; pr < pa; pr++) {
+      for (int pr = p0 + 1; pr < p1; pr++) {
         if (n == kSumChunkPairs) {
           flush(1.f, sn);
           zero();
           n = 0;
         }
         q = nq;
-        nq = load(pr + 1 < pa ? pr + 1 : pr);  // the last pair reloads itself (in bounds)
+        nq = load(pr + 1 < p1 ? pr + 1 : pr);  // the last pair reloads itself (in bounds)
         use(pr, q, rx, ry);
         n++;
       }
@@ -321,18 +364,18 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     flush(1.f, sn);
     zero();
     a0 = s0h; ab0 = s0b; x0 = s0xh; xb0 = s0xb; y0 = s0yh; yb0 = s0yb;
-    if (pn > 0) {
-      Sten nq = load(0);
+    if (q1 > q0) {
+      Sten nq = load(q0);
       int n = 0;
 #pragma unroll 1
-      for (int pr = 0; pr < pn; pr++) {
+      for (int pr = q0; pr < q1; pr++) {
         if (n == kSumChunkPairs) {
           flush(-1.f, ss);
           zero();
           n = 0;
         }
         const Sten q = nq;
-        nq = load(pr + 1 < pn ? pr + 1 : pr);
+        nq = load(pr + 1 < q1 ? pr + 1 : pr);
         P4 rx, ry;
         use(pr, q, rx, ry);
         n++;
@@ -340,12 +383,36 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
     }
     flush(-1.f, ss);
   }
-  double* out = sums + (size_t)cell * kNSum;
-  out[kSumE + lane] = sx;  // lanes 0..15: E side, 16..31: W side
-  if (lane < 16) {
-    out[kSumN + lane] = sn;
-    out[kSumS + lane] = ss;
+  if (!SPLIT) {
+    double* out = sums + (size_t)cell * kNSum;
+    out[kSumE + lane] = sx;  // lanes 0..15: E side, 16..31: W side
+    if (lane < 16) {
+      out[kSumN + lane] = sn;
+      out[kSumS + lane] = ss;
+    }
+    return;
   }
+  __syncthreads();  // red[] of the previous virtual block has been read
+  red[warp][kSumE + lane] = sx;
+  if (lane < 16) {
+    red[warp][kSumN + lane] = sn;
+    red[warp][kSumS + lane] = ss;
+  }
+  __syncthreads();
+  if (g == 0 && !skip) {
+    double* out = sums + (size_t)cell * kNSum;
+    for (int e = lane; e < kNSum; e += 32) {
+      double t = red[warp][e];
+      for (int w = 1; w < split; w++) t += red[warp + w][e];
+      out[e] = t;
+    }
+  }
+}
+
+__device__ __noinline__ void sums_body_split(const Params& P, const float4* __restrict__ f,
+                                            double* __restrict__ sums, int bx, int split,
+                                            double (*red)[kNSum]) {
+  sums_body_p<true>(P, f, sums, bx, split, red);
 }
 
 // -------------------------------------------------------------------------------------

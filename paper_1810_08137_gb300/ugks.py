@@ -28,7 +28,7 @@ EXPORTS = ("ugks_create", "ugks_destroy", "ugks_last_error", "ugks_get_grid",
            "ugks_batch_sync", "ugks_batch_set_walk_rows", "ugks_batch_get_walk_rows",
            "ugks_batch_set_walk_vtile", "ugks_batch_get_walk_vtile", "ugks_batch_set_persistent",
            "ugks_batch_get_persistent", "ugks_batch_set_wait_limit", "ugks_batch_tune",
-           "ugks_fp64_rate", "ugks_set_wait_limit")
+           "ugks_fp64_rate", "ugks_set_wait_limit", "ugks_set_sums_split", "ugks_get_sums_split")
 NKERNELS = 6
 
 
@@ -116,6 +116,8 @@ def lib(build_if_missing: bool = True):
         L.ugks_batch_tune.argtypes = [C.c_void_p, C.c_int, _P]
         L.ugks_fp64_rate.argtypes = [C.c_void_p, _P]
         L.ugks_set_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
+        L.ugks_set_sums_split.argtypes = [C.c_void_p, C.c_int]
+        L.ugks_get_sums_split.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -255,6 +257,14 @@ class Solver:
 
     def set_wait_limit(self, polls: int):
         self._check(self._L.ugks_set_wait_limit(self._h, C.c_longlong(int(polls))))
+
+    def set_sums_split(self, warps: int):
+        """FP32-f form: warps per cell of the velocity sums (1, 2, 4; 0 = automatic)."""
+        self._check(self._L.ugks_set_sums_split(self._h, int(warps)))
+
+    @property
+    def sums_split(self) -> int:
+        return int(self._L.ugks_get_sums_split(self._h))
 
     def residual(self) -> np.ndarray:
         r = np.empty(4)

@@ -73,6 +73,11 @@ CASES = {
     "periodic_5x4_v5x6_vpos": lambda: periodic_cfg(nx=5, ny=4, nu=5, nv=6, vmin=0.5, vmax=3.0),
     "periodic_6x5_v35x8_asym": lambda: periodic_cfg(nx=6, ny=5, nu=35, nv=8, vmin=-3.0, vmax=1.5,
                                                     kn=0.1),
+    # asymmetric grid with a v = 0 node away from the centre of the range (-2 + 5 * 0.4):
+    # the host builds the grid without floating-point contraction, so the node is exactly 0
+    # (H(0) = 1/2) on every host architecture, as in the oracle
+    "periodic_5x4_v9x21_asym0": lambda: periodic_cfg(nx=5, ny=4, nu=9, nv=21, vmin=-6.0, vmax=2.0,
+                                                     umin=-4.0, umax=4.0),
     # general viscosity laws (R3): variable hard sphere with omega = 0.81 and variable soft
     # sphere with omega = 0.75, alpha = 1.4 (tau through T^omega instead of the hard-sphere
     # shortcut), the latter in a channel at small Kn (dt/tau above 0.1 in many faces)
