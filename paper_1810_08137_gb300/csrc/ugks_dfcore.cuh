@@ -18,6 +18,45 @@ struct df {
   float hi, lo;
 };
 
+// ---- conversions between FP64 and pairs with the FP32 part on the integer pipe ----
+// (a conversion instruction between FP64 and FP32 runs on the 1/64-rate FP64 pipe; the
+// interface kernels convert tens of values per face).  IEEE-754 binary64 and binary32 differ
+// in exponent bias by 1023 - 127 = 896 and in significand width by 52 - 23 = 29 bits.
+// a with its significand cut to FP32 width (toward zero), as FP64 and as FP32; both 0 when |a|
+// is below the FP32 normal range (|a| < 2^-126).  |a| >= 2^128 (beyond FP32, infinities,
+// NaN) gives an FP32 NaN and cd = a, so that a non-finite input stays non-finite.
+__device__ __forceinline__ void f32_cut(double a, double& cd, float& cf) {
+  const long long b = __double_as_longlong(a);
+  const unsigned hw = (unsigned)((unsigned long long)b >> 32), lw = (unsigned)b;
+  const unsigned m = hw & 0x7fffffffu, sg = hw & 0x80000000u;
+  const bool normal = m >= 0x38100000u;  // biased FP64 exponent >= 897: FP32 exponent >= 1
+  const bool big = m >= 0x47f00000u;     // biased FP64 exponent >= 1151: FP32 exponent >= 255
+  const unsigned fb = sg | ((m - 0x38000000u) << 3) | (lw >> 29);
+  cf = big ? __uint_as_float(sg | 0x7fc00000u) : (normal ? __uint_as_float(fb) : 0.f);
+  cd = big ? a : (normal ? __longlong_as_double(b & ~0x1fffffffLL) : 0.0);
+}
+// FP64 value of an FP32 number (exact); 0 for zero and FP32 subnormals (flushed, as the
+// FP32 arithmetic here flushes them), infinities and NaN kept non-finite
+__device__ __forceinline__ double f64_of(float x) {
+  const unsigned u = __float_as_uint(x), m = u & 0x7fffffffu, sg = u & 0x80000000u;
+  const bool big = m >= 0x7f800000u;
+  const unsigned hw = big ? (sg | (m > 0x7f800000u ? 0x7ff80000u : 0x7ff00000u))
+                          : (sg | ((m >> 3) + 0x38000000u));
+  const unsigned lw = big ? 0u : (m << 29);
+  return m >= 0x00800000u ? __hiloint2double((int)hw, (int)lw) : 0.0;
+}
+// FP64 -> normalised pair: the cut high part, the remainder (exact in FP64) rounded to FP32,
+// renormalised (|lo| <= ulp(hi) / 2); |a - (hi + lo)| <= 2^-48 |a| or so
+__device__ __forceinline__ void split_f64(double a, float& hi, float& lo) {
+  double cd;
+  float cf;
+  f32_cut(a, cd, cf);
+  const float r = __double2float_rn(a - cd);
+  const float s = __fadd_rn(cf, r);
+  hi = s;
+  lo = __fsub_rn(r, __fsub_rn(s, cf));
+}
+
 __device__ __forceinline__ df two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -34,12 +73,13 @@ __device__ __forceinline__ df two_prod(float a, float b) {
 }
 
 __device__ __forceinline__ df df_of(float a) { return {a, 0.f}; }
-// From FP64 (set-up and per-cell constants only: FP64 conversions run on the FP64 pipe)
+// From FP64 (set-up and per-cell constants)
 __device__ __forceinline__ df df_of(double a) {
-  const float h = __double2float_rn(a);
-  return {h, __double2float_rn(a - (double)h)};
+  df r;
+  split_f64(a, r.hi, r.lo);
+  return r;
 }
-__device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(df a) { return f64_of(a.hi) + f64_of(a.lo); }
 
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_add(df a, df b) {
@@ -69,9 +109,9 @@ struct dd {
   float hi, lo;
   dd() = default;
   __device__ __forceinline__ constexpr dd(float h, float l) : hi(h), lo(l) {}
-  // from FP64: the nearest FP32 and the FP32 nearest to the remainder (conversions run on
-  // the FP64 pipe: inputs and constants only)
-  __device__ __forceinline__ dd(double a) : hi((float)a), lo((float)(a - (double)(float)a)) {}
+  // from FP64 (split_f64: one FP64 subtraction and one conversion, the rest on the integer
+  // and FP32 pipes)
+  __device__ __forceinline__ dd(double a) { split_f64(a, hi, lo); }
   __device__ __forceinline__ explicit dd(int n) : hi((float)n), lo(0.f) {}
 };
 __device__ __forceinline__ df as_df(dd a) { return {a.hi, a.lo}; }
@@ -80,7 +120,7 @@ __device__ __forceinline__ dd operator+(dd a, dd b) { return as_dd(df_add(as_df(
 __device__ __forceinline__ dd operator-(dd a, dd b) { return as_dd(df_sub(as_df(a), as_df(b))); }
 __device__ __forceinline__ dd operator*(dd a, dd b) { return as_dd(df_mul(as_df(a), as_df(b))); }
 __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
-__device__ __forceinline__ double to_double(dd a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(dd a) { return f64_of(a.hi) + f64_of(a.lo); }
 __device__ __forceinline__ double to_double(double a) { return a; }
 // nearest FP32 (the high part of a normalised pair)
 __device__ __forceinline__ float to_float(dd a) { return a.hi; }

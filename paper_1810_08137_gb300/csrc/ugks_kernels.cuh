@@ -901,8 +901,9 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
 enum { kRecF64 = 0, kRecF32 = 1, kRecDF = 2 };
 
 __device__ __forceinline__ float2 split_df(double a) {
-  const float h = __double2float_rn(a);
-  return make_float2(h, __double2float_rn(a - (double)h));
+  float2 r;
+  split_f64(a, r.x, r.y);
+  return r;
 }
 __device__ __forceinline__ void face_rec_df(const FaceRec& R, FaceRecD& D) {
 #pragma unroll
