@@ -211,10 +211,10 @@ __global__ void __launch_bounds__(128, 5) kb_sums(const SlotDev* __restrict__ sl
   sums_phase(slots, wk, red);
 }
 
-// six blocks per SM (80 registers, the rest on the stack): the interface is latency-bound on
-// its FP64 and double-FP32 chains, and 24 resident warps hide more of it than 12 (0.59 ->
-// 0.52 ms at 800x400x28^2)
-__global__ void __launch_bounds__(128, 6) kb_faces(const SlotDev* __restrict__ slots,
+// eight blocks per SM (64 registers, the rest on the stack): the interface is latency-bound
+// on its FP64 and double-FP32 chains, and 32 resident warps hide more of it than 12 (0.59 ->
+// 0.50 ms at 800x400x28^2; six blocks 0.52 ms)
+__global__ void __launch_bounds__(128, 8) kb_faces(const SlotDev* __restrict__ slots,
                                                 const BatchWork* __restrict__ wk) {
   faces_phase(slots, wk);
 }
