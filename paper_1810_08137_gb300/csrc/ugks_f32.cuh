@@ -434,7 +434,8 @@ constexpr int kRing = 2;       // rows of face and cell records staged in shared
 constexpr int kFRing = 4;      // rows of f staged in shared memory: P, C, N and the next one
 constexpr int kFPos = kStripW + 3;  // walk positions of a staged f row: UU, U, strip, D
 // 16-byte chunks of one row's records of a strip: W + 1 x-faces, W y-faces, W cells
-constexpr int kStripChunks = (kStripW + 1) * 8 + kStripW * 8 + kStripW * 4;
+constexpr int kFaceF4 = sizeof(FaceRecF) / 16, kCellF4 = sizeof(CellRecF) / 16;
+constexpr int kStripChunks = (kStripW + 1) * kFaceF4 + kStripW * kFaceF4 + kStripW * kCellF4;
 // shared memory of one warp of the walk (float4): f ring, then record ring
 // ... and one 16-byte slot for the two mbarriers of the record ring
 constexpr int kStripWarpF4 = kFRing * kFPos * 32 + kRing * kStripChunks + 1;
@@ -675,7 +676,7 @@ __device__ __forceinline__ bool strip_body_p(const Params& P, const float4* __re
   float4* fring = sm;
   float4* ring = sm + kFRing * kFPos * 32;
   const uint32_t bars = smem_addr(ring + kRing * kStripChunks);  // mbarrier of ring slot b at bars + 8 b
-  constexpr int oY = (W + 1) * 8, oC = oY + W * 8;
+  constexpr int oY = (W + 1) * kFaceF4, oC = oY + W * kFaceF4;
   auto stage_f = [&](int q) {
     if (q <= nsteps + 1) {
       const float4* src = pr_ + (long)(q - 1) * rs;

@@ -63,11 +63,15 @@ struct CellRec {
 //   inflow from a diffuse wall (wall != 0): X_h = gdt D, X_b = gdt (K[0][3] D + (K[0][3] - b_ref)
 //     g_ref,h), D = g_w - g_ref,h = g_ref,h (2^(E . (1, u, v, r2)) - 1) with E the wall
 //     Maxwellian's exponent relative to g_ref's and gdt = dt
+// 144 bytes (pad): the update walk stages a row's records in shared memory, and lanes with
+// u > 0 and u < 0 read different records of the row in the same instruction; at a 128-byte
+// stride two records would fall in the same shared-memory banks, at 144 bytes they do not.
 struct __align__(16) FaceRecF {
   float Q[2][8];
   float K[2][4];
   float E[4];
   float Mt4, nMt5, wall, gdt;
+  float pad[4];
 };
 // Eq. 3 as an increment e^{n+1} = e^n + d, per component, with the Maxwellians taken
 // relative to g_ref before they are weighted (the terms stay at the deviation's scale):

@@ -692,6 +692,7 @@ __device__ __forceinline__ void wall_face_f32(const Params& P, bool isx, double 
   RF.nMt5 = 0.f;
   RF.wall = (float)wall;
   RF.gdt = (float)P.dt;
+  RF.pad[0] = RF.pad[1] = RF.pad[2] = RF.pad[3] = 0.f;
 }
 
 // S2-S5 of one UGKS interface in the face frame (un, ut): interface primitive variables,
@@ -894,6 +895,7 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   RF.nMt5 = (float)(-Mt[4]);
   RF.wall = 0.f;
   RF.gdt = 0.f;
+  RF.pad[0] = RF.pad[1] = RF.pad[2] = RF.pad[3] = 0.f;
 }
 
 // Record kind written for the update kernels: FP64 FaceRec (FP64 form), FP32 FaceRecF
