@@ -42,7 +42,8 @@ class _Cfg(C.Structure):
                 ("vmin", C.c_double), ("vmax", C.c_double), ("K", C.c_int),
                 ("kn", C.c_double), ("omega", C.c_double), ("alpha", C.c_double),
                 ("cfl", C.c_double), ("dt", C.c_double), ("bc_kind", C.c_int * 4),
-                ("bc_rho", C.c_double * 4), ("bc_T", C.c_double * 4), ("bc_U", C.c_double * 4)]
+                ("bc_rho", C.c_double * 4), ("bc_T", C.c_double * 4), ("bc_U", C.c_double * 4),
+                ("pr", C.c_double)]
 
 
 _lib = None
@@ -91,6 +92,7 @@ def _cfg(cfg) -> _Cfg:
         c.bc_rho[s] = float(cfg.bc[s].rho)
         c.bc_T[s] = float(cfg.bc[s].T)
         c.bc_U[s] = float(cfg.bc[s].U)
+    c.pr = float(getattr(cfg, "pr", 1.0))
     return c
 
 
@@ -138,6 +140,25 @@ def slope_solve(prim, K: int, s) -> np.ndarray:
     a = np.empty(4)
     lib().orc_slope_solve(_p(prim), C.c_int(K), _p(s), _p(a))
     return a
+
+
+def shakhov_eq(prim, K: int, pr: float, q, u, v) -> np.ndarray:
+    """Shakhov equilibrium (h, b) at the velocities (u[i], v[i]): shape (n, 2)."""
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    out = np.empty((u.size, 2))
+    lib().orc_shakhov_eq(_p(np.ascontiguousarray(prim, dtype=np.float64)), C.c_int(K),
+                         C.c_double(pr), _p(np.ascontiguousarray(q, dtype=np.float64)),
+                         C.c_int(u.size), _p(u), _p(v), _p(out))
+    return out
+
+
+def heat_flux(cfg, f_cell, W_cell) -> np.ndarray:
+    """Heat flux (qx, qy) of one cell's f[nq][2] about the velocity of W_cell[4]."""
+    q = np.empty(2)
+    lib().orc_heat_flux(C.byref(_cfg(cfg)), _p(np.ascontiguousarray(f_cell, dtype=np.float64)),
+                        _p(np.ascontiguousarray(W_cell, dtype=np.float64)), _p(q))
+    return q
 
 
 def init_maxwellian(cfg, rho, U, V, T):

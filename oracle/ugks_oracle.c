@@ -27,6 +27,15 @@
  *   - boundaries: periodic; diffuse isothermal wall (zero net mass flux, first order in
  *     time); pressure ghost = Maxwellian(rho_bc, U and V of the adjacent cell, T_bc) with
  *     zero slopes.
+ *   - Prandtl number pr != 1 (not in the paper, which uses the BGK model of Eq. 1): the
+ *     Shakhov model.  Its equilibrium g+ = g [1 + (1 - Pr) (c.q) (c_t^2/RT - (D+2)) /
+ *     ((D+2) p RT)] (D = 2 + K degrees of freedom, c the peculiar velocity, c_t^2 = |c|^2 +
+ *     xi^2, q the heat flux, RT = 1/(2 lam)) replaces g in the collision term.  At an
+ *     interface the heat flux is that of the upwind interface values f_up about the
+ *     interface velocity, and the Shakhov part enters the integral solution through the
+ *     zeroth-order equilibrium term only (its Mt1 weight); the slopes a_L, a_R, b, A are
+ *     those of the Maxwellian.  In Eq. 3 both g+^n and g+^{n+1} carry the heat flux of f^n
+ *     about the cell's velocity (the heat flux of f^{n+1} is not known before f^{n+1}).
  */
 #include "ugks_oracle.h"
 
@@ -223,6 +232,39 @@ static double mom_p(const gmom_t* g, int r, int m, int n, const poly_t* P) {
   return mom_pq(g, r, m, n, P, &one);
 }
 
+/* Larger polynomial in (un, ut, xi) for the Shakhov term, and its product moments. */
+typedef struct { int n; term_t t[40]; } bpoly_t;
+
+/* S(un, ut, xi) / alpha = (qn cn + qt ct) (2 lam (cn^2 + ct^2 + xi^2) - (K + 4)),
+   cn = un - Un, ct = ut - Ut, expanded into monomials: a product of 4 and 8 terms. */
+static bpoly_t shakhov_poly(double Un, double Ut, double lam, int K, const double q[2],
+                            double alpha) {
+  term_t a[4] = {{q[0], 1, 0, 0}, {-q[0] * Un, 0, 0, 0}, {q[1], 0, 1, 0}, {-q[1] * Ut, 0, 0, 0}};
+  term_t b[8] = {{2.0 * lam, 2, 0, 0}, {-4.0 * lam * Un, 1, 0, 0}, {2.0 * lam * Un * Un, 0, 0, 0},
+                 {2.0 * lam, 0, 2, 0}, {-4.0 * lam * Ut, 0, 1, 0}, {2.0 * lam * Ut * Ut, 0, 0, 0},
+                 {2.0 * lam, 0, 0, 2}, {-(K + 4.0), 0, 0, 0}};
+  bpoly_t p;
+  p.n = 0;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 8; j++)
+      p.t[p.n++] = (term_t){alpha * a[i].c * b[j].c, a[i].pu + b[j].pu, a[i].pv + b[j].pv,
+                            a[i].px + b[j].px};
+  return p;
+}
+
+/* < un^m ut^n P B > over the un-range r (B a bpoly_t). */
+static double mom_pb(const gmom_t* g, int r, int m, int n, const poly_t* P, const bpoly_t* B) {
+  double s = 0.0;
+  for (int a = 0; a < P->n; a++)
+    for (int b = 0; b < B->n; b++) {
+      const term_t* x = &P->t[a];
+      const term_t* y = &B->t[b];
+      s += x->c * y->c * g->un[r][x->pu + y->pu + m] * g->ut[x->pv + y->pv + n] *
+           g->xi[x->px + y->px];
+    }
+  return s;
+}
+
 /* S4: solve <psi (a.psi)> = s for a, with the 4x4 moment matrix of the normalised
    Maxwellian (prim = rho, U, V, lam) and Gaussian elimination with partial pivoting. */
 void orc_slope_solve(const double prim[4], int K, const double s[4], double a[4]) {
@@ -263,6 +305,62 @@ static void prim_of(const double W[4], int K, double prim[4]) {
   prim[1] = U;
   prim[2] = V;
   prim[3] = (K + 2) * rho / (4.0 * eint);
+}
+
+/* Shakhov model: the factors sh, sb with which g_h = rho (lam/pi) exp(-lam |c|^2) gives the
+   Shakhov part of the reduced equilibrium, g+_h = g_h (1 + sh), g+_b = g_h (<xi^2> + sb).
+   S = alpha (c.q) (c_t^2/RT - (D+2)), alpha = (1 - Pr) / ((D+2) p RT) = (1 - Pr) 4 lam^2 /
+   ((K+4) rho); sh = <S> and sb = <xi^2 S> over the internal variable, with <xi^2> = K/(2 lam)
+   and <xi^4> = K (K+2) / (4 lam^2) the moments of its normalised Gaussian. */
+static void shakhov_factor(const double prim[4], int K, double pr, const double q[2], double u,
+                           double v, double* sh, double* sb) {
+  double rho = prim[0], lam = prim[3];
+  double d2 = K + 4.0;
+  double alpha = (1.0 - pr) * 4.0 * lam * lam / (d2 * rho);
+  double cu = u - prim[1], cv = v - prim[2];
+  double cq = cu * q[0] + cv * q[1];
+  double c2 = 2.0 * lam * (cu * cu + cv * cv);
+  double xi2 = K / (2.0 * lam), xi4 = K * (K + 2.0) / (4.0 * lam * lam);
+  *sh = alpha * cq * (c2 + 2.0 * lam * xi2 - d2);
+  *sb = alpha * cq * ((c2 - d2) * xi2 + 2.0 * lam * xi4);
+}
+
+void orc_shakhov_eq(const double prim[4], int K, double pr, const double q[2], int n,
+                    const double* u, const double* v, double* out) {
+  for (int i = 0; i < n; i++) {
+    double du = u[i] - prim[1], dv = v[i] - prim[2];
+    double gh = prim[0] * (prim[3] / M_PI) * exp(-prim[3] * (du * du + dv * dv));
+    double sh, sb;
+    shakhov_factor(prim, K, pr, q, u[i], v[i], &sh, &sb);
+    out[2 * i] = gh * (1.0 + sh);
+    out[2 * i + 1] = gh * (K / (2.0 * prim[3]) + sb);
+  }
+}
+
+/* Heat flux q = 1/2 sum w c (|c|^2 h + b), c = (u - U, v - V), of a reduced f[nq][2]. */
+static void heat_flux(int nq, const double* w, const double* uq, const double* vq,
+                      const double* f, double U, double V, double q[2]) {
+  q[0] = q[1] = 0.0;
+  for (int k = 0; k < nq; k++) {
+    double cu = uq[k] - U, cv = vq[k] - V;
+    double e = (cu * cu + cv * cv) * f[2 * k] + f[2 * k + 1];
+    q[0] += 0.5 * w[k] * cu * e;
+    q[1] += 0.5 * w[k] * cv * e;
+  }
+}
+
+void orc_heat_flux(const orc_cfg* c, const double* f, const double W[4], double q[2]) {
+  int nq = c->nu * c->nv;
+  double* u = malloc(sizeof(double) * c->nu);
+  double* v = malloc(sizeof(double) * c->nv);
+  double* w = malloc(sizeof(double) * nq);
+  double* uq = malloc(sizeof(double) * nq);
+  double* vq = malloc(sizeof(double) * nq);
+  orc_vgrid(c, u, v, w);
+  for (int m = 0; m < c->nv; m++)
+    for (int k = 0; k < c->nu; k++) { uq[m * c->nu + k] = u[k]; vq[m * c->nu + k] = v[m]; }
+  heat_flux(nq, w, uq, vq, f, W[1] / W[0], W[2] / W[0], q);
+  free(u); free(v); free(w); free(uq); free(vq);
 }
 
 void orc_init_maxwellian(const orc_cfg* c, const double* rho, const double* U, const double* V,
@@ -508,6 +606,20 @@ static void ugks_face(const ctx_t* x, const double* un, const double* ut,
                      Mt[2] * mom_pq(&g, 0, 1, 0, &psi, &pA));
   }
 
+  /* Shakhov model (pr != 1): heat flux of the interface values about (U0, V0), and the
+     Shakhov part of the zeroth-order equilibrium term in the macroscopic flux */
+  double pr = x->c->pr, q0[2] = {0.0, 0.0};
+  int shk = pr != 1.0;
+  if (shk) {
+    heat_flux(nq, w, un, ut, sc->fup, prim0[1], prim0[2], q0);
+    double alpha = (1.0 - pr) * 4.0 * lam0 * lam0 / ((K + 4.0) * rho0);
+    bpoly_t S0 = shakhov_poly(prim0[1], prim0[2], lam0, K, q0, alpha);
+    for (int i = 0; i < 4; i++) {
+      poly_t psi = psi_poly(i);
+      Feq[i] += rho0 * Mt[0] * mom_pb(&g, 0, 1, 0, &psi, &S0);
+    }
+  }
+
   /* S7: free-transport part of the macroscopic flux (4 reductions) */
   double Sf[4] = {0, 0, 0, 0}, Ss[4] = {0, 0, 0, 0};
   for (int q = 0; q < nq; q++) {
@@ -538,9 +650,11 @@ static void ugks_face(const ctx_t* x, const double* un, const double* ut,
       double PhA = P_h(A, un[q], ut[q], xi2), PbA = P_b(A, un[q], ut[q], xi2, xi4);
       double dh = un[q] * sc->snup[2 * q] + ut[q] * sc->stup[2 * q];
       double db = un[q] * sc->snup[2 * q + 1] + ut[q] * sc->stup[2 * q + 1];
-      ft[2 * q] = un[q] * (Mt[0] * gh + (Mt[1] * (un[q] * Pha + ut[q] * Phb) + Mt[2] * PhA) * gh +
+      double sh = 0.0, sb = 0.0;
+      if (shk) shakhov_factor(prim0, K, pr, q0, un[q], ut[q], &sh, &sb);
+      ft[2 * q] = un[q] * (Mt[0] * (gh + gh * sh) + (Mt[1] * (un[q] * Pha + ut[q] * Phb) + Mt[2] * PhA) * gh +
                            Mt[3] * sc->fup[2 * q] - Mt[4] * dh);
-      ft[2 * q + 1] = un[q] * (Mt[0] * gb + (Mt[1] * (un[q] * Pba + ut[q] * Pbb) + Mt[2] * PbA) * gh +
+      ft[2 * q + 1] = un[q] * (Mt[0] * (gb + gh * sb) + (Mt[1] * (un[q] * Pba + ut[q] * Pbb) + Mt[2] * PbA) * gh +
                                Mt[3] * sc->fup[2 * q + 1] - Mt[4] * db);
     }
   }
@@ -689,8 +803,8 @@ void orc_fluxes(const orc_cfg* c, const double* f, const double* W, double* Fx, 
 
 /* Cell update: Eq. 4 for W and Eq. 3 (trapezoidal in the collision term, solved for
    f^{n+1}) for f.  The flux terms are the time-integrated fluxes per unit face length. */
-static void update_cell(const orc_cfg* c, const double* uq, const double* vq, double dt,
-                        const double Wn[4], const double FxW[4], const double FxE[4],
+static void update_cell(const orc_cfg* c, const double* uq, const double* vq, const double* wq,
+                        double dt, const double Wn[4], const double FxW[4], const double FxE[4],
                         const double FyS[4], const double FyN[4], const double* fxW,
                         const double* fxE, const double* fyS, const double* fyN,
                         const double* fn, double* fnew, double Wnew[4]) {
@@ -702,6 +816,10 @@ static void update_cell(const orc_cfg* c, const double* uq, const double* vq, do
   prim_of(Wn, K, pn);
   prim_of(Wnew, K, pn1);
   double tn = orc_tau(c, pn[0], pn[3]), tn1 = orc_tau(c, pn1[0], pn1[3]);
+  /* Shakhov model: the heat flux of f^n about the cell's velocity, in g+^n and g+^{n+1} */
+  int shk = c->pr != 1.0;
+  double qn[2] = {0.0, 0.0};
+  if (shk) heat_flux(nq, wq, uq, vq, fn, pn[1], pn[2], qn);
   for (int q = 0; q < nq; q++) {
     double du = uq[q] - pn[1], dv = vq[q] - pn[2];
     double gnh = pn[0] * (pn[3] / M_PI) * exp(-pn[3] * (du * du + dv * dv));
@@ -709,6 +827,15 @@ static void update_cell(const orc_cfg* c, const double* uq, const double* vq, do
     du = uq[q] - pn1[1]; dv = vq[q] - pn1[2];
     double g1h = pn1[0] * (pn1[3] / M_PI) * exp(-pn1[3] * (du * du + dv * dv));
     double g1b = K / (2.0 * pn1[3]) * g1h;
+    if (shk) {
+      double sh, sb;
+      shakhov_factor(pn, K, c->pr, qn, uq[q], vq[q], &sh, &sb);
+      gnb = gnb + gnh * sb;
+      gnh = gnh + gnh * sh;
+      shakhov_factor(pn1, K, c->pr, qn, uq[q], vq[q], &sh, &sb);
+      g1b = g1b + g1h * sb;
+      g1h = g1h + g1h * sh;
+    }
     for (int cp = 0; cp < 2; cp++) {
       int n = 2 * q + cp;
       double gn = cp == 0 ? gnh : gnb, g1 = cp == 0 ? g1h : g1b;
@@ -728,14 +855,14 @@ void orc_step(const orc_cfg* c, double* f, double* W, int nsteps) {
   double* fy = malloc(sizeof(double) * (size_t)nfy * nq * 2);
   double* uq = malloc(sizeof(double) * nq);
   double* vq = malloc(sizeof(double) * nq);
+  double* wq = malloc(sizeof(double) * nq);
   {
     double* u = malloc(sizeof(double) * c->nu);
     double* v = malloc(sizeof(double) * c->nv);
-    double* w = malloc(sizeof(double) * nq);
-    orc_vgrid(c, u, v, w);
+    orc_vgrid(c, u, v, wq);
     for (int m = 0; m < c->nv; m++)
       for (int k = 0; k < c->nu; k++) { uq[m * c->nu + k] = u[k]; vq[m * c->nu + k] = v[m]; }
-    free(u); free(v); free(w);
+    free(u); free(v);
   }
   double dt = orc_dt(c);
   for (int s = 0; s < nsteps; s++) {
@@ -748,13 +875,13 @@ void orc_step(const orc_cfg* c, double* f, double* W, int nsteps) {
       double Wn[4], Wnew[4];
       for (int k = 0; k < 4; k++) Wn[k] = W[k * nc + cell];
       double* fc = f + (size_t)cell * nq * 2;
-      update_cell(c, uq, vq, dt, Wn, Fx + 4 * xw, Fx + 4 * xe, Fy + 4 * ys, Fy + 4 * yn,
+      update_cell(c, uq, vq, wq, dt, Wn, Fx + 4 * xw, Fx + 4 * xe, Fy + 4 * ys, Fy + 4 * yn,
                   fx + xw * nq * 2, fx + xe * nq * 2, fy + ys * nq * 2, fy + yn * nq * 2, fc, fc,
                   Wnew);
       for (int k = 0; k < 4; k++) W[k * nc + cell] = Wnew[k];
     }
   }
-  free(Fx); free(Fy); free(fx); free(fy); free(uq); free(vq);
+  free(Fx); free(Fy); free(fx); free(fy); free(uq); free(vq); free(wq);
 }
 
 /* One step for a list of cells only (the rest of the state is read, not written):
@@ -781,7 +908,7 @@ void orc_step_cells(const orc_cfg* c, const double* f, const double* W, int ncel
       face_y(&x, &wk, i, j - 1, FS, fys);
       face_y(&x, &wk, i, j, FN, fyn);
       for (int k = 0; k < 4; k++) Wn[k] = W[k * nc + cell];
-      update_cell(c, x.uq, x.vq, x.dt, Wn, FW, FE, FS, FN, fxw, fxe, fys, fyn,
+      update_cell(c, x.uq, x.vq, x.w, x.dt, Wn, FW, FE, FS, FN, fxw, fxe, fys, fyn,
                   f + (size_t)cell * nq * 2, f_out + (size_t)n * nq * 2, W_out + 4 * (size_t)n);
     }
     free(fxw); free(fxe); free(fys); free(fyn);

@@ -33,6 +33,7 @@ typedef struct {
   double cfl, dt;              /* dt <= 0: dt from the CFL number */
   int bc_kind[4];              /* W, E, S, N */
   double bc_rho[4], bc_T[4], bc_U[4];
+  double pr;                   /* Prandtl number: 1 = BGK (Eq. 1); otherwise the Shakhov model */
 } orc_cfg;
 
 void   orc_set_threads(int n);
@@ -54,6 +55,12 @@ void   orc_fluxes(const orc_cfg* c, const double* f, const double* W,
                   double* Fx, double* Fy, double* fx, double* fy);
 /* nsteps explicit UGKS steps in place (Eq. 3 for f, Eq. 4 for W). */
 void   orc_step(const orc_cfg* c, double* f, double* W, int nsteps);
+/* Shakhov equilibrium of prim = (rho, U, V, lam) with heat flux q = (qx, qy) at the n
+ * velocities (u[i], v[i]): out[i][0] = h, out[i][1] = b (reduced over the internal variable). */
+void   orc_shakhov_eq(const double prim[4], int K, double pr, const double q[2], int n,
+                      const double* u, const double* v, double* out);
+/* Heat flux q = 1/2 sum w c (|c|^2 h + b) of one cell's f[nq][2] about the velocity of W. */
+void   orc_heat_flux(const orc_cfg* c, const double* f, const double W[4], double q[2]);
 /* One step for the listed cells only: f_out[n][nq][2], W_out[n][4] for cell ids[n]. */
 void   orc_step_cells(const orc_cfg* c, const double* f, const double* W, int ncell,
                       const int* ids, double* f_out, double* W_out);

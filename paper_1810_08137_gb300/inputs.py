@@ -61,6 +61,8 @@ class Config:
     # (rho, U, V, T) of the FP32-f form's reference Maxwellian g_ref (f is stored as f - g_ref);
     # None: the library's default (1, 0, 0, 1).  Not used by the FP64 form.
     ref: tuple = None
+    # Prandtl number: 1 = the BGK model of Eq. 1; otherwise the Shakhov model
+    pr: float = 1.0
 
     @property
     def nc(self) -> int:

@@ -110,8 +110,23 @@ def time_weights(dt, tau, n=24):
     return C0, C1, C2, D0, D1
 
 
+def shakhov_s(pr, K, rho, Un, Ut, lam, q, un, ut, xi2):
+    """Shakhov factor S of g+ = g (1 + S) at (un, ut, |xi|^2), stated in physical terms:
+    S = (1 - Pr) (c . q) / ((D + 2) p RT) (c_t^2 / RT - (D + 2)), D = 2 + K, RT = 1/(2 lam),
+    p = rho RT, c_t^2 = |c|^2 + |xi|^2 (the internal variable integrated by quadrature)."""
+    RT = 1.0 / (2.0 * lam)
+    p = rho * RT
+    D = 2 + K
+    cn, ct = un - Un, ut - Ut
+    return (1.0 - pr) * (cn * q[0] + ct * q[1]) / ((D + 2) * p * RT) * (
+        (cn ** 2 + ct ** 2 + xi2) / RT - (D + 2))
+
+
 def ugks_face(cfg, dt, unq, utq, wq, f_up, sn_up, st_up, W0, WL, WR, delta, St, K):
-    """Brute-force macroscopic (rotated frame) and micro flux at one interface."""
+    """Brute-force macroscopic (rotated frame) and micro flux at one interface.  With a
+    Prandtl number pr != 1 (Shakhov model) the zeroth-order equilibrium term carries the
+    Shakhov factor of the interface heat flux (that of the upwind values about the
+    interface velocity)."""
     rho0 = W0[0]
     Un, Ut = W0[1] / rho0, W0[2] / rho0
     lam = (K + 2) * rho0 / (4 * (W0[3] - 0.5 * rho0 * (Un ** 2 + Ut ** 2)))
@@ -130,8 +145,16 @@ def ugks_face(cfg, dt, unq, utq, wq, f_up, sn_up, st_up, W0, WL, WR, delta, St, 
     A = np.linalg.solve(M, sA)
     pA = apsi(A, Q.un, Q.ut, Q.xi2)
     C0, C1, C2, D0, D1 = time_weights(dt, tau)
-    # equilibrium part: g0 [1 + (a.psi) x' + (b.psi) y' + (A.psi) t'], x' = -un s, y' = -ut s
-    eq = C0 - C1 * Q.un * pa - C1 * Q.ut * pb + C2 * pA
+    pr = getattr(cfg, "pr", 1.0)
+    q0 = np.zeros(2)
+    if pr != 1.0:
+        cn, ct = unq - Un, utq - Ut
+        e = (cn ** 2 + ct ** 2) * f_up[:, 0] + f_up[:, 1]
+        q0 = 0.5 * np.array([np.sum(wq * cn * e), np.sum(wq * ct * e)])
+    # equilibrium part: g0 [1 + S + (a.psi) x' + (b.psi) y' + (A.psi) t'], x' = -un s,
+    # y' = -ut s, the Shakhov factor S on the zeroth-order term only
+    S_q = shakhov_s(pr, K, rho0, Un, Ut, lam, q0, Q.un, Q.ut, Q.xi2)
+    eq = C0 * (1.0 + S_q) - C1 * Q.un * pa - C1 * Q.ut * pb + C2 * pA
     Feq = rho0 * np.einsum("in,n->i", psi, Q.w * Q.un * eq)
     # free transport, discrete sums
     d = unq[:, None] * sn_up + utq[:, None] * st_up  # (nq, 2)
@@ -157,7 +180,8 @@ def ugks_face(cfg, dt, unq, utq, wq, f_up, sn_up, st_up, W0, WL, WR, delta, St, 
                                                           0.5 * (aL + aR)[None, :]))
     X = xi2[None, :]
     paq = aq[:, 0:1] + aq[:, 1:2] * u + aq[:, 2:3] * v + 0.5 * aq[:, 3:4] * (u ** 2 + v ** 2 + X)
-    eqq = C0 - C1 * u * paq - C1 * v * apsi(b, u, v, X) + C2 * apsi(A, u, v, X)
+    S_d = shakhov_s(pr, K, rho0, Un, Ut, lam, q0, u, v, X)
+    eqq = C0 * (1.0 + S_d) - C1 * u * paq - C1 * v * apsi(b, u, v, X) + C2 * apsi(A, u, v, X)
     h_eq = (g0 * eqq * wxi[None, :]).sum(axis=1)
     b_eq = (g0 * eqq * X * wxi[None, :]).sum(axis=1)
     ft = np.stack([unq * (h_eq + fm[:, 0]), unq * (b_eq + fm[:, 1])], axis=1)

@@ -15,6 +15,7 @@ import pytest
 
 from oracle import oracle as O
 from tests import test_oracle_pins as T
+from tests import test_oracle_shakhov as TS
 
 SRC = open(O.SRC).read()
 
@@ -63,6 +64,22 @@ def _pin_mt(o):
     T.test_mt_against_time_quadrature(o, 1.0)
 
 
+def _pin_shk_moments(o):
+    TS.test_shakhov_equilibrium_moments(o, 2, 2.0 / 3.0)
+
+
+def _pin_shk_relax(o):
+    TS.test_shakhov_homogeneous_heat_flux_relaxation(o, 1, 0.5)
+
+
+def _pin_shk_bf(o):
+    TS.test_shakhov_bruteforce_periodic_4x4(o, 1, 0.05, 2.0 / 3.0)
+
+
+def _pin_shk_eq3(o):
+    TS.test_shakhov_step_satisfies_eq3_and_eq4(o, "channel")
+
+
 # (name, anchor in ugks_oracle.c, replacement, pin that must fail)
 MUTATIONS = [
     ("mu_ref (5-2w)(7-2w) -> (5-w)(7-w)", "(5.0 - 2.0 * om) * (7.0 - 2.0 * om)",
@@ -107,6 +124,20 @@ MUTATIONS = [
     ("Maxwellian b = K/2 h at set-up", "f[o + 1] = c->K / (2.0 * lam) * gh;", "f[o + 1] = c->K / 2.0 * gh;",
      _pin_moments),
     ("Mt4 limit: e^{-x} dropped", "c4 = em / x;", "c4 = 1.0 / x;", _pin_mt),
+    # Shakhov model (Prandtl number != 1)
+    ("Shakhov: D + 2 taken as 5 whatever K", "double d2 = K + 4.0;", "double d2 = 5.0;",
+     _pin_shk_moments),
+    ("Shakhov: <xi^4> term of the b factor dropped", "*sb = alpha * cq * ((c2 - d2) * xi2 + 2.0 * lam * xi4);",
+     "*sb = alpha * cq * (c2 - d2) * xi2;", _pin_shk_moments),
+    ("Shakhov: heat flux without the b part", "double e = (cu * cu + cv * cv) * f[2 * k] + f[2 * k + 1];",
+     "double e = (cu * cu + cv * cv) * f[2 * k];", _pin_shk_relax),
+    ("Shakhov: g+^{n+1} with W^n", "shakhov_factor(pn1, K, c->pr, qn, uq[q], vq[q], &sh, &sb);",
+     "shakhov_factor(pn, K, c->pr, qn, uq[q], vq[q], &sh, &sb);", _pin_shk_eq3),
+    ("Shakhov: interface heat flux about U = 0",
+     "heat_flux(nq, w, un, ut, sc->fup, prim0[1], prim0[2], q0);",
+     "heat_flux(nq, w, un, ut, sc->fup, 0.0, 0.0, q0);", _pin_shk_bf),
+    ("Shakhov: macroscopic flux without the Shakhov part",
+     "Feq[i] += rho0 * Mt[0] * mom_pb(&g, 0, 1, 0, &psi, &S0);", "Feq[i] += 0.0;", _pin_shk_bf),
 ]
 
 
