@@ -108,6 +108,17 @@ typedef struct {
    * mean state keeps that deviation small.  ref_T <= 0 selects (1, 0, 0, 1).  The state
    * exchanged through this ABI is always f itself. */
   double ref_rho, ref_U, ref_V, ref_T;
+  /* Prandtl number.  1 (or <= 0, the value of a zero-initialised config) selects the BGK
+   * model of Eq. 1; any other value the Shakhov model, whose equilibrium
+   * g+ = g [1 + (1 - Pr) (c.q) (c_t^2/RT - (D+2)) / ((D+2) p RT)] (D = 2 + K, c the
+   * peculiar velocity, c_t^2 = |c|^2 + xi^2, q the heat flux, RT = 1/(2 lam)) replaces g in
+   * the collision term.  The paper uses BGK; the Shakhov model follows the UGKS papers it
+   * cites, with these readings: at an interface the heat flux of the upwind interface
+   * values about the interface velocity, on the zeroth-order equilibrium term (Mt1) of the
+   * integral solution; in Eq. 3 the heat flux of f^n in the g+ of both steps n and n+1.  Supported
+   * by the UGKS_FP64 and UGKS_FP32F forms (UGKS_EINVAL for UGKS_DF64 and for
+   * ugks_step_noalloc). */
+  double pr;
 } ugks_config;
 
 typedef struct ugks_ctx* ugks_handle;

@@ -49,6 +49,8 @@ struct ugks_ctx {
   float2* gdf = nullptr;
   int nchunk_neg = 0, nchunk_pos = 0;
   int sums_split = 1;        // FP32 form: warps per cell of the sums kernel (velocity-space split)
+  double* hs = nullptr;      // Shakhov model: heat-flux moment sums, kNHeat per cell
+  CellShkF* cshk = nullptr;  // Shakhov model, FP32-f form: per-cell Shakhov factors
   // FP32 form: the step runs the batch kernels over a one-instance table, so an instance
   // stepped alone executes exactly the code it executes inside a batch
   SlotDev* d_slot = nullptr;
@@ -106,6 +108,9 @@ void axis(int n, double lo, double hi, std::vector<double>& x, std::vector<doubl
   }
 }
 
+// Prandtl number of a configuration: pr <= 0 (a zero-initialised field) means BGK, 1.
+double shakhov_pr(const ugks_config* c) { return c->pr > 0.0 ? c->pr : 1.0; }
+
 const char* validate(const ugks_config* c) {
   if (!c) return "cfg is NULL";
   if (c->nx < 1 || c->ny < 1) return "nx, ny must be >= 1";
@@ -121,6 +126,9 @@ const char* validate(const ugks_config* c) {
   if (!(c->dt > 0) && !(c->cfl > 0)) return "need cfl > 0 or dt > 0";
   if (c->precision != UGKS_FP64 && c->precision != UGKS_FP32F && c->precision != UGKS_DF64)
     return "bad precision";
+  if (!std::isfinite(c->pr)) return "pr must be finite";
+  if (shakhov_pr(c) != 1.0 && c->precision == UGKS_DF64)
+    return "Shakhov model (pr != 1): UGKS_FP64 or UGKS_FP32F form only";
   for (int s = 0; s < 4; s++) {
     const ugks_bc& b = c->bc[s];
     if (b.kind < 0 || b.kind > 2) return "bad boundary kind";
@@ -177,6 +185,7 @@ size_t predict_bytes(const ugks_config* c) {
   const size_t fcells = (nx + 4) * (ny + 4), nwe = (nx + 2) * (ny + 2);
   const size_t nfx = (nx + 1) * ny, nfy = nx * (ny + 1), nrb = (nc + 127) / 128;
   size_t b = 2 * fcells * fslot + 2 * 4 * sizeof(double) * nwe + sizeof(double) * kNSum * nwe;
+  if (shakhov_pr(c) != 1.0) b += sizeof(double) * kNHeat * nwe + (f32 ? sizeof(CellShkF) * nc : 0);
   b += f32 ? sizeof(FaceRecF) * (nfx + nfy) : (dfm ? sizeof(FaceRecD) : sizeof(FaceRec)) * (nfx + nfy);
   b += sizeof(double) * 4 * (nfx + nfy) + sizeof(double) * (nfx + nfy);
   b += f32 ? sizeof(CellRecF) * nc : (dfm ? sizeof(CellRecD) : sizeof(CellRec)) * nc;
@@ -585,6 +594,7 @@ extern "C" {
 ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const double* W_in,
                               double* f_out, double* W_out, void* cuda_stream) {
   const char* bad = validate(cfg);
+  if (!bad && shakhov_pr(cfg) != 1.0) bad = "the Shakhov model (pr != 1) needs ugks_create";
   if (bad || !f_in || !W_in || !f_out || !W_out || cfg->precision != UGKS_FP64) {
     fprintf(stderr, "ugks_step_noalloc: %s\n",
             bad ? bad : (cfg->precision != UGKS_FP64 ? "precision must be UGKS_FP64" : "NULL buffer"));
@@ -837,6 +847,9 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   P.mu_ref = 5.0 * (a + 1.0) * (a + 2.0) * sqrt(M_PI) / (4.0 * a * (5.0 - 2.0 * om) * (7.0 - 2.0 * om)) * cfg->kn;
   P.omega = om;
   P.omega_half = om == 0.5;
+  P.pr = shakhov_pr(cfg);
+  P.shk = P.pr != 1.0;
+  P.shk_c = (1.0 - P.pr) * 4.0 / (P.K + 4.0);
   set_derived(P);
   P.f_tdx = (float)(2.0 / P.dx);
   P.f_tdy = (float)(2.0 / P.dy);
@@ -918,6 +931,20 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             P.refsum[sd][kOffW0 + c] += hs[sd] * w * psi[c];
             P.refsum[sd][kOffSf + c] += hs[sd] * w * un[sd] * psi[c];
           }
+        if (P.shk) {  // Shakhov: raw heat-flux moments of g_ref per side and over the cell
+          const double mh[10] = {u * u, u * v, v * v, u * u * u, u * u * v, u * v * v, v * v * v, 0, 0, 0};
+          for (int sd = 0; sd < 4; sd++) {
+            for (int t = 0; t < 7; t++) P.refheat[sd][t] += hs[sd] * w * mh[t] * gh;
+            P.refheat[sd][7] += hs[sd] * w * gb;
+            P.refheat[sd][8] += hs[sd] * w * u * gb;
+            P.refheat[sd][9] += hs[sd] * w * v * gb;
+          }
+          const double mc[10] = {1.0, u, v, u * u, u * v, v * v, u * u * u, u * u * v, u * v * v, v * v * v};
+          for (int t = 0; t < 10; t++) P.refheat[4][t] += w * mc[t] * gh;
+          P.refheatC[0] += w * gb;
+          P.refheatC[1] += w * u * gb;
+          P.refheatC[2] += w * v * gb;
+        }
       }
     for (int c = 0; c < 4; c++) {
       P.refpair[0][c] = P.refsum[kSumE / 16][kOffW0 + c] + P.refsum[kSumW / 16][kOffW0 + c];
@@ -952,6 +979,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             alloc((void**)&h->W[0], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->W[1], 4 * sizeof(double) * h->nwe) &&
             alloc((void**)&h->sums, sizeof(double) * kNSum * (size_t)h->nwe) &&
+            (!P.shk || alloc((void**)&h->hs, sizeof(double) * kNHeat * (size_t)h->nwe)) &&
             (f32 || alloc((void**)&h->slopes, sizeof(double2) * 2 * (size_t)h->nwe * P.nq)) &&
             (f32 || alloc((void**)&h->xflux, sizeof(double2) * (size_t)(nfx + nfy) * P.nq)) &&
             (f32 ? alloc((void**)&h->fxf, sizeof(FaceRecF) * (size_t)nfx)
@@ -963,6 +991,7 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
             alloc((void**)&h->Fx, sizeof(double) * 4 * (size_t)nfx) &&
             alloc((void**)&h->Fy, sizeof(double) * 4 * (size_t)nfy) &&
             alloc((void**)&h->mt4, sizeof(double) * (size_t)(nfx + nfy)) &&
+            (!(f32 && P.shk) || alloc((void**)&h->cshk, sizeof(CellShkF) * (size_t)nc)) &&
             (f32 ? alloc((void**)&h->cellf, sizeof(CellRecF) * (size_t)nc)
                  : dfm ? alloc((void**)&h->celld, sizeof(CellRecD) * (size_t)nc)
                        : alloc((void**)&h->cells, sizeof(CellRec) * (size_t)nc)) &&
@@ -998,6 +1027,8 @@ ugks_status ugks_create(const ugks_config* cfg, void* cuda_stream, ugks_handle* 
   for (int n = 0; n < 5; n++)
     for (int m = 0; m < P.nv; m++) grid.push_back(h->hwv[m] * std::pow(h->hv[m], n));
   P.mvd = h->d_grid + 2 * (P.nu + P.nv);
+  P.hs = h->hs;
+  P.cshk = h->cshk;
   P.u = h->d_grid;
   P.v = h->d_grid + P.nu;
   P.wu = h->d_grid + P.nu + P.nv;
@@ -1090,7 +1121,8 @@ void ugks_destroy(ugks_handle h) {
   if (!h) return;
   void* ptrs[] = {h->f[0], h->f[1], h->W[0], h->W[1], h->sums, h->slopes, h->xflux, h->fxr, h->fyr, h->Fx, h->Fy,
                   h->cells, h->rpart, h->err, h->d_grid, h->stage, h->gref4, h->grefd, h->fxf, h->fyf,
-                  h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work, h->fxd, h->fyd, h->celld, h->gdf};
+                  h->cellf, h->mt4, h->ftab, h->d_slot, h->d_work, h->fxd, h->fyd, h->celld, h->gdf,
+                  h->hs, h->cshk};
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->xstream) {
     cudaStreamSynchronize(h->xstream);
@@ -1234,6 +1266,7 @@ ugks_status ugks_set_sums_split(ugks_handle h, int warps) {
   if (!h || !(warps == 0 || warps == 1 || warps == 2 || warps == 4))
     return fail(h, UGKS_EINVAL, "set_sums_split: warps must be 0, 1, 2 or 4");
   if (!h->d_slot) return fail(h, UGKS_EINVAL, "set_sums_split: FP32-f form only");
+  if (h->P.shk && warps > 1) return fail(h, UGKS_EINVAL, "set_sums_split: one warp per cell for the Shakhov model");
   CK(cudaStreamSynchronize(h->stream));
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
@@ -1460,6 +1493,7 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
 // two waves of the kernel's resident warps (sms x 5 blocks x 4 warps) and every warp keeps at
 // least two FP32 chunks of row pairs per half of the v axis.
 int auto_sums_split(const Params& P, int sms) {
+  if (P.shk) return 1;  // the Shakhov model's heat-flux sums run one warp per cell
   const long cells = (long)(P.nx + 2) * (P.ny + 2), resident = (long)sms * 5 * kWarpsPerBlock;
   int pmin = P.pr_neg < P.pr_all - P.pr_neg ? P.pr_neg : P.pr_all - P.pr_neg;
   if (pmin == 0) pmin = P.pr_all;

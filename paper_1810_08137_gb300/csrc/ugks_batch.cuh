@@ -101,7 +101,9 @@ __device__ __noinline__ void sums_phase(const SlotDev* __restrict__ slots, const
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    if (S.sums_split > 1)
+    if (S.P.shk)
+      sums_body_shk(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a]);
+    else if (S.sums_split > 1)
       sums_body_split(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], S.sums_split, red);
     else
       sums_body_p<false>(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], 1, red);
@@ -154,6 +156,14 @@ __device__ __forceinline__ void walk_item(const SlotDev& S, int ns, int nt, int 
   ck = t * vt + c;
 }
 
+// The Shakhov model's walk (general strip width), compiled as a function of its own so that
+// it adds no registers to the BGK walk.
+__device__ __noinline__ bool strip_body_shk(const SlotDev& S, int c, int bx, int by, int ck, float4* wsm,
+                                           unsigned& nrec) {
+  return strip_body_p<kStripW, false, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                            S.walk_rows, bx, by, ck, wsm, nrec, S.err);
+}
+
 // Update sweep: one warp per work item (strip, row tile, velocity chunk).
 __device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
                                             float4* strip_sm) {
@@ -184,7 +194,9 @@ __device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, cons
       // full strips (all but the last of a row when kStripW does not divide nx) with the
       // strip width known at compile time
       if (!ok) continue;  // a wait of this warp gave up: its walks are skipped (err is set)
-      if ((bx + 1) * kStripW <= S.P.nx)
+      if (S.P.shk)  // Shakhov model: the walk with g+ in the collision term
+        ok = strip_body_shk(S, c, bx, by, ck, wsm, nrec);
+      else if ((bx + 1) * kStripW <= S.P.nx)
         ok = strip_body_p<kStripW, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
                                          S.walk_rows, bx, by, ck, wsm, nrec, S.err);
       else

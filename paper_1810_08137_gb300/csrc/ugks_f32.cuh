@@ -236,6 +236,40 @@ __device__ __forceinline__ float chunk_x_sums(float u, float wu, float cu, float
   return kv[0];
 }
 
+// Shakhov model: the chunk's contribution to the raw heat-flux moments (the kNHeat layout:
+// E and W face values, the y face values of the current half, the cell values), from the
+// lane's FP32 chunk sums, reduced across the warp in FP32 like the other chunk sums: 43
+// entries in two transpose reduce-scatters of 32; r1 = entry lane, r2 = entry 32 + lane.
+// Entries: [0..9] E, [10..19] W (M20 M11 M02 M30 M21 M12 M03 B00 B10 B01 each), [20..29] the
+// half's y side, [30..42] the cell (M00 M10 M01 M20 M11 M02 M30 M21 M12 M03 B00 B10 B01).
+__device__ __forceinline__ void chunk_heat_sums(float u, float wu, float sy, float a0, float a1, float a2,
+                                                float a3, float ab0, float ab1, float x0, float x1,
+                                                float x2, float x3, float xb0, float xb1, float y0,
+                                                float y1, float y2, float y3, float yb0, float yb1,
+                                                int lane, float& r1, float& r2) {
+  const float hE = u > 0.f ? 1.f : (u < 0.f ? 0.f : 0.5f);
+  const float hW = u < 0.f ? 1.f : (u > 0.f ? 0.f : 0.5f);
+  const float uu = u * u, u3 = uu * u;
+  float e1[32], e2[32];
+  auto side = [&](float w, float F0, float F1, float F2, float F3, float Fb0, float Fb1, float* o) {
+    o[0] = w * uu * F0; o[1] = w * u * F1; o[2] = w * F2; o[3] = w * u3 * F0; o[4] = w * uu * F1;
+    o[5] = w * u * F2; o[6] = w * F3; o[7] = w * Fb0; o[8] = w * u * Fb0; o[9] = w * Fb1;
+  };
+  const float wE = wu * hE, wW = wu * hW;
+  side(wE, a0 + x0, a1 + x1, a2 + x2, a3 + x3, ab0 + xb0, ab1 + xb1, e1);
+  side(wW, a0 - x0, a1 - x1, a2 - x2, a3 - x3, ab0 - xb0, ab1 - xb1, e1 + 10);
+  side(wu, a0 + sy * y0, a1 + sy * y1, a2 + sy * y2, a3 + sy * y3, ab0 + sy * yb0, ab1 + sy * yb1, e1 + 20);
+  e1[30] = wu * a0;
+  e1[31] = wu * u * a0;
+  e2[0] = wu * a1; e2[1] = wu * uu * a0; e2[2] = wu * u * a1; e2[3] = wu * a2; e2[4] = wu * u3 * a0;
+  e2[5] = wu * uu * a1; e2[6] = wu * u * a2; e2[7] = wu * a3; e2[8] = wu * ab0; e2[9] = wu * u * ab0;
+  e2[10] = wu * ab1;
+#pragma unroll
+  for (int t = 11; t < 32; t++) e2[t] = 0.f;
+  r1 = warp_reduce_scatter<32>(e1, lane);
+  r2 = warp_reduce_scatter<32>(e2, lane);
+}
+
 // Velocity-space split (split = 1, 2 or 4 warps per cell, the warps of one cell in one
 // block): warp g of a cell's group takes the g-th of `split` contiguous ranges of row pairs in
 // each half of the v axis, and the group's FP64 face sums are added in shared memory (`red`,
@@ -244,8 +278,9 @@ __device__ __forceinline__ float chunk_x_sums(float u, float wu, float cu, float
 // must be uniform in `split` (it is: a block's cells belong to one instance).
 // SPLIT = false: one warp per cell (split 1), without the range and reduction code; the
 // caller inlines it and calls the split instance as a function of its own (sums_body_split),
-// so that the split path's registers do not weigh on the one-warp path.
-template <bool SPLIT>
+// so that the split path's registers do not weigh on the one-warp path.  SHK: the Shakhov
+// model's heat-flux moments too (P.hs; one warp per cell, called as sums_body_shk).
+template <bool SPLIT, bool SHK = false>
 __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
                                             double* __restrict__ sums, int bx, int split_,
                                             double (*red)[kNSum]) {
@@ -275,6 +310,7 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
   const float4* wt = P.pwt;
   // FP64 face sums owned by this lane: E/W entry `lane`; N and S entries `lane` (lane < 16)
   double sx = 0.0, sn = 0.0, ss = 0.0;
+  double hx1 = 0.0, hyn = 0.0, hys = 0.0, hx2 = 0.0;  // Shakhov moments owned by this lane
 
   // this warp's row pairs: [p0, p1) of the v >= 0 half (pairs pn .. pa - 1) and [q0, q1) of
   // the v < 0 half (pairs 0 .. pn - 1); the v = 0 row's share of the v < 0 half goes with the
@@ -332,6 +368,14 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
                                     yb0, yb1, lane);
       sside += (double)ry;
       sx += (double)rx;
+      if constexpr (SHK) {
+        float r1, r2;
+        chunk_heat_sums(u, wu, sy, a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3,
+                        yb0, yb1, lane, r1, r2);
+        if (lane >= 20 && lane < 30) (sy > 0.f ? hyn : hys) += (double)r1;
+        else hx1 += (double)r1;
+        hx2 += (double)r2;
+      }
     };
     // the v >= 0 half (pairs pn .. pa - 1), then the v < 0 half (pairs 0 .. pn - 1); the first
     // v >= 0 pair holds the v = 0 row (if any) as its first row
@@ -390,6 +434,17 @@ __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __res
       out[kSumN + lane] = sn;
       out[kSumS + lane] = ss;
     }
+    if constexpr (SHK) {
+      double* ho = P.hs + (size_t)cell * kNHeat;
+      if (lane < 20) ho[kHeatE + lane] = hx1;  // E then W
+      else if (lane < 30) {
+        ho[kHeatN + lane - 20] = hyn;
+        ho[kHeatS + lane - 20] = hys;
+      } else {
+        ho[kHeatC + lane - 30] = hx1;
+      }
+      if (lane < 11) ho[kHeatC + 2 + lane] = hx2;
+    }
     return;
   }
   __syncthreads();  // red[] of the previous virtual block has been read
@@ -413,6 +468,10 @@ __device__ __noinline__ void sums_body_split(const Params& P, const float4* __re
                                             double* __restrict__ sums, int bx, int split,
                                             double (*red)[kNSum]) {
   sums_body_p<true>(P, f, sums, bx, split, red);
+}
+__device__ __noinline__ void sums_body_shk(const Params& P, const float4* __restrict__ f,
+                                          double* __restrict__ sums, int bx) {
+  sums_body_p<false, true>(P, f, sums, bx, 1, nullptr);
 }
 
 // -------------------------------------------------------------------------------------
@@ -544,15 +603,41 @@ __device__ __forceinline__ P4 wall_p(const FaceRecF* R, const PairLane& L) {
   return X;
 }
 
+// Shakhov factor S_h of one g for both velocities (s: 8 coefficients on the monomials
+// 1, u, v, u^2, uv, v^2, u r2, v r2) and its linear b term Lb (l: on 1, u, v).
+__device__ __forceinline__ float2 shk_sh(const float4 a, const float4 b, const PairLane& L) {
+  float2 r = f2(fmaf(a.w, L.uu, fmaf(a.y, L.u, a.x)));
+  r = fma2(f2(a.z), L.v, r);
+  r = fma2(f2(b.x), L.uv, r);
+  r = fma2(f2(b.y), L.vv, r);
+  r = fma2(f2(b.z), L.ur2, r);
+  return fma2(f2(b.w), L.vr2, r);
+}
+
 // Eq. 3 increment of one cell (CellRecF); Xi / Xo: inflow / outflow flux in x and y.
+// SHK: the Shakhov model (CS: the cell's Shakhov factors, global memory): g+ in place of g.
+template <bool SHK = false>
 __device__ __forceinline__ P4 collide_p(const CellRecF* C, const PairLane& L, const P4& e,
-                                        const P4& Xix, const P4& Xox, const P4& Xiy, const P4& Xoy) {
+                                        const P4& Xix, const P4& Xox, const P4& Xiy, const P4& Xoy,
+                                        const CellShkF* CS = nullptr) {
   const float4 en = ld4(&C->dEn[0]);
   const float4 e1 = ld4(&C->dE1[0]);
   const float4 A = ld4(&C->A1);    // A1 An db1 dbn
   const float4 B = ld4(&C->nBs);   // -Bs irx iry inv
   // g - g_ref for g^n and g^{n+1}, from the exponents relative to g_ref's
-  const float2 Dn = mul2(L.grh, ex2m1_p(epoly_p(en, L))), D1 = mul2(L.grh, ex2m1_p(epoly_p(e1, L)));
+  float2 Dn = mul2(L.grh, ex2m1_p(epoly_p(en, L))), D1 = mul2(L.grh, ex2m1_p(epoly_p(e1, L)));
+  // Shakhov: D -> D + g_h S_h, and the b terms gain g_h Lb
+  float2 Xbn = f2(0.f), Xb1 = f2(0.f);
+  if constexpr (SHK) {
+    const float4* cs = reinterpret_cast<const float4*>(CS);
+    const float4 sn0 = __ldg(cs), sn1 = __ldg(cs + 1), s10 = __ldg(cs + 2), s11 = __ldg(cs + 3);
+    const float4 lbn = __ldg(cs + 4), lb1 = __ldg(cs + 5);
+    const float2 Gn = add2(Dn, L.grh), G1 = add2(D1, L.grh);
+    Dn = fma2(Gn, shk_sh(sn0, sn1, L), Dn);
+    D1 = fma2(G1, shk_sh(s10, s11, L), D1);
+    Xbn = mul2(Gn, fma2(f2(lbn.z), L.v, f2(fmaf(lbn.y, L.u, lbn.x))));
+    Xb1 = mul2(G1, fma2(f2(lb1.z), L.v, f2(fmaf(lb1.y, L.u, lb1.x))));
+  }
   const float2 r = fma2(L.v, f2(B.z), f2(L.u * B.y));
   const float aui = L.au * B.w;
   const float2 avi = mul2(L.av, f2(B.w));
@@ -560,9 +645,15 @@ __device__ __forceinline__ P4 collide_p(const CellRecF* C, const PairLane& L, co
   float2 db = fma2(f2(aui), sub2(Xix.b, Xox.b), mul2(avi, sub2(Xiy.b, Xoy.b)));
   // b g - g_ref,b = b D + (b - b_ref) g_ref,h
   dh = fma2(f2(A.x), D1, fma2(f2(A.y), Dn, fma2(r, L.grh, fma2(f2(B.x), e.h, dh))));
-  db = fma2(f2(A.x), fma2(f2(A.z + L.bref), D1, mul2(f2(A.z), L.grh)),
-            fma2(f2(A.y), fma2(f2(A.w + L.bref), Dn, mul2(f2(A.w), L.grh)),
-                 fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
+  if constexpr (!SHK) {
+    db = fma2(f2(A.x), fma2(f2(A.z + L.bref), D1, mul2(f2(A.z), L.grh)),
+              fma2(f2(A.y), fma2(f2(A.w + L.bref), Dn, mul2(f2(A.w), L.grh)),
+                   fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
+  } else {
+    db = fma2(f2(A.x), fma2(f2(A.z + L.bref), D1, fma2(f2(A.z), L.grh, Xb1)),
+              fma2(f2(A.y), fma2(f2(A.w + L.bref), Dn, fma2(f2(A.w), L.grh, Xbn)),
+                   fma2(r, L.grb, fma2(f2(B.x), e.b, db))));
+  }
   return {add2(e.h, dh), add2(e.b, db)};
 }
 
@@ -574,7 +665,7 @@ __device__ __forceinline__ P4 slope_d(const PairLane& L, const P4& rx, const P4&
 // initialised by the caller); nrec: record stages this warp has issued on them so far (the
 // phases of the mbarriers follow from it).  Returns false if a wait for records gave up
 // (err then has bit 1 set).
-template <int W, bool FULL>
+template <int W, bool FULL, bool SHK = false>
 __device__ __forceinline__ bool strip_body_p(const Params& P, const float4* __restrict__ f,
                                              float4* __restrict__ fo, const FaceRecF* __restrict__ fxr,
                                              const FaceRecF* __restrict__ fyr,
@@ -766,7 +857,8 @@ __device__ __forceinline__ bool strip_body_p(const Params& P, const float4* __re
         const P4 d = slope_d(L, rx, ry);
         const P4 Xox = face_p(RXi + su * (t + 1), xside, L, add4(c0, rx), d);
         const P4 Xoy = face_p(RY + cl(t), yside, L, add4(c0, ry), d);
-        const P4 o = collide_p(CC + cl(t), L, c0, Xix, Xox, Xiy[t], Xoy);
+        const P4 o = collide_p<SHK>(CC + cl(t), L, c0, Xix, Xox, Xiy[t], Xoy,
+                                    SHK ? P.cshk + (long)(jfirst + sv * st) * nx + i0 + cl(t) : nullptr);
         if (act) stp(pw + col(t), o);
         Xix = Xox;
         Xiy[t] = Xoy;

@@ -19,11 +19,21 @@ constexpr int kWarpsPerBlock = 4;    // warp-per-cell kernels: 4 cells per 128-t
 enum { kSumE = 0, kSumW = 16, kSumN = 32, kSumS = 48, kNSum = 64 };
 enum { kOffW0 = 0, kOffSt = 4, kOffSf = 8, kOffSs = 12 };
 constexpr int kSumsTotals = 14;    // per-thread totals of the sums kernel (shared memory)
+constexpr int kHeatTotals = 4;     // and the four more the Shakhov heat-flux sums need
 // dynamic shared memory of the sums kernel: per-warp sums, per-thread totals
 template <typename T>
 __host__ __device__ constexpr size_t sums_smem_bytes() {
-  return (kWarpsPerBlock * kNSum + kSumsTotals * 128) * sizeof(T);
+  return (kWarpsPerBlock * kNSum + (kSumsTotals + kHeatTotals) * 128) * sizeof(T) +
+         kWarpsPerBlock * 56 * sizeof(double);  // per-warp Shakhov heat-flux sums (kNHeat)
 }
+
+// Shakhov model: per-cell raw velocity moments the heat fluxes need (FP64, kNHeat per cell),
+// in the natural frame (u, v).  Per side E (u > 0), W (u < 0), N (v > 0), S (v < 0), of the
+// side's face values (f +/- the half slope), weighted by H(u_n) like the other face sums:
+//   M20 M11 M02 M30 M21 M12 M03 (h, M_ab = sum w u^a v^b h) and B00 B10 B01 (b);
+// then of the cell values over every velocity: M00 M10 M01 M20 M11 M02 M30 M21 M12 M03 B00
+// B10 B01.  (M00, M10, M01 and M20 + M02 + B00 of the faces are in the kNSum sums.)
+enum { kHeatE = 0, kHeatW = 10, kHeatN = 20, kHeatS = 30, kHeatC = 40, kNHeat = 56 };
 
 // What the update kernel needs about one face (written by the face kernel).
 // Micro flux in the face frame (u_n normal, u_t tangential), per component c (h, b):
@@ -48,6 +58,10 @@ struct CellRec {
   double Gn, Un, Vn, lamn, bn;   // g^n_h = Gn exp(-lamn (u-Un)^2) exp(-lamn (v-Vn)^2), g_b = bn g_h
   double G1, U1, V1, lam1, b1;   // same for g^{n+1}
   double cf, cgn, cg1, inv;
+  // Shakhov model: the heat flux of f^n (qx, qy) and alpha = (1 - Pr) 4 lam^2 / ((K+4) rho)
+  // of W^n and W^{n+1}; the Shakhov factors are S_h = alpha (c.q) (2 lam |c|^2 - 4) and
+  // S_b = alpha (c.q) (K/(2 lam)) (2 lam |c|^2 - 2): g+_h = g_h (1 + S_h), g+_b = g_h (b + S_b)
+  double qx, qy, an, a1;
 };
 
 // FP32 records of the FP32 form's update kernel (written by the FP64 face and cell
@@ -90,6 +104,16 @@ struct __align__(16) CellRecF {
   float nBs, irx, iry, inv; // -inv (cg1 + cgn), inv (Mt4_W - Mt4_E)/dx, inv (Mt4_S - Mt4_N)/dy
 };
 
+// FP32-f form, Shakhov model: per cell, the Shakhov factors of g^n and g^{n+1} in the
+// global velocity frame (FP32, from FP64 coefficients): S_h on the monomials
+// (1, u, v, u^2, uv, v^2, u r2, v r2) (sn, s1), and Lb = 2 b alpha (c.q) on (1, u, v) (ln, l1),
+// so that g+_h - g_ref,h = D + g_h S_h and g+_b - g_ref,b = b D + (b - b_ref) g_ref,h +
+// g_h (b S_h + Lb), D = g_h - g_ref,h.
+struct __align__(16) CellShkF {
+  float sn[8], s1[8];
+  float ln[4], l1[4];
+};
+
 // DF64 form: f of one velocity, (h, b) as double-FP32 pairs (h = hh + hl, b = bh + bl)
 struct __align__(16) DF4 {
   float hh, hl, bh, bl;
@@ -107,6 +131,16 @@ struct __align__(16) CellRecD {
 
 struct Params {
   int nx, ny, nu, nv, nq, K;
+  // Shakhov model (pr != 1): shk = 1, hs the heat-flux moment sums (kNHeat per cell, the
+  // cells of the sums buffer), shk_c = (1 - Pr) 4 / (K + 4) (alpha = shk_c lam^2 / rho)
+  int shk;
+  double pr, shk_c;
+  double* hs;
+  CellShkF* cshk;         // FP32-f form: the Shakhov cell records (written by the cells kernel)
+  double refheat[5][10];  // FP32-f form: the kNHeat moments of g_ref per side and of the cell
+                          // (zero in the FP64 form): E, W, N, S (10 each), cell (first 10
+                          // of its 13 in refheat[4], B-moments in refheatC)
+  double refheatC[3];
   int ex;                 // f row length in cells: nx + 4 (two-cell ghost ring)
   int wx;                 // W row length in cells: nx + 2 (one-cell ghost ring)
   double dx, dy, dt;

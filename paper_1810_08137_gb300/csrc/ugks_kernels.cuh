@@ -280,6 +280,46 @@ __device__ __forceinline__ void utab(const Params& P, int k, double& u, double& 
 
 // slopes: null, or [(nx+2)(ny+2) cells (W indexing)][nq][2] of (r_x,h r_x,b), (r_y,h r_y,b),
 // written for every cell whose sums are formed (the update kernel then reads them)
+// Sum over the warp (every lane gets it), FP64.
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+// Shakhov heat-flux moments of one side's face values, from the lane's (u = ud) v-weighted
+// sums F_b = sum_v w_v v^b (h face values), b = 0..3, and Fb_b (b face values), b = 0, 1,
+// with the lane weight wgt (w_u, times H(u_n) on the x sides): adds the warp's
+// M20 M11 M02 M30 M21 M12 M03 B00 B10 B01 to o[0..9] (lane 0 writes).
+__device__ __forceinline__ void heat_side(double wgt, double ud, double F0, double F1, double F2,
+                                          double F3, double Fb0, double Fb1, double* o) {
+  const double u2 = ud * ud;
+  const double v[10] = {wgt * u2 * F0, wgt * ud * F1, wgt * F2, wgt * u2 * ud * F0, wgt * u2 * F1,
+                        wgt * ud * F2, wgt * F3, wgt * Fb0, wgt * ud * Fb0, wgt * Fb1};
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 10; t++) {
+    const double r = warp_sum_d(v[t]);
+    if (lane == 0) o[t] += r;
+  }
+  __syncwarp();
+}
+// The same for the cell values over every velocity: M00 M10 M01 M20 M11 M02 M30 M21 M12 M03
+// B00 B10 B01 into o[0..12].
+__device__ __forceinline__ void heat_cell(double wgt, double ud, double C0, double C1, double C2,
+                                          double C3, double Cb0, double Cb1, double* o) {
+  const double u2 = ud * ud;
+  const double v[13] = {wgt * C0,      wgt * ud * C0, wgt * C1,      wgt * u2 * C0, wgt * ud * C1,
+                        wgt * C2,      wgt * u2 * ud * C0, wgt * u2 * C1, wgt * ud * C2, wgt * C3,
+                        wgt * Cb0,     wgt * ud * Cb0, wgt * Cb1};
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 13; t++) {
+    const double r = warp_sum_d(v[t]);
+    if (lane == 0) o[t] += r;
+  }
+  __syncwarp();
+}
+
 template <typename T, typename T2>
 __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict__ f,
                                           T* __restrict__ sums, unsigned char* smraw, int bx,
@@ -287,9 +327,14 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
   const int nv = P.nv, nu = P.nu, nq = P.nq;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wsum = reinterpret_cast<T*>(smraw) + warp * kNSum;
-  // per-thread totals over both halves, [14][128] (touched twice per u chunk)
+  // per-thread totals over both halves, [14 + 4][128] (touched twice per u chunk)
   T* tot = reinterpret_cast<T*>(smraw + kWarpsPerBlock * kNSum * sizeof(T)) + tid;
+  // Shakhov model: this warp's heat-flux moment sums (kNHeat, FP64)
+  double* hsum = reinterpret_cast<double*>(smraw + (kWarpsPerBlock * kNSum + (kSumsTotals + kHeatTotals) * 128) *
+                                                       sizeof(T)) + warp * kNHeat;
+  const bool heat = P.hs != nullptr;
   for (int t = lane; t < kNSum; t += 32) wsum[t] = T(0);
+  for (int t = lane; t < kNHeat; t += 32) hsum[t] = 0.0;
   __syncwarp();
 
   const int ncx = P.nx + 2;
@@ -328,9 +373,9 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     utab(P, kk, u, wu);
     if (!act) wu = T(0);
     const T cu = u * tdx;
-    // totals: tA0 tA1 tA2 tAb tR0 tR1 tR2 tRb tC0 tC1 tC2 tC3 tCb0 tCb1
+    // totals: tA0 tA1 tA2 tAb tR0 tR1 tR2 tRb tC0 tC1 tC2 tC3 tCb0 tCb1, then tA3 tAb1 tR3 tRb1
 #pragma unroll
-    for (int t = 0; t < kSumsTotals; t++) tot[t * 128] = T(0);
+    for (int t = 0; t < kSumsTotals + kHeatTotals; t++) tot[t * 128] = T(0);
     T a0, a1, a2, a3, ab0, ab1, x0, x1, x2, x3, xb0, xb1, y0, y1, y2, y3, y4, yb0, yb1, yb2;
     auto zero = [&]() {
       a0 = a1 = a2 = a3 = ab0 = ab1 = x0 = x1 = x2 = x3 = xb0 = xb1 = T(0);
@@ -414,9 +459,14 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
       const T Zb1 = cu * xb1 + tdy * yb2;
       finalize_y<T, T2>(u, wu, tdx, P0, P1, P2, P3, Pb0, Pb1, x0, x1, x2, xb0, Z1, Z2, Z3, Zb1, lane,
                         side);
-      const T h[kSumsTotals] = {a0, a1, a2, ab0, x0, x1, x2, xb0, y0, y1, y2, y3, yb0, yb1};
+      const T h[kSumsTotals + kHeatTotals] = {a0, a1, a2, ab0, x0, x1, x2, xb0, y0, y1, y2, y3, yb0, yb1,
+                                              a3, ab1, x3, xb1};
 #pragma unroll
-      for (int t = 0; t < kSumsTotals; t++) tot[t * 128] += h[t];
+      for (int t = 0; t < kSumsTotals + kHeatTotals; t++) tot[t * 128] += h[t];
+      if (heat) {  // Shakhov: raw moments of the half's y-side face values (kHeatN / kHeatS)
+        heat_side((double)wu, (double)u, (double)P0, (double)P1, (double)P2, (double)P3, (double)Pb0,
+                  (double)Pb1, hsum + (sy > T(0) ? kHeatN : kHeatS));
+      }
     };
     zero();
     rows(0, mneg);
@@ -463,11 +513,26 @@ __device__ __forceinline__ void sums_body(const Params& P, const T2* __restrict_
     }
     const T r = warp_reduce_scatter<32>(xv, lane);
     wsum[kSumE + lane] += r;  // lanes 0..15: E side, 16..31: W side
+    if (heat) {  // Shakhov: x-side face values and cell values (kHeatE, kHeatW, kHeatC)
+      const double tA3 = (double)tot[1792], tAb1 = (double)tot[1920], tR3 = (double)tot[2048];
+      const double tRb1 = (double)tot[2176];
+      const double hE_ = (double)(wu * hE), hW_ = (double)(wu * hW), ud = (double)u;
+      heat_side(hE_, ud, (double)(tA0 + tR0), (double)(tA1 + tR1), (double)(tA2 + tR2), tA3 + tR3,
+                (double)(tAb + tRb), tAb1 + tRb1, hsum + kHeatE);
+      heat_side(hW_, ud, (double)(tA0 - tR0), (double)(tA1 - tR1), (double)(tA2 - tR2), tA3 - tR3,
+                (double)(tAb - tRb), tAb1 - tRb1, hsum + kHeatW);
+      heat_cell((double)wu, ud, (double)tA0, (double)tA1, (double)tA2, tA3, (double)tAb, tAb1,
+                hsum + kHeatC);
+    }
   }
   __syncwarp();
   T* out = sums + (size_t)cell * kNSum;
   out[lane] = wsum[lane];
   out[lane + 32] = wsum[lane + 32];
+  if (heat) {
+    double* ho = P.hs + (size_t)cell * kNHeat;
+    for (int t = lane; t < kNHeat; t += 32) ho[t] = hsum[t];
+  }
 }
 template <typename T, typename T2>
 __global__ void __launch_bounds__(128) k_sums(Params P, const T2* __restrict__ f,
@@ -711,12 +776,53 @@ struct FaceCoreT {
   double rho, U, V, lam, X2, X4;
   double Mt[5];
   T aL[4], aR[4], b[4], A[4];
+  // Shakhov model: S_h and S_b on the face-frame monomials un^a ut^b (a + b <= 3), and the
+  // coefficients of alpha L = alpha (c.q) (for the FP32 record's b terms)
+  bool shk;
+  double sh[4][4], sb[4][4], aLq[3];
 };
+
+// Heat flux (qn, qt) about (U, V) from the raw moments of a distribution (face frame):
+// M[a][b] = sum w un^a ut^b h for a + b <= 3, B00 B10 B01 = sum w (1, un, ut) b;
+// q = 1/2 sum w c (|c|^2 h + b), c = (un - U, ut - V).
+__device__ __forceinline__ void heat_flux_of(const double (&M)[4][4], double B00, double B10, double B01,
+                                             double U, double V, double* q) {
+  const double cn3 = M[3][0] - 3.0 * U * M[2][0] + 3.0 * U * U * M[1][0] - U * U * U * M[0][0];
+  const double cnt2 = M[1][2] - 2.0 * V * M[1][1] + V * V * M[1][0] - U * M[0][2] + 2.0 * U * V * M[0][1] -
+                      U * V * V * M[0][0];
+  const double ct3 = M[0][3] - 3.0 * V * M[0][2] + 3.0 * V * V * M[0][1] - V * V * V * M[0][0];
+  const double ctn2 = M[2][1] - 2.0 * U * M[1][1] + U * U * M[0][1] - V * M[2][0] + 2.0 * U * V * M[1][0] -
+                      U * U * V * M[0][0];
+  q[0] = 0.5 * (cn3 + cnt2 + (B10 - U * B00));
+  q[1] = 0.5 * (ct3 + ctn2 + (B01 - V * B00));
+}
+
+// Shakhov factors on monomials of the face frame: alpha L R with L = qn cn + qt ct and
+// R = 2 lam (cn^2 + ct^2) + r0 (r0 = -4 for S_h, -2 for S_b / X2), cn = un - U, ct = ut - V.
+__device__ __forceinline__ void shakhov_poly(double alpha, double U, double V, double lam, const double* q,
+                                             double r0, double (&p)[4][4]) {
+  const double l[3] = {-(q[0] * U + q[1] * V), q[0], q[1]};  // 1, un, ut
+  double r[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};        // r[a][b]: un^a ut^b
+  r[0][0] = 2.0 * lam * (U * U + V * V) + r0;
+  r[1][0] = -4.0 * lam * U;
+  r[0][1] = -4.0 * lam * V;
+  r[2][0] = 2.0 * lam;
+  r[0][2] = 2.0 * lam;
+  for (int a = 0; a < 4; a++)
+    for (int b = 0; b < 4; b++) p[a][b] = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; a + b < 3; b++) {
+      p[a][b] += alpha * l[0] * r[a][b];
+      p[a + 1][b] += alpha * l[1] * r[a][b];
+      p[a][b + 1] += alpha * l[2] * r[a][b];
+    }
+}
 using FaceCore = FaceCoreT<double>;
 template <typename T>
 __device__ __forceinline__ void face_core(const Params& P, const double* W0, const double* St,
                                           const double* Sf, const double* Ss, const double* WL,
-                                          const double* WR, double tdelta, double* F, FaceCoreT<T>& c) {
+                                          const double* WR, double tdelta, double* F, FaceCoreT<T>& c,
+                                          const double* qsh = nullptr) {
   const int K = P.K;
   // S2: interface primitive variables and Maxwellian moments
   const double rho = W0[0], irho = rcp_nr(rho), U = W0[1] * irho, V = W0[2] * irho;
@@ -792,14 +898,38 @@ __device__ __forceinline__ void face_core(const Params& P, const double* W0, con
   c.lam = lam;
   c.X2 = X2;
   c.X4 = X4;
+  // Shakhov model: the zeroth-order equilibrium term g0 (1 + S) of the integral solution
+  // (weight Mt1): its part of the macroscopic flux from analytic full-range moments (FP64)
+  c.shk = qsh != nullptr;
+  if (c.shk) {
+    const double alpha = P.shk_c * lam * lam * irho;
+    shakhov_poly(alpha, U, V, lam, qsh, -4.0, c.sh);
+    shakhov_poly(alpha * X2, U, V, lam, qsh, -2.0, c.sb);
+    c.aLq[0] = -alpha * (qsh[0] * U + qsh[1] * V);
+    c.aLq[1] = alpha * qsh[0];
+    c.aLq[2] = alpha * qsh[1];
+    double Mu[7], Mv[7];
+    gauss_moments7_full<double>(U, h, Mu);
+    gauss_moments7_full<double>(V, h, Mv);
+    double e[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; a + b < 4; b++) {
+        const double ph = c.sh[a][b], pb = c.sb[a][b];
+        e[0] += ph * Mu[a + 1] * Mv[b];
+        e[1] += ph * Mu[a + 2] * Mv[b];
+        e[2] += ph * Mu[a + 1] * Mv[b + 1];
+        e[3] += 0.5 * (ph * (Mu[a + 3] * Mv[b] + Mu[a + 1] * Mv[b + 2]) + pb * Mu[a + 1] * Mv[b]);
+      }
+    for (int k = 0; k < 4; k++) F[k] += rho * Mt[0] * e[k];
+  }
 }
 
 // FP64 form: the interface (face_core) and its FP64 micro-flux record.
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
                           const double* Ss, const double* WL, const double* WR, double tdelta,
-                          bool isx, double* F, FaceRec& R) {
+                          bool isx, double* F, FaceRec& R, const double* qsh = nullptr) {
   FaceCore c;
-  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
+  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c, qsh);
   const double* Mt = c.Mt;
   const double X2 = c.X2, X4 = c.X4;
   R.G = c.rho * c.lam / kPi;
@@ -822,6 +952,20 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
     shape_b(c.b, X2, X4, pb);
     shape_b(c.A, X2, X4, pA);
     qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
+    if (c.shk) {  // Shakhov: Mt1 g0 S on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2)
+      for (int comp = 0; comp < 2; comp++) {
+        const double(&p)[4][4] = comp == 0 ? c.sh : c.sb;
+        double* q = R.Q[sd][comp];
+        q[0] += Mt[0] * p[0][0];
+        q[1] += Mt[0] * p[1][0];
+        q[2] += Mt[0] * p[0][1];
+        q[3] += Mt[0] * p[2][0];
+        q[4] += Mt[0] * p[1][1];
+        q[5] += Mt[0] * p[0][2];
+        q[6] += Mt[0] * p[3][0];  // = p[1][2]: the cubic part is (qn un + qt ut) 2 lam r2
+        q[7] += Mt[0] * p[0][3];  // = p[2][1]
+      }
+    }
   }
 }
 
@@ -832,9 +976,9 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
 __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St,
                                               const double* Sf, const double* Ss, const double* WL,
                                               const double* WR, double tdelta, bool isx, double* F,
-                                              double& Mt4, FaceRecF& RF) {
+                                              double& Mt4, FaceRecF& RF, const double* qsh = nullptr) {
   FaceCoreT<dd> c;
-  face_core<dd>(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c);
+  face_core<dd>(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c, qsh);
   const double* Mt = c.Mt;
   Mt4 = Mt[3];
   const float fM1 = (float)Mt[0], fM2 = (float)Mt[1], fM3 = (float)Mt[2];
@@ -875,6 +1019,17 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
     Qf[5] = fmaf(fM3, pA[3], fM2 * pb[2]);
     Qf[6] = fM2 * pa[3];
     Qf[7] = fM2 * pb[3];
+    if (c.shk) {  // Shakhov: Mt1 g0 S_h on the face-frame monomials (FP64 sums, then FP32)
+      const double* M = Mt;
+      Qf[0] += (float)(M[0] * c.sh[0][0]);
+      Qf[1] += (float)(M[0] * c.sh[1][0]);
+      Qf[2] += (float)(M[0] * c.sh[0][1]);
+      Qf[3] += (float)(M[0] * c.sh[2][0]);
+      Qf[4] += (float)(M[0] * c.sh[1][1]);
+      Qf[5] += (float)(M[0] * c.sh[0][2]);
+      Qf[6] += (float)(M[0] * c.sh[3][0]);
+      Qf[7] += (float)(M[0] * c.sh[0][3]);
+    }
 #pragma unroll
     for (int k = 0; k < 8; k++) RF.Q[sd][k] = fG * (isx ? Qf[k] : Qf[py[k]]);
     // b polynomial: P_b(a) = X2 P_h(a) + a4 (X4 - X2^2)/2, so Q_b = X2 Q_h + kap (Mt3 A4 +
@@ -884,6 +1039,12 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
     RF.K[sd][1] = isx ? kn : kt;
     RF.K[sd][2] = isx ? kt : kn;
     RF.K[sd][3] = fX2;
+    if (c.shk) {  // Shakhov: S_b = X2 S_h + 2 X2 alpha L, the second part linear in (un, ut)
+      const double m = 2.0 * Mt[0] * c.X2 * (c.rho * c.lam / kPi);
+      RF.K[sd][0] += (float)(m * c.aLq[0]);
+      RF.K[sd][1] += (float)(m * (isx ? c.aLq[1] : c.aLq[2]));
+      RF.K[sd][2] += (float)(m * (isx ? c.aLq[2] : c.aLq[1]));
+    }
   }
   constexpr double kLog2e = 1.4426950408889634;
   const double lam = c.lam, Ux = isx ? c.U : c.V, Vy = isx ? c.V : c.U;
@@ -1005,10 +1166,38 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
       WL[c] = W[s * nwe + cL];
       WR[c] = W[s * nwe + cR];
     }
+    // Shakhov model: heat flux of the interface values about the interface velocity, from
+    // the raw moments of both sides' face values (face frame), plus those of g_ref (FP32-f)
+    double qsh[2];
+    const double* qp = nullptr;
+    if (P.shk) {
+      const int hL = isx ? kHeatE : kHeatN, hR = isx ? kHeatW : kHeatS;
+      const double* a = P.hs + (size_t)cL * kNHeat + hL;
+      const double* b = P.hs + (size_t)cR * kNHeat + hR;
+      const double* ra = P.refheat[hL / 10];
+      const double* rb = P.refheat[hR / 10];
+      double n[10];  // natural frame: M20 M11 M02 M30 M21 M12 M03 B00 B10 B01
+      for (int t = 0; t < 10; t++) n[t] = (a[t] + b[t]) + (ra[t] + rb[t]);
+      double M[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+      M[0][0] = W0[0];
+      M[1][0] = W0[1];
+      M[0][1] = W0[2];
+      // face frame: (un, ut) = (u, v) on x faces, (v, u) on y faces
+      M[2][0] = isx ? n[0] : n[2];
+      M[1][1] = n[1];
+      M[0][2] = isx ? n[2] : n[0];
+      M[3][0] = isx ? n[3] : n[6];
+      M[2][1] = isx ? n[4] : n[5];
+      M[1][2] = isx ? n[5] : n[4];
+      M[0][3] = isx ? n[6] : n[3];
+      const double B00 = n[7], B10 = isx ? n[8] : n[9], B01 = isx ? n[9] : n[8];
+      heat_flux_of(M, B00, B10, B01, W0[1] / W0[0], W0[2] / W0[0], qsh);
+      qp = qsh;
+    }
     if constexpr (f32)
-      face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF);
+      face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF, qp);
     else
-      face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R);
+      face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, qp);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = (c == 1 || c == 2) && !isx ? Fr[3 - c] : Fr[c];
   }
@@ -1092,6 +1281,24 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
     }
     R.cf = 1.0 - R.cgn;
     R.inv = rcp_nr(1.0 + R.cg1);
+    // Shakhov model: heat flux of f^n about (Un, Vn) from the cell's raw moments (plus those
+    // of g_ref in the FP32-f form), and alpha of W^n and W^{n+1}
+    R.qx = R.qy = R.an = R.a1 = 0.0;
+    if (P.shk) {
+      const double* hc = P.hs + (size_t)w * kNHeat + kHeatC;
+      const double* rc = P.refheat[4];
+      double M[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+      M[0][0] = hc[0] + rc[0]; M[1][0] = hc[1] + rc[1]; M[0][1] = hc[2] + rc[2];
+      M[2][0] = hc[3] + rc[3]; M[1][1] = hc[4] + rc[4]; M[0][2] = hc[5] + rc[5];
+      M[3][0] = hc[6] + rc[6]; M[2][1] = hc[7] + rc[7]; M[1][2] = hc[8] + rc[8];
+      M[0][3] = hc[9] + rc[9];
+      double q[2];
+      heat_flux_of(M, hc[10] + P.refheatC[0], hc[11] + P.refheatC[1], hc[12] + P.refheatC[2], Un, Vn, q);
+      R.qx = q[0];
+      R.qy = q[1];
+      R.an = P.shk_c * ln * ln * irn;
+      R.a1 = P.shk_c * l1 * l1 * ir1;
+    }
     if (crf) {
       const int nfx = (nx + 1) * P.ny;
       constexpr double kLog2e = 1.4426950408889634;
@@ -1123,6 +1330,26 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       F.iry = (float)(R.inv * refy);
       F.inv = (float)R.inv;
       crf[c] = F;
+      if (P.shk) {  // Shakhov factors of g^n and g^{n+1}, global frame
+        CellShkF S;
+        double p[4][4];
+        const double q[2] = {R.qx, R.qy};
+        for (int g = 0; g < 2; g++) {
+          const double al = g == 0 ? R.an : R.a1, Ug = g == 0 ? Un : U1, Vg = g == 0 ? Vn : V1;
+          const double lg = g == 0 ? ln : l1, bg = g == 0 ? R.bn : R.b1;
+          shakhov_poly(al, Ug, Vg, lg, q, -4.0, p);
+          float* sg = g == 0 ? S.sn : S.s1;
+          float* lb = g == 0 ? S.ln : S.l1;
+          sg[0] = (float)p[0][0]; sg[1] = (float)p[1][0]; sg[2] = (float)p[0][1]; sg[3] = (float)p[2][0];
+          sg[4] = (float)p[1][1]; sg[5] = (float)p[0][2]; sg[6] = (float)p[3][0]; sg[7] = (float)p[0][3];
+          const double m = 2.0 * bg * al;
+          lb[0] = (float)(-m * (q[0] * Ug + q[1] * Vg));
+          lb[1] = (float)(m * q[0]);
+          lb[2] = (float)(m * q[1]);
+          lb[3] = 0.f;
+        }
+        P.cshk[c] = S;
+      }
     } else if (crd) {
       CellRecD D;
       D.Gn = split_df(R.Gn); D.Un = split_df(R.Un); D.Vn = split_df(R.Vn);
@@ -1630,8 +1857,23 @@ __global__ void __launch_bounds__(128) k_cell_update(Params P, const T2* __restr
       T flh = fxu * (XW.x - XE.x) + fyv * (XS.x - XN.x);
       T flb = fxu * (XW.y - XE.y) + fyv * (XS.y - XN.y);
       const T gnh = gun * ev[m], g1h = gu1 * ev[nv + m];
-      const T dh = inv * (flh + cg1 * (g1h - c.x) + cgn * (gnh - c.x));
-      const T db = inv * (flb + (cg1b * g1h - cg1 * c.y) + (cgnb * gnh - cgn * c.y));
+      T dh, db;
+      if (!P.shk) {
+        dh = inv * (flh + cg1 * (g1h - c.x) + cgn * (gnh - c.x));
+        db = inv * (flb + (cg1b * g1h - cg1 * c.y) + (cgnb * gnh - cgn * c.y));
+      } else {  // Shakhov: g+_h = g_h (1 + S_h), g+_b = g_h (b + S_b), heat flux of f^n
+        const double vd = P.v[m];
+        double cu = ud - C.Un, cv = vd - C.Vn;
+        double cq = cu * C.qx + cv * C.qy, c2 = 2.0 * C.lamn * (cu * cu + cv * cv);
+        const T shn = (T)(C.an * cq * (c2 - 4.0)), sbn = (T)(C.an * cq * C.bn * (c2 - 2.0));
+        cu = ud - C.U1; cv = vd - C.V1;
+        cq = cu * C.qx + cv * C.qy; c2 = 2.0 * C.lam1 * (cu * cu + cv * cv);
+        const T sh1 = (T)(C.a1 * cq * (c2 - 4.0)), sb1 = (T)(C.a1 * cq * C.b1 * (c2 - 2.0));
+        const T gpnh = gnh + gnh * shn, gp1h = g1h + g1h * sh1;
+        const T gpnb = gnh * ((T)C.bn + sbn), gp1b = g1h * ((T)C.b1 + sb1);
+        dh = inv * (flh + cg1 * (gp1h - c.x) + cgn * (gpnh - c.x));
+        db = inv * (flb + cg1 * (gp1b - c.y) + cgn * (gpnb - c.y));
+      }
       T2 o;
       o.x = c.x + dh;
       o.y = c.y + db;

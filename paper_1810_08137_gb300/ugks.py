@@ -49,7 +49,7 @@ class _Config(C.Structure):
                 ("omega", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
                 ("dt", C.c_double), ("bc", _BC * 4), ("precision", C.c_int),
                 ("ref_rho", C.c_double), ("ref_U", C.c_double), ("ref_V", C.c_double),
-                ("ref_T", C.c_double)]
+                ("ref_T", C.c_double), ("pr", C.c_double)]
 
 
 _lib = None
@@ -134,6 +134,7 @@ def to_c_config(cfg, precision: int = FP64) -> _Config:
     c.precision = int(precision)
     ref = getattr(cfg, "ref", None) or (0.0, 0.0, 0.0, 0.0)
     c.ref_rho, c.ref_U, c.ref_V, c.ref_T = (float(x) for x in ref)
+    c.pr = float(getattr(cfg, "pr", 1.0))
     return c
 
 
