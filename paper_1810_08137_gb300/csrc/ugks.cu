@@ -1481,9 +1481,12 @@ cudaError_t launch_batch(ugks_batch_ctx* b, cudaStream_t st) {
   kb_ghost_x<<<b->grid[0], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_ghost_y<<<b->grid[1], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_sums<<<b->grid[2], 128, kBatchSumsSmem, st>>>(b->d_slots, b->d_work);
+  kb_sums_shk<<<b->grid[2], 128, 0, st>>>(b->d_slots, b->d_work);  // Shakhov instances
   kb_faces<<<b->grid[3], 128, 0, st>>>(b->d_slots, b->d_work);
+  kb_faces_shk<<<b->grid[3], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_cells<<<b->grid[4], 128, 0, st>>>(b->d_slots, b->d_work);
   kb_strip<<<b->grid[5], 128, kStripSmem, st>>>(b->d_slots, b->d_work);
+  kb_strip_shk<<<b->grid[5], 128, kStripSmem, st>>>(b->d_slots, b->d_work);
   kb_flip<<<1, 256, 0, st>>>(b->d_slots, b->d_work);
   return cudaGetLastError();
 }
@@ -1545,6 +1548,9 @@ cudaError_t setup_single_f32(ugks_ctx* h) {
   if ((e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
       cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(kb_strip_shk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem)) !=
+      cudaSuccess)
+    return e;
   return upload_single_f32(h);
 }
 
@@ -1555,13 +1561,22 @@ cudaError_t launch_step_f32(ugks_ctx* h, cudaStream_t st) {
   if ((r = mark(h, 1)) != cudaSuccess) return r;
   kb_ghost_y<<<h->grid1[1], 128, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 2)) != cudaSuccess) return r;
-  kb_sums<<<h->grid1[2], 128, kBatchSumsSmem, st>>>(h->d_slot, h->d_work);
+  if (h->P.shk)  // the Shakhov model's sums, interface and walk
+    kb_sums_shk<<<h->grid1[2], 128, 0, st>>>(h->d_slot, h->d_work);
+  else
+    kb_sums<<<h->grid1[2], 128, kBatchSumsSmem, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 3)) != cudaSuccess) return r;
-  kb_faces<<<h->grid1[3], 128, 0, st>>>(h->d_slot, h->d_work);
+  if (h->P.shk)
+    kb_faces_shk<<<h->grid1[3], 128, 0, st>>>(h->d_slot, h->d_work);
+  else
+    kb_faces<<<h->grid1[3], 128, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 4)) != cudaSuccess) return r;
   kb_cells<<<h->grid1[4], 128, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 5)) != cudaSuccess) return r;
-  kb_strip<<<h->grid1[5], 128, kStripSmem, st>>>(h->d_slot, h->d_work);
+  if (h->P.shk)
+    kb_strip_shk<<<h->grid1[5], 128, kStripSmem, st>>>(h->d_slot, h->d_work);
+  else
+    kb_strip<<<h->grid1[5], 128, kStripSmem, st>>>(h->d_slot, h->d_work);
   kb_flip<<<1, 32, 0, st>>>(h->d_slot, h->d_work);
   if ((r = mark(h, 6)) != cudaSuccess) return r;
   if (h->profiling) h->events_used += UGKS_NKERNELS + 1;
@@ -1617,6 +1632,8 @@ ugks_status ugks_batch_create(int max_slots, size_t hbm_budget, void* cuda_strea
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSumsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kb_strip_shk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStripSmem);
   // persistent grids: resident blocks per SM x SMs
   const void* fns[kPhases] = {(const void*)kb_ghost_x, (const void*)kb_ghost_y, (const void*)kb_sums,
                               (const void*)kb_faces, (const void*)kb_cells, (const void*)kb_strip};

@@ -101,12 +101,23 @@ __device__ __noinline__ void sums_phase(const SlotDev* __restrict__ slots, const
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int a = find_instance(wk->start[2], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
-    if (S.P.shk)
-      sums_body_shk(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a]);
-    else if (S.sums_split > 1)
+    if (S.P.shk) continue;  // Shakhov instances: sums_phase_shk
+    if (S.sums_split > 1)
       sums_body_split(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], S.sums_split, red);
     else
       sums_body_p<false>(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], 1, red);
+  }
+}
+
+// The phases of the Shakhov model's instances (heat-flux sums, Shakhov interface, walk with
+// g+), over the same work table, skipping the BGK instances: functions and kernels of their
+// own, so that the BGK phases carry none of their code or registers.
+__device__ __noinline__ void sums_phase_shk(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+  const int total = wk->start[2][wk->n];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int a = find_instance(wk->start[2], wk->n, vb);
+    const SlotDev& S = slots[wk->slot[a]];
+    if (S.P.shk) sums_body_p<false, true>(S.P, S.f[S.cur], S.sums, vb - wk->start[2][a], 1, nullptr);
   }
 }
 
@@ -116,8 +127,21 @@ __device__ __noinline__ void faces_phase(const SlotDev* __restrict__ slots, cons
     const int a = find_instance(wk->start[3], wk->n, vb);
     const SlotDev& S = slots[wk->slot[a]];
     const int loc = vb - wk->start[3][a];
+    if (S.P.shk) continue;  // Shakhov instances: faces_phase_shk
     faces_body<kRecF32>(S.P, S.sums, S.W[S.cur], S.nwe, S.fxf, S.fyf, S.Fx, S.Fy, S.mt4,
                         loc * 128 + threadIdx.x);
+  }
+}
+
+__device__ __noinline__ void faces_phase_shk(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk) {
+  const int total = wk->start[3][wk->n];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int a = find_instance(wk->start[3], wk->n, vb);
+    const SlotDev& S = slots[wk->slot[a]];
+    if (!S.P.shk) continue;
+    const int loc = vb - wk->start[3][a];
+    faces_body<kRecF32, true>(S.P, S.sums, S.W[S.cur], S.nwe, S.fxf, S.fyf, S.Fx, S.Fy, S.mt4,
+                              loc * 128 + threadIdx.x);
   }
 }
 
@@ -156,17 +180,11 @@ __device__ __forceinline__ void walk_item(const SlotDev& S, int ns, int nt, int 
   ck = t * vt + c;
 }
 
-// The Shakhov model's walk (general strip width), compiled as a function of its own so that
-// it adds no registers to the BGK walk.
-__device__ __noinline__ bool strip_body_shk(const SlotDev& S, int c, int bx, int by, int ck, float4* wsm,
-                                           unsigned& nrec) {
-  return strip_body_p<kStripW, false, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
-                                            S.walk_rows, bx, by, ck, wsm, nrec, S.err);
-}
-
 // Update sweep: one warp per work item (strip, row tile, velocity chunk).
-__device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
-                                            float4* strip_sm) {
+// Returns the record stages this warp has issued on its mbarriers (the Shakhov walk of the
+// persistent step continues on them).
+__device__ __noinline__ unsigned strip_phase(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                             float4* strip_sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this warp's two mbarriers of the record ring (shared memory may have served another
   // phase before: initialise them here)
@@ -194,14 +212,48 @@ __device__ __noinline__ void strip_phase(const SlotDev* __restrict__ slots, cons
       // full strips (all but the last of a row when kStripW does not divide nx) with the
       // strip width known at compile time
       if (!ok) continue;  // a wait of this warp gave up: its walks are skipped (err is set)
-      if (S.P.shk)  // Shakhov model: the walk with g+ in the collision term
-        ok = strip_body_shk(S, c, bx, by, ck, wsm, nrec);
-      else if ((bx + 1) * kStripW <= S.P.nx)
+      if (S.P.shk) continue;  // Shakhov instances: strip_phase_shk
+      if ((bx + 1) * kStripW <= S.P.nx)
         ok = strip_body_p<kStripW, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
                                          S.walk_rows, bx, by, ck, wsm, nrec, S.err);
       else
         ok = strip_body_p<kStripW, false>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
                                           S.walk_rows, bx, by, ck, wsm, nrec, S.err);
+    }
+  }
+  return nrec;
+}
+
+// The walk of the Shakhov model's instances (g+ in the collision term; any strip width).
+// init: initialise this warp's mbarriers (a launch of its own); otherwise continue on the
+// ones strip_phase initialised in the same launch, after its nrec0 record stages.
+__device__ __noinline__ void strip_phase_shk(const SlotDev* __restrict__ slots, const BatchWork* __restrict__ wk,
+                                             float4* strip_sm, bool init, unsigned nrec0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* wsm = strip_sm + warp * kStripWarpF4;
+  const uint32_t bars = smem_addr(wsm + kFRing * kFPos * 32 + kRing * kStripChunks);
+  if (init && lane == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  unsigned nrec = nrec0;
+  bool ok = true;
+  const int total = wk->start[5][wk->n];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int a = find_instance(wk->start[5], wk->n, vb);
+    const SlotDev& S = slots[wk->slot[a]];
+    if (!S.P.shk) continue;
+    const int ns = (S.P.nx + kStripW - 1) / kStripW, nt = (S.P.ny + S.walk_rows - 1) / S.walk_rows;
+    const int it = (vb - wk->start[5][a]) * kWarpsPerBlock + warp;
+    const int nch = S.nchunk_neg + S.nchunk_pos;
+    if (it < ns * nt * nch && ok) {
+      const int c = S.cur;
+      int bx, by, ck;
+      walk_item(S, ns, nt, it, bx, by, ck);
+      ok = strip_body_p<kStripW, false, true>(S.P, S.f[c], S.f[c ^ 1], S.fxf, S.fyf, S.cellf, S.nchunk_neg,
+                                              S.walk_rows, bx, by, ck, wsm, nrec, S.err);
     }
   }
 }
@@ -241,6 +293,21 @@ __global__ void __launch_bounds__(128, 3) kb_strip(const SlotDev* __restrict__ s
                                                 const BatchWork* __restrict__ wk) {
   extern __shared__ __align__(16) float4 strip_sm[];  // kStripSmem bytes
   strip_phase(slots, wk, strip_sm);
+}
+
+// The Shakhov model's phases (instances with pr != 1; the others are skipped).
+__global__ void __launch_bounds__(128, 4) kb_sums_shk(const SlotDev* __restrict__ slots,
+                                                   const BatchWork* __restrict__ wk) {
+  sums_phase_shk(slots, wk);
+}
+__global__ void __launch_bounds__(128, 4) kb_faces_shk(const SlotDev* __restrict__ slots,
+                                                    const BatchWork* __restrict__ wk) {
+  faces_phase_shk(slots, wk);
+}
+__global__ void __launch_bounds__(128, 3) kb_strip_shk(const SlotDev* __restrict__ slots,
+                                                    const BatchWork* __restrict__ wk) {
+  extern __shared__ __align__(16) float4 strip_sm[];  // kStripSmem bytes
+  strip_phase_shk(slots, wk, strip_sm, true, 0u);
 }
 
 // After the step: every active instance swaps its buffers.
@@ -314,12 +381,15 @@ __global__ void __launch_bounds__(128, 3) kb_step(SlotDev* __restrict__ slots,
   ghost_y_phase(slots, wk, tab);
   if (!grid_sync(bar)) return;
   sums_phase(slots, wk, reinterpret_cast<double(*)[kNSum]>(step_sm));
+  sums_phase_shk(slots, wk);
   if (!grid_sync(bar)) return;
   faces_phase(slots, wk);
+  faces_phase_shk(slots, wk);
   if (!grid_sync(bar)) return;
   cells_phase(slots, wk, reinterpret_cast<double(*)[128]>(step_sm));
   if (!grid_sync(bar)) return;
-  strip_phase(slots, wk, step_sm);
+  const unsigned nrec = strip_phase(slots, wk, step_sm);
+  strip_phase_shk(slots, wk, step_sm, false, nrec);
   if (!grid_sync(bar)) return;
   if (blockIdx.x == 0)
     for (int a = threadIdx.x; a < wk->n; a += blockDim.x) slots[wk->slot[a]].cur ^= 1;

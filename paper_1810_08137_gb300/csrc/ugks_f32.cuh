@@ -279,7 +279,7 @@ __device__ __forceinline__ void chunk_heat_sums(float u, float wu, float sy, flo
 // SPLIT = false: one warp per cell (split 1), without the range and reduction code; the
 // caller inlines it and calls the split instance as a function of its own (sums_body_split),
 // so that the split path's registers do not weigh on the one-warp path.  SHK: the Shakhov
-// model's heat-flux moments too (P.hs; one warp per cell, called as sums_body_shk).
+// model's heat-flux moments too (P.hs; one warp per cell, in sums_phase_shk).
 template <bool SPLIT, bool SHK = false>
 __device__ __forceinline__ void sums_body_p(const Params& P, const float4* __restrict__ f,
                                             double* __restrict__ sums, int bx, int split_,
@@ -469,10 +469,7 @@ __device__ __noinline__ void sums_body_split(const Params& P, const float4* __re
                                             double (*red)[kNSum]) {
   sums_body_p<true>(P, f, sums, bx, split, red);
 }
-__device__ __noinline__ void sums_body_shk(const Params& P, const float4* __restrict__ f,
-                                          double* __restrict__ sums, int bx) {
-  sums_body_p<false, true>(P, f, sums, bx, 1, nullptr);
-}
+
 
 // -------------------------------------------------------------------------------------
 // S6 + S8 and Eq. 3 as an upwind strip walk.  For one velocity the micro flux through a face

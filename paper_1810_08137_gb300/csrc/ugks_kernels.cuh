@@ -1087,7 +1087,9 @@ __device__ __forceinline__ void face_rec_df(const FaceRec& R, FaceRecD& D) {
 }
 
 // rx, ry: the x- and y-face records of kind REC (FaceRec, FaceRecF or FaceRecD).
-template <int REC>
+// SHK: the Shakhov model's interface heat flux and terms (a separate instance, so that the
+// BGK interface carries none of their code).
+template <int REC, bool SHK = false>
 __device__ __forceinline__ void faces_body(const Params& P, const double* __restrict__ sums,
                                            const double* __restrict__ W, int nwe,
                                            void* __restrict__ rx, void* __restrict__ ry,
@@ -1170,7 +1172,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
     // the raw moments of both sides' face values (face frame), plus those of g_ref (FP32-f)
     double qsh[2];
     const double* qp = nullptr;
-    if (P.shk) {
+    if constexpr (SHK) {
       const int hL = isx ? kHeatE : kHeatN, hR = isx ? kHeatW : kHeatS;
       const double* a = P.hs + (size_t)cL * kNHeat + hL;
       const double* b = P.hs + (size_t)cR * kNHeat + hR;
@@ -1224,8 +1226,12 @@ template <int REC>
 __global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
                         int nwe, void* __restrict__ rx, void* __restrict__ ry,
                         double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ mt4) {
-  faces_body<REC>(P, sums, W, nwe, rx, ry, Fx, Fy, mt4, blockIdx.x * blockDim.x + threadIdx.x);
+  if (P.shk)
+    faces_body<REC, true>(P, sums, W, nwe, rx, ry, Fx, Fy, mt4, blockIdx.x * blockDim.x + threadIdx.x);
+  else
+    faces_body<REC, false>(P, sums, W, nwe, rx, ry, Fx, Fy, mt4, blockIdx.x * blockDim.x + threadIdx.x);
 }
+
 
 // -------------------------------------------------------------------------------------
 // Eq. 4 per cell, plus g^n, g^{n+1}, tau^n, tau^{n+1} for Eq. 3, residual partials and
