@@ -271,6 +271,33 @@ def split_bench(ugks, torch, stream, warmup, grids=(101, 201)):
     return {"unit": UNIT, "grids": out}
 
 
+def shakhov_bench(ugks, torch, stream, cfg, prim, warmup, steps=10):
+    """The Shakhov model (Pr = 2/3) on the bench workload: FP32-f and FP64 step times."""
+    shk = cfg.replace(pr=2.0 / 3.0, name=cfg.name + "_pr0.667")
+    out = {"workload": shk.name, "pr": shk.pr, "vc_per_step": shk.vc}
+    for prec, name, n in ((ugks.FP32F, "fp32f", steps), (ugks.FP64, "fp64", 2)):
+        s = ugks.Solver(shk, prec, stream=stream.cuda_stream)
+        s.init_maxwellian(*prim)
+        s.step(warmup)
+        s.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(n)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        s.profile(True)
+        s.step(max(1, n // 2))
+        kt = s.kernel_times()
+        s.profile(False)
+        s.close()
+        torch.cuda.empty_cache()
+        out[name] = {"ms_per_step": ms, "value": shk.vc / (ms * 1e-3), "steps": n,
+                     "kernel_ms_per_step": {k: kt[k][1] / max(kt[k][0], 1) for k in KERNELS}}
+    return out
+
+
 def batch_bench(ugks, torch, stream, steps, warmup):
     """Uneven batch: 64 channel instances drawn log-uniform (meshes 50x25..400x200,
     16^2..64^2 velocities, Kn 1e-3..1, inlet rho 1.05..1.5), FP32-f, stepped together;
@@ -473,6 +500,8 @@ def main():
         batch = None if args.no_batch else batch_bench(ugks, torch, stream, args.steps, args.warmup)
         large = None if args.no_large_velocity else large_velocity_bench(ugks, torch, stream, args.warmup)
         split = None if args.no_large_velocity else split_bench(ugks, torch, stream, args.warmup)
+        shakhov = None if args.no_large_velocity else shakhov_bench(ugks, torch, stream, cfg, prim,
+                                                                     args.warmup)
         serving = None if (args.no_serve or ws > 1) else serve_bench(ugks, stream)
 
     def form_json(prec):
@@ -569,6 +598,7 @@ def main():
         "serving": serving,
         "large_velocity": large,
         "sums_split": split,
+        "shakhov": shakhov,
     }
     if batch:
         batch["vs_fp64_single"] = batch["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])
