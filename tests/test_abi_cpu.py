@@ -82,3 +82,26 @@ def test_state_bytes_without_gpu():
     stage = 2 * (32 << 20)  # the two staging halves of the host-state conversion
     assert big32 < b32 < big32 + stage + 2000 * (ring + faces)
     assert ugks.state_bytes(I.channel_config(nx=80, ny=40, n_vel=20), ugks.FP64) > b64
+
+
+def test_shakhov_configuration_without_gpu():
+    """The Prandtl number is validated before any CUDA call: a non-finite pr and the
+    Shakhov model in the DF64 form are rejected; the Shakhov model adds its heat-flux
+    moment sums (56 doubles per cell of the sums ring) and, in the FP32-f form, the cells'
+    Shakhov records (96 bytes per cell) to the device bytes."""
+    import math
+
+    from paper_1810_08137_gb300 import inputs as I
+    from paper_1810_08137_gb300 import ugks
+    cfg = I.channel_config(nx=40, ny=20, n_vel=20)
+    for pr, prec in ((math.nan, ugks.FP64), (2.0 / 3.0, ugks.DF64)):
+        with pytest.raises(ugks.UGKSError) as e:
+            ugks.Solver(cfg.replace(pr=pr), prec)
+        assert e.value.status == 1
+    wring, nc = 42 * 22, 40 * 20
+    shk = cfg.replace(pr=2.0 / 3.0)
+    assert ugks.state_bytes(shk, ugks.FP64) - ugks.state_bytes(cfg, ugks.FP64) == 56 * 8 * wring
+    assert (ugks.state_bytes(shk, ugks.FP32F) - ugks.state_bytes(cfg, ugks.FP32F)
+            == 56 * 8 * wring + 96 * nc)
+    # a zero-initialised pr (<= 0) is BGK
+    assert ugks.state_bytes(cfg.replace(pr=0.0), ugks.FP64) == ugks.state_bytes(cfg, ugks.FP64)
