@@ -301,7 +301,9 @@ ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms);
  * is off limits, such as inside a host framework that owns every device allocation, or
  * where an allocation could block or fail at an awkward time -- and who therefore cannot
  * use ugks_create.  The paper has no counterpart; it is an interface convenience.
- *   cfg          problem statement; cfg->precision must be UGKS_FP64.
+ *   cfg          problem statement; cfg->precision must be UGKS_FP64, and the collision
+ *                model BGK (cfg->pr <= 0 or 1: the Shakhov model's extra sums need
+ *                ugks_create).
  *   f_in, W_in   device state at t^n, layouts f[nc][nq][2], W[4][nc] (FP64), read only.
  *   f_out, W_out device buffers for t^{n+1}, same layouts; must not overlap the inputs.
  *   cuda_stream  cudaStream_t or NULL.  The call is synchronous: it waits for its own work
@@ -318,7 +320,7 @@ ugks_status ugks_batch_tune(ugks_batch b, int trial_steps, double* best_ms);
  * on a device, and the first call after a reset, before any stream capture.  Every call
  * shares the array: calls that overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.
- * Errors: UGKS_EINVAL (bad or oversize cfg, NULL pointer), UGKS_ECUDA, UGKS_ENUMERIC. */
+ * Errors: UGKS_EINVAL (bad or oversize cfg, pr != 1, NULL pointer), UGKS_ECUDA, UGKS_ENUMERIC. */
 #define UGKS_NOALLOC_SCRATCH_BYTES (64u << 20)
 ugks_status ugks_step_noalloc(const ugks_config* cfg, const double* f_in, const double* W_in,
                               double* f_out, double* W_out, void* cuda_stream);
