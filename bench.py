@@ -55,7 +55,7 @@ FP64_SUMS_FLOPS_PER_VC = 2 * 43.4 + 13.3 + 18.4
 # capture of the current kernel summarised in profiles/fp32f_step_kernels_channel_400x200_v28.md
 # (dram__bytes_read.sum + dram__bytes_write.sum of one kb_strip launch at 400x200x28^2);
 # set to None when the kernel changes until it is captured again.
-UPDATE_TRAFFIC_PER_VC = (601.332224e6 + 465.995264e6) / 62.72e6
+UPDATE_TRAFFIC_PER_VC = (601.562112e6 + 465.784064e6) / 62.72e6
 
 
 class Clocks:
