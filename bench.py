@@ -56,6 +56,12 @@ FP64_SUMS_FLOPS_PER_VC = 2 * 43.4 + 13.3 + 18.4
 # (dram__bytes_read.sum + dram__bytes_write.sum of one kb_strip launch at 400x200x28^2);
 # set to None when the kernel changes until it is captured again.
 UPDATE_TRAFFIC_PER_VC = (601.562112e6 + 465.784064e6) / 62.72e6
+# FP32 lane operations of the FP32-f update kernel per velocity-cell on the FMA pipe (a packed
+# pair instruction = 2), from the same capture's instruction mix: FFMA2 43.4, FMUL2 15.0,
+# FADD2 6.6, FFMA 5.0, FADD 3.4, FMUL 1.4 per velocity-cell; the peak is the FMA pipe's
+# 128 FP32 lanes per SM per clock on 152 SMs at the 2070 MHz maximum clock.
+UPDATE_FP32_OPS_PER_VC = 2 * (43.4 + 15.0 + 6.6) + 5.0 + 3.4 + 1.4
+FP32_LANE_OPS_PEAK = 152 * 128 * 2.07e9
 
 
 class Clocks:
@@ -530,6 +536,10 @@ def main():
             roof = {"bound": "hbm", "kernel": "update", "achieved": ach_up, "peak": hbm,
                     "unit": "GB/s", "frac": ach_up / hbm, "traffic": traffic,
                     "peak_source": hbm_src, "algorithmic_bytes_per_vc": 2 * bpv}
+            ops = UPDATE_FP32_OPS_PER_VC * cfg.vc / t_launch
+            roof["alu"] = {"bound": "alu (FP32 FMA pipe)", "achieved": ops / 1e12,
+                           "peak": FP32_LANE_OPS_PEAK / 1e12, "unit": "T FP32 lane-ops/s",
+                           "frac": ops / FP32_LANE_OPS_PEAK, "ops_per_vc": UPDATE_FP32_OPS_PER_VC}
             roof_sums = {"achieved": ach_sm, "frac": ach_sm / hbm, "unit": "GB/s",
                          "algorithmic_bytes_per_vc": bpv}
         else:
