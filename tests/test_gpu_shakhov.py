@@ -136,8 +136,10 @@ def test_shakhov_channel_50_steps_fp32f(U, oracle):
     assert np.all(ew <= 1e-5), ew
 
 
-def test_shakhov_batch_alone_equals_mix(U):
-    """A Shakhov instance steps bitwise the same alone and in a batch with BGK instances."""
+@pytest.mark.parametrize("persistent", [True, False], ids=["persistent", "phases"])
+def test_shakhov_batch_alone_equals_mix(U, persistent):
+    """A Shakhov instance steps bitwise the same alone and in a batch with BGK instances, in
+    both step modes (one persistent launch; the phase launches)."""
     shk = _channel(nx=20, ny=10, n_vel=16, kn=0.05, name="shk")
     bgk = I.channel_config(nx=30, ny=15, n_vel=20, kn=0.1, name="bgk")
     prim_s = I.initial_prim(shk, I.seed_for(5, 1))
@@ -147,6 +149,7 @@ def test_shakhov_batch_alone_equals_mix(U):
         s.step(7)
         f_alone, W_alone = s.get_state()
     with U.Batch(4) as B:
+        B.set_persistent(persistent)
         a = B.admit(bgk)
         b = B.admit(shk)
         B.instance(a).init_maxwellian(*prim_b)
