@@ -577,7 +577,7 @@ def main():
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (f) + f64 (moments, W, interface scalars)" if main_prec == ugks.FP32F else "f64",
+        "dtype": "f32 (f) + f64 (velocity sums across f32 chunks, W, cell scalars) + f64/double-f32 (interface scalars)" if main_prec == ugks.FP32F else "f64",
         "data": "synthetic",
         "config": {"workload": cfg.name, "cells": cfg.nc, "velocities": cfg.nq,
                    "vc_per_step": cfg.vc, "kn": cfg.kn, "precision": args.prec,
