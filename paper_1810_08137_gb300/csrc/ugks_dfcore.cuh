@@ -45,13 +45,42 @@ __device__ __forceinline__ double f64_of(float x) {
   const unsigned lw = big ? 0u : (m << 29);
   return m >= 0x00800000u ? __hiloint2double((int)hw, (int)lw) : 0.0;
 }
-// FP64 -> normalised pair: the cut high part, the remainder (exact in FP64) rounded to FP32,
-// renormalised (|lo| <= ulp(hi) / 2); |a - (hi + lo)| <= 2^-48 |a| or so
+// FP64 -> FP32 rounded to nearest (ties to even) on the integer pipe: the binary64
+// significand rounded at its bit 29 (round bit 28, sticky bits 0..27), the exponent rebiased
+// by 896 (a carry out of the significand increments the exponent, as rounding requires).
+// Equal to the conversion instruction for results in the FP32 normal range; below it the
+// result is a signed zero, above it (and for infinities) the signed infinity; NaN stays NaN.
+__device__ __forceinline__ float f32_rn(double a) {
+  const long long b = __double_as_longlong(a);
+  const unsigned hw = (unsigned)((unsigned long long)b >> 32), lw = (unsigned)b;
+  const unsigned m = hw & 0x7fffffffu, sg = hw & 0x80000000u;
+  const unsigned up = ((lw & 0x10000000u) != 0u && (lw & 0x2fffffffu) != 0u) ? 1u : 0u;
+  const unsigned rb = (((m - 0x38000000u) << 3) | (lw >> 29)) + up;
+  const bool normal = m >= 0x38100000u, fin = m < 0x47f00000u;
+  const bool nan = m > 0x7ff00000u || (m == 0x7ff00000u && lw != 0u);
+  return __uint_as_float(fin ? (normal ? sg | rb : sg) : (sg | (nan ? 0x7fc00000u : 0x7f800000u)));
+}
+// FP64 -> normalised pair: the cut high part, the remainder rounded to FP32, renormalised
+// (|lo| <= ulp(hi) / 2); |a - (hi + lo)| is a few 2^-48 |a|.  The remainder a - cut(a) is
+// +-(the 29 low significand bits) 2^(E - 1075) (E the biased exponent): its FP32 rounding is
+// formed without the FP64 pipe, the 29-bit integer rounded to 24 bits by one FMA of its two
+// exact FP32 pieces (23 and 6 bits, each read off the bits of 2^23 + n) and then scaled by
+// powers of two.  For |a| < 2^-103 (E < 920, where that scale leaves the FP32 normal range) the
+// remainder is dropped: such values keep 24 bits (they only arise next to terms of order one).
 __device__ __forceinline__ void split_f64(double a, float& hi, float& lo) {
   double cd;
   float cf;
   f32_cut(a, cd, cf);
-  const float r = __double2float_rn(a - cd);
+  const long long b = __double_as_longlong(a);
+  const unsigned hw = (unsigned)((unsigned long long)b >> 32), lw = (unsigned)b;
+  const unsigned m = hw & 0x7fffffffu, sg = hw & 0x80000000u, E = m >> 20;
+  const unsigned ml = lw & 0x1fffffffu;
+  const float na = __fsub_rn(__uint_as_float(0x4b000000u | (ml >> 23)), 8388608.f);
+  const float nb = __fsub_rn(__uint_as_float(0x4b000000u | (ml & 0x7fffffu)), 8388608.f);
+  const float v = __fmaf_rn(na, 8388608.f, nb);  // ml rounded to 24 bits
+  const bool scaled = E >= 920u && m < 0x47f00000u;
+  const float sc = __uint_as_float(sg | ((scaled ? E - 919u : 1u) << 23));  // +-2^(E - 1046)
+  const float r = scaled ? __fmul_rn(__fmul_rn(v, 0x1p-29f), sc) : 0.f;
   const float s = __fadd_rn(cf, r);
   hi = s;
   lo = __fsub_rn(r, __fsub_rn(s, cf));

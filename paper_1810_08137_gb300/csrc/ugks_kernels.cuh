@@ -654,44 +654,28 @@ __host__ __device__ constexpr double inv_factorial(int n) {
 
 // Time integrals over one step of the Eq. 2 weights, x = dt/tau:
 //   Mt1 = dt c1, Mt2 = dt^2 c2, Mt3 = dt^2 c3, Mt4 = dt c4, Mt5 = dt^2 c5
-//   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x,
-// by their Taylor series below x = 0.1 (no cancellation there).
-// Power series of the c_k in y = -x by Horner, NT terms: c4 = sum y^n/(n+1)!,
-// c5 = sum (n+1) y^n/(n+2)!, c1 = x sum y^n/(n+2)!, c3 = x sum y^n/(n+3)!,
-// c2 = -x sum (n+1) y^n/(n+3)!.
+//   c4 = (1-e^{-x})/x, c1 = 1-c4, c5 = (c4-e^{-x})/x, c3 = 1/2 - c1/x, c2 = c5 - c1/x.
+// Below x = 0.1 they come from the functions phi_k(y) = sum_n y^n/(n+k)! at y = -x (the
+// exponential-integrator phi functions, phi_k = 1/k! + y phi_{k+1}): phi_3 by its power series
+// (Horner, NT terms), then phi_2 = 1/2 - x phi_3 and phi_1 = 1 - x phi_2, none of which
+// cancels for x < 0.1; in terms of them c4 = phi_1, c1 = x phi_2, c3 = x phi_3,
+// c5 = sum (n+1) y^n/(n+2)! = phi_1 - phi_2 and c2 = -x sum (n+1) y^n/(n+3)! =
+// -x (phi_2 - 2 phi_3), since (n+1)/(n+2)! = 1/(n+1)! - 1/(n+2)! and
+// (n+1)/(n+3)! = 1/(n+2)! - 2/(n+3)!.
 template <int NT>
-__device__ __forceinline__ void time_series_145(double y, double& h4, double& h5, double& h1) {
-  h4 = 0.0, h5 = 0.0, h1 = 0.0;
+__device__ __forceinline__ double phi3_series(double y) {
+  double h = 0.0;
 #pragma unroll
-  for (int n = NT - 1; n >= 0; n--) {
-    h4 = h4 * y + inv_factorial(n + 1);
-    h5 = h5 * y + (n + 1) * inv_factorial(n + 2);
-    h1 = h1 * y + inv_factorial(n + 2);
-  }
-}
-template <int NT, typename T>
-__device__ __forceinline__ void time_series_23(T y, T& h3, T& h2) {
-  h3 = T(0), h2 = T(0);
-#pragma unroll
-  for (int n = NT - 1; n >= 0; n--) {
-    h3 = h3 * y + T(inv_factorial(n + 3));
-    h2 = h2 * y + T((n + 1) * inv_factorial(n + 3));
-  }
+  for (int n = NT - 1; n >= 0; n--) h = h * y + inv_factorial(n + 3);
+  return h;
 }
 __device__ void time_weights(double dt, double x, double* Mt) {
   double c1, c2, c3, c4, c5;
   if (x < 0.1) {
-    // 8 terms below x = 0.01, 12 below 0.1: the first term left out is below 1e-20 and
-    // 1e-22 relative
-    double h4, h5, h1, h3, h2;
-    if (x < 0.01) {
-      time_series_145<8>(-x, h4, h5, h1);
-      time_series_23<8>(-x, h3, h2);
-    } else {
-      time_series_145<12>(-x, h4, h5, h1);
-      time_series_23<12>(-x, h3, h2);
-    }
-    c4 = h4; c5 = h5; c1 = x * h1; c3 = x * h3; c2 = -x * h2;
+    // 8 terms below x = 0.01, 12 below 0.1: the first term left out is below 1e-23 of phi_3
+    const double p3 = x < 0.01 ? phi3_series<8>(-x) : phi3_series<12>(-x);
+    const double p2 = 0.5 - x * p3, p1 = 1.0 - x * p2;
+    c4 = p1; c5 = p1 - p2; c1 = x * p2; c3 = x * p3; c2 = -x * (p2 - 2.0 * p3);
   } else {
     const double e = exp(-x), em = -expm1(-x), ix = 1.0 / x;
     c4 = em * ix;
@@ -972,7 +956,8 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
 // FP32-f form: the interface (face_core with its polynomial work in double-FP32: primitive
 // variables, half-range moments, Mt1..Mt5, micro-slope solves, compatibility condition,
 // macroscopic flux), then the FP32 record its update walk reads.  The record is rounded to
-// FP32 from the double-FP32 slopes and FP64 weights: the walk applies it to FP32 f.
+// FP32 from the double-FP32 slopes and FP64 weights (f32_rn: on the integer pipe, not the
+// 1/64-rate FP64 pipe the conversion instruction runs on): the walk applies it to FP32 f.
 __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0, const double* St,
                                               const double* Sf, const double* Ss, const double* WL,
                                               const double* WR, double tdelta, bool isx, double* F,
@@ -981,10 +966,10 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   face_core<dd>(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c, qsh);
   const double* Mt = c.Mt;
   Mt4 = Mt[3];
-  const float fM1 = (float)Mt[0], fM2 = (float)Mt[1], fM3 = (float)Mt[2];
-  const float fX2 = (float)c.X2;
-  const float fG = (float)(c.rho * c.lam / kPi);
-  const float kap = (float)(0.5 * (c.X4 - c.X2 * c.X2));  // (X4 - X2^2)/2 = K/(4 lam^2)
+  const float fM1 = f32_rn(Mt[0]), fM2 = f32_rn(Mt[1]), fM3 = f32_rn(Mt[2]);
+  const float fX2 = f32_rn(c.X2);
+  const float fG = f32_rn(c.rho * c.lam / kPi);
+  const float kap = f32_rn(0.5 * (c.X4 - c.X2 * c.X2));  // (X4 - X2^2)/2 = K/(4 lam^2)
   float aL[4], aR[4], b[4], A[4];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -1048,12 +1033,12 @@ __device__ __forceinline__ void face_math_f32(const Params& P, const double* W0,
   }
   constexpr double kLog2e = 1.4426950408889634;
   const double lam = c.lam, Ux = isx ? c.U : c.V, Vy = isx ? c.V : c.U;
-  RF.E[0] = (float)(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
-  RF.E[1] = (float)(2.0 * lam * Ux * kLog2e);
-  RF.E[2] = (float)(2.0 * lam * Vy * kLog2e);
-  RF.E[3] = (float)(-lam * kLog2e);
-  RF.Mt4 = (float)Mt[3];
-  RF.nMt5 = (float)(-Mt[4]);
+  RF.E[0] = f32_rn(-lam * (Ux * Ux + Vy * Vy) * kLog2e);
+  RF.E[1] = f32_rn(2.0 * lam * Ux * kLog2e);
+  RF.E[2] = f32_rn(2.0 * lam * Vy * kLog2e);
+  RF.E[3] = f32_rn(-lam * kLog2e);
+  RF.Mt4 = f32_rn(Mt[3]);
+  RF.nMt5 = f32_rn(-Mt[4]);
   RF.wall = 0.f;
   RF.gdt = 0.f;
   RF.pad[0] = RF.pad[1] = RF.pad[2] = RF.pad[3] = 0.f;
