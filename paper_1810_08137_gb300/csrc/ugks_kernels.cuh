@@ -752,7 +752,7 @@ __device__ __forceinline__ void wall_face_f32(const Params& P, bool isx, double 
 // Arithmetic: the primitive variables, exp and erfc of the half-range moments, tau and
 // Mt1..Mt5, the slope targets and the free-transport part of F in FP64; the moment
 // recurrences, the micro-slope solves, the compatibility moments and the equilibrium part of
-// F in T: double (FP64 form, DF64 form) or dd, double-FP32 on the FP32 pipe (FP32-f form,
+// F in T: double (FP64 form) or dd, double-FP32 on the FP32 pipe (FP32-f and DF64 forms,
 // about 2^-48 relative per operation, where FP64 would spend ~420 of its ~610 operations per
 // face on the 1/64-rate FP64 pipe).
 template <typename T>
@@ -908,12 +908,23 @@ __device__ __forceinline__ void face_core(const Params& P, const double* W0, con
   }
 }
 
-// FP64 form: the interface (face_core) and its FP64 micro-flux record.
+// FP64 form (T = double) and DF64 form (T = dd: the interface's polynomial work in
+// double-FP32, as in the FP32-f form, then the record's coefficients in FP64): the interface
+// (face_core) and its FP64 micro-flux record (the DF64 form splits it into pairs).
+template <typename T>
 __device__ void face_math(const Params& P, const double* W0, const double* St, const double* Sf,
                           const double* Ss, const double* WL, const double* WR, double tdelta,
                           bool isx, double* F, FaceRec& R, const double* qsh = nullptr) {
-  FaceCore c;
-  face_core(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c, qsh);
+  FaceCoreT<T> c;
+  face_core<T>(P, W0, St, Sf, Ss, WL, WR, tdelta, F, c, qsh);
+  double aL[4], aR[4], bs[4], As[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    aL[k] = to_double(c.aL[k]);
+    aR[k] = to_double(c.aR[k]);
+    bs[k] = to_double(c.b[k]);
+    As[k] = to_double(c.A[k]);
+  }
   const double* Mt = c.Mt;
   const double X2 = c.X2, X4 = c.X4;
   R.G = c.rho * c.lam / kPi;
@@ -927,14 +938,14 @@ __device__ void face_math(const Params& P, const double* W0, const double* St, c
   // S6/S8 coefficients (FP64 record)
   double pa[4], pb[4], pA[4];
   for (int sd = 0; sd < 2; sd++) {
-    const double* as = sd == 0 ? c.aL : c.aR;
+    const double* as = sd == 0 ? aL : aR;
     shape_h(as, X2, pa);
-    shape_h(c.b, X2, pb);
-    shape_h(c.A, X2, pA);
+    shape_h(bs, X2, pb);
+    shape_h(As, X2, pA);
     qcoef(Mt[0], Mt[1], Mt[2], pa, pb, pA, R.Q[sd][0]);
     shape_b(as, X2, X4, pa);
-    shape_b(c.b, X2, X4, pb);
-    shape_b(c.A, X2, X4, pA);
+    shape_b(bs, X2, X4, pb);
+    shape_b(As, X2, X4, pA);
     qcoef(Mt[0] * X2, Mt[1], Mt[2], pa, pb, pA, R.Q[sd][1]);
     if (c.shk) {  // Shakhov: Mt1 g0 S on (1, un, ut, un^2, un ut, ut^2, un r2, ut r2)
       for (int comp = 0; comp < 2; comp++) {
@@ -1183,8 +1194,10 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
     }
     if constexpr (f32)
       face_math_f32(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R.Mt4, RF, qp);
+    else if constexpr (REC == kRecDF)
+      face_math<dd>(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, qp);
     else
-      face_math(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, qp);
+      face_math<double>(P, W0, St, Sf, Ss, WL, WR, tdelta, isx, Fr, R, qp);
 #pragma unroll
     for (int c = 0; c < 4; c++) F[c] = (c == 1 || c == 2) && !isx ? Fr[3 - c] : Fr[c];
   }
@@ -1208,7 +1221,7 @@ __device__ __forceinline__ void faces_body(const Params& P, const double* __rest
 }
 // FP64 form (REC = kRecF64) and DF64 form (REC = kRecDF)
 template <int REC>
-__global__ void k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
+__global__ void __launch_bounds__(128, REC == kRecDF ? 4 : 3) k_faces(Params P, const double* __restrict__ sums, const double* __restrict__ W,
                         int nwe, void* __restrict__ rx, void* __restrict__ ry,
                         double* __restrict__ Fx, double* __restrict__ Fy, double* __restrict__ mt4) {
   if (P.shk)
@@ -1299,27 +1312,27 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
       // the amplitude's log2(G / G_ref) = log2(1 + d), d = G / G_ref - 1 formed in FP64 and
       // log1p in FP32: its error is an ulp of a result that is small where G is near
       // G_ref (an FP32 log2 of G itself put ~1e-7 relative noise on g per cell, visible in
-      // rho V at Kn 0.01)
+      // rho V at Kn 0.01); the record's FP32 fields rounded by f32_rn (integer pipe)
       constexpr float kLog2ef = 1.44269504f;
       const double r0 = P.ref_E0u, r1 = P.ref_E[1], r2 = P.ref_E[2], r3 = P.ref_E[3];
-      const double ldn = (double)(log1pf((float)fma(R.Gn, P.ref_iG, -1.0)) * kLog2ef);
-      const double ld1 = (double)(log1pf((float)fma(R.G1, P.ref_iG, -1.0)) * kLog2ef);
-      F.dEn[0] = (float)((ldn - ln * (Un * Un + Vn * Vn) * kLog2e) - r0);
-      F.dEn[1] = (float)(2.0 * ln * Un * kLog2e - r1);
-      F.dEn[2] = (float)(2.0 * ln * Vn * kLog2e - r2);
-      F.dEn[3] = (float)(-ln * kLog2e - r3);
-      F.dE1[0] = (float)((ld1 - l1 * (U1 * U1 + V1 * V1) * kLog2e) - r0);
-      F.dE1[1] = (float)(2.0 * l1 * U1 * kLog2e - r1);
-      F.dE1[2] = (float)(2.0 * l1 * V1 * kLog2e - r2);
-      F.dE1[3] = (float)(-l1 * kLog2e - r3);
-      F.A1 = (float)(R.inv * R.cg1);
-      F.An = (float)(R.inv * R.cgn);
-      F.db1 = (float)(R.b1 - P.ref_bf);
-      F.dbn = (float)(R.bn - P.ref_bf);
-      F.nBs = (float)(-(R.inv * (R.cg1 + R.cgn)));
-      F.irx = (float)(R.inv * refx);
-      F.iry = (float)(R.inv * refy);
-      F.inv = (float)R.inv;
+      const double ldn = f64_of(log1pf(f32_rn(fma(R.Gn, P.ref_iG, -1.0))) * kLog2ef);
+      const double ld1 = f64_of(log1pf(f32_rn(fma(R.G1, P.ref_iG, -1.0))) * kLog2ef);
+      F.dEn[0] = f32_rn((ldn - ln * (Un * Un + Vn * Vn) * kLog2e) - r0);
+      F.dEn[1] = f32_rn(2.0 * ln * Un * kLog2e - r1);
+      F.dEn[2] = f32_rn(2.0 * ln * Vn * kLog2e - r2);
+      F.dEn[3] = f32_rn(-ln * kLog2e - r3);
+      F.dE1[0] = f32_rn((ld1 - l1 * (U1 * U1 + V1 * V1) * kLog2e) - r0);
+      F.dE1[1] = f32_rn(2.0 * l1 * U1 * kLog2e - r1);
+      F.dE1[2] = f32_rn(2.0 * l1 * V1 * kLog2e - r2);
+      F.dE1[3] = f32_rn(-l1 * kLog2e - r3);
+      F.A1 = f32_rn(R.inv * R.cg1);
+      F.An = f32_rn(R.inv * R.cgn);
+      F.db1 = f32_rn(R.b1 - P.ref_bf);
+      F.dbn = f32_rn(R.bn - P.ref_bf);
+      F.nBs = f32_rn(-(R.inv * (R.cg1 + R.cgn)));
+      F.irx = f32_rn(R.inv * refx);
+      F.iry = f32_rn(R.inv * refy);
+      F.inv = f32_rn(R.inv);
       crf[c] = F;
       if (P.shk) {  // Shakhov factors of g^n and g^{n+1}, global frame
         CellShkF S;
@@ -1331,12 +1344,12 @@ __device__ __forceinline__ void cells_body(const Params& P, const double* __rest
           shakhov_poly(al, Ug, Vg, lg, q, -4.0, p);
           float* sg = g == 0 ? S.sn : S.s1;
           float* lb = g == 0 ? S.ln : S.l1;
-          sg[0] = (float)p[0][0]; sg[1] = (float)p[1][0]; sg[2] = (float)p[0][1]; sg[3] = (float)p[2][0];
-          sg[4] = (float)p[1][1]; sg[5] = (float)p[0][2]; sg[6] = (float)p[3][0]; sg[7] = (float)p[0][3];
+          sg[0] = f32_rn(p[0][0]); sg[1] = f32_rn(p[1][0]); sg[2] = f32_rn(p[0][1]); sg[3] = f32_rn(p[2][0]);
+          sg[4] = f32_rn(p[1][1]); sg[5] = f32_rn(p[0][2]); sg[6] = f32_rn(p[3][0]); sg[7] = f32_rn(p[0][3]);
           const double m = 2.0 * bg * al;
-          lb[0] = (float)(-m * (q[0] * Ug + q[1] * Vg));
-          lb[1] = (float)(m * q[0]);
-          lb[2] = (float)(m * q[1]);
+          lb[0] = f32_rn(-m * (q[0] * Ug + q[1] * Vg));
+          lb[1] = f32_rn(m * q[0]);
+          lb[2] = f32_rn(m * q[1]);
           lb[3] = 0.f;
         }
         P.cshk[c] = S;
