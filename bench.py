@@ -200,9 +200,25 @@ def cpu_baseline(cfg, prim, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s / 2 or n >= 3:
             break
     t = time.perf_counter() - t0
-    return {"value": cfg.vc * n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+    value = cfg.vc * n / t
+    # the same oracle on one thread: one step of a band of rows of the same channel (same
+    # velocity grid, Kn, boundaries) sized to about budget_s / 4 of single-thread work
+    oracle.set_threads(1)
+    per_thread = value / cores
+    ny_s = max(2, min(cfg.ny, int(cfg.ny * (budget_s / 4) * per_thread / cfg.vc)))
+    sub = cfg.replace(ny=ny_s, ly=cfg.ly * ny_s / cfg.ny)
+    sp = [x.reshape(cfg.ny, cfg.nx)[:ny_s].reshape(-1) for x in prim]
+    fs, Ws = oracle.init_maxwellian(sub, *sp)
+    t0 = time.perf_counter()
+    oracle.step(sub, fs, Ws, 1)
+    t1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} full step(s) of {cfg.name} ({cfg.vc} vc/step), FP64 C oracle, "
-                      f"OpenMP over faces and cells"}
+                      f"OpenMP over faces and cells",
+            "single_thread": {"value": sub.vc / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 step of a {sub.nx}x{sub.ny} band of {cfg.name} "
+                                        f"({sub.vc} vc)"}}
 
 
 def large_velocity_bench(ugks, torch, stream, warmup, grids=(51, 101, 151, 201)):
