@@ -47,3 +47,30 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.job_value(1, 100, 4, 2.0) == pytest.approx(100 * 4 / 2e-3)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores) runs without a GPU and
+    prints one JSON line with the keys of the benchmark line; a small mesh keeps it short."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--mesh", "100", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "vc/s"
+    assert d["metric"] == bench_metric() and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] >= 3 and d["n_gpus"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "channel_100x50_v28"
+
+
+def bench_metric():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.METRIC
