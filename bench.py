@@ -612,7 +612,8 @@ def main():
                        "step_hbm_frac": other["step_hbm_frac"],
                        "clocks": other["clocks"]},
         "df64_form": dict(dff, precision="df64: FP64-accurate, double-FP32 f and per-velocity "
-                                          "arithmetic on the FP32 pipe, FP64 interface and cell scalars",
+                                          "arithmetic on the FP32 pipe, interface in FP64 / "
+                                          "double-FP32, FP64 cell scalars",
                           vs_fp64=dff["value"] / (other["value"] if other_prec == ugks.FP64 else main["value"])),
         "vs_fp64": (main["value"] / other["value"]) if main_prec == ugks.FP32F else 1.0,
         "clocks": main["clocks"],
